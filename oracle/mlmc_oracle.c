@@ -1,0 +1,549 @@
+/*
+ * CPU oracle for the multilevel Monte Carlo estimator of x = exp(beta A) u
+ * (Acebron, Herrero, Monteiro, "A highly parallel algorithm for computing the
+ * action of a matrix exponential on a vector based on a multilevel Monte Carlo
+ * method").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Plain, slow, written to be checked against the
+ * paper by eye.  Only the test suite, the smoke check and the benchmark's CPU
+ * baseline leg may load it.  It shares no code with the GPU library.
+ *
+ * Contents
+ *   - Philox4x32-10 counter-based generator (Salmon, Moraes, Dror, Shaw,
+ *     "Parallel random numbers: as easy as 1, 2, 3", SC'11).
+ *   - neglog: -ln(u) from the series ln m = 2 atanh((m-1)/(m+1)), written out
+ *     so that both sides of a replay comparison make identical decisions.
+ *   - The splitting A = D - T of Sec. 2.1 (Eq. 1): a_ii, L_ii, d_i.
+ *   - Per-row Vose alias tables for the jump law k_ij = |a_ij| / L_ii
+ *     (Sec. 3, Eq. 12).
+ *   - The walk of Algorithm 2 (MLMCL), one interval of length Delta t_l at a
+ *     time, with the coupled fine (eta_2) and coarse (eta_1) weights, plus the
+ *     paired-step form of Eq. 7 (Lemma 2's xi_j) for an accurate difference.
+ *
+ * Readings of the paper taken here (the GPU path makes the same ones):
+ *   R1  every holding time uses the rate L_jj of the state being occupied
+ *       (the CTMC of Eq. 12); the listing draws S before the new state is
+ *       chosen, which read literally uses the old state's rate.  Variant
+ *       ORC_LITERAL_RATE reproduces that literal reading for comparison.
+ *   R2  one exponential clock per holding segment, carried across interval
+ *       boundaries (equal in law to redrawing tau at each interval, by
+ *       memorylessness).  Variant ORC_REDRAW redraws per interval as the
+ *       listing does.
+ *   R3  scaled time s = tau/beta in [0,1]: rate beta*L_jj, grid points k/N.
+ *       A jump at exactly s = k/N happens after grid point k is sampled; a
+ *       jump at s >= 1 is not taken.
+ *
+ * Build: gcc -O2 -fopenmp -ffp-contract=off -shared -fPIC (FMA contraction
+ * must be off so that every rounding is the IEEE one written here).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------ */
+/* Philox4x32-10                                                       */
+/* ------------------------------------------------------------------ */
+#define ORC_PHILOX_M0 0xD2511F53u
+#define ORC_PHILOX_M1 0xCD9E8D57u
+#define ORC_PHILOX_W0 0x9E3779B9u
+#define ORC_PHILOX_W1 0xBB67AE85u
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += ORC_PHILOX_W0;
+            k1 += ORC_PHILOX_W1;
+        }
+        uint64_t p0 = (uint64_t)ORC_PHILOX_M0 * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)ORC_PHILOX_M1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* ------------------------------------------------------------------ */
+/* Uniforms and -ln(u)                                                 */
+/* ------------------------------------------------------------------ */
+/* u = (2k+1) 2^-53 with k the top 52 bits of (x0:x1): exact, in (0,1). */
+double orc_uniform64(uint32_t x0, uint32_t x1)
+{
+    uint64_t w = ((uint64_t)x0 << 32) | (uint64_t)x1;
+    return (double)((w >> 11) | 1ull) * 0x1p-53;
+}
+
+/* u = (2k+1) 2^-24 with k the top 23 bits of x0: exact, in (0,1). */
+float orc_uniform32(uint32_t x0)
+{
+    return (float)((x0 >> 8) | 1u) * 0x1p-24f;
+}
+
+/* ln 2 split so that e*LN2_HI is exact for |e| < 2^11 (FP64) or 2^8 (FP32). */
+static const double ORC_LN2_HI64 = 0x1.62e42fefa3800p-1;
+static const double ORC_LN2_LO64 = 0x1.ef35793c76730p-45;
+static const float ORC_LN2_HI32 = 0x1.62e400p-1f;
+static const float ORC_LN2_LO32 = 0x1.7f7d1cp-20f;
+static const double ORC_SQRT_HALF64 = 0x1.6a09e667f3bcdp-1;
+static const float ORC_SQRT_HALF32 = 0x1.6a09e6p-1f;
+
+#define ORC_NEGLOG_TERMS64 12
+#define ORC_NEGLOG_TERMS32 6
+static double orc_c64[ORC_NEGLOG_TERMS64];
+static float orc_c32[ORC_NEGLOG_TERMS32];
+static int orc_coeffs_ready = 0;
+
+static void orc_init_coeffs(void)
+{
+    if (orc_coeffs_ready) return;
+    for (int k = 0; k < ORC_NEGLOG_TERMS64; ++k) orc_c64[k] = 1.0 / (double)(2 * k + 1);
+    for (int k = 0; k < ORC_NEGLOG_TERMS32; ++k) orc_c32[k] = 1.0f / (float)(2 * k + 1);
+    orc_coeffs_ready = 1;
+}
+
+/* -ln(u) for normal u in (0,1).  u = m 2^e with m in [sqrt(1/2), sqrt(2));
+ * ln m = 2 z (1 + z^2/3 + z^4/5 + ...), z = (m-1)/(m+1), |z| <= 0.1716,
+ * 12 terms (FP64).  ln u = e ln2 + ln m. */
+double orc_neglog64(double u)
+{
+    orc_init_coeffs();
+    uint64_t b;
+    memcpy(&b, &u, sizeof b);
+    int e = (int)((b >> 52) & 0x7ff) - 1022;
+    b = (b & 0x000fffffffffffffull) | (0x3feull << 52);
+    double m;
+    memcpy(&m, &b, sizeof m);
+    if (m < ORC_SQRT_HALF64) {
+        m = m * 2.0;
+        e = e - 1;
+    }
+    double z = (m - 1.0) / (m + 1.0);
+    double z2 = z * z;
+    double p = orc_c64[ORC_NEGLOG_TERMS64 - 1];
+    for (int k = ORC_NEGLOG_TERMS64 - 2; k >= 0; --k) p = p * z2 + orc_c64[k];
+    double lnm = (2.0 * z) * p;
+    double lnu = (double)e * ORC_LN2_HI64 + ((double)e * ORC_LN2_LO64 + lnm);
+    return -lnu;
+}
+
+/* FP32 version: same construction, 6 terms. */
+float orc_neglog32(float u)
+{
+    orc_init_coeffs();
+    uint32_t b;
+    memcpy(&b, &u, sizeof b);
+    int e = (int)((b >> 23) & 0xff) - 126;
+    b = (b & 0x007fffffu) | (0x7eu << 23);
+    float m;
+    memcpy(&m, &b, sizeof m);
+    if (m < ORC_SQRT_HALF32) {
+        m = m * 2.0f;
+        e = e - 1;
+    }
+    float z = (m - 1.0f) / (m + 1.0f);
+    float z2 = z * z;
+    float p = orc_c32[ORC_NEGLOG_TERMS32 - 1];
+    for (int k = ORC_NEGLOG_TERMS32 - 2; k >= 0; --k) p = p * z2 + orc_c32[k];
+    float lnm = (2.0f * z) * p;
+    float lnu = (float)e * ORC_LN2_HI32 + ((float)e * ORC_LN2_LO32 + lnm);
+    return -lnu;
+}
+
+void orc_neglog64_batch(const double *u, double *out, int64_t count)
+{
+    for (int64_t i = 0; i < count; ++i) out[i] = orc_neglog64(u[i]);
+}
+
+void orc_neglog32_batch(const float *u, float *out, int64_t count)
+{
+    for (int64_t i = 0; i < count; ++i) out[i] = orc_neglog32(u[i]);
+}
+
+/* ------------------------------------------------------------------ */
+/* Splitting A = D - T (Sec. 2.1, Eq. 1)                               */
+/* ------------------------------------------------------------------ */
+/* Per row i, scanning the CSR row in stored order:
+ *   a_ii   = the diagonal entry (0 if absent)
+ *   L_ii   = sum_{j != i} |a_ij|      (FP64, left to right)
+ *   deg_i  = number of stored off-diagonal entries
+ *   d_i    = a_ii + L_ii
+ * and the scaled quantities used by the walk in scaled time s = tau/t:
+ *   rate_i = t L_ii,   dl_i = t d_i,   inv_rate_i = 1/rate_i (inf if 0),
+ *   inv_rate32_i = (float)inv_rate_i,  dl32_i = (float)dl_i.            */
+int orc_split(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
+              double t, double *a_ii, double *L, int32_t *deg, double *dl,
+              double *inv_rate, float *inv_rate32, float *dl32)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double diag = 0.0, lsum = 0.0;
+        int32_t k = 0;
+        for (int64_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p) {
+            if ((int64_t)col[p] == i) {
+                diag = val[p];
+            } else {
+                lsum = lsum + fabs(val[p]);
+                k = k + 1;
+            }
+        }
+        a_ii[i] = diag;
+        L[i] = lsum;
+        deg[i] = k;
+        double rate = t * lsum;
+        dl[i] = t * (diag + lsum);
+        inv_rate[i] = (rate > 0.0) ? 1.0 / rate : INFINITY;
+        inv_rate32[i] = (float)inv_rate[i];
+        dl32[i] = (float)dl[i];
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Alias tables for the jump law k_ij = |a_ij| / L_ii (Eq. 12)         */
+/* ------------------------------------------------------------------ */
+/* Row i's off-diagonal entries, in stored order, become buckets
+ * b = 0..deg_i-1 stored at positions row_ptr[i] + b.  Vose's method:
+ *   p_b = (|a_b| * deg) / L_ii in FP64;
+ *   small = FIFO of b with p_b < 1, large = FIFO of b with p_b >= 1, both
+ *   filled in ascending b;
+ *   while both non-empty: l = pop(small), g = pop(large);
+ *       prob_l = p_l, alias_l = g;  p_g = (p_g + p_l) - 1;
+ *       push g to small if p_g < 1 else to large;
+ *   every bucket left in either queue keeps itself with probability 1.
+ * threshold_b = min(floor(prob_b 2^32), 2^32 - 1); a draw keeps bucket b's
+ * own column when x3 < threshold_b and takes the alias column otherwise.
+ * A row with L_ii = 0 (every off-diagonal stored as zero) never jumps; its
+ * buckets keep themselves. */
+int orc_alias(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
+              const double *L, const int32_t *deg, uint32_t *thr, int32_t *keep_col,
+              uint8_t *keep_neg, int32_t *alias_col, uint8_t *alias_neg)
+{
+    int64_t max_deg = 0;
+    for (int64_t i = 0; i < n; ++i)
+        if (deg[i] > max_deg) max_deg = deg[i];
+    double *p = (double *)malloc(sizeof(double) * (size_t)(max_deg + 1));
+    int32_t *bcol = (int32_t *)malloc(sizeof(int32_t) * (size_t)(max_deg + 1));
+    uint8_t *bneg = (uint8_t *)malloc((size_t)(max_deg + 1));
+    int32_t *small = (int32_t *)malloc(sizeof(int32_t) * (size_t)(max_deg + 1));
+    int32_t *large = (int32_t *)malloc(sizeof(int32_t) * (size_t)(max_deg + 1));
+    double *prob = (double *)malloc(sizeof(double) * (size_t)(max_deg + 1));
+    int32_t *alias = (int32_t *)malloc(sizeof(int32_t) * (size_t)(max_deg + 1));
+    if (!p || !bcol || !bneg || !small || !large || !prob || !alias) return -1;
+
+    for (int64_t i = 0; i < n; ++i) {
+        int32_t k = deg[i];
+        if (k == 0) continue;
+        int32_t b = 0;
+        for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q) {
+            if ((int64_t)col[q] == i) continue;
+            bcol[b] = col[q];
+            bneg[b] = (uint8_t)(val[q] < 0.0);
+            p[b] = (L[i] > 0.0) ? (fabs(val[q]) * (double)k) / L[i] : 1.0;
+            ++b;
+        }
+        /* FIFO queues as ring buffers of capacity k (each bucket sits in at
+         * most one queue at a time). */
+        int32_t s_head = 0, s_len = 0, g_head = 0, g_len = 0;
+        for (b = 0; b < k; ++b) {
+            if (p[b] < 1.0) small[(s_head + s_len++) % k] = b;
+            else large[(g_head + g_len++) % k] = b;
+        }
+        while (s_len > 0 && g_len > 0) {
+            int32_t l = small[s_head];
+            s_head = (s_head + 1) % k; s_len--;
+            int32_t g = large[g_head];
+            g_head = (g_head + 1) % k; g_len--;
+            prob[l] = p[l];
+            alias[l] = g;
+            p[g] = (p[g] + p[l]) - 1.0;
+            if (p[g] < 1.0) small[(s_head + s_len++) % k] = g;
+            else large[(g_head + g_len++) % k] = g;
+        }
+        while (g_len > 0) {
+            int32_t g = large[g_head];
+            g_head = (g_head + 1) % k; g_len--;
+            prob[g] = 1.0;
+            alias[g] = g;
+        }
+        while (s_len > 0) {
+            int32_t l = small[s_head];
+            s_head = (s_head + 1) % k; s_len--;
+            prob[l] = 1.0;
+            alias[l] = l;
+        }
+        for (b = 0; b < k; ++b) {
+            double scaled = floor(prob[b] * 4294967296.0);
+            uint32_t th = (scaled >= 4294967295.0) ? 0xFFFFFFFFu : (uint32_t)scaled;
+            int64_t pos = row_ptr[i] + b;
+            thr[pos] = th;
+            keep_col[pos] = bcol[b];
+            keep_neg[pos] = bneg[b];
+            alias_col[pos] = bcol[alias[b]];
+            alias_neg[pos] = bneg[alias[b]];
+        }
+    }
+    free(p); free(bcol); free(bneg); free(small); free(large); free(prob); free(alias);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* The walk (Algorithm 2, MLMCL)                                       */
+/* ------------------------------------------------------------------ */
+/* Variants select the Philox stream (counter word 3, bits 6-7): stream 1 is
+ * reserved for forward-mode walks. */
+enum { ORC_RESIDUAL = 0, ORC_REDRAW = 2, ORC_LITERAL_RATE = 3 };
+enum { ORC_FP64 = 0, ORC_FP32 = 1 };
+enum { ORC_OK = 0, ORC_WALK_LIMIT = 1 };
+
+typedef struct {
+    int64_t n;
+    const int64_t *row_ptr;
+    const int32_t *deg;
+    const double *dl;          /* t d_i */
+    const double *inv_rate;    /* 1/(t L_ii) */
+    const float *inv_rate32;
+    const uint32_t *thr;
+    const int32_t *keep_col;
+    const uint8_t *keep_neg;
+    const int32_t *alias_col;
+    const uint8_t *alias_neg;
+    const double *v;           /* right-hand side u of the paper */
+    uint64_t seed;
+    int32_t precision;         /* ORC_FP64 or ORC_FP32 time arithmetic */
+    int32_t variant;           /* ORC_RESIDUAL, ORC_REDRAW, ORC_LITERAL_RATE */
+    int64_t max_jumps;
+} orc_ctx;
+
+typedef struct {
+    int32_t end;       /* state at s = 1 */
+    int32_t jumps;
+    int32_t sign;      /* product of the jump signs phi */
+    uint32_t hash;     /* FNV-1a over the states entered by each jump */
+    double y;          /* contribution: sign u_end (eta_f - eta_c), or sign u_end eta_f */
+    double y_alg2;     /* the same from Algorithm 2's running products eta_2, eta_1 */
+    double log_f;      /* fine exponent */
+    double log_c;      /* coarse exponent (0 at the coarsest level) */
+    int32_t status;
+    int32_t pad;
+} orc_walk_rec;
+
+/* Counter layout: (rep bits 0-31, row, draw index, level | variant<<6 |
+ * rep bits 32-55 << 8); key = seed.  In the residual-clock walk the draw
+ * index equals the number of jumps taken so far. */
+static void orc_draw(const orc_ctx *c, int64_t row, int64_t rep, uint32_t event, int level,
+                     uint32_t x[4])
+{
+    uint32_t ctr[4], key[2];
+    ctr[0] = (uint32_t)((uint64_t)rep & 0xFFFFFFFFull);
+    ctr[1] = (uint32_t)row;
+    ctr[2] = event;
+    ctr[3] = (uint32_t)level | ((uint32_t)c->variant << 6) |
+             ((uint32_t)(((uint64_t)rep >> 32) & 0xFFFFFFull) << 8);
+    key[0] = (uint32_t)(c->seed & 0xFFFFFFFFull);
+    key[1] = (uint32_t)(c->seed >> 32);
+    orc_philox4x32_10(ctr, key, x);
+}
+
+/* Holding time in state j from draw x, in the walk's time precision, added
+ * to the clock value `from`. */
+static double orc_hold(const orc_ctx *c, int64_t j, const uint32_t x[4], double from)
+{
+    if (c->precision == ORC_FP32) {
+        float s = orc_neglog32(orc_uniform32(x[0])) * c->inv_rate32[j];
+        return (double)((float)from + s);
+    }
+    double s = orc_neglog64(orc_uniform64(x[0], x[1])) * c->inv_rate[j];
+    return from + s;
+}
+
+/* Choose the next state from row j's alias table with draw words x2, x3. */
+static int64_t orc_jump(const orc_ctx *c, int64_t j, const uint32_t x[4], int32_t *sign)
+{
+    uint32_t b = (uint32_t)(((uint64_t)x[2] * (uint64_t)(uint32_t)c->deg[j]) >> 32);
+    int64_t pos = c->row_ptr[j] + b;
+    int64_t to;
+    int neg;
+    if (x[3] < c->thr[pos]) {
+        to = c->keep_col[pos];
+        neg = c->keep_neg[pos];
+    } else {
+        to = c->alias_col[pos];
+        neg = c->alias_neg[pos];
+    }
+    if (neg) *sign = -*sign;
+    return to;
+}
+
+static int orc_before(const orc_ctx *c, double t_next, int64_t n_step, int64_t N)
+{
+    /* t_next < n/N in the time precision (n/N is exact in both). */
+    if (c->precision == ORC_FP32) return (float)t_next < (float)n_step / (float)N;
+    return t_next < (double)n_step / (double)N;
+}
+
+/* One walk of row `row`, replica `rep`, at level `level` (N = 2^level fine
+ * intervals on [0,1]).  coarse != 0: level > l0, so the walk also carries the
+ * coarse weight of level - 1 on the same path (Fig. 1).
+ *
+ * Algorithm 2's loop over n = 1..N: eta_2 (fine) takes e^{d_j dt/2} at both
+ * ends of every interval; eta_1 (coarse) takes e^{d_j dt} at the start of odd
+ * intervals and the end of even ones; between, every jump inside the interval
+ * flips both signs by sigma.  dt d_j is dl_j/N in scaled time.
+ *
+ * The returned y uses the paired-step form (Eq. 7): with X_k the state at
+ * grid point k and pairs (X_{2j-2}, X_{2j-1}, X_{2j}),
+ *   log_f = sum_j dt (d/2 + d + d/2),  log_c = sum_j dt (d + d),
+ *   diff  = sum_j dt (-d_{X_{2j-2}}/2 + d_{X_{2j-1}} - d_{X_{2j}}/2) (xi_j of
+ *           Lemma 2), so y = sign u_end e^{log_c} expm1(diff) avoids the
+ *           cancellation in eta_2 - eta_1. */
+int orc_walk(const orc_ctx *c, int64_t row, int64_t rep, int level, int coarse,
+             orc_walk_rec *out)
+{
+    const int64_t N = (int64_t)1 << level;
+    int64_t j = row;
+    int32_t sign = 1;
+    uint32_t ndraw = 0;   /* Philox draws used so far */
+    int64_t jumps = 0;
+    uint32_t hash = 2166136261u;
+    int status = ORC_OK;
+    uint32_t x[4];
+    double eta2 = 1.0, eta1 = 1.0;
+    double log_f = 0.0, log_c = 0.0, diff = 0.0;
+    int64_t x_prev2 = row, x_prev1 = row; /* states at grid points 2j-2, 2j-1 */
+
+    orc_draw(c, row, rep, ndraw++, level, x);
+    double t_next = orc_hold(c, j, x, 0.0);
+
+    for (int64_t step = 1; step <= N; ++step) {
+        double g = c->dl[j] / (double)N;
+        eta2 = eta2 * exp(g / 2.0);
+        if (step % 2 != 0) eta1 = eta1 * exp(g);
+        if (c->variant == ORC_REDRAW) {
+            /* Fresh clock at the start of the interval (the listing's tau). */
+            orc_draw(c, row, rep, ndraw++, level, x);
+            t_next = orc_hold(c, j, x, (double)(step - 1) / (double)N);
+        }
+        while (orc_before(c, t_next, step, N)) {
+            if (jumps >= c->max_jumps) {
+                status = ORC_WALK_LIMIT;
+                goto done;
+            }
+            int64_t from = j;
+            j = orc_jump(c, j, x, &sign);
+            hash = (hash ^ (uint32_t)j) * 16777619u;
+            jumps = jumps + 1;
+            orc_draw(c, row, rep, ndraw++, level, x);
+            /* R1: the new holding time uses the new state's rate; the
+             * literal reading uses the state just left. */
+            t_next = orc_hold(c, (c->variant == ORC_LITERAL_RATE) ? from : j, x, t_next);
+        }
+        g = c->dl[j] / (double)N;
+        eta2 = eta2 * exp(g / 2.0);
+        if (step % 2 == 0) eta1 = eta1 * exp(g);
+        if (step % 2 == 0) {
+            /* Pair (X_{step-2}, X_{step-1}, X_step) of Eq. 7. */
+            double d0 = c->dl[x_prev2] / (double)N;
+            double d1 = c->dl[x_prev1] / (double)N;
+            double d2 = c->dl[j] / (double)N;
+            log_f = log_f + (d0 / 2.0 + d1 + d2 / 2.0);
+            log_c = log_c + (d0 + d2);
+            diff = diff + ((d1 - d0 / 2.0) - d2 / 2.0);
+            x_prev2 = j;
+        } else {
+            x_prev1 = j;
+        }
+    }
+    if (N == 1) {
+        /* Level 0 has one interval and no pair: the fine exponent is
+         * dt (d_{X_0} + d_{X_1}) / 2 with dt = 1 in scaled time. */
+        log_f = c->dl[row] / 2.0 + c->dl[j] / 2.0;
+    }
+done:
+    out->end = (int32_t)j;
+    out->jumps = (int32_t)jumps;
+    out->sign = sign;
+    out->hash = hash;
+    out->status = status;
+    out->pad = 0;
+    if (status != ORC_OK) {
+        out->y = 0.0;
+        out->y_alg2 = 0.0;
+        out->log_f = 0.0;
+        out->log_c = 0.0;
+        return status;
+    }
+    double uj = c->v[j];
+    out->log_f = log_f;
+    out->log_c = coarse ? log_c : 0.0;
+    if (coarse) {
+        out->y = (double)sign * uj * (exp(log_c) * expm1(diff));
+        out->y_alg2 = (double)sign * uj * (eta2 - eta1);
+    } else {
+        out->y = (double)sign * uj * exp(log_f);
+        out->y_alg2 = (double)sign * uj * eta2;
+    }
+    return status;
+}
+
+int orc_walk_many(const orc_ctx *c, int64_t count, const int64_t *rows, const int64_t *reps,
+                  int level, int coarse, orc_walk_rec *out)
+{
+    int bad = 0;
+    for (int64_t k = 0; k < count; ++k)
+        if (orc_walk(c, rows[k], reps[k], level, coarse, &out[k]) != ORC_OK) bad = 1;
+    return bad;
+}
+
+/* MLMCL (Algorithm 2) for rows [row_begin, row_end) and replicas
+ * [rep_begin, rep_begin + reps): per-row sums of y into sum_y[row], and the
+ * totals sum y^2, jumps and walk-limit hits.  Rows are split over OpenMP
+ * threads; each row's sum is formed in replica order. */
+int orc_mlmcl(const orc_ctx *c, int64_t row_begin, int64_t row_end, int64_t rep_begin,
+              int64_t reps, int level, int coarse, int nthreads, double *sum_y,
+              double *sum_y2, int64_t *jumps, int64_t *limit_hits)
+{
+    double tot_y2 = 0.0;
+    int64_t tot_j = 0, tot_lim = 0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : tot_y2, tot_j, tot_lim)
+#endif
+    for (int64_t i = row_begin; i < row_end; ++i) {
+        double s = 0.0, s2 = 0.0;
+        int64_t jj = 0, lim = 0;
+        orc_walk_rec r;
+        for (int64_t k = 0; k < reps; ++k) {
+            if (orc_walk(c, i, rep_begin + k, level, coarse, &r) != ORC_OK) lim++;
+            s = s + r.y;
+            s2 = s2 + r.y * r.y;
+            jj += r.jumps;
+        }
+        sum_y[i] = sum_y[i] + s;
+        tot_y2 += s2;
+        tot_j += jj;
+        tot_lim += lim;
+    }
+    *sum_y2 = *sum_y2 + tot_y2;
+    *jumps = *jumps + tot_j;
+    *limit_hits = *limit_hits + tot_lim;
+    return 0;
+}
+
+int orc_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

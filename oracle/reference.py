@@ -1,0 +1,300 @@
+"""Deterministic FP64 references for x = exp(t A) v and its MLMC levels.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+Everything here is the plain definition written out with dense or sparse
+matrix products as the only library primitives:
+
+* :func:`split` -- the splitting A = D - T of Sec. 2.1 (Eq. 1).
+* :func:`expm_pade13` -- exp(M) by scaling and squaring with the diagonal
+  [13/13] Pade approximant (Higham, SIAM J. Matrix Anal. Appl. 26 (2005)),
+  for the dense n <= 4096 judge.
+* :func:`expmv_taylor` -- exp(tA)v by truncated Taylor series with s
+  substeps, s = ceil(t ||A||_1) (the scaling idea of Al-Mohy and Higham 2011,
+  cited by the paper), terms added until the last one is below 2^-53 of the
+  partial sum in the max norm.
+* :func:`strang` -- the level-l approximation of Eq. 2,
+  (e^{dt D/2} e^{-dt T} e^{dt D/2})^N v with N = 2^l and dt = t/N.
+* :func:`level_moments` -- exact E[Y] and E[Y^2] per start row for the
+  level-l correction Y of Algorithm 2, by transfer matrices over the grid
+  points (the walk's skeleton is a Markov chain with kernel exp(dt Q)).
+* :func:`brute_moments` -- the same by enumerating every skeleton path
+  (tiny n and N only).
+* :func:`dst_expmv_laplacian_2d` -- the closed form of exp(tA)v for the 2D
+  Dirichlet Laplacian by its sine eigenbasis.
+"""
+from __future__ import annotations
+
+import itertools
+import math
+from fractions import Fraction
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.linalg as sla
+
+
+# ---------------------------------------------------------------------------
+# Splitting (Sec. 2.1, Eq. 1)
+# ---------------------------------------------------------------------------
+def split(a_dense: np.ndarray):
+    """Return (d, Lii, T, sigma) with d_i = a_ii + L_ii, L_ii = sum_{j!=i}
+    |a_ij|, sigma_ij = [a_ij < 0], and T_ii = L_ii, T_ij = (-1)^sigma_ij L_ij
+    where L_ij = -|a_ij|, so that A = diag(d) - T."""
+    a = np.asarray(a_dense, dtype=np.float64)
+    n = a.shape[0]
+    off = a.copy()
+    np.fill_diagonal(off, 0.0)
+    lap_off = -np.abs(off)                       # L_ij, i != j
+    lii = -lap_off.sum(axis=1)                   # zero row sums
+    sigma = (off < 0).astype(np.int64)
+    t = np.where(sigma == 1, -1.0, 1.0) * lap_off
+    t[np.arange(n), np.arange(n)] = lii
+    d = np.diag(a) + lii
+    return d, lii, t, sigma
+
+
+def generators(a_dense: np.ndarray, t: float):
+    """Scaled-time generators of the walk: Q = -t L (unsigned, rows sum to
+    zero) and Qs = -t T (signed: off-diagonals t a_ij, diagonal -t L_ii),
+    and the scaled diagonal dl = t d."""
+    d, lii, tmat, _ = split(a_dense)
+    n = a_dense.shape[0]
+    off = np.abs(np.asarray(a_dense, dtype=np.float64))
+    np.fill_diagonal(off, 0.0)
+    q = t * off
+    q[np.arange(n), np.arange(n)] = -t * lii
+    return q, -t * tmat, t * d
+
+
+# ---------------------------------------------------------------------------
+# exp(M): Pade-13 scaling and squaring
+# ---------------------------------------------------------------------------
+_PADE_M = 13
+# b_j = (2m-j)! m! / ((2m)! j! (m-j)!), the numerator of the [m/m] Pade
+# approximant of e^x (the denominator is the same polynomial at -x).
+_PADE_B = [float(Fraction(math.factorial(2 * _PADE_M - j) * math.factorial(_PADE_M),
+                          math.factorial(2 * _PADE_M) * math.factorial(j)
+                          * math.factorial(_PADE_M - j))) for j in range(_PADE_M + 1)]
+_THETA_13 = 5.371920351148152
+
+
+def expm_pade13(m: np.ndarray) -> np.ndarray:
+    """exp(M) for a dense square matrix: scale by 2^-s so that ||M/2^s||_1 <=
+    theta_13, evaluate r_13 = q(-M)^{-1} q(M) with q(x) = sum b_j x^j, then
+    square s times."""
+    m = np.asarray(m, dtype=np.float64)
+    n = m.shape[0]
+    norm1 = np.abs(m).sum(axis=0).max() if n else 0.0
+    s = 0 if norm1 <= _THETA_13 else int(math.ceil(math.log2(norm1 / _THETA_13)))
+    a = m / (2.0 ** s)
+    b = _PADE_B
+    ident = np.eye(n)
+    a2 = a @ a
+    a4 = a2 @ a2
+    a6 = a4 @ a2
+    u = a @ (a6 @ (b[13] * a6 + b[11] * a4 + b[9] * a2)
+             + b[7] * a6 + b[5] * a4 + b[3] * a2 + b[1] * ident)
+    v = a6 @ (b[12] * a6 + b[10] * a4 + b[8] * a2) + b[6] * a6 + b[4] * a4 + b[2] * a2 \
+        + b[0] * ident
+    r = np.linalg.solve(v - u, v + u)
+    for _ in range(s):
+        r = r @ r
+    return r
+
+
+# ---------------------------------------------------------------------------
+# exp(tA) v: truncated Taylor with substeps
+# ---------------------------------------------------------------------------
+def expmv_taylor(a, t: float, v: np.ndarray, max_terms: int = 200) -> np.ndarray:
+    """exp(tA)v for a sparse or dense A: s = max(1, ceil(t ||A||_1))
+    substeps of length h = t/s; in each, w <- sum_k (hA)^k w / k! until two
+    consecutive terms are <= 2^-53 ||partial sum||_inf."""
+    if sp.issparse(a):
+        a = sp.csr_matrix(a, dtype=np.float64)
+        norm1 = float(abs(a).sum(axis=0).max()) if a.shape[0] else 0.0
+    else:
+        a = np.asarray(a, dtype=np.float64)
+        norm1 = float(np.abs(a).sum(axis=0).max()) if a.shape[0] else 0.0
+    w = np.array(v, dtype=np.float64, copy=True)
+    if t == 0.0 or norm1 == 0.0:
+        return w
+    s = max(1, int(math.ceil(abs(t) * norm1)))
+    h = t / s
+    for _ in range(s):
+        acc = w.copy()
+        term = w
+        small = 0
+        for k in range(1, max_terms + 1):
+            term = (h * (a @ term)) / k
+            acc = acc + term
+            if np.abs(term).max() <= 2.0 ** -53 * np.abs(acc).max():
+                small += 1
+                if small == 2:
+                    break
+            else:
+                small = 0
+        w = acc
+    return w
+
+
+def expmv(a, t: float, v: np.ndarray) -> np.ndarray:
+    """FP64 judge of exp(tA)v: dense Pade-13 for n <= 4096, Taylor above."""
+    n = a.shape[0]
+    if n <= 4096:
+        dense = a.toarray() if sp.issparse(a) else np.asarray(a, dtype=np.float64)
+        return expm_pade13(t * dense) @ np.asarray(v, dtype=np.float64)
+    return expmv_taylor(a, t, v)
+
+
+# ---------------------------------------------------------------------------
+# Strang levels (Eq. 2) and the telescoping corrections (Eq. 8-9)
+# ---------------------------------------------------------------------------
+def _split_sparse(a):
+    """Sparse splitting: returns (d, -T as sparse) of Eq. 1."""
+    a = sp.csr_matrix(a, dtype=np.float64)
+    diag = a.diagonal()
+    off = a - sp.diags(diag)
+    off.eliminate_zeros()
+    lii = np.asarray(abs(off).sum(axis=1)).ravel()
+    minus_t = (off - sp.diags(lii)).tocsr()      # off-diagonals a_ij, diagonal -L_ii
+    return diag + lii, minus_t
+
+
+def strang(a, t: float, v: np.ndarray, level: int) -> np.ndarray:
+    """x-bar of Eq. 2 with N = 2^level steps of dt = t/N:
+    apply e^{dt D/2} e^{-dt T} e^{dt D/2} N times to v."""
+    n_steps = 1 << level
+    dt = t / n_steps
+    d, minus_t = _split_sparse(a)
+    half = np.exp(dt * d / 2.0)
+    dense = None
+    if a.shape[0] <= 2048:
+        dense = expm_pade13(dt * minus_t.toarray())
+    w = np.array(v, dtype=np.float64, copy=True)
+    for _ in range(n_steps):
+        w = half * w
+        w = dense @ w if dense is not None else expmv_taylor(minus_t, dt, w)
+        w = half * w
+    return w
+
+
+def level_means(a, t: float, v: np.ndarray, l0: int, top: int):
+    """Exact per-level corrections m_l of Eq. 9 for l = l0..top:
+    m_l0 = x-bar^(l0), m_l = x-bar^(l) - x-bar^(l-1)."""
+    xs = {l: strang(a, t, v, l) for l in range(max(0, l0 - 1) if l0 > 0 else 0, top + 1)}
+    out = {l0: xs[l0]}
+    for l in range(l0 + 1, top + 1):
+        out[l] = xs[l] - xs[l - 1]
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Exact moments of one level's correction (Lemma 1-2)
+# ---------------------------------------------------------------------------
+def _weights(level: int, coarse: bool):
+    """Exponent weights c_k on grid points k = 0..N (scaled time, dl units):
+    fine c_f = (1/2, 1, ..., 1, 1/2)/N; coarse (level - 1 on even points)
+    c_c = (1, 0, 2, 0, ..., 2, 0, 1)/N."""
+    n = 1 << level
+    cf = np.full(n + 1, 1.0 / n)
+    cf[0] = cf[-1] = 0.5 / n
+    if not coarse:
+        return cf, None
+    cc = np.zeros(n + 1)
+    cc[0::2] = 2.0 / n
+    cc[0] = cc[-1] = 1.0 / n
+    return cf, cc
+
+
+def _functional(kernel: np.ndarray, dl: np.ndarray, c: np.ndarray, g: np.ndarray):
+    """F_i = E_i[exp(sum_k c_k dl_{X_k}) g(X_N)] for the chain with one-step
+    kernel ``kernel``: D_0 K D_1 K ... K D_N g."""
+    w = np.exp(c[-1] * dl) * g
+    for k in range(len(c) - 2, -1, -1):
+        w = np.exp(c[k] * dl) * (kernel @ w)
+    return w
+
+
+def level_moments(a_dense: np.ndarray, t: float, v: np.ndarray, level: int, coarse: bool):
+    """Exact (E[Y], E[Y^2]) per start row for the level-``level`` sample of
+    Algorithm 2: Y = phi v_{X_N} (e^{E_f} - e^{E_c}) when ``coarse``, else
+    phi v_{X_N} e^{E_f}.  The mean uses the signed kernel exp(dt Qs); the
+    second moment uses the unsigned exp(dt Q), since phi^2 = 1 and fine and
+    coarse share phi."""
+    q, qs, dl = generators(a_dense, t)
+    n_steps = 1 << level
+    ks = expm_pade13(qs / n_steps)
+    ku = expm_pade13(q / n_steps)
+    v = np.asarray(v, dtype=np.float64)
+    cf, cc = _weights(level, coarse)
+    if not coarse:
+        m1 = _functional(ks, dl, cf, v)
+        m2 = _functional(ku, dl, 2 * cf, v * v)
+        return m1, m2
+    m1 = _functional(ks, dl, cf, v) - _functional(ks, dl, cc, v)
+    m2 = (_functional(ku, dl, 2 * cf, v * v) - 2.0 * _functional(ku, dl, cf + cc, v * v)
+          + _functional(ku, dl, 2 * cc, v * v))
+    return m1, m2
+
+
+def brute_moments(a_dense: np.ndarray, t: float, v: np.ndarray, level: int, coarse: bool):
+    """(E[Y], E[Y^2]) per start row by summing over every skeleton path
+    (X_1, ..., X_N) in {0..n-1}^N with probability prod K(X_{k-1}, X_k)
+    (signed kernel for the mean, unsigned for the second moment)."""
+    q, qs, dl = generators(a_dense, t)
+    n = a_dense.shape[0]
+    n_steps = 1 << level
+    ks = expm_pade13(qs / n_steps)
+    ku = expm_pade13(q / n_steps)
+    cf, cc = _weights(level, coarse)
+    m1 = np.zeros(n)
+    m2 = np.zeros(n)
+    for i in range(n):
+        for path in itertools.product(range(n), repeat=n_steps):
+            states = (i,) + path
+            ps = 1.0
+            pu = 1.0
+            for k in range(n_steps):
+                ps *= ks[states[k], states[k + 1]]
+                pu *= ku[states[k], states[k + 1]]
+            ef = sum(cf[k] * dl[s] for k, s in enumerate(states))
+            vend = v[states[-1]]
+            if coarse:
+                ec = sum(cc[k] * dl[s] for k, s in enumerate(states))
+                y = vend * (math.exp(ef) - math.exp(ec))
+            else:
+                y = vend * math.exp(ef)
+            m1[i] += ps * y
+            m2[i] += pu * y * y
+    return m1, m2
+
+
+# ---------------------------------------------------------------------------
+# Closed forms
+# ---------------------------------------------------------------------------
+def dst_expmv_laplacian_2d(g: int, scale: float, t: float, v: np.ndarray) -> np.ndarray:
+    """exp(t * scale * L5) v for the g x g Dirichlet 5-point Laplacian L5
+    (row index ix*g + iy) from its eigenbasis: S_kp = sqrt(2/(g+1))
+    sin(k p pi/(g+1)), eigenvalues -4 + 2cos(p pi/(g+1)) + 2cos(q pi/(g+1))."""
+    k = np.arange(1, g + 1)
+    s = np.sqrt(2.0 / (g + 1)) * np.sin(np.outer(k, k) * np.pi / (g + 1))
+    lam1 = -2.0 + 2.0 * np.cos(k * np.pi / (g + 1))
+    lam = lam1[:, None] + lam1[None, :]
+    vm = np.asarray(v, dtype=np.float64).reshape(g, g)
+    coef = s @ vm @ s
+    return (s @ (np.exp(t * scale * lam) * coef) @ s).ravel()
+
+
+def level_variance_total(m1: np.ndarray, m2: np.ndarray) -> float:
+    """V_l as the scalar total variance sum_i (E[Y_i^2] - E[Y_i]^2)."""
+    return float(np.sum(m2 - m1 * m1))
+
+
+def choose_l0(d: np.ndarray, lii: np.ndarray, t: float) -> int:
+    """Coarsest level by Eq. 16, l0 = log2(2 beta d_max), read with d_max =
+    max_i max(|d_i|, L_ii) and rounded up, never below 0."""
+    dm = float(np.max(np.maximum(np.abs(d), lii))) if d.size else 0.0
+    if dm * t <= 0.0:
+        return 0
+    return max(0, int(math.ceil(math.log2(2.0 * t * dm))))

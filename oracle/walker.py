@@ -1,0 +1,211 @@
+"""ctypes binding to the oracle's C walker (``mlmc_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+The C file is compiled by :func:`build` with ``-ffp-contract=off`` so that
+every floating-point operation rounds exactly as written; the GPU library
+makes the same operations with explicit round-to-nearest intrinsics, which is
+what lets index trajectories be compared bit for bit.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mlmc_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_build", "liborc_mlmc.so")
+_lib = None
+
+RESIDUAL, REDRAW, LITERAL_RATE = 0, 2, 3
+FP64, FP32 = 0, 1
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library (gcc, OpenMP, no FMA contraction)."""
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or \
+            os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+                               "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class WalkRec(ct.Structure):
+    _fields_ = [("end", ct.c_int32), ("jumps", ct.c_int32), ("sign", ct.c_int32),
+                ("hash", ct.c_uint32), ("y", ct.c_double), ("y_alg2", ct.c_double),
+                ("log_f", ct.c_double), ("log_c", ct.c_double), ("status", ct.c_int32),
+                ("pad", ct.c_int32)]
+
+
+WALK_DTYPE = np.dtype([("end", np.int32), ("jumps", np.int32), ("sign", np.int32),
+                       ("hash", np.uint32), ("y", np.float64), ("y_alg2", np.float64),
+                       ("log_f", np.float64), ("log_c", np.float64), ("status", np.int32),
+                       ("pad", np.int32)])
+assert WALK_DTYPE.itemsize == ct.sizeof(WalkRec)
+
+
+class Ctx(ct.Structure):
+    _fields_ = [("n", ct.c_int64), ("row_ptr", ct.c_void_p), ("deg", ct.c_void_p),
+                ("dl", ct.c_void_p), ("inv_rate", ct.c_void_p), ("inv_rate32", ct.c_void_p),
+                ("thr", ct.c_void_p), ("keep_col", ct.c_void_p), ("keep_neg", ct.c_void_p),
+                ("alias_col", ct.c_void_p), ("alias_neg", ct.c_void_p), ("v", ct.c_void_p),
+                ("seed", ct.c_uint64), ("precision", ct.c_int32), ("variant", ct.c_int32),
+                ("max_jumps", ct.c_int64)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ct.CDLL(build())
+        P = ct.c_void_p
+        _lib.orc_philox4x32_10.argtypes = [P, P, P]
+        _lib.orc_uniform64.argtypes = [ct.c_uint32, ct.c_uint32]
+        _lib.orc_uniform64.restype = ct.c_double
+        _lib.orc_uniform32.argtypes = [ct.c_uint32]
+        _lib.orc_uniform32.restype = ct.c_float
+        _lib.orc_neglog64.argtypes = [ct.c_double]
+        _lib.orc_neglog64.restype = ct.c_double
+        _lib.orc_neglog32.argtypes = [ct.c_float]
+        _lib.orc_neglog32.restype = ct.c_float
+        _lib.orc_neglog64_batch.argtypes = [P, P, ct.c_int64]
+        _lib.orc_neglog32_batch.argtypes = [P, P, ct.c_int64]
+        _lib.orc_split.argtypes = [ct.c_int64, P, P, P, ct.c_double, P, P, P, P, P, P, P]
+        _lib.orc_alias.argtypes = [ct.c_int64, P, P, P, P, P, P, P, P, P, P]
+        _lib.orc_alias.restype = ct.c_int
+        _lib.orc_walk.argtypes = [ct.POINTER(Ctx), ct.c_int64, ct.c_int64, ct.c_int, ct.c_int,
+                                  ct.POINTER(WalkRec)]
+        _lib.orc_walk_many.argtypes = [ct.POINTER(Ctx), ct.c_int64, P, P, ct.c_int, ct.c_int, P]
+        _lib.orc_mlmcl.argtypes = [ct.POINTER(Ctx), ct.c_int64, ct.c_int64, ct.c_int64,
+                                   ct.c_int64, ct.c_int, ct.c_int, ct.c_int, P, P, P, P]
+        _lib.orc_max_threads.restype = ct.c_int
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ct.c_void_p)
+
+
+def philox(ctr, key) -> np.ndarray:
+    """Philox4x32-10 of one counter (4 x uint32) under one key (2 x uint32)."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().orc_philox4x32_10(_p(c), _p(k), _p(out))
+    return out
+
+
+def neglog64(u: np.ndarray) -> np.ndarray:
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    out = np.empty_like(u)
+    lib().orc_neglog64_batch(_p(u), _p(out), u.size)
+    return out
+
+
+def neglog32(u: np.ndarray) -> np.ndarray:
+    u = np.ascontiguousarray(u, dtype=np.float32)
+    out = np.empty_like(u)
+    lib().orc_neglog32_batch(_p(u), _p(out), u.size)
+    return out
+
+
+@dataclass
+class Tables:
+    """The oracle's per-row split quantities and alias tables."""
+    n: int
+    row_ptr: np.ndarray
+    a_ii: np.ndarray
+    L: np.ndarray
+    deg: np.ndarray
+    dl: np.ndarray
+    inv_rate: np.ndarray
+    inv_rate32: np.ndarray
+    dl32: np.ndarray
+    thr: np.ndarray
+    keep_col: np.ndarray
+    keep_neg: np.ndarray
+    alias_col: np.ndarray
+    alias_neg: np.ndarray
+
+
+def build_tables(a, t: float) -> Tables:
+    """Splitting (Eq. 1) and alias tables (Eq. 12) of the CSR matrix ``a``
+    for time ``t``.  ``a`` has fields n, row_ptr, col, val."""
+    n = a.n
+    rp = np.ascontiguousarray(a.row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(a.col, dtype=np.int32)
+    val = np.ascontiguousarray(a.val, dtype=np.float64)
+    nnz = int(rp[-1])
+    a_ii = np.zeros(n)
+    L = np.zeros(n)
+    deg = np.zeros(n, dtype=np.int32)
+    dl = np.zeros(n)
+    inv_rate = np.zeros(n)
+    inv_rate32 = np.zeros(n, dtype=np.float32)
+    dl32 = np.zeros(n, dtype=np.float32)
+    lib().orc_split(n, _p(rp), _p(col), _p(val), float(t), _p(a_ii), _p(L), _p(deg), _p(dl),
+                    _p(inv_rate), _p(inv_rate32), _p(dl32))
+    m = max(nnz, 1)
+    thr = np.zeros(m, dtype=np.uint32)
+    keep_col = np.full(m, -1, dtype=np.int32)
+    keep_neg = np.zeros(m, dtype=np.uint8)
+    alias_col = np.full(m, -1, dtype=np.int32)
+    alias_neg = np.zeros(m, dtype=np.uint8)
+    rc = lib().orc_alias(n, _p(rp), _p(col), _p(val), _p(L), _p(deg), _p(thr), _p(keep_col),
+                         _p(keep_neg), _p(alias_col), _p(alias_neg))
+    if rc != 0:
+        raise MemoryError("oracle alias build failed")
+    return Tables(n, rp, a_ii, L, deg, dl, inv_rate, inv_rate32, dl32, thr, keep_col, keep_neg,
+                  alias_col, alias_neg)
+
+
+class Walker:
+    """Replays walks of Algorithm 2 on one matrix, time and right-hand side."""
+
+    def __init__(self, a, t: float, v: np.ndarray, seed: int, precision: int = FP64,
+                 variant: int = RESIDUAL, max_jumps: int = 1 << 30, tables: Tables = None):
+        self.tables = tables if tables is not None else build_tables(a, t)
+        self.v = np.ascontiguousarray(v, dtype=np.float64)
+        tb = self.tables
+        self._keep = (tb, self.v)
+        self.ctx = Ctx(tb.n, _p(tb.row_ptr).value, _p(tb.deg).value, _p(tb.dl).value,
+                       _p(tb.inv_rate).value, _p(tb.inv_rate32).value, _p(tb.thr).value,
+                       _p(tb.keep_col).value, _p(tb.keep_neg).value, _p(tb.alias_col).value,
+                       _p(tb.alias_neg).value, _p(self.v).value, ct.c_uint64(seed),
+                       precision, variant, max_jumps)
+
+    def walk(self, row: int, rep: int, level: int, coarse: bool) -> WalkRec:
+        r = WalkRec()
+        lib().orc_walk(ct.byref(self.ctx), row, rep, level, int(coarse), ct.byref(r))
+        return r
+
+    def walks(self, rows, reps, level: int, coarse: bool) -> np.ndarray:
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        reps = np.ascontiguousarray(reps, dtype=np.int64)
+        out = np.zeros(rows.size, dtype=WALK_DTYPE)
+        lib().orc_walk_many(ct.byref(self.ctx), rows.size, _p(rows), _p(reps), level,
+                            int(coarse), _p(out))
+        return out
+
+    def mlmcl(self, level: int, coarse: bool, rep_begin: int, reps: int, rows=None,
+              nthreads: int = 0):
+        """Algorithm 2 over rows [r0, r1) x replicas [rep_begin, rep_begin+reps):
+        returns (per-row sum of y, total sum of y^2, total jumps, limit hits)."""
+        r0, r1 = (0, self.tables.n) if rows is None else rows
+        sum_y = np.zeros(self.tables.n)
+        sum_y2 = np.zeros(1)
+        jumps = np.zeros(1, dtype=np.int64)
+        lim = np.zeros(1, dtype=np.int64)
+        lib().orc_mlmcl(ct.byref(self.ctx), r0, r1, rep_begin, reps, level, int(coarse),
+                        nthreads, _p(sum_y), _p(sum_y2), _p(jumps), _p(lim))
+        return sum_y, float(sum_y2[0]), int(jumps[0]), int(lim[0])
+
+
+def max_threads() -> int:
+    return int(lib().orc_max_threads())
