@@ -1,0 +1,216 @@
+/*
+ * mlmc.h -- C ABI of libmlmc: multilevel Monte Carlo estimation of
+ * x = exp(t A) v on one GPU (GB300, sm_103a).
+ *
+ * Method: Acebron, Herrero, Monteiro, "A highly parallel algorithm for
+ * computing the action of a matrix exponential on a vector based on a
+ * multilevel Monte Carlo method".
+ *   - A = D - T splitting, Sec. 2.1, Eq. 1;
+ *   - Strang level approximation, Eq. 2, with dt_l = t / 2^l (Sec. 2.2);
+ *   - path law: continuous-time Markov chain with exponential holding times
+ *     of rate L_jj and jumps j -> k with probability |a_jk| / L_jj
+ *     (Sec. 3, Eq. 12);
+ *   - coupled fine/coarse walks on one path (Fig. 1, Algorithm 2);
+ *   - telescoping estimator and sample sizes, Eq. 8-11, Algorithm 1.
+ *
+ * Conventions for every entry point
+ *   - The return value is an mlmc_status; nothing throws across the ABI.
+ *     On failure mlmc_last_error() returns a message for the calling thread.
+ *   - Matrices are canonical CSR: row_ptr int64 [n+1] with row_ptr[0] = 0,
+ *     col int32 [nnz] strictly increasing within each row (so no duplicate
+ *     entries), vals float64 [nnz].  A missing diagonal entry means a_ii = 0.
+ *     nnz must be below 2^31.
+ *   - "Host or device" pointers may be either: the library copies through
+ *     unified addressing.  Pinned host memory makes those copies faster.
+ *   - All GPU work is ordered on the plan's stream (the `cuda_stream`
+ *     argument of mlmc_plan_create, a cudaStream_t; NULL = legacy default
+ *     stream).  Entry points that return results to the caller synchronise
+ *     that stream before returning.
+ *   - A plan is not thread safe: one host thread at a time per plan.
+ */
+#ifndef MLMC_H
+#define MLMC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MLMC_OK = 0,
+    MLMC_ERR_INVALID_ARG = 1,   /* bad sizes, pointers, CSR structure, NaN/Inf */
+    MLMC_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+    MLMC_ERR_OOM = 3,           /* device allocation failed */
+    MLMC_ERR_NOT_CONVERGED = 4, /* budget exhausted; x and stats still written */
+    MLMC_ERR_WALK_LIMIT = 5,    /* a walk exceeded max_jumps_per_walk */
+    MLMC_ERR_NUMERIC = 6        /* a non-finite weight was produced */
+} mlmc_status;
+
+enum { MLMC_FP64 = 0, MLMC_FP32_KAHAN = 1 };   /* walk arithmetic */
+enum { MLMC_BACKWARD = 0, MLMC_FORWARD = 1 };  /* estimator mode */
+enum { MLMC_PLAIN = 0, MLMC_LEARNED = 1 };     /* jump proposal */
+
+/* Level schedule and budgets (Algorithm 1 inputs).
+ *   l0                coarsest level; -1 selects Eq. 16,
+ *                     l0 = ceil(log2(2 t max_i max(|d_i|, L_ii))), >= 0
+ *   num_levels        initial number of levels L - l0 + 1 (Algorithm 1 uses 5)
+ *   max_levels        the controller adds levels up to this many
+ *   pilot_walks       walks per row per level in the pilot run
+ *   precision         MLMC_FP64 or MLMC_FP32_KAHAN
+ *   mode              MLMC_BACKWARD (Algorithm 2 from every row)
+ *   proposal          MLMC_PLAIN
+ *   max_jumps_per_walk  a walk that would exceed it stops, contributes 0 and
+ *                     makes the call return MLMC_ERR_WALK_LIMIT
+ *   max_walks_per_row sample budget per level (per row)
+ *   time_budget_s     wall-clock budget of one mlmc_expmv call
+ *   walks_per_lane    work granularity of the walk kernel (0 = automatic)
+ *   block_threads     threads per block of the walk kernel (0 = automatic) */
+typedef struct {
+    int32_t l0;
+    int32_t num_levels;
+    int32_t max_levels;
+    int32_t precision;
+    int32_t mode;
+    int32_t proposal;
+    int64_t pilot_walks;
+    int64_t max_jumps_per_walk;
+    int64_t max_walks_per_row;
+    double time_budget_s;
+    int32_t walks_per_lane;
+    int32_t block_threads;
+} mlmc_schedule;
+
+/* Per-level statistics of the last mlmc_expmv call.
+ *   level            l; dt_l = t / 2^l
+ *   walks_per_row    M_l
+ *   mean_norm2       ||m_l||_2^2 of the level's mean correction vector
+ *   var              V_l: total variance of one sample (one walk from every
+ *                    row), sum_i Var(Y_i), unbiased estimate
+ *   cost_events_per_walk  mean events (holding-time draws = jumps + 1)
+ *   jumps            total jumps taken at this level
+ *   seconds          GPU time spent in this level's walk launches */
+typedef struct {
+    int32_t level;
+    int32_t pad;
+    int64_t walks_per_row;
+    double mean_norm2;
+    double var;
+    double cost_events_per_walk;
+    int64_t jumps;
+    double seconds;
+} mlmc_level_stats;
+
+/* One replayed walk (mlmc_trace): the state at s = 1, the number of jumps,
+ * the product of jump signs phi, an FNV-1a hash of the states entered by
+ * each jump (offset basis 2166136261, prime 16777619, over the 32-bit state
+ * indices), the contribution y, and a status (0 ok, 1 jump limit). */
+typedef struct {
+    int32_t end;
+    int32_t jumps;
+    int32_t sign;
+    uint32_t hash;
+    double y;
+    int32_t status;
+    int32_t pad;
+} mlmc_walk_record;
+
+typedef struct mlmc_plan mlmc_plan;
+
+/* Fill *sched with the defaults: l0 = -1 (Eq. 16), num_levels = 5,
+ * max_levels = 12, FP64, backward, plain, pilot_walks = 64,
+ * max_jumps_per_walk = 1<<20, max_walks_per_row = 1<<34,
+ * time_budget_s = 600, automatic launch shape. */
+mlmc_status mlmc_schedule_default(mlmc_schedule *sched);
+
+/* Create a plan for x = exp(t A) v (Sec. 2.1-3).  Copies the CSR matrix
+ * (host or device pointers) to the device, validates it, and builds on the
+ * device the per-row split quantities of Eq. 1 and the alias tables of the
+ * jump law of Eq. 12.
+ *   out        receives the plan (owned by the caller; free with
+ *              mlmc_plan_destroy)
+ *   n          matrix order, 1 <= n < 2^31
+ *   nnz        stored entries, must equal row_ptr[n]
+ *   t          time (the paper's beta), t >= 0, finite
+ *   sched      NULL for the defaults
+ *   rel_tol    target relative RMS error of mlmc_expmv, > 0
+ *   cuda_stream  cudaStream_t for all work of the plan
+ * Errors: INVALID_ARG for a bad CSR (row_ptr not monotone or not ending at
+ * nnz, a column out of range or not strictly increasing, a non-finite
+ * value), t < 0, n or nnz out of range; OOM; CUDA. */
+mlmc_status mlmc_plan_create(mlmc_plan **out, int64_t n, int64_t nnz, const int64_t *row_ptr,
+                             const int32_t *col, const double *vals, double t,
+                             const mlmc_schedule *sched, double rel_tol, void *cuda_stream);
+
+/* Rebuild the split quantities and alias tables from the plan's resident
+ * copy of A (the same kernels as at creation).  Asynchronous on the plan's
+ * stream. */
+mlmc_status mlmc_plan_rebuild(mlmc_plan *plan);
+
+/* x = exp(t A) v by Algorithm 1: a pilot of pilot_walks per row on levels
+ * l0..l0+num_levels-1, Giles' sample sizes M_l (Eq. 11, read as
+ * M_l = ceil(2/eps^2 sqrt(V_l/C_l) sum_k sqrt(V_k C_k)), eps = rel_tol ||x||),
+ * top-up walks, and a new level while the bias estimate
+ * max(||m_L||, ||m_{L-1}||/4)/3 exceeds eps/sqrt(2).
+ *   v, x   host or device pointers to n doubles (may not alias)
+ *   seed   Philox key; the same seed reproduces the same walks
+ * Synchronises the plan's stream.  NOT_CONVERGED still writes x. */
+mlmc_status mlmc_expmv(mlmc_plan *plan, const double *v, double *x, uint64_t seed);
+
+/* Statistics of the last mlmc_expmv: up to `cap` levels into out (host),
+ * the level count into *n_levels and the estimated relative RMS error
+ * sqrt(sum_l V_l/M_l)/||x|| into *est_rel_err (either pointer may be NULL). */
+mlmc_status mlmc_stats(const mlmc_plan *plan, mlmc_level_stats *out, int32_t cap,
+                       int32_t *n_levels, double *est_rel_err);
+
+/* MLMCL of Algorithm 2 for every row: walks rep_begin .. rep_begin+reps-1
+ * of each row at level `level` (N = 2^level steps of dt = t/N); `coarse`
+ * nonzero adds the coupled level-1 weight on the same path and returns the
+ * difference P_l - P_{l-1}.
+ *   v        device pointer, n doubles (the right-hand side)
+ *   sum_y    device pointer, n doubles: sum_y[i] += sum over the walks of Y
+ *   totals   device pointer, 4 doubles: [0] += sum Y^2, [1] += jumps,
+ *            [2] += walks, [3] += walks that hit the jump limit
+ * Asynchronous on the plan's stream; uses the plan's precision. */
+mlmc_status mlmc_mlmcl(mlmc_plan *plan, int32_t level, int32_t coarse, int64_t rep_begin,
+                       int64_t reps, const double *v, uint64_t seed, double *sum_y,
+                       double *totals);
+
+/* Replay walks rep_begin .. rep_begin+reps-1 of every row at one level and
+ * record each (the same kernel and launch shape as mlmc_mlmcl, with
+ * recording on).  rec: device pointer, n*reps records, index row*reps +
+ * (rep - rep_begin).  Asynchronous. */
+mlmc_status mlmc_trace(mlmc_plan *plan, int32_t level, int32_t coarse, int64_t rep_begin,
+                       int64_t reps, const double *v, uint64_t seed, mlmc_walk_record *rec);
+
+/* Copy the device tables to host arrays (any pointer may be NULL):
+ *   l_ii, dl (= t d_i), inv_rate (1/(t L_ii), +inf when L_ii = 0): n doubles
+ *   inv_rate32, dl32: n floats (the FP32 copies the FP32 walk uses)
+ *   deg: n int32 (off-diagonal count)
+ *   thr, keep_col, alias_col: nnz entries at positions row_ptr[i] + b for
+ *   bucket b < deg_i; keep_neg/alias_neg: nnz bytes (1 = negative a_ij).
+ * Synchronises the plan's stream. */
+mlmc_status mlmc_export_tables(const mlmc_plan *plan, double *l_ii, double *dl, double *inv_rate,
+                               float *inv_rate32, float *dl32, int32_t *deg, uint32_t *thr,
+                               int32_t *keep_col, uint8_t *keep_neg, int32_t *alias_col,
+                               uint8_t *alias_neg);
+
+/* Plan facts: n, nnz, the chosen l0, and t. Any pointer may be NULL. */
+mlmc_status mlmc_plan_info(const mlmc_plan *plan, int64_t *n, int64_t *nnz, int32_t *l0,
+                           double *t);
+
+/* Free the plan and all its device memory (NULL is a no-op). */
+void mlmc_plan_destroy(mlmc_plan *plan);
+
+/* Message for the last failure on the calling thread ("" if none). */
+const char *mlmc_last_error(void);
+
+/* Kernels launched on the plan's stream since creation (all of this
+ * library's kernels, for launch accounting). */
+int64_t mlmc_launch_count(const mlmc_plan *plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MLMC_H */

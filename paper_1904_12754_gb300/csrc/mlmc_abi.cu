@@ -1,0 +1,529 @@
+// C ABI of libmlmc and the MLMC controller (Algorithm 1).
+//
+// The controller keeps, per level l (slot l - l0), the device vector S_l of
+// per-row sums of Y and four totals (sum Y^2, jumps, walks, limit hits).
+// After each round of launches it reduces sum_i S_l,i^2 on the device and
+// reads back a handful of scalars per level:
+//   V_l   = (sum Y^2 - sum_i S_l,i^2 / M_l) / (M_l - 1)    total variance of
+//           one sample (one walk from every row), unbiased;
+//   C_l   = n (1 + jumps / walks)                          events per sample;
+//   m_l   = S_l / M_l,  ||m_l||^2 = sum_i S_l,i^2 / M_l^2.
+// With eps = rel_tol ||x|| it sets M_l = ceil(2/eps^2 sqrt(V_l/C_l)
+// sum_k sqrt(V_k C_k)) (Giles' optimum; the paper's Eq. 11 prints it without
+// the root and the factor 2), tops levels up, and stops when
+// sum_l V_l/M_l <= eps^2/2 and max(||m_L||, ||m_{L-1}||/4)/3 <= eps/sqrt(2)
+// (weak order 2, Eq. 13); otherwise it appends level L+1 (Algorithm 1).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "mlmc_internal.h"
+
+namespace mlmc {
+
+namespace {
+thread_local std::string g_last_error;
+
+mlmc_status fail(mlmc_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+mlmc_status cuda_fail(cudaError_t err, const char* what) {
+  return fail(err == cudaErrorMemoryAllocation ? MLMC_ERR_OOM : MLMC_ERR_CUDA,
+              std::string(what) + ": " + cudaGetErrorString(err));
+}
+
+#define MLMC_CUDA(call, what)                   \
+  do {                                          \
+    cudaError_t e_ = (call);                    \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+// The device neglog uses literal coefficients; they must be the correctly
+// rounded 1/(2k+1), which is what IEEE division on the host produces.
+bool coefficients_ok() {
+  for (int k = 0; k < kNeglogTerms64; ++k) {
+    volatile double d = static_cast<double>(2 * k + 1);
+    if (neglog_c64(k) != 1.0 / d) return false;
+  }
+  for (int k = 0; k < kNeglogTerms32; ++k) {
+    volatile float d = static_cast<float>(2 * k + 1);
+    if (neglog_c32(k) != 1.0f / d) return false;
+  }
+  return true;
+}
+
+template <typename T>
+cudaError_t dev_alloc(T** p, size_t count) {
+  return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (count > 0 ? count : 1));
+}
+
+void free_plan(mlmc_plan* p) {
+  if (!p) return;
+  cudaFree(p->d_row_ptr);
+  cudaFree(p->d_col);
+  cudaFree(p->d_val);
+  cudaFree(p->d_meta32);
+  cudaFree(p->d_meta64);
+  cudaFree(p->d_lii);
+  cudaFree(p->d_alias);
+  cudaFree(p->d_flags);
+  cudaFree(p->d_work);
+  cudaFree(p->d_totals);
+  cudaFree(p->d_v);
+  cudaFree(p->d_v32);
+  cudaFree(p->d_x);
+  cudaFree(p->d_norm2);
+  if (!p->levels.empty()) cudaFree(p->levels[0].sum_y);
+  if (p->ev0) cudaEventDestroy(p->ev0);
+  if (p->ev1) cudaEventDestroy(p->ev1);
+  delete p;
+}
+
+mlmc_status read_flags(mlmc_plan* p, uint32_t* out) {
+  MLMC_CUDA(cudaMemcpyAsync(out, p->d_flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, p->stream),
+            "read flags");
+  MLMC_CUDA(cudaStreamSynchronize(p->stream), "synchronize");
+  return MLMC_OK;
+}
+
+std::string flag_text(uint32_t f) {
+  std::string s;
+  if (f & kFlagBadRowPtr) s += " row_ptr not monotone / not ending at nnz;";
+  if (f & kFlagBadCol) s += " column index out of range;";
+  if (f & kFlagUnsorted) s += " columns not strictly increasing within a row;";
+  if (f & kFlagNonFinite) s += " non-finite matrix value;";
+  if (f & kFlagWalkLimit) s += " a walk exceeded max_jumps_per_walk;";
+  if (f & kFlagNonFiniteY) s += " non-finite walk weight;";
+  return s;
+}
+
+struct HostLevel {
+  double y2, jumps, walks, limit, sumsq;
+};
+
+}  // namespace
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+// Per-level device scalars live at d_totals[slot * kTotSlots].
+static double* totals_of(mlmc_plan* p, int slot) { return p->d_totals + slot * kTotSlots; }
+
+static mlmc_status run_level(mlmc_plan* p, int slot, int64_t extra, uint64_t seed,
+                             std::vector<char>& timed) {
+  LevelAcc& L = p->levels[slot];
+  WalkLaunch w;
+  w.level = p->l0 + slot;
+  w.coarse = slot > 0;
+  w.rep_begin = L.reps;
+  w.reps = extra;
+  w.seed = seed;
+  w.v = p->d_v;
+  w.sum_y = L.sum_y;
+  w.totals = totals_of(p, slot);
+  MLMC_CUDA(cudaEventRecord(p->ev0, p->stream), "event record");
+  MLMC_CUDA(launch_walk(p, w), "walk kernel launch");
+  MLMC_CUDA(cudaEventRecord(p->ev1, p->stream), "event record");
+  MLMC_CUDA(cudaEventSynchronize(p->ev1), "event synchronize");
+  float ms = 0.f;
+  MLMC_CUDA(cudaEventElapsedTime(&ms, p->ev0, p->ev1), "event elapsed");
+  L.seconds += 1e-3 * ms;
+  L.reps += extra;
+  timed[slot] = 1;
+  return MLMC_OK;
+}
+
+// Reduce sum_i S_i^2 per level and ||x||^2, and read the scalars back.
+static mlmc_status collect(mlmc_plan* p, int nl, std::vector<HostLevel>& out, double* norm2) {
+  for (int k = 0; k < nl; ++k) {
+    MLMC_CUDA(cudaMemsetAsync(totals_of(p, k) + kTotSumSq, 0, sizeof(double), p->stream), "memset");
+    MLMC_CUDA(launch_sumsq(p, p->levels[k].sum_y, totals_of(p, k) + kTotSumSq, 1.0), "sumsq");
+  }
+  MLMC_CUDA(launch_finalize(p, nl, nullptr, p->d_norm2), "finalize");
+  std::vector<double> h(static_cast<size_t>(nl) * kTotSlots + 1);
+  MLMC_CUDA(cudaMemcpyAsync(h.data(), p->d_totals, sizeof(double) * nl * kTotSlots,
+                            cudaMemcpyDeviceToHost, p->stream), "read totals");
+  MLMC_CUDA(cudaMemcpyAsync(h.data() + nl * kTotSlots, p->d_norm2, sizeof(double),
+                            cudaMemcpyDeviceToHost, p->stream), "read norm");
+  MLMC_CUDA(cudaStreamSynchronize(p->stream), "synchronize");
+  out.resize(nl);
+  for (int k = 0; k < nl; ++k) {
+    const double* t = h.data() + k * kTotSlots;
+    out[k] = HostLevel{t[kTotY2], t[kTotJumps], t[kTotWalks], t[kTotLimit], t[kTotSumSq]};
+  }
+  *norm2 = h[nl * kTotSlots];
+  return MLMC_OK;
+}
+
+static double level_var(const mlmc_plan* p, int k, const HostLevel& h) {
+  const double m = static_cast<double>(p->levels[k].reps);
+  if (m < 2) return 0.0;
+  return std::max(0.0, (h.y2 - h.sumsq / m) / (m - 1.0));
+}
+
+static double level_cost(const mlmc_plan* p, const HostLevel& h) {
+  const double per_walk = h.walks > 0 ? 1.0 + h.jumps / h.walks : 1.0;
+  return static_cast<double>(p->n) * per_walk;
+}
+
+}  // namespace mlmc
+
+using namespace mlmc;
+
+extern "C" {
+
+mlmc_status mlmc_schedule_default(mlmc_schedule* s) {
+  if (!s) return fail(MLMC_ERR_INVALID_ARG, "mlmc_schedule_default: NULL schedule");
+  std::memset(s, 0, sizeof(*s));
+  s->l0 = -1;
+  s->num_levels = 5;
+  s->max_levels = 12;
+  s->precision = MLMC_FP64;
+  s->mode = MLMC_BACKWARD;
+  s->proposal = MLMC_PLAIN;
+  s->pilot_walks = 64;
+  s->max_jumps_per_walk = 1 << 20;
+  s->max_walks_per_row = 1ll << 34;
+  s->time_budget_s = 600.0;
+  s->walks_per_lane = 0;
+  s->block_threads = 0;
+  return MLMC_OK;
+}
+
+const char* mlmc_last_error(void) { return g_last_error.c_str(); }
+
+mlmc_status mlmc_plan_create(mlmc_plan** out, int64_t n, int64_t nnz, const int64_t* row_ptr,
+                             const int32_t* col, const double* vals, double t,
+                             const mlmc_schedule* sched, double rel_tol, void* cuda_stream) {
+  g_last_error.clear();
+  if (!out) return fail(MLMC_ERR_INVALID_ARG, "mlmc_plan_create: NULL out");
+  *out = nullptr;
+  if (!coefficients_ok()) return fail(MLMC_ERR_NUMERIC, "neglog coefficients are not 1/(2k+1)");
+  if (n < 1 || n >= (1ll << 31)) return fail(MLMC_ERR_INVALID_ARG, "n must be in [1, 2^31)");
+  if (nnz < 0 || nnz >= (1ll << 31)) return fail(MLMC_ERR_INVALID_ARG, "nnz must be in [0, 2^31)");
+  if (!row_ptr || (nnz > 0 && (!col || !vals)))
+    return fail(MLMC_ERR_INVALID_ARG, "NULL CSR pointer");
+  if (!(t >= 0.0) || !std::isfinite(t)) return fail(MLMC_ERR_INVALID_ARG, "t must be finite and >= 0");
+  if (!(rel_tol > 0.0) || !std::isfinite(rel_tol))
+    return fail(MLMC_ERR_INVALID_ARG, "rel_tol must be finite and > 0");
+  mlmc_schedule s;
+  if (sched) s = *sched; else mlmc_schedule_default(&s);
+  if (s.num_levels < 1 || s.max_levels < s.num_levels || s.max_levels > 32)
+    return fail(MLMC_ERR_INVALID_ARG, "need 1 <= num_levels <= max_levels <= 32");
+  if (s.precision != MLMC_FP64 && s.precision != MLMC_FP32_KAHAN)
+    return fail(MLMC_ERR_INVALID_ARG, "unknown precision");
+  if (s.mode != MLMC_BACKWARD) return fail(MLMC_ERR_INVALID_ARG, "only MLMC_BACKWARD is available");
+  if (s.proposal != MLMC_PLAIN) return fail(MLMC_ERR_INVALID_ARG, "only MLMC_PLAIN is available");
+  if (s.pilot_walks < 2 || s.max_jumps_per_walk < 0 || s.max_jumps_per_walk > 0xFFFFFFF0ll ||
+      s.max_walks_per_row < s.pilot_walks || s.max_walks_per_row > (1ll << 55))
+    return fail(MLMC_ERR_INVALID_ARG, "bad schedule budgets");
+  if (s.l0 > 24 || (s.l0 >= 0 && s.l0 + s.max_levels - 1 > 24))
+    return fail(MLMC_ERR_INVALID_ARG, "levels above 24 are not supported");
+  if (s.walks_per_lane < 0 || s.block_threads < 0 || s.block_threads % 32 != 0 ||
+      s.block_threads > 256)
+    return fail(MLMC_ERR_INVALID_ARG, "block_threads must be a multiple of 32 up to 256");
+
+  mlmc_plan* p = new mlmc_plan();
+  p->n = n;
+  p->nnz = nnz;
+  p->t = t;
+  p->rel_tol = rel_tol;
+  p->sched = s;
+  p->stream = static_cast<cudaStream_t>(cuda_stream);
+  auto bail = [&](mlmc_status st) {
+    free_plan(p);
+    return st;
+  };
+#define PLAN_CUDA(call, what)                                  \
+  do {                                                         \
+    cudaError_t e_ = (call);                                   \
+    if (e_ != cudaSuccess) return bail(cuda_fail(e_, what));   \
+  } while (0)
+  PLAN_CUDA(cudaGetDevice(&p->device), "cudaGetDevice");
+  PLAN_CUDA(cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device),
+            "device attribute");
+  PLAN_CUDA(dev_alloc(&p->d_row_ptr, n + 1), "alloc row_ptr");
+  PLAN_CUDA(dev_alloc(&p->d_col, nnz), "alloc col");
+  PLAN_CUDA(dev_alloc(&p->d_val, nnz), "alloc val");
+  PLAN_CUDA(dev_alloc(&p->d_meta32, n), "alloc meta32");
+  PLAN_CUDA(dev_alloc(&p->d_meta64, n), "alloc meta64");
+  PLAN_CUDA(dev_alloc(&p->d_lii, n), "alloc lii");
+  PLAN_CUDA(dev_alloc(&p->d_alias, nnz), "alloc alias");
+  PLAN_CUDA(dev_alloc(&p->d_flags, 4), "alloc flags");
+  PLAN_CUDA(dev_alloc(&p->d_work, 1), "alloc work");
+  PLAN_CUDA(dev_alloc(&p->d_totals, static_cast<size_t>(s.max_levels) * kTotSlots), "alloc totals");
+  PLAN_CUDA(dev_alloc(&p->d_v, n), "alloc v");
+  PLAN_CUDA(dev_alloc(&p->d_v32, n), "alloc v32");
+  PLAN_CUDA(dev_alloc(&p->d_x, n), "alloc x");
+  PLAN_CUDA(dev_alloc(&p->d_norm2, 4), "alloc scalars");
+  double* sums = nullptr;
+  PLAN_CUDA(dev_alloc(&sums, static_cast<size_t>(n) * s.max_levels), "alloc level sums");
+  p->levels.resize(s.max_levels);
+  for (int k = 0; k < s.max_levels; ++k) p->levels[k].sum_y = sums + static_cast<size_t>(k) * n;
+  PLAN_CUDA(cudaEventCreate(&p->ev0), "event create");
+  PLAN_CUDA(cudaEventCreate(&p->ev1), "event create");
+
+  PLAN_CUDA(cudaMemcpyAsync(p->d_row_ptr, row_ptr, sizeof(int64_t) * (n + 1), cudaMemcpyDefault,
+                            p->stream), "copy row_ptr");
+  if (nnz > 0) {
+    PLAN_CUDA(cudaMemcpyAsync(p->d_col, col, sizeof(int32_t) * nnz, cudaMemcpyDefault, p->stream),
+              "copy col");
+    PLAN_CUDA(cudaMemcpyAsync(p->d_val, vals, sizeof(double) * nnz, cudaMemcpyDefault, p->stream),
+              "copy vals");
+  }
+  PLAN_CUDA(cudaMemsetAsync(p->d_flags, 0, sizeof(uint32_t) * 4, p->stream), "memset flags");
+  PLAN_CUDA(launch_validate(p), "validate kernel");
+  uint32_t flags = 0;
+  {
+    mlmc_status st = read_flags(p, &flags);
+    if (st != MLMC_OK) return bail(st);
+  }
+  if (flags) return bail(fail(MLMC_ERR_INVALID_ARG, "invalid CSR:" + flag_text(flags)));
+  mlmc_status st = mlmc_plan_rebuild(p);
+  if (st != MLMC_OK) return bail(st);
+  unsigned long long bits = 0;
+  PLAN_CUDA(cudaMemcpyAsync(&bits, p->d_norm2, sizeof(bits), cudaMemcpyDeviceToHost, p->stream),
+            "read dmax");
+  PLAN_CUDA(cudaStreamSynchronize(p->stream), "synchronize");
+  std::memcpy(&p->dmax_scaled, &bits, sizeof(bits));
+  if (s.l0 >= 0) {
+    p->l0 = s.l0;
+  } else {
+    // Eq. 16, l0 = log2(2 t d_max), with d_max = max_i max(|d_i|, L_ii),
+    // rounded up (values within 1e-9 of an integer count as that integer).
+    const double x = 2.0 * p->dmax_scaled;
+    p->l0 = x > 0.0 ? std::max(0, static_cast<int>(std::ceil(std::log2(x) - 1e-9))) : 0;
+  }
+  if (p->l0 + s.max_levels - 1 > 24) {
+    p->sched.max_levels = std::max(s.num_levels, 25 - p->l0);
+    if (p->l0 + p->sched.max_levels - 1 > 24)
+      return bail(fail(MLMC_ERR_INVALID_ARG, "l0 from Eq. 16 leaves no room for the levels"));
+  }
+#undef PLAN_CUDA
+  *out = p;
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_plan_rebuild(mlmc_plan* p) {
+  if (!p) return fail(MLMC_ERR_INVALID_ARG, "NULL plan");
+  MLMC_CUDA(launch_build_tables(p), "table build");
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_plan_info(const mlmc_plan* p, int64_t* n, int64_t* nnz, int32_t* l0, double* t) {
+  if (!p) return fail(MLMC_ERR_INVALID_ARG, "NULL plan");
+  if (n) *n = p->n;
+  if (nnz) *nnz = p->nnz;
+  if (l0) *l0 = p->l0;
+  if (t) *t = p->t;
+  return MLMC_OK;
+}
+
+int64_t mlmc_launch_count(const mlmc_plan* p) { return p ? p->launches : 0; }
+
+void mlmc_plan_destroy(mlmc_plan* p) { free_plan(p); }
+
+mlmc_status mlmc_mlmcl(mlmc_plan* p, int32_t level, int32_t coarse, int64_t rep_begin,
+                       int64_t reps, const double* v, uint64_t seed, double* sum_y,
+                       double* totals) {
+  if (!p || !v || !sum_y || !totals) return fail(MLMC_ERR_INVALID_ARG, "NULL argument");
+  if (level < 0 || level > 24 || (coarse && level < 1))
+    return fail(MLMC_ERR_INVALID_ARG, "level must be in [0,24] (>= 1 when coarse)");
+  if (rep_begin < 0 || reps < 0 || rep_begin + reps > (1ll << 56))
+    return fail(MLMC_ERR_INVALID_ARG, "replica range out of [0, 2^56)");
+  WalkLaunch w;
+  w.level = level;
+  w.coarse = coarse != 0;
+  w.rep_begin = rep_begin;
+  w.reps = reps;
+  w.seed = seed;
+  w.v = v;
+  w.sum_y = sum_y;
+  w.totals = totals;
+  MLMC_CUDA(launch_walk(p, w), "walk kernel launch");
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_trace(mlmc_plan* p, int32_t level, int32_t coarse, int64_t rep_begin,
+                       int64_t reps, const double* v, uint64_t seed, mlmc_walk_record* rec) {
+  if (!p || !v || !rec) return fail(MLMC_ERR_INVALID_ARG, "NULL argument");
+  if (level < 0 || level > 24 || (coarse && level < 1))
+    return fail(MLMC_ERR_INVALID_ARG, "level must be in [0,24] (>= 1 when coarse)");
+  if (rep_begin < 0 || reps < 0 || rep_begin + reps > (1ll << 56))
+    return fail(MLMC_ERR_INVALID_ARG, "replica range out of [0, 2^56)");
+  double* scratch = nullptr;
+  MLMC_CUDA(dev_alloc(&scratch, static_cast<size_t>(p->n) + kTotSlots), "alloc trace sums");
+  cudaError_t err = cudaMemsetAsync(scratch, 0, sizeof(double) * (p->n + kTotSlots), p->stream);
+  WalkLaunch w;
+  w.level = level;
+  w.coarse = coarse != 0;
+  w.rep_begin = rep_begin;
+  w.reps = reps;
+  w.seed = seed;
+  w.v = v;
+  w.sum_y = scratch;
+  w.totals = scratch + p->n;
+  w.trace = rec;
+  if (err == cudaSuccess) err = launch_walk(p, w);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(p->stream);
+  cudaFree(scratch);
+  if (err != cudaSuccess) return cuda_fail(err, "trace launch");
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_expmv(mlmc_plan* p, const double* v, double* x, uint64_t seed) {
+  g_last_error.clear();
+  if (!p || !v || !x) return fail(MLMC_ERR_INVALID_ARG, "NULL argument");
+  const auto t_start = std::chrono::steady_clock::now();
+  const mlmc_schedule& s = p->sched;
+  MLMC_CUDA(cudaMemcpyAsync(p->d_v, v, sizeof(double) * p->n, cudaMemcpyDefault, p->stream), "copy v");
+  MLMC_CUDA(cudaMemsetAsync(p->d_flags, 0, sizeof(uint32_t) * 4, p->stream), "memset flags");
+  MLMC_CUDA(cudaMemsetAsync(p->levels[0].sum_y, 0, sizeof(double) * p->n * s.max_levels, p->stream),
+            "memset sums");
+  MLMC_CUDA(cudaMemsetAsync(p->d_totals, 0, sizeof(double) * kTotSlots * s.max_levels, p->stream),
+            "memset totals");
+  for (auto& L : p->levels) {
+    L.reps = 0;
+    L.seconds = 0.0;
+  }
+  std::vector<char> timed(s.max_levels, 0);
+  int nl = s.num_levels;
+  mlmc_status st = MLMC_OK;
+  for (int k = 0; k < nl && st == MLMC_OK; ++k) st = run_level(p, k, s.pilot_walks, seed, timed);
+  if (st != MLMC_OK) return st;
+
+  std::vector<HostLevel> h;
+  double norm2 = 0.0;
+  bool converged = false;
+  mlmc_status result = MLMC_OK;
+  for (int iter = 0; iter < 64; ++iter) {
+    if ((st = collect(p, nl, h, &norm2)) != MLMC_OK) return st;
+    double eps = p->rel_tol * std::sqrt(norm2);
+    // Optimal sample sizes and top-up.
+    std::vector<double> V(nl), C(nl);
+    double root_sum = 0.0;
+    for (int k = 0; k < nl; ++k) {
+      V[k] = level_var(p, k, h[k]);
+      C[k] = level_cost(p, h[k]);
+      root_sum += std::sqrt(V[k] * C[k]);
+    }
+    bool topped = false;
+    if (eps > 0.0) {
+      for (int k = 0; k < nl; ++k) {
+        if (V[k] <= 0.0) continue;
+        double target = std::ceil(2.0 / (eps * eps) * std::sqrt(V[k] / C[k]) * root_sum);
+        target = std::min(target, static_cast<double>(s.max_walks_per_row));
+        const int64_t want = static_cast<int64_t>(target);
+        if (want > p->levels[k].reps) {
+          if ((st = run_level(p, k, want - p->levels[k].reps, seed, timed)) != MLMC_OK) return st;
+          topped = true;
+        }
+      }
+    }
+    if (topped) {
+      if ((st = collect(p, nl, h, &norm2)) != MLMC_OK) return st;
+      eps = p->rel_tol * std::sqrt(norm2);
+    }
+    double var = 0.0;
+    for (int k = 0; k < nl; ++k) var += level_var(p, k, h[k]) / static_cast<double>(p->levels[k].reps);
+    auto mnorm = [&](int k) {
+      const double m = static_cast<double>(p->levels[k].reps);
+      return std::sqrt(h[k].sumsq) / m;
+    };
+    const double bias = nl > 1 ? std::max(mnorm(nl - 1), mnorm(nl - 2) / 4.0) / 3.0 : 0.0;
+    const bool var_ok = var <= 0.5 * eps * eps * (1.0 + 1e-12);
+    const bool bias_ok = bias <= eps / std::sqrt(2.0);
+    p->last_est_rel_err = norm2 > 0 ? std::sqrt(var / norm2) : 0.0;
+    if (var_ok && bias_ok) {
+      converged = true;
+      break;
+    }
+    const double elapsed =
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    if (elapsed > s.time_budget_s) break;
+    if (!bias_ok && nl < s.max_levels) {
+      if ((st = run_level(p, nl, s.pilot_walks, seed, timed)) != MLMC_OK) return st;
+      ++nl;
+      continue;
+    }
+    bool capped = true;
+    for (int k = 0; k < nl; ++k)
+      if (level_var(p, k, h[k]) > 0.0 && p->levels[k].reps < s.max_walks_per_row) capped = false;
+    if (capped || !bias_ok) break;
+  }
+  if (!converged) result = fail(MLMC_ERR_NOT_CONVERGED, "budget exhausted before the tolerance");
+
+  // Final cross-level sum (Eq. 10) in FP64 and copy-out.
+  MLMC_CUDA(launch_finalize(p, nl, p->d_x, p->d_norm2), "finalize");
+  MLMC_CUDA(cudaMemcpyAsync(x, p->d_x, sizeof(double) * p->n, cudaMemcpyDefault, p->stream), "copy x");
+  uint32_t flags = 0;
+  if ((st = read_flags(p, &flags)) != MLMC_OK) return st;
+  p->last_stats.clear();
+  for (int k = 0; k < nl; ++k) {
+    mlmc_level_stats ls{};
+    ls.level = p->l0 + k;
+    ls.walks_per_row = p->levels[k].reps;
+    const double m = static_cast<double>(p->levels[k].reps);
+    ls.mean_norm2 = h[k].sumsq / (m * m);
+    ls.var = level_var(p, k, h[k]);
+    ls.cost_events_per_walk = h[k].walks > 0 ? 1.0 + h[k].jumps / h[k].walks : 1.0;
+    ls.jumps = static_cast<int64_t>(h[k].jumps);
+    ls.seconds = p->levels[k].seconds;
+    p->last_stats.push_back(ls);
+  }
+  if (flags & kFlagWalkLimit) return fail(MLMC_ERR_WALK_LIMIT, "walk limit:" + flag_text(flags));
+  if (flags & kFlagNonFiniteY) return fail(MLMC_ERR_NUMERIC, "numeric:" + flag_text(flags));
+  return result;
+}
+
+mlmc_status mlmc_stats(const mlmc_plan* p, mlmc_level_stats* out, int32_t cap, int32_t* n_levels,
+                       double* est_rel_err) {
+  if (!p) return fail(MLMC_ERR_INVALID_ARG, "NULL plan");
+  const int32_t nl = static_cast<int32_t>(p->last_stats.size());
+  if (out)
+    for (int32_t k = 0; k < nl && k < cap; ++k) out[k] = p->last_stats[k];
+  if (n_levels) *n_levels = nl;
+  if (est_rel_err) *est_rel_err = p->last_est_rel_err;
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_export_tables(const mlmc_plan* pc, double* l_ii, double* dl, double* inv_rate,
+                               float* inv_rate32, float* dl32, int32_t* deg, uint32_t* thr,
+                               int32_t* keep_col, uint8_t* keep_neg, int32_t* alias_col,
+                               uint8_t* alias_neg) {
+  mlmc_plan* p = const_cast<mlmc_plan*>(pc);
+  if (!p) return fail(MLMC_ERR_INVALID_ARG, "NULL plan");
+  std::vector<Meta32> m32(p->n);
+  std::vector<Meta64> m64(p->n);
+  std::vector<AliasEntry> al(p->nnz > 0 ? p->nnz : 1);
+  std::vector<double> lii(p->n);
+  MLMC_CUDA(cudaMemcpyAsync(m32.data(), p->d_meta32, sizeof(Meta32) * p->n, cudaMemcpyDeviceToHost, p->stream), "copy");
+  MLMC_CUDA(cudaMemcpyAsync(m64.data(), p->d_meta64, sizeof(Meta64) * p->n, cudaMemcpyDeviceToHost, p->stream), "copy");
+  MLMC_CUDA(cudaMemcpyAsync(lii.data(), p->d_lii, sizeof(double) * p->n, cudaMemcpyDeviceToHost, p->stream), "copy");
+  if (p->nnz > 0)
+    MLMC_CUDA(cudaMemcpyAsync(al.data(), p->d_alias, sizeof(AliasEntry) * p->nnz, cudaMemcpyDeviceToHost, p->stream), "copy");
+  MLMC_CUDA(cudaStreamSynchronize(p->stream), "synchronize");
+  for (int64_t i = 0; i < p->n; ++i) {
+    if (l_ii) l_ii[i] = lii[i];
+    if (dl) dl[i] = m64[i].dl;
+    if (inv_rate) inv_rate[i] = m64[i].inv_rate;
+    if (inv_rate32) inv_rate32[i] = m32[i].inv_rate;
+    if (dl32) dl32[i] = m32[i].dl;
+    if (deg) deg[i] = m32[i].deg;
+    for (int32_t b = 0; b < m32[i].deg; ++b) {
+      const AliasEntry& e = al[m32[i].start + b];
+      const int64_t q = m32[i].start + b;
+      if (thr) thr[q] = e.thr;
+      if (keep_col) keep_col[q] = static_cast<int32_t>(e.keep & kColMask);
+      if (keep_neg) keep_neg[q] = static_cast<uint8_t>(e.keep >> 31);
+      if (alias_col) alias_col[q] = static_cast<int32_t>(e.alias & kColMask);
+      if (alias_neg) alias_neg[q] = static_cast<uint8_t>(e.alias >> 31);
+    }
+  }
+  return MLMC_OK;
+}
+
+}  // extern "C"

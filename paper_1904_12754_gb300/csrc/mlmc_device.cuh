@@ -1,0 +1,156 @@
+// Device primitives of the MLMC walk: Philox4x32-10, uniforms, -ln(u), and
+// the packed table layouts.  Every floating-point step uses an explicit
+// round-to-nearest intrinsic (no FMA contraction), so a walk's decisions are
+// a fixed function of its counter and can be replayed exactly on a CPU.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mlmc {
+
+// ---------------------------------------------------------------------------
+// Table layouts (device)
+// ---------------------------------------------------------------------------
+// Per-row record for the FP32 walk: alias row start (= CSR row start),
+// off-diagonal count, 1/(t L_ii) and t d_i (Eq. 1, scaled time).  16 bytes:
+// one LDG.128 per visited state.
+struct __align__(16) Meta32 {
+  int32_t start;
+  int32_t deg;
+  float inv_rate;
+  float dl;
+};
+
+// Per-row record for the FP64 walk (32 bytes, one sector).
+struct __align__(16) Meta64 {
+  int32_t start;
+  int32_t deg;
+  int32_t pad0;
+  int32_t pad1;
+  double inv_rate;
+  double dl;
+};
+
+// Alias entry (16 bytes, one LDG.128 per jump): threshold, kept column and
+// alias column, each column with the sign of a_ij in bit 31.
+// While a row's table is being built the same 16 bytes hold the bucket's
+// working probability (double) and the next-bucket link of the Vose queue.
+struct __align__(16) AliasEntry {
+  uint32_t thr;
+  uint32_t keep;
+  uint32_t alias;
+  uint32_t pad;
+};
+
+constexpr uint32_t kSignBit = 0x80000000u;
+constexpr uint32_t kColMask = 0x7FFFFFFFu;
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11)
+// ---------------------------------------------------------------------------
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
+constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += kPhiloxW0;
+      k1 += kPhiloxW1;
+    }
+    const uint32_t hi0 = __umulhi(kPhiloxM0, c.x);
+    const uint32_t lo0 = kPhiloxM0 * c.x;
+    const uint32_t hi1 = __umulhi(kPhiloxM1, c.z);
+    const uint32_t lo1 = kPhiloxM1 * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+// ---------------------------------------------------------------------------
+// Uniforms in (0,1): odd multiples of 2^-53 (FP64) or 2^-24 (FP32), exact.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double uniform64(uint32_t x0, uint32_t x1) {
+  const unsigned long long w = (static_cast<unsigned long long>(x0) << 32) | x1;
+  return __dmul_rn(__ull2double_rn((w >> 11) | 1ull), 0x1p-53);
+}
+
+__device__ __forceinline__ float uniform32(uint32_t x0) {
+  return __fmul_rn(__uint2float_rn((x0 >> 8) | 1u), 0x1p-24f);
+}
+
+// ---------------------------------------------------------------------------
+// -ln(u) for normal u in (0,1).
+// u = m 2^e, m in [sqrt(1/2), sqrt(2)); ln m = 2 atanh(z) = 2 z sum_k
+// z^{2k}/(2k+1) with z = (m-1)/(m+1), |z| <= 0.1716 (12 terms FP64, 6 FP32);
+// ln u = e ln2_hi + (e ln2_lo + ln m), ln2_hi with trailing zero bits so the
+// product is exact.  Coefficients are 1/(2k+1) correctly rounded; the host
+// checks these literals against its own IEEE division at library load.
+// ---------------------------------------------------------------------------
+constexpr double kLn2Hi64 = 0x1.62e42fefa3800p-1;
+constexpr double kLn2Lo64 = 0x1.ef35793c76730p-45;
+constexpr float kLn2Hi32 = 0x1.62e400p-1f;
+constexpr float kLn2Lo32 = 0x1.7f7d1cp-20f;
+constexpr double kSqrtHalf64 = 0x1.6a09e667f3bcdp-1;
+constexpr float kSqrtHalf32 = 0x1.6a09e6p-1f;
+
+constexpr int kNeglogTerms64 = 12;
+constexpr int kNeglogTerms32 = 6;
+
+__host__ __device__ constexpr double neglog_c64(int k) {
+  constexpr double c[kNeglogTerms64] = {
+      0x1.0000000000000p+0, 0x1.5555555555555p-2, 0x1.999999999999ap-3, 0x1.2492492492492p-3,
+      0x1.c71c71c71c71cp-4, 0x1.745d1745d1746p-4, 0x1.3b13b13b13b14p-4, 0x1.1111111111111p-4,
+      0x1.e1e1e1e1e1e1ep-5, 0x1.af286bca1af28p-5, 0x1.8618618618618p-5, 0x1.642c8590b2164p-5};
+  return c[k];
+}
+
+__host__ __device__ constexpr float neglog_c32(int k) {
+  constexpr float c[kNeglogTerms32] = {0x1.000000p+0f, 0x1.555556p-2f, 0x1.99999ap-3f,
+                                       0x1.24924ap-3f, 0x1.c71c72p-4f, 0x1.745d18p-4f};
+  return c[k];
+}
+
+__device__ __forceinline__ double neglog64(double u) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(u));
+  int e = static_cast<int>((b >> 52) & 0x7ffull) - 1022;
+  double m = __longlong_as_double(
+      static_cast<long long>((b & 0x000fffffffffffffull) | (0x3feull << 52)));
+  if (m < kSqrtHalf64) {
+    m = __dmul_rn(m, 2.0);
+    e -= 1;
+  }
+  const double z = __ddiv_rn(__dsub_rn(m, 1.0), __dadd_rn(m, 1.0));
+  const double z2 = __dmul_rn(z, z);
+  double p = neglog_c64(kNeglogTerms64 - 1);
+#pragma unroll
+  for (int k = kNeglogTerms64 - 2; k >= 0; --k) p = __dadd_rn(__dmul_rn(p, z2), neglog_c64(k));
+  const double lnm = __dmul_rn(__dmul_rn(2.0, z), p);
+  const double ed = static_cast<double>(e);
+  const double lnu = __dadd_rn(__dmul_rn(ed, kLn2Hi64), __dadd_rn(__dmul_rn(ed, kLn2Lo64), lnm));
+  return -lnu;
+}
+
+__device__ __forceinline__ float neglog32(float u) {
+  const uint32_t b = __float_as_uint(u);
+  int e = static_cast<int>((b >> 23) & 0xffu) - 126;
+  float m = __uint_as_float((b & 0x007fffffu) | (0x7eu << 23));
+  if (m < kSqrtHalf32) {
+    m = __fmul_rn(m, 2.0f);
+    e -= 1;
+  }
+  const float z = __fdiv_rn(__fsub_rn(m, 1.0f), __fadd_rn(m, 1.0f));
+  const float z2 = __fmul_rn(z, z);
+  float p = neglog_c32(kNeglogTerms32 - 1);
+#pragma unroll
+  for (int k = kNeglogTerms32 - 2; k >= 0; --k) p = __fadd_rn(__fmul_rn(p, z2), neglog_c32(k));
+  const float lnm = __fmul_rn(__fmul_rn(2.0f, z), p);
+  const float ef = static_cast<float>(e);
+  const float lnu = __fadd_rn(__fmul_rn(ef, kLn2Hi32), __fadd_rn(__fmul_rn(ef, kLn2Lo32), lnm));
+  return -lnu;
+}
+
+}  // namespace mlmc

@@ -1,0 +1,103 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/mlmc.h"
+#include "mlmc_device.cuh"
+
+namespace mlmc {
+
+// Error flags raised by kernels (bitwise OR into Plan::d_flags[0]).
+enum : uint32_t {
+  kFlagBadRowPtr = 1u << 0,
+  kFlagBadCol = 1u << 1,
+  kFlagUnsorted = 1u << 2,
+  kFlagNonFinite = 1u << 3,
+  kFlagWalkLimit = 1u << 4,
+  kFlagNonFiniteY = 1u << 5,
+};
+
+// Device accumulators of one level: sums of Y per row, and totals.
+struct LevelAcc {
+  double* sum_y = nullptr;  // [n]
+  int64_t reps = 0;         // walks per row taken so far
+  double seconds = 0.0;
+};
+
+// Totals slots of the per-level device scalars (doubles).
+enum { kTotY2 = 0, kTotJumps = 1, kTotWalks = 2, kTotLimit = 3, kTotSumSq = 4, kTotSlots = 8 };
+
+struct WalkLaunch {
+  int level = 0;
+  bool coarse = false;
+  int64_t rep_begin = 0;
+  int64_t reps = 0;
+  uint64_t seed = 0;
+  const double* v = nullptr;
+  double* sum_y = nullptr;
+  double* totals = nullptr;         // kTotSlots doubles
+  mlmc_walk_record* trace = nullptr;  // non-null selects the recording kernel
+};
+
+}  // namespace mlmc
+
+struct mlmc_plan {
+  int64_t n = 0;
+  int64_t nnz = 0;
+  double t = 0.0;
+  double rel_tol = 0.0;
+  int32_t l0 = 0;
+  mlmc_schedule sched{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int num_sms = 0;
+  int64_t launches = 0;
+
+  // Resident CSR copy.
+  int64_t* d_row_ptr = nullptr;
+  int32_t* d_col = nullptr;
+  double* d_val = nullptr;
+
+  // Tables (Eq. 1 split, Eq. 12 alias).
+  mlmc::Meta32* d_meta32 = nullptr;
+  mlmc::Meta64* d_meta64 = nullptr;
+  double* d_lii = nullptr;
+  mlmc::AliasEntry* d_alias = nullptr;
+  double dmax_scaled = 0.0;  // max_i max(|t d_i|, t L_ii)
+
+  // Work buffers.
+  uint32_t* d_flags = nullptr;                 // [4]
+  unsigned long long* d_work = nullptr;        // [1] dynamic work counter
+  double* d_totals = nullptr;                  // [max_levels * kTotSlots]
+  double* d_v = nullptr;                       // [n]
+  float* d_v32 = nullptr;                      // [n] FP32 copy for the FP32 walk
+  double* d_x = nullptr;                       // [n]
+  double* d_norm2 = nullptr;                   // [2]
+  std::vector<mlmc::LevelAcc> levels;          // per level slot (index l - l0)
+  std::vector<mlmc_level_stats> last_stats;
+  double last_est_rel_err = 0.0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace mlmc {
+
+// Thread-local error message.
+void set_error(const std::string& msg);
+
+// Table kernels (mlmc_tables.cu).
+cudaError_t launch_validate(mlmc_plan* p);
+cudaError_t launch_build_tables(mlmc_plan* p);
+
+// Walk kernels (mlmc_walk.cu).
+cudaError_t launch_walk(mlmc_plan* p, const WalkLaunch& w);
+
+// Reductions (mlmc_reduce.cu).
+cudaError_t launch_sumsq(mlmc_plan* p, const double* a, double* out, double scale);
+cudaError_t launch_finalize(mlmc_plan* p, int num_levels, double* x, double* norm2);
+
+}  // namespace mlmc

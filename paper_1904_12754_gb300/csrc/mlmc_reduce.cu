@@ -1,0 +1,89 @@
+// FP64 reductions of the controller: sum of squares of a level's per-row
+// sums (for V_l and ||m_l||), and the final cross-level sum
+// x = sum_l S_l / M_l (Eq. 10) with ||x||^2.
+#include "mlmc_internal.h"
+
+namespace mlmc {
+namespace {
+
+constexpr int kRedBlock = 256;
+constexpr int kMaxLevels = 32;
+
+struct FinalizeArgs {
+  const double* s[kMaxLevels];
+  double inv_m[kMaxLevels];
+  int count;
+};
+
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double part[kRedBlock / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
+  __syncthreads();
+  v = threadIdx.x < kRedBlock / 32 ? part[threadIdx.x] : 0.0;
+  if (threadIdx.x < 32) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  }
+  return v;
+}
+
+__global__ void __launch_bounds__(kRedBlock) k_sumsq(int64_t n, const double* __restrict__ a,
+                                                     double* __restrict__ out, double scale) {
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(kRedBlock) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * kRedBlock) {
+    const double x = a[i];
+    acc += x * x;
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) atomicAdd(out, acc * scale);
+}
+
+__global__ void __launch_bounds__(kRedBlock) k_finalize(int64_t n, FinalizeArgs f,
+                                                        double* __restrict__ x,
+                                                        double* __restrict__ norm2) {
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(kRedBlock) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * kRedBlock) {
+    double xi = 0.0;
+    for (int l = 0; l < f.count; ++l) xi += f.s[l][i] * f.inv_m[l];
+    if (x) x[i] = xi;
+    acc += xi * xi;
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) atomicAdd(norm2, acc);
+}
+
+int red_grid(const mlmc_plan* p) {
+  const int64_t want = (p->n + kRedBlock - 1) / kRedBlock;
+  const int64_t cap = static_cast<int64_t>(p->num_sms) * 8;
+  return static_cast<int>(want < 1 ? 1 : (want > cap ? cap : want));
+}
+
+}  // namespace
+
+cudaError_t launch_sumsq(mlmc_plan* p, const double* a, double* out, double scale) {
+  k_sumsq<<<red_grid(p), kRedBlock, 0, p->stream>>>(p->n, a, out, scale);
+  p->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(mlmc_plan* p, int num_levels, double* x, double* norm2) {
+  if (num_levels > kMaxLevels) return cudaErrorInvalidValue;
+  FinalizeArgs f{};
+  for (int k = 0; k < num_levels; ++k) {
+    const LevelAcc& L = p->levels[k];
+    f.s[k] = L.sum_y;
+    f.inv_m[k] = L.reps > 0 ? 1.0 / static_cast<double>(L.reps) : 0.0;
+  }
+  f.count = num_levels;
+  cudaError_t err = cudaMemsetAsync(norm2, 0, sizeof(double), p->stream);
+  if (err != cudaSuccess) return err;
+  k_finalize<<<red_grid(p), kRedBlock, 0, p->stream>>>(p->n, f, x, norm2);
+  p->launches++;
+  return cudaGetLastError();
+}
+
+}  // namespace mlmc

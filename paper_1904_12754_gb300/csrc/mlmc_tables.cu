@@ -1,0 +1,181 @@
+// Table build on the device: CSR validation, the split A = D - T of Sec. 2.1
+// (Eq. 1) and per-row Vose alias tables for the jump law of Eq. 12.
+//
+// One thread owns one row and scans it in stored order, so every sum and
+// every alias decision is a fixed sequence of IEEE operations (explicit
+// round-to-nearest, no contraction): the tables are identical bit for bit to
+// any implementation that performs the same sequence.
+#include <cmath>
+
+#include "mlmc_internal.h"
+
+namespace mlmc {
+namespace {
+
+constexpr int kTableBlock = 256;
+
+__global__ void k_validate(int64_t n, int64_t nnz, const int64_t* __restrict__ row_ptr,
+                           const int32_t* __restrict__ col, const double* __restrict__ val,
+                           uint32_t* __restrict__ flags) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t b = row_ptr[i];
+    const int64_t e = row_ptr[i + 1];
+    uint32_t f = 0;
+    if ((i == 0 && b != 0) || e < b || e > nnz || b < 0) {
+      atomicOr(flags, kFlagBadRowPtr);
+      continue;
+    }
+    if (i == n - 1 && e != nnz) f |= kFlagBadRowPtr;
+    int64_t prev = -1;
+    for (int64_t q = b; q < e; ++q) {
+      const int64_t c = col[q];
+      if (c < 0 || c >= n) f |= kFlagBadCol;
+      if (c <= prev) f |= kFlagUnsorted;
+      prev = c;
+      if (!isfinite(val[q])) f |= kFlagNonFinite;
+    }
+    if (f) atomicOr(flags, f);
+  }
+}
+
+// Per row i (one thread):
+//   pass 1  a_ii, L_ii = sum_{j != i} |a_ij| (stored order), deg_i; the
+//           scaled rate t L_ii and dl_i = t (a_ii + L_ii); both meta records.
+//   pass 2  p_b = (|a_b| deg) / L_ii for bucket b (the b-th off-diagonal),
+//           kept in the bucket's own entry with a FIFO link (small queue:
+//           p < 1, large queue: p >= 1, both in ascending b).
+//   pass 3  Vose: pop l from small and g from large; finalise l with
+//           threshold floor(p_l 2^32) and alias g; p_g = (p_g + p_l) - 1;
+//           append g to small (p_g < 1) or large.  Leftovers keep themselves.
+// A finalised entry overwrites its working values; at that point the bucket
+// is in no queue and its probability is no longer needed, so the build uses
+// no memory beyond the table itself.
+__global__ void k_build_tables(int64_t n, double t, const int64_t* __restrict__ row_ptr,
+                               const int32_t* __restrict__ col, const double* __restrict__ val,
+                               Meta32* __restrict__ meta32, Meta64* __restrict__ meta64,
+                               double* __restrict__ lii_out, AliasEntry* __restrict__ alias,
+                               unsigned long long* __restrict__ dmax_bits) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t rb = row_ptr[i];
+    const int64_t re = row_ptr[i + 1];
+    double diag = 0.0, lsum = 0.0;
+    int64_t dpos = -1;
+    for (int64_t q = rb; q < re; ++q) {
+      if (col[q] == i) {
+        diag = val[q];
+        dpos = q - rb;
+      } else {
+        lsum = __dadd_rn(lsum, fabs(val[q]));
+      }
+    }
+    const int32_t k = static_cast<int32_t>((re - rb) - (dpos >= 0 ? 1 : 0));
+    const double rate = __dmul_rn(t, lsum);
+    const double dl = __dmul_rn(t, __dadd_rn(diag, lsum));
+    const double inv_rate = rate > 0.0 ? __ddiv_rn(1.0, rate) : __longlong_as_double(0x7ff0000000000000ll);
+    Meta32 m32;
+    m32.start = static_cast<int32_t>(rb);
+    m32.deg = k;
+    m32.inv_rate = __double2float_rn(inv_rate);
+    m32.dl = __double2float_rn(dl);
+    meta32[i] = m32;
+    Meta64 m64;
+    m64.start = static_cast<int32_t>(rb);
+    m64.deg = k;
+    m64.pad0 = 0;
+    m64.pad1 = 0;
+    m64.inv_rate = inv_rate;
+    m64.dl = dl;
+    meta64[i] = m64;
+    lii_out[i] = lsum;
+    const double dm = fmax(fabs(dl), rate);
+    atomicMax(dmax_bits, static_cast<unsigned long long>(__double_as_longlong(dm)));
+    if (k == 0) continue;
+
+    // Bucket b lives at alias[rb + b]; its CSR position skips the diagonal.
+    AliasEntry* row = alias + rb;
+    auto csr_of = [&](int32_t b) -> int64_t { return rb + b + ((dpos >= 0 && b >= dpos) ? 1 : 0); };
+    auto col_word = [&](int32_t b) -> uint32_t {
+      const int64_t q = csr_of(b);
+      return static_cast<uint32_t>(col[q]) | (val[q] < 0.0 ? kSignBit : 0u);
+    };
+    auto p_of = [&](int32_t b) -> double& { return *reinterpret_cast<double*>(&row[b]); };
+    auto next_of = [&](int32_t b) -> int32_t& { return *reinterpret_cast<int32_t*>(&row[b].alias); };
+    auto finalise = [&](int32_t b, double prob, int32_t alias_b) {
+      const double scaled = floor(__dmul_rn(prob, 4294967296.0));
+      AliasEntry e;
+      e.thr = scaled >= 4294967295.0 ? 0xFFFFFFFFu : static_cast<uint32_t>(scaled);
+      e.keep = col_word(b);
+      e.alias = col_word(alias_b);
+      e.pad = 0u;
+      row[b] = e;
+    };
+
+    const double kd = static_cast<double>(k);
+    int32_t s_head = -1, s_tail = -1, g_head = -1, g_tail = -1;
+    auto push = [&](int32_t& head, int32_t& tail, int32_t b) {
+      next_of(b) = -1;
+      if (tail < 0) head = b; else next_of(tail) = b;
+      tail = b;
+    };
+    auto pop = [&](int32_t& head, int32_t& tail) -> int32_t {
+      const int32_t b = head;
+      head = next_of(b);
+      if (head < 0) tail = -1;
+      return b;
+    };
+    for (int32_t b = 0; b < k; ++b) {
+      const double w = fabs(val[csr_of(b)]);
+      const double p = lsum > 0.0 ? __ddiv_rn(__dmul_rn(w, kd), lsum) : 1.0;
+      p_of(b) = p;
+      if (p < 1.0) push(s_head, s_tail, b); else push(g_head, g_tail, b);
+    }
+    while (s_head >= 0 && g_head >= 0) {
+      const int32_t l = pop(s_head, s_tail);
+      const int32_t g = pop(g_head, g_tail);
+      const double pl = p_of(l);
+      const double pg = __dsub_rn(__dadd_rn(p_of(g), pl), 1.0);
+      finalise(l, pl, g);
+      p_of(g) = pg;
+      if (pg < 1.0) push(s_head, s_tail, g); else push(g_head, g_tail, g);
+    }
+    while (g_head >= 0) {
+      const int32_t g = pop(g_head, g_tail);
+      finalise(g, 1.0, g);
+    }
+    while (s_head >= 0) {
+      const int32_t l = pop(s_head, s_tail);
+      finalise(l, 1.0, l);
+    }
+  }
+}
+
+int grid_for(const mlmc_plan* p, int64_t items, int block) {
+  const int64_t want = (items + block - 1) / block;
+  const int64_t cap = static_cast<int64_t>(p->num_sms) * 16;
+  return static_cast<int>(want < 1 ? 1 : (want > cap ? cap : want));
+}
+
+}  // namespace
+
+cudaError_t launch_validate(mlmc_plan* p) {
+  k_validate<<<grid_for(p, p->n, kTableBlock), kTableBlock, 0, p->stream>>>(
+      p->n, p->nnz, p->d_row_ptr, p->d_col, p->d_val, p->d_flags);
+  p->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_tables(mlmc_plan* p) {
+  cudaError_t err = cudaMemsetAsync(p->d_norm2, 0, sizeof(double), p->stream);
+  if (err != cudaSuccess) return err;
+  // Narrow blocks: the work per row is as uneven as the degree distribution.
+  constexpr int kBuildBlock = 64;
+  k_build_tables<<<grid_for(p, p->n, kBuildBlock), kBuildBlock, 0, p->stream>>>(
+      p->n, p->t, p->d_row_ptr, p->d_col, p->d_val, p->d_meta32, p->d_meta64, p->d_lii,
+      p->d_alias, reinterpret_cast<unsigned long long*>(p->d_norm2));
+  p->launches++;
+  return cudaGetLastError();
+}
+
+}  // namespace mlmc

@@ -1,0 +1,468 @@
+// The walk kernel: MLMCL of Algorithm 2 for every row, event-driven.
+//
+// A walk of row i at level l (N = 2^l intervals of scaled time 1/N) is the
+// continuous-time Markov chain of Sec. 3 in scaled time s = tau/t: in state j
+// it holds for an Exp(t L_jj) time, then jumps to k with probability
+// |a_jk|/L_jj (alias table) and multiplies its sign by sign(a_jk).  Instead of
+// stepping through the N intervals (the paper's O(N) loop), the kernel visits
+// only events and counts grid points in closed form: a jump at time s falls
+// after grid point g = floor(s N) (exact: N is a power of two), so the state
+// held on (a, b] of grid indices contributes
+//   fine   (b - a)              grid points of level l,
+//   coarse floor(b/2) - floor(a/2) grid points of level l-1,
+//   and to the fine-minus-coarse difference (b mod 2) - (a mod 2),
+// with the first segment starting at a = -1 and the last ending at b = N.
+// Then, with h = (dl_start + dl_end)/2 (the half-weighted endpoints of Eq. 7),
+//   E_f = (acc_f - h)/N,  E_c = (acc_c - h)/(N/2),  E_f - E_c = (acc_d + h)/N
+// and the sample is Y = sign v_end e^{E_f} at the coarsest level and
+// Y = sign v_end e^{E_c} expm1(E_f - E_c) above it (Fig. 1; no cancellation).
+// Every walk draws one Philox4x32-10 block per holding time, counter
+// (rep_lo, row, jump index, level | rep_hi << 8), key = seed: words 0-1 give
+// the time, words 2-3 the bucket and the alias coin of the jump that ends it.
+//
+// Work decomposition: a warp takes one (row, chunk of walks) item at a time
+// from a global counter; its lanes share the chunk as a pool and a lane whose
+// walk ends takes the next unclaimed one at once (ballot + prefix count), so
+// lanes stay busy although walk lengths are geometric.  Per-row sums are reduced across the warp and added
+// with one FP64 atomic per item; totals are flushed once per warp.
+// The FP32 variant keeps times, exponents and weights in FP32 and sums Y per
+// row with Kahan compensation and sum Y^2 (which sets the sample sizes through
+// the variance estimate) as an exact-product FP32 pair; FP64 appears only in
+// the per-item warp reductions and the atomics.
+#include <cmath>
+
+#include "mlmc_internal.h"
+
+namespace mlmc {
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+struct WalkArgs {
+  const void* meta;
+  const AliasEntry* alias;
+  const void* v_walk;      // right-hand side in the walk precision
+  int64_t n;
+  int64_t rep_begin;
+  int64_t reps;
+  int64_t chunk;           // walks per item (multiple of 32)
+  int64_t chunks_per_row;
+  unsigned long long total_items;
+  int level;
+  uint32_t ctr3;           // level | stream << 6
+  uint32_t key0, key1;
+  int64_t max_jumps;
+  double* sum_y;
+  double* totals;
+  uint32_t* flags;
+  unsigned long long* work;
+  mlmc_walk_record* trace;
+};
+
+template <bool FP64>
+struct Prec;
+
+template <>
+struct Prec<false> {
+  using T = float;
+  using Meta = Meta32;
+  using VT = float;
+  __device__ static T uniform(uint4 x) { return uniform32(x.x); }
+  __device__ static T neglog(T u) { return neglog32(u); }
+  __device__ static T mul(T a, T b) { return __fmul_rn(a, b); }
+  __device__ static T add(T a, T b) { return __fadd_rn(a, b); }
+  __device__ static T sub(T a, T b) { return __fsub_rn(a, b); }
+  __device__ static T fma(T a, T b, T c) { return __fmaf_rn(a, b, c); }
+  __device__ static T from_int(int x) { return static_cast<float>(x); }
+  __device__ static T ex(T a) { return expf(a); }
+  __device__ static T exm1(T a) { return expm1f(a); }
+  __device__ static int floor_int(T a) { return static_cast<int>(floorf(a)); }
+};
+
+template <>
+struct Prec<true> {
+  using T = double;
+  using Meta = Meta64;
+  using VT = double;
+  __device__ static T uniform(uint4 x) { return uniform64(x.x, x.y); }
+  __device__ static T neglog(T u) { return neglog64(u); }
+  __device__ static T mul(T a, T b) { return __dmul_rn(a, b); }
+  __device__ static T add(T a, T b) { return __dadd_rn(a, b); }
+  __device__ static T sub(T a, T b) { return __dsub_rn(a, b); }
+  __device__ static T fma(T a, T b, T c) { return __fma_rn(a, b, c); }
+  __device__ static T from_int(int x) { return static_cast<double>(x); }
+  __device__ static T ex(T a) { return exp(a); }
+  __device__ static T exm1(T a) { return expm1(a); }
+  __device__ static int floor_int(T a) { return static_cast<int>(floor(a)); }
+};
+
+// Compensated (Kahan) accumulator.
+template <typename T>
+struct Kahan {
+  T s = 0, c = 0;
+  __device__ void add(T y);
+};
+template <>
+__device__ void Kahan<float>::add(float y) {
+  const float yy = __fsub_rn(y, c);
+  const float tt = __fadd_rn(s, yy);
+  c = __fsub_rn(__fsub_rn(tt, s), yy);
+  s = tt;
+}
+template <>
+__device__ void Kahan<double>::add(double y) {
+  s = __dadd_rn(s, y);
+}
+
+// Sum of non-negative terms kept as an unevaluated FP32 pair (hi + lo): each
+// y^2 enters as its exact product split (fl(y*y), fma error) and the running
+// sum uses Fast2Sum (|hi| >= each term).  Used for sum Y^2, whose
+// cancellation against (sum Y)^2/M decides the variance estimate.
+template <typename T>
+struct SquareSum;
+template <>
+struct SquareSum<float> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add_square(float y) {
+    const float p = __fmul_rn(y, y);
+    const float pe = __fmaf_rn(y, y, -p);
+    const float t = __fadd_rn(hi, p);
+    const float e = __fsub_rn(p, __fsub_rn(t, hi));
+    hi = t;
+    lo = __fadd_rn(lo, __fadd_rn(e, pe));
+  }
+  __device__ __forceinline__ double value() const {
+    return static_cast<double>(hi) + static_cast<double>(lo);
+  }
+};
+template <>
+struct SquareSum<double> {
+  double hi = 0.0;
+  __device__ __forceinline__ void add_square(double y) { hi = __dadd_rn(hi, __dmul_rn(y, y)); }
+  __device__ __forceinline__ double value() const { return hi; }
+};
+
+// Warp sum of a (sum, compensation) pair into one double.
+template <typename T>
+__device__ __forceinline__ double warp_sum(const Kahan<T>& k) {
+  double v = static_cast<double>(k.s) - static_cast<double>(k.c);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+template <typename Meta>
+__device__ __forceinline__ Meta load_meta(const Meta* m, int64_t j);
+
+template <>
+__device__ __forceinline__ Meta64 load_meta<Meta64>(const Meta64* m, int64_t j) {
+  const int4 a = __ldg(reinterpret_cast<const int4*>(m + j));
+  const double2 b = __ldg(reinterpret_cast<const double2*>(m + j) + 1);
+  Meta64 out;
+  out.start = a.x;
+  out.deg = a.y;
+  out.pad0 = 0;
+  out.pad1 = 0;
+  out.inv_rate = b.x;
+  out.dl = b.y;
+  return out;
+}
+
+template <>
+__device__ __forceinline__ Meta32 load_meta<Meta32>(const Meta32* m, int64_t j) {
+  const int4 r = __ldg(reinterpret_cast<const int4*>(m) + j);
+  Meta32 out;
+  out.start = r.x;
+  out.deg = r.y;
+  out.inv_rate = __int_as_float(r.z);
+  out.dl = __int_as_float(r.w);
+  return out;
+}
+
+template <bool FP64, bool COARSE, bool TRACE>
+__global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk(WalkArgs a) {
+  using P = Prec<FP64>;
+  using T = typename P::T;
+  using Meta = typename P::Meta;
+  using VT = typename P::VT;
+  const Meta* __restrict__ meta = static_cast<const Meta*>(a.meta);
+  const int lane = threadIdx.x & 31;
+  const int n_grid = 1 << a.level;                 // fine grid points 0..N
+  const T n_fine = P::from_int(n_grid);
+  const T inv_n = static_cast<T>(1.0 / n_grid);  // exact: a power of two
+  const int n_coarse = n_grid >> 1;
+
+  SquareSum<T> tot_y2;
+  double tot_y2_fixed = 0.0;  // per-item constant part (walks without a jump)
+  unsigned long long tot_jumps = 0, tot_walks = 0, tot_limit = 0;
+  uint32_t bad = 0;
+  const VT* __restrict__ vv = static_cast<const VT*>(a.v_walk);
+
+  for (;;) {
+    unsigned long long item = 0;
+    if (lane == 0) item = atomicAdd(a.work, 1ull);
+    item = __shfl_sync(kFull, item, 0);
+    if (item >= a.total_items) break;
+    const int64_t row = static_cast<int64_t>(item / static_cast<unsigned long long>(a.chunks_per_row));
+    const int64_t chunk = static_cast<int64_t>(item) - row * a.chunks_per_row;
+    const int64_t r_lo = chunk * a.chunk;
+    const int64_t r_hi = min(r_lo + a.chunk, a.reps);
+    const Meta m0 = load_meta(meta, row);
+    const T dl0 = static_cast<T>(m0.dl);
+    // A walk that never jumps stays at the row for the whole interval: its
+    // sample is 0 above l0 and v_row e^{dl_row} at l0 (E_f = dl_row exactly
+    // as the grid weights sum to 1), the same for every such walk.
+    T y_still = 0;
+    if (!COARSE) y_still = P::mul(static_cast<T>(__ldg(vv + row)), P::ex(dl0));
+    if (!isfinite(y_still)) {
+      bad |= kFlagNonFiniteY;
+      y_still = 0;
+    }
+
+    Kahan<T> acc_y;
+    uint32_t item_jumps = 0;  // this lane's jumps in this item (< 2^32)
+    uint32_t n_still = 0;     // this lane's walks without a jump
+    if (lane == 0) tot_walks += static_cast<unsigned long long>(r_hi - r_lo);
+    const uint32_t row32 = static_cast<uint32_t>(row);
+    const uint32_t span = static_cast<uint32_t>(r_hi - r_lo);
+    const uint64_t rep_base = static_cast<uint64_t>(a.rep_begin + r_lo);
+    // The item's walks form a pool: a lane whose walk ends claims the next
+    // unclaimed replica offset (ballot + prefix count), so lanes stay busy
+    // until the pool is empty.
+    uint32_t next = 32;                        // warp-uniform: next unclaimed offset
+    uint32_t r = static_cast<uint32_t>(lane);  // this lane's replica offset
+    bool live = r < span;
+    // Counter words of the current walk: replica bits 0-31 and word 3.
+    uint32_t c_lo = static_cast<uint32_t>(rep_base + r);
+    uint32_t c_hi = a.ctr3 | (static_cast<uint32_t>((rep_base + r) >> 32) << 8);
+    // Walk state.
+    Meta m = m0;
+    int32_t j = static_cast<int32_t>(row);
+    uint32_t e = 0;          // jumps taken (= Philox draw index)
+    uint32_t neg = 0;        // sign bit of the product of jump signs
+    T s = 0;                 // current time in [0,1)
+    T acc = 0;               // coarse: acc_c; coarsest: acc_f
+    T acc_d = 0;             // coarse only
+    int kprev = -1;          // grid index of the segment start (fine)
+    uint32_t hash = 2166136261u;
+
+    while (__any_sync(kFull, live)) {
+      bool fin = false;
+      if (live) {
+        const uint4 x = philox4x32_10(make_uint4(c_lo, row32, e, c_hi), a.key0, a.key1);
+        const T hold = P::mul(P::neglog(P::uniform(x)), static_cast<T>(m.inv_rate));
+        const T s_new = P::add(s, hold);
+        bool done = !(s_new < static_cast<T>(1));
+        int status = 0;
+        if (!done && static_cast<int64_t>(e) >= a.max_jumps) {
+          done = true;
+          status = 1;
+        }
+        if (!done) {
+          // Jump at s_new, after fine grid point g.
+          const int g = P::floor_int(P::mul(s_new, n_fine));
+          const T dlj = static_cast<T>(m.dl);
+          if (COARSE) {
+            const int kc_prev = kprev >> 1;   // floor(a/2), also for a = -1
+            acc = P::fma(P::from_int((g >> 1) - kc_prev), dlj, acc);
+            acc_d = P::fma(P::from_int((g & 1) - (kprev & 1)), dlj, acc_d);
+          } else {
+            acc = P::fma(P::from_int(g - kprev), dlj, acc);
+          }
+          kprev = g;
+          const uint32_t bucket = __umulhi(x.z, static_cast<uint32_t>(m.deg));
+          const uint4 ent = __ldg(reinterpret_cast<const uint4*>(a.alias + m.start) + bucket);
+          const uint32_t pick = (x.w < ent.x) ? ent.y : ent.z;
+          neg ^= pick >> 31;
+          j = static_cast<int32_t>(pick & kColMask);
+          if (TRACE) hash = (hash ^ static_cast<uint32_t>(j)) * 16777619u;
+          m = load_meta(meta, j);
+          s = s_new;
+          ++e;
+        } else if (!TRACE && e == 0 && status == 0) {
+          // No jump: the state is still the initial one.
+          ++n_still;
+          fin = true;
+        } else {
+          // Walk ends at state j (s = 1).
+          fin = true;
+          T y = 0;
+          if (status == 0) {
+            if (e == 0) {
+              y = y_still;
+            } else {
+              const T dle = static_cast<T>(m.dl);
+              const T h = P::mul(P::add(dl0, dle), static_cast<T>(0.5));
+              const T vend = static_cast<T>(__ldg(vv + j));
+              if (COARSE) {
+                const T acc_c = P::fma(P::from_int(n_coarse - (kprev >> 1)), dle, acc);
+                const T accd = P::fma(P::from_int(-(kprev & 1)), dle, acc_d);
+                const T ec = P::mul(P::sub(acc_c, h), P::mul(inv_n, static_cast<T>(2)));
+                const T diff = P::mul(P::add(accd, h), inv_n);
+                y = P::mul(vend, P::mul(P::ex(ec), P::exm1(diff)));
+              } else {
+                const T acc_f = P::fma(P::from_int(n_grid - kprev), dle, acc);
+                const T ef = P::mul(P::sub(acc_f, h), inv_n);
+                y = P::mul(vend, P::ex(ef));
+              }
+              if (neg) y = -y;
+              if (!isfinite(y)) {
+                bad |= kFlagNonFiniteY;
+                y = 0;
+              }
+            }
+          } else {
+            bad |= kFlagWalkLimit;
+            ++tot_limit;
+          }
+          acc_y.add(y);
+          tot_y2.add_square(y);
+          item_jumps += e;
+          if (TRACE) {
+            mlmc_walk_record rec;
+            rec.end = j;
+            rec.jumps = static_cast<int32_t>(e);
+            rec.sign = neg ? -1 : 1;
+            rec.hash = hash;
+            rec.y = static_cast<double>(y);
+            rec.status = status;
+            rec.pad = 0;
+            a.trace[row * a.reps + (r_lo + r)] = rec;
+          }
+        }
+      }
+      // Refill: finished lanes take the next walks of the pool.
+      const unsigned fmask = __ballot_sync(kFull, fin);
+      if (fin) {
+        r = next + static_cast<uint32_t>(__popc(fmask & ((1u << lane) - 1u)));
+        live = r < span;
+        c_lo = static_cast<uint32_t>(rep_base + r);
+        c_hi = a.ctr3 | (static_cast<uint32_t>((rep_base + r) >> 32) << 8);
+        m = load_meta(meta, row);
+        j = static_cast<int32_t>(row);
+        e = 0;
+        neg = 0;
+        s = 0;
+        acc = 0;
+        acc_d = 0;
+        kprev = -1;
+        hash = 2166136261u;
+      }
+      next += static_cast<uint32_t>(__popc(fmask));
+    }
+    tot_jumps += item_jumps;
+    double ys = warp_sum(acc_y);
+    if (!COARSE) {
+      const unsigned long long still = warp_sum_u64(n_still);
+      const double yc = static_cast<double>(y_still);
+      ys += static_cast<double>(still) * yc;
+      if (lane == 0) tot_y2_fixed += static_cast<double>(still) * (yc * yc);
+    }
+    if (lane == 0 && ys != 0.0) atomicAdd(a.sum_y + row, ys);
+  }
+  // Flush this warp's totals.
+  double y2 = tot_y2.value() + tot_y2_fixed;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) y2 += __shfl_xor_sync(kFull, y2, o);
+  const unsigned long long jw = warp_sum_u64(tot_jumps);
+  const unsigned long long ww = warp_sum_u64(tot_walks);
+  const unsigned long long lw = warp_sum_u64(tot_limit);
+  bad = __reduce_or_sync(kFull, bad);
+  if (lane == 0) {
+    if (ww) {
+      atomicAdd(a.totals + kTotY2, y2);
+      atomicAdd(a.totals + kTotJumps, static_cast<double>(jw));
+      atomicAdd(a.totals + kTotWalks, static_cast<double>(ww));
+      if (lw) atomicAdd(a.totals + kTotLimit, static_cast<double>(lw));
+    }
+    if (bad) atomicOr(a.flags, bad);
+  }
+}
+
+__global__ void k_to_float(int64_t n, const double* __restrict__ in, float* __restrict__ out) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    out[i] = __double2float_rn(in[i]);
+}
+
+cudaError_t launch_to_float(mlmc_plan* p, const double* in, float* out) {
+  const int64_t want = (p->n + 255) / 256;
+  const int grid = static_cast<int>(want < p->num_sms * 8 ? want : p->num_sms * 8);
+  k_to_float<<<grid, 256, 0, p->stream>>>(p->n, in, out);
+  p->launches++;
+  return cudaGetLastError();
+}
+
+template <bool FP64, bool COARSE, bool TRACE>
+cudaError_t launch_one(mlmc_plan* p, const WalkArgs& args, int block) {
+  auto kern = k_walk<FP64, COARSE, TRACE>;
+  int per_sm = 0;
+  cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, 0);
+  if (err != cudaSuccess) return err;
+  const unsigned long long warps_needed = args.total_items;
+  const int warps_per_block = block / 32;
+  unsigned long long grid = static_cast<unsigned long long>(p->num_sms) * (per_sm > 0 ? per_sm : 1);
+  const unsigned long long need = (warps_needed + warps_per_block - 1) / warps_per_block;
+  if (need < grid) grid = need;
+  if (grid < 1) grid = 1;
+  kern<<<static_cast<unsigned>(grid), block, 0, p->stream>>>(args);
+  p->launches++;
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_walk(mlmc_plan* p, const WalkLaunch& w) {
+  if (w.reps <= 0 || p->n <= 0) return cudaSuccess;
+  const bool fp64 = p->sched.precision == MLMC_FP64;
+  WalkArgs a{};
+  a.meta = fp64 ? static_cast<const void*>(p->d_meta64) : static_cast<const void*>(p->d_meta32);
+  a.alias = p->d_alias;
+  if (fp64) {
+    a.v_walk = w.v;
+  } else {
+    cudaError_t cerr = launch_to_float(p, w.v, p->d_v32);
+    if (cerr != cudaSuccess) return cerr;
+    a.v_walk = p->d_v32;
+  }
+  a.n = p->n;
+  a.rep_begin = w.rep_begin;
+  a.reps = w.reps;
+  int64_t per_lane = p->sched.walks_per_lane;
+  if (per_lane <= 0) {
+    // Enough walks per lane to amortise the item fetch and the warp's tail.
+    per_lane = (w.reps + 31) / 32;
+    if (per_lane > 64) per_lane = 64;
+  }
+  a.chunk = 32 * per_lane;
+  a.chunks_per_row = (w.reps + a.chunk - 1) / a.chunk;
+  a.total_items = static_cast<unsigned long long>(p->n) * static_cast<unsigned long long>(a.chunks_per_row);
+  a.level = w.level;
+  a.ctr3 = static_cast<uint32_t>(w.level) & 0x3Fu;
+  a.key0 = static_cast<uint32_t>(w.seed & 0xFFFFFFFFull);
+  a.key1 = static_cast<uint32_t>(w.seed >> 32);
+  a.max_jumps = p->sched.max_jumps_per_walk;
+  a.sum_y = w.sum_y;
+  a.totals = w.totals;
+  a.flags = p->d_flags;
+  a.work = p->d_work;
+  a.trace = w.trace;
+  cudaError_t err = cudaMemsetAsync(p->d_work, 0, sizeof(unsigned long long), p->stream);
+  if (err != cudaSuccess) return err;
+  const int block = p->sched.block_threads > 0 ? p->sched.block_threads : 256;
+  const bool trace = w.trace != nullptr;
+  if (fp64) {
+    if (w.coarse) return trace ? launch_one<true, true, true>(p, a, block) : launch_one<true, true, false>(p, a, block);
+    return trace ? launch_one<true, false, true>(p, a, block) : launch_one<true, false, false>(p, a, block);
+  }
+  if (w.coarse) return trace ? launch_one<false, true, true>(p, a, block) : launch_one<false, true, false>(p, a, block);
+  return trace ? launch_one<false, false, true>(p, a, block) : launch_one<false, false, false>(p, a, block);
+}
+
+}  // namespace mlmc

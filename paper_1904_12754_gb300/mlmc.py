@@ -1,0 +1,244 @@
+"""Thin Python binding of libmlmc (``include/mlmc.h``): argument marshalling
+only.  Every step of the estimator runs in the library's CUDA kernels; there
+is no CPU fallback, and loading fails loudly when the library is missing.
+
+Arrays may be numpy arrays (host memory) or torch tensors (host or device);
+the library copies host/device data through unified addressing.  Entry points
+documented as device-only in the header take torch CUDA tensors.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MLMC_OK, MLMC_ERR_INVALID_ARG, MLMC_ERR_CUDA, MLMC_ERR_OOM = 0, 1, 2, 3
+MLMC_ERR_NOT_CONVERGED, MLMC_ERR_WALK_LIMIT, MLMC_ERR_NUMERIC = 4, 5, 6
+FP64, FP32_KAHAN = 0, 1
+BACKWARD, FORWARD = 0, 1
+PLAIN, LEARNED = 0, 1
+
+_STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "NOT_CONVERGED",
+           5: "WALK_LIMIT", 6: "NUMERIC"}
+
+
+class MlmcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"mlmc {_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Schedule(ct.Structure):
+    _fields_ = [("l0", ct.c_int32), ("num_levels", ct.c_int32), ("max_levels", ct.c_int32),
+                ("precision", ct.c_int32), ("mode", ct.c_int32), ("proposal", ct.c_int32),
+                ("pilot_walks", ct.c_int64), ("max_jumps_per_walk", ct.c_int64),
+                ("max_walks_per_row", ct.c_int64), ("time_budget_s", ct.c_double),
+                ("walks_per_lane", ct.c_int32), ("block_threads", ct.c_int32)]
+
+
+class LevelStats(ct.Structure):
+    _fields_ = [("level", ct.c_int32), ("pad", ct.c_int32), ("walks_per_row", ct.c_int64),
+                ("mean_norm2", ct.c_double), ("var", ct.c_double),
+                ("cost_events_per_walk", ct.c_double), ("jumps", ct.c_int64),
+                ("seconds", ct.c_double)]
+
+
+WALK_RECORD_DTYPE = np.dtype([("end", np.int32), ("jumps", np.int32), ("sign", np.int32),
+                              ("hash", np.uint32), ("y", np.float64), ("status", np.int32),
+                              ("pad", np.int32)])
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libmlmc.so (building it first if asked).  Raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise ImportError(f"libmlmc.so not built ({path}); run __graft_entry__.build()")
+        _build.build()
+    lib = ct.CDLL(path)
+    P, I64, I32, D = ct.c_void_p, ct.c_int64, ct.c_int32, ct.c_double
+    lib.mlmc_schedule_default.argtypes = [ct.POINTER(Schedule)]
+    lib.mlmc_plan_create.argtypes = [ct.POINTER(P), I64, I64, P, P, P, D, ct.POINTER(Schedule),
+                                     D, P]
+    lib.mlmc_plan_rebuild.argtypes = [P]
+    lib.mlmc_expmv.argtypes = [P, P, P, ct.c_uint64]
+    lib.mlmc_stats.argtypes = [P, P, I32, ct.POINTER(I32), ct.POINTER(D)]
+    lib.mlmc_mlmcl.argtypes = [P, I32, I32, I64, I64, P, ct.c_uint64, P, P]
+    lib.mlmc_trace.argtypes = [P, I32, I32, I64, I64, P, ct.c_uint64, P]
+    lib.mlmc_export_tables.argtypes = [P] + [P] * 11
+    lib.mlmc_plan_info.argtypes = [P, ct.POINTER(I64), ct.POINTER(I64), ct.POINTER(I32),
+                                   ct.POINTER(D)]
+    lib.mlmc_plan_destroy.argtypes = [P]
+    lib.mlmc_plan_destroy.restype = None
+    lib.mlmc_last_error.restype = ct.c_char_p
+    lib.mlmc_launch_count.argtypes = [P]
+    lib.mlmc_launch_count.restype = I64
+    for name in ("mlmc_schedule_default", "mlmc_plan_create", "mlmc_plan_rebuild", "mlmc_expmv",
+                 "mlmc_stats", "mlmc_mlmcl", "mlmc_trace", "mlmc_export_tables",
+                 "mlmc_plan_info"):
+        getattr(lib, name).restype = ct.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status: int, allow=()):
+    if status != MLMC_OK and status not in allow:
+        msg = _lib.mlmc_last_error().decode(errors="replace")
+        raise MlmcError(status, msg)
+    return status
+
+
+def _nbytes(a) -> int:
+    if isinstance(a, np.ndarray):
+        return a.nbytes
+    if hasattr(a, "element_size"):
+        return a.numel() * a.element_size()
+    return -1
+
+
+def _need(a, nbytes: int, what: str):
+    """Refuse a buffer smaller than the entry point will touch."""
+    have = _nbytes(a)
+    if have >= 0 and have < nbytes:
+        raise ValueError(f"{what}: buffer of {have} bytes, need {nbytes}")
+
+
+def _ptr(a) -> int:
+    """Address of a numpy array or torch tensor (host or device)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if isinstance(a, int):
+        return a
+    raise TypeError(f"cannot take the address of {type(a)}")
+
+
+def schedule_default(**overrides) -> Schedule:
+    lib = load()
+    s = Schedule()
+    _check(lib.mlmc_schedule_default(ct.byref(s)))
+    for k, v in overrides.items():
+        if not hasattr(s, k):
+            raise KeyError(k)
+        setattr(s, k, v)
+    return s
+
+
+class Plan:
+    """An mlmc_plan: x = exp(t A) v for one CSR matrix A and time t."""
+
+    def __init__(self, n: int, row_ptr, col, vals, t: float, sched: Schedule = None,
+                 rel_tol: float = 1e-3, stream: int = 0):
+        lib = load()
+        self._lib = lib
+        self._h = ct.c_void_p()
+        nnz = int(row_ptr[-1]) if isinstance(row_ptr, np.ndarray) else int(row_ptr[-1].item())
+        self._keep = (row_ptr, col, vals)
+        _check(lib.mlmc_plan_create(ct.byref(self._h), int(n), nnz, _ptr(row_ptr), _ptr(col),
+                                    _ptr(vals), float(t),
+                                    ct.byref(sched) if sched is not None else None,
+                                    float(rel_tol), ct.c_void_p(stream)))
+        self.n, self.nnz = int(n), nnz
+
+    @classmethod
+    def from_csr(cls, a, t: float, sched: Schedule = None, rel_tol: float = 1e-3,
+                 stream: int = 0):
+        return cls(a.n, np.ascontiguousarray(a.row_ptr, np.int64),
+                   np.ascontiguousarray(a.col, np.int32), np.ascontiguousarray(a.val, np.float64),
+                   t, sched, rel_tol, stream)
+
+    def close(self):
+        if self._h:
+            self._lib.mlmc_plan_destroy(self._h)
+            self._h = ct.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    def rebuild(self):
+        _check(self._lib.mlmc_plan_rebuild(self._h))
+
+    def expmv(self, v, x, seed: int, allow_not_converged: bool = False) -> int:
+        _need(v, 8 * self.n, "v")
+        _need(x, 8 * self.n, "x")
+        allow = (MLMC_ERR_NOT_CONVERGED,) if allow_not_converged else ()
+        return _check(self._lib.mlmc_expmv(self._h, _ptr(v), _ptr(x), ct.c_uint64(seed)), allow)
+
+    def stats(self):
+        cap = 32
+        arr = (LevelStats * cap)()
+        nl = ct.c_int32()
+        err = ct.c_double()
+        _check(self._lib.mlmc_stats(self._h, arr, cap, ct.byref(nl), ct.byref(err)))
+        levels = [{f: getattr(arr[k], f) for f, _ in LevelStats._fields_ if f != "pad"}
+                  for k in range(nl.value)]
+        return levels, err.value
+
+    def mlmcl(self, level: int, coarse: bool, rep_begin: int, reps: int, v, seed: int, sum_y,
+              totals):
+        _need(v, 8 * self.n, "v")
+        _need(sum_y, 8 * self.n, "sum_y")
+        _need(totals, 8 * 4, "totals")
+        _check(self._lib.mlmc_mlmcl(self._h, level, int(coarse), rep_begin, reps, _ptr(v),
+                                    ct.c_uint64(seed), _ptr(sum_y), _ptr(totals)))
+
+    def trace(self, level: int, coarse: bool, rep_begin: int, reps: int, v, seed: int, rec):
+        _need(v, 8 * self.n, "v")
+        _need(rec, WALK_RECORD_DTYPE.itemsize * self.n * reps, "rec")
+        _check(self._lib.mlmc_trace(self._h, level, int(coarse), rep_begin, reps, _ptr(v),
+                                    ct.c_uint64(seed), _ptr(rec)))
+
+    def export_tables(self) -> dict:
+        n, nnz = self.n, self.nnz
+        out = dict(l_ii=np.zeros(n), dl=np.zeros(n), inv_rate=np.zeros(n),
+                   inv_rate32=np.zeros(n, np.float32), dl32=np.zeros(n, np.float32),
+                   deg=np.zeros(n, np.int32), thr=np.zeros(max(nnz, 1), np.uint32),
+                   keep_col=np.full(max(nnz, 1), -1, np.int32),
+                   keep_neg=np.zeros(max(nnz, 1), np.uint8),
+                   alias_col=np.full(max(nnz, 1), -1, np.int32),
+                   alias_neg=np.zeros(max(nnz, 1), np.uint8))
+        keys = ["l_ii", "dl", "inv_rate", "inv_rate32", "dl32", "deg", "thr", "keep_col",
+                "keep_neg", "alias_col", "alias_neg"]
+        _check(self._lib.mlmc_export_tables(self._h, *[_ptr(out[k]) for k in keys]))
+        return out
+
+    def info(self) -> dict:
+        n, nnz, l0, t = ct.c_int64(), ct.c_int64(), ct.c_int32(), ct.c_double()
+        _check(self._lib.mlmc_plan_info(self._h, ct.byref(n), ct.byref(nnz), ct.byref(l0),
+                                        ct.byref(t)))
+        return dict(n=n.value, nnz=nnz.value, l0=l0.value, t=t.value)
+
+    def launch_count(self) -> int:
+        return int(self._lib.mlmc_launch_count(self._h))

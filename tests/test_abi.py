@@ -1,0 +1,55 @@
+"""The C-ABI library loads and exports every entry point its header
+declares (no compute calls: this runs without a GPU)."""
+import ctypes as ct
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(mlmc_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__ as g
+    g.build()
+    from paper_1904_12754_gb300 import mlmc
+    return mlmc.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for want in ("mlmc_plan_create", "mlmc_expmv", "mlmc_stats", "mlmc_plan_destroy",
+                 "mlmc_last_error", "mlmc_mlmcl", "mlmc_trace"):
+        assert want in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_host_only_calls(lib):
+    from paper_1904_12754_gb300 import mlmc
+    s = mlmc.schedule_default()
+    assert s.l0 == -1 and s.num_levels == 5 and s.precision == mlmc.FP64
+    assert lib.mlmc_plan_create(None, 1, 0, None, None, None, 0.0, None, 1e-3, None) == \
+        mlmc.MLMC_ERR_INVALID_ARG
+    assert b"NULL" in lib.mlmc_last_error()
+    h = ct.c_void_p()
+    # rejected before any device work: negative t, bad tolerance, n = 0
+    rp = (ct.c_int64 * 2)(0, 0)
+    for n, t, tol in ((1, -1.0, 1e-3), (1, 1.0, 0.0), (0, 1.0, 1e-3)):
+        st = lib.mlmc_plan_create(ct.byref(h), n, 0, rp, None, None, t, None, tol, None)
+        assert st == mlmc.MLMC_ERR_INVALID_ARG
+    lib.mlmc_plan_destroy(None)
