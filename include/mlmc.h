@@ -89,7 +89,11 @@ typedef struct {
  *                    row), sum_i Var(Y_i), unbiased estimate
  *   cost_events_per_walk  mean events (holding-time draws = jumps + 1)
  *   jumps            total jumps taken at this level
- *   seconds          GPU time spent in this level's walk launches */
+ *   seconds          GPU time of this level's walk launches (CUDA events on
+ *                    the plan's stream)
+ *   launches         walk kernel launches at this level (a top-up is split
+ *                    into launches of about 2^31 walks)
+ *   still_walks      walks that ended without a jump */
 typedef struct {
     int32_t level;
     int32_t pad;
@@ -99,6 +103,8 @@ typedef struct {
     double cost_events_per_walk;
     int64_t jumps;
     double seconds;
+    int64_t launches;
+    int64_t still_walks;
 } mlmc_level_stats;
 
 /* One replayed walk (mlmc_trace): the state at s = 1, the number of jumps,
@@ -169,8 +175,9 @@ mlmc_status mlmc_stats(const mlmc_plan *plan, mlmc_level_stats *out, int32_t cap
  * difference P_l - P_{l-1}.
  *   v        device pointer, n doubles (the right-hand side)
  *   sum_y    device pointer, n doubles: sum_y[i] += sum over the walks of Y
- *   totals   device pointer, 4 doubles: [0] += sum Y^2, [1] += jumps,
- *            [2] += walks, [3] += walks that hit the jump limit
+ *   totals   device pointer, 5 doubles: [0] += sum Y^2, [1] += jumps,
+ *            [2] += walks, [3] += walks that hit the jump limit,
+ *            [4] += walks that ended without a jump
  * Asynchronous on the plan's stream; uses the plan's precision. */
 mlmc_status mlmc_mlmcl(mlmc_plan *plan, int32_t level, int32_t coarse, int64_t rep_begin,
                        int64_t reps, const double *v, uint64_t seed, double *sum_y,

@@ -78,6 +78,10 @@ void free_plan(mlmc_plan* p) {
   cudaFree(p->d_x);
   cudaFree(p->d_norm2);
   if (!p->levels.empty()) cudaFree(p->levels[0].sum_y);
+  for (auto& L : p->levels) {
+    if (L.ev0) cudaEventDestroy(L.ev0);
+    if (L.ev1) cudaEventDestroy(L.ev1);
+  }
   if (p->ev0) cudaEventDestroy(p->ev0);
   if (p->ev1) cudaEventDestroy(p->ev1);
   delete p;
@@ -102,7 +106,7 @@ std::string flag_text(uint32_t f) {
 }
 
 struct HostLevel {
-  double y2, jumps, walks, limit, sumsq;
+  double y2, jumps, walks, limit, still, sumsq;
 };
 
 }  // namespace
@@ -112,27 +116,50 @@ void set_error(const std::string& msg) { g_last_error = msg; }
 // Per-level device scalars live at d_totals[slot * kTotSlots].
 static double* totals_of(mlmc_plan* p, int slot) { return p->d_totals + slot * kTotSlots; }
 
+// Launch `extra` more walks per row at level slot `slot`.  The walks are
+// issued in batches of at most kBatchWalks, with a synchronisation after
+// each, so that a large top-up stops at the wall-clock deadline; *stopped is
+// set when it did.
 static mlmc_status run_level(mlmc_plan* p, int slot, int64_t extra, uint64_t seed,
-                             std::vector<char>& timed) {
+                             std::vector<char>& timed,
+                             std::chrono::steady_clock::time_point deadline, bool* stopped) {
+  constexpr int64_t kBatchWalks = int64_t{1} << 36;  // ~0.5-1 s of FP32 walks
   LevelAcc& L = p->levels[slot];
-  WalkLaunch w;
-  w.level = p->l0 + slot;
-  w.coarse = slot > 0;
-  w.rep_begin = L.reps;
-  w.reps = extra;
-  w.seed = seed;
-  w.v = p->d_v;
-  w.sum_y = L.sum_y;
-  w.totals = totals_of(p, slot);
-  MLMC_CUDA(cudaEventRecord(p->ev0, p->stream), "event record");
-  MLMC_CUDA(launch_walk(p, w), "walk kernel launch");
-  MLMC_CUDA(cudaEventRecord(p->ev1, p->stream), "event record");
-  MLMC_CUDA(cudaEventSynchronize(p->ev1), "event synchronize");
-  float ms = 0.f;
-  MLMC_CUDA(cudaEventElapsedTime(&ms, p->ev0, p->ev1), "event elapsed");
-  L.seconds += 1e-3 * ms;
-  L.reps += extra;
-  timed[slot] = 1;
+  const int64_t batch_reps = std::max<int64_t>(32, kBatchWalks / p->n);
+  if (stopped) *stopped = false;
+  for (int64_t done = 0; done < extra;) {
+    const int64_t reps = std::min(batch_reps, extra - done);
+    WalkLaunch w;
+    w.level = p->l0 + slot;
+    w.coarse = slot > 0;
+    w.rep_begin = L.reps;
+    w.reps = reps;
+    w.seed = seed;
+    w.v = p->d_v;
+    w.sum_y = L.sum_y;
+    w.totals = totals_of(p, slot);
+    int64_t nl = 0;
+    MLMC_CUDA(cudaEventRecord(L.ev0, p->stream), "event record");
+    MLMC_CUDA(launch_walk(p, w, &nl), "walk kernel launch");
+    MLMC_CUDA(cudaEventRecord(L.ev1, p->stream), "event record");
+    L.launches += nl;
+    L.reps += reps;
+    done += reps;
+    timed[slot] = 1;
+    if (done < extra) {
+      // Mid top-up: read this batch's time now and check the deadline.
+      MLMC_CUDA(cudaEventSynchronize(L.ev1), "event synchronize");
+      float ms = 0.f;
+      MLMC_CUDA(cudaEventElapsedTime(&ms, L.ev0, L.ev1), "event elapsed");
+      L.seconds += 1e-3 * ms;
+      if (std::chrono::steady_clock::now() > deadline) {
+        if (stopped) *stopped = true;
+        return MLMC_OK;
+      }
+    } else {
+      L.pending = true;  // read by collect() after its synchronisation
+    }
+  }
   return MLMC_OK;
 }
 
@@ -149,10 +176,19 @@ static mlmc_status collect(mlmc_plan* p, int nl, std::vector<HostLevel>& out, do
   MLMC_CUDA(cudaMemcpyAsync(h.data() + nl * kTotSlots, p->d_norm2, sizeof(double),
                             cudaMemcpyDeviceToHost, p->stream), "read norm");
   MLMC_CUDA(cudaStreamSynchronize(p->stream), "synchronize");
+  for (int k = 0; k < nl; ++k) {
+    LevelAcc& L = p->levels[k];
+    if (!L.pending) continue;
+    float ms = 0.f;
+    MLMC_CUDA(cudaEventElapsedTime(&ms, L.ev0, L.ev1), "event elapsed");
+    L.seconds += 1e-3 * ms;
+    L.pending = false;
+  }
   out.resize(nl);
   for (int k = 0; k < nl; ++k) {
     const double* t = h.data() + k * kTotSlots;
-    out[k] = HostLevel{t[kTotY2], t[kTotJumps], t[kTotWalks], t[kTotLimit], t[kTotSumSq]};
+    out[k] = HostLevel{t[kTotY2], t[kTotJumps], t[kTotWalks], t[kTotLimit], t[kTotStill],
+                       t[kTotSumSq]};
   }
   *norm2 = h[nl * kTotSlots];
   return MLMC_OK;
@@ -262,7 +298,11 @@ mlmc_status mlmc_plan_create(mlmc_plan** out, int64_t n, int64_t nnz, const int6
   double* sums = nullptr;
   PLAN_CUDA(dev_alloc(&sums, static_cast<size_t>(n) * s.max_levels), "alloc level sums");
   p->levels.resize(s.max_levels);
-  for (int k = 0; k < s.max_levels; ++k) p->levels[k].sum_y = sums + static_cast<size_t>(k) * n;
+  for (int k = 0; k < s.max_levels; ++k) {
+    p->levels[k].sum_y = sums + static_cast<size_t>(k) * n;
+    PLAN_CUDA(cudaEventCreate(&p->levels[k].ev0), "event create");
+    PLAN_CUDA(cudaEventCreate(&p->levels[k].ev1), "event create");
+  }
   PLAN_CUDA(cudaEventCreate(&p->ev0), "event create");
   PLAN_CUDA(cudaEventCreate(&p->ev1), "event create");
 
@@ -388,11 +428,17 @@ mlmc_status mlmc_expmv(mlmc_plan* p, const double* v, double* x, uint64_t seed) 
   for (auto& L : p->levels) {
     L.reps = 0;
     L.seconds = 0.0;
+    L.launches = 0;
+    L.pending = false;
   }
   std::vector<char> timed(s.max_levels, 0);
   int nl = s.num_levels;
   mlmc_status st = MLMC_OK;
-  for (int k = 0; k < nl && st == MLMC_OK; ++k) st = run_level(p, k, s.pilot_walks, seed, timed);
+  const auto deadline = t_start + std::chrono::duration_cast<std::chrono::steady_clock::duration>(
+                                      std::chrono::duration<double>(s.time_budget_s));
+  bool out_of_time = false;
+  for (int k = 0; k < nl && st == MLMC_OK; ++k)
+    st = run_level(p, k, s.pilot_walks, seed, timed, deadline, nullptr);
   if (st != MLMC_OK) return st;
 
   std::vector<HostLevel> h;
@@ -418,8 +464,11 @@ mlmc_status mlmc_expmv(mlmc_plan* p, const double* v, double* x, uint64_t seed) 
         target = std::min(target, static_cast<double>(s.max_walks_per_row));
         const int64_t want = static_cast<int64_t>(target);
         if (want > p->levels[k].reps) {
-          if ((st = run_level(p, k, want - p->levels[k].reps, seed, timed)) != MLMC_OK) return st;
+          if ((st = run_level(p, k, want - p->levels[k].reps, seed, timed, deadline,
+                              &out_of_time)) != MLMC_OK)
+            return st;
           topped = true;
+          if (out_of_time) break;
         }
       }
     }
@@ -441,11 +490,10 @@ mlmc_status mlmc_expmv(mlmc_plan* p, const double* v, double* x, uint64_t seed) 
       converged = true;
       break;
     }
-    const double elapsed =
-        std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
-    if (elapsed > s.time_budget_s) break;
+    if (out_of_time || std::chrono::steady_clock::now() > deadline) break;
     if (!bias_ok && nl < s.max_levels) {
-      if ((st = run_level(p, nl, s.pilot_walks, seed, timed)) != MLMC_OK) return st;
+      if ((st = run_level(p, nl, s.pilot_walks, seed, timed, deadline, nullptr)) != MLMC_OK)
+        return st;
       ++nl;
       continue;
     }
@@ -472,6 +520,8 @@ mlmc_status mlmc_expmv(mlmc_plan* p, const double* v, double* x, uint64_t seed) 
     ls.cost_events_per_walk = h[k].walks > 0 ? 1.0 + h[k].jumps / h[k].walks : 1.0;
     ls.jumps = static_cast<int64_t>(h[k].jumps);
     ls.seconds = p->levels[k].seconds;
+    ls.launches = p->levels[k].launches;
+    ls.still_walks = static_cast<int64_t>(h[k].still);
     p->last_stats.push_back(ls);
   }
   if (flags & kFlagWalkLimit) return fail(MLMC_ERR_WALK_LIMIT, "walk limit:" + flag_text(flags));

@@ -27,10 +27,14 @@ struct LevelAcc {
   double* sum_y = nullptr;  // [n]
   int64_t reps = 0;         // walks per row taken so far
   double seconds = 0.0;
+  int64_t launches = 0;     // walk kernel launches
+  bool pending = false;     // events recorded since the last read-out
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
 // Totals slots of the per-level device scalars (doubles).
-enum { kTotY2 = 0, kTotJumps = 1, kTotWalks = 2, kTotLimit = 3, kTotSumSq = 4, kTotSlots = 8 };
+enum { kTotY2 = 0, kTotJumps = 1, kTotWalks = 2, kTotLimit = 3, kTotStill = 4, kTotSumSq = 5,
+       kTotSlots = 8 };
 
 struct WalkLaunch {
   int level = 0;
@@ -93,8 +97,9 @@ void set_error(const std::string& msg);
 cudaError_t launch_validate(mlmc_plan* p);
 cudaError_t launch_build_tables(mlmc_plan* p);
 
-// Walk kernels (mlmc_walk.cu).
-cudaError_t launch_walk(mlmc_plan* p, const WalkLaunch& w);
+// Walk kernels (mlmc_walk.cu).  Splits the replica range into launches of at
+// most about 2^31 walks; returns the number of launches in *launches.
+cudaError_t launch_walk(mlmc_plan* p, const WalkLaunch& w, int64_t* launches = nullptr);
 
 // Reductions (mlmc_reduce.cu).
 cudaError_t launch_sumsq(mlmc_plan* p, const double* a, double* out, double scale);

@@ -29,6 +29,7 @@
 // row with Kahan compensation and sum Y^2 (which sets the sample sizes through
 // the variance estimate) as an exact-product FP32 pair; FP64 appears only in
 // the per-item warp reductions and the atomics.
+#include <algorithm>
 #include <cmath>
 
 #include "mlmc_internal.h"
@@ -57,6 +58,8 @@ struct WalkArgs {
   uint32_t* flags;
   unsigned long long* work;
   mlmc_walk_record* trace;
+  int64_t trace_stride;    // records per row (the whole replica range)
+  int64_t trace_base;      // offset of this launch's first replica
 };
 
 template <bool FP64>
@@ -200,7 +203,7 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk(WalkArgs a) {
 
   SquareSum<T> tot_y2;
   double tot_y2_fixed = 0.0;  // per-item constant part (walks without a jump)
-  unsigned long long tot_jumps = 0, tot_walks = 0, tot_limit = 0;
+  unsigned long long tot_jumps = 0, tot_walks = 0, tot_limit = 0, tot_still = 0;
   uint32_t bad = 0;
   const VT* __restrict__ vv = static_cast<const VT*>(a.v_walk);
 
@@ -333,7 +336,7 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk(WalkArgs a) {
             rec.y = static_cast<double>(y);
             rec.status = status;
             rec.pad = 0;
-            a.trace[row * a.reps + (r_lo + r)] = rec;
+            a.trace[row * a.trace_stride + a.trace_base + (r_lo + r)] = rec;
           }
         }
       }
@@ -358,8 +361,9 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk(WalkArgs a) {
     }
     tot_jumps += item_jumps;
     double ys = warp_sum(acc_y);
+    const unsigned long long still = warp_sum_u64(n_still);
+    if (lane == 0) tot_still += still;
     if (!COARSE) {
-      const unsigned long long still = warp_sum_u64(n_still);
       const double yc = static_cast<double>(y_still);
       ys += static_cast<double>(still) * yc;
       if (lane == 0) tot_y2_fixed += static_cast<double>(still) * (yc * yc);
@@ -373,6 +377,7 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk(WalkArgs a) {
   const unsigned long long jw = warp_sum_u64(tot_jumps);
   const unsigned long long ww = warp_sum_u64(tot_walks);
   const unsigned long long lw = warp_sum_u64(tot_limit);
+  const unsigned long long sw = warp_sum_u64(tot_still);
   bad = __reduce_or_sync(kFull, bad);
   if (lane == 0) {
     if (ww) {
@@ -380,6 +385,7 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk(WalkArgs a) {
       atomicAdd(a.totals + kTotJumps, static_cast<double>(jw));
       atomicAdd(a.totals + kTotWalks, static_cast<double>(ww));
       if (lw) atomicAdd(a.totals + kTotLimit, static_cast<double>(lw));
+      if (sw) atomicAdd(a.totals + kTotStill, static_cast<double>(sw));
     }
     if (bad) atomicOr(a.flags, bad);
   }
@@ -418,7 +424,8 @@ cudaError_t launch_one(mlmc_plan* p, const WalkArgs& args, int block) {
 
 }  // namespace
 
-cudaError_t launch_walk(mlmc_plan* p, const WalkLaunch& w) {
+cudaError_t launch_walk(mlmc_plan* p, const WalkLaunch& w, int64_t* launches) {
+  if (launches) *launches = 0;
   if (w.reps <= 0 || p->n <= 0) return cudaSuccess;
   const bool fp64 = p->sched.precision == MLMC_FP64;
   WalkArgs a{};
@@ -432,17 +439,6 @@ cudaError_t launch_walk(mlmc_plan* p, const WalkLaunch& w) {
     a.v_walk = p->d_v32;
   }
   a.n = p->n;
-  a.rep_begin = w.rep_begin;
-  a.reps = w.reps;
-  int64_t per_lane = p->sched.walks_per_lane;
-  if (per_lane <= 0) {
-    // Enough walks per lane to amortise the item fetch and the warp's tail.
-    per_lane = (w.reps + 31) / 32;
-    if (per_lane > 64) per_lane = 64;
-  }
-  a.chunk = 32 * per_lane;
-  a.chunks_per_row = (w.reps + a.chunk - 1) / a.chunk;
-  a.total_items = static_cast<unsigned long long>(p->n) * static_cast<unsigned long long>(a.chunks_per_row);
   a.level = w.level;
   a.ctr3 = static_cast<uint32_t>(w.level) & 0x3Fu;
   a.key0 = static_cast<uint32_t>(w.seed & 0xFFFFFFFFull);
@@ -453,16 +449,40 @@ cudaError_t launch_walk(mlmc_plan* p, const WalkLaunch& w) {
   a.flags = p->d_flags;
   a.work = p->d_work;
   a.trace = w.trace;
-  cudaError_t err = cudaMemsetAsync(p->d_work, 0, sizeof(unsigned long long), p->stream);
-  if (err != cudaSuccess) return err;
+  a.trace_stride = w.reps;
   const int block = p->sched.block_threads > 0 ? p->sched.block_threads : 256;
   const bool trace = w.trace != nullptr;
-  if (fp64) {
-    if (w.coarse) return trace ? launch_one<true, true, true>(p, a, block) : launch_one<true, true, false>(p, a, block);
-    return trace ? launch_one<true, false, true>(p, a, block) : launch_one<true, false, false>(p, a, block);
+  // Bounded launches (about 2^31 walks each, tens of milliseconds): the
+  // controller's time budget is checked between them and no single kernel
+  // runs for seconds.
+  const int64_t cap = std::max<int64_t>(32, (int64_t{1} << 31) / p->n);
+  for (int64_t done = 0; done < w.reps; done += cap) {
+    const int64_t reps = std::min(cap, w.reps - done);
+    a.rep_begin = w.rep_begin + done;
+    a.reps = reps;
+    a.trace_base = done;
+    int64_t per_lane = p->sched.walks_per_lane;
+    if (per_lane <= 0) {
+      // Enough walks per item to amortise the item fetch and the pool's tail.
+      per_lane = (reps + 31) / 32;
+      if (per_lane > 64) per_lane = 64;
+    }
+    a.chunk = 32 * per_lane;
+    a.chunks_per_row = (reps + a.chunk - 1) / a.chunk;
+    a.total_items = static_cast<unsigned long long>(p->n) * static_cast<unsigned long long>(a.chunks_per_row);
+    cudaError_t err = cudaMemsetAsync(p->d_work, 0, sizeof(unsigned long long), p->stream);
+    if (err != cudaSuccess) return err;
+    if (fp64) {
+      if (w.coarse) err = trace ? launch_one<true, true, true>(p, a, block) : launch_one<true, true, false>(p, a, block);
+      else err = trace ? launch_one<true, false, true>(p, a, block) : launch_one<true, false, false>(p, a, block);
+    } else {
+      if (w.coarse) err = trace ? launch_one<false, true, true>(p, a, block) : launch_one<false, true, false>(p, a, block);
+      else err = trace ? launch_one<false, false, true>(p, a, block) : launch_one<false, false, false>(p, a, block);
+    }
+    if (err != cudaSuccess) return err;
+    if (launches) ++*launches;
   }
-  if (w.coarse) return trace ? launch_one<false, true, true>(p, a, block) : launch_one<false, true, false>(p, a, block);
-  return trace ? launch_one<false, false, true>(p, a, block) : launch_one<false, false, false>(p, a, block);
+  return cudaSuccess;
 }
 
 }  // namespace mlmc

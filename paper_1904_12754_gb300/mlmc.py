@@ -43,7 +43,7 @@ class LevelStats(ct.Structure):
     _fields_ = [("level", ct.c_int32), ("pad", ct.c_int32), ("walks_per_row", ct.c_int64),
                 ("mean_norm2", ct.c_double), ("var", ct.c_double),
                 ("cost_events_per_walk", ct.c_double), ("jumps", ct.c_int64),
-                ("seconds", ct.c_double)]
+                ("seconds", ct.c_double), ("launches", ct.c_int64), ("still_walks", ct.c_int64)]
 
 
 WALK_RECORD_DTYPE = np.dtype([("end", np.int32), ("jumps", np.int32), ("sign", np.int32),
@@ -210,7 +210,7 @@ class Plan:
               totals):
         _need(v, 8 * self.n, "v")
         _need(sum_y, 8 * self.n, "sum_y")
-        _need(totals, 8 * 4, "totals")
+        _need(totals, 8 * 5, "totals")
         _check(self._lib.mlmc_mlmcl(self._h, level, int(coarse), rep_begin, reps, _ptr(v),
                                     ct.c_uint64(seed), _ptr(sum_y), _ptr(totals)))
 
