@@ -190,6 +190,30 @@ mlmc_status mlmc_mlmcl(mlmc_plan *plan, int32_t level, int32_t coarse, int64_t r
 mlmc_status mlmc_trace(mlmc_plan *plan, int32_t level, int32_t coarse, int64_t rep_begin,
                        int64_t reps, const double *v, uint64_t seed, mlmc_walk_record *rec);
 
+/* mlmc_trace without device allocation.  The paper has no counterpart: this
+ * is a library service.  mlmc_trace takes its scratch (per-row sums, launch
+ * totals, the work counter, an FP32 copy of v) from cudaMalloc and gives it
+ * back with cudaFree, and cudaFree synchronises the whole device.  A caller
+ * whose device memory is reserved up front by another allocator, or that
+ * cannot let a device-wide synchronisation stall its other streams, calls
+ * this instead: it records the same walks with the same kernel, and its
+ * scratch is a static device array of about 3 MB that every GPU loading the
+ * library holds until the process exits.
+ *   Arguments, record layout and results are those of mlmc_trace; rec and v
+ *   are device pointers owned by the caller.
+ *   n (the plan's order) must not exceed 262144 (2^18) rows, else
+ *   MLMC_ERR_INVALID_ARG with a message naming the limit.
+ *   The plan's device must be the current device.  The first call on a
+ *   device looks up the array's device address (cudaGetSymbolAddress), so
+ *   make that first call before any stream capture.
+ *   Asynchronous on the plan's stream; makes no allocation.  Every call on a
+ *   device shares the array and it keeps the previous call's contents; the
+ *   call clears what must start at zero.  Calls whose GPU work overlaps (on
+ *   different streams, or from different plans on one device) race on it. */
+mlmc_status mlmc_trace_noalloc(mlmc_plan *plan, int32_t level, int32_t coarse, int64_t rep_begin,
+                               int64_t reps, const double *v, uint64_t seed,
+                               mlmc_walk_record *rec);
+
 /* Copy the device tables to host arrays (any pointer may be NULL):
  *   l_ii, dl (= t d_i), inv_rate (1/(t L_ii), +inf when L_ii = 0): n doubles
  *   inv_rate32, dl32: n floats (the FP32 copies the FP32 walk uses)

@@ -100,6 +100,10 @@ cudaError_t launch_build_tables(mlmc_plan* p);
 // Walk kernels (mlmc_walk.cu).  Splits the replica range into launches of at
 // most about 2^31 walks; returns the number of launches in *launches.
 cudaError_t launch_walk(mlmc_plan* p, const WalkLaunch& w, int64_t* launches = nullptr);
+// As launch_walk, with the work counter and the FP32 copy of v in the given
+// device memory instead of the plan's buffers.
+cudaError_t launch_walk_scratch(mlmc_plan* p, const WalkLaunch& w, unsigned long long* work,
+                                float* v32, int64_t* launches = nullptr);
 
 // Reductions (mlmc_reduce.cu).
 cudaError_t launch_sumsq(mlmc_plan* p, const double* a, double* out, double scale);

@@ -485,4 +485,65 @@ cudaError_t launch_walk(mlmc_plan* p, const WalkLaunch& w, int64_t* launches) {
   return cudaSuccess;
 }
 
+// The same launch sequence as launch_walk, with the work counter and the FP32
+// copy of v taken from caller-supplied device memory instead of the plan's
+// buffers (used by the entry point whose scratch is static device memory).
+cudaError_t launch_walk_scratch(mlmc_plan* p, const WalkLaunch& w, unsigned long long* work,
+                                float* v32, int64_t* launches) {
+  if (launches) *launches = 0;
+  if (w.reps <= 0 || p->n <= 0) return cudaSuccess;
+  const bool fp64 = p->sched.precision == MLMC_FP64;
+  WalkArgs a{};
+  a.meta = fp64 ? static_cast<const void*>(p->d_meta64) : static_cast<const void*>(p->d_meta32);
+  a.alias = p->d_alias;
+  if (fp64) {
+    a.v_walk = w.v;
+  } else {
+    cudaError_t cerr = launch_to_float(p, w.v, v32);
+    if (cerr != cudaSuccess) return cerr;
+    a.v_walk = v32;
+  }
+  a.n = p->n;
+  a.level = w.level;
+  a.ctr3 = static_cast<uint32_t>(w.level) & 0x3Fu;
+  a.key0 = static_cast<uint32_t>(w.seed & 0xFFFFFFFFull);
+  a.key1 = static_cast<uint32_t>(w.seed >> 32);
+  a.max_jumps = p->sched.max_jumps_per_walk;
+  a.sum_y = w.sum_y;
+  a.totals = w.totals;
+  a.flags = p->d_flags;
+  a.work = work;
+  a.trace = w.trace;
+  a.trace_stride = w.reps;
+  const int block = p->sched.block_threads > 0 ? p->sched.block_threads : 256;
+  const bool trace = w.trace != nullptr;
+  const int64_t cap = std::max<int64_t>(32, (int64_t{1} << 31) / p->n);
+  for (int64_t done = 0; done < w.reps; done += cap) {
+    const int64_t reps = std::min(cap, w.reps - done);
+    a.rep_begin = w.rep_begin + done;
+    a.reps = reps;
+    a.trace_base = done;
+    int64_t per_lane = p->sched.walks_per_lane;
+    if (per_lane <= 0) {
+      per_lane = (reps + 31) / 32;
+      if (per_lane > 64) per_lane = 64;
+    }
+    a.chunk = 32 * per_lane;
+    a.chunks_per_row = (reps + a.chunk - 1) / a.chunk;
+    a.total_items = static_cast<unsigned long long>(p->n) * static_cast<unsigned long long>(a.chunks_per_row);
+    cudaError_t err = cudaMemsetAsync(work, 0, sizeof(unsigned long long), p->stream);
+    if (err != cudaSuccess) return err;
+    if (fp64) {
+      if (w.coarse) err = trace ? launch_one<true, true, true>(p, a, block) : launch_one<true, true, false>(p, a, block);
+      else err = trace ? launch_one<true, false, true>(p, a, block) : launch_one<true, false, false>(p, a, block);
+    } else {
+      if (w.coarse) err = trace ? launch_one<false, true, true>(p, a, block) : launch_one<false, true, false>(p, a, block);
+      else err = trace ? launch_one<false, false, true>(p, a, block) : launch_one<false, false, false>(p, a, block);
+    }
+    if (err != cudaSuccess) return err;
+    if (launches) ++*launches;
+  }
+  return cudaSuccess;
+}
+
 }  // namespace mlmc

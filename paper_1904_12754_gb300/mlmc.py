@@ -77,6 +77,7 @@ def load(build_if_missing: bool = False):
     lib.mlmc_stats.argtypes = [P, P, I32, ct.POINTER(I32), ct.POINTER(D)]
     lib.mlmc_mlmcl.argtypes = [P, I32, I32, I64, I64, P, ct.c_uint64, P, P]
     lib.mlmc_trace.argtypes = [P, I32, I32, I64, I64, P, ct.c_uint64, P]
+    lib.mlmc_trace_noalloc.argtypes = [P, I32, I32, I64, I64, P, ct.c_uint64, P]
     lib.mlmc_export_tables.argtypes = [P] + [P] * 11
     lib.mlmc_plan_info.argtypes = [P, ct.POINTER(I64), ct.POINTER(I64), ct.POINTER(I32),
                                    ct.POINTER(D)]
@@ -86,7 +87,8 @@ def load(build_if_missing: bool = False):
     lib.mlmc_launch_count.argtypes = [P]
     lib.mlmc_launch_count.restype = I64
     for name in ("mlmc_schedule_default", "mlmc_plan_create", "mlmc_plan_rebuild", "mlmc_expmv",
-                 "mlmc_stats", "mlmc_mlmcl", "mlmc_trace", "mlmc_export_tables",
+                 "mlmc_stats", "mlmc_mlmcl", "mlmc_trace", "mlmc_trace_noalloc",
+                 "mlmc_export_tables",
                  "mlmc_plan_info"):
         getattr(lib, name).restype = ct.c_int
     _lib = lib
@@ -219,6 +221,16 @@ class Plan:
         _need(rec, WALK_RECORD_DTYPE.itemsize * self.n * reps, "rec")
         _check(self._lib.mlmc_trace(self._h, level, int(coarse), rep_begin, reps, _ptr(v),
                                     ct.c_uint64(seed), _ptr(rec)))
+
+    def trace_noalloc(self, level: int, coarse: bool, rep_begin: int, reps: int, v, seed: int,
+                      rec):
+        """As trace(), through mlmc_trace_noalloc: no device allocation, the
+        library's static scratch instead (at most 2^18 rows).  Asynchronous
+        on the plan's stream."""
+        _need(v, 8 * self.n, "v")
+        _need(rec, WALK_RECORD_DTYPE.itemsize * self.n * reps, "rec")
+        _check(self._lib.mlmc_trace_noalloc(self._h, level, int(coarse), rep_begin, reps,
+                                            _ptr(v), ct.c_uint64(seed), _ptr(rec)))
 
     def export_tables(self) -> dict:
         n, nnz = self.n, self.nnz
