@@ -425,7 +425,7 @@ OPS_END_JUMPED = {True: 31, False: 24}
 OPS_END_STILL = 1
 # DRAM bytes of one captured walk launch (ncu, see profiles/); None when the
 # kernel changed after the capture.
-TRAFFIC_CAPTURE = None
+TRAFFIC_CAPTURE = 15625984  # one 4.1e8-walk launch at l0 (profiles/walk_fp32_ba_n1e5_l0.md)
 
 
 def walk_roofline(level_log, walk_s, clocks, peaks, total_ms):
