@@ -214,6 +214,49 @@ mlmc_status mlmc_trace_noalloc(mlmc_plan *plan, int32_t level, int32_t coarse, i
                                int64_t reps, const double *v, uint64_t seed,
                                mlmc_walk_record *rec);
 
+/* ---------------------------------------------------------------------
+ * Batches: many problems solved together.  A problem is a plan with one
+ * right-hand side; a plan may appear several times (several right-hand
+ * sides of one matrix) and plans may differ in size and in t.
+ * --------------------------------------------------------------------- */
+typedef struct mlmc_batch mlmc_batch;
+
+/* Create a batch over plans[0..count-1] (not owned; they must outlive the
+ * batch, share one device and one precision).  sched supplies the level
+ * schedule and budgets (NULL = the first plan's); each plan keeps its own
+ * l0.  rel_tol is the per-problem target.  cuda_stream is the caller's
+ * stream: mlmc_batch_expmv orders its work after work queued there.
+ * Creation runs the launch-shape autotuner (walks per lane of a work item,
+ * per problem-size bucket n < 1e4, < 1e5, >= 1e5; a few short walk
+ * launches) and captures the CUDA graph of one controller round. */
+mlmc_status mlmc_batch_create(mlmc_batch **out, mlmc_plan *const *plans, int32_t count,
+                              const mlmc_schedule *sched, double rel_tol, void *cuda_stream);
+
+/* x_k = exp(t_k A_k) v_k for every problem k, by Algorithm 1 run for all
+ * problems in lockstep rounds; each round is one graph launch (all walks of
+ * the round in one persistent kernel, then the batched reductions) and one
+ * synchronisation.  v[k], x[k]: host or device pointers to n_k doubles;
+ * seeds[k]: Philox key of problem k.  Returns NOT_CONVERGED if any problem
+ * stopped on a budget (every x is still written). */
+mlmc_status mlmc_batch_expmv(mlmc_batch *batch, const double *const *v, double *const *x,
+                             const uint64_t *seeds);
+
+/* Per-level statistics of problem `problem` after mlmc_batch_expmv (as
+ * mlmc_stats; seconds and launches are 0: walks of all problems share
+ * launches). */
+mlmc_status mlmc_batch_stats(const mlmc_batch *batch, int32_t problem, mlmc_level_stats *out,
+                             int32_t cap, int32_t *n_levels, double *est_rel_err);
+
+/* Rounds (graph launches), GPU seconds of the rounds and number of converged
+ * problems of the last mlmc_batch_expmv; any pointer may be NULL. */
+mlmc_status mlmc_batch_info(const mlmc_batch *batch, int64_t *rounds, double *gpu_seconds,
+                            int32_t *converged);
+
+/* The autotuner's walks per lane for the three size buckets (cap >= 3). */
+mlmc_status mlmc_batch_autotune(const mlmc_batch *batch, int32_t *walks_per_lane, int32_t cap);
+
+void mlmc_batch_destroy(mlmc_batch *batch);
+
 /* Copy the device tables to host arrays (any pointer may be NULL):
  *   l_ii, dl (= t d_i), inv_rate (1/(t L_ii), +inf when L_ii = 0): n doubles
  *   inv_rate32, dl32: n floats (the FP32 copies the FP32 walk uses)

@@ -188,25 +188,248 @@ __device__ __forceinline__ Meta32 load_meta<Meta32>(const Meta32* m, int64_t j) 
   return out;
 }
 
+// Walk-side parameters of one work item's walks (one plan or one batch
+// problem).
+struct ItemArgs {
+  const void* meta;
+  const AliasEntry* alias;
+  const void* v_walk;
+  int level;
+  uint32_t ctr3;
+  uint32_t key0, key1;
+  int64_t max_jumps;
+  double* sum_y;
+  int64_t rep_begin;
+  mlmc_walk_record* trace;
+  int64_t trace_stride;
+  int64_t trace_base;
+};
+
+// Per-warp running totals of the walks a warp has finished.
+template <typename T>
+struct WalkTotals {
+  SquareSum<T> y2;
+  double y2_fixed = 0.0;  // per-item constant part (walks without a jump)
+  unsigned long long jumps = 0, walks = 0, limit = 0, still = 0;
+  uint32_t bad = 0;
+};
+
+// Add a warp's totals into totals[] (one lane) and clear them.
+template <typename T>
+__device__ __forceinline__ void flush_totals(WalkTotals<T>& t, double* totals, uint32_t* flags,
+                                             int lane) {
+  double y2 = t.y2.value() + t.y2_fixed;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) y2 += __shfl_xor_sync(kFull, y2, o);
+  const unsigned long long jw = warp_sum_u64(t.jumps);
+  const unsigned long long ww = warp_sum_u64(t.walks);
+  const unsigned long long lw = warp_sum_u64(t.limit);
+  const unsigned long long sw = warp_sum_u64(t.still);
+  const uint32_t bad = __reduce_or_sync(kFull, t.bad);
+  if (lane == 0) {
+    if (ww) {
+      atomicAdd(totals + kTotY2, y2);
+      atomicAdd(totals + kTotJumps, static_cast<double>(jw));
+      atomicAdd(totals + kTotWalks, static_cast<double>(ww));
+      if (lw) atomicAdd(totals + kTotLimit, static_cast<double>(lw));
+      if (sw) atomicAdd(totals + kTotStill, static_cast<double>(sw));
+    }
+    if (bad) atomicOr(flags, bad);
+  }
+  t = WalkTotals<T>();
+}
+
+// One work item: walks r_lo .. r_hi-1 (replica offsets relative to
+// a.rep_begin) of row `row`, run by the whole warp as a pool.  Adds the
+// item's sum of Y to a.sum_y[row] (one atomic) and its totals to `tot`.
 template <bool FP64, bool COARSE, bool TRACE>
-__global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk(WalkArgs a) {
+__device__ __forceinline__ void walk_item(const ItemArgs& a, int64_t row, int64_t r_lo,
+                                          int64_t r_hi, WalkTotals<typename Prec<FP64>::T>& tot,
+                                          int lane) {
   using P = Prec<FP64>;
   using T = typename P::T;
   using Meta = typename P::Meta;
   using VT = typename P::VT;
   const Meta* __restrict__ meta = static_cast<const Meta*>(a.meta);
-  const int lane = threadIdx.x & 31;
+  const VT* __restrict__ vv = static_cast<const VT*>(a.v_walk);
   const int n_grid = 1 << a.level;                 // fine grid points 0..N
   const T n_fine = P::from_int(n_grid);
   const T inv_n = static_cast<T>(1.0 / n_grid);  // exact: a power of two
   const int n_coarse = n_grid >> 1;
+  const Meta m0 = load_meta(meta, row);
+  const T dl0 = static_cast<T>(m0.dl);
+  // A walk that never jumps stays at the row for the whole interval: its
+  // sample is 0 above l0 and v_row e^{dl_row} at l0 (E_f = dl_row exactly
+  // as the grid weights sum to 1), the same for every such walk.
+  T y_still = 0;
+  if (!COARSE) y_still = P::mul(static_cast<T>(__ldg(vv + row)), P::ex(dl0));
+  if (!isfinite(y_still)) {
+    tot.bad |= kFlagNonFiniteY;
+    y_still = 0;
+  }
 
-  SquareSum<T> tot_y2;
-  double tot_y2_fixed = 0.0;  // per-item constant part (walks without a jump)
-  unsigned long long tot_jumps = 0, tot_walks = 0, tot_limit = 0, tot_still = 0;
-  uint32_t bad = 0;
-  const VT* __restrict__ vv = static_cast<const VT*>(a.v_walk);
+  Kahan<T> acc_y;
+  uint32_t item_jumps = 0;  // this lane's jumps in this item (< 2^32)
+  uint32_t n_still = 0;     // this lane's walks without a jump
+  if (lane == 0) tot.walks += static_cast<unsigned long long>(r_hi - r_lo);
+  const uint32_t row32 = static_cast<uint32_t>(row);
+  const uint32_t span = static_cast<uint32_t>(r_hi - r_lo);
+  const uint64_t rep_base = static_cast<uint64_t>(a.rep_begin + r_lo);
+  // The item's walks form a pool: a lane whose walk ends claims the next
+  // unclaimed replica offset (ballot + prefix count), so lanes stay busy
+  // until the pool is empty.
+  uint32_t next = 32;                        // warp-uniform: next unclaimed offset
+  uint32_t r = static_cast<uint32_t>(lane);  // this lane's replica offset
+  bool live = r < span;
+  // Counter words of the current walk: replica bits 0-31 and word 3.
+  uint32_t c_lo = static_cast<uint32_t>(rep_base + r);
+  uint32_t c_hi = a.ctr3 | (static_cast<uint32_t>((rep_base + r) >> 32) << 8);
+  // Walk state.
+  Meta m = m0;
+  int32_t j = static_cast<int32_t>(row);
+  uint32_t e = 0;          // jumps taken (= Philox draw index)
+  uint32_t neg = 0;        // sign bit of the product of jump signs
+  T s = 0;                 // current time in [0,1)
+  T acc = 0;               // coarse: acc_c; coarsest: acc_f
+  T acc_d = 0;             // coarse only
+  int kprev = -1;          // grid index of the segment start (fine)
+  uint32_t hash = 2166136261u;
 
+  while (__any_sync(kFull, live)) {
+    bool fin = false;
+    if (live) {
+      const uint4 x = philox4x32_10(make_uint4(c_lo, row32, e, c_hi), a.key0, a.key1);
+      const T hold = P::mul(P::neglog(P::uniform(x)), static_cast<T>(m.inv_rate));
+      const T s_new = P::add(s, hold);
+      bool done = !(s_new < static_cast<T>(1));
+      int status = 0;
+      if (!done && static_cast<int64_t>(e) >= a.max_jumps) {
+        done = true;
+        status = 1;
+      }
+      if (!done) {
+        // Jump at s_new, after fine grid point g.
+        const int g = P::floor_int(P::mul(s_new, n_fine));
+        const T dlj = static_cast<T>(m.dl);
+        if (COARSE) {
+          const int kc_prev = kprev >> 1;   // floor(a/2), also for a = -1
+          acc = P::fma(P::from_int((g >> 1) - kc_prev), dlj, acc);
+          acc_d = P::fma(P::from_int((g & 1) - (kprev & 1)), dlj, acc_d);
+        } else {
+          acc = P::fma(P::from_int(g - kprev), dlj, acc);
+        }
+        kprev = g;
+        const uint32_t bucket = __umulhi(x.z, static_cast<uint32_t>(m.deg));
+        const uint4 ent = __ldg(reinterpret_cast<const uint4*>(a.alias + m.start) + bucket);
+        const uint32_t pick = (x.w < ent.x) ? ent.y : ent.z;
+        neg ^= pick >> 31;
+        j = static_cast<int32_t>(pick & kColMask);
+        if (TRACE) hash = (hash ^ static_cast<uint32_t>(j)) * 16777619u;
+        m = load_meta(meta, j);
+        s = s_new;
+        ++e;
+      } else if (!TRACE && e == 0 && status == 0) {
+        // No jump: the state is still the initial one.
+        ++n_still;
+        fin = true;
+      } else {
+        // Walk ends at state j (s = 1).
+        fin = true;
+        T y = 0;
+        if (status == 0) {
+          if (e == 0) {
+            y = y_still;
+          } else {
+            const T dle = static_cast<T>(m.dl);
+            const T h = P::mul(P::add(dl0, dle), static_cast<T>(0.5));
+            const T vend = static_cast<T>(__ldg(vv + j));
+            if (COARSE) {
+              const T acc_c = P::fma(P::from_int(n_coarse - (kprev >> 1)), dle, acc);
+              const T accd = P::fma(P::from_int(-(kprev & 1)), dle, acc_d);
+              const T ec = P::mul(P::sub(acc_c, h), P::mul(inv_n, static_cast<T>(2)));
+              const T diff = P::mul(P::add(accd, h), inv_n);
+              y = P::mul(vend, P::mul(P::ex(ec), P::exm1(diff)));
+            } else {
+              const T acc_f = P::fma(P::from_int(n_grid - kprev), dle, acc);
+              const T ef = P::mul(P::sub(acc_f, h), inv_n);
+              y = P::mul(vend, P::ex(ef));
+            }
+            if (neg) y = -y;
+            if (!isfinite(y)) {
+              tot.bad |= kFlagNonFiniteY;
+              y = 0;
+            }
+          }
+        } else {
+          tot.bad |= kFlagWalkLimit;
+          ++tot.limit;
+        }
+        acc_y.add(y);
+        tot.y2.add_square(y);
+        item_jumps += e;
+        if (TRACE) {
+          mlmc_walk_record rec;
+          rec.end = j;
+          rec.jumps = static_cast<int32_t>(e);
+          rec.sign = neg ? -1 : 1;
+          rec.hash = hash;
+          rec.y = static_cast<double>(y);
+          rec.status = status;
+          rec.pad = 0;
+          a.trace[row * a.trace_stride + a.trace_base + (r_lo + r)] = rec;
+        }
+      }
+    }
+    // Refill: finished lanes take the next walks of the pool.
+    const unsigned fmask = __ballot_sync(kFull, fin);
+    if (fin) {
+      r = next + static_cast<uint32_t>(__popc(fmask & ((1u << lane) - 1u)));
+      live = r < span;
+      c_lo = static_cast<uint32_t>(rep_base + r);
+      c_hi = a.ctr3 | (static_cast<uint32_t>((rep_base + r) >> 32) << 8);
+      m = load_meta(meta, row);
+      j = static_cast<int32_t>(row);
+      e = 0;
+      neg = 0;
+      s = 0;
+      acc = 0;
+      acc_d = 0;
+      kprev = -1;
+      hash = 2166136261u;
+    }
+    next += static_cast<uint32_t>(__popc(fmask));
+  }
+  tot.jumps += item_jumps;
+  double ys = warp_sum(acc_y);
+  const unsigned long long still = warp_sum_u64(n_still);
+  if (lane == 0) tot.still += still;
+  if (!COARSE) {
+    const double yc = static_cast<double>(y_still);
+    ys += static_cast<double>(still) * yc;
+    if (lane == 0) tot.y2_fixed += static_cast<double>(still) * (yc * yc);
+  }
+  if (lane == 0 && ys != 0.0) atomicAdd(a.sum_y + row, ys);
+}
+
+template <bool FP64, bool COARSE, bool TRACE>
+__global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk(WalkArgs a) {
+  using T = typename Prec<FP64>::T;
+  const int lane = threadIdx.x & 31;
+  ItemArgs ia;
+  ia.meta = a.meta;
+  ia.alias = a.alias;
+  ia.v_walk = a.v_walk;
+  ia.level = a.level;
+  ia.ctr3 = a.ctr3;
+  ia.key0 = a.key0;
+  ia.key1 = a.key1;
+  ia.max_jumps = a.max_jumps;
+  ia.sum_y = a.sum_y;
+  ia.rep_begin = a.rep_begin;
+  ia.trace = a.trace;
+  ia.trace_stride = a.trace_stride;
+  ia.trace_base = a.trace_base;
+  WalkTotals<T> tot;
   for (;;) {
     unsigned long long item = 0;
     if (lane == 0) item = atomicAdd(a.work, 1ull);
@@ -216,178 +439,61 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk(WalkArgs a) {
     const int64_t chunk = static_cast<int64_t>(item) - row * a.chunks_per_row;
     const int64_t r_lo = chunk * a.chunk;
     const int64_t r_hi = min(r_lo + a.chunk, a.reps);
-    const Meta m0 = load_meta(meta, row);
-    const T dl0 = static_cast<T>(m0.dl);
-    // A walk that never jumps stays at the row for the whole interval: its
-    // sample is 0 above l0 and v_row e^{dl_row} at l0 (E_f = dl_row exactly
-    // as the grid weights sum to 1), the same for every such walk.
-    T y_still = 0;
-    if (!COARSE) y_still = P::mul(static_cast<T>(__ldg(vv + row)), P::ex(dl0));
-    if (!isfinite(y_still)) {
-      bad |= kFlagNonFiniteY;
-      y_still = 0;
-    }
-
-    Kahan<T> acc_y;
-    uint32_t item_jumps = 0;  // this lane's jumps in this item (< 2^32)
-    uint32_t n_still = 0;     // this lane's walks without a jump
-    if (lane == 0) tot_walks += static_cast<unsigned long long>(r_hi - r_lo);
-    const uint32_t row32 = static_cast<uint32_t>(row);
-    const uint32_t span = static_cast<uint32_t>(r_hi - r_lo);
-    const uint64_t rep_base = static_cast<uint64_t>(a.rep_begin + r_lo);
-    // The item's walks form a pool: a lane whose walk ends claims the next
-    // unclaimed replica offset (ballot + prefix count), so lanes stay busy
-    // until the pool is empty.
-    uint32_t next = 32;                        // warp-uniform: next unclaimed offset
-    uint32_t r = static_cast<uint32_t>(lane);  // this lane's replica offset
-    bool live = r < span;
-    // Counter words of the current walk: replica bits 0-31 and word 3.
-    uint32_t c_lo = static_cast<uint32_t>(rep_base + r);
-    uint32_t c_hi = a.ctr3 | (static_cast<uint32_t>((rep_base + r) >> 32) << 8);
-    // Walk state.
-    Meta m = m0;
-    int32_t j = static_cast<int32_t>(row);
-    uint32_t e = 0;          // jumps taken (= Philox draw index)
-    uint32_t neg = 0;        // sign bit of the product of jump signs
-    T s = 0;                 // current time in [0,1)
-    T acc = 0;               // coarse: acc_c; coarsest: acc_f
-    T acc_d = 0;             // coarse only
-    int kprev = -1;          // grid index of the segment start (fine)
-    uint32_t hash = 2166136261u;
-
-    while (__any_sync(kFull, live)) {
-      bool fin = false;
-      if (live) {
-        const uint4 x = philox4x32_10(make_uint4(c_lo, row32, e, c_hi), a.key0, a.key1);
-        const T hold = P::mul(P::neglog(P::uniform(x)), static_cast<T>(m.inv_rate));
-        const T s_new = P::add(s, hold);
-        bool done = !(s_new < static_cast<T>(1));
-        int status = 0;
-        if (!done && static_cast<int64_t>(e) >= a.max_jumps) {
-          done = true;
-          status = 1;
-        }
-        if (!done) {
-          // Jump at s_new, after fine grid point g.
-          const int g = P::floor_int(P::mul(s_new, n_fine));
-          const T dlj = static_cast<T>(m.dl);
-          if (COARSE) {
-            const int kc_prev = kprev >> 1;   // floor(a/2), also for a = -1
-            acc = P::fma(P::from_int((g >> 1) - kc_prev), dlj, acc);
-            acc_d = P::fma(P::from_int((g & 1) - (kprev & 1)), dlj, acc_d);
-          } else {
-            acc = P::fma(P::from_int(g - kprev), dlj, acc);
-          }
-          kprev = g;
-          const uint32_t bucket = __umulhi(x.z, static_cast<uint32_t>(m.deg));
-          const uint4 ent = __ldg(reinterpret_cast<const uint4*>(a.alias + m.start) + bucket);
-          const uint32_t pick = (x.w < ent.x) ? ent.y : ent.z;
-          neg ^= pick >> 31;
-          j = static_cast<int32_t>(pick & kColMask);
-          if (TRACE) hash = (hash ^ static_cast<uint32_t>(j)) * 16777619u;
-          m = load_meta(meta, j);
-          s = s_new;
-          ++e;
-        } else if (!TRACE && e == 0 && status == 0) {
-          // No jump: the state is still the initial one.
-          ++n_still;
-          fin = true;
-        } else {
-          // Walk ends at state j (s = 1).
-          fin = true;
-          T y = 0;
-          if (status == 0) {
-            if (e == 0) {
-              y = y_still;
-            } else {
-              const T dle = static_cast<T>(m.dl);
-              const T h = P::mul(P::add(dl0, dle), static_cast<T>(0.5));
-              const T vend = static_cast<T>(__ldg(vv + j));
-              if (COARSE) {
-                const T acc_c = P::fma(P::from_int(n_coarse - (kprev >> 1)), dle, acc);
-                const T accd = P::fma(P::from_int(-(kprev & 1)), dle, acc_d);
-                const T ec = P::mul(P::sub(acc_c, h), P::mul(inv_n, static_cast<T>(2)));
-                const T diff = P::mul(P::add(accd, h), inv_n);
-                y = P::mul(vend, P::mul(P::ex(ec), P::exm1(diff)));
-              } else {
-                const T acc_f = P::fma(P::from_int(n_grid - kprev), dle, acc);
-                const T ef = P::mul(P::sub(acc_f, h), inv_n);
-                y = P::mul(vend, P::ex(ef));
-              }
-              if (neg) y = -y;
-              if (!isfinite(y)) {
-                bad |= kFlagNonFiniteY;
-                y = 0;
-              }
-            }
-          } else {
-            bad |= kFlagWalkLimit;
-            ++tot_limit;
-          }
-          acc_y.add(y);
-          tot_y2.add_square(y);
-          item_jumps += e;
-          if (TRACE) {
-            mlmc_walk_record rec;
-            rec.end = j;
-            rec.jumps = static_cast<int32_t>(e);
-            rec.sign = neg ? -1 : 1;
-            rec.hash = hash;
-            rec.y = static_cast<double>(y);
-            rec.status = status;
-            rec.pad = 0;
-            a.trace[row * a.trace_stride + a.trace_base + (r_lo + r)] = rec;
-          }
-        }
-      }
-      // Refill: finished lanes take the next walks of the pool.
-      const unsigned fmask = __ballot_sync(kFull, fin);
-      if (fin) {
-        r = next + static_cast<uint32_t>(__popc(fmask & ((1u << lane) - 1u)));
-        live = r < span;
-        c_lo = static_cast<uint32_t>(rep_base + r);
-        c_hi = a.ctr3 | (static_cast<uint32_t>((rep_base + r) >> 32) << 8);
-        m = load_meta(meta, row);
-        j = static_cast<int32_t>(row);
-        e = 0;
-        neg = 0;
-        s = 0;
-        acc = 0;
-        acc_d = 0;
-        kprev = -1;
-        hash = 2166136261u;
-      }
-      next += static_cast<uint32_t>(__popc(fmask));
-    }
-    tot_jumps += item_jumps;
-    double ys = warp_sum(acc_y);
-    const unsigned long long still = warp_sum_u64(n_still);
-    if (lane == 0) tot_still += still;
-    if (!COARSE) {
-      const double yc = static_cast<double>(y_still);
-      ys += static_cast<double>(still) * yc;
-      if (lane == 0) tot_y2_fixed += static_cast<double>(still) * (yc * yc);
-    }
-    if (lane == 0 && ys != 0.0) atomicAdd(a.sum_y + row, ys);
+    walk_item<FP64, COARSE, TRACE>(ia, row, r_lo, r_hi, tot, lane);
   }
-  // Flush this warp's totals.
-  double y2 = tot_y2.value() + tot_y2_fixed;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) y2 += __shfl_xor_sync(kFull, y2, o);
-  const unsigned long long jw = warp_sum_u64(tot_jumps);
-  const unsigned long long ww = warp_sum_u64(tot_walks);
-  const unsigned long long lw = warp_sum_u64(tot_limit);
-  const unsigned long long sw = warp_sum_u64(tot_still);
-  bad = __reduce_or_sync(kFull, bad);
-  if (lane == 0) {
-    if (ww) {
-      atomicAdd(a.totals + kTotY2, y2);
-      atomicAdd(a.totals + kTotJumps, static_cast<double>(jw));
-      atomicAdd(a.totals + kTotWalks, static_cast<double>(ww));
-      if (lw) atomicAdd(a.totals + kTotLimit, static_cast<double>(lw));
-      if (sw) atomicAdd(a.totals + kTotStill, static_cast<double>(sw));
+  flush_totals(tot, a.totals, a.flags, lane);
+}
+
+// Batched walks: the items of many (problem, level, replica range) segments
+// in one persistent launch.  A warp maps its item to a segment by binary
+// search over the segments' first items, then runs the same per-item walk as
+// k_walk with that problem's tables and adds its totals to the problem's
+// level totals.
+template <bool FP64>
+__global__ void __launch_bounds__(256, FP64 ? 3 : 4)
+    k_walk_batch(const BatchProblemDev* __restrict__ probs, const BatchHeaderDev* __restrict__ hdr,
+                 const BatchSegmentDev* __restrict__ segs, unsigned long long* __restrict__ work,
+                 uint32_t* __restrict__ flags) {
+  using T = typename Prec<FP64>::T;
+  const int lane = threadIdx.x & 31;
+  const unsigned long long total = hdr->total_items;
+  const int nseg = hdr->segments;
+  WalkTotals<T> tot;
+  for (;;) {
+    unsigned long long item = 0;
+    if (lane == 0) item = atomicAdd(work, 1ull);
+    item = __shfl_sync(kFull, item, 0);
+    if (item >= total) break;
+    int lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (segs[mid].item_begin <= item) lo = mid; else hi = mid - 1;
     }
-    if (bad) atomicOr(a.flags, bad);
+    const BatchSegmentDev sg = segs[lo];
+    const BatchProblemDev pb = probs[sg.problem];
+    const unsigned long long local = item - sg.item_begin;
+    const int64_t row = static_cast<int64_t>(local / static_cast<unsigned long long>(sg.chunks_per_row));
+    const int64_t chunk = static_cast<int64_t>(local) - row * sg.chunks_per_row;
+    const int64_t r_lo = chunk * sg.chunk;
+    const int64_t r_hi = min(r_lo + sg.chunk, sg.reps);
+    const int level = pb.l0 + sg.slot;
+    ItemArgs ia;
+    ia.meta = pb.meta;
+    ia.alias = pb.alias;
+    ia.v_walk = pb.v_walk;
+    ia.level = level;
+    ia.ctr3 = static_cast<uint32_t>(level) & 0x3Fu;
+    ia.key0 = pb.key0;
+    ia.key1 = pb.key1;
+    ia.max_jumps = pb.max_jumps;
+    ia.sum_y = pb.sums + static_cast<int64_t>(sg.slot) * pb.n;
+    ia.rep_begin = sg.rep_begin;
+    ia.trace = nullptr;
+    ia.trace_stride = 0;
+    ia.trace_base = 0;
+    if (sg.slot > 0) walk_item<FP64, true, false>(ia, row, r_lo, r_hi, tot, lane);
+    else walk_item<FP64, false, false>(ia, row, r_lo, r_hi, tot, lane);
+    flush_totals(tot, pb.totals + static_cast<int64_t>(sg.slot) * kTotSlots, flags, lane);
   }
 }
 
@@ -544,6 +650,19 @@ cudaError_t launch_walk_scratch(mlmc_plan* p, const WalkLaunch& w, unsigned long
     if (launches) ++*launches;
   }
   return cudaSuccess;
+}
+
+cudaError_t launch_walk_batch(bool fp64, const BatchProblemDev* probs, const BatchHeaderDev* hdr,
+                              const BatchSegmentDev* segs, unsigned long long* work,
+                              uint32_t* flags, int num_sms, int block, cudaStream_t stream) {
+  int per_sm = 0;
+  cudaError_t err = fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_batch<true>, block, 0)
+                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_batch<false>, block, 0);
+  if (err != cudaSuccess) return err;
+  const unsigned grid = static_cast<unsigned>(num_sms * (per_sm > 0 ? per_sm : 1));
+  if (fp64) k_walk_batch<true><<<grid, block, 0, stream>>>(probs, hdr, segs, work, flags);
+  else k_walk_batch<false><<<grid, block, 0, stream>>>(probs, hdr, segs, work, flags);
+  return cudaGetLastError();
 }
 
 }  // namespace mlmc

@@ -84,11 +84,19 @@ def load(build_if_missing: bool = False):
     lib.mlmc_plan_destroy.argtypes = [P]
     lib.mlmc_plan_destroy.restype = None
     lib.mlmc_last_error.restype = ct.c_char_p
+    lib.mlmc_batch_create.argtypes = [ct.POINTER(P), P, I32, ct.POINTER(Schedule), D, P]
+    lib.mlmc_batch_expmv.argtypes = [P, P, P, P]
+    lib.mlmc_batch_stats.argtypes = [P, I32, P, I32, ct.POINTER(I32), ct.POINTER(D)]
+    lib.mlmc_batch_info.argtypes = [P, ct.POINTER(I64), ct.POINTER(D), ct.POINTER(I32)]
+    lib.mlmc_batch_autotune.argtypes = [P, P, I32]
+    lib.mlmc_batch_destroy.argtypes = [P]
+    lib.mlmc_batch_destroy.restype = None
     lib.mlmc_launch_count.argtypes = [P]
     lib.mlmc_launch_count.restype = I64
     for name in ("mlmc_schedule_default", "mlmc_plan_create", "mlmc_plan_rebuild", "mlmc_expmv",
                  "mlmc_stats", "mlmc_mlmcl", "mlmc_trace", "mlmc_trace_noalloc",
-                 "mlmc_export_tables",
+                 "mlmc_export_tables", "mlmc_batch_create", "mlmc_batch_expmv",
+                 "mlmc_batch_stats", "mlmc_batch_info", "mlmc_batch_autotune",
                  "mlmc_plan_info"):
         getattr(lib, name).restype = ct.c_int
     _lib = lib
@@ -254,3 +262,68 @@ class Plan:
 
     def launch_count(self) -> int:
         return int(self._lib.mlmc_launch_count(self._h))
+
+
+class Batch:
+    """An mlmc_batch over plans (one problem per entry; repeat a plan for
+    several right-hand sides)."""
+
+    def __init__(self, plans, sched: Schedule = None, rel_tol: float = 1e-3, stream: int = 0):
+        lib = load()
+        self._lib = lib
+        self._plans = list(plans)
+        arr = (ct.c_void_p * len(self._plans))(*[p.handle for p in self._plans])
+        self._h = ct.c_void_p()
+        _check(lib.mlmc_batch_create(ct.byref(self._h), arr, len(self._plans),
+                                     ct.byref(sched) if sched is not None else None,
+                                     float(rel_tol), ct.c_void_p(stream)))
+
+    def close(self):
+        if self._h:
+            self._lib.mlmc_batch_destroy(self._h)
+            self._h = ct.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def expmv(self, vs, xs, seeds, allow_not_converged: bool = False) -> int:
+        k = len(self._plans)
+        if len(vs) != k or len(xs) != k or len(seeds) != k:
+            raise ValueError("one v, x and seed per problem")
+        for p, v, x in zip(self._plans, vs, xs):
+            _need(v, 8 * p.n, "v")
+            _need(x, 8 * p.n, "x")
+        va = (ct.c_void_p * k)(*[_ptr(v) for v in vs])
+        xa = (ct.c_void_p * k)(*[_ptr(x) for x in xs])
+        sa = (ct.c_uint64 * k)(*[int(s) for s in seeds])
+        allow = (MLMC_ERR_NOT_CONVERGED,) if allow_not_converged else ()
+        return _check(self._lib.mlmc_batch_expmv(self._h, va, xa, sa), allow)
+
+    def stats(self, problem: int):
+        cap = 32
+        arr = (LevelStats * cap)()
+        nl = ct.c_int32()
+        err = ct.c_double()
+        _check(self._lib.mlmc_batch_stats(self._h, problem, arr, cap, ct.byref(nl), ct.byref(err)))
+        levels = [{f: getattr(arr[j], f) for f, _ in LevelStats._fields_ if f != "pad"}
+                  for j in range(nl.value)]
+        return levels, err.value
+
+    def info(self) -> dict:
+        r, g, c = ct.c_int64(), ct.c_double(), ct.c_int32()
+        _check(self._lib.mlmc_batch_info(self._h, ct.byref(r), ct.byref(g), ct.byref(c)))
+        return dict(rounds=r.value, gpu_seconds=g.value, converged=c.value)
+
+    def autotune(self):
+        out = (ct.c_int32 * 3)()
+        _check(self._lib.mlmc_batch_autotune(self._h, out, 3))
+        return list(out)
