@@ -459,6 +459,85 @@ def log(msg: str):
     print(f"[bench] {msg}", file=sys.stderr, flush=True)
 
 
+# ---------------------------------------------------------------------------
+# Secondary workload: batching (256 Laplacian instances, 1-8 right-hand sides)
+# ---------------------------------------------------------------------------
+def run_batch_workload(args):
+    """Batched solver against a loop of single-plan solves on the same
+    inputs (every instance and right-hand side, same seeds, same tolerance).
+    Prints one JSON line; not the default benchmark."""
+    import torch
+    import mlmc_inputs as I
+    import __graft_entry__ as g
+    g.build()
+    from paper_1904_12754_gb300 import mlmc as M
+    stream = torch.cuda.current_stream()
+    inst = I.workload_c3()
+    tol = args.tol
+    sched = M.schedule_default(precision=M.FP32_KAHAN, num_levels=3, max_levels=10, pilot_walks=64,
+                               time_budget_s=600.0)
+    plans, probs = [], []
+    t0 = time.perf_counter()
+    for w, rhs in inst:
+        p = M.Plan.from_csr(w.a, w.t, sched, rel_tol=tol, stream=stream.cuda_stream)
+        plans.append(p)
+        for r in range(rhs.shape[0]):
+            probs.append((p, torch.from_numpy(np.ascontiguousarray(rhs[r])).cuda()))
+    torch.cuda.synchronize()
+    t_plans = time.perf_counter() - t0
+    rows = sum(p.n for p in plans)
+    log(f"{len(plans)} instances, {len(probs)} problems, {rows} rows; plans in {t_plans:.1f} s")
+    xs = [torch.zeros(p.n, dtype=torch.float64, device="cuda") for p, _ in probs]
+    seeds = [7 + 13 * k for k in range(len(probs))]
+
+    def events_of(levels, n):
+        return sum(lv["walks_per_row"] * n + lv["jumps"] for lv in levels)
+
+    # plain: one mlmc_expmv per problem
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain_events, plain_conv = 0, 0
+    for k, (p, v) in enumerate(probs):
+        rc = p.expmv(v, xs[k], seeds[k], allow_not_converged=True)
+        lv, _ = p.stats()
+        plain_events += events_of(lv, p.n)
+        plain_conv += rc == 0
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+    log(f"plain loop: {t_plain:.2f} s, {plain_conv}/{len(probs)} converged")
+    # batched
+    t0 = time.perf_counter()
+    batch = M.Batch([p for p, _ in probs], sched, rel_tol=tol, stream=stream.cuda_stream)
+    t_create = time.perf_counter() - t0
+    batch.expmv([v for _, v in probs], xs, seeds, allow_not_converged=True)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    batch.expmv([v for _, v in probs], xs, seeds, allow_not_converged=True)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    info = batch.info()
+    batch_events = sum(events_of(batch.stats(k)[0], p.n) for k, (p, _) in enumerate(probs))
+    ests = [batch.stats(k)[1] for k in range(len(probs))]
+    log(f"batch: {t_batch:.2f} s, {info['rounds']} rounds, {info['converged']}/{len(probs)} converged")
+    line = {"metric": "time to per-instance rel. RMS tolerance, batched vs plain", "unit": "s",
+            "value": t_batch, "higher_is_better": False, "n_gpus": 1, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "256 Laplacian instances (2D/3D), n log-uniform in [1e3, 1e6], "
+                                   "t ~ U[0.1, 2], 1-8 right-hand sides", "tol": tol,
+                       "problems": len(probs), "rows": rows},
+            "batched": {"seconds": t_batch, "walk_steps_per_s": batch_events / t_batch,
+                        "rounds": info["rounds"], "gpu_seconds": info["gpu_seconds"],
+                        "converged": info["converged"], "max_est_rel_err": max(ests),
+                        "create_s": t_create, "walks_per_lane_by_bucket": batch.autotune()},
+            "plain": {"seconds": t_plain, "walk_steps_per_s": plain_events / t_plain,
+                      "converged": plain_conv},
+            "speedup": t_plain / t_batch}
+    print(json.dumps(line), flush=True)
+    batch.close()
+    for p in plans:
+        p.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -469,10 +548,15 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=15.0)
     ap.add_argument("--step-budget", type=float, default=8.0,
                     help="controller wall-clock budget of one step (s)")
+    ap.add_argument("--workload", choices=["tc", "batch"], default="tc",
+                    help="tc: the metric's workload (default); batch: batched vs plain")
+    ap.add_argument("--tol", type=float, default=1e-2, help="tolerance of --workload batch")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
-    if args.impl == "reference":
+    if args.workload == "batch":
+        run_batch_workload(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
