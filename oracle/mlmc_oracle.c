@@ -224,76 +224,134 @@ int orc_split(int64_t n, const int64_t *row_ptr, const int32_t *col, const doubl
  * own column when x3 < threshold_b and takes the alias column otherwise.
  * A row with L_ii = 0 (every off-diagonal stored as zero) never jumps; its
  * buckets keep themselves. */
-int orc_alias(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
-              const double *L, const int32_t *deg, uint32_t *thr, int32_t *keep_col,
-              uint8_t *keep_neg, int32_t *alias_col, uint8_t *alias_neg)
+/* Vose over one row's bucket probabilities p[0..k-1] (modified in place);
+ * prob/alias receive each bucket's keep probability and alias bucket. */
+static void orc_vose_row(int32_t k, double *p, double *prob, int32_t *alias, int32_t *small,
+                         int32_t *large)
+{
+    int32_t s_head = 0, s_len = 0, g_head = 0, g_len = 0;
+    for (int32_t b = 0; b < k; ++b) {
+        if (p[b] < 1.0) small[(s_head + s_len++) % k] = b;
+        else large[(g_head + g_len++) % k] = b;
+    }
+    while (s_len > 0 && g_len > 0) {
+        int32_t l = small[s_head];
+        s_head = (s_head + 1) % k; s_len--;
+        int32_t g = large[g_head];
+        g_head = (g_head + 1) % k; g_len--;
+        prob[l] = p[l];
+        alias[l] = g;
+        p[g] = (p[g] + p[l]) - 1.0;
+        if (p[g] < 1.0) small[(s_head + s_len++) % k] = g;
+        else large[(g_head + g_len++) % k] = g;
+    }
+    while (g_len > 0) {
+        int32_t g = large[g_head];
+        g_head = (g_head + 1) % k; g_len--;
+        prob[g] = 1.0;
+        alias[g] = g;
+    }
+    while (s_len > 0) {
+        int32_t l = small[s_head];
+        s_head = (s_head + 1) % k; s_len--;
+        prob[l] = 1.0;
+        alias[l] = l;
+    }
+}
+
+static uint32_t orc_threshold(double prob)
+{
+    double scaled = floor(prob * 4294967296.0);
+    return (scaled >= 4294967295.0) ? 0xFFFFFFFFu : (uint32_t)scaled;
+}
+
+/* Alias tables for the jump law of Eq. 12 (see the comment above), or, when
+ * h != NULL, for the importance-sampling proposal
+ *   q_b = (1 - alpha) |a_b| h(col_b) / sum_c |a_c| h(col_c) + alpha |a_b| / L_ii
+ * (a defensive mixture with the paper's law k_b = |a_b| / L_ii), with
+ * p_b = q_b deg and lr_b = log(k_b / q_b) recorded for the kept and alias
+ * columns of each bucket.  The walk adds lr of every jump to its exponent,
+ * which keeps the estimator unbiased whatever h > 0 is. */
+static int orc_alias_impl(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
+                          const double *L, const int32_t *deg, const float *h, double alpha,
+                          uint32_t *thr, int32_t *keep_col, uint8_t *keep_neg, int32_t *alias_col,
+                          uint8_t *alias_neg, float *lr_keep, float *lr_alias)
 {
     int64_t max_deg = 0;
     for (int64_t i = 0; i < n; ++i)
         if (deg[i] > max_deg) max_deg = deg[i];
-    double *p = (double *)malloc(sizeof(double) * (size_t)(max_deg + 1));
-    int32_t *bcol = (int32_t *)malloc(sizeof(int32_t) * (size_t)(max_deg + 1));
-    uint8_t *bneg = (uint8_t *)malloc((size_t)(max_deg + 1));
-    int32_t *small = (int32_t *)malloc(sizeof(int32_t) * (size_t)(max_deg + 1));
-    int32_t *large = (int32_t *)malloc(sizeof(int32_t) * (size_t)(max_deg + 1));
-    double *prob = (double *)malloc(sizeof(double) * (size_t)(max_deg + 1));
-    int32_t *alias = (int32_t *)malloc(sizeof(int32_t) * (size_t)(max_deg + 1));
-    if (!p || !bcol || !bneg || !small || !large || !prob || !alias) return -1;
+    size_t cap = (size_t)(max_deg + 1);
+    double *p = (double *)malloc(sizeof(double) * cap);
+    double *lr = (double *)malloc(sizeof(double) * cap);
+    int32_t *bcol = (int32_t *)malloc(sizeof(int32_t) * cap);
+    uint8_t *bneg = (uint8_t *)malloc(cap);
+    int32_t *small = (int32_t *)malloc(sizeof(int32_t) * cap);
+    int32_t *large = (int32_t *)malloc(sizeof(int32_t) * cap);
+    double *prob = (double *)malloc(sizeof(double) * cap);
+    int32_t *alias = (int32_t *)malloc(sizeof(int32_t) * cap);
+    if (!p || !lr || !bcol || !bneg || !small || !large || !prob || !alias) return -1;
 
     for (int64_t i = 0; i < n; ++i) {
         int32_t k = deg[i];
         if (k == 0) continue;
         int32_t b = 0;
+        double hsum = 0.0;
         for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q) {
             if ((int64_t)col[q] == i) continue;
             bcol[b] = col[q];
             bneg[b] = (uint8_t)(val[q] < 0.0);
-            p[b] = (L[i] > 0.0) ? (fabs(val[q]) * (double)k) / L[i] : 1.0;
+            if (h) hsum = hsum + fabs(val[q]) * (double)h[col[q]];
             ++b;
         }
-        /* FIFO queues as ring buffers of capacity k (each bucket sits in at
-         * most one queue at a time). */
-        int32_t s_head = 0, s_len = 0, g_head = 0, g_len = 0;
+        b = 0;
+        for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q) {
+            if ((int64_t)col[q] == i) continue;
+            double w = fabs(val[q]);
+            if (L[i] <= 0.0) {
+                p[b] = 1.0;
+                lr[b] = 0.0;
+            } else if (!h || !(hsum > 0.0)) {
+                p[b] = (w * (double)k) / L[i];
+                lr[b] = 0.0;
+            } else {
+                double kb = w / L[i];
+                double qb = (1.0 - alpha) * ((w * (double)h[col[q]]) / hsum) + alpha * kb;
+                p[b] = qb * (double)k;
+                lr[b] = (qb > 0.0) ? log(kb / qb) : 0.0;
+            }
+            ++b;
+        }
+        orc_vose_row(k, p, prob, alias, small, large);
         for (b = 0; b < k; ++b) {
-            if (p[b] < 1.0) small[(s_head + s_len++) % k] = b;
-            else large[(g_head + g_len++) % k] = b;
-        }
-        while (s_len > 0 && g_len > 0) {
-            int32_t l = small[s_head];
-            s_head = (s_head + 1) % k; s_len--;
-            int32_t g = large[g_head];
-            g_head = (g_head + 1) % k; g_len--;
-            prob[l] = p[l];
-            alias[l] = g;
-            p[g] = (p[g] + p[l]) - 1.0;
-            if (p[g] < 1.0) small[(s_head + s_len++) % k] = g;
-            else large[(g_head + g_len++) % k] = g;
-        }
-        while (g_len > 0) {
-            int32_t g = large[g_head];
-            g_head = (g_head + 1) % k; g_len--;
-            prob[g] = 1.0;
-            alias[g] = g;
-        }
-        while (s_len > 0) {
-            int32_t l = small[s_head];
-            s_head = (s_head + 1) % k; s_len--;
-            prob[l] = 1.0;
-            alias[l] = l;
-        }
-        for (b = 0; b < k; ++b) {
-            double scaled = floor(prob[b] * 4294967296.0);
-            uint32_t th = (scaled >= 4294967295.0) ? 0xFFFFFFFFu : (uint32_t)scaled;
             int64_t pos = row_ptr[i] + b;
-            thr[pos] = th;
+            thr[pos] = orc_threshold(prob[b]);
             keep_col[pos] = bcol[b];
             keep_neg[pos] = bneg[b];
             alias_col[pos] = bcol[alias[b]];
             alias_neg[pos] = bneg[alias[b]];
+            if (lr_keep) lr_keep[pos] = (float)lr[b];
+            if (lr_alias) lr_alias[pos] = (float)lr[alias[b]];
         }
     }
-    free(p); free(bcol); free(bneg); free(small); free(large); free(prob); free(alias);
+    free(p); free(lr); free(bcol); free(bneg); free(small); free(large); free(prob); free(alias);
     return 0;
+}
+
+int orc_alias(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
+              const double *L, const int32_t *deg, uint32_t *thr, int32_t *keep_col,
+              uint8_t *keep_neg, int32_t *alias_col, uint8_t *alias_neg)
+{
+    return orc_alias_impl(n, row_ptr, col, val, L, deg, NULL, 0.0, thr, keep_col, keep_neg,
+                          alias_col, alias_neg, NULL, NULL);
+}
+
+int orc_alias_is(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
+                 const double *L, const int32_t *deg, const float *h, double alpha, uint32_t *thr,
+                 int32_t *keep_col, uint8_t *keep_neg, int32_t *alias_col, uint8_t *alias_neg,
+                 float *lr_keep, float *lr_alias)
+{
+    return orc_alias_impl(n, row_ptr, col, val, L, deg, h, alpha, thr, keep_col, keep_neg,
+                          alias_col, alias_neg, lr_keep, lr_alias);
 }
 
 /* ------------------------------------------------------------------ */
@@ -318,6 +376,8 @@ typedef struct {
     const int32_t *alias_col;
     const uint8_t *alias_neg;
     const double *v;           /* right-hand side u of the paper */
+    const float *lr_keep;      /* NULL, or log(k/q) of each bucket's kept column */
+    const float *lr_alias;     /* ... and of its alias column (proposal tables) */
     uint64_t seed;
     int32_t precision;         /* ORC_FP64 or ORC_FP32 time arithmetic */
     int32_t variant;           /* ORC_RESIDUAL, ORC_REDRAW, ORC_LITERAL_RATE */
@@ -366,19 +426,24 @@ static double orc_hold(const orc_ctx *c, int64_t j, const uint32_t x[4], double 
     return from + s;
 }
 
-/* Choose the next state from row j's alias table with draw words x2, x3. */
-static int64_t orc_jump(const orc_ctx *c, int64_t j, const uint32_t x[4], int32_t *sign)
+/* Choose the next state from row j's alias table with draw words x2, x3;
+ * *lr receives log(k/q) of the chosen column (0 without a proposal). */
+static int64_t orc_jump(const orc_ctx *c, int64_t j, const uint32_t x[4], int32_t *sign,
+                        double *lr)
 {
     uint32_t b = (uint32_t)(((uint64_t)x[2] * (uint64_t)(uint32_t)c->deg[j]) >> 32);
     int64_t pos = c->row_ptr[j] + b;
     int64_t to;
     int neg;
+    *lr = 0.0;
     if (x[3] < c->thr[pos]) {
         to = c->keep_col[pos];
         neg = c->keep_neg[pos];
+        if (c->lr_keep) *lr = (double)c->lr_keep[pos];
     } else {
         to = c->alias_col[pos];
         neg = c->alias_neg[pos];
+        if (c->lr_alias) *lr = (double)c->lr_alias[pos];
     }
     if (neg) *sign = -*sign;
     return to;
@@ -419,6 +484,7 @@ int orc_walk(const orc_ctx *c, int64_t row, int64_t rep, int level, int coarse,
     uint32_t x[4];
     double eta2 = 1.0, eta1 = 1.0;
     double log_f = 0.0, log_c = 0.0, diff = 0.0;
+    double log_is = 0.0;  /* sum of log(k/q) over the jumps (proposal tables) */
     int64_t x_prev2 = row, x_prev1 = row; /* states at grid points 2j-2, 2j-1 */
 
     orc_draw(c, row, rep, ndraw++, level, x);
@@ -439,7 +505,9 @@ int orc_walk(const orc_ctx *c, int64_t row, int64_t rep, int level, int coarse,
                 goto done;
             }
             int64_t from = j;
-            j = orc_jump(c, j, x, &sign);
+            double lr = 0.0;
+            j = orc_jump(c, j, x, &sign, &lr);
+            log_is = log_is + lr;
             hash = (hash ^ (uint32_t)j) * 16777619u;
             jumps = jumps + 1;
             orc_draw(c, row, rep, ndraw++, level, x);
@@ -486,11 +554,11 @@ done:
     out->log_f = log_f;
     out->log_c = coarse ? log_c : 0.0;
     if (coarse) {
-        out->y = (double)sign * uj * (exp(log_c) * expm1(diff));
-        out->y_alg2 = (double)sign * uj * (eta2 - eta1);
+        out->y = (double)sign * uj * (exp(log_c + log_is) * expm1(diff));
+        out->y_alg2 = (double)sign * uj * (eta2 - eta1) * exp(log_is);
     } else {
-        out->y = (double)sign * uj * exp(log_f);
-        out->y_alg2 = (double)sign * uj * eta2;
+        out->y = (double)sign * uj * exp(log_f + log_is);
+        out->y_alg2 = (double)sign * uj * eta2 * exp(log_is);
     }
     return status;
 }

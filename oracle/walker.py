@@ -56,7 +56,7 @@ class Ctx(ct.Structure):
                 ("dl", ct.c_void_p), ("inv_rate", ct.c_void_p), ("inv_rate32", ct.c_void_p),
                 ("thr", ct.c_void_p), ("keep_col", ct.c_void_p), ("keep_neg", ct.c_void_p),
                 ("alias_col", ct.c_void_p), ("alias_neg", ct.c_void_p), ("v", ct.c_void_p),
-                ("seed", ct.c_uint64), ("precision", ct.c_int32), ("variant", ct.c_int32),
+                ("lr_keep", ct.c_void_p), ("lr_alias", ct.c_void_p), ("seed", ct.c_uint64), ("precision", ct.c_int32), ("variant", ct.c_int32),
                 ("max_jumps", ct.c_int64)]
 
 
@@ -79,6 +79,9 @@ def lib():
         _lib.orc_split.argtypes = [ct.c_int64, P, P, P, ct.c_double, P, P, P, P, P, P, P]
         _lib.orc_alias.argtypes = [ct.c_int64, P, P, P, P, P, P, P, P, P, P]
         _lib.orc_alias.restype = ct.c_int
+        _lib.orc_alias_is.argtypes = [ct.c_int64, P, P, P, P, P, P, ct.c_double, P, P, P, P, P, P,
+                                      P]
+        _lib.orc_alias_is.restype = ct.c_int
         _lib.orc_walk.argtypes = [ct.POINTER(Ctx), ct.c_int64, ct.c_int64, ct.c_int, ct.c_int,
                                   ct.POINTER(WalkRec)]
         _lib.orc_walk_many.argtypes = [ct.POINTER(Ctx), ct.c_int64, P, P, ct.c_int, ct.c_int, P]
@@ -132,11 +135,16 @@ class Tables:
     keep_neg: np.ndarray
     alias_col: np.ndarray
     alias_neg: np.ndarray
+    lr_keep: np.ndarray = None   # proposal tables only: log(k/q) of the kept column
+    lr_alias: np.ndarray = None  # ... and of the alias column
 
 
-def build_tables(a, t: float) -> Tables:
+def build_tables(a, t: float, h=None, alpha: float = 0.1) -> Tables:
     """Splitting (Eq. 1) and alias tables (Eq. 12) of the CSR matrix ``a``
-    for time ``t``.  ``a`` has fields n, row_ptr, col, val."""
+    for time ``t``.  ``a`` has fields n, row_ptr, col, val.  With ``h`` (n
+    positive float32 values) the tables sample the importance-sampling
+    proposal q = (1-alpha) |a_ij| h_j / sum + alpha k_ij instead, and record
+    log(k/q) per entry."""
     n = a.n
     rp = np.ascontiguousarray(a.row_ptr, dtype=np.int64)
     col = np.ascontiguousarray(a.col, dtype=np.int32)
@@ -157,12 +165,21 @@ def build_tables(a, t: float) -> Tables:
     keep_neg = np.zeros(m, dtype=np.uint8)
     alias_col = np.full(m, -1, dtype=np.int32)
     alias_neg = np.zeros(m, dtype=np.uint8)
-    rc = lib().orc_alias(n, _p(rp), _p(col), _p(val), _p(L), _p(deg), _p(thr), _p(keep_col),
-                         _p(keep_neg), _p(alias_col), _p(alias_neg))
+    if h is None:
+        rc = lib().orc_alias(n, _p(rp), _p(col), _p(val), _p(L), _p(deg), _p(thr), _p(keep_col),
+                             _p(keep_neg), _p(alias_col), _p(alias_neg))
+        lr_keep = lr_alias = None
+    else:
+        hh = np.ascontiguousarray(h, dtype=np.float32)
+        lr_keep = np.zeros(m, dtype=np.float32)
+        lr_alias = np.zeros(m, dtype=np.float32)
+        rc = lib().orc_alias_is(n, _p(rp), _p(col), _p(val), _p(L), _p(deg), _p(hh), float(alpha),
+                                _p(thr), _p(keep_col), _p(keep_neg), _p(alias_col),
+                                _p(alias_neg), _p(lr_keep), _p(lr_alias))
     if rc != 0:
         raise MemoryError("oracle alias build failed")
     return Tables(n, rp, a_ii, L, deg, dl, inv_rate, inv_rate32, dl32, thr, keep_col, keep_neg,
-                  alias_col, alias_neg)
+                  alias_col, alias_neg, lr_keep, lr_alias)
 
 
 class Walker:
@@ -174,10 +191,12 @@ class Walker:
         self.v = np.ascontiguousarray(v, dtype=np.float64)
         tb = self.tables
         self._keep = (tb, self.v)
+        lrk = _p(tb.lr_keep).value if tb.lr_keep is not None else None
+        lra = _p(tb.lr_alias).value if tb.lr_alias is not None else None
         self.ctx = Ctx(tb.n, _p(tb.row_ptr).value, _p(tb.deg).value, _p(tb.dl).value,
                        _p(tb.inv_rate).value, _p(tb.inv_rate32).value, _p(tb.thr).value,
                        _p(tb.keep_col).value, _p(tb.keep_neg).value, _p(tb.alias_col).value,
-                       _p(tb.alias_neg).value, _p(self.v).value, ct.c_uint64(seed),
+                       _p(tb.alias_neg).value, _p(self.v).value, lrk, lra, ct.c_uint64(seed),
                        precision, variant, max_jumps)
 
     def walk(self, row: int, rep: int, level: int, coarse: bool) -> WalkRec:

@@ -174,3 +174,65 @@ def test_walk_limit_is_reported():
     wk = W.Walker(a, 50.0, np.ones(6), seed=1, max_jumps=3)
     r = wk.walk(0, 0, 2, False)
     assert r.status == 1 and r.y == 0.0
+
+
+# ---------------------------------------------------------------------------
+# Importance-sampling proposal tables (the learned-proposal path)
+# ---------------------------------------------------------------------------
+def test_proposal_tables_sample_the_mixture_and_record_log_ratios():
+    a = I.random_sparse(80, 6, seed=12, signed=True, diag=True)
+    h = np.random.default_rng(4).uniform(0.2, 5.0, a.n).astype(np.float32)
+    alpha = 0.15
+    tb = W.build_tables(a, 0.7, h, alpha)
+    dense = a.dense()
+    for i in range(a.n):
+        if tb.deg[i] == 0:
+            continue
+        off = [j for j in range(a.n) if j != i and dense[i, j] != 0.0]
+        k = {j: abs(dense[i, j]) / tb.L[i] for j in off}
+        hs = sum(abs(dense[i, j]) * float(h[j]) for j in off)
+        q = {j: (1 - alpha) * abs(dense[i, j]) * float(h[j]) / hs + alpha * k[j] for j in off}
+        law = _exact_jump_law(tb, i)
+        assert max(abs(law.get(j, 0.0) - q[j]) for j in off) <= 1e-8
+        for b in range(int(tb.deg[i])):
+            pos = int(tb.row_ptr[i]) + b
+            for c, lr in ((tb.keep_col[pos], tb.lr_keep[pos]), (tb.alias_col[pos], tb.lr_alias[pos])):
+                assert abs(float(lr) - np.log(k[int(c)] / q[int(c)])) <= 1e-6 * (1 + abs(float(lr)))
+
+
+@pytest.mark.parametrize("level,coarse", [(1, False), (3, True)])
+def test_proposal_walks_are_unbiased(level, coarse):
+    # E_q[Y prod k/q] equals the exact mean of the plain walk (Eq. 3, 8).
+    a = I.random_sparse(6, 2, seed=3, signed=True, diag=True)
+    v = np.random.default_rng(5).random(6) - 0.3
+    h = np.random.default_rng(6).uniform(0.1, 10.0, 6).astype(np.float32)
+    m1, m2 = R.level_moments(a.dense(), 0.7, v, level, coarse)
+    tb = W.build_tables(a, 0.7, h, 0.2)
+    wk = W.Walker(a, 0.7, v, seed=21, tables=tb)
+    reps = 200_000
+    s, s2, _, _ = wk.mlmcl(level, coarse, 0, reps)
+    rows = m2 - m1 * m1 > 0
+    # standard error from the proposal's own sample (its variance differs)
+    per_row_var = np.maximum(s2 / reps / a.n, 1e-30)
+    z = (s[rows] / reps - m1[rows]) / np.sqrt(np.maximum(m2[rows], per_row_var) / reps)
+    assert np.abs(z).max() <= 4.0
+
+
+def test_value_function_proposal_reduces_variance():
+    # With h = x the jump choice follows the value of the next state (the
+    # zero-variance importance-sampling idea); on a scale-free graph with
+    # beta = 1/lambda_max the per-walk variance drops.
+    a = I.ba_graph(500, 4, seed=3)
+    t = 1.0 / I.lambda_max(a)
+    v = np.ones(a.n)
+    x = R.expmv(a.scipy(), t, v)
+    m1, _ = R.level_moments(a.dense(), t, v, 3, False)
+
+    def rel_var(tables):
+        wk = W.Walker(a, t, v, seed=5, tables=tables)
+        s, s2, _, _ = wk.mlmcl(3, False, 0, 4000)
+        return (s2 - (s * s).sum() / 4000) / 3999 / (m1 ** 2).sum()
+
+    plain = rel_var(W.build_tables(a, t))
+    learned = rel_var(W.build_tables(a, t, x.astype(np.float32), 0.1))
+    assert learned < 0.8 * plain
