@@ -59,7 +59,8 @@ enum { MLMC_PLAIN = 0, MLMC_LEARNED = 1 };     /* jump proposal */
  *   pilot_walks       walks per row per level in the pilot run
  *   precision         MLMC_FP64 or MLMC_FP32_KAHAN
  *   mode              MLMC_BACKWARD (Algorithm 2 from every row)
- *   proposal          MLMC_PLAIN
+ *   proposal          MLMC_PLAIN at creation (mlmc_plan_set_proposal switches
+ *                     the plan to MLMC_LEARNED)
  *   max_jumps_per_walk  a walk that would exceed it stops, contributes 0 and
  *                     makes the call return MLMC_ERR_WALK_LIMIT
  *   max_walks_per_row sample budget per level (per row)
@@ -152,6 +153,26 @@ mlmc_status mlmc_plan_create(mlmc_plan **out, int64_t n, int64_t nnz, const int6
  * copy of A (the same kernels as at creation).  Asynchronous on the plan's
  * stream. */
 mlmc_status mlmc_plan_rebuild(mlmc_plan *plan);
+
+/* Importance-sampling proposal for the jumps (the learned part; the paper
+ * has no counterpart beyond its jump law, Eq. 12).  With h (n positive
+ * finite floats, host or device, e.g. an estimate of x) every row's jump
+ * law becomes the defensive mixture
+ *   q_ij = (1 - alpha) |a_ij| h_j / sum_k |a_ik| h_k + alpha |a_ij| / L_ii,
+ * sampled by alias tables built on the device, and every jump adds
+ * log(k_ij / q_ij) to the walk's exponent, so every estimate stays unbiased
+ * for any h > 0.  alpha in (0, 1].  Later walks of the plan (mlmc_expmv,
+ * mlmc_mlmcl, mlmc_trace, mlmc_trace_noalloc) use the proposal; h = NULL
+ * returns to the plain law.  The table build is asynchronous; h is read
+ * once (the call synchronises the plan's stream to validate it). */
+mlmc_status mlmc_plan_set_proposal(mlmc_plan *plan, const float *h, double alpha);
+
+/* The proposal tables, exported like mlmc_export_tables (positions
+ * row_ptr[i] + b for bucket b < deg_i), plus lr_keep / lr_alias = log(k/q)
+ * of the kept and alias columns.  Any pointer may be NULL.  Synchronises. */
+mlmc_status mlmc_export_proposal(const mlmc_plan *plan, uint32_t *thr, int32_t *keep_col,
+                                 uint8_t *keep_neg, int32_t *alias_col, uint8_t *alias_neg,
+                                 float *lr_keep, float *lr_alias);
 
 /* x = exp(t A) v by Algorithm 1: a pilot of pilot_walks per row on levels
  * l0..l0+num_levels-1, Giles' sample sizes M_l (Eq. 11, read as

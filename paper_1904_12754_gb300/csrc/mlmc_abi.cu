@@ -70,6 +70,8 @@ void free_plan(mlmc_plan* p) {
   cudaFree(p->d_meta64);
   cudaFree(p->d_lii);
   cudaFree(p->d_alias);
+  cudaFree(p->d_alias_is);
+  cudaFree(p->d_h);
   cudaFree(p->d_flags);
   cudaFree(p->d_work);
   cudaFree(p->d_totals);
@@ -252,7 +254,9 @@ mlmc_status mlmc_plan_create(mlmc_plan** out, int64_t n, int64_t nnz, const int6
   if (s.precision != MLMC_FP64 && s.precision != MLMC_FP32_KAHAN)
     return fail(MLMC_ERR_INVALID_ARG, "unknown precision");
   if (s.mode != MLMC_BACKWARD) return fail(MLMC_ERR_INVALID_ARG, "only MLMC_BACKWARD is available");
-  if (s.proposal != MLMC_PLAIN) return fail(MLMC_ERR_INVALID_ARG, "only MLMC_PLAIN is available");
+  if (s.proposal != MLMC_PLAIN)
+    return fail(MLMC_ERR_INVALID_ARG,
+                "create the plan with MLMC_PLAIN; a proposal is set by mlmc_plan_set_proposal");
   if (s.pilot_walks < 2 || s.max_jumps_per_walk < 0 || s.max_jumps_per_walk > 0xFFFFFFF0ll ||
       s.max_walks_per_row < s.pilot_walks || s.max_walks_per_row > (1ll << 55))
     return fail(MLMC_ERR_INVALID_ARG, "bad schedule budgets");
@@ -350,6 +354,63 @@ mlmc_status mlmc_plan_create(mlmc_plan** out, int64_t n, int64_t nnz, const int6
 mlmc_status mlmc_plan_rebuild(mlmc_plan* p) {
   if (!p) return fail(MLMC_ERR_INVALID_ARG, "NULL plan");
   MLMC_CUDA(launch_build_tables(p), "table build");
+  if (p->proposal_active) MLMC_CUDA(launch_build_is_tables(p), "proposal table build");
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_plan_set_proposal(mlmc_plan* p, const float* h, double alpha) {
+  if (!p) return fail(MLMC_ERR_INVALID_ARG, "NULL plan");
+  if (!h) {
+    p->proposal_active = false;
+    p->sched.proposal = MLMC_PLAIN;
+    return MLMC_OK;
+  }
+  if (!(alpha > 0.0) || !(alpha <= 1.0))
+    return fail(MLMC_ERR_INVALID_ARG, "alpha must be in (0, 1]: the proposal mixes in the plain law");
+  if (!p->d_alias_is) {
+    MLMC_CUDA(dev_alloc(&p->d_alias_is, static_cast<size_t>(p->nnz)), "alloc proposal tables");
+    MLMC_CUDA(dev_alloc(&p->d_h, static_cast<size_t>(p->n)), "alloc h");
+  }
+  MLMC_CUDA(cudaMemcpyAsync(p->d_h, h, sizeof(float) * p->n, cudaMemcpyDefault, p->stream), "copy h");
+  // h must be positive and finite on every row (checked on the host copy).
+  std::vector<float> hh(p->n);
+  MLMC_CUDA(cudaMemcpyAsync(hh.data(), p->d_h, sizeof(float) * p->n, cudaMemcpyDeviceToHost,
+                            p->stream), "read h");
+  MLMC_CUDA(cudaStreamSynchronize(p->stream), "synchronize");
+  for (int64_t i = 0; i < p->n; ++i)
+    if (!(hh[i] > 0.0f) || !std::isfinite(hh[i]))
+      return fail(MLMC_ERR_INVALID_ARG, "h must be positive and finite (row " + std::to_string(i) + ")");
+  p->alpha = alpha;
+  MLMC_CUDA(launch_build_is_tables(p), "proposal table build");
+  p->proposal_active = true;
+  p->sched.proposal = MLMC_LEARNED;
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_export_proposal(const mlmc_plan* pc, uint32_t* thr, int32_t* keep_col,
+                                 uint8_t* keep_neg, int32_t* alias_col, uint8_t* alias_neg,
+                                 float* lr_keep, float* lr_alias) {
+  mlmc_plan* p = const_cast<mlmc_plan*>(pc);
+  if (!p) return fail(MLMC_ERR_INVALID_ARG, "NULL plan");
+  if (!p->proposal_active) return fail(MLMC_ERR_INVALID_ARG, "no proposal set on this plan");
+  std::vector<Meta32> m32(p->n);
+  std::vector<AliasEntryIS> al(p->nnz > 0 ? p->nnz : 1);
+  MLMC_CUDA(cudaMemcpyAsync(m32.data(), p->d_meta32, sizeof(Meta32) * p->n, cudaMemcpyDeviceToHost, p->stream), "copy");
+  if (p->nnz > 0)
+    MLMC_CUDA(cudaMemcpyAsync(al.data(), p->d_alias_is, sizeof(AliasEntryIS) * p->nnz, cudaMemcpyDeviceToHost, p->stream), "copy");
+  MLMC_CUDA(cudaStreamSynchronize(p->stream), "synchronize");
+  for (int64_t i = 0; i < p->n; ++i)
+    for (int32_t b = 0; b < m32[i].deg; ++b) {
+      const int64_t q = m32[i].start + b;
+      const AliasEntryIS& e = al[q];
+      if (thr) thr[q] = e.thr;
+      if (keep_col) keep_col[q] = static_cast<int32_t>(e.keep & kColMask);
+      if (keep_neg) keep_neg[q] = static_cast<uint8_t>(e.keep >> 31);
+      if (alias_col) alias_col[q] = static_cast<int32_t>(e.alias & kColMask);
+      if (alias_neg) alias_neg[q] = static_cast<uint8_t>(e.alias >> 31);
+      if (lr_keep) lr_keep[q] = e.lr_keep;
+      if (lr_alias) lr_alias[q] = e.lr_alias;
+    }
   return MLMC_OK;
 }
 

@@ -258,7 +258,9 @@ double trial_ms(mlmc_plan* p, int per_lane, double* scratch, cudaEvent_t e0, cud
   w.level = p->l0;
   w.coarse = false;
   w.rep_begin = 0;
-  w.reps = std::max<int64_t>(64, (int64_t{1} << 24) / p->n);
+  // Enough walks per row that every candidate's item size is reachable
+  // (32 x 64 = 2048), but at most ~2^31 walks.
+  w.reps = std::max<int64_t>(64, std::min<int64_t>(2048, (int64_t{1} << 31) / p->n));
   w.seed = 0x5eedull;
   w.v = p->d_v;
   w.sum_y = scratch;

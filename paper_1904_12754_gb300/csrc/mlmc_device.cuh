@@ -43,6 +43,20 @@ struct __align__(16) AliasEntry {
   uint32_t pad;
 };
 
+// Alias entry of an importance-sampling proposal (32 bytes, one sector):
+// the plain entry plus log(k/q) of the kept and of the alias column, where
+// k is the paper's jump law and q the proposal.
+struct __align__(16) AliasEntryIS {
+  uint32_t thr;
+  uint32_t keep;
+  uint32_t alias;
+  uint32_t pad;
+  float lr_keep;
+  float lr_alias;
+  uint32_t pad1;
+  uint32_t pad2;
+};
+
 constexpr uint32_t kSignBit = 0x80000000u;
 constexpr uint32_t kColMask = 0x7FFFFFFFu;
 

@@ -110,6 +110,12 @@ struct mlmc_plan {
   double* d_lii = nullptr;
   mlmc::AliasEntry* d_alias = nullptr;
   double dmax_scaled = 0.0;  // max_i max(|t d_i|, t L_ii)
+  // Importance-sampling proposal (mlmc_plan_set_proposal): when active the
+  // walks use d_alias_is and carry log(k/q) in their exponent.
+  mlmc::AliasEntryIS* d_alias_is = nullptr;
+  float* d_h = nullptr;
+  double alpha = 0.0;
+  bool proposal_active = false;
 
   // Work buffers.
   uint32_t* d_flags = nullptr;                 // [4]
@@ -133,6 +139,7 @@ void set_error(const std::string& msg);
 // Table kernels (mlmc_tables.cu).
 cudaError_t launch_validate(mlmc_plan* p);
 cudaError_t launch_build_tables(mlmc_plan* p);
+cudaError_t launch_build_is_tables(mlmc_plan* p);
 
 // Walk kernels (mlmc_walk.cu).  Splits the replica range into launches of at
 // most about 2^31 walks; returns the number of launches in *launches.

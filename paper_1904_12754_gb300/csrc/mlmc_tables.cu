@@ -151,6 +151,106 @@ __global__ void k_build_tables(int64_t n, double t, const int64_t* __restrict__ 
   }
 }
 
+// Proposal tables: per row i with h > 0 on the columns,
+//   q_b = (1 - alpha) (|a_b| h(col_b)) / sum_c |a_c| h(col_c) + alpha |a_b| / L_ii
+// (a defensive mixture with the paper's law k_b = |a_b| / L_ii),
+// p_b = q_b deg, then the same Vose construction as k_build_tables; each
+// entry also stores lr = log(k/q) of its kept and alias columns.  During the
+// build an entry holds its working probability (bytes 0-7), its FIFO link
+// (bytes 8-11) and its own lr (bytes 16-19, which is also its final lr_keep).
+__global__ void k_build_is_tables(int64_t n, const int64_t* __restrict__ row_ptr,
+                                  const int32_t* __restrict__ col, const double* __restrict__ val,
+                                  const double* __restrict__ lii, const float* __restrict__ h,
+                                  double alpha, AliasEntryIS* __restrict__ alias) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t rb = row_ptr[i];
+    const int64_t re = row_ptr[i + 1];
+    int64_t dpos = -1;
+    double hsum = 0.0;
+    for (int64_t q = rb; q < re; ++q) {
+      if (col[q] == i) {
+        dpos = q - rb;
+      } else {
+        hsum = __dadd_rn(hsum, __dmul_rn(fabs(val[q]), static_cast<double>(h[col[q]])));
+      }
+    }
+    const int32_t k = static_cast<int32_t>((re - rb) - (dpos >= 0 ? 1 : 0));
+    if (k == 0) continue;
+    const double L = lii[i];
+    AliasEntryIS* row = alias + rb;
+    auto csr_of = [&](int32_t b) -> int64_t { return rb + b + ((dpos >= 0 && b >= dpos) ? 1 : 0); };
+    auto col_word = [&](int32_t b) -> uint32_t {
+      const int64_t q = csr_of(b);
+      return static_cast<uint32_t>(col[q]) | (val[q] < 0.0 ? kSignBit : 0u);
+    };
+    auto p_of = [&](int32_t b) -> double& { return *reinterpret_cast<double*>(&row[b]); };
+    auto next_of = [&](int32_t b) -> int32_t& { return *reinterpret_cast<int32_t*>(&row[b].alias); };
+    auto finalise = [&](int32_t b, double prob, int32_t alias_b) {
+      const double scaled = floor(__dmul_rn(prob, 4294967296.0));
+      const float lr_alias = row[alias_b].lr_keep;  // alias_b's own lr
+      row[b].thr = scaled >= 4294967295.0 ? 0xFFFFFFFFu : static_cast<uint32_t>(scaled);
+      row[b].keep = col_word(b);
+      row[b].alias = col_word(alias_b);
+      row[b].pad = 0u;
+      row[b].lr_alias = lr_alias;
+      row[b].pad1 = 0u;
+      row[b].pad2 = 0u;
+    };
+    const double kd = static_cast<double>(k);
+    const double keep_mix = __dsub_rn(1.0, alpha);
+    int32_t s_head = -1, s_tail = -1, g_head = -1, g_tail = -1;
+    auto push = [&](int32_t& head, int32_t& tail, int32_t b) {
+      next_of(b) = -1;
+      if (tail < 0) head = b; else next_of(tail) = b;
+      tail = b;
+    };
+    auto pop = [&](int32_t& head, int32_t& tail) -> int32_t {
+      const int32_t b = head;
+      head = next_of(b);
+      if (head < 0) tail = -1;
+      return b;
+    };
+    for (int32_t b = 0; b < k; ++b) {
+      const int64_t q = csr_of(b);
+      const double w = fabs(val[q]);
+      double p = 1.0, lr = 0.0;
+      if (L > 0.0) {
+        if (hsum > 0.0) {
+          const double kb = __ddiv_rn(w, L);
+          const double qb = __dadd_rn(
+              __dmul_rn(keep_mix, __ddiv_rn(__dmul_rn(w, static_cast<double>(h[col[q]])), hsum)),
+              __dmul_rn(alpha, kb));
+          p = __dmul_rn(qb, kd);
+          lr = qb > 0.0 ? log(kb / qb) : 0.0;
+        } else {
+          p = __ddiv_rn(__dmul_rn(w, kd), L);
+        }
+      }
+      p_of(b) = p;
+      row[b].lr_keep = static_cast<float>(lr);
+      if (p < 1.0) push(s_head, s_tail, b); else push(g_head, g_tail, b);
+    }
+    while (s_head >= 0 && g_head >= 0) {
+      const int32_t l = pop(s_head, s_tail);
+      const int32_t g = pop(g_head, g_tail);
+      const double pl = p_of(l);
+      const double pg = __dsub_rn(__dadd_rn(p_of(g), pl), 1.0);
+      finalise(l, pl, g);
+      p_of(g) = pg;
+      if (pg < 1.0) push(s_head, s_tail, g); else push(g_head, g_tail, g);
+    }
+    while (g_head >= 0) {
+      const int32_t g = pop(g_head, g_tail);
+      finalise(g, 1.0, g);
+    }
+    while (s_head >= 0) {
+      const int32_t l = pop(s_head, s_tail);
+      finalise(l, 1.0, l);
+    }
+  }
+}
+
 int grid_for(const mlmc_plan* p, int64_t items, int block) {
   const int64_t want = (items + block - 1) / block;
   const int64_t cap = static_cast<int64_t>(p->num_sms) * 16;
@@ -174,6 +274,14 @@ cudaError_t launch_build_tables(mlmc_plan* p) {
   k_build_tables<<<grid_for(p, p->n, kBuildBlock), kBuildBlock, 0, p->stream>>>(
       p->n, p->t, p->d_row_ptr, p->d_col, p->d_val, p->d_meta32, p->d_meta64, p->d_lii,
       p->d_alias, reinterpret_cast<unsigned long long*>(p->d_norm2));
+  p->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_is_tables(mlmc_plan* p) {
+  constexpr int kBuildBlock = 64;
+  k_build_is_tables<<<grid_for(p, p->n, kBuildBlock), kBuildBlock, 0, p->stream>>>(
+      p->n, p->d_row_ptr, p->d_col, p->d_val, p->d_lii, p->d_h, p->alpha, p->d_alias_is);
   p->launches++;
   return cudaGetLastError();
 }

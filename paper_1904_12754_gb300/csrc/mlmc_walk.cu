@@ -41,7 +41,7 @@ constexpr unsigned kFull = 0xFFFFFFFFu;
 
 struct WalkArgs {
   const void* meta;
-  const AliasEntry* alias;
+  const void* alias;       // AliasEntry, or AliasEntryIS with a proposal
   const void* v_walk;      // right-hand side in the walk precision
   int64_t n;
   int64_t rep_begin;
@@ -192,7 +192,7 @@ __device__ __forceinline__ Meta32 load_meta<Meta32>(const Meta32* m, int64_t j) 
 // problem).
 struct ItemArgs {
   const void* meta;
-  const AliasEntry* alias;
+  const void* alias;      // AliasEntry, or AliasEntryIS with a proposal
   const void* v_walk;
   int level;
   uint32_t ctr3;
@@ -242,7 +242,7 @@ __device__ __forceinline__ void flush_totals(WalkTotals<T>& t, double* totals, u
 // One work item: walks r_lo .. r_hi-1 (replica offsets relative to
 // a.rep_begin) of row `row`, run by the whole warp as a pool.  Adds the
 // item's sum of Y to a.sum_y[row] (one atomic) and its totals to `tot`.
-template <bool FP64, bool COARSE, bool TRACE>
+template <bool FP64, bool COARSE, bool TRACE, bool IS>
 __device__ __forceinline__ void walk_item(const ItemArgs& a, int64_t row, int64_t r_lo,
                                           int64_t r_hi, WalkTotals<typename Prec<FP64>::T>& tot,
                                           int lane) {
@@ -293,6 +293,7 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, int64_t row, int64_
   T acc = 0;               // coarse: acc_c; coarsest: acc_f
   T acc_d = 0;             // coarse only
   int kprev = -1;          // grid index of the segment start (fine)
+  T lw = 0;                // proposal only: sum of log(k/q) over the jumps
   uint32_t hash = 2166136261u;
 
   while (__any_sync(kFull, live)) {
@@ -320,8 +321,20 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, int64_t row, int64_
         }
         kprev = g;
         const uint32_t bucket = __umulhi(x.z, static_cast<uint32_t>(m.deg));
-        const uint4 ent = __ldg(reinterpret_cast<const uint4*>(a.alias + m.start) + bucket);
-        const uint32_t pick = (x.w < ent.x) ? ent.y : ent.z;
+        uint32_t pick;
+        if (IS) {
+          const uint4* ep = reinterpret_cast<const uint4*>(
+              static_cast<const AliasEntryIS*>(a.alias) + m.start + bucket);
+          const uint4 e0 = __ldg(ep);
+          const uint2 e1 = __ldg(reinterpret_cast<const uint2*>(ep + 1));
+          const bool keep = x.w < e0.x;
+          pick = keep ? e0.y : e0.z;
+          lw = P::add(lw, static_cast<T>(__uint_as_float(keep ? e1.x : e1.y)));
+        } else {
+          const uint4 ent = __ldg(reinterpret_cast<const uint4*>(
+                                      static_cast<const AliasEntry*>(a.alias) + m.start) + bucket);
+          pick = (x.w < ent.x) ? ent.y : ent.z;
+        }
         neg ^= pick >> 31;
         j = static_cast<int32_t>(pick & kColMask);
         if (TRACE) hash = (hash ^ static_cast<uint32_t>(j)) * 16777619u;
@@ -348,11 +361,11 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, int64_t row, int64_
               const T accd = P::fma(P::from_int(-(kprev & 1)), dle, acc_d);
               const T ec = P::mul(P::sub(acc_c, h), P::mul(inv_n, static_cast<T>(2)));
               const T diff = P::mul(P::add(accd, h), inv_n);
-              y = P::mul(vend, P::mul(P::ex(ec), P::exm1(diff)));
+              y = P::mul(vend, P::mul(P::ex(IS ? P::add(ec, lw) : ec), P::exm1(diff)));
             } else {
               const T acc_f = P::fma(P::from_int(n_grid - kprev), dle, acc);
               const T ef = P::mul(P::sub(acc_f, h), inv_n);
-              y = P::mul(vend, P::ex(ef));
+              y = P::mul(vend, P::ex(IS ? P::add(ef, lw) : ef));
             }
             if (neg) y = -y;
             if (!isfinite(y)) {
@@ -411,7 +424,7 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, int64_t row, int64_
   if (lane == 0 && ys != 0.0) atomicAdd(a.sum_y + row, ys);
 }
 
-template <bool FP64, bool COARSE, bool TRACE>
+template <bool FP64, bool COARSE, bool TRACE, bool IS>
 __global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk(WalkArgs a) {
   using T = typename Prec<FP64>::T;
   const int lane = threadIdx.x & 31;
@@ -439,7 +452,7 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk(WalkArgs a) {
     const int64_t chunk = static_cast<int64_t>(item) - row * a.chunks_per_row;
     const int64_t r_lo = chunk * a.chunk;
     const int64_t r_hi = min(r_lo + a.chunk, a.reps);
-    walk_item<FP64, COARSE, TRACE>(ia, row, r_lo, r_hi, tot, lane);
+    walk_item<FP64, COARSE, TRACE, IS>(ia, row, r_lo, r_hi, tot, lane);
   }
   flush_totals(tot, a.totals, a.flags, lane);
 }
@@ -459,18 +472,40 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4)
   const unsigned long long total = hdr->total_items;
   const int nseg = hdr->segments;
   WalkTotals<T> tot;
+  // The warp's current segment; its totals are flushed when the warp's next
+  // item falls in another segment (items come in segment order, so a warp
+  // usually stays in one segment for many items).
+  int cur = -1;
+  unsigned long long seg_lo = 0, seg_hi = 0;
+  BatchSegmentDev sg{};
+  BatchProblemDev pb{};
+  // A warp claims kGrab consecutive items per atomic, so that it crosses a
+  // segment boundary (search + flush) at most about once per claim.
+  constexpr unsigned kGrab = 8;
+  unsigned long long base = 0;
+  unsigned left = 0;
   for (;;) {
-    unsigned long long item = 0;
-    if (lane == 0) item = atomicAdd(work, 1ull);
-    item = __shfl_sync(kFull, item, 0);
-    if (item >= total) break;
-    int lo = 0, hi = nseg - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (segs[mid].item_begin <= item) lo = mid; else hi = mid - 1;
+    if (left == 0) {
+      if (lane == 0) base = atomicAdd(work, static_cast<unsigned long long>(kGrab));
+      base = __shfl_sync(kFull, base, 0);
+      left = kGrab;
     }
-    const BatchSegmentDev sg = segs[lo];
-    const BatchProblemDev pb = probs[sg.problem];
+    const unsigned long long item = base + (kGrab - left);
+    --left;
+    if (item >= total) break;
+    if (item < seg_lo || item >= seg_hi) {
+      if (cur >= 0) flush_totals(tot, pb.totals + static_cast<int64_t>(sg.slot) * kTotSlots, flags, lane);
+      int lo = 0, hi = nseg - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (segs[mid].item_begin <= item) lo = mid; else hi = mid - 1;
+      }
+      cur = lo;
+      sg = segs[lo];
+      pb = probs[sg.problem];
+      seg_lo = sg.item_begin;
+      seg_hi = seg_lo + static_cast<unsigned long long>(pb.n) * static_cast<unsigned long long>(sg.chunks_per_row);
+    }
     const unsigned long long local = item - sg.item_begin;
     const int64_t row = static_cast<int64_t>(local / static_cast<unsigned long long>(sg.chunks_per_row));
     const int64_t chunk = static_cast<int64_t>(local) - row * sg.chunks_per_row;
@@ -491,10 +526,10 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4)
     ia.trace = nullptr;
     ia.trace_stride = 0;
     ia.trace_base = 0;
-    if (sg.slot > 0) walk_item<FP64, true, false>(ia, row, r_lo, r_hi, tot, lane);
-    else walk_item<FP64, false, false>(ia, row, r_lo, r_hi, tot, lane);
-    flush_totals(tot, pb.totals + static_cast<int64_t>(sg.slot) * kTotSlots, flags, lane);
+    if (sg.slot > 0) walk_item<FP64, true, false, false>(ia, row, r_lo, r_hi, tot, lane);
+    else walk_item<FP64, false, false, false>(ia, row, r_lo, r_hi, tot, lane);
   }
+  if (cur >= 0) flush_totals(tot, pb.totals + static_cast<int64_t>(sg.slot) * kTotSlots, flags, lane);
 }
 
 __global__ void k_to_float(int64_t n, const double* __restrict__ in, float* __restrict__ out) {
@@ -511,9 +546,9 @@ cudaError_t launch_to_float(mlmc_plan* p, const double* in, float* out) {
   return cudaGetLastError();
 }
 
-template <bool FP64, bool COARSE, bool TRACE>
+template <bool FP64, bool COARSE, bool TRACE, bool IS>
 cudaError_t launch_one(mlmc_plan* p, const WalkArgs& args, int block) {
-  auto kern = k_walk<FP64, COARSE, TRACE>;
+  auto kern = k_walk<FP64, COARSE, TRACE, IS>;
   int per_sm = 0;
   cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, 0);
   if (err != cudaSuccess) return err;
@@ -528,6 +563,22 @@ cudaError_t launch_one(mlmc_plan* p, const WalkArgs& args, int block) {
   return cudaGetLastError();
 }
 
+template <bool FP64, bool COARSE, bool TRACE>
+cudaError_t dispatch_is(mlmc_plan* p, const WalkArgs& a, int block, bool is) {
+  return is ? launch_one<FP64, COARSE, TRACE, true>(p, a, block)
+            : launch_one<FP64, COARSE, TRACE, false>(p, a, block);
+}
+
+cudaError_t dispatch_walk(mlmc_plan* p, const WalkArgs& a, int block, bool fp64, bool coarse,
+                          bool trace, bool is) {
+  if (fp64) {
+    if (coarse) return trace ? dispatch_is<true, true, true>(p, a, block, is) : dispatch_is<true, true, false>(p, a, block, is);
+    return trace ? dispatch_is<true, false, true>(p, a, block, is) : dispatch_is<true, false, false>(p, a, block, is);
+  }
+  if (coarse) return trace ? dispatch_is<false, true, true>(p, a, block, is) : dispatch_is<false, true, false>(p, a, block, is);
+  return trace ? dispatch_is<false, false, true>(p, a, block, is) : dispatch_is<false, false, false>(p, a, block, is);
+}
+
 }  // namespace
 
 cudaError_t launch_walk(mlmc_plan* p, const WalkLaunch& w, int64_t* launches) {
@@ -536,7 +587,8 @@ cudaError_t launch_walk(mlmc_plan* p, const WalkLaunch& w, int64_t* launches) {
   const bool fp64 = p->sched.precision == MLMC_FP64;
   WalkArgs a{};
   a.meta = fp64 ? static_cast<const void*>(p->d_meta64) : static_cast<const void*>(p->d_meta32);
-  a.alias = p->d_alias;
+  a.alias = p->proposal_active ? static_cast<const void*>(p->d_alias_is)
+                               : static_cast<const void*>(p->d_alias);
   if (fp64) {
     a.v_walk = w.v;
   } else {
@@ -578,13 +630,7 @@ cudaError_t launch_walk(mlmc_plan* p, const WalkLaunch& w, int64_t* launches) {
     a.total_items = static_cast<unsigned long long>(p->n) * static_cast<unsigned long long>(a.chunks_per_row);
     cudaError_t err = cudaMemsetAsync(p->d_work, 0, sizeof(unsigned long long), p->stream);
     if (err != cudaSuccess) return err;
-    if (fp64) {
-      if (w.coarse) err = trace ? launch_one<true, true, true>(p, a, block) : launch_one<true, true, false>(p, a, block);
-      else err = trace ? launch_one<true, false, true>(p, a, block) : launch_one<true, false, false>(p, a, block);
-    } else {
-      if (w.coarse) err = trace ? launch_one<false, true, true>(p, a, block) : launch_one<false, true, false>(p, a, block);
-      else err = trace ? launch_one<false, false, true>(p, a, block) : launch_one<false, false, false>(p, a, block);
-    }
+    err = dispatch_walk(p, a, block, fp64, w.coarse, trace, p->proposal_active);
     if (err != cudaSuccess) return err;
     if (launches) ++*launches;
   }
@@ -601,7 +647,8 @@ cudaError_t launch_walk_scratch(mlmc_plan* p, const WalkLaunch& w, unsigned long
   const bool fp64 = p->sched.precision == MLMC_FP64;
   WalkArgs a{};
   a.meta = fp64 ? static_cast<const void*>(p->d_meta64) : static_cast<const void*>(p->d_meta32);
-  a.alias = p->d_alias;
+  a.alias = p->proposal_active ? static_cast<const void*>(p->d_alias_is)
+                               : static_cast<const void*>(p->d_alias);
   if (fp64) {
     a.v_walk = w.v;
   } else {
@@ -639,13 +686,7 @@ cudaError_t launch_walk_scratch(mlmc_plan* p, const WalkLaunch& w, unsigned long
     a.total_items = static_cast<unsigned long long>(p->n) * static_cast<unsigned long long>(a.chunks_per_row);
     cudaError_t err = cudaMemsetAsync(work, 0, sizeof(unsigned long long), p->stream);
     if (err != cudaSuccess) return err;
-    if (fp64) {
-      if (w.coarse) err = trace ? launch_one<true, true, true>(p, a, block) : launch_one<true, true, false>(p, a, block);
-      else err = trace ? launch_one<true, false, true>(p, a, block) : launch_one<true, false, false>(p, a, block);
-    } else {
-      if (w.coarse) err = trace ? launch_one<false, true, true>(p, a, block) : launch_one<false, true, false>(p, a, block);
-      else err = trace ? launch_one<false, false, true>(p, a, block) : launch_one<false, false, false>(p, a, block);
-    }
+    err = dispatch_walk(p, a, block, fp64, w.coarse, trace, p->proposal_active);
     if (err != cudaSuccess) return err;
     if (launches) ++*launches;
   }

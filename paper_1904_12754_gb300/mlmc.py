@@ -91,12 +91,15 @@ def load(build_if_missing: bool = False):
     lib.mlmc_batch_autotune.argtypes = [P, P, I32]
     lib.mlmc_batch_destroy.argtypes = [P]
     lib.mlmc_batch_destroy.restype = None
+    lib.mlmc_plan_set_proposal.argtypes = [P, P, D]
+    lib.mlmc_export_proposal.argtypes = [P] + [P] * 7
     lib.mlmc_launch_count.argtypes = [P]
     lib.mlmc_launch_count.restype = I64
     for name in ("mlmc_schedule_default", "mlmc_plan_create", "mlmc_plan_rebuild", "mlmc_expmv",
                  "mlmc_stats", "mlmc_mlmcl", "mlmc_trace", "mlmc_trace_noalloc",
                  "mlmc_export_tables", "mlmc_batch_create", "mlmc_batch_expmv",
                  "mlmc_batch_stats", "mlmc_batch_info", "mlmc_batch_autotune",
+                 "mlmc_plan_set_proposal", "mlmc_export_proposal",
                  "mlmc_plan_info"):
         getattr(lib, name).restype = ct.c_int
     _lib = lib
@@ -252,6 +255,24 @@ class Plan:
         keys = ["l_ii", "dl", "inv_rate", "inv_rate32", "dl32", "deg", "thr", "keep_col",
                 "keep_neg", "alias_col", "alias_neg"]
         _check(self._lib.mlmc_export_tables(self._h, *[_ptr(out[k]) for k in keys]))
+        return out
+
+    def set_proposal(self, h, alpha: float = 0.1):
+        """Importance-sampling jump proposal q ~ (1-alpha)|a_ij| h_j + alpha k_ij
+        (h: n positive float32 values, host or device; None = plain law)."""
+        if h is not None:
+            _need(h, 4 * self.n, "h")
+        _check(self._lib.mlmc_plan_set_proposal(self._h, _ptr(h) if h is not None else None,
+                                                float(alpha)))
+
+    def export_proposal(self) -> dict:
+        m = max(self.nnz, 1)
+        out = dict(thr=np.zeros(m, np.uint32), keep_col=np.full(m, -1, np.int32),
+                   keep_neg=np.zeros(m, np.uint8), alias_col=np.full(m, -1, np.int32),
+                   alias_neg=np.zeros(m, np.uint8), lr_keep=np.zeros(m, np.float32),
+                   lr_alias=np.zeros(m, np.float32))
+        keys = ["thr", "keep_col", "keep_neg", "alias_col", "alias_neg", "lr_keep", "lr_alias"]
+        _check(self._lib.mlmc_export_proposal(self._h, *[_ptr(out[k]) for k in keys]))
         return out
 
     def info(self) -> dict:
