@@ -278,6 +278,52 @@ mlmc_status mlmc_batch_autotune(const mlmc_batch *batch, int32_t *walks_per_lane
 
 void mlmc_batch_destroy(mlmc_batch *batch);
 
+/* ---------------------------------------------------------------------
+ * The learned proposal's network (not in the paper): a 16 -> 64 -> 64 -> 1
+ * MLP, BF16 weights and activations on the tensor cores (tcgen05, FP32
+ * accumulation in tensor memory), FP32 master weights, Adam.  Inputs are
+ * per-node features (n x 16 BF16, device), output z (n FP32, device); the
+ * proposal uses h = exp(z).
+ * --------------------------------------------------------------------- */
+typedef struct mlmc_mlp mlmc_mlp;
+
+/* Create an MLP with seeded initial weights; all work on cuda_stream. */
+mlmc_status mlmc_mlp_create(mlmc_mlp **out, uint64_t seed, void *cuda_stream);
+void mlmc_mlp_destroy(mlmc_mlp *mlp);
+
+/* Number of FP32 parameters (packed: W1[16][64] row = input, b1[64],
+ * W2[64][64] row = input, b2[64], w3[64], b3). */
+int32_t mlmc_mlp_param_count(void);
+
+/* Set (set != NULL) and/or read (get != NULL) the packed FP32 parameters
+ * (host or device pointers).  Synchronises. */
+mlmc_status mlmc_mlp_params(mlmc_mlp *mlp, const float *set, float *get);
+
+/* z = MLP(x) for n rows: x device bf16 [n][16], z device float [n]. */
+mlmc_status mlmc_mlp_forward(mlmc_mlp *mlp, const uint16_t *x, int64_t n, float *z);
+
+/* Loss mean_i (z_i - y_i)^2 over the n rows and its gradient with respect
+ * to the packed parameters (forward and backward kernels of the training
+ * step; loss and grad may be host or device pointers). */
+mlmc_status mlmc_mlp_loss_grad(mlmc_mlp *mlp, const uint16_t *x, const float *y, int64_t n,
+                               float *loss, float *grad);
+
+/* `steps` Adam steps (learning rate lr) on uniform minibatches of `batch`
+ * rows of (x, y); *final_loss (host, may be NULL) gets the last batch loss. */
+mlmc_status mlmc_mlp_train(mlmc_mlp *mlp, const uint16_t *x, const float *y, int64_t n,
+                           int32_t steps, int32_t batch, float lr, uint64_t seed,
+                           float *final_loss);
+
+/* Learn and install a proposal: `pilot_walks` walks per row at l0 under the
+ * plain law give per-row estimates x-hat; the MLP is trained on per-node
+ * features (degree, t L_ii, t d_i, v, k^m v for m = 1..4 with k the jump
+ * law, neighbour degree statistics) to predict log(|x-hat| + 1e-3
+ * max|x-hat|), and h = exp(MLP) is installed with
+ * mlmc_plan_set_proposal(plan, h, alpha).  v: host or device, n doubles. */
+mlmc_status mlmc_learn_proposal(mlmc_plan *plan, mlmc_mlp *mlp, const double *v, uint64_t seed,
+                                int64_t pilot_walks, int32_t steps, int32_t batch, float lr,
+                                double alpha, float *final_loss);
+
 /* Copy the device tables to host arrays (any pointer may be NULL):
  *   l_ii, dl (= t d_i), inv_rate (1/(t L_ii), +inf when L_ii = 0): n doubles
  *   inv_rate32, dl32: n floats (the FP32 copies the FP32 walk uses)

@@ -1,0 +1,801 @@
+// The learned proposal's network: a 16 -> 64 -> 64 -> 1 MLP with BF16
+// weights and FP32 accumulation, trained on the GPU.
+//
+//   H1 = relu(X W1 + b1)      tcgen05 (BF16 x BF16 -> FP32 in TMEM), K = 16
+//   H2 = relu(H1 W2 + b2)     tcgen05, K = 64
+//   z  = H2 w3 + b3           CUDA cores (one output)
+// Loss: mean (z - y)^2.  Backward:
+//   dz = 2 (z - y) / B; dw3 = sum dz H2; db3 = sum dz
+//   dA2 = dz w3 * [A2 > 0]
+//   dH1 = dA2 W2^T            tcgen05 (dA2 rounded to BF16), K = 64
+//   dA1 = dH1 * [A1 > 0]
+//   dW2 = H1^T dA2, dW1 = X^T dA1, db = column sums   CUDA cores, FP32
+// Adam updates FP32 master weights; BF16 copies feed the tensor cores.
+// Rounding points (for an independent re-computation): X, W1, W2 and H1 are
+// BF16 (round to nearest even); dA2 is rounded to BF16 for the dH1 GEMM;
+// everything else is FP32.
+//
+// tcgen05 tile kernel: one CTA of 128 threads computes a 128 x 64 output
+// tile.  Operands are staged in shared memory in the canonical no-swizzle
+// K-major layout (8-row x 16-byte core matrices; core matrices adjacent in K
+// are 128 bytes apart, 8-row groups K/8*128 bytes apart); thread 0 issues
+// K/16 tcgen05.mma into a TMEM accumulator and commits to an mbarrier;
+// every warp then reads its 32 TMEM lanes with tcgen05.ld.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_bf16.h>
+
+#include "mlmc_internal.h"
+
+namespace mlmc {
+namespace {
+
+constexpr int kIn = 16;
+constexpr int kHid = 64;
+// Packed FP32 parameter vector: W1 [16][64] (row = input), b1 [64],
+// W2 [64][64] (row = input), b2 [64], w3 [64], b3 [1].
+constexpr int kOffW1 = 0;
+constexpr int kOffB1 = kOffW1 + kIn * kHid;
+constexpr int kOffW2 = kOffB1 + kHid;
+constexpr int kOffB2 = kOffW2 + kHid * kHid;
+constexpr int kOffW3 = kOffB2 + kHid;
+constexpr int kOffB3 = kOffW3 + kHid;
+constexpr int kParams = kOffB3 + 1;
+
+constexpr int kTileM = 128;
+constexpr int kTmemCols = 128;          // accumulator needs 64; the rest is slack
+constexpr int kTileSmem = 64 * 1024;    // dynamic shared memory per tile CTA
+constexpr uint32_t kWaitLimit = 1u << 26;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Shared-memory matrix descriptor: start, leading (K) byte offset, stride
+// (M/N) byte offset, version 1, no swizzle.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return static_cast<uint64_t>((addr >> 4) & 0x3FFFu) |
+         (static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16) |
+         (static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major,
+// N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+constexpr uint32_t umma_idesc(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(n >> 3) << 17) |
+         (static_cast<uint32_t>(m >> 4) << 24);
+}
+
+// Byte offset of element (row, k) of a K-major operand with K columns in the
+// no-swizzle canonical layout.
+__device__ __forceinline__ uint32_t core_offset(int row, int k, int K) {
+  return static_cast<uint32_t>((row >> 3) * (K / 8) * 128 + (k >> 3) * 128 + (row & 7) * 16 +
+                               (k & 7) * 2);
+}
+
+// Out[m][n] = epilogue( sum_k A[m][k] B[n][k] ) for one 128-row tile.
+//   A: rows of K bf16 (row-major, lda = K); B: N=64 rows of K bf16 (the
+//   K-major form of the right operand).  Epilogue: + bias[n] if bias,
+//   relu if relu, stored as bf16 (out_bf16) and/or fp32 (out_f32); the
+//   pre-activation sign mask is kept in pre_f32 if given.
+template <int K>
+__global__ void __launch_bounds__(128)
+    k_mlp_tile(int64_t M, const __nv_bfloat16* __restrict__ A, const __nv_bfloat16* __restrict__ B,
+               const float* __restrict__ bias, bool relu, __nv_bfloat16* __restrict__ out_bf16,
+               float* __restrict__ out_f32, float* __restrict__ pre_f32, uint32_t* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* sA = smem;                       // 128 x K bf16
+  unsigned char* sB = smem + kTileM * K * 2;      // 64 x K bf16
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + kTileM * K * 2 + kHid * K * 2);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 1);
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+  const int64_t row0 = static_cast<int64_t>(blockIdx.x) * kTileM;
+
+  // Stage A (zero rows past M) and B, 16 bytes per copy.
+  constexpr int kChunks = K / 8;  // 16-byte chunks per row
+  for (int c = tid; c < kTileM * kChunks; c += 128) {
+    const int r = c / kChunks, kc = c % kChunks;
+    uint4 val = make_uint4(0, 0, 0, 0);
+    if (row0 + r < M) val = *reinterpret_cast<const uint4*>(A + (row0 + r) * K + kc * 8);
+    *reinterpret_cast<uint4*>(sA + core_offset(r, kc * 8, K)) = val;
+  }
+  for (int c = tid; c < kHid * kChunks; c += 128) {
+    const int r = c / kChunks, kc = c % kChunks;
+    *reinterpret_cast<uint4*>(sB + core_offset(r, kc * 8, K)) =
+        *reinterpret_cast<const uint4*>(B + r * K + kc * 8);
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (tid == 0) {
+    constexpr uint32_t idesc = umma_idesc(kTileM, kHid);
+    const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+    constexpr uint32_t lbo = 128, sbo = (K / 8) * 128;
+#pragma unroll
+    for (int ks = 0; ks < K / 16; ++ks) {
+      const uint64_t ad = umma_desc(a0 + ks * 256, lbo, sbo);
+      const uint64_t bd = umma_desc(b0 + ks * 256, lbo, sbo);
+      const uint32_t acc = ks > 0 ? 1u : 0u;
+      asm volatile(
+          "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+          " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+          "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(mbar))
+                 : "memory");
+  }
+  // Bounded wait for the MMAs (phase 0).
+  uint32_t done = 0;
+  for (uint32_t it = 0; it < kWaitLimit && !done; ++it) {
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(smem_u32(mbar)), "r"(0u)
+        : "memory");
+  }
+  // Every thread of the block must agree before the warp-collective loads.
+  done = __syncthreads_and(done);
+  if (!done && tid == 0) atomicOr(err, 1u);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+  if (done) {
+    // Warp w reads TMEM lanes 32w..32w+31 (its rows), 16 columns at a time.
+    const int r = warp * 32 + (tid & 31);
+    const int64_t grow = row0 + r;
+#pragma unroll
+    for (int cb = 0; cb < kHid / 16; ++cb) {
+      uint32_t v[16];
+      const uint32_t taddr = tmem + (static_cast<uint32_t>(warp * 32) << 16) + cb * 16;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+          "%14,%15}, [%16];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+            "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+            "=r"(v[14]), "=r"(v[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (grow < M) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int col = cb * 16 + j;
+          float a = __uint_as_float(v[j]);
+          if (bias) a += bias[col];
+          if (pre_f32) pre_f32[grow * kHid + col] = a;
+          const float o = relu ? fmaxf(a, 0.0f) : a;
+          if (out_bf16) out_bf16[grow * kHid + col] = __float2bfloat16_rn(o);
+          if (out_f32) out_f32[grow * kHid + col] = o;
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+}
+
+// z = H2 w3 + b3, and (training) dz, dA2 = dz w3 [A2 > 0] (FP32 and BF16),
+// the loss and dw3 / db3 partial sums.
+__global__ void k_mlp_head(int64_t M, const float* __restrict__ h2, const float* __restrict__ a2,
+                           const float* __restrict__ p, const float* __restrict__ y,
+                           float* __restrict__ z, float* __restrict__ da2,
+                           __nv_bfloat16* __restrict__ da2_bf16, float* __restrict__ grad,
+                           float* __restrict__ loss) {
+  const float* w3 = p + kOffW3;
+  const float b3 = p[kOffB3];
+  __shared__ float s_dw3[kHid];
+  __shared__ float s_db3, s_loss;
+  if (threadIdx.x < kHid) s_dw3[threadIdx.x] = 0.f;
+  if (threadIdx.x == 0) s_db3 = s_loss = 0.f;
+  __syncthreads();
+  const float inv_b = 1.0f / static_cast<float>(M);
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < M;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    float zi = b3;
+    for (int j = 0; j < kHid; ++j) zi += h2[i * kHid + j] * w3[j];
+    if (z) z[i] = zi;
+    if (y) {
+      const float r = zi - y[i];
+      const float dz = 2.0f * r * inv_b;
+      atomicAdd(&s_loss, r * r * inv_b);
+      atomicAdd(&s_db3, dz);
+      for (int j = 0; j < kHid; ++j) {
+        atomicAdd(&s_dw3[j], dz * h2[i * kHid + j]);
+        const float d = a2[i * kHid + j] > 0.f ? dz * w3[j] : 0.f;
+        da2[i * kHid + j] = d;
+        da2_bf16[i * kHid + j] = __float2bfloat16_rn(d);
+      }
+    }
+  }
+  __syncthreads();
+  if (y) {
+    if (threadIdx.x < kHid) atomicAdd(&grad[kOffW3 + threadIdx.x], s_dw3[threadIdx.x]);
+    if (threadIdx.x == 0) {
+      atomicAdd(&grad[kOffB3], s_db3);
+      atomicAdd(loss, s_loss);
+    }
+  }
+}
+
+// grad_W[k][j] += sum_i in[i][k] d[i][j] and grad_b[j] += sum_i d[i][j],
+// with in given as bf16 (X or H1) and d as fp32 (dA1 or dA2); d may be
+// masked by a pre-activation sign (dA1 = dH1 [A1 > 0]).
+template <int KIN>
+__global__ void k_mlp_wgrad(int64_t M, const __nv_bfloat16* __restrict__ in,
+                            const float* __restrict__ d, const float* __restrict__ mask_pre,
+                            float* __restrict__ gW, float* __restrict__ gb) {
+  __shared__ float s_in[32][KIN];
+  __shared__ float s_d[32][kHid];
+  // each thread owns KIN*64/256 weight entries
+  constexpr int kPer = KIN * kHid / 256;
+  float acc[kPer];
+  float accb = 0.f;
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) acc[q] = 0.f;
+  for (int64_t base = static_cast<int64_t>(blockIdx.x) * 32; base < M;
+       base += static_cast<int64_t>(gridDim.x) * 32) {
+    for (int e = threadIdx.x; e < 32 * KIN; e += 256) {
+      const int r = e / KIN, k = e % KIN;
+      s_in[r][k] = base + r < M ? __bfloat162float(in[(base + r) * KIN + k]) : 0.f;
+    }
+    for (int e = threadIdx.x; e < 32 * kHid; e += 256) {
+      const int r = e / kHid, j = e % kHid;
+      float dv = 0.f;
+      if (base + r < M) {
+        dv = d[(base + r) * kHid + j];
+        if (mask_pre && !(mask_pre[(base + r) * kHid + j] > 0.f)) dv = 0.f;
+      }
+      s_d[r][j] = dv;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int e = threadIdx.x * kPer + q;
+      const int k = e / kHid, j = e % kHid;
+      float s = 0.f;
+      for (int r = 0; r < 32; ++r) s += s_in[r][k] * s_d[r][j];
+      acc[q] += s;
+    }
+    if (threadIdx.x < kHid) {
+      float s = 0.f;
+      for (int r = 0; r < 32; ++r) s += s_d[r][threadIdx.x];
+      accb += s;
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    const int e = threadIdx.x * kPer + q;
+    atomicAdd(&gW[e], acc[q]);
+  }
+  if (threadIdx.x < kHid) atomicAdd(&gb[threadIdx.x], accb);
+}
+
+// BF16 operand copies of the weights: W1t [64][16] = W1^T, W2t [64][64] =
+// W2^T (forward: rows = outputs, K = inputs) and W2 [64][64] itself (the
+// dH1 GEMM: rows = layer-1 units, K = layer-2 units).
+__global__ void k_mlp_pack(const float* __restrict__ p, __nv_bfloat16* __restrict__ w1t,
+                           __nv_bfloat16* __restrict__ w2t, __nv_bfloat16* __restrict__ w2) {
+  for (int e = threadIdx.x; e < kIn * kHid; e += blockDim.x) {
+    const int k = e / kHid, j = e % kHid;
+    w1t[j * kIn + k] = __float2bfloat16_rn(p[kOffW1 + e]);
+  }
+  for (int e = threadIdx.x; e < kHid * kHid; e += blockDim.x) {
+    const int k = e / kHid, j = e % kHid;
+    w2t[j * kHid + k] = __float2bfloat16_rn(p[kOffW2 + e]);
+    w2[e] = __float2bfloat16_rn(p[kOffW2 + e]);
+  }
+}
+
+// Adam on the FP32 master parameters.
+__global__ void k_mlp_adam(float* __restrict__ p, const float* __restrict__ g,
+                           float* __restrict__ m1, float* __restrict__ m2, float lr, float b1,
+                           float b2, float eps, float c1, float c2) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < kParams; e += gridDim.x * blockDim.x) {
+    const float ge = g[e];
+    m1[e] = b1 * m1[e] + (1.f - b1) * ge;
+    m2[e] = b2 * m2[e] + (1.f - b2) * ge * ge;
+    p[e] -= lr * (m1[e] / c1) / (sqrtf(m2[e] / c2) + eps);
+  }
+}
+
+// out_i = sum_{j != i} (|a_ij| / L_ii) in_j: one step of the paper's jump
+// law k (Eq. 12); rows without jumps keep in_i.
+__global__ void k_jump_mean(int64_t n, const int64_t* __restrict__ row_ptr,
+                            const int32_t* __restrict__ col, const double* __restrict__ val,
+                            const double* __restrict__ lii, const float* __restrict__ in,
+                            float* __restrict__ out) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const double L = lii[i];
+    if (!(L > 0.0)) {
+      out[i] = in[i];
+      continue;
+    }
+    double acc = 0.0;
+    for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q)
+      if (col[q] != i) acc += fabs(val[q]) * static_cast<double>(in[col[q]]);
+    out[i] = static_cast<float>(acc / L);
+  }
+}
+
+__global__ void k_to_float32(int64_t n, const double* __restrict__ in, float* __restrict__ out) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    out[i] = static_cast<float>(in[i]);
+}
+
+// Per-node features of the proposal network (16, BF16).  The pilot
+// estimates are the targets, never inputs, so the network smooths their
+// noise.  With k = the jump law and p_m = k^m v (the mean of v after m
+// jumps): 1, log1p(deg), t L_ii, t d_i, v_i, p_1..p_4, neighbour mean and max
+// of log1p(deg), neighbour mean of t d, log(|v|+eps), log(|p_2|+eps),
+// log(|p_4|+eps); eps = 1e-6.
+__global__ void k_mlp_features(int64_t n, const int64_t* __restrict__ row_ptr,
+                               const int32_t* __restrict__ col, const Meta64* __restrict__ meta,
+                               const double* __restrict__ lii, double t, const float* __restrict__ v,
+                               const float* __restrict__ p1, const float* __restrict__ p2,
+                               const float* __restrict__ p3, const float* __restrict__ p4,
+                               __nv_bfloat16* __restrict__ x) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    float f[kIn];
+    const Meta64 m = meta[i];
+    f[0] = 1.f;
+    f[1] = log1pf(static_cast<float>(m.deg));
+    f[2] = static_cast<float>(t * lii[i]);
+    f[3] = static_cast<float>(m.dl);
+    f[4] = v[i];
+    f[5] = p1[i];
+    f[6] = p2[i];
+    f[7] = p3[i];
+    f[8] = p4[i];
+    float sd = 0.f, mx = 0.f, sdl = 0.f;
+    int c = 0;
+    for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q) {
+      const int64_t j = col[q];
+      if (j == i) continue;
+      const Meta64 mj = meta[j];
+      const float ld = log1pf(static_cast<float>(mj.deg));
+      sd += ld;
+      mx = fmaxf(mx, ld);
+      sdl += static_cast<float>(mj.dl);
+      ++c;
+    }
+    const float ic = c > 0 ? 1.f / static_cast<float>(c) : 0.f;
+    f[9] = sd * ic;
+    f[10] = mx;
+    f[11] = sdl * ic;
+    f[12] = logf(fabsf(v[i]) + 1e-6f);
+    f[13] = logf(fabsf(p2[i]) + 1e-6f);
+    f[14] = logf(fabsf(p4[i]) + 1e-6f);
+    f[15] = 0.f;
+#pragma unroll
+    for (int k = 0; k < kIn; ++k) x[i * kIn + k] = __float2bfloat16_rn(f[k]);
+  }
+}
+
+// log(|x| + eps) targets and, for the proposal, h = exp(z) clamped.
+__global__ void k_log_target(int64_t n, const double* __restrict__ xhat, float floor_abs,
+                             float* __restrict__ y) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    y[i] = logf(fabsf(static_cast<float>(xhat[i])) + floor_abs);
+}
+
+__global__ void k_exp_h(int64_t n, const float* __restrict__ z, float* __restrict__ h) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    h[i] = expf(fminf(fmaxf(z[i], -60.f), 60.f));
+}
+
+// Gather rows idx[0..B) of X (bf16, 16 wide) and y.
+__global__ void k_gather(int64_t B, const int64_t* __restrict__ idx, const __nv_bfloat16* __restrict__ x,
+                         const float* __restrict__ y, __nv_bfloat16* __restrict__ xb,
+                         float* __restrict__ yb) {
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < B * kIn;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = e / kIn, k = e % kIn;
+    xb[e] = x[idx[r] * kIn + k];
+    if (k == 0) yb[r] = y[idx[r]];
+  }
+}
+
+}  // namespace
+}  // namespace mlmc
+
+using namespace mlmc;
+
+struct mlmc_mlp {
+  cudaStream_t stream = nullptr;
+  int num_sms = 0;
+  float* d_p = nullptr;      // FP32 master parameters
+  float* d_g = nullptr;      // gradients
+  float* d_m1 = nullptr;     // Adam moments
+  float* d_m2 = nullptr;
+  float* d_loss = nullptr;
+  uint32_t* d_err = nullptr;
+  __nv_bfloat16* d_w1t = nullptr;
+  __nv_bfloat16* d_w2t = nullptr;
+  __nv_bfloat16* d_w2 = nullptr;
+  // activations for up to cap rows
+  int64_t cap = 0;
+  __nv_bfloat16* d_h1 = nullptr;
+  float* d_a1 = nullptr;
+  float* d_a2 = nullptr;
+  float* d_h2 = nullptr;
+  float* d_da2 = nullptr;
+  __nv_bfloat16* d_da2b = nullptr;
+  float* d_dh1 = nullptr;
+  int64_t adam_t = 0;
+  int64_t launches = 0;
+};
+
+namespace {
+
+mlmc_status mfail(mlmc_status st, const std::string& msg) {
+  set_error(msg);
+  return st;
+}
+
+#define MLP_CUDA(call, what)                                                                   \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess)                                                                     \
+      return mfail(e_ == cudaErrorMemoryAllocation ? MLMC_ERR_OOM : MLMC_ERR_CUDA,             \
+                   std::string("mlp ") + (what) + ": " + cudaGetErrorString(e_));              \
+  } while (0)
+
+mlmc_status ensure_cap(mlmc_mlp* m, int64_t rows) {
+  if (rows <= m->cap) return MLMC_OK;
+  cudaFree(m->d_h1);
+  cudaFree(m->d_a1);
+  cudaFree(m->d_a2);
+  cudaFree(m->d_h2);
+  cudaFree(m->d_da2);
+  cudaFree(m->d_da2b);
+  cudaFree(m->d_dh1);
+  const size_t r = static_cast<size_t>(rows) * kHid;
+  MLP_CUDA(cudaMalloc(&m->d_h1, r * 2), "alloc");
+  MLP_CUDA(cudaMalloc(&m->d_a1, r * 4), "alloc");
+  MLP_CUDA(cudaMalloc(&m->d_a2, r * 4), "alloc");
+  MLP_CUDA(cudaMalloc(&m->d_h2, r * 4), "alloc");
+  MLP_CUDA(cudaMalloc(&m->d_da2, r * 4), "alloc");
+  MLP_CUDA(cudaMalloc(&m->d_da2b, r * 2), "alloc");
+  MLP_CUDA(cudaMalloc(&m->d_dh1, r * 4), "alloc");
+  m->cap = rows;
+  return MLMC_OK;
+}
+
+template <int K>
+cudaError_t tile(mlmc_mlp* m, int64_t M, const __nv_bfloat16* A, const __nv_bfloat16* B,
+                 const float* bias, bool relu, __nv_bfloat16* ob, float* of, float* pre) {
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_tile<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kTileSmem);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  const unsigned grid = static_cast<unsigned>((M + kTileM - 1) / kTileM);
+  if (grid == 0) return cudaSuccess;
+  k_mlp_tile<K><<<grid, 128, kTileSmem, m->stream>>>(M, A, B, bias, relu, ob, of, pre, m->d_err);
+  m->launches++;
+  return cudaGetLastError();
+}
+
+// Forward of rows x[0..M) (bf16, 16 wide) into z (and the activations).
+mlmc_status forward(mlmc_mlp* m, const __nv_bfloat16* x, int64_t M, float* z, const float* y,
+                    bool train) {
+  mlmc_status st = ensure_cap(m, M);
+  if (st != MLMC_OK) return st;
+  MLP_CUDA((k_mlp_pack<<<1, 256, 0, m->stream>>>(m->d_p, m->d_w1t, m->d_w2t, m->d_w2),
+            cudaGetLastError()), "pack");
+  MLP_CUDA(tile<kIn>(m, M, x, m->d_w1t, m->d_p + kOffB1, true, m->d_h1, nullptr, m->d_a1),
+           "layer 1");
+  MLP_CUDA(tile<kHid>(m, M, m->d_h1, m->d_w2t, m->d_p + kOffB2, true, nullptr, m->d_h2, m->d_a2),
+           "layer 2");
+  const unsigned g = static_cast<unsigned>(std::min<int64_t>((M + 255) / 256, m->num_sms * 4));
+  if (train) MLP_CUDA(cudaMemsetAsync(m->d_loss, 0, sizeof(float), m->stream), "memset");
+  k_mlp_head<<<std::max(1u, g), 256, 0, m->stream>>>(M, m->d_h2, m->d_a2, m->d_p, train ? y : nullptr,
+                                                       z, m->d_da2, m->d_da2b, m->d_g, m->d_loss);
+  MLP_CUDA(cudaGetLastError(), "head");
+  m->launches += 2;
+  return MLMC_OK;
+}
+
+mlmc_status backward(mlmc_mlp* m, const __nv_bfloat16* x, int64_t M) {
+  // dH1 = dA2 W2^T on the tensor cores; then the weight gradients.
+  MLP_CUDA(tile<kHid>(m, M, m->d_da2b, m->d_w2, nullptr, false, nullptr, m->d_dh1, nullptr), "dH1");
+  const unsigned g = static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>((M + 31) / 32, m->num_sms * 4)));
+  k_mlp_wgrad<kHid><<<g, 256, 0, m->stream>>>(M, m->d_h1, m->d_da2, nullptr, m->d_g + kOffW2,
+                                               m->d_g + kOffB2);
+  MLP_CUDA(cudaGetLastError(), "dW2");
+  k_mlp_wgrad<kIn><<<g, 256, 0, m->stream>>>(M, x, m->d_dh1, m->d_a1, m->d_g + kOffW1,
+                                              m->d_g + kOffB1);
+  MLP_CUDA(cudaGetLastError(), "dW1");
+  m->launches += 2;
+  return MLMC_OK;
+}
+
+mlmc_status check_err(mlmc_mlp* m) {
+  uint32_t e = 0;
+  MLP_CUDA(cudaMemcpyAsync(&e, m->d_err, sizeof(e), cudaMemcpyDeviceToHost, m->stream), "read err");
+  MLP_CUDA(cudaStreamSynchronize(m->stream), "sync");
+  if (e) return mfail(MLMC_ERR_CUDA, "mlp: tensor-core completion wait timed out");
+  return MLMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mlmc_status mlmc_mlp_create(mlmc_mlp** out, uint64_t seed, void* cuda_stream) {
+  if (!out) return mfail(MLMC_ERR_INVALID_ARG, "NULL out");
+  mlmc_mlp* m = new mlmc_mlp();
+  m->stream = static_cast<cudaStream_t>(cuda_stream);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  auto bail = [&](cudaError_t e) {
+    mlmc_mlp_destroy(m);
+    return mfail(MLMC_ERR_CUDA, std::string("mlp create: ") + cudaGetErrorString(e));
+  };
+  cudaError_t e = cudaSuccess;
+  if ((e = cudaMalloc(&m->d_p, kParams * 4)) != cudaSuccess) return bail(e);
+  if ((e = cudaMalloc(&m->d_g, kParams * 4)) != cudaSuccess) return bail(e);
+  if ((e = cudaMalloc(&m->d_m1, kParams * 4)) != cudaSuccess) return bail(e);
+  if ((e = cudaMalloc(&m->d_m2, kParams * 4)) != cudaSuccess) return bail(e);
+  if ((e = cudaMalloc(&m->d_loss, 4)) != cudaSuccess) return bail(e);
+  if ((e = cudaMalloc(&m->d_err, 4)) != cudaSuccess) return bail(e);
+  if ((e = cudaMalloc(&m->d_w1t, kIn * kHid * 2)) != cudaSuccess) return bail(e);
+  if ((e = cudaMalloc(&m->d_w2t, kHid * kHid * 2)) != cudaSuccess) return bail(e);
+  if ((e = cudaMalloc(&m->d_w2, kHid * kHid * 2)) != cudaSuccess) return bail(e);
+  // He-style initialisation from a seeded host generator (splitmix64).
+  std::vector<float> p(kParams, 0.f);
+  uint64_t s = seed ^ 0x9E3779B97F4A7C15ull;
+  auto next = [&]() {
+    s += 0x9E3779B97F4A7C15ull;
+    uint64_t z = s;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (static_cast<double>(z >> 11) + 0.5) * 0x1p-53;
+  };
+  for (int e2 = 0; e2 < kIn * kHid; ++e2) p[kOffW1 + e2] = static_cast<float>((next() - 0.5) * 2.0 * std::sqrt(6.0 / kIn));
+  for (int e2 = 0; e2 < kHid * kHid; ++e2) p[kOffW2 + e2] = static_cast<float>((next() - 0.5) * 2.0 * std::sqrt(6.0 / kHid));
+  for (int e2 = 0; e2 < kHid; ++e2) p[kOffW3 + e2] = static_cast<float>((next() - 0.5) * 2.0 * std::sqrt(3.0 / kHid));
+  if ((e = cudaMemcpy(m->d_p, p.data(), kParams * 4, cudaMemcpyHostToDevice)) != cudaSuccess) return bail(e);
+  cudaMemset(m->d_m1, 0, kParams * 4);
+  cudaMemset(m->d_m2, 0, kParams * 4);
+  cudaMemset(m->d_err, 0, 4);
+  *out = m;
+  return MLMC_OK;
+}
+
+void mlmc_mlp_destroy(mlmc_mlp* m) {
+  if (!m) return;
+  cudaFree(m->d_p);
+  cudaFree(m->d_g);
+  cudaFree(m->d_m1);
+  cudaFree(m->d_m2);
+  cudaFree(m->d_loss);
+  cudaFree(m->d_err);
+  cudaFree(m->d_w1t);
+  cudaFree(m->d_w2t);
+  cudaFree(m->d_w2);
+  cudaFree(m->d_h1);
+  cudaFree(m->d_a1);
+  cudaFree(m->d_a2);
+  cudaFree(m->d_h2);
+  cudaFree(m->d_da2);
+  cudaFree(m->d_da2b);
+  cudaFree(m->d_dh1);
+  delete m;
+}
+
+int32_t mlmc_mlp_param_count(void) { return kParams; }
+
+mlmc_status mlmc_mlp_params(mlmc_mlp* m, const float* set, float* get) {
+  if (!m) return mfail(MLMC_ERR_INVALID_ARG, "NULL mlp");
+  if (set) MLP_CUDA(cudaMemcpyAsync(m->d_p, set, kParams * 4, cudaMemcpyDefault, m->stream), "set");
+  if (get) MLP_CUDA(cudaMemcpyAsync(get, m->d_p, kParams * 4, cudaMemcpyDefault, m->stream), "get");
+  MLP_CUDA(cudaStreamSynchronize(m->stream), "sync");
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_mlp_forward(mlmc_mlp* m, const uint16_t* x, int64_t n, float* z) {
+  if (!m || !x || !z || n < 1) return mfail(MLMC_ERR_INVALID_ARG, "mlmc_mlp_forward: bad argument");
+  mlmc_status st = forward(m, reinterpret_cast<const __nv_bfloat16*>(x), n, z, nullptr, false);
+  if (st != MLMC_OK) return st;
+  return check_err(m);
+}
+
+mlmc_status mlmc_mlp_loss_grad(mlmc_mlp* m, const uint16_t* x, const float* y, int64_t n,
+                               float* loss, float* grad) {
+  if (!m || !x || !y || n < 1) return mfail(MLMC_ERR_INVALID_ARG, "mlmc_mlp_loss_grad: bad argument");
+  MLP_CUDA(cudaMemsetAsync(m->d_g, 0, kParams * 4, m->stream), "memset");
+  float* zs = nullptr;
+  MLP_CUDA(cudaMallocAsync(&zs, sizeof(float) * n, m->stream), "alloc z");
+  mlmc_status st = forward(m, reinterpret_cast<const __nv_bfloat16*>(x), n, zs, y, true);
+  if (st == MLMC_OK) st = backward(m, reinterpret_cast<const __nv_bfloat16*>(x), n);
+  cudaFreeAsync(zs, m->stream);
+  if (st != MLMC_OK) return st;
+  if (loss) MLP_CUDA(cudaMemcpyAsync(loss, m->d_loss, 4, cudaMemcpyDefault, m->stream), "loss");
+  if (grad) MLP_CUDA(cudaMemcpyAsync(grad, m->d_g, kParams * 4, cudaMemcpyDefault, m->stream), "grad");
+  return check_err(m);
+}
+
+mlmc_status mlmc_mlp_train(mlmc_mlp* m, const uint16_t* x, const float* y, int64_t n, int32_t steps,
+                           int32_t batch, float lr, uint64_t seed, float* final_loss) {
+  if (!m || !x || !y || n < 1 || steps < 1 || batch < 1)
+    return mfail(MLMC_ERR_INVALID_ARG, "mlmc_mlp_train: bad argument");
+  const int64_t B = std::min<int64_t>(batch, n);
+  __nv_bfloat16* xb = nullptr;
+  float* yb = nullptr;
+  int64_t* idx = nullptr;
+  float* zs = nullptr;
+  MLP_CUDA(cudaMalloc(&xb, sizeof(__nv_bfloat16) * B * kIn), "alloc");
+  MLP_CUDA(cudaMalloc(&yb, sizeof(float) * B), "alloc");
+  MLP_CUDA(cudaMalloc(&idx, sizeof(int64_t) * B), "alloc");
+  MLP_CUDA(cudaMalloc(&zs, sizeof(float) * B), "alloc");
+  std::vector<int64_t> h_idx(B);
+  uint64_t s = seed * 0x9E3779B97F4A7C15ull + 1;
+  mlmc_status st = MLMC_OK;
+  for (int it = 0; it < steps && st == MLMC_OK; ++it) {
+    for (int64_t r = 0; r < B; ++r) {  // uniform minibatch rows (xorshift)
+      s ^= s << 13;
+      s ^= s >> 7;
+      s ^= s << 17;
+      h_idx[r] = static_cast<int64_t>(s % static_cast<uint64_t>(n));
+    }
+    if (cudaMemcpyAsync(idx, h_idx.data(), sizeof(int64_t) * B, cudaMemcpyHostToDevice, m->stream) != cudaSuccess) {
+      st = mfail(MLMC_ERR_CUDA, "mlp train: copy idx");
+      break;
+    }
+    k_gather<<<m->num_sms * 2, 256, 0, m->stream>>>(B, idx, reinterpret_cast<const __nv_bfloat16*>(x), y, xb, yb);
+    cudaMemsetAsync(m->d_g, 0, kParams * 4, m->stream);
+    st = forward(m, xb, B, zs, yb, true);
+    if (st == MLMC_OK) st = backward(m, xb, B);
+    if (st != MLMC_OK) break;
+    ++m->adam_t;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - std::pow(b1, static_cast<float>(m->adam_t));
+    const float c2 = 1.f - std::pow(b2, static_cast<float>(m->adam_t));
+    k_mlp_adam<<<(kParams + 255) / 256, 256, 0, m->stream>>>(m->d_p, m->d_g, m->d_m1, m->d_m2, lr,
+                                                              b1, b2, 1e-8f, c1, c2);
+    m->launches += 2;
+    if (cudaGetLastError() != cudaSuccess) st = mfail(MLMC_ERR_CUDA, "mlp train: launch");
+  }
+  cudaStreamSynchronize(m->stream);
+  if (st == MLMC_OK && final_loss) cudaMemcpy(final_loss, m->d_loss, 4, cudaMemcpyDeviceToHost);
+  cudaFree(xb);
+  cudaFree(yb);
+  cudaFree(idx);
+  cudaFree(zs);
+  if (st != MLMC_OK) return st;
+  return check_err(m);
+}
+
+// Learn a proposal for `plan`: a pilot of `pilot_walks` walks per row at
+// l0 gives per-row estimates x-hat (the method's own statistics); the MLP
+// is trained on features -> log|x-hat|; h = exp(z) becomes the plan's
+// importance-sampling proposal (mlmc_plan_set_proposal with alpha).
+mlmc_status mlmc_learn_proposal(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t seed,
+                                int64_t pilot_walks, int32_t steps, int32_t batch, float lr,
+                                double alpha, float* final_loss) {
+  if (!p || !m || !v || pilot_walks < 1) return mfail(MLMC_ERR_INVALID_ARG, "mlmc_learn_proposal: bad argument");
+  const bool was = p->proposal_active;
+  p->proposal_active = false;  // the pilot uses the paper's jump law
+  double* sums = nullptr;
+  double* dv = nullptr;
+  __nv_bfloat16* feat = nullptr;
+  float* y = nullptr;
+  float* z = nullptr;
+  float* h = nullptr;
+  float* pv = nullptr;  // v and k^m v, m = 1..4 (5 x n floats)
+  auto cleanup = [&]() {
+    cudaFree(pv);
+    cudaFree(sums);
+    cudaFree(dv);
+    cudaFree(feat);
+    cudaFree(y);
+    cudaFree(z);
+    cudaFree(h);
+  };
+#define LP_CUDA(call, what)                                                                    \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) {                                                                   \
+      cleanup();                                                                               \
+      p->proposal_active = was;                                                                \
+      return mfail(MLMC_ERR_CUDA, std::string("learn proposal ") + (what) + ": " +             \
+                                      cudaGetErrorString(e_));                                 \
+    }                                                                                          \
+  } while (0)
+  LP_CUDA(cudaMalloc(&sums, sizeof(double) * (p->n + kTotSlots)), "alloc");
+  LP_CUDA(cudaMalloc(&dv, sizeof(double) * p->n), "alloc");
+  LP_CUDA(cudaMalloc(&feat, sizeof(__nv_bfloat16) * p->n * kIn), "alloc");
+  LP_CUDA(cudaMalloc(&y, sizeof(float) * p->n), "alloc");
+  LP_CUDA(cudaMalloc(&z, sizeof(float) * p->n), "alloc");
+  LP_CUDA(cudaMalloc(&h, sizeof(float) * p->n), "alloc");
+  LP_CUDA(cudaMalloc(&pv, sizeof(float) * p->n * 5), "alloc");
+  LP_CUDA(cudaMemcpyAsync(dv, v, sizeof(double) * p->n, cudaMemcpyDefault, p->stream), "copy v");
+  LP_CUDA(cudaMemsetAsync(sums, 0, sizeof(double) * (p->n + kTotSlots), p->stream), "memset");
+  WalkLaunch w;
+  w.level = p->l0;
+  w.coarse = false;
+  w.rep_begin = 0;
+  w.reps = pilot_walks;
+  w.seed = seed;
+  w.v = dv;
+  w.sum_y = sums;
+  w.totals = sums + p->n;
+  LP_CUDA(launch_walk(p, w), "pilot walks");
+  // x-hat = sums / pilot, in place
+  const double scale = 1.0 / static_cast<double>(pilot_walks);
+  double xmax = 0.0;
+  {
+    std::vector<double> hsum(p->n);
+    LP_CUDA(cudaMemcpyAsync(hsum.data(), sums, sizeof(double) * p->n, cudaMemcpyDeviceToHost, p->stream), "read");
+    LP_CUDA(cudaStreamSynchronize(p->stream), "sync");
+    for (auto& q : hsum) {
+      q *= scale;
+      xmax = std::max(xmax, std::fabs(q));
+    }
+    LP_CUDA(cudaMemcpyAsync(sums, hsum.data(), sizeof(double) * p->n, cudaMemcpyHostToDevice, p->stream), "write");
+  }
+  const unsigned g = static_cast<unsigned>(std::min<int64_t>((p->n + 255) / 256, p->num_sms * 8));
+  k_to_float32<<<g, 256, 0, p->stream>>>(p->n, dv, pv);
+  for (int mstep = 1; mstep <= 4; ++mstep)
+    k_jump_mean<<<g, 256, 0, p->stream>>>(p->n, p->d_row_ptr, p->d_col, p->d_val, p->d_lii,
+                                           pv + (mstep - 1) * p->n, pv + mstep * p->n);
+  k_mlp_features<<<g, 256, 0, p->stream>>>(p->n, p->d_row_ptr, p->d_col, p->d_meta64, p->d_lii, p->t,
+                                            pv, pv + p->n, pv + 2 * p->n, pv + 3 * p->n,
+                                            pv + 4 * p->n, feat);
+  LP_CUDA(cudaGetLastError(), "features");
+  // Targets log(|x-hat| + 1e-3 max|x-hat|): rows the pilot never reached do
+  // not get arbitrarily small h.
+  k_log_target<<<g, 256, 0, p->stream>>>(p->n, sums, static_cast<float>(1e-3 * xmax + 1e-30), y);
+  LP_CUDA(cudaGetLastError(), "targets");
+  LP_CUDA(cudaStreamSynchronize(p->stream), "sync");
+  m->stream = p->stream;
+  mlmc_status st = mlmc_mlp_train(m, reinterpret_cast<const uint16_t*>(feat), y, p->n, steps, batch,
+                                  lr, seed ^ 0xABCDEFull, final_loss);
+  if (st == MLMC_OK) st = forward(m, feat, p->n, z, nullptr, false);
+  if (st == MLMC_OK) st = check_err(m);
+  if (st != MLMC_OK) {
+    cleanup();
+    p->proposal_active = was;
+    return st;
+  }
+  k_exp_h<<<g, 256, 0, p->stream>>>(p->n, z, h);
+  LP_CUDA(cudaGetLastError(), "h");
+  st = mlmc_plan_set_proposal(p, h, alpha);
+  cleanup();
+  if (st != MLMC_OK) p->proposal_active = was;
+  return st;
+#undef LP_CUDA
+}
+
+}  // extern "C"

@@ -408,6 +408,7 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, int64_t row, int64_
       acc = 0;
       acc_d = 0;
       kprev = -1;
+      lw = 0;
       hash = 2166136261u;
     }
     next += static_cast<uint32_t>(__popc(fmask));

@@ -93,13 +93,24 @@ def load(build_if_missing: bool = False):
     lib.mlmc_batch_destroy.restype = None
     lib.mlmc_plan_set_proposal.argtypes = [P, P, D]
     lib.mlmc_export_proposal.argtypes = [P] + [P] * 7
+    lib.mlmc_mlp_create.argtypes = [ct.POINTER(P), ct.c_uint64, P]
+    lib.mlmc_mlp_destroy.argtypes = [P]
+    lib.mlmc_mlp_destroy.restype = None
+    lib.mlmc_mlp_param_count.restype = I32
+    lib.mlmc_mlp_params.argtypes = [P, P, P]
+    lib.mlmc_mlp_forward.argtypes = [P, P, I64, P]
+    lib.mlmc_mlp_loss_grad.argtypes = [P, P, P, I64, P, P]
+    lib.mlmc_mlp_train.argtypes = [P, P, P, I64, I32, I32, ct.c_float, ct.c_uint64, P]
+    lib.mlmc_learn_proposal.argtypes = [P, P, P, ct.c_uint64, I64, I32, I32, ct.c_float, D, P]
     lib.mlmc_launch_count.argtypes = [P]
     lib.mlmc_launch_count.restype = I64
     for name in ("mlmc_schedule_default", "mlmc_plan_create", "mlmc_plan_rebuild", "mlmc_expmv",
                  "mlmc_stats", "mlmc_mlmcl", "mlmc_trace", "mlmc_trace_noalloc",
                  "mlmc_export_tables", "mlmc_batch_create", "mlmc_batch_expmv",
                  "mlmc_batch_stats", "mlmc_batch_info", "mlmc_batch_autotune",
-                 "mlmc_plan_set_proposal", "mlmc_export_proposal",
+                 "mlmc_plan_set_proposal", "mlmc_export_proposal", "mlmc_mlp_create",
+                 "mlmc_mlp_params", "mlmc_mlp_forward", "mlmc_mlp_loss_grad", "mlmc_mlp_train",
+                 "mlmc_learn_proposal",
                  "mlmc_plan_info"):
         getattr(lib, name).restype = ct.c_int
     _lib = lib
@@ -260,6 +271,10 @@ class Plan:
     def set_proposal(self, h, alpha: float = 0.1):
         """Importance-sampling jump proposal q ~ (1-alpha)|a_ij| h_j + alpha k_ij
         (h: n positive float32 values, host or device; None = plain law)."""
+        if isinstance(h, np.ndarray):
+            h = np.ascontiguousarray(h, dtype=np.float32)
+        elif h is not None and hasattr(h, "dtype") and str(h.dtype) != "torch.float32":
+            raise TypeError("h must be float32")
         if h is not None:
             _need(h, 4 * self.n, "h")
         _check(self._lib.mlmc_plan_set_proposal(self._h, _ptr(h) if h is not None else None,
@@ -348,3 +363,73 @@ class Batch:
         out = (ct.c_int32 * 3)()
         _check(self._lib.mlmc_batch_autotune(self._h, out, 3))
         return list(out)
+
+
+class MLP:
+    """The learned proposal's network (mlmc_mlp_*): 16 -> 64 -> 64 -> 1,
+    BF16 tensor-core layers, FP32 master weights."""
+
+    def __init__(self, seed: int = 1, stream: int = 0):
+        lib = load()
+        self._lib = lib
+        self._h = ct.c_void_p()
+        _check(lib.mlmc_mlp_create(ct.byref(self._h), ct.c_uint64(seed), ct.c_void_p(stream)))
+        self.nparams = int(lib.mlmc_mlp_param_count())
+
+    def close(self):
+        if self._h:
+            self._lib.mlmc_mlp_destroy(self._h)
+            self._h = ct.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    def params(self, set_to=None) -> np.ndarray:
+        out = np.zeros(self.nparams, np.float32)
+        if set_to is not None:
+            _need(set_to, 4 * self.nparams, "params")
+        _check(self._lib.mlmc_mlp_params(self._h, _ptr(set_to) if set_to is not None else None,
+                                         _ptr(out)))
+        return out
+
+    def forward(self, x_bf16, n: int, z):
+        _need(x_bf16, 2 * 16 * n, "x")
+        _need(z, 4 * n, "z")
+        _check(self._lib.mlmc_mlp_forward(self._h, _ptr(x_bf16), n, _ptr(z)))
+
+    def loss_grad(self, x_bf16, y, n: int):
+        _need(x_bf16, 2 * 16 * n, "x")
+        _need(y, 4 * n, "y")
+        loss = np.zeros(1, np.float32)
+        grad = np.zeros(self.nparams, np.float32)
+        _check(self._lib.mlmc_mlp_loss_grad(self._h, _ptr(x_bf16), _ptr(y), n, _ptr(loss),
+                                            _ptr(grad)))
+        return float(loss[0]), grad
+
+    def train(self, x_bf16, y, n: int, steps: int, batch: int, lr: float, seed: int) -> float:
+        loss = np.zeros(1, np.float32)
+        _check(self._lib.mlmc_mlp_train(self._h, _ptr(x_bf16), _ptr(y), n, steps, batch,
+                                        ct.c_float(lr), ct.c_uint64(seed), _ptr(loss)))
+        return float(loss[0])
+
+    def learn_proposal(self, plan, v, seed: int, pilot_walks: int = 256, steps: int = 300,
+                       batch: int = 8192, lr: float = 3e-3, alpha: float = 0.1) -> float:
+        _need(v, 8 * plan.n, "v")
+        loss = np.zeros(1, np.float32)
+        _check(self._lib.mlmc_learn_proposal(plan.handle, self._h, _ptr(v), ct.c_uint64(seed),
+                                             pilot_walks, steps, batch, ct.c_float(lr),
+                                             float(alpha), _ptr(loss)))
+        return float(loss[0])
