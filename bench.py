@@ -327,6 +327,24 @@ def run_ours(args):
     peaks, peak_kind = _peaks()
     roof = walk_roofline(level_log, walk_s, clocks, peaks, total_ms)
 
+    # Learned proposal on the same workload and budget: per-walk variance at
+    # l0 and the error estimate one budget-bounded solve reaches.
+    var_plain, _ = _level0_variance(plan, dv, 256, 1234)
+    t0 = time.perf_counter()
+    with M.MLP(seed=3, stream=stream.cuda_stream) as net:
+        train_loss = net.learn_proposal(plan, dv, seed=99, pilot_walks=64, steps=300, batch=8192)
+    torch.cuda.synchronize()
+    t_learn = time.perf_counter() - t0
+    var_learned, _ = _level0_variance(plan, dv, 256, 1234)
+    sec_l, est_l, _, ev_l = _timed_solve(plan, dv, dx, seed0 + 777)
+    plan.set_proposal(None)
+    learned = {"level0_var_per_walk_plain": var_plain, "level0_var_per_walk_learned": var_learned,
+               "variance_ratio": var_learned / var_plain, "learn_seconds": t_learn,
+               "train_loss": train_loss, "step_seconds": sec_l, "est_rel_err": est_l,
+               "plain_est_rel_err_same_budget": float(np.mean(ests)),
+               "walk_steps_per_s": ev_l / sec_l}
+    log(f"learned proposal: variance ratio {var_learned / var_plain:.3f}, est err {est_l:.3g}")
+
     # Time to tolerance on the same graph with beta = 1/d_max (Sec. 5).
     t_dmax = 1.0 / w.extra["d_max"]
     sched_d = M.schedule_default(precision=M.FP32_KAHAN, num_levels=w.num_levels, max_levels=10,
@@ -392,6 +410,7 @@ def run_ours(args):
                 "beta_1_over_d_max_rel_err_vs_fp64": err_dmax,
                 "beta_1_over_d_max_walk_steps_per_s": float(np.sum(tt_events) / np.sum(tt)),
                 "d_max": w.extra["d_max"]},
+            "learned_vs_plain": learned,
             "est_rel_err": float(np.mean(ests)), "rel_err_vs_fp64": err,
             "table_build_ms": table_ms, "plan_create_s": t_plan,
             "walks_per_step": walks_total / args.steps, "jumps_per_step": jumps_total / args.steps,
@@ -538,6 +557,143 @@ def run_batch_workload(args):
         p.close()
 
 
+# ---------------------------------------------------------------------------
+# Secondary workloads: learned proposal, precision path
+# ---------------------------------------------------------------------------
+def _level0_variance(plan, v_dev, reps, seed):
+    import torch
+    n = plan.n
+    s = torch.zeros(n, dtype=torch.float64, device="cuda")
+    tot = torch.zeros(8, dtype=torch.float64, device="cuda")
+    plan.mlmcl(plan.info()["l0"], False, 1 << 40, reps, v_dev, seed, s, tot)
+    torch.cuda.synchronize()
+    sv = s.cpu().numpy()
+    y2 = float(tot[0])
+    return (y2 - float(sv @ sv) / reps) / (reps - 1), float(np.linalg.norm(sv / reps))
+
+
+def _timed_solve(plan, v_dev, x_dev, seed):
+    import torch
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    rc = plan.expmv(v_dev, x_dev, seed, allow_not_converged=True)
+    e1.record(stream)
+    e1.synchronize()
+    levels, est = plan.stats()
+    events = sum(lv["walks_per_row"] * plan.n + lv["jumps"] for lv in levels)
+    return e0.elapsed_time(e1) / 1e3, est, rc == 0, events
+
+
+def run_learned_workload(args):
+    """Plain jump law against the learned proposal on the same inputs."""
+    import torch
+    import mlmc_inputs as I
+    import __graft_entry__ as g
+    g.build()
+    from paper_1904_12754_gb300 import mlmc as M
+    st = torch.cuda.current_stream().cuda_stream
+    out = {"metric": "learned proposal vs plain MLMC", "n_gpus": 1, "dtype": "f32",
+           "data": "synthetic"}
+    # (1) the configured learned workload: BA n=1e6, m=8, beta=1/lambda_max
+    w = I.workload_c5()
+    log(f"{w.name}: n={w.a.n} nnz={w.a.nnz} lambda_max={w.extra['lambda_max']:.2f}")
+    sched = M.schedule_default(precision=M.FP32_KAHAN, num_levels=4, max_levels=10,
+                               time_budget_s=args.step_budget)
+    dv = torch.from_numpy(w.v).cuda()
+    dx = torch.zeros(w.a.n, dtype=torch.float64, device="cuda")
+    with M.Plan.from_csr(w.a, w.t, sched, rel_tol=1e-3, stream=st) as plan:
+        var_p, _ = _level0_variance(plan, dv, 256, 11)
+        tp, ep, cp, evp = _timed_solve(plan, dv, dx, 21)
+        t0 = time.perf_counter()
+        with M.MLP(seed=3, stream=st) as net:
+            loss = net.learn_proposal(plan, dv, seed=5, pilot_walks=64, steps=300, batch=8192)
+        torch.cuda.synchronize()
+        t_learn = time.perf_counter() - t0
+        var_l, _ = _level0_variance(plan, dv, 256, 11)
+        tl, el, cl, evl = _timed_solve(plan, dv, dx, 21)
+    out["ba_n1e6_m8_beta_inv_lambda_max"] = {
+        "level0_var_per_walk_plain": var_p, "level0_var_per_walk_learned": var_l,
+        "variance_ratio": var_l / var_p, "learn_seconds": t_learn, "train_loss": loss,
+        "budget_s": args.step_budget,
+        "plain": {"seconds": tp, "est_rel_err": ep, "converged": cp, "walk_steps_per_s": evp / tp},
+        "learned": {"seconds": tl, "est_rel_err": el, "converged": cl,
+                    "walk_steps_per_s": evl / tl},
+        "extrapolated_time_to_1e-3_s": {"plain": tp * (ep / 1e-3) ** 2,
+                                        "learned": t_learn + tl * (el / 1e-3) ** 2}}
+    log(f"BA: variance ratio {var_l / var_p:.3f}, est err plain {ep:.3g} learned {el:.3g}")
+    # (2) localized right-hand side: convection-diffusion 128^3, v = exp(-|x|^2)
+    w = I.workload_c4()
+    tol = args.tol
+    sched = M.schedule_default(precision=M.FP32_KAHAN, num_levels=4, max_levels=10,
+                               time_budget_s=300.0)
+    dv = torch.from_numpy(w.v).cuda()
+    dx = torch.zeros(w.a.n, dtype=torch.float64, device="cuda")
+    with M.Plan.from_csr(w.a, w.t, sched, rel_tol=tol, stream=st) as plan:
+        var_p, _ = _level0_variance(plan, dv, 64, 11)
+        tp, ep, cp, evp = _timed_solve(plan, dv, dx, 21)
+        xp = dx.cpu().numpy()
+        t0 = time.perf_counter()
+        with M.MLP(seed=3, stream=st) as net:
+            loss = net.learn_proposal(plan, dv, seed=5, pilot_walks=64, steps=300, batch=8192)
+        torch.cuda.synchronize()
+        t_learn = time.perf_counter() - t0
+        var_l, _ = _level0_variance(plan, dv, 64, 11)
+        tl, el, cl, evl = _timed_solve(plan, dv, dx, 21)
+        xl = dx.cpu().numpy()
+    from oracle import reference as R  # FP64 judge (CPU baseline leg)
+    ref = R.expmv_taylor(w.a.scipy(), w.t, w.v)
+    nref = np.linalg.norm(ref)
+    out["convdiff3d_128_bump"] = {
+        "tol": tol, "level0_var_per_walk_plain": var_p, "level0_var_per_walk_learned": var_l,
+        "variance_ratio": var_l / var_p, "learn_seconds": t_learn, "train_loss": loss,
+        "plain": {"time_to_tol_s": tp, "est_rel_err": ep, "converged": cp,
+                  "rel_err_vs_fp64": float(np.linalg.norm(xp - ref) / nref)},
+        "learned": {"time_to_tol_s": tl, "time_incl_learning_s": tl + t_learn, "est_rel_err": el,
+                    "converged": cl, "rel_err_vs_fp64": float(np.linalg.norm(xl - ref) / nref)},
+        "speedup_excl_learning": tp / tl, "speedup_incl_learning": tp / (tl + t_learn)}
+    log(f"convdiff: plain {tp:.2f} s, learned {tl:.2f} s (+{t_learn:.2f} s learning)")
+    out["value"] = out["convdiff3d_128_bump"]["speedup_incl_learning"]
+    out["unit"] = "x (plain time / learned time incl. learning)"
+    out["higher_is_better"] = True
+    print(json.dumps(out), flush=True)
+
+
+def run_precision_workload(args):
+    """FP32 + Kahan walk against the all-FP64 walk on the convection-
+    diffusion workload, each with its error against the FP64 Taylor judge."""
+    import torch
+    import mlmc_inputs as I
+    import __graft_entry__ as g
+    g.build()
+    from paper_1904_12754_gb300 import mlmc as M
+    from oracle import reference as R  # FP64 judge
+    st = torch.cuda.current_stream().cuda_stream
+    w = I.workload_c4()
+    ref = R.expmv_taylor(w.a.scipy(), w.t, w.v)
+    nref = np.linalg.norm(ref)
+    dv = torch.from_numpy(w.v).cuda()
+    dx = torch.zeros(w.a.n, dtype=torch.float64, device="cuda")
+    res = {}
+    for name, prec in (("fp32_kahan", M.FP32_KAHAN), ("fp64", M.FP64)):
+        sched = M.schedule_default(precision=prec, num_levels=4, max_levels=10,
+                                   time_budget_s=args.step_budget)
+        with M.Plan.from_csr(w.a, w.t, sched, rel_tol=args.tol, stream=st) as plan:
+            sec, est, conv, events = _timed_solve(plan, dv, dx, 7)
+            levels, _ = plan.stats()
+        x = dx.cpu().numpy()
+        res[name] = {"seconds": sec, "walk_steps_per_s": events / sec, "est_rel_err": est,
+                     "converged": conv, "rel_err_vs_fp64_taylor": float(np.linalg.norm(x - ref) / nref),
+                     "levels": len(levels)}
+        log(f"{name}: {sec:.2f} s, est {est:.3g}, err {res[name]['rel_err_vs_fp64_taylor']:.3g}")
+    out = {"metric": "precision path: FP32+Kahan vs FP64 walk, error vs FP64 Taylor",
+           "config": {"workload": w.name, "n": w.a.n, "nnz": w.a.nnz, "t": w.t, "tol": args.tol},
+           "n_gpus": 1, "data": "synthetic", **res,
+           "value": res["fp64"]["seconds"] / res["fp32_kahan"]["seconds"],
+           "unit": "x (FP64 time / FP32 time)", "higher_is_better": True}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -548,14 +704,19 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=15.0)
     ap.add_argument("--step-budget", type=float, default=8.0,
                     help="controller wall-clock budget of one step (s)")
-    ap.add_argument("--workload", choices=["tc", "batch"], default="tc",
-                    help="tc: the metric's workload (default); batch: batched vs plain")
+    ap.add_argument("--workload", choices=["tc", "batch", "learned", "precision"], default="tc",
+                    help="tc: the metric's workload (default); batch: batched vs plain; "
+                         "learned: learned proposal vs plain; precision: FP32 vs FP64 walk")
     ap.add_argument("--tol", type=float, default=1e-2, help="tolerance of --workload batch")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.workload == "batch":
         run_batch_workload(args)
+    elif args.workload == "learned":
+        run_learned_workload(args)
+    elif args.workload == "precision":
+        run_precision_workload(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
