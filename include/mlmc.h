@@ -184,9 +184,22 @@ mlmc_status mlmc_export_proposal(const mlmc_plan *plan, uint32_t *thr, int32_t *
  * Synchronises the plan's stream.  NOT_CONVERGED still writes x. */
 mlmc_status mlmc_expmv(mlmc_plan *plan, const double *v, double *x, uint64_t seed);
 
-/* Statistics of the last mlmc_expmv: up to `cap` levels into out (host),
- * the level count into *n_levels and the estimated relative RMS error
- * sqrt(sum_l V_l/M_l)/||x|| into *est_rel_err (either pointer may be NULL). */
+/* One entry x_i = (exp(t A) v)_i: Algorithm 2 as printed, walks from row i
+ * only, with the controller of Algorithm 1 on the scalar (eps = rel_tol
+ * |x_i|).  v: host or device, n doubles; xi: host.  This is what the paper's
+ * tables measure for the heat equation (a single point). */
+mlmc_status mlmc_expmv_entry(mlmc_plan *plan, int64_t i, const double *v, double *xi,
+                             uint64_t seed);
+
+/* The scalar 1^T exp(t A) v (with v = 1: the total communicability of
+ * Eq. 24), to relative error rel_tol on the scalar: walks from every row,
+ * eps = rel_tol |1^T x|.  total: host. */
+mlmc_status mlmc_expmv_sum(mlmc_plan *plan, const double *v, double *total, uint64_t seed);
+
+/* Statistics of the last mlmc_expmv / _entry / _sum: up to `cap` levels
+ * into out (host), the level count into *n_levels and the estimated relative
+ * RMS error sqrt(sum_l V_l/M_l)/|target| into *est_rel_err (either pointer
+ * may be NULL). */
 mlmc_status mlmc_stats(const mlmc_plan *plan, mlmc_level_stats *out, int32_t cap,
                        int32_t *n_levels, double *est_rel_err);
 

@@ -79,6 +79,7 @@ void free_plan(mlmc_plan* p) {
   cudaFree(p->d_v32);
   cudaFree(p->d_x);
   cudaFree(p->d_norm2);
+  cudaFree(p->d_sumpair);
   if (!p->levels.empty()) cudaFree(p->levels[0].sum_y);
   for (auto& L : p->levels) {
     if (L.ev0) cudaEventDestroy(L.ev0);
@@ -108,7 +109,7 @@ std::string flag_text(uint32_t f) {
 }
 
 struct HostLevel {
-  double y2, jumps, walks, limit, still, sumsq;
+  double y2, jumps, walks, limit, still, sumsq, sum;
 };
 
 }  // namespace
@@ -127,11 +128,14 @@ static mlmc_status run_level(mlmc_plan* p, int slot, int64_t extra, uint64_t see
                              std::chrono::steady_clock::time_point deadline, bool* stopped) {
   constexpr int64_t kBatchWalks = int64_t{1} << 36;  // ~0.5-1 s of FP32 walks
   LevelAcc& L = p->levels[slot];
-  const int64_t batch_reps = std::max<int64_t>(32, kBatchWalks / p->n);
+  const int64_t rows = p->ctl_row_count < 0 ? p->n : p->ctl_row_count;
+  const int64_t batch_reps = std::max<int64_t>(32, kBatchWalks / rows);
   if (stopped) *stopped = false;
   for (int64_t done = 0; done < extra;) {
     const int64_t reps = std::min(batch_reps, extra - done);
     WalkLaunch w;
+    w.row_begin = p->ctl_row_begin;
+    w.row_count = p->ctl_row_count;
     w.level = p->l0 + slot;
     w.coarse = slot > 0;
     w.rep_begin = L.reps;
@@ -168,8 +172,13 @@ static mlmc_status run_level(mlmc_plan* p, int slot, int64_t extra, uint64_t see
 // Reduce sum_i S_i^2 per level and ||x||^2, and read the scalars back.
 static mlmc_status collect(mlmc_plan* p, int nl, std::vector<HostLevel>& out, double* norm2) {
   for (int k = 0; k < nl; ++k) {
-    MLMC_CUDA(cudaMemsetAsync(totals_of(p, k) + kTotSumSq, 0, sizeof(double), p->stream), "memset");
-    MLMC_CUDA(launch_sumsq(p, p->levels[k].sum_y, totals_of(p, k) + kTotSumSq, 1.0), "sumsq");
+    MLMC_CUDA(cudaMemsetAsync(totals_of(p, k) + kTotSumSq, 0, 2 * sizeof(double), p->stream), "memset");
+    MLMC_CUDA(launch_sum_sumsq(p, p->levels[k].sum_y, p->d_sumpair), "sum");
+    MLMC_CUDA(cudaMemcpyAsync(totals_of(p, k) + kTotSumSq, p->d_sumpair + 1, sizeof(double),
+                              cudaMemcpyDeviceToDevice, p->stream), "copy");
+    MLMC_CUDA(cudaMemcpyAsync(totals_of(p, k) + kTotSum, p->d_sumpair, sizeof(double),
+                              cudaMemcpyDeviceToDevice, p->stream), "copy");
+    MLMC_CUDA(cudaMemsetAsync(p->d_sumpair, 0, 2 * sizeof(double), p->stream), "memset");
   }
   MLMC_CUDA(launch_finalize(p, nl, nullptr, p->d_norm2), "finalize");
   std::vector<double> h(static_cast<size_t>(nl) * kTotSlots + 1);
@@ -190,7 +199,7 @@ static mlmc_status collect(mlmc_plan* p, int nl, std::vector<HostLevel>& out, do
   for (int k = 0; k < nl; ++k) {
     const double* t = h.data() + k * kTotSlots;
     out[k] = HostLevel{t[kTotY2], t[kTotJumps], t[kTotWalks], t[kTotLimit], t[kTotStill],
-                       t[kTotSumSq]};
+                       t[kTotSumSq], t[kTotSum]};
   }
   *norm2 = h[nl * kTotSlots];
   return MLMC_OK;
@@ -204,7 +213,7 @@ static double level_var(const mlmc_plan* p, int k, const HostLevel& h) {
 
 static double level_cost(const mlmc_plan* p, const HostLevel& h) {
   const double per_walk = h.walks > 0 ? 1.0 + h.jumps / h.walks : 1.0;
-  return static_cast<double>(p->n) * per_walk;
+  return static_cast<double>(p->ctl_row_count < 0 ? p->n : p->ctl_row_count) * per_walk;
 }
 
 }  // namespace mlmc
@@ -299,6 +308,8 @@ mlmc_status mlmc_plan_create(mlmc_plan** out, int64_t n, int64_t nnz, const int6
   PLAN_CUDA(dev_alloc(&p->d_v32, n), "alloc v32");
   PLAN_CUDA(dev_alloc(&p->d_x, n), "alloc x");
   PLAN_CUDA(dev_alloc(&p->d_norm2, 4), "alloc scalars");
+  PLAN_CUDA(dev_alloc(&p->d_sumpair, 2), "alloc scalars");
+  PLAN_CUDA(cudaMemsetAsync(p->d_sumpair, 0, 2 * sizeof(double), p->stream), "memset");
   double* sums = nullptr;
   PLAN_CUDA(dev_alloc(&sums, static_cast<size_t>(n) * s.max_levels), "alloc level sums");
   p->levels.resize(s.max_levels);
@@ -475,9 +486,14 @@ mlmc_status mlmc_trace(mlmc_plan* p, int32_t level, int32_t coarse, int64_t rep_
   return MLMC_OK;
 }
 
-mlmc_status mlmc_expmv(mlmc_plan* p, const double* v, double* x, uint64_t seed) {
-  g_last_error.clear();
-  if (!p || !v || !x) return fail(MLMC_ERR_INVALID_ARG, "NULL argument");
+// The controller of Algorithm 1 for one of three targets: the vector x
+// (FULL, error in the 2-norm), one entry x_row (ENTRY: only that row walks),
+// or the scalar 1^T x (SUM).  All three share V_l (rows are independent);
+// they differ in the norm that sets eps and in the bias test.
+enum Target { kFull = 0, kEntry = 1, kSum = 2 };
+
+static mlmc_status controller(mlmc_plan* p, const double* v, double* x, double* scalar,
+                              uint64_t seed, Target target) {
   const auto t_start = std::chrono::steady_clock::now();
   const mlmc_schedule& s = p->sched;
   MLMC_CUDA(cudaMemcpyAsync(p->d_v, v, sizeof(double) * p->n, cudaMemcpyDefault, p->stream), "copy v");
@@ -508,7 +524,13 @@ mlmc_status mlmc_expmv(mlmc_plan* p, const double* v, double* x, uint64_t seed) 
   mlmc_status result = MLMC_OK;
   for (int iter = 0; iter < 64; ++iter) {
     if ((st = collect(p, nl, h, &norm2)) != MLMC_OK) return st;
-    double eps = p->rel_tol * std::sqrt(norm2);
+    auto size_of_x = [&]() {
+      if (target == kFull) return std::sqrt(norm2);
+      double tsum = 0.0;
+      for (int k = 0; k < nl; ++k) tsum += h[k].sum / static_cast<double>(p->levels[k].reps);
+      return std::fabs(tsum);
+    };
+    double eps = p->rel_tol * size_of_x();
     // Optimal sample sizes and top-up.
     std::vector<double> V(nl), C(nl);
     double root_sum = 0.0;
@@ -535,18 +557,19 @@ mlmc_status mlmc_expmv(mlmc_plan* p, const double* v, double* x, uint64_t seed) 
     }
     if (topped) {
       if ((st = collect(p, nl, h, &norm2)) != MLMC_OK) return st;
-      eps = p->rel_tol * std::sqrt(norm2);
+      eps = p->rel_tol * size_of_x();
     }
     double var = 0.0;
     for (int k = 0; k < nl; ++k) var += level_var(p, k, h[k]) / static_cast<double>(p->levels[k].reps);
     auto mnorm = [&](int k) {
       const double m = static_cast<double>(p->levels[k].reps);
-      return std::sqrt(h[k].sumsq) / m;
+      return (target == kFull ? std::sqrt(h[k].sumsq) : std::fabs(h[k].sum)) / m;
     };
     const double bias = nl > 1 ? std::max(mnorm(nl - 1), mnorm(nl - 2) / 4.0) / 3.0 : 0.0;
     const bool var_ok = var <= 0.5 * eps * eps * (1.0 + 1e-12);
     const bool bias_ok = bias <= eps / std::sqrt(2.0);
-    p->last_est_rel_err = norm2 > 0 ? std::sqrt(var / norm2) : 0.0;
+    const double xs = size_of_x();
+    p->last_est_rel_err = xs > 0 ? std::sqrt(var) / xs : 0.0;
     if (var_ok && bias_ok) {
       converged = true;
       break;
@@ -566,8 +589,14 @@ mlmc_status mlmc_expmv(mlmc_plan* p, const double* v, double* x, uint64_t seed) 
   if (!converged) result = fail(MLMC_ERR_NOT_CONVERGED, "budget exhausted before the tolerance");
 
   // Final cross-level sum (Eq. 10) in FP64 and copy-out.
-  MLMC_CUDA(launch_finalize(p, nl, p->d_x, p->d_norm2), "finalize");
-  MLMC_CUDA(cudaMemcpyAsync(x, p->d_x, sizeof(double) * p->n, cudaMemcpyDefault, p->stream), "copy x");
+  if (target == kFull) {
+    MLMC_CUDA(launch_finalize(p, nl, p->d_x, p->d_norm2), "finalize");
+    MLMC_CUDA(cudaMemcpyAsync(x, p->d_x, sizeof(double) * p->n, cudaMemcpyDefault, p->stream), "copy x");
+  } else {
+    double tsum = 0.0;
+    for (int k = 0; k < nl; ++k) tsum += h[k].sum / static_cast<double>(p->levels[k].reps);
+    *scalar = tsum;
+  }
   uint32_t flags = 0;
   if ((st = read_flags(p, &flags)) != MLMC_OK) return st;
   p->last_stats.clear();
@@ -588,6 +617,34 @@ mlmc_status mlmc_expmv(mlmc_plan* p, const double* v, double* x, uint64_t seed) 
   if (flags & kFlagWalkLimit) return fail(MLMC_ERR_WALK_LIMIT, "walk limit:" + flag_text(flags));
   if (flags & kFlagNonFiniteY) return fail(MLMC_ERR_NUMERIC, "numeric:" + flag_text(flags));
   return result;
+}
+
+mlmc_status mlmc_expmv(mlmc_plan* p, const double* v, double* x, uint64_t seed) {
+  g_last_error.clear();
+  if (!p || !v || !x) return fail(MLMC_ERR_INVALID_ARG, "NULL argument");
+  p->ctl_row_begin = 0;
+  p->ctl_row_count = -1;
+  return controller(p, v, x, nullptr, seed, kFull);
+}
+
+mlmc_status mlmc_expmv_entry(mlmc_plan* p, int64_t i, const double* v, double* xi, uint64_t seed) {
+  g_last_error.clear();
+  if (!p || !v || !xi) return fail(MLMC_ERR_INVALID_ARG, "NULL argument");
+  if (i < 0 || i >= p->n) return fail(MLMC_ERR_INVALID_ARG, "row index out of range");
+  p->ctl_row_begin = i;
+  p->ctl_row_count = 1;
+  const mlmc_status st = controller(p, v, nullptr, xi, seed, kEntry);
+  p->ctl_row_begin = 0;
+  p->ctl_row_count = -1;
+  return st;
+}
+
+mlmc_status mlmc_expmv_sum(mlmc_plan* p, const double* v, double* total, uint64_t seed) {
+  g_last_error.clear();
+  if (!p || !v || !total) return fail(MLMC_ERR_INVALID_ARG, "NULL argument");
+  p->ctl_row_begin = 0;
+  p->ctl_row_count = -1;
+  return controller(p, v, nullptr, total, seed, kSum);
 }
 
 mlmc_status mlmc_stats(const mlmc_plan* p, mlmc_level_stats* out, int32_t cap, int32_t* n_levels,

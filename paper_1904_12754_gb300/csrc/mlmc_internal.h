@@ -34,9 +34,11 @@ struct LevelAcc {
 
 // Totals slots of the per-level device scalars (doubles).
 enum { kTotY2 = 0, kTotJumps = 1, kTotWalks = 2, kTotLimit = 3, kTotStill = 4, kTotSumSq = 5,
-       kTotSlots = 8 };
+       kTotSum = 6, kTotSlots = 8 };
 
 struct WalkLaunch {
+  int64_t row_begin = 0;   // rows row_begin .. row_begin + row_count - 1
+  int64_t row_count = -1;  // -1: every row
   int level = 0;
   bool coarse = false;
   int64_t rep_begin = 0;
@@ -124,9 +126,13 @@ struct mlmc_plan {
   double* d_v = nullptr;                       // [n]
   float* d_v32 = nullptr;                      // [n] FP32 copy for the FP32 walk
   double* d_x = nullptr;                       // [n]
-  double* d_norm2 = nullptr;                   // [2]
+  double* d_norm2 = nullptr;                   // [4]
+  double* d_sumpair = nullptr;                 // [2] sum, sum of squares
   std::vector<mlmc::LevelAcc> levels;          // per level slot (index l - l0)
   std::vector<mlmc_level_stats> last_stats;
+  // Rows walked by the controller (ENTRY mode: one row); -1 = every row.
+  int64_t ctl_row_begin = 0;
+  int64_t ctl_row_count = -1;
   double last_est_rel_err = 0.0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
@@ -151,6 +157,8 @@ cudaError_t launch_walk_scratch(mlmc_plan* p, const WalkLaunch& w, unsigned long
 
 // Reductions (mlmc_reduce.cu).
 cudaError_t launch_sumsq(mlmc_plan* p, const double* a, double* out, double scale);
+// out[0] += sum_i a_i, out[1] += sum_i a_i^2 (out must be zeroed by the caller).
+cudaError_t launch_sum_sumsq(mlmc_plan* p, const double* a, double* out);
 cudaError_t launch_finalize(mlmc_plan* p, int num_levels, double* x, double* norm2);
 
 }  // namespace mlmc

@@ -41,6 +41,24 @@ __global__ void __launch_bounds__(kRedBlock) k_sumsq(int64_t n, const double* __
   if (threadIdx.x == 0) atomicAdd(out, acc * scale);
 }
 
+__global__ void __launch_bounds__(kRedBlock) k_sum_sumsq(int64_t n, const double* __restrict__ a,
+                                                         double* __restrict__ out) {
+  double s1 = 0.0, s2 = 0.0;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(kRedBlock) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * kRedBlock) {
+    const double x = a[i];
+    s1 += x;
+    s2 += x * x;
+  }
+  s1 = block_sum(s1);
+  __syncthreads();
+  s2 = block_sum(s2);
+  if (threadIdx.x == 0) {
+    atomicAdd(out, s1);
+    atomicAdd(out + 1, s2);
+  }
+}
+
 __global__ void __launch_bounds__(kRedBlock) k_finalize(int64_t n, FinalizeArgs f,
                                                         double* __restrict__ x,
                                                         double* __restrict__ norm2) {
@@ -66,6 +84,12 @@ int red_grid(const mlmc_plan* p) {
 
 cudaError_t launch_sumsq(mlmc_plan* p, const double* a, double* out, double scale) {
   k_sumsq<<<red_grid(p), kRedBlock, 0, p->stream>>>(p->n, a, out, scale);
+  p->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sum_sumsq(mlmc_plan* p, const double* a, double* out) {
+  k_sum_sumsq<<<red_grid(p), kRedBlock, 0, p->stream>>>(p->n, a, out);
   p->launches++;
   return cudaGetLastError();
 }

@@ -49,6 +49,7 @@ struct WalkArgs {
   int64_t chunk;           // walks per item (multiple of 32)
   int64_t chunks_per_row;
   unsigned long long total_items;
+  int64_t row_begin;       // first row of the launch
   int level;
   uint32_t ctr3;           // level | stream << 6
   uint32_t key0, key1;
@@ -449,11 +450,11 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk(WalkArgs a) {
     if (lane == 0) item = atomicAdd(a.work, 1ull);
     item = __shfl_sync(kFull, item, 0);
     if (item >= a.total_items) break;
-    const int64_t row = static_cast<int64_t>(item / static_cast<unsigned long long>(a.chunks_per_row));
-    const int64_t chunk = static_cast<int64_t>(item) - row * a.chunks_per_row;
+    const int64_t rel = static_cast<int64_t>(item / static_cast<unsigned long long>(a.chunks_per_row));
+    const int64_t chunk = static_cast<int64_t>(item) - rel * a.chunks_per_row;
     const int64_t r_lo = chunk * a.chunk;
     const int64_t r_hi = min(r_lo + a.chunk, a.reps);
-    walk_item<FP64, COARSE, TRACE, IS>(ia, row, r_lo, r_hi, tot, lane);
+    walk_item<FP64, COARSE, TRACE, IS>(ia, a.row_begin + rel, r_lo, r_hi, tot, lane);
   }
   flush_totals(tot, a.totals, a.flags, lane);
 }
@@ -628,7 +629,9 @@ cudaError_t launch_walk(mlmc_plan* p, const WalkLaunch& w, int64_t* launches) {
     }
     a.chunk = 32 * per_lane;
     a.chunks_per_row = (reps + a.chunk - 1) / a.chunk;
-    a.total_items = static_cast<unsigned long long>(p->n) * static_cast<unsigned long long>(a.chunks_per_row);
+    a.row_begin = w.row_count < 0 ? 0 : w.row_begin;
+    a.total_items = static_cast<unsigned long long>(w.row_count < 0 ? p->n : w.row_count) *
+                    static_cast<unsigned long long>(a.chunks_per_row);
     cudaError_t err = cudaMemsetAsync(p->d_work, 0, sizeof(unsigned long long), p->stream);
     if (err != cudaSuccess) return err;
     err = dispatch_walk(p, a, block, fp64, w.coarse, trace, p->proposal_active);
@@ -684,7 +687,9 @@ cudaError_t launch_walk_scratch(mlmc_plan* p, const WalkLaunch& w, unsigned long
     }
     a.chunk = 32 * per_lane;
     a.chunks_per_row = (reps + a.chunk - 1) / a.chunk;
-    a.total_items = static_cast<unsigned long long>(p->n) * static_cast<unsigned long long>(a.chunks_per_row);
+    a.row_begin = w.row_count < 0 ? 0 : w.row_begin;
+    a.total_items = static_cast<unsigned long long>(w.row_count < 0 ? p->n : w.row_count) *
+                    static_cast<unsigned long long>(a.chunks_per_row);
     cudaError_t err = cudaMemsetAsync(work, 0, sizeof(unsigned long long), p->stream);
     if (err != cudaSuccess) return err;
     err = dispatch_walk(p, a, block, fp64, w.coarse, trace, p->proposal_active);

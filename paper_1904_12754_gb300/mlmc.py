@@ -75,6 +75,8 @@ def load(build_if_missing: bool = False):
     lib.mlmc_plan_rebuild.argtypes = [P]
     lib.mlmc_expmv.argtypes = [P, P, P, ct.c_uint64]
     lib.mlmc_stats.argtypes = [P, P, I32, ct.POINTER(I32), ct.POINTER(D)]
+    lib.mlmc_expmv_entry.argtypes = [P, I64, P, ct.POINTER(D), ct.c_uint64]
+    lib.mlmc_expmv_sum.argtypes = [P, P, ct.POINTER(D), ct.c_uint64]
     lib.mlmc_mlmcl.argtypes = [P, I32, I32, I64, I64, P, ct.c_uint64, P, P]
     lib.mlmc_trace.argtypes = [P, I32, I32, I64, I64, P, ct.c_uint64, P]
     lib.mlmc_trace_noalloc.argtypes = [P, I32, I32, I64, I64, P, ct.c_uint64, P]
@@ -105,6 +107,7 @@ def load(build_if_missing: bool = False):
     lib.mlmc_launch_count.argtypes = [P]
     lib.mlmc_launch_count.restype = I64
     for name in ("mlmc_schedule_default", "mlmc_plan_create", "mlmc_plan_rebuild", "mlmc_expmv",
+                 "mlmc_expmv_entry", "mlmc_expmv_sum",
                  "mlmc_stats", "mlmc_mlmcl", "mlmc_trace", "mlmc_trace_noalloc",
                  "mlmc_export_tables", "mlmc_batch_create", "mlmc_batch_expmv",
                  "mlmc_batch_stats", "mlmc_batch_info", "mlmc_batch_autotune",
@@ -219,6 +222,24 @@ class Plan:
         _need(x, 8 * self.n, "x")
         allow = (MLMC_ERR_NOT_CONVERGED,) if allow_not_converged else ()
         return _check(self._lib.mlmc_expmv(self._h, _ptr(v), _ptr(x), ct.c_uint64(seed)), allow)
+
+    def expmv_entry(self, i: int, v, seed: int, allow_not_converged: bool = False) -> float:
+        """x_i = (exp(tA)v)_i by walks from row i only (Algorithm 2)."""
+        _need(v, 8 * self.n, "v")
+        out = ct.c_double()
+        allow = (MLMC_ERR_NOT_CONVERGED,) if allow_not_converged else ()
+        _check(self._lib.mlmc_expmv_entry(self._h, int(i), _ptr(v), ct.byref(out),
+                                          ct.c_uint64(seed)), allow)
+        return out.value
+
+    def expmv_sum(self, v, seed: int, allow_not_converged: bool = False) -> float:
+        """1^T exp(tA) v (total communicability for v = 1)."""
+        _need(v, 8 * self.n, "v")
+        out = ct.c_double()
+        allow = (MLMC_ERR_NOT_CONVERGED,) if allow_not_converged else ()
+        _check(self._lib.mlmc_expmv_sum(self._h, _ptr(v), ct.byref(out), ct.c_uint64(seed)),
+               allow)
+        return out.value
 
     def stats(self):
         cap = 32

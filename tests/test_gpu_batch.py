@@ -130,3 +130,45 @@ def test_batch_reaches_tolerance_on_every_problem():
             assert err <= 2.5 * tol, (k, err)
     for p in cache.values():
         p.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_entry_pilot_sample_matches_oracle(precision):
+    # Algorithm 2 for one entry: walks from row i only.
+    from paper_1904_12754_gb300 import mlmc as M
+    a, t, v = _problems()[0]
+    levels, pilot = 3, 4096
+    sched = _pilot_only_schedule(precision, levels, pilot)
+    wk = W.Walker(a, t, v, seed=13, precision=W.FP64 if precision == 0 else W.FP32)
+    with M.Plan.from_csr(a, t, sched, rel_tol=1e-9, stream=stream_handle()) as plan:
+        l0 = plan.info()["l0"]
+        for i in (0, 17, a.n - 1):
+            xi = plan.expmv_entry(i, v, seed=13, allow_not_converged=True)
+            want = 0.0
+            for l in range(l0, l0 + levels):
+                s, _, _, _ = wk.mlmcl(l, l > l0, 0, pilot, rows=(i, i + 1))
+                want += s[i] / pilot
+            tol = 1e-11 if precision == 0 else 2e-5
+            assert abs(xi - want) <= tol * max(1.0, abs(want)), (i, xi, want)
+
+
+def test_entry_and_total_communicability_reach_tolerance():
+    from paper_1904_12754_gb300 import mlmc as M
+    w = I.workload_c1()
+    ref = R.expmv(w.a.scipy(), w.t, w.v)
+    sched = M.schedule_default(precision=M.FP64, num_levels=3, max_levels=8)
+    with M.Plan.from_csr(w.a, w.t, sched, rel_tol=1e-3, stream=stream_handle()) as plan:
+        for i in (0, 500, 1023):
+            xi = plan.expmv_entry(i, w.v, seed=3 + i)
+            _, est = plan.stats()
+            assert est <= 1e-3
+            assert abs(xi - ref[i]) <= 4e-3 * abs(ref[i]), (i, xi, ref[i])
+    b = I.ba_graph(3000, 4, seed=2)
+    t = 1.0 / np.diff(b.row_ptr).max()
+    tc_ref = R.expmv(b.scipy(), t, np.ones(b.n)).sum()
+    sched = M.schedule_default(precision=M.FP32_KAHAN, num_levels=3, max_levels=8)
+    with M.Plan.from_csr(b, t, sched, rel_tol=1e-4, stream=stream_handle()) as plan:
+        tc = plan.expmv_sum(np.ones(b.n), seed=9)
+        _, est = plan.stats()
+    assert est <= 1e-4
+    assert abs(tc - tc_ref) <= 4e-4 * tc_ref
