@@ -58,7 +58,14 @@ enum { MLMC_PLAIN = 0, MLMC_LEARNED = 1 };     /* jump proposal */
  *   max_levels        the controller adds levels up to this many
  *   pilot_walks       walks per row per level in the pilot run
  *   precision         MLMC_FP64 or MLMC_FP32_KAHAN
- *   mode              MLMC_BACKWARD (Algorithm 2 from every row)
+ *   mode              MLMC_BACKWARD (Algorithm 2 from every row) or
+ *                     MLMC_FORWARD (the full-vector representation, Eq. 5:
+ *                     walks on A^T from starts drawn ~|v_s|, each adding
+ *                     sign(v_s) (W/w_s)|v_s| e^E to x[end]; W/w_s corrects
+ *                     the integer start weights w_s = ceil(|v_s|/max|v| 2^20),
+ *                     so the estimate is exact in expectation).  In forward
+ *                     mode pilot_walks and max_walks_per_row are per row of
+ *                     A and are multiplied by n (total walks).
  *   proposal          MLMC_PLAIN at creation (mlmc_plan_set_proposal switches
  *                     the plan to MLMC_LEARNED)
  *   max_jumps_per_walk  a walk that would exceed it stops, contributes 0 and
@@ -111,7 +118,8 @@ typedef struct {
 /* One replayed walk (mlmc_trace): the state at s = 1, the number of jumps,
  * the product of jump signs phi, an FNV-1a hash of the states entered by
  * each jump (offset basis 2166136261, prime 16777619, over the 32-bit state
- * indices), the contribution y, and a status (0 ok, 1 jump limit). */
+ * indices), the contribution y, and a status (0 ok, 1 jump limit).  `pad`
+ * holds the start state in forward mode (0 in backward mode). */
 typedef struct {
     int32_t end;
     int32_t jumps;
@@ -212,7 +220,10 @@ mlmc_status mlmc_stats(const mlmc_plan *plan, mlmc_level_stats *out, int32_t cap
  *   totals   device pointer, 5 doubles: [0] += sum Y^2, [1] += jumps,
  *            [2] += walks, [3] += walks that hit the jump limit,
  *            [4] += walks that ended without a jump
- * Asynchronous on the plan's stream; uses the plan's precision. */
+ * Asynchronous on the plan's stream; uses the plan's precision.
+ * Forward-mode plans: reps counts walks (not per row), rep_begin is the first
+ * walk index, and each walk adds to sum_y at its end state; the call reads
+ * the start-weight total back and so synchronises. */
 mlmc_status mlmc_mlmcl(mlmc_plan *plan, int32_t level, int32_t coarse, int64_t rep_begin,
                        int64_t reps, const double *v, uint64_t seed, double *sum_y,
                        double *totals);
@@ -220,7 +231,8 @@ mlmc_status mlmc_mlmcl(mlmc_plan *plan, int32_t level, int32_t coarse, int64_t r
 /* Replay walks rep_begin .. rep_begin+reps-1 of every row at one level and
  * record each (the same kernel and launch shape as mlmc_mlmcl, with
  * recording on).  rec: device pointer, n*reps records, index row*reps +
- * (rep - rep_begin).  Asynchronous. */
+ * (rep - rep_begin); forward-mode plans: reps records, index g - rep_begin
+ * for walk g.  Synchronises. */
 mlmc_status mlmc_trace(mlmc_plan *plan, int32_t level, int32_t coarse, int64_t rep_begin,
                        int64_t reps, const double *v, uint64_t seed, mlmc_walk_record *rec);
 

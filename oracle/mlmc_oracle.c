@@ -400,15 +400,39 @@ typedef struct {
 /* Counter layout: (rep bits 0-31, row, draw index, level | variant<<6 |
  * rep bits 32-55 << 8); key = seed.  In the residual-clock walk the draw
  * index equals the number of jumps taken so far. */
-static void orc_draw(const orc_ctx *c, int64_t row, int64_t rep, uint32_t event, int level,
-                     uint32_t x[4])
+/* The three fixed counter words of one walk.  Backward: (rep bits 0-31,
+ * row, -, level | variant << 6 | rep bits 32-55 << 8).  Forward walk g:
+ * (g bits 0-31, g bits 32-63, -, level | 1 << 6). */
+typedef struct {
+    uint32_t w0, w1, w3;
+} orc_ctr;
+
+static orc_ctr orc_ctr_backward(const orc_ctx *c, int64_t row, int64_t rep, int level)
+{
+    orc_ctr k;
+    k.w0 = (uint32_t)((uint64_t)rep & 0xFFFFFFFFull);
+    k.w1 = (uint32_t)row;
+    k.w3 = (uint32_t)level | ((uint32_t)c->variant << 6) |
+           ((uint32_t)(((uint64_t)rep >> 32) & 0xFFFFFFull) << 8);
+    return k;
+}
+
+static orc_ctr orc_ctr_forward(uint64_t g, int level)
+{
+    orc_ctr k;
+    k.w0 = (uint32_t)(g & 0xFFFFFFFFull);
+    k.w1 = (uint32_t)(g >> 32);
+    k.w3 = (uint32_t)level | (1u << 6);
+    return k;
+}
+
+static void orc_draw_k(const orc_ctx *c, orc_ctr k, uint32_t event, uint32_t x[4])
 {
     uint32_t ctr[4], key[2];
-    ctr[0] = (uint32_t)((uint64_t)rep & 0xFFFFFFFFull);
-    ctr[1] = (uint32_t)row;
+    ctr[0] = k.w0;
+    ctr[1] = k.w1;
     ctr[2] = event;
-    ctr[3] = (uint32_t)level | ((uint32_t)c->variant << 6) |
-             ((uint32_t)(((uint64_t)rep >> 32) & 0xFFFFFFull) << 8);
+    ctr[3] = k.w3;
     key[0] = (uint32_t)(c->seed & 0xFFFFFFFFull);
     key[1] = (uint32_t)(c->seed >> 32);
     orc_philox4x32_10(ctr, key, x);
@@ -471,8 +495,8 @@ static int orc_before(const orc_ctx *c, double t_next, int64_t n_step, int64_t N
  *   diff  = sum_j dt (-d_{X_{2j-2}}/2 + d_{X_{2j-1}} - d_{X_{2j}}/2) (xi_j of
  *           Lemma 2), so y = sign u_end e^{log_c} expm1(diff) avoids the
  *           cancellation in eta_2 - eta_1. */
-int orc_walk(const orc_ctx *c, int64_t row, int64_t rep, int level, int coarse,
-             orc_walk_rec *out)
+static int orc_walk_core(const orc_ctx *c, int64_t row, orc_ctr kc, int level, int coarse,
+                         int use_v_end, orc_walk_rec *out)
 {
     const int64_t N = (int64_t)1 << level;
     int64_t j = row;
@@ -487,7 +511,7 @@ int orc_walk(const orc_ctx *c, int64_t row, int64_t rep, int level, int coarse,
     double log_is = 0.0;  /* sum of log(k/q) over the jumps (proposal tables) */
     int64_t x_prev2 = row, x_prev1 = row; /* states at grid points 2j-2, 2j-1 */
 
-    orc_draw(c, row, rep, ndraw++, level, x);
+    orc_draw_k(c, kc, ndraw++, x);
     double t_next = orc_hold(c, j, x, 0.0);
 
     for (int64_t step = 1; step <= N; ++step) {
@@ -496,7 +520,7 @@ int orc_walk(const orc_ctx *c, int64_t row, int64_t rep, int level, int coarse,
         if (step % 2 != 0) eta1 = eta1 * exp(g);
         if (c->variant == ORC_REDRAW) {
             /* Fresh clock at the start of the interval (the listing's tau). */
-            orc_draw(c, row, rep, ndraw++, level, x);
+            orc_draw_k(c, kc, ndraw++, x);
             t_next = orc_hold(c, j, x, (double)(step - 1) / (double)N);
         }
         while (orc_before(c, t_next, step, N)) {
@@ -510,7 +534,7 @@ int orc_walk(const orc_ctx *c, int64_t row, int64_t rep, int level, int coarse,
             log_is = log_is + lr;
             hash = (hash ^ (uint32_t)j) * 16777619u;
             jumps = jumps + 1;
-            orc_draw(c, row, rep, ndraw++, level, x);
+            orc_draw_k(c, kc, ndraw++, x);
             /* R1: the new holding time uses the new state's rate; the
              * literal reading uses the state just left. */
             t_next = orc_hold(c, (c->variant == ORC_LITERAL_RATE) ? from : j, x, t_next);
@@ -550,7 +574,7 @@ done:
         out->log_c = 0.0;
         return status;
     }
-    double uj = c->v[j];
+    double uj = use_v_end ? c->v[j] : 1.0;
     out->log_f = log_f;
     out->log_c = coarse ? log_c : 0.0;
     if (coarse) {
@@ -561,6 +585,63 @@ done:
         out->y_alg2 = (double)sign * uj * eta2 * exp(log_is);
     }
     return status;
+}
+
+int orc_walk(const orc_ctx *c, int64_t row, int64_t rep, int level, int coarse,
+             orc_walk_rec *out)
+{
+    return orc_walk_core(c, row, orc_ctr_backward(c, row, rep, level), level, coarse, 1, out);
+}
+
+/* Forward mode (Eq. 5; reading R6): the tables in c are those of B = A^T.
+ * Walk g draws its start from the integer weights w (prefix sums cdf,
+ * total W): r = floor(u W / 2^64) with u the 64-bit word (x0:x1) of the
+ * draw at index 0xFFFFFFFF, start = the smallest s with cdf[s] > r.  Its
+ * contribution is y = v_s (W / w_s) sign e^{...}, added to x[end]. */
+int orc_walk_fwd(const orc_ctx *c, const int64_t *cdf, const int64_t *w, uint64_t W, uint64_t g,
+                 int level, int coarse, orc_walk_rec *out)
+{
+    orc_ctr kc = orc_ctr_forward(g, level);
+    uint32_t x[4];
+    orc_draw_k(c, kc, 0xFFFFFFFFu, x);
+    uint64_t u = ((uint64_t)x[0] << 32) | (uint64_t)x[1];
+    uint64_t r = (uint64_t)(((unsigned __int128)u * (unsigned __int128)W) >> 64);
+    int64_t lo = 0, hi = c->n - 1;
+    while (lo < hi) { /* binary search: smallest s with cdf[s] > r */
+        int64_t mid = (lo + hi) / 2;
+        if ((uint64_t)cdf[mid] > r) hi = mid; else lo = mid + 1;
+    }
+    int status = orc_walk_core(c, lo, kc, level, coarse, 0, out);
+    double f = c->v[lo] * ((double)W / (double)w[lo]);
+    out->y = out->y * f;
+    out->y_alg2 = out->y_alg2 * f;
+    out->pad = (int32_t)lo;
+    return status;
+}
+
+int orc_walk_fwd_many(const orc_ctx *c, const int64_t *cdf, const int64_t *w, uint64_t W,
+                      uint64_t g0, int64_t count, int level, int coarse, orc_walk_rec *out)
+{
+    int bad = 0;
+    for (int64_t k = 0; k < count; ++k)
+        if (orc_walk_fwd(c, cdf, w, W, g0 + (uint64_t)k, level, coarse, &out[k]) != ORC_OK) bad = 1;
+    return bad;
+}
+
+/* Algorithm 2 in forward mode for walks g0 .. g0+count-1: sum_x[end] += y. */
+int orc_mlmcl_fwd(const orc_ctx *c, const int64_t *cdf, const int64_t *w, uint64_t W, uint64_t g0,
+                  int64_t count, int level, int coarse, double *sum_x, double *sum_y2,
+                  int64_t *jumps, int64_t *limit_hits)
+{
+    orc_walk_rec r;
+    for (int64_t k = 0; k < count; ++k) {
+        if (orc_walk_fwd(c, cdf, w, W, g0 + (uint64_t)k, level, coarse, &r) != ORC_OK)
+            *limit_hits = *limit_hits + 1;
+        sum_x[r.end] = sum_x[r.end] + r.y;
+        *sum_y2 = *sum_y2 + r.y * r.y;
+        *jumps = *jumps + r.jumps;
+    }
+    return 0;
 }
 
 int orc_walk_many(const orc_ctx *c, int64_t count, const int64_t *rows, const int64_t *reps,

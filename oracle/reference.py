@@ -179,6 +179,27 @@ def strang(a, t: float, v: np.ndarray, level: int) -> np.ndarray:
     return w
 
 
+def strang_forward(a, t: float, v: np.ndarray, level: int) -> np.ndarray:
+    """Mean of the forward-mode level-l estimate (Eq. 5 read on B = A^T):
+    with B = D' - T' split by Eq. 1 (d'_i = a_ii + sum_{k != i} |a_ki|), the
+    backward Strang operator of B is S_B = (e^{dt D'/2} e^{-dt T'} e^{dt D'/2})^N
+    and the forward walks estimate S_B^T v; S_B^T applies e^{-dt T'^T}, whose
+    off-diagonals are a_ij and diagonal -L'_ii."""
+    n_steps = 1 << level
+    dt = t / n_steps
+    b = sp.csr_matrix(a, dtype=np.float64).T.tocsr()
+    d_b, minus_tb = _split_sparse(b)          # d' and -T' (of B)
+    minus_tbt = minus_tb.T.tocsr()            # -T'^T
+    half = np.exp(dt * d_b / 2.0)
+    dense = expm_pade13(dt * minus_tbt.toarray()) if a.shape[0] <= 2048 else None
+    w = np.array(v, dtype=np.float64, copy=True)
+    for _ in range(n_steps):
+        w = half * w
+        w = dense @ w if dense is not None else expmv_taylor(minus_tbt, dt, w)
+        w = half * w
+    return w
+
+
 def level_means(a, t: float, v: np.ndarray, l0: int, top: int):
     """Exact per-level corrections m_l of Eq. 9 for l = l0..top:
     m_l0 = x-bar^(l0), m_l = x-bar^(l) - x-bar^(l-1)."""

@@ -88,6 +88,10 @@ def lib():
         _lib.orc_mlmcl.argtypes = [ct.POINTER(Ctx), ct.c_int64, ct.c_int64, ct.c_int64,
                                    ct.c_int64, ct.c_int, ct.c_int, ct.c_int, P, P, P, P]
         _lib.orc_max_threads.restype = ct.c_int
+        _lib.orc_walk_fwd_many.argtypes = [ct.POINTER(Ctx), P, P, ct.c_uint64, ct.c_uint64,
+                                           ct.c_int64, ct.c_int, ct.c_int, P]
+        _lib.orc_mlmcl_fwd.argtypes = [ct.POINTER(Ctx), P, P, ct.c_uint64, ct.c_uint64, ct.c_int64,
+                                       ct.c_int, ct.c_int, P, P, P, P]
     return _lib
 
 
@@ -228,3 +232,50 @@ class Walker:
 
 def max_threads() -> int:
     return int(lib().orc_max_threads())
+
+
+def transpose(a):
+    """Canonical CSR of A^T (forward mode walks on it)."""
+    import scipy.sparse as sp
+    m = sp.csr_matrix((a.val, a.col, a.row_ptr), shape=(a.n, a.n)).T.tocsr()
+    m.sort_indices()
+    from types import SimpleNamespace
+    return SimpleNamespace(n=a.n, row_ptr=m.indptr.astype(np.int64), col=m.indices.astype(np.int32),
+                           val=m.data.astype(np.float64))
+
+
+def start_weights(v: np.ndarray):
+    """Integer start weights w_s = ceil(|v_s|/max|v| * 2^20) (0 where v_s = 0),
+    their inclusive prefix sums and total (exact integer arithmetic)."""
+    av = np.abs(np.asarray(v, dtype=np.float64))
+    vmax = av.max()
+    w = np.where(av > 0, np.ceil((av / vmax) * 1048576.0), 0).astype(np.int64)
+    cdf = np.cumsum(w).astype(np.int64)
+    return w, cdf, int(cdf[-1])
+
+
+class ForwardWalker(Walker):
+    """Forward-mode walks (Eq. 5): tables of A^T, starts drawn ~ |v|."""
+
+    def __init__(self, a, t: float, v: np.ndarray, seed: int, precision: int = FP64,
+                 max_jumps: int = 1 << 30, h=None, alpha: float = 0.1):
+        b = transpose(a)
+        tables = build_tables(b, t, h, alpha) if h is not None else build_tables(b, t)
+        super().__init__(b, t, v, seed, precision=precision, max_jumps=max_jumps, tables=tables)
+        self.w, self.cdf, self.W = start_weights(v)
+
+    def walks_fwd(self, g0: int, count: int, level: int, coarse: bool) -> np.ndarray:
+        out = np.zeros(count, dtype=WALK_DTYPE)
+        lib().orc_walk_fwd_many(ct.byref(self.ctx), _p(self.cdf), _p(self.w), ct.c_uint64(self.W),
+                                ct.c_uint64(g0), count, level, int(coarse), _p(out))
+        return out
+
+    def mlmcl_fwd(self, level: int, coarse: bool, g0: int, count: int):
+        sum_x = np.zeros(self.tables.n)
+        sum_y2 = np.zeros(1)
+        jumps = np.zeros(1, dtype=np.int64)
+        lim = np.zeros(1, dtype=np.int64)
+        lib().orc_mlmcl_fwd(ct.byref(self.ctx), _p(self.cdf), _p(self.w), ct.c_uint64(self.W),
+                            ct.c_uint64(g0), count, level, int(coarse), _p(sum_x), _p(sum_y2),
+                            _p(jumps), _p(lim))
+        return sum_x, float(sum_y2[0]), int(jumps[0]), int(lim[0])

@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmlmc.so")
 SOURCES = ["mlmc_abi.cu", "mlmc_tables.cu", "mlmc_walk.cu", "mlmc_reduce.cu", "mlmc_noalloc.cu",
-           "mlmc_batch.cu", "mlmc_mlp.cu"]
+           "mlmc_batch.cu", "mlmc_mlp.cu",
+           "mlmc_forward.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(HERE, "..", "include")]

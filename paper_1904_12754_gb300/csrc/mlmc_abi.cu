@@ -80,6 +80,9 @@ void free_plan(mlmc_plan* p) {
   cudaFree(p->d_x);
   cudaFree(p->d_norm2);
   cudaFree(p->d_sumpair);
+  cudaFree(p->d_wstart);
+  cudaFree(p->d_cdf);
+  cudaFree(p->d_scan_tmp);
   if (!p->levels.empty()) cudaFree(p->levels[0].sum_y);
   for (auto& L : p->levels) {
     if (L.ev0) cudaEventDestroy(L.ev0);
@@ -116,6 +119,25 @@ struct HostLevel {
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 
+static bool forward_mode(const mlmc_plan* p) { return p->sched.mode == MLMC_FORWARD; }
+
+// Forward mode: start weights and prefix sums for v (device), W read back.
+static mlmc_status prepare_starts(mlmc_plan* p, const double* v) {
+  MLMC_CUDA(launch_start_table(p, v, p->d_wstart, p->d_cdf, p->d_scan_tmp,
+                               reinterpret_cast<unsigned long long*>(p->d_norm2 + 2)),
+            "start table");
+  int64_t W = 0;
+  MLMC_CUDA(cudaMemcpyAsync(&W, p->d_cdf + (p->n - 1), sizeof(int64_t), cudaMemcpyDeviceToHost,
+                            p->stream), "read W");
+  MLMC_CUDA(cudaStreamSynchronize(p->stream), "synchronize");
+  p->start_total = static_cast<unsigned long long>(W);
+  return MLMC_OK;
+}
+
+static cudaError_t launch_any(mlmc_plan* p, const WalkLaunch& w, int64_t* nl) {
+  return forward_mode(p) ? launch_walk_forward(p, w, nl) : launch_walk(p, w, nl);
+}
+
 // Per-level device scalars live at d_totals[slot * kTotSlots].
 static double* totals_of(mlmc_plan* p, int slot) { return p->d_totals + slot * kTotSlots; }
 
@@ -128,7 +150,7 @@ static mlmc_status run_level(mlmc_plan* p, int slot, int64_t extra, uint64_t see
                              std::chrono::steady_clock::time_point deadline, bool* stopped) {
   constexpr int64_t kBatchWalks = int64_t{1} << 36;  // ~0.5-1 s of FP32 walks
   LevelAcc& L = p->levels[slot];
-  const int64_t rows = p->ctl_row_count < 0 ? p->n : p->ctl_row_count;
+  const int64_t rows = forward_mode(p) ? 1 : (p->ctl_row_count < 0 ? p->n : p->ctl_row_count);
   const int64_t batch_reps = std::max<int64_t>(32, kBatchWalks / rows);
   if (stopped) *stopped = false;
   for (int64_t done = 0; done < extra;) {
@@ -146,7 +168,7 @@ static mlmc_status run_level(mlmc_plan* p, int slot, int64_t extra, uint64_t see
     w.totals = totals_of(p, slot);
     int64_t nl = 0;
     MLMC_CUDA(cudaEventRecord(L.ev0, p->stream), "event record");
-    MLMC_CUDA(launch_walk(p, w, &nl), "walk kernel launch");
+    MLMC_CUDA(launch_any(p, w, &nl), "walk kernel launch");
     MLMC_CUDA(cudaEventRecord(L.ev1, p->stream), "event record");
     L.launches += nl;
     L.reps += reps;
@@ -205,14 +227,25 @@ static mlmc_status collect(mlmc_plan* p, int nl, std::vector<HostLevel>& out, do
   return MLMC_OK;
 }
 
-static double level_var(const mlmc_plan* p, int k, const HostLevel& h) {
+// The controller's three targets: the vector x (FULL, error in the 2-norm),
+// one entry x_row (ENTRY: only that row walks), or the scalar 1^T x (SUM).
+enum Target { kFull = 0, kEntry = 1, kSum = 2 };
+
+// Unbiased V_l of one sample's contribution to the target.  Backward mode:
+// rows are independent, so sum_i Var(Y_i) = (sum Y^2 - ||S||^2/M)/(M-1) for
+// every target.  Forward mode: one walk adds y to a single entry, so the
+// vector target uses the same expression while the scalar target 1^T x has
+// Var(y) = (sum Y^2 - (sum_i S_i)^2/M)/(M-1).
+static double level_var(const mlmc_plan* p, int k, const HostLevel& h, Target target) {
   const double m = static_cast<double>(p->levels[k].reps);
   if (m < 2) return 0.0;
-  return std::max(0.0, (h.y2 - h.sumsq / m) / (m - 1.0));
+  const double sq = (p->sched.mode == MLMC_FORWARD && target == kSum) ? h.sum * h.sum : h.sumsq;
+  return std::max(0.0, (h.y2 - sq / m) / (m - 1.0));
 }
 
 static double level_cost(const mlmc_plan* p, const HostLevel& h) {
   const double per_walk = h.walks > 0 ? 1.0 + h.jumps / h.walks : 1.0;
+  if (forward_mode(p)) return per_walk;  // one sample = one walk
   return static_cast<double>(p->ctl_row_count < 0 ? p->n : p->ctl_row_count) * per_walk;
 }
 
@@ -262,7 +295,8 @@ mlmc_status mlmc_plan_create(mlmc_plan** out, int64_t n, int64_t nnz, const int6
     return fail(MLMC_ERR_INVALID_ARG, "need 1 <= num_levels <= max_levels <= 32");
   if (s.precision != MLMC_FP64 && s.precision != MLMC_FP32_KAHAN)
     return fail(MLMC_ERR_INVALID_ARG, "unknown precision");
-  if (s.mode != MLMC_BACKWARD) return fail(MLMC_ERR_INVALID_ARG, "only MLMC_BACKWARD is available");
+  if (s.mode != MLMC_BACKWARD && s.mode != MLMC_FORWARD)
+    return fail(MLMC_ERR_INVALID_ARG, "mode must be MLMC_BACKWARD or MLMC_FORWARD");
   if (s.proposal != MLMC_PLAIN)
     return fail(MLMC_ERR_INVALID_ARG,
                 "create the plan with MLMC_PLAIN; a proposal is set by mlmc_plan_set_proposal");
@@ -337,6 +371,32 @@ mlmc_status mlmc_plan_create(mlmc_plan** out, int64_t n, int64_t nnz, const int6
     if (st != MLMC_OK) return bail(st);
   }
   if (flags) return bail(fail(MLMC_ERR_INVALID_ARG, "invalid CSR:" + flag_text(flags)));
+  if (s.mode == MLMC_FORWARD) {
+    // Forward mode walks on B = A^T: transpose on the device and keep B as
+    // the plan's matrix (tables, proposals and features are built from it).
+    int64_t* rp_t = nullptr;
+    int32_t* col_t = nullptr;
+    double* val_t = nullptr;
+    int64_t* work = nullptr;
+    const int64_t scan_tmp = n / 256 + 64;
+    PLAN_CUDA(dev_alloc(&rp_t, n + 1), "alloc transpose");
+    PLAN_CUDA(dev_alloc(&col_t, nnz), "alloc transpose");
+    PLAN_CUDA(dev_alloc(&val_t, nnz), "alloc transpose");
+    PLAN_CUDA(dev_alloc(&work, 2 * n + scan_tmp), "alloc transpose");
+    cudaError_t terr = launch_transpose(p, p->d_row_ptr, p->d_col, p->d_val, rp_t, col_t, val_t, work);
+    if (terr == cudaSuccess) terr = cudaStreamSynchronize(p->stream);
+    cudaFree(work);
+    cudaFree(p->d_row_ptr);
+    cudaFree(p->d_col);
+    cudaFree(p->d_val);
+    p->d_row_ptr = rp_t;
+    p->d_col = col_t;
+    p->d_val = val_t;
+    if (terr != cudaSuccess) return bail(cuda_fail(terr, "transpose"));
+    PLAN_CUDA(dev_alloc(&p->d_wstart, n), "alloc start weights");
+    PLAN_CUDA(dev_alloc(&p->d_cdf, n), "alloc start cdf");
+    PLAN_CUDA(dev_alloc(&p->d_scan_tmp, scan_tmp), "alloc scan scratch");
+  }
   mlmc_status st = mlmc_plan_rebuild(p);
   if (st != MLMC_OK) return bail(st);
   unsigned long long bits = 0;
@@ -455,7 +515,11 @@ mlmc_status mlmc_mlmcl(mlmc_plan* p, int32_t level, int32_t coarse, int64_t rep_
   w.v = v;
   w.sum_y = sum_y;
   w.totals = totals;
-  MLMC_CUDA(launch_walk(p, w), "walk kernel launch");
+  if (forward_mode(p)) {
+    mlmc_status sst = prepare_starts(p, v);
+    if (sst != MLMC_OK) return sst;
+  }
+  MLMC_CUDA(launch_any(p, w, nullptr), "walk kernel launch");
   return MLMC_OK;
 }
 
@@ -479,18 +543,23 @@ mlmc_status mlmc_trace(mlmc_plan* p, int32_t level, int32_t coarse, int64_t rep_
   w.sum_y = scratch;
   w.totals = scratch + p->n;
   w.trace = rec;
-  if (err == cudaSuccess) err = launch_walk(p, w);
+  if (err == cudaSuccess && forward_mode(p)) {
+    mlmc_status sst = prepare_starts(p, v);
+    if (sst != MLMC_OK) {
+      cudaFree(scratch);
+      return sst;
+    }
+  }
+  if (err == cudaSuccess) err = launch_any(p, w, nullptr);
   if (err == cudaSuccess) err = cudaStreamSynchronize(p->stream);
   cudaFree(scratch);
   if (err != cudaSuccess) return cuda_fail(err, "trace launch");
   return MLMC_OK;
 }
 
-// The controller of Algorithm 1 for one of three targets: the vector x
-// (FULL, error in the 2-norm), one entry x_row (ENTRY: only that row walks),
-// or the scalar 1^T x (SUM).  All three share V_l (rows are independent);
-// they differ in the norm that sets eps and in the bias test.
-enum Target { kFull = 0, kEntry = 1, kSum = 2 };
+// The controller of Algorithm 1 for one of three targets (Target above).
+// They differ in the norm that sets eps, in the bias test and, in forward
+// mode, in V_l.
 
 static mlmc_status controller(mlmc_plan* p, const double* v, double* x, double* scalar,
                               uint64_t seed, Target target) {
@@ -510,12 +579,21 @@ static mlmc_status controller(mlmc_plan* p, const double* v, double* x, double* 
   }
   std::vector<char> timed(s.max_levels, 0);
   int nl = s.num_levels;
+  // Forward mode counts walks, not walks per row: the pilot and the budget
+  // are scaled by n so that both modes spend the same effort.
+  const int64_t unit = forward_mode(p) ? p->n : 1;
+  const int64_t pilot = s.pilot_walks * unit;
+  const double max_reps = static_cast<double>(s.max_walks_per_row) * static_cast<double>(unit);
+  if (forward_mode(p)) {
+    mlmc_status sst = prepare_starts(p, p->d_v);
+    if (sst != MLMC_OK) return sst;
+  }
   mlmc_status st = MLMC_OK;
   const auto deadline = t_start + std::chrono::duration_cast<std::chrono::steady_clock::duration>(
                                       std::chrono::duration<double>(s.time_budget_s));
   bool out_of_time = false;
   for (int k = 0; k < nl && st == MLMC_OK; ++k)
-    st = run_level(p, k, s.pilot_walks, seed, timed, deadline, nullptr);
+    st = run_level(p, k, pilot, seed, timed, deadline, nullptr);
   if (st != MLMC_OK) return st;
 
   std::vector<HostLevel> h;
@@ -535,7 +613,7 @@ static mlmc_status controller(mlmc_plan* p, const double* v, double* x, double* 
     std::vector<double> V(nl), C(nl);
     double root_sum = 0.0;
     for (int k = 0; k < nl; ++k) {
-      V[k] = level_var(p, k, h[k]);
+      V[k] = level_var(p, k, h[k], target);
       C[k] = level_cost(p, h[k]);
       root_sum += std::sqrt(V[k] * C[k]);
     }
@@ -544,7 +622,7 @@ static mlmc_status controller(mlmc_plan* p, const double* v, double* x, double* 
       for (int k = 0; k < nl; ++k) {
         if (V[k] <= 0.0) continue;
         double target = std::ceil(2.0 / (eps * eps) * std::sqrt(V[k] / C[k]) * root_sum);
-        target = std::min(target, static_cast<double>(s.max_walks_per_row));
+        target = std::min(target, max_reps);
         const int64_t want = static_cast<int64_t>(target);
         if (want > p->levels[k].reps) {
           if ((st = run_level(p, k, want - p->levels[k].reps, seed, timed, deadline,
@@ -560,7 +638,7 @@ static mlmc_status controller(mlmc_plan* p, const double* v, double* x, double* 
       eps = p->rel_tol * size_of_x();
     }
     double var = 0.0;
-    for (int k = 0; k < nl; ++k) var += level_var(p, k, h[k]) / static_cast<double>(p->levels[k].reps);
+    for (int k = 0; k < nl; ++k) var += level_var(p, k, h[k], target) / static_cast<double>(p->levels[k].reps);
     auto mnorm = [&](int k) {
       const double m = static_cast<double>(p->levels[k].reps);
       return (target == kFull ? std::sqrt(h[k].sumsq) : std::fabs(h[k].sum)) / m;
@@ -576,14 +654,15 @@ static mlmc_status controller(mlmc_plan* p, const double* v, double* x, double* 
     }
     if (out_of_time || std::chrono::steady_clock::now() > deadline) break;
     if (!bias_ok && nl < s.max_levels) {
-      if ((st = run_level(p, nl, s.pilot_walks, seed, timed, deadline, nullptr)) != MLMC_OK)
+      if ((st = run_level(p, nl, pilot, seed, timed, deadline, nullptr)) != MLMC_OK)
         return st;
       ++nl;
       continue;
     }
     bool capped = true;
     for (int k = 0; k < nl; ++k)
-      if (level_var(p, k, h[k]) > 0.0 && p->levels[k].reps < s.max_walks_per_row) capped = false;
+      if (level_var(p, k, h[k], target) > 0.0 && static_cast<double>(p->levels[k].reps) < max_reps)
+        capped = false;
     if (capped || !bias_ok) break;
   }
   if (!converged) result = fail(MLMC_ERR_NOT_CONVERGED, "budget exhausted before the tolerance");
@@ -606,7 +685,7 @@ static mlmc_status controller(mlmc_plan* p, const double* v, double* x, double* 
     ls.walks_per_row = p->levels[k].reps;
     const double m = static_cast<double>(p->levels[k].reps);
     ls.mean_norm2 = h[k].sumsq / (m * m);
-    ls.var = level_var(p, k, h[k]);
+    ls.var = level_var(p, k, h[k], target);
     ls.cost_events_per_walk = h[k].walks > 0 ? 1.0 + h[k].jumps / h[k].walks : 1.0;
     ls.jumps = static_cast<int64_t>(h[k].jumps);
     ls.seconds = p->levels[k].seconds;
@@ -631,6 +710,8 @@ mlmc_status mlmc_expmv_entry(mlmc_plan* p, int64_t i, const double* v, double* x
   g_last_error.clear();
   if (!p || !v || !xi) return fail(MLMC_ERR_INVALID_ARG, "NULL argument");
   if (i < 0 || i >= p->n) return fail(MLMC_ERR_INVALID_ARG, "row index out of range");
+  if (forward_mode(p))
+    return fail(MLMC_ERR_INVALID_ARG, "mlmc_expmv_entry needs an MLMC_BACKWARD plan");
   p->ctl_row_begin = i;
   p->ctl_row_count = 1;
   const mlmc_status st = controller(p, v, nullptr, xi, seed, kEntry);

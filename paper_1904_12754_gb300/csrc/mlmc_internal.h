@@ -115,6 +115,12 @@ struct mlmc_plan {
   // Importance-sampling proposal (mlmc_plan_set_proposal): when active the
   // walks use d_alias_is and carry log(k/q) in their exponent.
   mlmc::AliasEntryIS* d_alias_is = nullptr;
+  // Forward mode (the tables above are then built from A^T): start weights,
+  // their prefix sums and total, scan scratch.
+  int64_t* d_wstart = nullptr;
+  int64_t* d_cdf = nullptr;
+  int64_t* d_scan_tmp = nullptr;
+  unsigned long long start_total = 0;
   float* d_h = nullptr;
   double alpha = 0.0;
   bool proposal_active = false;
@@ -150,6 +156,13 @@ cudaError_t launch_build_is_tables(mlmc_plan* p);
 // Walk kernels (mlmc_walk.cu).  Splits the replica range into launches of at
 // most about 2^31 walks; returns the number of launches in *launches.
 cudaError_t launch_walk(mlmc_plan* p, const WalkLaunch& w, int64_t* launches = nullptr);
+// Forward-mode walks (mlmc_walk.cu) and their set-up (mlmc_forward.cu).
+cudaError_t launch_walk_forward(mlmc_plan* p, const WalkLaunch& w, int64_t* launches = nullptr);
+cudaError_t launch_transpose(mlmc_plan* p, const int64_t* rp, const int32_t* col, const double* val,
+                             int64_t* rp_t, int32_t* col_t, double* val_t, int64_t* work);
+cudaError_t launch_start_table(mlmc_plan* p, const double* v, int64_t* w, int64_t* cdf,
+                               int64_t* tmp, unsigned long long* vmax_bits);
+cudaError_t scan_int64(mlmc_plan* p, int64_t n, const int64_t* in, int64_t* out, int64_t* tmp);
 // As launch_walk, with the work counter and the FP32 copy of v in the given
 // device memory instead of the plan's buffers.
 cudaError_t launch_walk_scratch(mlmc_plan* p, const WalkLaunch& w, unsigned long long* work,

@@ -705,6 +705,10 @@ mlmc_status mlmc_learn_proposal(mlmc_plan* p, mlmc_mlp* m, const double* v, uint
                                 int64_t pilot_walks, int32_t steps, int32_t batch, float lr,
                                 double alpha, float* final_loss) {
   if (!p || !m || !v || pilot_walks < 1) return mfail(MLMC_ERR_INVALID_ARG, "mlmc_learn_proposal: bad argument");
+  // The targets are backward value estimates (x-hat per start row); a
+  // forward walk's value would be the adjoint problem's.
+  if (p->sched.mode != MLMC_BACKWARD)
+    return mfail(MLMC_ERR_INVALID_ARG, "mlmc_learn_proposal: backward-mode plans only");
   const bool was = p->proposal_active;
   p->proposal_active = false;  // the pilot uses the paper's jump law
   double* sums = nullptr;

@@ -55,6 +55,8 @@ extern "C" mlmc_status mlmc_trace_noalloc(mlmc_plan* p, int32_t level, int32_t c
                         "mlmc_trace_noalloc: level must be in [0,24] (>= 1 when coarse)");
   if (rep_begin < 0 || reps < 0 || rep_begin + reps > (int64_t{1} << 56))
     return noalloc_fail(MLMC_ERR_INVALID_ARG, "mlmc_trace_noalloc: replica range out of [0, 2^56)");
+  if (p->sched.mode == MLMC_FORWARD)
+    return noalloc_fail(MLMC_ERR_INVALID_ARG, "mlmc_trace_noalloc: backward-mode plans only");
   if (p->n > kNoAllocMaxRows)
     return noalloc_fail(MLMC_ERR_INVALID_ARG,
                         "mlmc_trace_noalloc: n = " + std::to_string(p->n) +

@@ -534,6 +534,212 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4)
   if (cur >= 0) flush_totals(tot, pb.totals + static_cast<int64_t>(sg.slot) * kTotSlots, flags, lane);
 }
 
+// ---------------------------------------------------------------------------
+// Forward mode (Eq. 5): walk g starts at s ~ w_s / W (integer weights, see
+// mlmc_forward.cu), runs on the tables of B = A^T, and adds
+// y = (v_s W / w_s) sign e^{E} (level l0) or ... e^{E_c} expm1(E_f - E_c)
+// (above l0) to x[end].  Counter words: (g bits 0-31, g bits 32-63, draw
+// index, level | 1 << 6); the start draw uses draw index 0xFFFFFFFF.  Lanes
+// that end in the same iteration on the same state add their values with
+// one atomic (match_any + shuffles).
+// ---------------------------------------------------------------------------
+struct FwdArgs {
+  const void* meta;
+  const void* alias;
+  const double* v;              // right-hand side (start weights use FP64 v)
+  const int64_t* cdf;           // inclusive prefix sums of the integer weights
+  const int64_t* w;             // integer weights
+  int64_t n;
+  unsigned long long W;         // cdf[n-1]
+  int64_t walk_begin;
+  int64_t walks;
+  int64_t chunk;
+  unsigned long long total_items;
+  int level;
+  uint32_t ctr3;                // level | 1 << 6
+  uint32_t key0, key1;
+  int64_t max_jumps;
+  double* sum_x;
+  double* totals;
+  uint32_t* flags;
+  unsigned long long* work;
+  mlmc_walk_record* trace;      // index g - walk_begin
+};
+
+template <bool FP64, bool COARSE, bool TRACE, bool IS>
+__global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk_fwd(FwdArgs a) {
+  using P = Prec<FP64>;
+  using T = typename P::T;
+  using Meta = typename P::Meta;
+  const Meta* __restrict__ meta = static_cast<const Meta*>(a.meta);
+  const int lane = threadIdx.x & 31;
+  const int n_grid = 1 << a.level;
+  const T n_fine = P::from_int(n_grid);
+  const T inv_n = static_cast<T>(1.0 / n_grid);
+  const int n_coarse = n_grid >> 1;
+  WalkTotals<T> tot;
+  for (;;) {
+    unsigned long long item = 0;
+    if (lane == 0) item = atomicAdd(a.work, 1ull);
+    item = __shfl_sync(kFull, item, 0);
+    if (item >= a.total_items) break;
+    const int64_t w_lo = static_cast<int64_t>(item) * a.chunk;
+    const uint32_t span = static_cast<uint32_t>(min(a.chunk, a.walks - w_lo));
+    if (lane == 0) tot.walks += span;
+    uint32_t next = 32;
+    uint32_t r = static_cast<uint32_t>(lane);
+    bool live = r < span;
+    Kahan<T> acc_unused;
+    uint32_t item_jumps = 0;
+    // Walk state.
+    uint64_t g = 0;
+    Meta m{};
+    int32_t j = 0;
+    T dl0 = 0, f = 0;
+    uint32_t e = 0, neg = 0;
+    T s = 0, acc = 0, acc_d = 0, lw = 0;
+    int kprev = -1;
+    int32_t start = 0;
+    uint32_t hash = 2166136261u;
+    auto begin_walk = [&]() {
+      g = static_cast<uint64_t>(a.walk_begin + w_lo + r);
+      const uint4 x = philox4x32_10(make_uint4(static_cast<uint32_t>(g), static_cast<uint32_t>(g >> 32),
+                                               0xFFFFFFFFu, a.ctr3),
+                                    a.key0, a.key1);
+      const unsigned long long u = (static_cast<unsigned long long>(x.x) << 32) | x.y;
+      const unsigned long long rr = __umul64hi(u, a.W);
+      int64_t lo = 0, hi = a.n - 1;  // smallest index with cdf > rr
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (static_cast<unsigned long long>(__ldg(a.cdf + mid)) > rr) hi = mid; else lo = mid + 1;
+      }
+      start = static_cast<int32_t>(lo);
+      j = start;
+      m = load_meta(meta, j);
+      dl0 = static_cast<T>(m.dl);
+      const double fd = __ldg(a.v + j) * (static_cast<double>(a.W) / static_cast<double>(__ldg(a.w + j)));
+      f = static_cast<T>(fd);
+      e = 0;
+      neg = 0;
+      s = 0;
+      acc = 0;
+      acc_d = 0;
+      lw = 0;
+      kprev = -1;
+      hash = 2166136261u;
+    };
+    if (live) begin_walk();
+    while (__any_sync(kFull, live)) {
+      bool fin = false;
+      T y = 0;
+      if (live) {
+        const uint4 x = philox4x32_10(
+            make_uint4(static_cast<uint32_t>(g), static_cast<uint32_t>(g >> 32), e, a.ctr3), a.key0, a.key1);
+        const T hold = P::mul(P::neglog(P::uniform(x)), static_cast<T>(m.inv_rate));
+        const T s_new = P::add(s, hold);
+        bool done = !(s_new < static_cast<T>(1));
+        int status = 0;
+        if (!done && static_cast<int64_t>(e) >= a.max_jumps) {
+          done = true;
+          status = 1;
+        }
+        if (!done) {
+          const int gi = P::floor_int(P::mul(s_new, n_fine));
+          const T dlj = static_cast<T>(m.dl);
+          if (COARSE) {
+            const int kc_prev = kprev >> 1;
+            acc = P::fma(P::from_int((gi >> 1) - kc_prev), dlj, acc);
+            acc_d = P::fma(P::from_int((gi & 1) - (kprev & 1)), dlj, acc_d);
+          } else {
+            acc = P::fma(P::from_int(gi - kprev), dlj, acc);
+          }
+          kprev = gi;
+          const uint32_t bucket = __umulhi(x.z, static_cast<uint32_t>(m.deg));
+          uint32_t pick;
+          if (IS) {
+            const uint4* ep = reinterpret_cast<const uint4*>(
+                static_cast<const AliasEntryIS*>(a.alias) + m.start + bucket);
+            const uint4 e0 = __ldg(ep);
+            const uint2 e1 = __ldg(reinterpret_cast<const uint2*>(ep + 1));
+            const bool keep = x.w < e0.x;
+            pick = keep ? e0.y : e0.z;
+            lw = P::add(lw, static_cast<T>(__uint_as_float(keep ? e1.x : e1.y)));
+          } else {
+            const uint4 ent = __ldg(reinterpret_cast<const uint4*>(
+                                        static_cast<const AliasEntry*>(a.alias) + m.start) + bucket);
+            pick = (x.w < ent.x) ? ent.y : ent.z;
+          }
+          neg ^= pick >> 31;
+          j = static_cast<int32_t>(pick & kColMask);
+          if (TRACE) hash = (hash ^ static_cast<uint32_t>(j)) * 16777619u;
+          m = load_meta(meta, j);
+          s = s_new;
+          ++e;
+        } else {
+          fin = true;
+          if (status == 0) {
+            const T dle = static_cast<T>(m.dl);
+            const T h = P::mul(P::add(dl0, dle), static_cast<T>(0.5));
+            if (COARSE) {
+              if (e != 0) {
+                const T acc_c = P::fma(P::from_int(n_coarse - (kprev >> 1)), dle, acc);
+                const T accd = P::fma(P::from_int(-(kprev & 1)), dle, acc_d);
+                const T ec = P::mul(P::sub(acc_c, h), P::mul(inv_n, static_cast<T>(2)));
+                const T diff = P::mul(P::add(accd, h), inv_n);
+                y = P::mul(f, P::mul(P::ex(IS ? P::add(ec, lw) : ec), P::exm1(diff)));
+              }
+            } else {
+              const T acc_f = P::fma(P::from_int(n_grid - kprev), dle, acc);
+              const T ef = P::mul(P::sub(acc_f, h), inv_n);
+              y = P::mul(f, P::ex(IS ? P::add(ef, lw) : ef));
+            }
+            if (neg) y = -y;
+            if (!isfinite(y)) {
+              tot.bad |= kFlagNonFiniteY;
+              y = 0;
+            }
+          } else {
+            tot.bad |= kFlagWalkLimit;
+            ++tot.limit;
+          }
+          if (e == 0) ++tot.still;
+          tot.y2.add_square(y);
+          item_jumps += e;
+          if (TRACE) {
+            mlmc_walk_record rec;
+            rec.end = j;
+            rec.jumps = static_cast<int32_t>(e);
+            rec.sign = neg ? -1 : 1;
+            rec.hash = hash;
+            rec.y = static_cast<double>(y);
+            rec.status = status;
+            rec.pad = start;
+            a.trace[g - a.walk_begin] = rec;
+          }
+        }
+      }
+      const unsigned fmask = __ballot_sync(kFull, fin);
+      if (fin) {
+        // Add y to x[end], one atomic per distinct end state of the warp.
+        const unsigned peers = __match_any_sync(fmask, j);
+        double total = 0.0;
+        for (unsigned mm = peers; mm; mm &= mm - 1) {
+          const int src = __ffs(mm) - 1;
+          total += __shfl_sync(peers, static_cast<double>(y), src);
+        }
+        if (lane == __ffs(peers) - 1 && total != 0.0) atomicAdd(a.sum_x + j, total);
+        r = next + static_cast<uint32_t>(__popc(fmask & ((1u << lane) - 1u)));
+        live = r < span;
+        if (live) begin_walk();
+      }
+      next += static_cast<uint32_t>(__popc(fmask));
+    }
+    tot.jumps += item_jumps;
+    (void)acc_unused;
+  }
+  flush_totals(tot, a.totals, a.flags, lane);
+}
+
 __global__ void k_to_float(int64_t n, const double* __restrict__ in, float* __restrict__ out) {
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x)
@@ -581,7 +787,82 @@ cudaError_t dispatch_walk(mlmc_plan* p, const WalkArgs& a, int block, bool fp64,
   return trace ? dispatch_is<false, false, true>(p, a, block, is) : dispatch_is<false, false, false>(p, a, block, is);
 }
 
+template <bool FP64, bool COARSE, bool TRACE, bool IS>
+cudaError_t launch_fwd_one(mlmc_plan* p, const FwdArgs& args, int block) {
+  auto kern = k_walk_fwd<FP64, COARSE, TRACE, IS>;
+  int per_sm = 0;
+  cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, 0);
+  if (err != cudaSuccess) return err;
+  unsigned long long grid = static_cast<unsigned long long>(p->num_sms) * (per_sm > 0 ? per_sm : 1);
+  const unsigned long long need = (args.total_items + block / 32 - 1) / (block / 32);
+  if (need < grid) grid = need;
+  if (grid < 1) grid = 1;
+  kern<<<static_cast<unsigned>(grid), block, 0, p->stream>>>(args);
+  p->launches++;
+  return cudaGetLastError();
+}
+
+template <bool FP64, bool COARSE, bool TRACE>
+cudaError_t fwd_is(mlmc_plan* p, const FwdArgs& a, int block, bool is) {
+  return is ? launch_fwd_one<FP64, COARSE, TRACE, true>(p, a, block)
+            : launch_fwd_one<FP64, COARSE, TRACE, false>(p, a, block);
+}
+
+cudaError_t dispatch_fwd(mlmc_plan* p, const FwdArgs& a, int block, bool fp64, bool coarse,
+                         bool trace, bool is) {
+  if (fp64) {
+    if (coarse) return trace ? fwd_is<true, true, true>(p, a, block, is) : fwd_is<true, true, false>(p, a, block, is);
+    return trace ? fwd_is<true, false, true>(p, a, block, is) : fwd_is<true, false, false>(p, a, block, is);
+  }
+  if (coarse) return trace ? fwd_is<false, true, true>(p, a, block, is) : fwd_is<false, true, false>(p, a, block, is);
+  return trace ? fwd_is<false, false, true>(p, a, block, is) : fwd_is<false, false, false>(p, a, block, is);
+}
+
 }  // namespace
+
+// Forward-mode walks: w.rep_begin = first walk index, w.reps = walks; the
+// start table (cdf, weights, W) must be current for w.v (launch_start_table).
+cudaError_t launch_walk_forward(mlmc_plan* p, const WalkLaunch& w, int64_t* launches) {
+  if (launches) *launches = 0;
+  if (w.reps <= 0 || p->n <= 0) return cudaSuccess;
+  const bool fp64 = p->sched.precision == MLMC_FP64;
+  FwdArgs a{};
+  a.meta = fp64 ? static_cast<const void*>(p->d_meta64) : static_cast<const void*>(p->d_meta32);
+  a.alias = p->proposal_active ? static_cast<const void*>(p->d_alias_is)
+                               : static_cast<const void*>(p->d_alias);
+  a.v = w.v;
+  a.cdf = p->d_cdf;
+  a.w = p->d_wstart;
+  a.n = p->n;
+  a.W = p->start_total;
+  a.level = w.level;
+  a.ctr3 = (static_cast<uint32_t>(w.level) & 0x3Fu) | (1u << 6);
+  a.key0 = static_cast<uint32_t>(w.seed & 0xFFFFFFFFull);
+  a.key1 = static_cast<uint32_t>(w.seed >> 32);
+  a.max_jumps = p->sched.max_jumps_per_walk;
+  a.sum_x = w.sum_y;
+  a.totals = w.totals;
+  a.flags = p->d_flags;
+  a.work = p->d_work;
+  a.trace = w.trace;
+  const int block = p->sched.block_threads > 0 ? p->sched.block_threads : 256;
+  const int64_t per_lane = p->sched.walks_per_lane > 0 ? p->sched.walks_per_lane : 64;
+  a.chunk = 32 * per_lane;
+  const int64_t cap = int64_t{1} << 31;
+  for (int64_t done = 0; done < w.reps; done += cap) {
+    const int64_t walks = std::min(cap, w.reps - done);
+    a.walk_begin = w.rep_begin + done;
+    a.walks = walks;
+    a.total_items = static_cast<unsigned long long>((walks + a.chunk - 1) / a.chunk);
+    if (w.trace) a.trace = w.trace + done;
+    cudaError_t err = cudaMemsetAsync(p->d_work, 0, sizeof(unsigned long long), p->stream);
+    if (err != cudaSuccess) return err;
+    err = dispatch_fwd(p, a, block, fp64, w.coarse, w.trace != nullptr, p->proposal_active);
+    if (err != cudaSuccess) return err;
+    if (launches) ++*launches;
+  }
+  return cudaSuccess;
+}
 
 cudaError_t launch_walk(mlmc_plan* p, const WalkLaunch& w, int64_t* launches) {
   if (launches) *launches = 0;

@@ -185,6 +185,11 @@ class Plan:
                                     ct.byref(sched) if sched is not None else None,
                                     float(rel_tol), ct.c_void_p(stream)))
         self.n, self.nnz = int(n), nnz
+        self.mode = int(sched.mode) if sched is not None else BACKWARD
+
+    def _trace_records(self, reps: int) -> int:
+        # forward mode: one record per walk; backward: one per (row, rep)
+        return reps if self.mode == FORWARD else self.n * reps
 
     @classmethod
     def from_csr(cls, a, t: float, sched: Schedule = None, rel_tol: float = 1e-3,
@@ -260,8 +265,10 @@ class Plan:
                                     ct.c_uint64(seed), _ptr(sum_y), _ptr(totals)))
 
     def trace(self, level: int, coarse: bool, rep_begin: int, reps: int, v, seed: int, rec):
+        """Walk records: backward plans n*reps (row-major by row), forward
+        plans reps (walk rep_begin + k at k, start state in `pad`)."""
         _need(v, 8 * self.n, "v")
-        _need(rec, WALK_RECORD_DTYPE.itemsize * self.n * reps, "rec")
+        _need(rec, WALK_RECORD_DTYPE.itemsize * self._trace_records(reps), "rec")
         _check(self._lib.mlmc_trace(self._h, level, int(coarse), rep_begin, reps, _ptr(v),
                                     ct.c_uint64(seed), _ptr(rec)))
 
