@@ -53,6 +53,19 @@ def _env_rank():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def aggregate_over_ranks(dist, elapsed: float, count: float, device="cpu"):
+    """Whole-job figures of a weak-scaling run: (max elapsed over ranks, sum
+    of counts over ranks).  Without a process group, the rank's own pair."""
+    if dist is None:
+        return float(elapsed), float(count)
+    import torch
+    t = torch.tensor([float(elapsed), float(count)], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(t[1])
+
+
 def _workload():
     import mlmc_inputs as I
     return I.workload_c2()
@@ -287,14 +300,7 @@ def run_ours(args):
 
     total_ms = float(sum(step_ms))
     # whole-job aggregate: sum of events over ranks / max time over ranks
-    if dist is not None:
-        t = torch.tensor([total_ms, float(events)], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        total_ms_all, events_all = float(tmax[0]), float(t[1])
-    else:
-        total_ms_all, events_all = total_ms, float(events)
+    total_ms_all, events_all = aggregate_over_ranks(dist, total_ms, events, "cuda")
     value = events_all / (total_ms_all * 1e-3)
 
     # accuracy of the last step against the FP64 judge (CPU baseline leg)
@@ -317,12 +323,8 @@ def run_ours(args):
     t_e2e = time.perf_counter() - t_e2e
     e2e_value = e2e_events / t_e2e
     log(f"e2e: {t_e2e:.2f} s for {args.steps} step(s)")
-    if dist is not None:
-        t = torch.tensor([t_e2e, float(e2e_events)], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        e2e_value = float(t[1]) / float(tmax[0])
+    t_e2e_all, e2e_events_all = aggregate_over_ranks(dist, t_e2e, e2e_events, "cuda")
+    e2e_value = e2e_events_all / t_e2e_all
 
     peaks, peak_kind = _peaks()
     roof = walk_roofline(level_log, walk_s, clocks, peaks, total_ms)
@@ -430,21 +432,26 @@ def run_ours(args):
 # Walk-kernel roofline: ALU (issue) bound with this workload's tables in L2.
 # Algorithmic operations of the FP32 walk, counted from the kernel source
 # (each integer/FP32 operation, compare, select, load, exp = 1):
-#   every event   97  = Philox4x32-10 60 (10 rounds x 2 mul.hi, 2 mul.lo,
-#                       2 three-input xor) + uniform 4 + -ln(u) 30 + hold 3
+#   Philox draw   60  (10 rounds x 2 wide multiplies, 2 three-input xors, 2 key adds)
+#   holding time  37  (uniform 4, -ln(u) 30, scale + add + compare 3), for
+#                     every event except the first of a walk that never jumps:
+#                     that one is decided by comparing the uniform's index with
+#                     the row's threshold index (2)
 #   every jump    22 (levels above l0) / 15 (l0): grid index, counts, bucket,
 #                 alias gather and select, sign, next-state gather
 #   walk end      31 / 24 for a walk that jumped (exponents, exp/expm1, Kahan
 #                 and pair sums); 1 for a walk that never jumped
 # peak = 152 SMs x 128 lanes x SM clock (one operation per lane per clock).
 # ---------------------------------------------------------------------------
-OPS_EVENT = 97
+OPS_DRAW = 60
+OPS_HOLD = 37
+OPS_STILL_TEST = 2
 OPS_JUMP = {True: 22, False: 15}
 OPS_END_JUMPED = {True: 31, False: 24}
 OPS_END_STILL = 1
 # DRAM bytes of one captured walk launch (ncu, see profiles/); None when the
 # kernel changed after the capture.
-TRAFFIC_CAPTURE = 15625984  # one 4.1e8-walk launch at l0 (profiles/walk_fp32_ba_n1e5_l0.md)
+TRAFFIC_CAPTURE = None
 
 
 def walk_roofline(level_log, walk_s, clocks, peaks, total_ms):
@@ -455,7 +462,8 @@ def walk_roofline(level_log, walk_s, clocks, peaks, total_ms):
         c = lv["coarse"]
         ev = lv["walks"] + lv["jumps"]
         still = lv.get("still_walks", 0)
-        ops += OPS_EVENT * ev + OPS_JUMP[c] * lv["jumps"] + OPS_END_JUMPED[c] * (lv["walks"] - still) \
+        ops += OPS_DRAW * ev + OPS_HOLD * (ev - still) + OPS_STILL_TEST * still \
+            + OPS_JUMP[c] * lv["jumps"] + OPS_END_JUMPED[c] * (lv["walks"] - still) \
             + OPS_END_STILL * still
         events += ev
         launches += lv.get("launches", 0)
@@ -694,6 +702,72 @@ def run_precision_workload(args):
     print(json.dumps(out), flush=True)
 
 
+def run_kernel_workload(args):
+    """The walk kernel alone (Algorithm 2's MLMCL launch, mlmc_mlmcl): the
+    metric's graph and precision, 4096 walks per row at l0 (about 4e8 walks
+    in one launch) and at l0 + 1 (coarse-coupled), each launch timed with
+    CUDA events on the plan's stream after an L2 flush.  This is the burst
+    figure of the dominant kernel and the command the kernel profiles run."""
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_1904_12754_gb300 import mlmc as M
+    w = _workload()
+    stream = torch.cuda.current_stream()
+    sched = M.schedule_default(precision=M.FP32_KAHAN if w.precision == "fp32" else M.FP64)
+    plan = M.Plan.from_csr(w.a, w.t, sched, rel_tol=w.tol, stream=stream.cuda_stream)
+    l0 = plan.info()["l0"]
+    n = w.a.n
+    dv = torch.from_numpy(w.v).cuda()
+    sums = torch.zeros(n, dtype=torch.float64, device="cuda")
+    tot = torch.zeros(5, dtype=torch.float64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    reps = args.kernel_reps
+    res = {}
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.3)
+    for name, level, coarse in (("l0", l0, False), ("l0+1", l0 + 1, True)):
+        for k in range(args.warmup):
+            plan.mlmcl(level, coarse, 0, reps, dv, 11 + k, sums, tot)
+        torch.cuda.synchronize()
+        ms, events, jumps, walks, still = [], 0.0, 0.0, 0.0, 0.0
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            tot.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plan.mlmcl(level, coarse, reps * (k + 1), reps, dv, 1000 + k, sums, tot)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            t = tot.cpu().numpy()
+            jumps += t[1]
+            walks += t[2]
+            still += t[4]
+        events = walks + jumps
+        total_s = 1e-3 * sum(ms)
+        res[name] = {"level": level, "coarse": coarse, "walks_per_row": reps,
+                     "launch_ms": ms, "walks": walks / args.steps, "jumps": jumps / args.steps,
+                     "still_walks": still / args.steps, "events_per_s": events / total_s}
+        log(f"{name}: {statistics.median(ms):.3f} ms per launch, {events / total_s:.4g} events/s")
+    clocks = sampler.stop()
+    peaks, _ = _peaks()
+    lv = [dict(coarse=False, walks=res["l0"]["walks"], jumps=res["l0"]["jumps"],
+               still_walks=res["l0"]["still_walks"], launches=1)]
+    roof = walk_roofline(lv, 1e-3 * statistics.mean(res["l0"]["launch_ms"]), clocks, peaks,
+                         statistics.mean(res["l0"]["launch_ms"]))
+    out = {"metric": "walk kernel alone: walk-steps/s at l0 (one launch, L2 flushed before it)",
+           "value": res["l0"]["events_per_s"], "unit": UNIT, "higher_is_better": True,
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "dtype": "f32",
+           "data": "synthetic",
+           "config": {"workload": w.name, "n": n, "nnz": w.a.nnz, "t": w.t, "l0": l0,
+                      "walks_per_row": reps, "l2": "flushed before each launch"},
+           "levels": res, "roofline": roof, "clocks": clocks}
+    print(json.dumps(out), flush=True)
+    plan.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -704,9 +778,13 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=15.0)
     ap.add_argument("--step-budget", type=float, default=8.0,
                     help="controller wall-clock budget of one step (s)")
-    ap.add_argument("--workload", choices=["tc", "batch", "learned", "precision"], default="tc",
+    ap.add_argument("--workload", choices=["tc", "batch", "learned", "precision", "kernel"],
+                    default="tc",
                     help="tc: the metric's workload (default); batch: batched vs plain; "
-                         "learned: learned proposal vs plain; precision: FP32 vs FP64 walk")
+                         "learned: learned proposal vs plain; precision: FP32 vs FP64 walk; "
+                         "kernel: the walk kernel alone")
+    ap.add_argument("--kernel-reps", type=int, default=4096,
+                    help="walks per row of one launch in --workload kernel")
     ap.add_argument("--tol", type=float, default=1e-2, help="tolerance of --workload batch")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -717,6 +795,8 @@ def main():
         run_learned_workload(args)
     elif args.workload == "precision":
         run_precision_workload(args)
+    elif args.workload == "kernel":
+        run_kernel_workload(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

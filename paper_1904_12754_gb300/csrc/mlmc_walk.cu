@@ -21,9 +21,11 @@
 // the time, words 2-3 the bucket and the alias coin of the jump that ends it.
 //
 // Work decomposition: a warp takes one (row, chunk of walks) item at a time
-// from a global counter; its lanes share the chunk as a pool and a lane whose
-// walk ends takes the next unclaimed one at once (ballot + prefix count), so
-// lanes stay busy although walk lengths are geometric.  Per-row sums are reduced across the warp and added
+// from a global counter.  Its lanes first screen the chunk's walks 32 at a
+// time (first holding time only): walks that never jump are counted, the
+// others go to a per-warp queue in shared memory, from which a lane whose
+// walk ends takes the next one at once, so lanes stay busy although walk
+// lengths are geometric.  Per-row sums are reduced across the warp and added
 // with one FP64 atomic per item; totals are flushed once per warp.
 // The FP32 variant keeps times, exponents and weights in FP32 and sums Y per
 // row with Kahan compensation and sum Y^2 (which sets the sample sizes through
@@ -31,6 +33,7 @@
 // the per-item warp reductions and the atomics.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "mlmc_internal.h"
 
@@ -240,12 +243,72 @@ __device__ __forceinline__ void flush_totals(WalkTotals<T>& t, double* totals, u
   t = WalkTotals<T>();
 }
 
+// Per-warp queue of screened walks that jump at least once: replica offset,
+// the bucket and coin words of the first jump and either the first holding
+// time (FP64) or the Philox word it is drawn from (FP32).  A ring of
+// kQueueCap slots; screening adds at most 32 entries and only while fewer
+// than 32 are queued, so it never holds more than 63.
+constexpr uint32_t kQueueCap = 64;
+template <bool FP64>
+struct WarpQueue {
+  uint32_t r[kQueueCap];
+  uint32_t xz[kQueueCap];
+  uint32_t xw[kQueueCap];
+  typename std::conditional<FP64, double, uint32_t>::type first[kQueueCap];
+};
+constexpr int kMaxWarps = 8;  // blocks of at most 256 threads
+
+// FP32 walks: the largest uniform index i (u = (2i+1) 2^-24, i < 2^23) whose
+// first holding time fl(-ln(u)) / (t L_row) reaches s = 1, or -1 if none.  The
+// holding time is non-increasing in i (the FP32 -ln(u) is strictly
+// decreasing over all 2^23 uniforms, an exhaustive host check of the same
+// arithmetic, and rounding a product with a positive factor is monotone), so
+// a walk never jumps exactly when its index is <= the returned one.  The 32
+// lanes test 32 points of the open interval per round: the passing points
+// form a prefix, and an interval of at most 33 points is settled in one
+// round (5 rounds from 2^23).
+__device__ __forceinline__ int32_t still_index32(float inv_rate, int lane) {
+  int32_t lo = -1, hi = 1 << 23;  // the test holds at lo (or lo = -1), fails at hi (or hi = 2^23)
+  while (hi - lo > 1) {
+    const int64_t width = hi - lo;
+    const int32_t c = lo + static_cast<int32_t>((static_cast<int64_t>(lane + 1) * width) / 33);
+    bool pass;
+    if (c <= lo) {
+      pass = true;
+    } else if (c >= hi) {
+      pass = false;
+    } else {
+      const float u = __fmul_rn(__uint2float_rn(2u * static_cast<uint32_t>(c) + 1u), 0x1p-24f);
+      pass = !(__fmul_rn(neglog32(u), inv_rate) < 1.0f);
+    }
+    const int t = __popc(__ballot_sync(kFull, pass));
+    const int32_t c_last = __shfl_sync(kFull, c, t > 0 ? t - 1 : 0);
+    const int32_t c_first_fail = __shfl_sync(kFull, c, t < 32 ? t : 31);
+    if (t > 0 && c_last > lo) lo = c_last;
+    if (t < 32 && c_first_fail < hi) hi = c_first_fail;
+  }
+  return lo;
+}
+
 // One work item: walks r_lo .. r_hi-1 (replica offsets relative to
-// a.rep_begin) of row `row`, run by the whole warp as a pool.  Adds the
-// item's sum of Y to a.sum_y[row] (one atomic) and its totals to `tot`.
+// a.rep_begin) of row `row`, run by the whole warp in two interleaved stages.
+//   screen  the 32 lanes draw the first holding time of 32 new walks; a walk
+//           whose first time reaches s = 1 never leaves the row (its sample
+//           is the same for every such walk: it is only counted), the others
+//           are queued;
+//   walk    a lane without a walk takes the next queued one, makes its first
+//           jump with the queued draw and continues event by event.
+// Screening runs whenever fewer than 32 walks are queued, so every lane of
+// the walk stage has work while any is left, and walks that never jump (most
+// of them when t L_ii is small) cost one draw at full SIMD width instead of a
+// pass through the jump and end paths.  A walk's draws depend only on its own
+// counter, so the trajectories are those of the walk-by-walk definition.
+// Adds the item's sum of Y to a.sum_y[row] (one atomic) and its totals to
+// `tot`.
 template <bool FP64, bool COARSE, bool TRACE, bool IS>
 __device__ __forceinline__ void walk_item(const ItemArgs& a, int64_t row, int64_t r_lo,
                                           int64_t r_hi, WalkTotals<typename Prec<FP64>::T>& tot,
+                                          WarpQueue<FP64>* __restrict__ q,
                                           int lane) {
   using P = Prec<FP64>;
   using T = typename P::T;
@@ -259,6 +322,8 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, int64_t row, int64_
   const int n_coarse = n_grid >> 1;
   const Meta m0 = load_meta(meta, row);
   const T dl0 = static_cast<T>(m0.dl);
+  const T inv_rate0 = static_cast<T>(m0.inv_rate);
+  const int32_t still_max = FP64 ? 0 : still_index32(static_cast<float>(m0.inv_rate), lane);
   // A walk that never jumps stays at the row for the whole interval: its
   // sample is 0 above l0 and v_row e^{dl_row} at l0 (E_f = dl_row exactly
   // as the grid weights sum to 1), the same for every such walk.
@@ -271,21 +336,17 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, int64_t row, int64_
 
   Kahan<T> acc_y;
   uint32_t item_jumps = 0;  // this lane's jumps in this item (< 2^32)
-  uint32_t n_still = 0;     // this lane's walks without a jump
+  uint32_t n_still = 0;     // walks without a jump screened by this lane
   if (lane == 0) tot.walks += static_cast<unsigned long long>(r_hi - r_lo);
   const uint32_t row32 = static_cast<uint32_t>(row);
   const uint32_t span = static_cast<uint32_t>(r_hi - r_lo);
   const uint64_t rep_base = static_cast<uint64_t>(a.rep_begin + r_lo);
-  // The item's walks form a pool: a lane whose walk ends claims the next
-  // unclaimed replica offset (ballot + prefix count), so lanes stay busy
-  // until the pool is empty.
-  uint32_t next = 32;                        // warp-uniform: next unclaimed offset
-  uint32_t r = static_cast<uint32_t>(lane);  // this lane's replica offset
-  bool live = r < span;
-  // Counter words of the current walk: replica bits 0-31 and word 3.
-  uint32_t c_lo = static_cast<uint32_t>(rep_base + r);
-  uint32_t c_hi = a.ctr3 | (static_cast<uint32_t>((rep_base + r) >> 32) << 8);
+  const unsigned lanes_below = (1u << lane) - 1u;
+  uint32_t screened = 0;           // warp-uniform: walks screened so far
+  uint32_t qhead = 0, qtail = 0;   // warp-uniform queue positions
+  bool live = false;               // this lane holds a walk
   // Walk state.
+  uint32_t r = 0, c_lo = 0, c_hi = 0;  // replica offset and its counter words
   Meta m = m0;
   int32_t j = static_cast<int32_t>(row);
   uint32_t e = 0;          // jumps taken (= Philox draw index)
@@ -297,13 +358,107 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, int64_t row, int64_
   T lw = 0;                // proposal only: sum of log(k/q) over the jumps
   uint32_t hash = 2166136261u;
 
-  while (__any_sync(kFull, live)) {
-    bool fin = false;
+  for (;;) {
+    // Screen the first holding times of the next 32 walks.
+    while (qtail - qhead < 32u && screened < span) {
+      const uint32_t rs = screened + static_cast<uint32_t>(lane);
+      bool push = false;
+      T h1 = 0;
+      uint4 x1 = make_uint4(0u, 0u, 0u, 0u);
+      if (rs < span) {
+        const uint64_t rep = rep_base + rs;
+        x1 = philox4x32_10(make_uint4(static_cast<uint32_t>(rep), row32, 0u,
+                                      a.ctr3 | (static_cast<uint32_t>(rep >> 32) << 8)),
+                           a.key0, a.key1);
+        if (FP64) {
+          h1 = P::mul(P::neglog(P::uniform(x1)), inv_rate0);
+          push = h1 < static_cast<T>(1);
+        } else {
+          push = static_cast<int32_t>(x1.x >> 9) > still_max;  // the uniform's index
+        }
+        if (!push) {
+          ++n_still;
+          if (TRACE) {
+            mlmc_walk_record rec;
+            rec.end = static_cast<int32_t>(row);
+            rec.jumps = 0;
+            rec.sign = 1;
+            rec.hash = 2166136261u;
+            rec.y = static_cast<double>(y_still);
+            rec.status = 0;
+            rec.pad = 0;
+            a.trace[row * a.trace_stride + a.trace_base + (r_lo + rs)] = rec;
+          }
+        }
+      }
+      const unsigned pm = __ballot_sync(kFull, push);
+      if (push) {
+        const uint32_t slot = (qtail + static_cast<uint32_t>(__popc(pm & lanes_below))) & (kQueueCap - 1);
+        q->r[slot] = rs;
+        q->xz[slot] = x1.z;
+        q->xw[slot] = x1.w;
+        if constexpr (FP64) q->first[slot] = h1;
+        else q->first[slot] = x1.x;
+      }
+      qtail += static_cast<uint32_t>(__popc(pm));
+      screened += 32u;
+    }
+    __syncwarp();
+    // Lanes without a walk take queued ones.
+    const unsigned idle = __ballot_sync(kFull, !live);
+    bool popped = false;
+    uint32_t slot = 0;
+    if (!live) {
+      const uint32_t k = qhead + static_cast<uint32_t>(__popc(idle & lanes_below));
+      if (k < qtail) {
+        slot = k & (kQueueCap - 1);
+        r = q->r[slot];
+        popped = true;
+        live = true;
+        const uint64_t rep = rep_base + r;
+        c_lo = static_cast<uint32_t>(rep);
+        c_hi = a.ctr3 | (static_cast<uint32_t>(rep >> 32) << 8);
+        m = m0;
+        j = static_cast<int32_t>(row);
+        e = 0;
+        neg = 0;
+        s = 0;
+        acc = 0;
+        acc_d = 0;
+        kprev = -1;
+        lw = 0;
+        hash = 2166136261u;
+      }
+    }
+    qhead = min(qhead + static_cast<uint32_t>(__popc(idle)), qtail);
+    if (!__any_sync(kFull, live)) break;  // queue empty and every walk screened
     if (live) {
-      const uint4 x = philox4x32_10(make_uint4(c_lo, row32, e, c_hi), a.key0, a.key1);
-      const T hold = P::mul(P::neglog(P::uniform(x)), static_cast<T>(m.inv_rate));
-      const T s_new = P::add(s, hold);
-      bool done = !(s_new < static_cast<T>(1));
+      T s_new;
+      uint32_t xz, xw;
+      bool done;
+      if constexpr (FP64) {
+        if (popped) {
+          // first event: its holding time was drawn at screening
+          s_new = q->first[slot];
+          xz = q->xz[slot];
+          xw = q->xw[slot];
+          done = false;
+        } else {
+          const uint4 x = philox4x32_10(make_uint4(c_lo, row32, e, c_hi), a.key0, a.key1);
+          s_new = P::add(s, P::mul(P::neglog(P::uniform(x)), static_cast<T>(m.inv_rate)));
+          xz = x.z;
+          xw = x.w;
+          done = !(s_new < static_cast<T>(1));
+        }
+      } else {
+        // a first event takes its queued Philox words (s = 0 and m = m0 here)
+        const uint4 x = popped ? make_uint4(q->first[slot], 0u, q->xz[slot], q->xw[slot])
+                               : philox4x32_10(make_uint4(c_lo, row32, e, c_hi), a.key0, a.key1);
+        s_new = P::add(s, P::mul(P::neglog(P::uniform(x)), static_cast<T>(m.inv_rate)));
+        xz = x.z;
+        xw = x.w;
+        done = !(s_new < static_cast<T>(1));
+      }
       int status = 0;
       if (!done && static_cast<int64_t>(e) >= a.max_jumps) {
         done = true;
@@ -321,20 +476,20 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, int64_t row, int64_
           acc = P::fma(P::from_int(g - kprev), dlj, acc);
         }
         kprev = g;
-        const uint32_t bucket = __umulhi(x.z, static_cast<uint32_t>(m.deg));
+        const uint32_t bucket = __umulhi(xz, static_cast<uint32_t>(m.deg));
         uint32_t pick;
         if (IS) {
           const uint4* ep = reinterpret_cast<const uint4*>(
               static_cast<const AliasEntryIS*>(a.alias) + m.start + bucket);
           const uint4 e0 = __ldg(ep);
           const uint2 e1 = __ldg(reinterpret_cast<const uint2*>(ep + 1));
-          const bool keep = x.w < e0.x;
+          const bool keep = xw < e0.x;
           pick = keep ? e0.y : e0.z;
           lw = P::add(lw, static_cast<T>(__uint_as_float(keep ? e1.x : e1.y)));
         } else {
           const uint4 ent = __ldg(reinterpret_cast<const uint4*>(
                                       static_cast<const AliasEntry*>(a.alias) + m.start) + bucket);
-          pick = (x.w < ent.x) ? ent.y : ent.z;
+          pick = (xw < ent.x) ? ent.y : ent.z;
         }
         neg ^= pick >> 31;
         j = static_cast<int32_t>(pick & kColMask);
@@ -342,37 +497,28 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, int64_t row, int64_
         m = load_meta(meta, j);
         s = s_new;
         ++e;
-      } else if (!TRACE && e == 0 && status == 0) {
-        // No jump: the state is still the initial one.
-        ++n_still;
-        fin = true;
       } else {
-        // Walk ends at state j (s = 1).
-        fin = true;
+        // Walk ends at state j (s = 1) after e >= 1 jumps, or at the limit.
         T y = 0;
         if (status == 0) {
-          if (e == 0) {
-            y = y_still;
+          const T dle = static_cast<T>(m.dl);
+          const T h = P::mul(P::add(dl0, dle), static_cast<T>(0.5));
+          const T vend = static_cast<T>(__ldg(vv + j));
+          if (COARSE) {
+            const T acc_c = P::fma(P::from_int(n_coarse - (kprev >> 1)), dle, acc);
+            const T accd = P::fma(P::from_int(-(kprev & 1)), dle, acc_d);
+            const T ec = P::mul(P::sub(acc_c, h), P::mul(inv_n, static_cast<T>(2)));
+            const T diff = P::mul(P::add(accd, h), inv_n);
+            y = P::mul(vend, P::mul(P::ex(IS ? P::add(ec, lw) : ec), P::exm1(diff)));
           } else {
-            const T dle = static_cast<T>(m.dl);
-            const T h = P::mul(P::add(dl0, dle), static_cast<T>(0.5));
-            const T vend = static_cast<T>(__ldg(vv + j));
-            if (COARSE) {
-              const T acc_c = P::fma(P::from_int(n_coarse - (kprev >> 1)), dle, acc);
-              const T accd = P::fma(P::from_int(-(kprev & 1)), dle, acc_d);
-              const T ec = P::mul(P::sub(acc_c, h), P::mul(inv_n, static_cast<T>(2)));
-              const T diff = P::mul(P::add(accd, h), inv_n);
-              y = P::mul(vend, P::mul(P::ex(IS ? P::add(ec, lw) : ec), P::exm1(diff)));
-            } else {
-              const T acc_f = P::fma(P::from_int(n_grid - kprev), dle, acc);
-              const T ef = P::mul(P::sub(acc_f, h), inv_n);
-              y = P::mul(vend, P::ex(IS ? P::add(ef, lw) : ef));
-            }
-            if (neg) y = -y;
-            if (!isfinite(y)) {
-              tot.bad |= kFlagNonFiniteY;
-              y = 0;
-            }
+            const T acc_f = P::fma(P::from_int(n_grid - kprev), dle, acc);
+            const T ef = P::mul(P::sub(acc_f, h), inv_n);
+            y = P::mul(vend, P::ex(IS ? P::add(ef, lw) : ef));
+          }
+          if (neg) y = -y;
+          if (!isfinite(y)) {
+            tot.bad |= kFlagNonFiniteY;
+            y = 0;
           }
         } else {
           tot.bad |= kFlagWalkLimit;
@@ -392,27 +538,10 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, int64_t row, int64_
           rec.pad = 0;
           a.trace[row * a.trace_stride + a.trace_base + (r_lo + r)] = rec;
         }
+        live = false;
       }
     }
-    // Refill: finished lanes take the next walks of the pool.
-    const unsigned fmask = __ballot_sync(kFull, fin);
-    if (fin) {
-      r = next + static_cast<uint32_t>(__popc(fmask & ((1u << lane) - 1u)));
-      live = r < span;
-      c_lo = static_cast<uint32_t>(rep_base + r);
-      c_hi = a.ctr3 | (static_cast<uint32_t>((rep_base + r) >> 32) << 8);
-      m = load_meta(meta, row);
-      j = static_cast<int32_t>(row);
-      e = 0;
-      neg = 0;
-      s = 0;
-      acc = 0;
-      acc_d = 0;
-      kprev = -1;
-      lw = 0;
-      hash = 2166136261u;
-    }
-    next += static_cast<uint32_t>(__popc(fmask));
+    __syncwarp();  // queue slots read above are free before the next screening
   }
   tot.jumps += item_jumps;
   double ys = warp_sum(acc_y);
@@ -444,6 +573,8 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk(WalkArgs a) {
   ia.trace = a.trace;
   ia.trace_stride = a.trace_stride;
   ia.trace_base = a.trace_base;
+  __shared__ WarpQueue<FP64> queues[kMaxWarps];
+  WarpQueue<FP64>* q = &queues[threadIdx.x >> 5];
   WalkTotals<T> tot;
   for (;;) {
     unsigned long long item = 0;
@@ -454,7 +585,7 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk(WalkArgs a) {
     const int64_t chunk = static_cast<int64_t>(item) - rel * a.chunks_per_row;
     const int64_t r_lo = chunk * a.chunk;
     const int64_t r_hi = min(r_lo + a.chunk, a.reps);
-    walk_item<FP64, COARSE, TRACE, IS>(ia, a.row_begin + rel, r_lo, r_hi, tot, lane);
+    walk_item<FP64, COARSE, TRACE, IS>(ia, a.row_begin + rel, r_lo, r_hi, tot, q, lane);
   }
   flush_totals(tot, a.totals, a.flags, lane);
 }
@@ -473,6 +604,8 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4)
   const int lane = threadIdx.x & 31;
   const unsigned long long total = hdr->total_items;
   const int nseg = hdr->segments;
+  __shared__ WarpQueue<FP64> queues[kMaxWarps];
+  WarpQueue<FP64>* q = &queues[threadIdx.x >> 5];
   WalkTotals<T> tot;
   // The warp's current segment; its totals are flushed when the warp's next
   // item falls in another segment (items come in segment order, so a warp
@@ -528,8 +661,8 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4)
     ia.trace = nullptr;
     ia.trace_stride = 0;
     ia.trace_base = 0;
-    if (sg.slot > 0) walk_item<FP64, true, false, false>(ia, row, r_lo, r_hi, tot, lane);
-    else walk_item<FP64, false, false, false>(ia, row, r_lo, r_hi, tot, lane);
+    if (sg.slot > 0) walk_item<FP64, true, false, false>(ia, row, r_lo, r_hi, tot, q, lane);
+    else walk_item<FP64, false, false, false>(ia, row, r_lo, r_hi, tot, q, lane);
   }
   if (cur >= 0) flush_totals(tot, pb.totals + static_cast<int64_t>(sg.slot) * kTotSlots, flags, lane);
 }

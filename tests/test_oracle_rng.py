@@ -91,3 +91,14 @@ def test_exponential_law_of_holding_draws():
     cdf = 1.0 - np.exp(-e)
     ks = np.max(np.abs(cdf - (np.arange(1, e.size + 1) / e.size)))
     assert ks < 1.63 / np.sqrt(e.size)  # alpha = 0.01
+
+
+def test_neglog32_is_strictly_decreasing_over_every_fp32_uniform():
+    # All 2^23 FP32 uniforms u = (2i+1) 2^-24: -ln(u) must decrease with i.
+    # The GPU walk relies on it to decide "the first holding time reaches
+    # s = 1" by comparing i with a per-row threshold index.
+    i = np.arange(1 << 23, dtype=np.float64)
+    u = ((2.0 * i + 1.0) * 2.0 ** -24).astype(np.float32)
+    assert np.all(u.astype(np.float64) == (2.0 * i + 1.0) * 2.0 ** -24)
+    g = W.neglog32(u).astype(np.float64)
+    assert np.all(np.diff(g) < 0)
