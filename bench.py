@@ -714,7 +714,8 @@ def run_kernel_workload(args):
     from paper_1904_12754_gb300 import mlmc as M
     w = _workload()
     stream = torch.cuda.current_stream()
-    sched = M.schedule_default(precision=M.FP32_KAHAN if w.precision == "fp32" else M.FP64)
+    sched = M.schedule_default(precision=M.FP32_KAHAN if w.precision == "fp32" else M.FP64,
+                               walks_per_lane=args.walks_per_lane, block_threads=args.block)
     plan = M.Plan.from_csr(w.a, w.t, sched, rel_tol=w.tol, stream=stream.cuda_stream)
     l0 = plan.info()["l0"]
     n = w.a.n
@@ -762,7 +763,9 @@ def run_kernel_workload(args):
            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "dtype": "f32",
            "data": "synthetic",
            "config": {"workload": w.name, "n": n, "nnz": w.a.nnz, "t": w.t, "l0": l0,
-                      "walks_per_row": reps, "l2": "flushed before each launch"},
+                      "walks_per_row": reps, "l2": "flushed before each launch",
+                      "walks_per_lane": args.walks_per_lane or "default",
+                      "block": args.block or "default"},
            "levels": res, "roofline": roof, "clocks": clocks}
     print(json.dumps(out), flush=True)
     plan.close()
@@ -785,6 +788,10 @@ def main():
                          "kernel: the walk kernel alone")
     ap.add_argument("--kernel-reps", type=int, default=4096,
                     help="walks per row of one launch in --workload kernel")
+    ap.add_argument("--walks-per-lane", type=int, default=0,
+                    help="--workload kernel: walks per lane of one work item (0 = library default)")
+    ap.add_argument("--block", type=int, default=0,
+                    help="--workload kernel: threads per block (0 = library default)")
     ap.add_argument("--tol", type=float, default=1e-2, help="tolerance of --workload batch")
     args = ap.parse_args()
     if args.warmup < 3:

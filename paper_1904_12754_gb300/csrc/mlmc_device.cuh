@@ -84,6 +84,34 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
   return c;
 }
 
+// The ten round keys of one Philox key: (k0 + r W0, k1 + r W1), r = 0..9.  A
+// launch passes them as a constant kernel parameter so that each round xors
+// its key straight from the parameter bank instead of forming it.
+struct PhiloxRoundKeys {
+  uint32_t k0[10];
+  uint32_t k1[10];
+};
+
+__host__ __device__ inline PhiloxRoundKeys philox_round_keys(uint32_t k0, uint32_t k1) {
+  PhiloxRoundKeys rk;
+  for (int r = 0; r < 10; ++r) {
+    rk.k0[r] = k0 + static_cast<uint32_t>(r) * kPhiloxW0;
+    rk.k1[r] = k1 + static_cast<uint32_t>(r) * kPhiloxW1;
+  }
+  return rk;
+}
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const PhiloxRoundKeys& rk) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const unsigned long long p0 = static_cast<unsigned long long>(kPhiloxM0) * c.x;
+    const unsigned long long p1 = static_cast<unsigned long long>(kPhiloxM1) * c.z;
+    c = make_uint4(static_cast<uint32_t>(p1 >> 32) ^ c.y ^ rk.k0[r], static_cast<uint32_t>(p1),
+                   static_cast<uint32_t>(p0 >> 32) ^ c.w ^ rk.k1[r], static_cast<uint32_t>(p0));
+  }
+  return c;
+}
+
 // ---------------------------------------------------------------------------
 // Uniforms in (0,1): odd multiples of 2^-53 (FP64) or 2^-24 (FP32), exact.
 // ---------------------------------------------------------------------------

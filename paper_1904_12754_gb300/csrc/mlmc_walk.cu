@@ -56,6 +56,7 @@ struct WalkArgs {
   int level;
   uint32_t ctr3;           // level | stream << 6
   uint32_t key0, key1;
+  PhiloxRoundKeys rk;      // round keys of (key0, key1)
   int64_t max_jumps;
   double* sum_y;
   double* totals;
@@ -64,6 +65,18 @@ struct WalkArgs {
   mlmc_walk_record* trace;
   int64_t trace_stride;    // records per row (the whole replica range)
   int64_t trace_base;      // offset of this launch's first replica
+};
+
+// Key sources of the walk's draws: the round keys of a launch-constant
+// parameter (single-plan launches), or formed from the key on the fly (the
+// batch kernel, whose key changes with the problem).
+struct KeysFromParam {
+  const PhiloxRoundKeys* rk;
+  __device__ __forceinline__ uint4 draw(uint4 c) const { return philox4x32_10(c, *rk); }
+};
+struct KeysOnTheFly {
+  uint32_t k0, k1;
+  __device__ __forceinline__ uint4 draw(uint4 c) const { return philox4x32_10(c, k0, k1); }
 };
 
 template <bool FP64>
@@ -246,9 +259,9 @@ __device__ __forceinline__ void flush_totals(WalkTotals<T>& t, double* totals, u
 // Per-warp queue of screened walks that jump at least once: replica offset,
 // the bucket and coin words of the first jump and either the first holding
 // time (FP64) or the Philox word it is drawn from (FP32).  A ring of
-// kQueueCap slots; screening adds at most 32 entries and only while fewer
-// than 32 are queued, so it never holds more than 63.
-constexpr uint32_t kQueueCap = 64;
+// kQueueCap slots; a screening round adds at most 64 entries and runs only
+// while fewer than 32 are queued, so it never holds more than 95.
+constexpr uint32_t kQueueCap = 128;
 template <bool FP64>
 struct WarpQueue {
   uint32_t r[kQueueCap];
@@ -292,7 +305,7 @@ __device__ __forceinline__ int32_t still_index32(float inv_rate, int lane) {
 
 // One work item: walks r_lo .. r_hi-1 (replica offsets relative to
 // a.rep_begin) of row `row`, run by the whole warp in two interleaved stages.
-//   screen  the 32 lanes draw the first holding time of 32 new walks; a walk
+//   screen  the 32 lanes draw the first holding time of 64 new walks; a walk
 //           whose first time reaches s = 1 never leaves the row (its sample
 //           is the same for every such walk: it is only counted), the others
 //           are queued;
@@ -305,11 +318,11 @@ __device__ __forceinline__ int32_t still_index32(float inv_rate, int lane) {
 // counter, so the trajectories are those of the walk-by-walk definition.
 // Adds the item's sum of Y to a.sum_y[row] (one atomic) and its totals to
 // `tot`.
-template <bool FP64, bool COARSE, bool TRACE, bool IS>
-__device__ __forceinline__ void walk_item(const ItemArgs& a, int64_t row, int64_t r_lo,
-                                          int64_t r_hi, WalkTotals<typename Prec<FP64>::T>& tot,
-                                          WarpQueue<FP64>* __restrict__ q,
-                                          int lane) {
+template <bool FP64, bool COARSE, bool TRACE, bool IS, class Keys>
+__device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, int64_t row,
+                                          int64_t r_lo, int64_t r_hi,
+                                          WalkTotals<typename Prec<FP64>::T>& tot,
+                                          WarpQueue<FP64>* __restrict__ q, int lane) {
   using P = Prec<FP64>;
   using T = typename P::T;
   using Meta = typename P::Meta;
@@ -359,24 +372,28 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, int64_t row, int64_
   uint32_t hash = 2166136261u;
 
   for (;;) {
-    // Screen the first holding times of the next 32 walks.
+    // Screen the first holding times of the next 64 walks (two per lane:
+    // independent Philox chains that the lane's instructions interleave).
     while (qtail - qhead < 32u && screened < span) {
-      const uint32_t rs = screened + static_cast<uint32_t>(lane);
-      bool push = false;
-      T h1 = 0;
-      uint4 x1 = make_uint4(0u, 0u, 0u, 0u);
-      if (rs < span) {
-        const uint64_t rep = rep_base + rs;
-        x1 = philox4x32_10(make_uint4(static_cast<uint32_t>(rep), row32, 0u,
-                                      a.ctr3 | (static_cast<uint32_t>(rep >> 32) << 8)),
-                           a.key0, a.key1);
+      uint4 x[2];
+      T h1[2] = {0, 0};
+      bool push[2];
+#pragma unroll
+      for (int w = 0; w < 2; ++w) {
+        const uint64_t rep = rep_base + screened + static_cast<uint32_t>(32 * w + lane);
+        x[w] = keys.draw(make_uint4(static_cast<uint32_t>(rep), row32, 0u,
+                                    a.ctr3 | (static_cast<uint32_t>(rep >> 32) << 8)));
+      }
+#pragma unroll
+      for (int w = 0; w < 2; ++w) {
+        const uint32_t rs = screened + static_cast<uint32_t>(32 * w + lane);
         if (FP64) {
-          h1 = P::mul(P::neglog(P::uniform(x1)), inv_rate0);
-          push = h1 < static_cast<T>(1);
+          h1[w] = P::mul(P::neglog(P::uniform(x[w])), inv_rate0);
+          push[w] = rs < span && h1[w] < static_cast<T>(1);
         } else {
-          push = static_cast<int32_t>(x1.x >> 9) > still_max;  // the uniform's index
+          push[w] = rs < span && static_cast<int32_t>(x[w].x >> 9) > still_max;  // uniform index
         }
-        if (!push) {
+        if (rs < span && !push[w]) {
           ++n_still;
           if (TRACE) {
             mlmc_walk_record rec;
@@ -390,18 +407,19 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, int64_t row, int64_
             a.trace[row * a.trace_stride + a.trace_base + (r_lo + rs)] = rec;
           }
         }
+        const unsigned pm = __ballot_sync(kFull, push[w]);
+        if (push[w]) {
+          const uint32_t slot =
+              (qtail + static_cast<uint32_t>(__popc(pm & lanes_below))) & (kQueueCap - 1);
+          q->r[slot] = rs;
+          q->xz[slot] = x[w].z;
+          q->xw[slot] = x[w].w;
+          if constexpr (FP64) q->first[slot] = h1[w];
+          else q->first[slot] = x[w].x;
+        }
+        qtail += static_cast<uint32_t>(__popc(pm));
       }
-      const unsigned pm = __ballot_sync(kFull, push);
-      if (push) {
-        const uint32_t slot = (qtail + static_cast<uint32_t>(__popc(pm & lanes_below))) & (kQueueCap - 1);
-        q->r[slot] = rs;
-        q->xz[slot] = x1.z;
-        q->xw[slot] = x1.w;
-        if constexpr (FP64) q->first[slot] = h1;
-        else q->first[slot] = x1.x;
-      }
-      qtail += static_cast<uint32_t>(__popc(pm));
-      screened += 32u;
+      screened += 64u;
     }
     __syncwarp();
     // Lanes without a walk take queued ones.
@@ -444,7 +462,7 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, int64_t row, int64_
           xw = q->xw[slot];
           done = false;
         } else {
-          const uint4 x = philox4x32_10(make_uint4(c_lo, row32, e, c_hi), a.key0, a.key1);
+          const uint4 x = keys.draw(make_uint4(c_lo, row32, e, c_hi));
           s_new = P::add(s, P::mul(P::neglog(P::uniform(x)), static_cast<T>(m.inv_rate)));
           xz = x.z;
           xw = x.w;
@@ -453,7 +471,7 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, int64_t row, int64_
       } else {
         // a first event takes its queued Philox words (s = 0 and m = m0 here)
         const uint4 x = popped ? make_uint4(q->first[slot], 0u, q->xz[slot], q->xw[slot])
-                               : philox4x32_10(make_uint4(c_lo, row32, e, c_hi), a.key0, a.key1);
+                               : keys.draw(make_uint4(c_lo, row32, e, c_hi));
         s_new = P::add(s, P::mul(P::neglog(P::uniform(x)), static_cast<T>(m.inv_rate)));
         xz = x.z;
         xw = x.w;
@@ -556,7 +574,7 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, int64_t row, int64_
 }
 
 template <bool FP64, bool COARSE, bool TRACE, bool IS>
-__global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk(WalkArgs a) {
+__global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk(const __grid_constant__ WalkArgs a) {
   using T = typename Prec<FP64>::T;
   const int lane = threadIdx.x & 31;
   ItemArgs ia;
@@ -585,7 +603,8 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk(WalkArgs a) {
     const int64_t chunk = static_cast<int64_t>(item) - rel * a.chunks_per_row;
     const int64_t r_lo = chunk * a.chunk;
     const int64_t r_hi = min(r_lo + a.chunk, a.reps);
-    walk_item<FP64, COARSE, TRACE, IS>(ia, a.row_begin + rel, r_lo, r_hi, tot, q, lane);
+    walk_item<FP64, COARSE, TRACE, IS>(ia, KeysFromParam{&a.rk}, a.row_begin + rel, r_lo, r_hi,
+                                       tot, q, lane);
   }
   flush_totals(tot, a.totals, a.flags, lane);
 }
@@ -661,8 +680,9 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4)
     ia.trace = nullptr;
     ia.trace_stride = 0;
     ia.trace_base = 0;
-    if (sg.slot > 0) walk_item<FP64, true, false, false>(ia, row, r_lo, r_hi, tot, q, lane);
-    else walk_item<FP64, false, false, false>(ia, row, r_lo, r_hi, tot, q, lane);
+    const KeysOnTheFly keys{pb.key0, pb.key1};
+    if (sg.slot > 0) walk_item<FP64, true, false, false>(ia, keys, row, r_lo, r_hi, tot, q, lane);
+    else walk_item<FP64, false, false, false>(ia, keys, row, r_lo, r_hi, tot, q, lane);
   }
   if (cur >= 0) flush_totals(tot, pb.totals + static_cast<int64_t>(sg.slot) * kTotSlots, flags, lane);
 }
@@ -691,6 +711,7 @@ struct FwdArgs {
   int level;
   uint32_t ctr3;                // level | 1 << 6
   uint32_t key0, key1;
+  PhiloxRoundKeys rk;           // round keys of (key0, key1)
   int64_t max_jumps;
   double* sum_x;
   double* totals;
@@ -700,7 +721,7 @@ struct FwdArgs {
 };
 
 template <bool FP64, bool COARSE, bool TRACE, bool IS>
-__global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk_fwd(FwdArgs a) {
+__global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk_fwd(const __grid_constant__ FwdArgs a) {
   using P = Prec<FP64>;
   using T = typename P::T;
   using Meta = typename P::Meta;
@@ -738,7 +759,7 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk_fwd(FwdArgs a) {
       g = static_cast<uint64_t>(a.walk_begin + w_lo + r);
       const uint4 x = philox4x32_10(make_uint4(static_cast<uint32_t>(g), static_cast<uint32_t>(g >> 32),
                                                0xFFFFFFFFu, a.ctr3),
-                                    a.key0, a.key1);
+                                    a.rk);
       const unsigned long long u = (static_cast<unsigned long long>(x.x) << 32) | x.y;
       const unsigned long long rr = __umul64hi(u, a.W);
       int64_t lo = 0, hi = a.n - 1;  // smallest index with cdf > rr
@@ -767,7 +788,7 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk_fwd(FwdArgs a) {
       T y = 0;
       if (live) {
         const uint4 x = philox4x32_10(
-            make_uint4(static_cast<uint32_t>(g), static_cast<uint32_t>(g >> 32), e, a.ctr3), a.key0, a.key1);
+            make_uint4(static_cast<uint32_t>(g), static_cast<uint32_t>(g >> 32), e, a.ctr3), a.rk);
         const T hold = P::mul(P::neglog(P::uniform(x)), static_cast<T>(m.inv_rate));
         const T s_new = P::add(s, hold);
         bool done = !(s_new < static_cast<T>(1));
@@ -972,6 +993,7 @@ cudaError_t launch_walk_forward(mlmc_plan* p, const WalkLaunch& w, int64_t* laun
   a.ctr3 = (static_cast<uint32_t>(w.level) & 0x3Fu) | (1u << 6);
   a.key0 = static_cast<uint32_t>(w.seed & 0xFFFFFFFFull);
   a.key1 = static_cast<uint32_t>(w.seed >> 32);
+  a.rk = philox_round_keys(a.key0, a.key1);
   a.max_jumps = p->sched.max_jumps_per_walk;
   a.sum_x = w.sum_y;
   a.totals = w.totals;
@@ -1017,6 +1039,7 @@ cudaError_t launch_walk(mlmc_plan* p, const WalkLaunch& w, int64_t* launches) {
   a.ctr3 = static_cast<uint32_t>(w.level) & 0x3Fu;
   a.key0 = static_cast<uint32_t>(w.seed & 0xFFFFFFFFull);
   a.key1 = static_cast<uint32_t>(w.seed >> 32);
+  a.rk = philox_round_keys(a.key0, a.key1);
   a.max_jumps = p->sched.max_jumps_per_walk;
   a.sum_y = w.sum_y;
   a.totals = w.totals;
@@ -1039,7 +1062,7 @@ cudaError_t launch_walk(mlmc_plan* p, const WalkLaunch& w, int64_t* launches) {
     if (per_lane <= 0) {
       // Enough walks per item to amortise the item fetch and the pool's tail.
       per_lane = (reps + 31) / 32;
-      if (per_lane > 64) per_lane = 64;
+      if (per_lane > 128) per_lane = 128;
     }
     a.chunk = 32 * per_lane;
     a.chunks_per_row = (reps + a.chunk - 1) / a.chunk;
@@ -1079,6 +1102,7 @@ cudaError_t launch_walk_scratch(mlmc_plan* p, const WalkLaunch& w, unsigned long
   a.ctr3 = static_cast<uint32_t>(w.level) & 0x3Fu;
   a.key0 = static_cast<uint32_t>(w.seed & 0xFFFFFFFFull);
   a.key1 = static_cast<uint32_t>(w.seed >> 32);
+  a.rk = philox_round_keys(a.key0, a.key1);
   a.max_jumps = p->sched.max_jumps_per_walk;
   a.sum_y = w.sum_y;
   a.totals = w.totals;
@@ -1097,7 +1121,7 @@ cudaError_t launch_walk_scratch(mlmc_plan* p, const WalkLaunch& w, unsigned long
     int64_t per_lane = p->sched.walks_per_lane;
     if (per_lane <= 0) {
       per_lane = (reps + 31) / 32;
-      if (per_lane > 64) per_lane = 64;
+      if (per_lane > 128) per_lane = 128;
     }
     a.chunk = 32 * per_lane;
     a.chunks_per_row = (reps + a.chunk - 1) / a.chunk;
