@@ -712,7 +712,15 @@ def run_kernel_workload(args):
     import __graft_entry__ as g
     g.build()
     from paper_1904_12754_gb300 import mlmc as M
-    w = _workload()
+    if args.kernel_matrix == "lap3d":
+        # long walks: unscaled 7-point Laplacian, t L_ii = 6 (about 7 events
+        # per walk), the instance family of the batched workload
+        import mlmc_inputs as I
+        a = I.laplacian_3d(64)
+        w = I.Workload(name="lap3d_g64_t1_fp32", a=a, t=1.0, v=I.uniform_v(a.n, 20190429),
+                       precision="fp32", num_levels=3, tol=1e-3, extra={})
+    else:
+        w = _workload()
     stream = torch.cuda.current_stream()
     sched = M.schedule_default(precision=M.FP32_KAHAN if w.precision == "fp32" else M.FP64,
                                walks_per_lane=args.walks_per_lane, block_threads=args.block)
@@ -788,6 +796,9 @@ def main():
                          "kernel: the walk kernel alone")
     ap.add_argument("--kernel-reps", type=int, default=4096,
                     help="walks per row of one launch in --workload kernel")
+    ap.add_argument("--kernel-matrix", choices=["ba", "lap3d"], default="ba",
+                    help="--workload kernel: ba = the metric's graph (short walks), "
+                         "lap3d = 64^3 Laplacian at t = 1 (long walks)")
     ap.add_argument("--walks-per-lane", type=int, default=0,
                     help="--workload kernel: walks per lane of one work item (0 = library default)")
     ap.add_argument("--block", type=int, default=0,

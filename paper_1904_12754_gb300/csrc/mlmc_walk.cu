@@ -256,11 +256,50 @@ __device__ __forceinline__ void flush_totals(WalkTotals<T>& t, double* totals, u
   t = WalkTotals<T>();
 }
 
+// Totals of the backward walk kernels, split by who updates them: the sum
+// of Y^2 and the error flags per lane (registers), the counters per warp
+// (shared memory, written by lane 0 after a warp reduction per item).
+template <typename T>
+struct LaneTotals {
+  SquareSum<T> y2;
+  uint32_t bad = 0;
+};
+struct WarpCounters {
+  double y2_fixed;  // walks without a jump: count x y_still^2 per item
+  unsigned long long jumps, walks, limit, still;
+};
+
+// Add a warp's totals into totals[] (one lane) and clear them.
+template <typename T>
+__device__ __forceinline__ void flush_warp(LaneTotals<T>& t, WarpCounters* wc, double* totals,
+                                           uint32_t* flags, int lane) {
+  double y2 = t.y2.value();
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) y2 += __shfl_xor_sync(kFull, y2, o);
+  const uint32_t bad = __reduce_or_sync(kFull, t.bad);
+  __syncwarp();
+  if (lane == 0) {
+    if (wc->walks) {
+      atomicAdd(totals + kTotY2, y2 + wc->y2_fixed);
+      atomicAdd(totals + kTotJumps, static_cast<double>(wc->jumps));
+      atomicAdd(totals + kTotWalks, static_cast<double>(wc->walks));
+      if (wc->limit) atomicAdd(totals + kTotLimit, static_cast<double>(wc->limit));
+      if (wc->still) atomicAdd(totals + kTotStill, static_cast<double>(wc->still));
+    }
+    if (bad) atomicOr(flags, bad);
+    wc->y2_fixed = 0.0;
+    wc->jumps = wc->walks = wc->limit = wc->still = 0;
+  }
+  __syncwarp();
+  t = LaneTotals<T>();
+}
+
 // Per-warp queue of screened walks that jump at least once: replica offset,
 // the bucket and coin words of the first jump and either the first holding
 // time (FP64) or the Philox word it is drawn from (FP32).  A ring of
-// kQueueCap slots; a screening round adds at most 64 entries and runs only
-// while fewer than 32 are queued, so it never holds more than 95.
+// kQueueCap slots; a screening round adds at most 64 entries (two walks per
+// lane) and runs only while fewer than 32 are queued, so it never holds more
+// than 95.
 constexpr uint32_t kQueueCap = 128;
 template <bool FP64>
 struct WarpQueue {
@@ -268,6 +307,16 @@ struct WarpQueue {
   uint32_t xz[kQueueCap];
   uint32_t xw[kQueueCap];
   typename std::conditional<FP64, double, uint32_t>::type first[kQueueCap];
+};
+// Per-warp queue of walks that ended at s = 1 (their samples are evaluated 32
+// at a time): the exponents and the end state with the sign in bit 31.  At
+// most 32 are added per iteration and fewer than 32 are left after one, so
+// it never holds more than 63.
+template <bool FP64>
+struct EndQueue {
+  typename std::conditional<FP64, double, float>::type x1[kQueueCap];
+  typename std::conditional<FP64, double, float>::type x2[kQueueCap];
+  uint32_t js[kQueueCap];
 };
 constexpr int kMaxWarps = 8;  // blocks of at most 256 threads
 
@@ -309,8 +358,15 @@ __device__ __forceinline__ int32_t still_index32(float inv_rate, int lane) {
 //           whose first time reaches s = 1 never leaves the row (its sample
 //           is the same for every such walk: it is only counted), the others
 //           are queued;
-//   walk    a lane without a walk takes the next queued one, makes its first
-//           jump with the queued draw and continues event by event.
+//   walk    lanes without a walk take queued ones; an iteration has two
+//           waves: the refilled lanes make their first jump with the queued
+//           draw, then every live lane draws its next holding time and jumps
+//           or ends, so most walks finish in one iteration with the draw on
+//           (nearly) all lanes.
+// Rows whose walks are long (t L_row > 1) are not screened: an iteration is
+// one event per lane, a lane whose walk ends claims the next walk index at
+// once (ballot + prefix count), and the samples of ended walks are evaluated
+// 32 at a time from a second queue (few lanes end per iteration).
 // Screening runs whenever fewer than 32 walks are queued, so every lane of
 // the walk stage has work while any is left, and walks that never jump (most
 // of them when t L_ii is small) cost one draw at full SIMD width instead of a
@@ -318,11 +374,13 @@ __device__ __forceinline__ int32_t still_index32(float inv_rate, int lane) {
 // counter, so the trajectories are those of the walk-by-walk definition.
 // Adds the item's sum of Y to a.sum_y[row] (one atomic) and its totals to
 // `tot`.
-template <bool FP64, bool COARSE, bool TRACE, bool IS, class Keys>
+template <bool FP64, bool COARSE, bool TRACE, bool IS, class Keys, bool kScreen = true>
 __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, int64_t row,
                                           int64_t r_lo, int64_t r_hi,
-                                          WalkTotals<typename Prec<FP64>::T>& tot,
-                                          WarpQueue<FP64>* __restrict__ q, int lane) {
+                                          LaneTotals<typename Prec<FP64>::T>& tot,
+                                          WarpCounters* __restrict__ wc,
+                                          WarpQueue<FP64>* __restrict__ q,
+                                          EndQueue<FP64>* __restrict__ eq, int lane) {
   using P = Prec<FP64>;
   using T = typename P::T;
   using Meta = typename P::Meta;
@@ -336,7 +394,13 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
   const Meta m0 = load_meta(meta, row);
   const T dl0 = static_cast<T>(m0.dl);
   const T inv_rate0 = static_cast<T>(m0.inv_rate);
-  const int32_t still_max = FP64 ? 0 : still_index32(static_cast<float>(m0.inv_rate), lane);
+  // Two waves per iteration (with screening) for rows whose walks are short
+  // (t L_row <= 1: few events per walk, the first jump and the end usually
+  // fall in the same iteration); one wave without screening for the others.
+  constexpr int kWays = 2;
+  const bool two_wave = kScreen && static_cast<T>(m0.inv_rate) >= static_cast<T>(1);
+  const int32_t still_max =
+      (FP64 || !two_wave) ? 0 : still_index32(static_cast<float>(m0.inv_rate), lane);
   // A walk that never jumps stays at the row for the whole interval: its
   // sample is 0 above l0 and v_row e^{dl_row} at l0 (E_f = dl_row exactly
   // as the grid weights sum to 1), the same for every such walk.
@@ -350,13 +414,15 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
   Kahan<T> acc_y;
   uint32_t item_jumps = 0;  // this lane's jumps in this item (< 2^32)
   uint32_t n_still = 0;     // walks without a jump screened by this lane
-  if (lane == 0) tot.walks += static_cast<unsigned long long>(r_hi - r_lo);
+  uint32_t n_limit = 0;     // this lane's walks stopped at the jump limit
   const uint32_t row32 = static_cast<uint32_t>(row);
   const uint32_t span = static_cast<uint32_t>(r_hi - r_lo);
   const uint64_t rep_base = static_cast<uint64_t>(a.rep_begin + r_lo);
   const unsigned lanes_below = (1u << lane) - 1u;
   uint32_t screened = 0;           // warp-uniform: walks screened so far
   uint32_t qhead = 0, qtail = 0;   // warp-uniform queue positions
+  uint32_t ehead = 0, etail = 0;   // warp-uniform end-queue positions
+  uint32_t claimed = 0;            // warp-uniform: walks claimed (one-wave rows)
   bool live = false;               // this lane holds a walk
   // Walk state.
   uint32_t r = 0, c_lo = 0, c_hi = 0;  // replica offset and its counter words
@@ -371,204 +437,306 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
   T lw = 0;                // proposal only: sum of log(k/q) over the jumps
   uint32_t hash = 2166136261u;
 
+  // Start walk r of the item (state at s = 0 in the row).
+  auto start_walk = [&](uint32_t r_new) {
+    r = r_new;
+    const uint64_t rep = rep_base + r;
+    c_lo = static_cast<uint32_t>(rep);
+    c_hi = a.ctr3 | (static_cast<uint32_t>(rep >> 32) << 8);
+    m = m0;
+    j = static_cast<int32_t>(row);
+    e = 0;
+    neg = 0;
+    s = 0;
+    acc = 0;
+    acc_d = 0;
+    kprev = -1;
+    lw = 0;
+    hash = 2166136261u;
+  };
+  // Jump at time s_new (after fine grid point g) with bucket word xz and
+  // alias coin xw: count the grid points of the segment that ends, pick the
+  // next state from the alias table of the current one.
+  auto jump = [&](T s_new, uint32_t xz, uint32_t xw) {
+    const int g = P::floor_int(P::mul(s_new, n_fine));
+    const T dlj = static_cast<T>(m.dl);
+    if (COARSE) {
+      const int kc_prev = kprev >> 1;   // floor(a/2), also for a = -1
+      acc = P::fma(P::from_int((g >> 1) - kc_prev), dlj, acc);
+      acc_d = P::fma(P::from_int((g & 1) - (kprev & 1)), dlj, acc_d);
+    } else {
+      acc = P::fma(P::from_int(g - kprev), dlj, acc);
+    }
+    kprev = g;
+    const uint32_t bucket = __umulhi(xz, static_cast<uint32_t>(m.deg));
+    uint32_t pick;
+    if (IS) {
+      const uint4* ep = reinterpret_cast<const uint4*>(
+          static_cast<const AliasEntryIS*>(a.alias) + m.start + bucket);
+      const uint4 e0 = __ldg(ep);
+      const uint2 e1 = __ldg(reinterpret_cast<const uint2*>(ep + 1));
+      const bool keep = xw < e0.x;
+      pick = keep ? e0.y : e0.z;
+      lw = P::add(lw, static_cast<T>(__uint_as_float(keep ? e1.x : e1.y)));
+    } else {
+      const uint4 ent = __ldg(reinterpret_cast<const uint4*>(
+                                  static_cast<const AliasEntry*>(a.alias) + m.start) + bucket);
+      pick = (xw < ent.x) ? ent.y : ent.z;
+    }
+    neg ^= pick >> 31;
+    j = static_cast<int32_t>(pick & kColMask);
+    if (TRACE) hash = (hash ^ static_cast<uint32_t>(j)) * 16777619u;
+    m = load_meta(meta, j);
+    s = s_new;
+    ++e;
+  };
+  // Sample of a walk that ended at s = 1 after e >= 1 jumps, from its
+  // exponents: x1 = E_f (l0) or E_c (above), plus the proposal's log-ratio;
+  // x2 = E_f - E_c (above l0); js = end state | sign << 31.
+  auto sample = [&](T x1, T x2, uint32_t js) {
+    const T vend = static_cast<T>(__ldg(vv + (js & kColMask)));
+    T y = COARSE ? P::mul(vend, P::mul(P::ex(x1), P::exm1(x2))) : P::mul(vend, P::ex(x1));
+    if (js >> 31) y = -y;
+    if (!isfinite(y)) {
+      tot.bad |= kFlagNonFiniteY;
+      y = 0;
+    }
+    acc_y.add(y);
+    tot.y2.add_square(y);
+    return y;
+  };
+  // The exponents of the walk that ends at state j (s = 1).
+  auto exponents = [&](T& x1, T& x2) {
+    const T dle = static_cast<T>(m.dl);
+    const T h = P::mul(P::add(dl0, dle), static_cast<T>(0.5));
+    if (COARSE) {
+      const T acc_c = P::fma(P::from_int(n_coarse - (kprev >> 1)), dle, acc);
+      const T accd = P::fma(P::from_int(-(kprev & 1)), dle, acc_d);
+      const T ec = P::mul(P::sub(acc_c, h), P::mul(inv_n, static_cast<T>(2)));
+      x1 = IS ? P::add(ec, lw) : ec;
+      x2 = P::mul(P::add(accd, h), inv_n);
+    } else {
+      const T acc_f = P::fma(P::from_int(n_grid - kprev), dle, acc);
+      const T ef = P::mul(P::sub(acc_f, h), inv_n);
+      x1 = IS ? P::add(ef, lw) : ef;
+      x2 = 0;
+    }
+  };
+  // The walk ends at state j: at s = 1 after e >= 1 jumps (status 0), or at
+  // the jump limit (status 1, sample 0).  A deferred status-0 end (no trace)
+  // only records its exponents (ending = true); the samples are evaluated
+  // 32 at a time from the warp's end queue.
+  bool ending = false;
+  T end_x1 = 0, end_x2 = 0;
+  auto finish = [&](int status, bool defer) {
+    item_jumps += e;
+    live = false;
+    if (status == 0 && e == 0) {
+      // never jumped: counted, its sample y_still is added per item
+      ++n_still;
+      if (TRACE) {
+        mlmc_walk_record rec;
+        rec.end = j;
+        rec.jumps = 0;
+        rec.sign = 1;
+        rec.hash = hash;
+        rec.y = static_cast<double>(y_still);
+        rec.status = 0;
+        rec.pad = 0;
+        a.trace[row * a.trace_stride + a.trace_base + (r_lo + r)] = rec;
+      }
+      return;
+    }
+    if (status != 0) {
+      tot.bad |= kFlagWalkLimit;
+      ++n_limit;
+      acc_y.add(static_cast<T>(0));
+      tot.y2.add_square(static_cast<T>(0));
+    } else if (!TRACE && defer) {
+      exponents(end_x1, end_x2);
+      ending = true;
+      return;
+    }
+    T y = 0;
+    if (status == 0) {
+      T x1, x2;
+      exponents(x1, x2);
+      y = sample(x1, x2, static_cast<uint32_t>(j) | (neg << 31));
+    }
+    if (TRACE) {
+      mlmc_walk_record rec;
+      rec.end = j;
+      rec.jumps = static_cast<int32_t>(e);
+      rec.sign = neg ? -1 : 1;
+      rec.hash = hash;
+      rec.y = static_cast<double>(y);
+      rec.status = status;
+      rec.pad = 0;
+      a.trace[row * a.trace_stride + a.trace_base + (r_lo + r)] = rec;
+    }
+  };
+  // Move this iteration's ended walks into the end queue; evaluate 32
+  // samples at once when at least 32 are queued, or all of them at the end
+  // of the item (drain).  Called by the whole warp.
+  auto settle_ends = [&](bool drain) {
+    if (TRACE) return;
+    const unsigned em = __ballot_sync(kFull, ending);
+    if (ending) {
+      const uint32_t slot = (etail + static_cast<uint32_t>(__popc(em & lanes_below))) & (kQueueCap - 1);
+      eq->x1[slot] = end_x1;
+      eq->x2[slot] = end_x2;
+      eq->js[slot] = static_cast<uint32_t>(j) | (neg << 31);
+      ending = false;
+    }
+    etail += static_cast<uint32_t>(__popc(em));
+    while (etail - ehead >= 32u || (drain && etail != ehead)) {
+      __syncwarp();
+      const uint32_t k = ehead + static_cast<uint32_t>(lane);
+      if (k < etail) {
+        const uint32_t slot = k & (kQueueCap - 1);
+        sample(eq->x1[slot], eq->x2[slot], eq->js[slot]);
+      }
+      ehead = min(ehead + 32u, etail);
+      __syncwarp();
+    }
+  };
+
   for (;;) {
-    // Screen the first holding times of the next 64 walks (two per lane:
-    // independent Philox chains that the lane's instructions interleave).
-    while (qtail - qhead < 32u && screened < span) {
-      uint4 x[2];
-      T h1[2] = {0, 0};
-      bool push[2];
+    if (two_wave) {
+      // Screen the first holding times of the next 64 walks (two per lane:
+      // independent Philox chains that the lane's instructions interleave).
+      while (qtail - qhead < 32u && screened < span) {
+        uint4 x[kWays];
+        T h1[kWays] = {};
+        bool push[kWays];
 #pragma unroll
-      for (int w = 0; w < 2; ++w) {
-        const uint64_t rep = rep_base + screened + static_cast<uint32_t>(32 * w + lane);
-        x[w] = keys.draw(make_uint4(static_cast<uint32_t>(rep), row32, 0u,
-                                    a.ctr3 | (static_cast<uint32_t>(rep >> 32) << 8)));
-      }
+        for (int w = 0; w < kWays; ++w) {
+          const uint64_t rep = rep_base + screened + static_cast<uint32_t>(32 * w + lane);
+          x[w] = keys.draw(make_uint4(static_cast<uint32_t>(rep), row32, 0u,
+                                      a.ctr3 | (static_cast<uint32_t>(rep >> 32) << 8)));
+        }
 #pragma unroll
-      for (int w = 0; w < 2; ++w) {
-        const uint32_t rs = screened + static_cast<uint32_t>(32 * w + lane);
-        if (FP64) {
-          h1[w] = P::mul(P::neglog(P::uniform(x[w])), inv_rate0);
-          push[w] = rs < span && h1[w] < static_cast<T>(1);
-        } else {
-          push[w] = rs < span && static_cast<int32_t>(x[w].x >> 9) > still_max;  // uniform index
-        }
-        if (rs < span && !push[w]) {
-          ++n_still;
-          if (TRACE) {
-            mlmc_walk_record rec;
-            rec.end = static_cast<int32_t>(row);
-            rec.jumps = 0;
-            rec.sign = 1;
-            rec.hash = 2166136261u;
-            rec.y = static_cast<double>(y_still);
-            rec.status = 0;
-            rec.pad = 0;
-            a.trace[row * a.trace_stride + a.trace_base + (r_lo + rs)] = rec;
-          }
-        }
-        const unsigned pm = __ballot_sync(kFull, push[w]);
-        if (push[w]) {
-          const uint32_t slot =
-              (qtail + static_cast<uint32_t>(__popc(pm & lanes_below))) & (kQueueCap - 1);
-          q->r[slot] = rs;
-          q->xz[slot] = x[w].z;
-          q->xw[slot] = x[w].w;
-          if constexpr (FP64) q->first[slot] = h1[w];
-          else q->first[slot] = x[w].x;
-        }
-        qtail += static_cast<uint32_t>(__popc(pm));
-      }
-      screened += 64u;
-    }
-    __syncwarp();
-    // Lanes without a walk take queued ones.
-    const unsigned idle = __ballot_sync(kFull, !live);
-    bool popped = false;
-    uint32_t slot = 0;
-    if (!live) {
-      const uint32_t k = qhead + static_cast<uint32_t>(__popc(idle & lanes_below));
-      if (k < qtail) {
-        slot = k & (kQueueCap - 1);
-        r = q->r[slot];
-        popped = true;
-        live = true;
-        const uint64_t rep = rep_base + r;
-        c_lo = static_cast<uint32_t>(rep);
-        c_hi = a.ctr3 | (static_cast<uint32_t>(rep >> 32) << 8);
-        m = m0;
-        j = static_cast<int32_t>(row);
-        e = 0;
-        neg = 0;
-        s = 0;
-        acc = 0;
-        acc_d = 0;
-        kprev = -1;
-        lw = 0;
-        hash = 2166136261u;
-      }
-    }
-    qhead = min(qhead + static_cast<uint32_t>(__popc(idle)), qtail);
-    if (!__any_sync(kFull, live)) break;  // queue empty and every walk screened
-    if (live) {
-      T s_new;
-      uint32_t xz, xw;
-      bool done;
-      if constexpr (FP64) {
-        if (popped) {
-          // first event: its holding time was drawn at screening
-          s_new = q->first[slot];
-          xz = q->xz[slot];
-          xw = q->xw[slot];
-          done = false;
-        } else {
-          const uint4 x = keys.draw(make_uint4(c_lo, row32, e, c_hi));
-          s_new = P::add(s, P::mul(P::neglog(P::uniform(x)), static_cast<T>(m.inv_rate)));
-          xz = x.z;
-          xw = x.w;
-          done = !(s_new < static_cast<T>(1));
-        }
-      } else {
-        // a first event takes its queued Philox words (s = 0 and m = m0 here)
-        const uint4 x = popped ? make_uint4(q->first[slot], 0u, q->xz[slot], q->xw[slot])
-                               : keys.draw(make_uint4(c_lo, row32, e, c_hi));
-        s_new = P::add(s, P::mul(P::neglog(P::uniform(x)), static_cast<T>(m.inv_rate)));
-        xz = x.z;
-        xw = x.w;
-        done = !(s_new < static_cast<T>(1));
-      }
-      int status = 0;
-      if (!done && static_cast<int64_t>(e) >= a.max_jumps) {
-        done = true;
-        status = 1;
-      }
-      if (!done) {
-        // Jump at s_new, after fine grid point g.
-        const int g = P::floor_int(P::mul(s_new, n_fine));
-        const T dlj = static_cast<T>(m.dl);
-        if (COARSE) {
-          const int kc_prev = kprev >> 1;   // floor(a/2), also for a = -1
-          acc = P::fma(P::from_int((g >> 1) - kc_prev), dlj, acc);
-          acc_d = P::fma(P::from_int((g & 1) - (kprev & 1)), dlj, acc_d);
-        } else {
-          acc = P::fma(P::from_int(g - kprev), dlj, acc);
-        }
-        kprev = g;
-        const uint32_t bucket = __umulhi(xz, static_cast<uint32_t>(m.deg));
-        uint32_t pick;
-        if (IS) {
-          const uint4* ep = reinterpret_cast<const uint4*>(
-              static_cast<const AliasEntryIS*>(a.alias) + m.start + bucket);
-          const uint4 e0 = __ldg(ep);
-          const uint2 e1 = __ldg(reinterpret_cast<const uint2*>(ep + 1));
-          const bool keep = xw < e0.x;
-          pick = keep ? e0.y : e0.z;
-          lw = P::add(lw, static_cast<T>(__uint_as_float(keep ? e1.x : e1.y)));
-        } else {
-          const uint4 ent = __ldg(reinterpret_cast<const uint4*>(
-                                      static_cast<const AliasEntry*>(a.alias) + m.start) + bucket);
-          pick = (xw < ent.x) ? ent.y : ent.z;
-        }
-        neg ^= pick >> 31;
-        j = static_cast<int32_t>(pick & kColMask);
-        if (TRACE) hash = (hash ^ static_cast<uint32_t>(j)) * 16777619u;
-        m = load_meta(meta, j);
-        s = s_new;
-        ++e;
-      } else {
-        // Walk ends at state j (s = 1) after e >= 1 jumps, or at the limit.
-        T y = 0;
-        if (status == 0) {
-          const T dle = static_cast<T>(m.dl);
-          const T h = P::mul(P::add(dl0, dle), static_cast<T>(0.5));
-          const T vend = static_cast<T>(__ldg(vv + j));
-          if (COARSE) {
-            const T acc_c = P::fma(P::from_int(n_coarse - (kprev >> 1)), dle, acc);
-            const T accd = P::fma(P::from_int(-(kprev & 1)), dle, acc_d);
-            const T ec = P::mul(P::sub(acc_c, h), P::mul(inv_n, static_cast<T>(2)));
-            const T diff = P::mul(P::add(accd, h), inv_n);
-            y = P::mul(vend, P::mul(P::ex(IS ? P::add(ec, lw) : ec), P::exm1(diff)));
+        for (int w = 0; w < kWays; ++w) {
+          const uint32_t rs = screened + static_cast<uint32_t>(32 * w + lane);
+          if (FP64) {
+            h1[w] = P::mul(P::neglog(P::uniform(x[w])), inv_rate0);
+            push[w] = rs < span && h1[w] < static_cast<T>(1);
           } else {
-            const T acc_f = P::fma(P::from_int(n_grid - kprev), dle, acc);
-            const T ef = P::mul(P::sub(acc_f, h), inv_n);
-            y = P::mul(vend, P::ex(IS ? P::add(ef, lw) : ef));
+            push[w] = rs < span && static_cast<int32_t>(x[w].x >> 9) > still_max;  // uniform index
           }
-          if (neg) y = -y;
-          if (!isfinite(y)) {
-            tot.bad |= kFlagNonFiniteY;
-            y = 0;
+          if (rs < span && !push[w]) {
+            ++n_still;
+            if (TRACE) {
+              mlmc_walk_record rec;
+              rec.end = static_cast<int32_t>(row);
+              rec.jumps = 0;
+              rec.sign = 1;
+              rec.hash = 2166136261u;
+              rec.y = static_cast<double>(y_still);
+              rec.status = 0;
+              rec.pad = 0;
+              a.trace[row * a.trace_stride + a.trace_base + (r_lo + rs)] = rec;
+            }
           }
-        } else {
-          tot.bad |= kFlagWalkLimit;
-          ++tot.limit;
+          const unsigned pm = __ballot_sync(kFull, push[w]);
+          if (push[w]) {
+            const uint32_t slot =
+                (qtail + static_cast<uint32_t>(__popc(pm & lanes_below))) & (kQueueCap - 1);
+            q->r[slot] = rs;
+            q->xz[slot] = x[w].z;
+            q->xw[slot] = x[w].w;
+            if constexpr (FP64) q->first[slot] = h1[w];
+            else q->first[slot] = x[w].x;
+          }
+          qtail += static_cast<uint32_t>(__popc(pm));
         }
-        acc_y.add(y);
-        tot.y2.add_square(y);
-        item_jumps += e;
-        if (TRACE) {
-          mlmc_walk_record rec;
-          rec.end = j;
-          rec.jumps = static_cast<int32_t>(e);
-          rec.sign = neg ? -1 : 1;
-          rec.hash = hash;
-          rec.y = static_cast<double>(y);
-          rec.status = status;
-          rec.pad = 0;
-          a.trace[row * a.trace_stride + a.trace_base + (r_lo + r)] = rec;
-        }
-        live = false;
+        screened += 32u * kWays;
       }
+      __syncwarp();
+      // Refill wave: lanes without a walk take queued ones and make their
+      // first jump with the queued draw.
+      const unsigned idle = __ballot_sync(kFull, !live);
+      if (!live) {
+        const uint32_t k = qhead + static_cast<uint32_t>(__popc(idle & lanes_below));
+        if (k < qtail) {
+          const uint32_t slot = k & (kQueueCap - 1);
+          start_walk(q->r[slot]);
+          T s1;
+          if constexpr (FP64) {
+            s1 = q->first[slot];  // drawn at screening
+          } else {
+            // s = 0 and m = m0: the first event's time from the queued word
+            s1 = P::add(s, P::mul(P::neglog(P::uniform(make_uint4(q->first[slot], 0u, 0u, 0u))),
+                                  static_cast<T>(m.inv_rate)));
+          }
+          const uint32_t xz = q->xz[slot], xw = q->xw[slot];
+          if (static_cast<int64_t>(e) >= a.max_jumps) {
+            finish(1, false);
+          } else {
+            jump(s1, xz, xw);
+            live = true;
+          }
+        }
+      }
+      qhead = min(qhead + static_cast<uint32_t>(__popc(idle)), qtail);
+      __syncwarp();  // queue slots read above are free for the next screening
+      if (!__any_sync(kFull, live)) break;  // queue empty and every walk screened
+      // Draw wave: every live lane draws its next holding time, then jumps
+      // or ends (short walks: most lanes end here together, so the sample
+      // is evaluated at once).
+      if (live) {
+        const uint4 x = keys.draw(make_uint4(c_lo, row32, e, c_hi));
+        const T s_new = P::add(s, P::mul(P::neglog(P::uniform(x)), static_cast<T>(m.inv_rate)));
+        if (!(s_new < static_cast<T>(1))) {
+          finish(0, false);
+        } else if (static_cast<int64_t>(e) >= a.max_jumps) {
+          finish(1, false);
+        } else {
+          jump(s_new, x.z, x.w);
+        }
+      }
+    } else {
+      // One wave (rows whose walks are long: no screening): lanes without a
+      // walk claim the next unclaimed walks of the item and every live lane
+      // makes one event; few lanes end per iteration, so the samples of
+      // ended walks go to the end queue.
+      const unsigned idle = __ballot_sync(kFull, !live);
+      if (!live) {
+        const uint32_t k = claimed + static_cast<uint32_t>(__popc(idle & lanes_below));
+        if (k < span) {
+          start_walk(k);
+          live = true;
+        }
+      }
+      claimed = min(claimed + static_cast<uint32_t>(__popc(idle)), span);
+      if (!__any_sync(kFull, live)) break;  // every walk of the item done
+      if (live) {
+        const uint4 x = keys.draw(make_uint4(c_lo, row32, e, c_hi));
+        const T s_new = P::add(s, P::mul(P::neglog(P::uniform(x)), static_cast<T>(m.inv_rate)));
+        if (!(s_new < static_cast<T>(1))) {
+          finish(0, true);
+        } else if (static_cast<int64_t>(e) >= a.max_jumps) {
+          finish(1, true);
+        } else {
+          jump(s_new, x.z, x.w);
+        }
+      }
+      settle_ends(false);
     }
-    __syncwarp();  // queue slots read above are free before the next screening
   }
-  tot.jumps += item_jumps;
+  settle_ends(true);
   double ys = warp_sum(acc_y);
+  const unsigned long long jumps = warp_sum_u64(item_jumps);
   const unsigned long long still = warp_sum_u64(n_still);
-  if (lane == 0) tot.still += still;
-  if (!COARSE) {
-    const double yc = static_cast<double>(y_still);
-    ys += static_cast<double>(still) * yc;
-    if (lane == 0) tot.y2_fixed += static_cast<double>(still) * (yc * yc);
+  const unsigned long long limit = warp_sum_u64(n_limit);
+  const double yc = static_cast<double>(y_still);
+  if (!COARSE) ys += static_cast<double>(still) * yc;
+  if (lane == 0) {
+    wc->walks += static_cast<unsigned long long>(r_hi - r_lo);
+    wc->jumps += jumps;
+    wc->still += still;
+    wc->limit += limit;
+    if (!COARSE) wc->y2_fixed += static_cast<double>(still) * (yc * yc);
   }
   if (lane == 0 && ys != 0.0) atomicAdd(a.sum_y + row, ys);
 }
@@ -592,8 +760,14 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk(const __grid_constan
   ia.trace_stride = a.trace_stride;
   ia.trace_base = a.trace_base;
   __shared__ WarpQueue<FP64> queues[kMaxWarps];
+  __shared__ WarpCounters counters[kMaxWarps];
+  __shared__ EndQueue<FP64> ends[kMaxWarps];
   WarpQueue<FP64>* q = &queues[threadIdx.x >> 5];
-  WalkTotals<T> tot;
+  EndQueue<FP64>* eq = &ends[threadIdx.x >> 5];
+  WarpCounters* wc = &counters[threadIdx.x >> 5];
+  if (lane == 0) *wc = WarpCounters{};
+  __syncwarp();
+  LaneTotals<T> tot;
   for (;;) {
     unsigned long long item = 0;
     if (lane == 0) item = atomicAdd(a.work, 1ull);
@@ -604,9 +778,9 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk(const __grid_constan
     const int64_t r_lo = chunk * a.chunk;
     const int64_t r_hi = min(r_lo + a.chunk, a.reps);
     walk_item<FP64, COARSE, TRACE, IS>(ia, KeysFromParam{&a.rk}, a.row_begin + rel, r_lo, r_hi,
-                                       tot, q, lane);
+                                       tot, wc, q, eq, lane);
   }
-  flush_totals(tot, a.totals, a.flags, lane);
+  flush_warp(tot, wc, a.totals, a.flags, lane);
 }
 
 // Batched walks: the items of many (problem, level, replica range) segments
@@ -614,6 +788,19 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk(const __grid_constan
 // search over the segments' first items, then runs the same per-item walk as
 // k_walk with that problem's tables and adds its totals to the problem's
 // level totals.
+// Per-warp copy of the current segment's walk parameters (shared memory, so
+// that they are not held in registers across the walk loop).
+struct BatchWarpState {
+  ItemArgs ia;
+  double* totals;          // the segment's level totals
+  int64_t n;               // rows of the segment's problem
+  int64_t reps;            // replicas of the segment
+  int64_t chunk;           // walks per item
+  int64_t chunks_per_row;
+  int32_t slot;            // level slot (0 = l0, coarse above)
+  uint32_t key0, key1;
+};
+
 template <bool FP64>
 __global__ void __launch_bounds__(256, FP64 ? 3 : 4)
     k_walk_batch(const BatchProblemDev* __restrict__ probs, const BatchHeaderDev* __restrict__ hdr,
@@ -623,16 +810,21 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4)
   const int lane = threadIdx.x & 31;
   const unsigned long long total = hdr->total_items;
   const int nseg = hdr->segments;
-  __shared__ WarpQueue<FP64> queues[kMaxWarps];
-  WarpQueue<FP64>* q = &queues[threadIdx.x >> 5];
-  WalkTotals<T> tot;
+  __shared__ BatchWarpState states[kMaxWarps];
+  __shared__ WarpCounters counters[kMaxWarps];
+  __shared__ EndQueue<FP64> ends[kMaxWarps];
+  WarpQueue<FP64>* q = nullptr;  // no screening in this kernel
+  EndQueue<FP64>* eq = &ends[threadIdx.x >> 5];
+  BatchWarpState& st = states[threadIdx.x >> 5];
+  WarpCounters* wc = &counters[threadIdx.x >> 5];
+  if (lane == 0) *wc = WarpCounters{};
+  __syncwarp();
+  LaneTotals<T> tot;
   // The warp's current segment; its totals are flushed when the warp's next
   // item falls in another segment (items come in segment order, so a warp
   // usually stays in one segment for many items).
-  int cur = -1;
+  bool have = false;
   unsigned long long seg_lo = 0, seg_hi = 0;
-  BatchSegmentDev sg{};
-  BatchProblemDev pb{};
   // A warp claims kGrab consecutive items per atomic, so that it crosses a
   // segment boundary (search + flush) at most about once per claim.
   constexpr unsigned kGrab = 8;
@@ -648,43 +840,60 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4)
     --left;
     if (item >= total) break;
     if (item < seg_lo || item >= seg_hi) {
-      if (cur >= 0) flush_totals(tot, pb.totals + static_cast<int64_t>(sg.slot) * kTotSlots, flags, lane);
+      if (have) flush_warp(tot, wc, st.totals, flags, lane);
       int lo = 0, hi = nseg - 1;
       while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if (segs[mid].item_begin <= item) lo = mid; else hi = mid - 1;
       }
-      cur = lo;
-      sg = segs[lo];
-      pb = probs[sg.problem];
-      seg_lo = sg.item_begin;
-      seg_hi = seg_lo + static_cast<unsigned long long>(pb.n) * static_cast<unsigned long long>(sg.chunks_per_row);
+      __syncwarp();
+      if (lane == 0) {
+        const BatchSegmentDev sg = segs[lo];
+        const BatchProblemDev pb = probs[sg.problem];
+        const int level = pb.l0 + sg.slot;
+        st.ia.meta = pb.meta;
+        st.ia.alias = pb.alias;
+        st.ia.v_walk = pb.v_walk;
+        st.ia.level = level;
+        st.ia.ctr3 = static_cast<uint32_t>(level) & 0x3Fu;
+        st.ia.key0 = pb.key0;
+        st.ia.key1 = pb.key1;
+        st.ia.max_jumps = pb.max_jumps;
+        st.ia.sum_y = pb.sums + static_cast<int64_t>(sg.slot) * pb.n;
+        st.ia.rep_begin = sg.rep_begin;
+        st.ia.trace = nullptr;
+        st.ia.trace_stride = 0;
+        st.ia.trace_base = 0;
+        st.totals = pb.totals + static_cast<int64_t>(sg.slot) * kTotSlots;
+        st.n = pb.n;
+        st.reps = sg.reps;
+        st.chunk = sg.chunk;
+        st.chunks_per_row = sg.chunks_per_row;
+        st.slot = sg.slot;
+        st.key0 = pb.key0;
+        st.key1 = pb.key1;
+      }
+      __syncwarp();
+      seg_lo = segs[lo].item_begin;
+      seg_hi = seg_lo + static_cast<unsigned long long>(st.n) *
+                            static_cast<unsigned long long>(st.chunks_per_row);
+      have = true;
     }
-    const unsigned long long local = item - sg.item_begin;
-    const int64_t row = static_cast<int64_t>(local / static_cast<unsigned long long>(sg.chunks_per_row));
-    const int64_t chunk = static_cast<int64_t>(local) - row * sg.chunks_per_row;
-    const int64_t r_lo = chunk * sg.chunk;
-    const int64_t r_hi = min(r_lo + sg.chunk, sg.reps);
-    const int level = pb.l0 + sg.slot;
-    ItemArgs ia;
-    ia.meta = pb.meta;
-    ia.alias = pb.alias;
-    ia.v_walk = pb.v_walk;
-    ia.level = level;
-    ia.ctr3 = static_cast<uint32_t>(level) & 0x3Fu;
-    ia.key0 = pb.key0;
-    ia.key1 = pb.key1;
-    ia.max_jumps = pb.max_jumps;
-    ia.sum_y = pb.sums + static_cast<int64_t>(sg.slot) * pb.n;
-    ia.rep_begin = sg.rep_begin;
-    ia.trace = nullptr;
-    ia.trace_stride = 0;
-    ia.trace_base = 0;
-    const KeysOnTheFly keys{pb.key0, pb.key1};
-    if (sg.slot > 0) walk_item<FP64, true, false, false>(ia, keys, row, r_lo, r_hi, tot, q, lane);
-    else walk_item<FP64, false, false, false>(ia, keys, row, r_lo, r_hi, tot, q, lane);
+    const unsigned long long local = item - seg_lo;
+    const int64_t row = static_cast<int64_t>(local / static_cast<unsigned long long>(st.chunks_per_row));
+    const int64_t chunk = static_cast<int64_t>(local) - row * st.chunks_per_row;
+    const int64_t r_lo = chunk * st.chunk;
+    const int64_t r_hi = min(r_lo + st.chunk, st.reps);
+    const KeysOnTheFly keys{st.key0, st.key1};
+    // Without screening (one event per lane per iteration for every row):
+    // the batched instances' walks are mostly long, and the screening stage
+    // would hold more state than this kernel's registers allow.
+    if (st.slot > 0)
+      walk_item<FP64, true, false, false, KeysOnTheFly, false>(st.ia, keys, row, r_lo, r_hi, tot, wc, q, eq, lane);
+    else
+      walk_item<FP64, false, false, false, KeysOnTheFly, false>(st.ia, keys, row, r_lo, r_hi, tot, wc, q, eq, lane);
   }
-  if (cur >= 0) flush_totals(tot, pb.totals + static_cast<int64_t>(sg.slot) * kTotSlots, flags, lane);
+  if (have) flush_warp(tot, wc, st.totals, flags, lane);
 }
 
 // ---------------------------------------------------------------------------
