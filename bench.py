@@ -779,6 +779,156 @@ def run_kernel_workload(args):
     print(json.dumps(out), flush=True)
     plan.close()
 
+# ---------------------------------------------------------------------------
+# Level statistics and complexity (the paper's Fig. 2, Fig. 4 and Fig. 5)
+# ---------------------------------------------------------------------------
+def _slope(xs, ys):
+    xs, ys = np.asarray(xs, float), np.asarray(ys, float)
+    ok = np.isfinite(ys)
+    if ok.sum() < 2:
+        return None
+    return float(np.polyfit(xs[ok], ys[ok], 1)[0])
+
+
+def run_levels_workload(args):
+    """m_l and V_l of the coupled corrections P_l - P_{l-1} against the level
+    (Fig. 2): total communicability (v = 1, beta = 1) of Newman-Watts
+    small-world networks (k = 2, p = 0.1) of three sizes, FP64 walks, a fixed
+    number of walks per row at every level (one mlmc_mlmcl launch each).
+    Reported per level: the mean correction per row (1^T m_l / n) and the
+    per-row variance V_l, with least-squares slopes of their log2 over the
+    finer levels (the paper's analysis: both -2)."""
+    import torch
+    import mlmc_inputs as I
+    import __graft_entry__ as g
+    g.build()
+    from paper_1904_12754_gb300 import mlmc as M
+    stream = torch.cuda.current_stream()
+    out = {"metric": "MLMC level statistics m_l, V_l vs level (TC of small-world networks)",
+           "n_gpus": 1, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "Newman-Watts small world k=2 p=0.1, beta=1, v=1, FP64 walk",
+                      "levels": list(range(0, args.max_level + 1))}, "networks": {}}
+    for n, reps in ((10 ** 4, 8192), (10 ** 5, 1024), (10 ** 6, 128)):
+        a = I.small_world(n, 2, 0.1, seed=20190429)
+        sched = M.schedule_default(precision=M.FP64)
+        plan = M.Plan.from_csr(a, 1.0, sched, rel_tol=1e-3, stream=stream.cuda_stream)
+        dv = torch.ones(n, dtype=torch.float64, device="cuda")
+        sums = torch.zeros(n, dtype=torch.float64, device="cuda")
+        tot = torch.zeros(5, dtype=torch.float64, device="cuda")
+        rows = []
+        for lvl in range(0, args.max_level + 1):
+            sums.zero_()
+            tot.zero_()
+            t0 = time.perf_counter()
+            plan.mlmcl(lvl, lvl > 0, 0, reps, dv, 77 + lvl, sums, tot)
+            torch.cuda.synchronize()
+            sec = time.perf_counter() - t0
+            sv = sums.cpu().numpy()
+            t = tot.cpu().numpy()
+            mean = float(sv.sum() / (n * reps))
+            var = float((t[0] - float((sv * sv).sum()) / reps) / (reps - 1) / n)
+            rows.append({"level": lvl, "m_l": mean, "V_l": var, "walks": int(t[2]),
+                         "jumps": int(t[1]), "seconds": sec})
+        fine = [r for r in rows if r["level"] >= 3]
+        lv = [r["level"] for r in fine]
+        out["networks"][f"n={n}"] = {
+            "n": n, "nnz": a.nnz, "max_degree": int(np.diff(a.row_ptr).max()),
+            "walks_per_row": reps, "levels": rows,
+            "slope_log2_abs_m_l": _slope(lv, [np.log2(abs(r["m_l"])) if r["m_l"] else np.nan for r in fine]),
+            "slope_log2_V_l": _slope(lv, [np.log2(r["V_l"]) if r["V_l"] > 0 else np.nan for r in fine])}
+        log(f"n={n}: slopes m_l {out['networks'][f'n={n}']['slope_log2_abs_m_l']}, "
+            f"V_l {out['networks'][f'n={n}']['slope_log2_V_l']}")
+        plan.close()
+    print(json.dumps(out), flush=True)
+
+
+def run_complexity_workload(args):
+    """Time to tolerance of MLMC and of single-level Monte Carlo (Fig. 5) and
+    the MLMC time against the initial level l0 (Fig. 4), on total and single
+    node communicability (beta = 1, v = 1) of a Newman-Watts small-world
+    network with n = 1e6, FP32 walks.  The single-level run uses the finest
+    level the MLMC run reached at the same tolerance (the same splitting-bias
+    budget).  Besides GPU seconds, the cost is given in the paper's units
+    (Eq. 14: sum over levels of M_l (N_l + jumps)), where the interval loop
+    makes a fine level expensive; the event-driven walk's cost per walk does
+    not grow with the level."""
+    import torch
+    import mlmc_inputs as I
+    import __graft_entry__ as g
+    g.build()
+    from paper_1904_12754_gb300 import mlmc as M
+    stream = torch.cuda.current_stream()
+    n = 10 ** 6
+    a = I.small_world(n, 2, 0.1, seed=20190429)
+    dv = torch.ones(n, dtype=torch.float64, device="cuda")
+    node = 0
+
+    def solve(target, tol, l0=-1, levels=3, max_levels=12, seed=5):
+        sched = M.schedule_default(precision=M.FP32_KAHAN, num_levels=levels, max_levels=max_levels,
+                                   time_budget_s=60.0)
+        if l0 >= 0:
+            sched.l0 = l0
+        with M.Plan.from_csr(a, 1.0, sched, rel_tol=tol, stream=stream.cuda_stream) as plan:
+            best = None
+            for rep in range(3):  # first solve warms up; keep the fastest of the others
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                if target == "entry":
+                    val = plan.expmv_entry(node, dv, seed=seed + rep, allow_not_converged=True)
+                else:
+                    val = plan.expmv_sum(dv, seed=seed + rep, allow_not_converged=True)
+                sec = time.perf_counter() - t0
+                lv, est = plan.stats()
+                rows = 1 if target == "entry" else n
+                walks = sum(l["walks_per_row"] for l in lv) * rows
+                paper_cost = sum(l["walks_per_row"] * rows * (2 ** l["level"]) + l["jumps"] for l in lv)
+                rec = {"seconds": sec, "value": val, "est_rel_err": est, "levels": [l["level"] for l in lv],
+                       "walks": walks, "paper_cost_units": paper_cost,
+                       "events": sum(l["walks_per_row"] * rows + l["jumps"] for l in lv)}
+                if rep > 0 and (best is None or sec < best["seconds"]):
+                    best = rec
+            return best
+
+    tols = [1e-2, 5e-3, 2.5e-3, 1.25e-3, 6.25e-4]
+    fig5 = {}
+    for target in ("entry", "sum"):
+        res = []
+        for tol in tols:
+            ml = solve(target, tol)
+            finest = max(ml["levels"])
+            mc = solve(target, tol, l0=finest, levels=1, max_levels=1)
+            res.append({"tol": tol, "mlmc": ml, "mc_single_level": dict(mc, level=finest)})
+            log(f"{target} tol {tol:g}: MLMC {ml['seconds']:.4f} s (levels {ml['levels']}), "
+                f"MC at level {finest} {mc['seconds']:.4f} s")
+        lt = np.log10(tols)
+        fig5[target] = {
+            "runs": res,
+            "slope_log10_seconds": {"mlmc": _slope(lt, [np.log10(r["mlmc"]["seconds"]) for r in res]),
+                                    "mc": _slope(lt, [np.log10(r["mc_single_level"]["seconds"]) for r in res])},
+            "slope_log10_paper_cost": {
+                "mlmc": _slope(lt, [np.log10(r["mlmc"]["paper_cost_units"]) for r in res]),
+                "mc": _slope(lt, [np.log10(r["mc_single_level"]["paper_cost_units"]) for r in res])},
+            "slope_log10_events": {
+                "mlmc": _slope(lt, [np.log10(r["mlmc"]["events"]) for r in res]),
+                "mc": _slope(lt, [np.log10(r["mc_single_level"]["events"]) for r in res])}}
+    fig4 = []
+    for l0 in range(0, 8):
+        r = solve("sum", 6.25e-4, l0=l0)
+        fig4.append(dict(r, l0=l0))
+        log(f"l0 sweep: l0={l0} {r['seconds']:.4f} s, levels {r['levels']}")
+    tb_l0 = None
+    with M.Plan.from_csr(a, 1.0, M.schedule_default(precision=M.FP32_KAHAN), rel_tol=1e-3,
+                         stream=stream.cuda_stream) as plan:
+        tb_l0 = plan.info()["l0"]
+    out = {"metric": "MLMC vs single-level MC time to tolerance; MLMC time vs l0",
+           "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "Newman-Watts small world n=1e6 k=2 p=0.1, beta=1, v=1",
+                      "nnz": a.nnz, "max_degree": int(np.diff(a.row_ptr).max()), "entry_node": node,
+                      "l0_eq16": tb_l0},
+           "fig5_time_vs_tol": fig5, "fig4_time_vs_l0": fig4}
+    print(json.dumps(out), flush=True)
+
+
 
 def main():
     ap = argparse.ArgumentParser()
@@ -790,11 +940,14 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=15.0)
     ap.add_argument("--step-budget", type=float, default=8.0,
                     help="controller wall-clock budget of one step (s)")
-    ap.add_argument("--workload", choices=["tc", "batch", "learned", "precision", "kernel"],
+    ap.add_argument("--workload", choices=["tc", "batch", "learned", "precision", "kernel",
+                                           "levels", "complexity"],
                     default="tc",
                     help="tc: the metric's workload (default); batch: batched vs plain; "
                          "learned: learned proposal vs plain; precision: FP32 vs FP64 walk; "
-                         "kernel: the walk kernel alone")
+                         "kernel: the walk kernel alone; levels: m_l and V_l vs level; "
+                         "complexity: MLMC vs single-level MC and the l0 sweep")
+    ap.add_argument("--max-level", type=int, default=10, help="--workload levels: finest level")
     ap.add_argument("--kernel-reps", type=int, default=4096,
                     help="walks per row of one launch in --workload kernel")
     ap.add_argument("--kernel-matrix", choices=["ba", "lap3d"], default="ba",
@@ -816,6 +969,10 @@ def main():
         run_precision_workload(args)
     elif args.workload == "kernel":
         run_kernel_workload(args)
+    elif args.workload == "levels":
+        run_levels_workload(args)
+    elif args.workload == "complexity":
+        run_complexity_workload(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

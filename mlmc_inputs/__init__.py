@@ -160,6 +160,33 @@ def ba_graph(n: int, m: int, seed: int) -> CSR:
     return to_csr(a)
 
 
+def small_world(n: int, k: int, p: float, seed: int) -> CSR:
+    """Symmetric 0/1 adjacency of a Newman-Watts small-world network: a ring
+    on which every node links to its k nearest neighbours on each side, plus,
+    for each of the n k ring edges independently with probability p, a
+    shortcut from the edge's first node to a node drawn uniformly from the
+    other n - 1.  Shortcuts that repeat an existing edge are merged (0/1
+    entries); there are no self-loops.  Stands in for the paper's small-world
+    test networks (Sec. 4-5)."""
+    if n < 2 * k + 2:
+        raise ValueError("need n >= 2k + 2")
+    rng = np.random.default_rng(seed)
+    i = np.repeat(np.arange(n, dtype=np.int64), k)
+    m = np.tile(np.arange(1, k + 1, dtype=np.int64), n)
+    ring_dst = (i + m) % n
+    take = rng.random(n * k) < p
+    u = rng.integers(0, n - 1, size=n * k)
+    short_dst = np.where(u >= i, u + 1, u)      # uniform over the other n - 1 nodes
+    src = np.concatenate([i, i[take]])
+    dst = np.concatenate([ring_dst, short_dst[take]])
+    r = np.concatenate([src, dst])
+    c = np.concatenate([dst, src])
+    a = sp.csr_matrix((np.ones(r.size), (r, c)), shape=(n, n))
+    a.sum_duplicates()
+    a.data[:] = 1.0
+    return to_csr(a)
+
+
 def random_sparse(n: int, per_row: int, seed: int, signed: bool = True,
                   diag: bool = True, scale: float = 1.0) -> CSR:
     """Random sparse matrix with about ``per_row`` off-diagonal entries per
