@@ -382,6 +382,8 @@ typedef struct {
     int32_t precision;         /* ORC_FP64 or ORC_FP32 time arithmetic */
     int32_t variant;           /* ORC_RESIDUAL, ORC_REDRAW, ORC_LITERAL_RATE */
     int64_t max_jumps;
+    const double *f;           /* NULL, or the constant source vector F of Algorithm 3 */
+    double t;                  /* the time t (the source term's quadrature step is t/N) */
 } orc_ctx;
 
 typedef struct {
@@ -395,6 +397,8 @@ typedef struct {
     double log_c;      /* coarse exponent (0 at the coarsest level) */
     int32_t status;
     int32_t pad;
+    double src;        /* source part (Algorithm 3): fine minus coarse Simpson sums */
+    double src_abs;    /* |fine part| + |coarse part| (scale of its rounding) */
 } orc_walk_rec;
 
 /* Counter layout: (rep bits 0-31, row, draw index, level | variant<<6 |
@@ -510,6 +514,14 @@ static int orc_walk_core(const orc_ctx *c, int64_t row, orc_ctr kc, int level, i
     double log_f = 0.0, log_c = 0.0, diff = 0.0;
     double log_is = 0.0;  /* sum of log(k/q) over the jumps (proposal tables) */
     int64_t x_prev2 = row, x_prev1 = row; /* states at grid points 2j-2, 2j-1 */
+    /* Algorithm 3 (reading R17): Simpson sums over the grid points of
+     * w_n sign(t_n) eta(t_n) F at the state occupied at t_n; the fine rule
+     * on the N steps (weights 1, 4, 2, ..., 4, 1), the coarse one on the
+     * N/2 steps of level l-1 (the even grid points).  Grid point 0: weight
+     * 1, eta 1, the start row. */
+    const int src_on = c->f != NULL && N >= 2;
+    double integ2 = src_on ? c->f[row] : 0.0;
+    double integ1 = integ2;
 
     orc_draw_k(c, kc, ndraw++, x);
     double t_next = orc_hold(c, j, x, 0.0);
@@ -542,6 +554,15 @@ static int orc_walk_core(const orc_ctx *c, int64_t row, orc_ctr kc, int level, i
         g = c->dl[j] / (double)N;
         eta2 = eta2 * exp(g / 2.0);
         if (step % 2 == 0) eta1 = eta1 * exp(g);
+        if (src_on) {
+            double w = (step == N) ? 1.0 : ((step % 2 != 0) ? 4.0 : 2.0);
+            integ2 = integ2 + w * (double)sign * eta2 * c->f[j];
+            if (step % 2 == 0) {
+                int64_t m = step / 2;
+                double wc = (m == N / 2) ? 1.0 : ((m % 2 != 0) ? 4.0 : 2.0);
+                integ1 = integ1 + wc * (double)sign * eta1 * c->f[j];
+            }
+        }
         if (step % 2 == 0) {
             /* Pair (X_{step-2}, X_{step-1}, X_step) of Eq. 7. */
             double d0 = c->dl[x_prev2] / (double)N;
@@ -567,12 +588,20 @@ done:
     out->hash = hash;
     out->status = status;
     out->pad = 0;
+    out->src = 0.0;
+    out->src_abs = 0.0;
     if (status != ORC_OK) {
         out->y = 0.0;
         out->y_alg2 = 0.0;
         out->log_f = 0.0;
         out->log_c = 0.0;
         return status;
+    }
+    if (src_on) {
+        double sf = c->t / (3.0 * (double)N) * integ2;
+        double sc = (coarse && N >= 4) ? 2.0 * c->t / (3.0 * (double)N) * integ1 : 0.0;
+        out->src = sf - sc;
+        out->src_abs = fabs(sf) + fabs(sc);
     }
     double uj = use_v_end ? c->v[j] : 1.0;
     out->log_f = log_f;
@@ -673,8 +702,9 @@ int orc_mlmcl(const orc_ctx *c, int64_t row_begin, int64_t row_end, int64_t rep_
         orc_walk_rec r;
         for (int64_t k = 0; k < reps; ++k) {
             if (orc_walk(c, i, rep_begin + k, level, coarse, &r) != ORC_OK) lim++;
-            s = s + r.y;
-            s2 = s2 + r.y * r.y;
+            double yt = r.y + r.src;  /* with a source term: both parts of the sample */
+            s = s + yt;
+            s2 = s2 + yt * yt;
             jj += r.jumps;
         }
         sum_y[i] = sum_y[i] + s;

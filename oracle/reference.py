@@ -22,6 +22,8 @@ matrix products as the only library primitives:
   (tiny n and N only).
 * :func:`dst_expmv_laplacian_2d` -- the closed form of exp(tA)v for the 2D
   Dirichlet Laplacian by its sine eigenbasis.
+* :func:`strang_source`, :func:`expmv_source_exact` -- the level-l mean of
+  Algorithm 3's Simpson source term and the exact int_0^t exp(sA) f ds.
 """
 from __future__ import annotations
 
@@ -198,6 +200,50 @@ def strang_forward(a, t: float, v: np.ndarray, level: int) -> np.ndarray:
         w = dense @ w if dense is not None else expmv_taylor(minus_tbt, dt, w)
         w = half * w
     return w
+
+
+def _strang_step_operator(a, dt: float):
+    """One step of Eq. 2 as a callable w -> e^{dt D/2} e^{-dt T} e^{dt D/2} w."""
+    d, minus_t = _split_sparse(a)
+    half = np.exp(dt * d / 2.0)
+    dense = expm_pade13(dt * minus_t.toarray()) if a.shape[0] <= 2048 else None
+
+    def step(w):
+        w = half * w
+        w = dense @ w if dense is not None else expmv_taylor(minus_t, dt, w)
+        return half * w
+    return step
+
+
+def strang_source(a, t: float, f: np.ndarray, level: int, coarse: bool = False) -> np.ndarray:
+    """Mean of the source part of Algorithm 3 at level l (reading R17): the
+    Simpson rule (h/3) sum_{n=0}^{K} w_n S^n f over K steps of length h with
+    weights 1, 4, 2, 4, ..., 4, 1, where S is the one-step Strang operator of
+    Eq. 2 for step h.  coarse=False: K = N = 2^level, h = t/N; coarse=True:
+    the same path's level-(l-1) rule, K = N/2, h = 2t/N.  K must be even."""
+    n_steps = (1 << level) // (2 if coarse else 1)
+    if n_steps < 2 or n_steps % 2:
+        raise ValueError("Simpson's rule needs an even number of steps >= 2")
+    h = t / n_steps
+    step = _strang_step_operator(sp.csr_matrix(a, dtype=np.float64), h)
+    w = np.array(f, dtype=np.float64, copy=True)
+    acc = w.copy()                              # n = 0, weight 1
+    for k in range(1, n_steps + 1):
+        w = step(w)
+        weight = 1.0 if k == n_steps else (4.0 if k % 2 else 2.0)
+        acc = acc + weight * w
+    return (h / 3.0) * acc
+
+
+def expmv_source_exact(a, t: float, f: np.ndarray) -> np.ndarray:
+    """int_0^t exp(sA) f ds, from the exponential of the augmented matrix
+    [[tA, t f], [0, 0]] (its top-right column; dense, n <= 4096)."""
+    dense = a.toarray() if sp.issparse(a) else np.asarray(a, dtype=np.float64)
+    n = dense.shape[0]
+    m = np.zeros((n + 1, n + 1))
+    m[:n, :n] = t * dense
+    m[:n, n] = t * np.asarray(f, dtype=np.float64)
+    return expm_pade13(m)[:n, n]
 
 
 def level_means(a, t: float, v: np.ndarray, l0: int, top: int):

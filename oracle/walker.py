@@ -41,13 +41,13 @@ class WalkRec(ct.Structure):
     _fields_ = [("end", ct.c_int32), ("jumps", ct.c_int32), ("sign", ct.c_int32),
                 ("hash", ct.c_uint32), ("y", ct.c_double), ("y_alg2", ct.c_double),
                 ("log_f", ct.c_double), ("log_c", ct.c_double), ("status", ct.c_int32),
-                ("pad", ct.c_int32)]
+                ("pad", ct.c_int32), ("src", ct.c_double), ("src_abs", ct.c_double)]
 
 
 WALK_DTYPE = np.dtype([("end", np.int32), ("jumps", np.int32), ("sign", np.int32),
                        ("hash", np.uint32), ("y", np.float64), ("y_alg2", np.float64),
                        ("log_f", np.float64), ("log_c", np.float64), ("status", np.int32),
-                       ("pad", np.int32)])
+                       ("pad", np.int32), ("src", np.float64), ("src_abs", np.float64)])
 assert WALK_DTYPE.itemsize == ct.sizeof(WalkRec)
 
 
@@ -56,8 +56,9 @@ class Ctx(ct.Structure):
                 ("dl", ct.c_void_p), ("inv_rate", ct.c_void_p), ("inv_rate32", ct.c_void_p),
                 ("thr", ct.c_void_p), ("keep_col", ct.c_void_p), ("keep_neg", ct.c_void_p),
                 ("alias_col", ct.c_void_p), ("alias_neg", ct.c_void_p), ("v", ct.c_void_p),
-                ("lr_keep", ct.c_void_p), ("lr_alias", ct.c_void_p), ("seed", ct.c_uint64), ("precision", ct.c_int32), ("variant", ct.c_int32),
-                ("max_jumps", ct.c_int64)]
+                ("lr_keep", ct.c_void_p), ("lr_alias", ct.c_void_p), ("seed", ct.c_uint64),
+                ("precision", ct.c_int32), ("variant", ct.c_int32), ("max_jumps", ct.c_int64),
+                ("f", ct.c_void_p), ("t", ct.c_double)]
 
 
 def lib():
@@ -190,18 +191,24 @@ class Walker:
     """Replays walks of Algorithm 2 on one matrix, time and right-hand side."""
 
     def __init__(self, a, t: float, v: np.ndarray, seed: int, precision: int = FP64,
-                 variant: int = RESIDUAL, max_jumps: int = 1 << 30, tables: Tables = None):
+                 variant: int = RESIDUAL, max_jumps: int = 1 << 30, tables: Tables = None,
+                 f: np.ndarray = None):
+        """f: the constant source vector of Algorithm 3 (None: no source term);
+        with it every walk also carries its Simpson source part (record field
+        `src`), and mlmcl sums y + src."""
         self.tables = tables if tables is not None else build_tables(a, t)
         self.v = np.ascontiguousarray(v, dtype=np.float64)
+        self.f = None if f is None else np.ascontiguousarray(f, dtype=np.float64)
         tb = self.tables
-        self._keep = (tb, self.v)
+        self._keep = (tb, self.v, self.f)
         lrk = _p(tb.lr_keep).value if tb.lr_keep is not None else None
         lra = _p(tb.lr_alias).value if tb.lr_alias is not None else None
         self.ctx = Ctx(tb.n, _p(tb.row_ptr).value, _p(tb.deg).value, _p(tb.dl).value,
                        _p(tb.inv_rate).value, _p(tb.inv_rate32).value, _p(tb.thr).value,
                        _p(tb.keep_col).value, _p(tb.keep_neg).value, _p(tb.alias_col).value,
                        _p(tb.alias_neg).value, _p(self.v).value, lrk, lra, ct.c_uint64(seed),
-                       precision, variant, max_jumps)
+                       precision, variant, max_jumps,
+                       _p(self.f).value if self.f is not None else None, float(t))
 
     def walk(self, row: int, rep: int, level: int, coarse: bool) -> WalkRec:
         r = WalkRec()
