@@ -175,6 +175,24 @@ mlmc_status mlmc_plan_rebuild(mlmc_plan *plan);
  * once (the call synchronises the plan's stream to validate it). */
 mlmc_status mlmc_plan_set_proposal(mlmc_plan *plan, const float *h, double alpha);
 
+/* Source term of an inhomogeneous system du/dt = A u + F with constant F
+ * (Sec. 5: the solution exp(tA) u0 + int_0^t exp(sA) F ds, the integral by
+ * Simpson's rule on each level's time grid, evaluated along the same walks as
+ * the exponential; Algorithm 3).  With f (n finite doubles, host or device)
+ * every later walk of the plan (mlmc_expmv, mlmc_expmv_entry,
+ * mlmc_expmv_sum, mlmc_mlmcl, mlmc_trace, mlmc_trace_noalloc) adds to its
+ * sample t/(3N) sum_k w_k sign(t_k) eta(t_k) F[X(t_k)] over the N + 1 grid
+ * points of its level (w = 1, 4, 2, ..., 4, 1; eta the Strang weight of
+ * Eq. 2 at t_k) and, above l0, subtracts the same sum of level l-1 (N/2
+ * steps of 2t/N), so mlmc_expmv returns the solution u(t) with u0 = v.
+ * The closed form of the geometric sum over each holding segment keeps the
+ * cost per walk independent of N.  Needs a backward-mode plan with l0 >= 1
+ * (Simpson needs an even number of steps on every level) and no proposal;
+ * mlmc_mlmcl / mlmc_trace then need level >= 1 (>= 2 when coarse).  Batches
+ * do not take plans with a source.  f = NULL removes the source term.
+ * Synchronises the plan's stream (f is validated on the host). */
+mlmc_status mlmc_plan_set_source(mlmc_plan *plan, const double *f);
+
 /* The proposal tables, exported like mlmc_export_tables (positions
  * row_ptr[i] + b for bucket b < deg_i), plus lr_keep / lr_alias = log(k/q)
  * of the kept and alias columns.  Any pointer may be NULL.  Synchronises. */

@@ -72,6 +72,8 @@ void free_plan(mlmc_plan* p) {
   cudaFree(p->d_alias);
   cudaFree(p->d_alias_is);
   cudaFree(p->d_h);
+  cudaFree(p->d_src);
+  cudaFree(p->d_src32);
   cudaFree(p->d_flags);
   cudaFree(p->d_work);
   cudaFree(p->d_totals);
@@ -429,6 +431,35 @@ mlmc_status mlmc_plan_rebuild(mlmc_plan* p) {
   return MLMC_OK;
 }
 
+mlmc_status mlmc_plan_set_source(mlmc_plan* p, const double* f) {
+  if (!p) return fail(MLMC_ERR_INVALID_ARG, "NULL plan");
+  if (!f) {
+    p->source_active = false;
+    return MLMC_OK;
+  }
+  if (forward_mode(p)) return fail(MLMC_ERR_INVALID_ARG, "mlmc_plan_set_source: backward-mode plans only");
+  if (p->proposal_active)
+    return fail(MLMC_ERR_INVALID_ARG, "mlmc_plan_set_source: remove the proposal first");
+  if (p->l0 < 1)
+    return fail(MLMC_ERR_INVALID_ARG,
+                "mlmc_plan_set_source: Simpson's rule needs an even number of steps on every "
+                "level; create the plan with l0 >= 1");
+  if (!p->d_src) {
+    MLMC_CUDA(dev_alloc(&p->d_src, static_cast<size_t>(p->n)), "alloc source");
+    MLMC_CUDA(dev_alloc(&p->d_src32, static_cast<size_t>(p->n)), "alloc source");
+  }
+  MLMC_CUDA(cudaMemcpyAsync(p->d_src, f, sizeof(double) * p->n, cudaMemcpyDefault, p->stream),
+            "copy source");
+  std::vector<double> hf(p->n);
+  MLMC_CUDA(cudaMemcpyAsync(hf.data(), p->d_src, sizeof(double) * p->n, cudaMemcpyDeviceToHost,
+                            p->stream), "read source");
+  MLMC_CUDA(cudaStreamSynchronize(p->stream), "synchronize");
+  for (double x : hf)
+    if (!std::isfinite(x)) return fail(MLMC_ERR_INVALID_ARG, "mlmc_plan_set_source: f must be finite");
+  p->source_active = true;
+  return MLMC_OK;
+}
+
 mlmc_status mlmc_plan_set_proposal(mlmc_plan* p, const float* h, double alpha) {
   if (!p) return fail(MLMC_ERR_INVALID_ARG, "NULL plan");
   if (!h) {
@@ -436,6 +467,8 @@ mlmc_status mlmc_plan_set_proposal(mlmc_plan* p, const float* h, double alpha) {
     p->sched.proposal = MLMC_PLAIN;
     return MLMC_OK;
   }
+  if (p->source_active)
+    return fail(MLMC_ERR_INVALID_ARG, "mlmc_plan_set_proposal: the plan has a source term");
   if (!(alpha > 0.0) || !(alpha <= 1.0))
     return fail(MLMC_ERR_INVALID_ARG, "alpha must be in (0, 1]: the proposal mixes in the plain law");
   if (!p->d_alias_is) {
@@ -504,6 +537,8 @@ mlmc_status mlmc_mlmcl(mlmc_plan* p, int32_t level, int32_t coarse, int64_t rep_
   if (!p || !v || !sum_y || !totals) return fail(MLMC_ERR_INVALID_ARG, "NULL argument");
   if (level < 0 || level > 24 || (coarse && level < 1))
     return fail(MLMC_ERR_INVALID_ARG, "level must be in [0,24] (>= 1 when coarse)");
+  if (p->source_active && (level < 1 || (coarse && level < 2)))
+    return fail(MLMC_ERR_INVALID_ARG, "with a source term the level must be >= 1 (>= 2 when coarse)");
   if (rep_begin < 0 || reps < 0 || rep_begin + reps > (1ll << 56))
     return fail(MLMC_ERR_INVALID_ARG, "replica range out of [0, 2^56)");
   WalkLaunch w;
@@ -528,6 +563,8 @@ mlmc_status mlmc_trace(mlmc_plan* p, int32_t level, int32_t coarse, int64_t rep_
   if (!p || !v || !rec) return fail(MLMC_ERR_INVALID_ARG, "NULL argument");
   if (level < 0 || level > 24 || (coarse && level < 1))
     return fail(MLMC_ERR_INVALID_ARG, "level must be in [0,24] (>= 1 when coarse)");
+  if (p->source_active && (level < 1 || (coarse && level < 2)))
+    return fail(MLMC_ERR_INVALID_ARG, "with a source term the level must be >= 1 (>= 2 when coarse)");
   if (rep_begin < 0 || reps < 0 || rep_begin + reps > (1ll << 56))
     return fail(MLMC_ERR_INVALID_ARG, "replica range out of [0, 2^56)");
   double* scratch = nullptr;

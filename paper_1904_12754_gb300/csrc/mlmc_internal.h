@@ -124,6 +124,11 @@ struct mlmc_plan {
   float* d_h = nullptr;
   double alpha = 0.0;
   bool proposal_active = false;
+  // Source term (mlmc_plan_set_source): when active every walk also carries
+  // the Simpson sums of F along its path (Algorithm 3).
+  double* d_src = nullptr;   // [n] F
+  float* d_src32 = nullptr;  // [n] FP32 copy for the FP32 walk
+  bool source_active = false;
 
   // Work buffers.
   uint32_t* d_flags = nullptr;                 // [4]

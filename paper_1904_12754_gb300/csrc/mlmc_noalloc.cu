@@ -53,6 +53,9 @@ extern "C" mlmc_status mlmc_trace_noalloc(mlmc_plan* p, int32_t level, int32_t c
   if (level < 0 || level > 24 || (coarse && level < 1))
     return noalloc_fail(MLMC_ERR_INVALID_ARG,
                         "mlmc_trace_noalloc: level must be in [0,24] (>= 1 when coarse)");
+  if (p->source_active && (level < 1 || (coarse && level < 2)))
+    return noalloc_fail(MLMC_ERR_INVALID_ARG,
+                        "mlmc_trace_noalloc: with a source term the level must be >= 1 (>= 2 when coarse)");
   if (rep_begin < 0 || reps < 0 || rep_begin + reps > (int64_t{1} << 56))
     return noalloc_fail(MLMC_ERR_INVALID_ARG, "mlmc_trace_noalloc: replica range out of [0, 2^56)");
   if (p->sched.mode == MLMC_FORWARD)

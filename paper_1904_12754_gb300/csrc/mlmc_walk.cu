@@ -65,6 +65,8 @@ struct WalkArgs {
   mlmc_walk_record* trace;
   int64_t trace_stride;    // records per row (the whole replica range)
   int64_t trace_base;      // offset of this launch's first replica
+  const void* f_walk;      // source vector in the walk precision (source walks only)
+  double t;                // the time t (source walks only)
 };
 
 // Key sources of the walk's draws: the round keys of a launch-constant
@@ -220,6 +222,8 @@ struct ItemArgs {
   mlmc_walk_record* trace;
   int64_t trace_stride;
   int64_t trace_base;
+  const void* f_walk;     // source vector (source walks only)
+  double t;               // the time t (source walks only)
 };
 
 // Per-warp running totals of the walks a warp has finished.
@@ -320,6 +324,42 @@ struct EndQueue {
 };
 constexpr int kMaxWarps = 8;  // blocks of at most 256 threads
 
+// Source term (Algorithm 3, Simpson's rule on a grid of K steps, K even): the
+// weighted sum over grid points k in (a, b] of w_k e^{W_k / K}, where the walk
+// holds one state (scaled rate term dl) on (a, b], W_k = P_a + (k - a) dl -
+// (dl0 + dl)/2 is the Strang exponent at grid point k (P_a: the sum of the
+// scaled d of the states at grid points 0..a, dl0: the start state's), and
+// w_k = 1 at k = 0 and k = K, 4 at odd k, 2 at even k in between.  With
+// r = e^{dl/K} the terms are geometric: sum_k (3 - (-1)^k) r^k in closed
+// form, minus one term at each end point of the grid that (a, b] contains.
+template <bool FP64>
+__device__ __forceinline__ typename Prec<FP64>::T simpson_segment(
+    int a, int b, int K, typename Prec<FP64>::T inv_k, typename Prec<FP64>::T pa,
+    typename Prec<FP64>::T dl, typename Prec<FP64>::T dl0) {
+  using P = Prec<FP64>;
+  using T = typename P::T;
+  const int L = b - a;
+  if (L <= 0) return static_cast<T>(0);
+  const T h = P::mul(dl, inv_k);  // exponent step per grid step
+  // exponent at grid point a + 1
+  const T e1 = P::mul(P::add(P::sub(pa, P::mul(dl0, static_cast<T>(0.5))),
+                             P::mul(dl, static_cast<T>(0.5))), inv_k);
+  const T em1 = P::exm1(P::mul(P::from_int(L), h));           // r^L - 1
+  // sum_{q < L} r^q and sum_{q < L} (-r)^q = (1 - (-r)^L) / (1 + r)
+  const T g1 = (h == static_cast<T>(0)) ? P::from_int(L) : em1 / P::exm1(h);
+  const T rl = P::add(em1, static_cast<T>(1));
+  const T g2 = ((L & 1) ? P::add(static_cast<T>(1), rl) : P::sub(static_cast<T>(1), rl)) /
+               P::add(static_cast<T>(1), P::ex(h));
+  // (3 - (-1)^k) r^k summed over k = a+1 .. b, divided by r^{a+1}
+  const T sgeo = ((a + 1) & 1) ? P::add(P::mul(static_cast<T>(3), g1), g2)
+                               : P::sub(P::mul(static_cast<T>(3), g1), g2);
+  T total = P::mul(P::ex(e1), sgeo);
+  if (a < 0) total = P::sub(total, static_cast<T>(1));       // k = 0: weight 1, e^0
+  if (b == K)                                                 // k = K: weight 1
+    total = P::sub(total, P::ex(P::add(e1, P::mul(P::from_int(K - a - 1), h))));
+  return total;
+}
+
 // FP32 walks: the largest uniform index i (u = (2i+1) 2^-24, i < 2^23) whose
 // first holding time fl(-ln(u)) / (t L_row) reaches s = 1, or -1 if none.  The
 // holding time is non-increasing in i (the FP32 -ln(u) is strictly
@@ -374,7 +414,8 @@ __device__ __forceinline__ int32_t still_index32(float inv_rate, int lane) {
 // counter, so the trajectories are those of the walk-by-walk definition.
 // Adds the item's sum of Y to a.sum_y[row] (one atomic) and its totals to
 // `tot`.
-template <bool FP64, bool COARSE, bool TRACE, bool IS, class Keys, bool kScreen = true>
+template <bool FP64, bool COARSE, bool TRACE, bool IS, class Keys, bool kScreen = true,
+          bool SRC = false>
 __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, int64_t row,
                                           int64_t r_lo, int64_t r_hi,
                                           LaneTotals<typename Prec<FP64>::T>& tot,
@@ -406,6 +447,24 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
   // as the grid weights sum to 1), the same for every such walk.
   T y_still = 0;
   if (!COARSE) y_still = P::mul(static_cast<T>(__ldg(vv + row)), P::ex(dl0));
+  // Source term: the sample also gets t/(3N) times the fine Simpson sum
+  // minus, above l0, 2t/(3N) times the coarse one (level l-1's rule on the
+  // even grid points).  A walk that never jumps has a fixed source part.
+  const VT* __restrict__ ff = static_cast<const VT*>(a.f_walk);
+  const T src_scale_f = SRC ? static_cast<T>(a.t / (3.0 * n_grid)) : static_cast<T>(0);
+  const T src_scale_c = SRC ? static_cast<T>(2.0 * a.t / (3.0 * n_grid)) : static_cast<T>(0);
+  const T inv_nc = P::mul(inv_n, static_cast<T>(2));
+  if (SRC) {
+    const T fr = static_cast<T>(__ldg(ff + row));
+    T ys = P::mul(src_scale_f,
+                  P::mul(fr, simpson_segment<FP64>(-1, n_grid, n_grid, inv_n, static_cast<T>(0),
+                                                   dl0, dl0)));
+    if (COARSE)
+      ys = P::sub(ys, P::mul(src_scale_c,
+                             P::mul(fr, simpson_segment<FP64>(-1, n_coarse, n_coarse, inv_nc,
+                                                              static_cast<T>(0), dl0, dl0))));
+    y_still = P::add(y_still, ys);
+  }
   if (!isfinite(y_still)) {
     tot.bad |= kFlagNonFiniteY;
     y_still = 0;
@@ -436,6 +495,7 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
   int kprev = -1;          // grid index of the segment start (fine)
   T lw = 0;                // proposal only: sum of log(k/q) over the jumps
   uint32_t hash = 2166136261u;
+  T src_f = 0, src_c = 0;  // source only: fine and coarse Simpson sums so far
 
   // Start walk r of the item (state at s = 0 in the row).
   auto start_walk = [&](uint32_t r_new) {
@@ -453,12 +513,27 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
     kprev = -1;
     lw = 0;
     hash = 2166136261u;
+    src_f = 0;
+    src_c = 0;
+  };
+  // Source term: add the Simpson sums of the segment (kprev, b] held in
+  // state j (sign neg) before the exponent sums move past it.
+  auto source_segment = [&](int b) {
+    const T fj = static_cast<T>(__ldg(ff + j));
+    const T sfj = neg ? -fj : fj;
+    const T dlj = static_cast<T>(m.dl);
+    const T pa = COARSE ? P::add(P::add(acc, acc), acc_d) : acc;  // fine prefix at kprev
+    src_f = P::add(src_f, P::mul(sfj, simpson_segment<FP64>(kprev, b, n_grid, inv_n, pa, dlj, dl0)));
+    if (COARSE)
+      src_c = P::add(src_c, P::mul(sfj, simpson_segment<FP64>(kprev >> 1, b >> 1, n_coarse, inv_nc,
+                                                             acc, dlj, dl0)));
   };
   // Jump at time s_new (after fine grid point g) with bucket word xz and
   // alias coin xw: count the grid points of the segment that ends, pick the
   // next state from the alias table of the current one.
   auto jump = [&](T s_new, uint32_t xz, uint32_t xw) {
     const int g = P::floor_int(P::mul(s_new, n_fine));
+    if (SRC) source_segment(g);
     const T dlj = static_cast<T>(m.dl);
     if (COARSE) {
       const int kc_prev = kprev >> 1;   // floor(a/2), also for a = -1
@@ -493,10 +568,11 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
   // Sample of a walk that ended at s = 1 after e >= 1 jumps, from its
   // exponents: x1 = E_f (l0) or E_c (above), plus the proposal's log-ratio;
   // x2 = E_f - E_c (above l0); js = end state | sign << 31.
-  auto sample = [&](T x1, T x2, uint32_t js) {
+  auto sample = [&](T x1, T x2, uint32_t js, T extra) {
     const T vend = static_cast<T>(__ldg(vv + (js & kColMask)));
     T y = COARSE ? P::mul(vend, P::mul(P::ex(x1), P::exm1(x2))) : P::mul(vend, P::ex(x1));
     if (js >> 31) y = -y;
+    if (SRC) y = P::add(y, extra);
     if (!isfinite(y)) {
       tot.bad |= kFlagNonFiniteY;
       y = 0;
@@ -552,7 +628,7 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
       ++n_limit;
       acc_y.add(static_cast<T>(0));
       tot.y2.add_square(static_cast<T>(0));
-    } else if (!TRACE && defer) {
+    } else if (!TRACE && !SRC && defer) {
       exponents(end_x1, end_x2);
       ending = true;
       return;
@@ -561,7 +637,12 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
     if (status == 0) {
       T x1, x2;
       exponents(x1, x2);
-      y = sample(x1, x2, static_cast<uint32_t>(j) | (neg << 31));
+      T extra = 0;
+      if (SRC) {
+        source_segment(n_grid);
+        extra = P::sub(P::mul(src_scale_f, src_f), COARSE ? P::mul(src_scale_c, src_c) : static_cast<T>(0));
+      }
+      y = sample(x1, x2, static_cast<uint32_t>(j) | (neg << 31), extra);
     }
     if (TRACE) {
       mlmc_walk_record rec;
@@ -594,7 +675,7 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
       const uint32_t k = ehead + static_cast<uint32_t>(lane);
       if (k < etail) {
         const uint32_t slot = k & (kQueueCap - 1);
-        sample(eq->x1[slot], eq->x2[slot], eq->js[slot]);
+        sample(eq->x1[slot], eq->x2[slot], eq->js[slot], static_cast<T>(0));
       }
       ehead = min(ehead + 32u, etail);
       __syncwarp();
@@ -729,19 +810,21 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
   const unsigned long long jumps = warp_sum_u64(item_jumps);
   const unsigned long long still = warp_sum_u64(n_still);
   const unsigned long long limit = warp_sum_u64(n_limit);
+  // Walks that never jump: y_still each (0 above l0 unless a source term
+  // adds its fixed Simpson part).
   const double yc = static_cast<double>(y_still);
-  if (!COARSE) ys += static_cast<double>(still) * yc;
+  if (!COARSE || SRC) ys += static_cast<double>(still) * yc;
   if (lane == 0) {
     wc->walks += static_cast<unsigned long long>(r_hi - r_lo);
     wc->jumps += jumps;
     wc->still += still;
     wc->limit += limit;
-    if (!COARSE) wc->y2_fixed += static_cast<double>(still) * (yc * yc);
+    if (!COARSE || SRC) wc->y2_fixed += static_cast<double>(still) * (yc * yc);
   }
   if (lane == 0 && ys != 0.0) atomicAdd(a.sum_y + row, ys);
 }
 
-template <bool FP64, bool COARSE, bool TRACE, bool IS>
+template <bool FP64, bool COARSE, bool TRACE, bool IS, bool SRC = false>
 __global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk(const __grid_constant__ WalkArgs a) {
   using T = typename Prec<FP64>::T;
   const int lane = threadIdx.x & 31;
@@ -759,6 +842,8 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk(const __grid_constan
   ia.trace = a.trace;
   ia.trace_stride = a.trace_stride;
   ia.trace_base = a.trace_base;
+  ia.f_walk = a.f_walk;
+  ia.t = a.t;
   __shared__ WarpQueue<FP64> queues[kMaxWarps];
   __shared__ WarpCounters counters[kMaxWarps];
   __shared__ EndQueue<FP64> ends[kMaxWarps];
@@ -777,7 +862,8 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk(const __grid_constan
     const int64_t chunk = static_cast<int64_t>(item) - rel * a.chunks_per_row;
     const int64_t r_lo = chunk * a.chunk;
     const int64_t r_hi = min(r_lo + a.chunk, a.reps);
-    walk_item<FP64, COARSE, TRACE, IS>(ia, KeysFromParam{&a.rk}, a.row_begin + rel, r_lo, r_hi,
+    walk_item<FP64, COARSE, TRACE, IS, KeysFromParam, true, SRC>(ia, KeysFromParam{&a.rk},
+                                                                a.row_begin + rel, r_lo, r_hi,
                                        tot, wc, q, eq, lane);
   }
   flush_warp(tot, wc, a.totals, a.flags, lane);
@@ -864,6 +950,8 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4)
         st.ia.trace = nullptr;
         st.ia.trace_stride = 0;
         st.ia.trace_base = 0;
+        st.ia.f_walk = nullptr;
+        st.ia.t = 0.0;
         st.totals = pb.totals + static_cast<int64_t>(sg.slot) * kTotSlots;
         st.n = pb.n;
         st.reps = sg.reps;
@@ -1117,9 +1205,9 @@ cudaError_t launch_to_float(mlmc_plan* p, const double* in, float* out) {
   return cudaGetLastError();
 }
 
-template <bool FP64, bool COARSE, bool TRACE, bool IS>
+template <bool FP64, bool COARSE, bool TRACE, bool IS, bool SRC>
 cudaError_t launch_one(mlmc_plan* p, const WalkArgs& args, int block) {
-  auto kern = k_walk<FP64, COARSE, TRACE, IS>;
+  auto kern = k_walk<FP64, COARSE, TRACE, IS, SRC>;
   int per_sm = 0;
   cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, 0);
   if (err != cudaSuccess) return err;
@@ -1134,20 +1222,22 @@ cudaError_t launch_one(mlmc_plan* p, const WalkArgs& args, int block) {
   return cudaGetLastError();
 }
 
+// Proposal and source term are exclusive (checked when either is set).
 template <bool FP64, bool COARSE, bool TRACE>
-cudaError_t dispatch_is(mlmc_plan* p, const WalkArgs& a, int block, bool is) {
-  return is ? launch_one<FP64, COARSE, TRACE, true>(p, a, block)
-            : launch_one<FP64, COARSE, TRACE, false>(p, a, block);
+cudaError_t dispatch_is(mlmc_plan* p, const WalkArgs& a, int block, bool is, bool src) {
+  if (src) return launch_one<FP64, COARSE, TRACE, false, true>(p, a, block);
+  return is ? launch_one<FP64, COARSE, TRACE, true, false>(p, a, block)
+            : launch_one<FP64, COARSE, TRACE, false, false>(p, a, block);
 }
 
 cudaError_t dispatch_walk(mlmc_plan* p, const WalkArgs& a, int block, bool fp64, bool coarse,
-                          bool trace, bool is) {
+                          bool trace, bool is, bool src) {
   if (fp64) {
-    if (coarse) return trace ? dispatch_is<true, true, true>(p, a, block, is) : dispatch_is<true, true, false>(p, a, block, is);
-    return trace ? dispatch_is<true, false, true>(p, a, block, is) : dispatch_is<true, false, false>(p, a, block, is);
+    if (coarse) return trace ? dispatch_is<true, true, true>(p, a, block, is, src) : dispatch_is<true, true, false>(p, a, block, is, src);
+    return trace ? dispatch_is<true, false, true>(p, a, block, is, src) : dispatch_is<true, false, false>(p, a, block, is, src);
   }
-  if (coarse) return trace ? dispatch_is<false, true, true>(p, a, block, is) : dispatch_is<false, true, false>(p, a, block, is);
-  return trace ? dispatch_is<false, false, true>(p, a, block, is) : dispatch_is<false, false, false>(p, a, block, is);
+  if (coarse) return trace ? dispatch_is<false, true, true>(p, a, block, is, src) : dispatch_is<false, true, false>(p, a, block, is, src);
+  return trace ? dispatch_is<false, false, true>(p, a, block, is, src) : dispatch_is<false, false, false>(p, a, block, is, src);
 }
 
 template <bool FP64, bool COARSE, bool TRACE, bool IS>
@@ -1243,6 +1333,16 @@ cudaError_t launch_walk(mlmc_plan* p, const WalkLaunch& w, int64_t* launches) {
     if (cerr != cudaSuccess) return cerr;
     a.v_walk = p->d_v32;
   }
+  const bool src = p->source_active;
+  if (src) {
+    if (w.level < 1 || (w.coarse && w.level < 2)) return cudaErrorInvalidValue;
+    if (!fp64) {
+      cudaError_t cerr = launch_to_float(p, p->d_src, p->d_src32);
+      if (cerr != cudaSuccess) return cerr;
+    }
+    a.f_walk = fp64 ? static_cast<const void*>(p->d_src) : static_cast<const void*>(p->d_src32);
+    a.t = p->t;
+  }
   a.n = p->n;
   a.level = w.level;
   a.ctr3 = static_cast<uint32_t>(w.level) & 0x3Fu;
@@ -1280,7 +1380,7 @@ cudaError_t launch_walk(mlmc_plan* p, const WalkLaunch& w, int64_t* launches) {
                     static_cast<unsigned long long>(a.chunks_per_row);
     cudaError_t err = cudaMemsetAsync(p->d_work, 0, sizeof(unsigned long long), p->stream);
     if (err != cudaSuccess) return err;
-    err = dispatch_walk(p, a, block, fp64, w.coarse, trace, p->proposal_active);
+    err = dispatch_walk(p, a, block, fp64, w.coarse, trace, p->proposal_active, src);
     if (err != cudaSuccess) return err;
     if (launches) ++*launches;
   }
@@ -1305,6 +1405,16 @@ cudaError_t launch_walk_scratch(mlmc_plan* p, const WalkLaunch& w, unsigned long
     cudaError_t cerr = launch_to_float(p, w.v, v32);
     if (cerr != cudaSuccess) return cerr;
     a.v_walk = v32;
+  }
+  const bool src = p->source_active;
+  if (src) {
+    if (w.level < 1 || (w.coarse && w.level < 2)) return cudaErrorInvalidValue;
+    if (!fp64) {
+      cudaError_t cerr = launch_to_float(p, p->d_src, p->d_src32);
+      if (cerr != cudaSuccess) return cerr;
+    }
+    a.f_walk = fp64 ? static_cast<const void*>(p->d_src) : static_cast<const void*>(p->d_src32);
+    a.t = p->t;
   }
   a.n = p->n;
   a.level = w.level;
@@ -1339,7 +1449,7 @@ cudaError_t launch_walk_scratch(mlmc_plan* p, const WalkLaunch& w, unsigned long
                     static_cast<unsigned long long>(a.chunks_per_row);
     cudaError_t err = cudaMemsetAsync(work, 0, sizeof(unsigned long long), p->stream);
     if (err != cudaSuccess) return err;
-    err = dispatch_walk(p, a, block, fp64, w.coarse, trace, p->proposal_active);
+    err = dispatch_walk(p, a, block, fp64, w.coarse, trace, p->proposal_active, src);
     if (err != cudaSuccess) return err;
     if (launches) ++*launches;
   }

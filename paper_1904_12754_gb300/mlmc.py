@@ -94,6 +94,7 @@ def load(build_if_missing: bool = False):
     lib.mlmc_batch_destroy.argtypes = [P]
     lib.mlmc_batch_destroy.restype = None
     lib.mlmc_plan_set_proposal.argtypes = [P, P, D]
+    lib.mlmc_plan_set_source.argtypes = [P, P]
     lib.mlmc_export_proposal.argtypes = [P] + [P] * 7
     lib.mlmc_mlp_create.argtypes = [ct.POINTER(P), ct.c_uint64, P]
     lib.mlmc_mlp_destroy.argtypes = [P]
@@ -111,7 +112,8 @@ def load(build_if_missing: bool = False):
                  "mlmc_stats", "mlmc_mlmcl", "mlmc_trace", "mlmc_trace_noalloc",
                  "mlmc_export_tables", "mlmc_batch_create", "mlmc_batch_expmv",
                  "mlmc_batch_stats", "mlmc_batch_info", "mlmc_batch_autotune",
-                 "mlmc_plan_set_proposal", "mlmc_export_proposal", "mlmc_mlp_create",
+                 "mlmc_plan_set_proposal", "mlmc_plan_set_source", "mlmc_export_proposal",
+                 "mlmc_mlp_create",
                  "mlmc_mlp_params", "mlmc_mlp_forward", "mlmc_mlp_loss_grad", "mlmc_mlp_train",
                  "mlmc_learn_proposal",
                  "mlmc_plan_info"):
@@ -295,6 +297,19 @@ class Plan:
                 "keep_neg", "alias_col", "alias_neg"]
         _check(self._lib.mlmc_export_tables(self._h, *[_ptr(out[k]) for k in keys]))
         return out
+
+    def set_source(self, f):
+        """Constant source F of du/dt = A u + F (n float64 values, host or
+        device; None removes it): later estimates return
+        exp(tA) v + int_0^t exp(sA) F ds (Simpson's rule along the walks)."""
+        if isinstance(f, np.ndarray):
+            f = np.ascontiguousarray(f, dtype=np.float64)
+        elif f is not None and hasattr(f, "dtype") and str(f.dtype) != "torch.float64":
+            raise TypeError("f must be float64")
+        if f is not None:
+            _need(f, 8 * self.n, "f")
+        self._source = f
+        _check(self._lib.mlmc_plan_set_source(self._h, _ptr(f)))
 
     def set_proposal(self, h, alpha: float = 0.1):
         """Importance-sampling jump proposal q ~ (1-alpha)|a_ij| h_j + alpha k_ij
