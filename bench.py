@@ -930,6 +930,55 @@ def run_complexity_workload(args):
 
 
 
+def run_source_workload(args):
+    """The inhomogeneous problem du/dt = A u + F, u(0) = v (Sec. 5, Algorithm
+    3): the convection-diffusion operator of the precision workload on a 64^3
+    grid, v the Gaussian bump, F = 1 (a uniform load), t ||A||_inf = 8, FP32
+    walks, tolerance --tol.  The same plan solves it without the source
+    (exp(tA)v) and with it (mlmc_plan_set_source); both against the FP64
+    judge (Taylor, the integral from the sparse augmented matrix)."""
+    import torch
+    import mlmc_inputs as I
+    import __graft_entry__ as g
+    g.build()
+    from paper_1904_12754_gb300 import mlmc as M
+    from oracle import reference as R  # FP64 judge
+    stream = torch.cuda.current_stream()
+    a = I.convdiff_3d(64)
+    t = 8.0 / float(abs(a.scipy()).sum(axis=1).max())
+    g_ = 64
+    h = 8.0 / (g_ + 1)
+    xs = -4.0 + h * np.arange(1, g_ + 1)
+    X, Y, Z = np.meshgrid(xs, xs, xs, indexing="ij")
+    v = np.exp(-(X ** 2 + Y ** 2 + Z ** 2)).ravel()
+    f = np.ones(a.n)
+    ref_h = R.expmv_taylor(a.scipy(), t, v)
+    ref_s = ref_h + R.expmv_source_taylor(a.scipy(), t, f)
+    dv = torch.from_numpy(v).cuda()
+    dx = torch.zeros(a.n, dtype=torch.float64, device="cuda")
+    sched = M.schedule_default(precision=M.FP32_KAHAN, num_levels=3, max_levels=10,
+                               time_budget_s=args.step_budget)
+    res = {}
+    with M.Plan.from_csr(a, t, sched, rel_tol=args.tol, stream=stream.cuda_stream) as plan:
+        for name, src, ref in (("homogeneous", None, ref_h), ("with_source", f, ref_s)):
+            plan.set_source(src)
+            _timed_solve(plan, dv, dx, 20)  # warm-up (loads this kernel variant)
+            sec, est, conv, events = _timed_solve(plan, dv, dx, 21)
+            x = dx.cpu().numpy()
+            lv, _ = plan.stats()
+            res[name] = {"seconds": sec, "est_rel_err": est, "converged": conv,
+                         "walk_steps_per_s": events / sec, "levels": [l["level"] for l in lv],
+                         "rel_err_vs_fp64": float(np.linalg.norm(x - ref) / np.linalg.norm(ref))}
+            log(f"{name}: {sec:.3f} s, est {est:.3g}, err {res[name]['rel_err_vs_fp64']:.3g}")
+        l0 = plan.info()["l0"]
+    out = {"metric": "inhomogeneous solve (Algorithm 3 source term): time to tolerance",
+           "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "convection-diffusion 64^3, v = Gaussian bump, F = 1, t||A||=8",
+                      "n": a.n, "nnz": a.nnz, "t": t, "tol": args.tol, "l0": l0},
+           **res, "value": res["with_source"]["seconds"], "unit": "s", "higher_is_better": False}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -941,12 +990,13 @@ def main():
     ap.add_argument("--step-budget", type=float, default=8.0,
                     help="controller wall-clock budget of one step (s)")
     ap.add_argument("--workload", choices=["tc", "batch", "learned", "precision", "kernel",
-                                           "levels", "complexity"],
+                                           "levels", "complexity", "source"],
                     default="tc",
                     help="tc: the metric's workload (default); batch: batched vs plain; "
                          "learned: learned proposal vs plain; precision: FP32 vs FP64 walk; "
                          "kernel: the walk kernel alone; levels: m_l and V_l vs level; "
-                         "complexity: MLMC vs single-level MC and the l0 sweep")
+                         "complexity: MLMC vs single-level MC and the l0 sweep; "
+                         "source: the inhomogeneous problem (Algorithm 3)")
     ap.add_argument("--max-level", type=int, default=10, help="--workload levels: finest level")
     ap.add_argument("--kernel-reps", type=int, default=4096,
                     help="walks per row of one launch in --workload kernel")
@@ -973,6 +1023,8 @@ def main():
         run_levels_workload(args)
     elif args.workload == "complexity":
         run_complexity_workload(args)
+    elif args.workload == "source":
+        run_source_workload(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -246,6 +246,19 @@ def expmv_source_exact(a, t: float, f: np.ndarray) -> np.ndarray:
     return expm_pade13(m)[:n, n]
 
 
+def expmv_source_taylor(a, t: float, f: np.ndarray) -> np.ndarray:
+    """int_0^t exp(sA) f ds for large sparse A: exp(t B) applied to e_{n+1}
+    with the sparse augmented B = [[A, f], [0, 0]] (truncated Taylor with
+    substeps), top n entries."""
+    a = sp.csr_matrix(a, dtype=np.float64)
+    n = a.shape[0]
+    col = sp.csr_matrix(np.asarray(f, dtype=np.float64).reshape(n, 1))
+    b = sp.bmat([[a, col], [None, sp.csr_matrix((1, 1))]], format="csr")
+    e = np.zeros(n + 1)
+    e[n] = 1.0
+    return expmv_taylor(b, t, e)[:n]
+
+
 def level_means(a, t: float, v: np.ndarray, l0: int, top: int):
     """Exact per-level corrections m_l of Eq. 9 for l = l0..top:
     m_l0 = x-bar^(l0), m_l = x-bar^(l) - x-bar^(l-1)."""

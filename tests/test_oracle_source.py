@@ -121,3 +121,9 @@ def test_mlmcl_sums_both_parts():
     rec = wk.walks(rows, np.tile(np.arange(50), a.n), 2, True)
     want = (rec["y"] + rec["src"]).reshape(a.n, 50).sum(axis=1)
     assert np.allclose(sy, want, rtol=1e-12, atol=1e-14)
+
+
+def test_sparse_augmented_taylor_matches_dense_integral():
+    a, t, _, f = _signed()
+    assert np.allclose(R.expmv_source_taylor(a.scipy(), t, f),
+                       R.expmv_source_exact(a.scipy(), t, f), rtol=1e-12, atol=1e-14)
