@@ -713,20 +713,28 @@ def run_kernel_workload(args):
     import __graft_entry__ as g
     g.build()
     from paper_1904_12754_gb300 import mlmc as M
+    import mlmc_inputs as I
     if args.kernel_matrix == "lap3d":
         # long walks: unscaled 7-point Laplacian, t L_ii = 6 (about 7 events
         # per walk), the instance family of the batched workload
-        import mlmc_inputs as I
         a = I.laplacian_3d(64)
         w = I.Workload(name="lap3d_g64_t1_fp32", a=a, t=1.0, v=I.uniform_v(a.n, 20190429),
                        precision="fp32", num_levels=3, tol=1e-3, extra={})
+    elif args.kernel_matrix == "c4":
+        w = I.workload_c4()          # tables ~233 MB: larger than L2
+        w.precision = "fp32"
+    elif args.kernel_matrix == "c5":
+        w = I.workload_c5()          # tables ~272 MB: larger than L2
+        w.precision = "fp32"
     else:
         w = _workload()
     stream = torch.cuda.current_stream()
     sched = M.schedule_default(precision=M.FP32_KAHAN if w.precision == "fp32" else M.FP64,
-                               walks_per_lane=args.walks_per_lane, block_threads=args.block)
+                               walks_per_lane=args.walks_per_lane, block_threads=args.block,
+                               l2_persist=args.l2_persist)
     plan = M.Plan.from_csr(w.a, w.t, sched, rel_tol=w.tol, stream=stream.cuda_stream)
     l0 = plan.info()["l0"]
+    l2win = plan.l2_window()
     n = w.a.n
     dv = torch.from_numpy(w.v).cuda()
     sums = torch.zeros(n, dtype=torch.float64, device="cuda")
@@ -774,7 +782,7 @@ def run_kernel_workload(args):
            "config": {"workload": w.name, "n": n, "nnz": w.a.nnz, "t": w.t, "l0": l0,
                       "walks_per_row": reps, "l2": "flushed before each launch",
                       "walks_per_lane": args.walks_per_lane or "default",
-                      "block": args.block or "default"},
+                      "block": args.block or "default", "l2_window": l2win},
            "levels": res, "roofline": roof, "clocks": clocks}
     print(json.dumps(out), flush=True)
     plan.close()
@@ -1000,9 +1008,12 @@ def main():
     ap.add_argument("--max-level", type=int, default=10, help="--workload levels: finest level")
     ap.add_argument("--kernel-reps", type=int, default=4096,
                     help="walks per row of one launch in --workload kernel")
-    ap.add_argument("--kernel-matrix", choices=["ba", "lap3d"], default="ba",
+    ap.add_argument("--kernel-matrix", choices=["ba", "lap3d", "c4", "c5"], default="ba",
                     help="--workload kernel: ba = the metric's graph (short walks), "
-                         "lap3d = 64^3 Laplacian at t = 1 (long walks)")
+                         "lap3d = 64^3 Laplacian at t = 1 (long walks), c4 = convection-diffusion "
+                         "128^3, c5 = BA n = 1e6 m = 8 (tables larger than L2)")
+    ap.add_argument("--l2-persist", type=int, default=1, choices=[0, 1],
+                    help="--workload kernel: L2 access-policy window over the tables")
     ap.add_argument("--walks-per-lane", type=int, default=0,
                     help="--workload kernel: walks per lane of one work item (0 = library default)")
     ap.add_argument("--block", type=int, default=0,

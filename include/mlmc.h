@@ -73,7 +73,15 @@ enum { MLMC_PLAIN = 0, MLMC_LEARNED = 1 };     /* jump proposal */
  *   max_walks_per_row sample budget per level (per row)
  *   time_budget_s     wall-clock budget of one mlmc_expmv call
  *   walks_per_lane    work granularity of the walk kernel (0 = automatic)
- *   block_threads     threads per block of the walk kernel (0 = automatic) */
+ *   block_threads     threads per block of the walk kernel (0 = automatic)
+ *   l2_persist        1 (default): the walk kernels read the row records and
+ *                     alias entries through an L2 access-policy window
+ *                     (persisting hits, streaming misses), and plan creation
+ *                     raises this process's persisting-L2 set-aside to cover
+ *                     the tables up to the device maximum (never lowering it;
+ *                     the set-aside belongs to the process's CUDA context and
+ *                     ends with it); the hit ratio is set-aside / window.
+ *                     0: plain caching. */
 typedef struct {
     int32_t l0;
     int32_t num_levels;
@@ -87,6 +95,8 @@ typedef struct {
     double time_budget_s;
     int32_t walks_per_lane;
     int32_t block_threads;
+    int32_t l2_persist;
+    int32_t reserved;
 } mlmc_schedule;
 
 /* Per-level statistics of the last mlmc_expmv call.
@@ -380,6 +390,11 @@ mlmc_status mlmc_export_tables(const mlmc_plan *plan, double *l_ii, double *dl, 
                                uint8_t *alias_neg);
 
 /* Plan facts: n, nnz, the chosen l0, and t. Any pointer may be NULL. */
+/* The L2 access-policy window of the plan's walk kernels (l2_persist):
+ * bytes of the window (0 when off or unsupported) and the fraction of it
+ * kept persisting.  Either pointer may be NULL. */
+mlmc_status mlmc_plan_l2_window(const mlmc_plan *plan, int64_t *bytes, double *hit_ratio);
+
 mlmc_status mlmc_plan_info(const mlmc_plan *plan, int64_t *n, int64_t *nnz, int32_t *l0,
                            double *t);
 

@@ -66,10 +66,8 @@ void free_plan(mlmc_plan* p) {
   cudaFree(p->d_row_ptr);
   cudaFree(p->d_col);
   cudaFree(p->d_val);
-  cudaFree(p->d_meta32);
-  cudaFree(p->d_meta64);
+  cudaFree(p->d_tables);
   cudaFree(p->d_lii);
-  cudaFree(p->d_alias);
   cudaFree(p->d_alias_is);
   cudaFree(p->d_h);
   cudaFree(p->d_src);
@@ -255,6 +253,21 @@ static double level_cost(const mlmc_plan* p, const HostLevel& h) {
 
 using namespace mlmc;
 
+namespace mlmc {
+int l2_window_attr(const mlmc_plan* p, const void* base, size_t bytes, cudaLaunchAttribute* attr) {
+  if (p->l2_persist_bytes == 0 || p->l2_max_window == 0 || !base || bytes == 0) return 0;
+  const size_t win = std::min(bytes, p->l2_max_window);
+  attr->id = cudaLaunchAttributeAccessPolicyWindow;
+  attr->val.accessPolicyWindow.base_ptr = const_cast<void*>(base);
+  attr->val.accessPolicyWindow.num_bytes = win;
+  attr->val.accessPolicyWindow.hitRatio =
+      static_cast<float>(std::min(1.0, static_cast<double>(p->l2_persist_bytes) / static_cast<double>(win)));
+  attr->val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+  attr->val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+  return 1;
+}
+}  // namespace mlmc
+
 extern "C" {
 
 mlmc_status mlmc_schedule_default(mlmc_schedule* s) {
@@ -272,6 +285,7 @@ mlmc_status mlmc_schedule_default(mlmc_schedule* s) {
   s->time_budget_s = 600.0;
   s->walks_per_lane = 0;
   s->block_threads = 0;
+  s->l2_persist = 1;
   return MLMC_OK;
 }
 
@@ -307,6 +321,8 @@ mlmc_status mlmc_plan_create(mlmc_plan** out, int64_t n, int64_t nnz, const int6
     return fail(MLMC_ERR_INVALID_ARG, "bad schedule budgets");
   if (s.l0 > 24 || (s.l0 >= 0 && s.l0 + s.max_levels - 1 > 24))
     return fail(MLMC_ERR_INVALID_ARG, "levels above 24 are not supported");
+  if (s.l2_persist != 0 && s.l2_persist != 1)
+    return fail(MLMC_ERR_INVALID_ARG, "l2_persist must be 0 or 1");
   if (s.walks_per_lane < 0 || s.block_threads < 0 || s.block_threads % 32 != 0 ||
       s.block_threads > 256)
     return fail(MLMC_ERR_INVALID_ARG, "block_threads must be a multiple of 32 up to 256");
@@ -333,10 +349,41 @@ mlmc_status mlmc_plan_create(mlmc_plan** out, int64_t n, int64_t nnz, const int6
   PLAN_CUDA(dev_alloc(&p->d_row_ptr, n + 1), "alloc row_ptr");
   PLAN_CUDA(dev_alloc(&p->d_col, nnz), "alloc col");
   PLAN_CUDA(dev_alloc(&p->d_val, nnz), "alloc val");
-  PLAN_CUDA(dev_alloc(&p->d_meta32, n), "alloc meta32");
-  PLAN_CUDA(dev_alloc(&p->d_meta64, n), "alloc meta64");
+  {
+    // meta32 | alias | meta64, each part 256-byte aligned
+    auto up = [](size_t b) { return (b + 255) & ~size_t{255}; };
+    const size_t b32 = up(sizeof(Meta32) * static_cast<size_t>(n));
+    const size_t ba = up(sizeof(AliasEntry) * static_cast<size_t>(nnz > 0 ? nnz : 1));
+    const size_t b64 = up(sizeof(Meta64) * static_cast<size_t>(n));
+    PLAN_CUDA(dev_alloc(&p->d_tables, b32 + ba + b64), "alloc tables");
+    p->d_meta32 = reinterpret_cast<Meta32*>(p->d_tables);
+    p->d_alias = reinterpret_cast<AliasEntry*>(p->d_tables + b32);
+    p->d_meta64 = reinterpret_cast<Meta64*>(p->d_tables + b32 + ba);
+    p->l2_base32 = p->d_tables;
+    p->l2_bytes32 = b32 + ba;
+    p->l2_base64 = p->d_alias;
+    p->l2_bytes64 = ba + b64;
+    if (s.l2_persist) {
+      int max_persist = 0, max_window = 0;
+      if (cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, p->device) != cudaSuccess ||
+          cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, p->device) != cudaSuccess) {
+        max_persist = 0;
+        max_window = 0;
+        cudaGetLastError();
+      }
+      const size_t want = s.precision == MLMC_FP64 ? p->l2_bytes64 : p->l2_bytes32;
+      const size_t aside = std::min<size_t>(want, static_cast<size_t>(max_persist));
+      size_t cur = 0;
+      if (aside > 0 && max_window > 0 && cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize) == cudaSuccess) {
+        if (cur >= aside || cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, aside) == cudaSuccess) {
+          p->l2_persist_bytes = aside;
+          p->l2_max_window = static_cast<size_t>(max_window);
+        }
+      }
+      cudaGetLastError();  // a refused set-aside only turns the window off
+    }
+  }
   PLAN_CUDA(dev_alloc(&p->d_lii, n), "alloc lii");
-  PLAN_CUDA(dev_alloc(&p->d_alias, nnz), "alloc alias");
   PLAN_CUDA(dev_alloc(&p->d_flags, 4), "alloc flags");
   PLAN_CUDA(dev_alloc(&p->d_work, 1), "alloc work");
   PLAN_CUDA(dev_alloc(&p->d_totals, static_cast<size_t>(s.max_levels) * kTotSlots), "alloc totals");
@@ -428,6 +475,18 @@ mlmc_status mlmc_plan_rebuild(mlmc_plan* p) {
   if (!p) return fail(MLMC_ERR_INVALID_ARG, "NULL plan");
   MLMC_CUDA(launch_build_tables(p), "table build");
   if (p->proposal_active) MLMC_CUDA(launch_build_is_tables(p), "proposal table build");
+  return MLMC_OK;
+}
+
+
+mlmc_status mlmc_plan_l2_window(const mlmc_plan* p, int64_t* bytes, double* hit_ratio) {
+  if (!p) return fail(MLMC_ERR_INVALID_ARG, "NULL plan");
+  cudaLaunchAttribute attr;
+  const bool fp64 = p->sched.precision == MLMC_FP64;
+  const int na = l2_window_attr(p, fp64 ? p->l2_base64 : p->l2_base32,
+                                fp64 ? p->l2_bytes64 : p->l2_bytes32, &attr);
+  if (bytes) *bytes = na ? static_cast<int64_t>(attr.val.accessPolicyWindow.num_bytes) : 0;
+  if (hit_ratio) *hit_ratio = na ? attr.val.accessPolicyWindow.hitRatio : 0.0;
   return MLMC_OK;
 }
 
@@ -529,7 +588,15 @@ mlmc_status mlmc_plan_info(const mlmc_plan* p, int64_t* n, int64_t* nnz, int32_t
 
 int64_t mlmc_launch_count(const mlmc_plan* p) { return p ? p->launches : 0; }
 
-void mlmc_plan_destroy(mlmc_plan* p) { free_plan(p); }
+void mlmc_plan_destroy(mlmc_plan* p) {
+  // Lines this plan's windows left persisting go back to normal use.
+  if (p && p->l2_persist_bytes > 0) {
+    cudaStreamSynchronize(p->stream);
+    cudaCtxResetPersistingL2Cache();
+    cudaGetLastError();
+  }
+  free_plan(p);
+}
 
 mlmc_status mlmc_mlmcl(mlmc_plan* p, int32_t level, int32_t coarse, int64_t rep_begin,
                        int64_t reps, const double* v, uint64_t seed, double* sum_y,

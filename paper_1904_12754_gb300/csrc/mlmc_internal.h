@@ -106,7 +106,10 @@ struct mlmc_plan {
   int32_t* d_col = nullptr;
   double* d_val = nullptr;
 
-  // Tables (Eq. 1 split, Eq. 12 alias).
+  // Tables (Eq. 1 split, Eq. 12 alias), carved from one allocation in the
+  // order meta32 | alias | meta64 so that each precision's walk reads one
+  // contiguous range (its L2 access-policy window).
+  unsigned char* d_tables = nullptr;
   mlmc::Meta32* d_meta32 = nullptr;
   mlmc::Meta64* d_meta64 = nullptr;
   double* d_lii = nullptr;
@@ -130,6 +133,16 @@ struct mlmc_plan {
   float* d_src32 = nullptr;  // [n] FP32 copy for the FP32 walk
   bool source_active = false;
 
+  // L2 access-policy windows of the walk kernels (l2_persist): FP32 walks
+  // read meta32 + alias, FP64 walks alias + meta64, proposal walks the
+  // proposal tables.  Zero bytes: no window.
+  size_t l2_persist_bytes = 0;     // persisting set-aside this plan asked for
+  size_t l2_max_window = 0;        // device limit on one window
+  const void* l2_base32 = nullptr;
+  size_t l2_bytes32 = 0;
+  const void* l2_base64 = nullptr;
+  size_t l2_bytes64 = 0;
+
   // Work buffers.
   uint32_t* d_flags = nullptr;                 // [4]
   unsigned long long* d_work = nullptr;        // [1] dynamic work counter
@@ -152,6 +165,10 @@ namespace mlmc {
 
 // Thread-local error message.
 void set_error(const std::string& msg);
+
+// The L2 access-policy window for a walk launch over `base`..+`bytes`
+// (count 0 when off); fills attr and returns the attribute count.
+int l2_window_attr(const mlmc_plan* p, const void* base, size_t bytes, cudaLaunchAttribute* attr);
 
 // Table kernels (mlmc_tables.cu).
 cudaError_t launch_validate(mlmc_plan* p);

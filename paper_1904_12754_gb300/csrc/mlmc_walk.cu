@@ -1217,8 +1217,21 @@ cudaError_t launch_one(mlmc_plan* p, const WalkArgs& args, int block) {
   const unsigned long long need = (warps_needed + warps_per_block - 1) / warps_per_block;
   if (need < grid) grid = need;
   if (grid < 1) grid = 1;
-  kern<<<static_cast<unsigned>(grid), block, 0, p->stream>>>(args);
+  // The tables this walk reads, through the plan's L2 access-policy window.
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(static_cast<unsigned>(grid));
+  cfg.blockDim = dim3(static_cast<unsigned>(block));
+  cfg.stream = p->stream;
+  cfg.attrs = attr;
+  if (IS)
+    cfg.numAttrs = l2_window_attr(p, p->d_alias_is, sizeof(AliasEntryIS) * static_cast<size_t>(p->nnz), attr);
+  else
+    cfg.numAttrs = FP64 ? l2_window_attr(p, p->l2_base64, p->l2_bytes64, attr)
+                        : l2_window_attr(p, p->l2_base32, p->l2_bytes32, attr);
+  err = cudaLaunchKernelEx(&cfg, kern, args);
   p->launches++;
+  if (err != cudaSuccess) return err;
   return cudaGetLastError();
 }
 
@@ -1250,7 +1263,19 @@ cudaError_t launch_fwd_one(mlmc_plan* p, const FwdArgs& args, int block) {
   const unsigned long long need = (args.total_items + block / 32 - 1) / (block / 32);
   if (need < grid) grid = need;
   if (grid < 1) grid = 1;
-  kern<<<static_cast<unsigned>(grid), block, 0, p->stream>>>(args);
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(static_cast<unsigned>(grid));
+  cfg.blockDim = dim3(static_cast<unsigned>(block));
+  cfg.stream = p->stream;
+  cfg.attrs = attr;
+  if (IS)
+    cfg.numAttrs = l2_window_attr(p, p->d_alias_is, sizeof(AliasEntryIS) * static_cast<size_t>(p->nnz), attr);
+  else
+    cfg.numAttrs = FP64 ? l2_window_attr(p, p->l2_base64, p->l2_bytes64, attr)
+                        : l2_window_attr(p, p->l2_base32, p->l2_bytes32, attr);
+  err = cudaLaunchKernelEx(&cfg, kern, args);
+  if (err != cudaSuccess) return err;
   p->launches++;
   return cudaGetLastError();
 }

@@ -36,7 +36,8 @@ class Schedule(ct.Structure):
                 ("precision", ct.c_int32), ("mode", ct.c_int32), ("proposal", ct.c_int32),
                 ("pilot_walks", ct.c_int64), ("max_jumps_per_walk", ct.c_int64),
                 ("max_walks_per_row", ct.c_int64), ("time_budget_s", ct.c_double),
-                ("walks_per_lane", ct.c_int32), ("block_threads", ct.c_int32)]
+                ("walks_per_lane", ct.c_int32), ("block_threads", ct.c_int32),
+                ("l2_persist", ct.c_int32), ("reserved", ct.c_int32)]
 
 
 class LevelStats(ct.Structure):
@@ -95,6 +96,7 @@ def load(build_if_missing: bool = False):
     lib.mlmc_batch_destroy.restype = None
     lib.mlmc_plan_set_proposal.argtypes = [P, P, D]
     lib.mlmc_plan_set_source.argtypes = [P, P]
+    lib.mlmc_plan_l2_window.argtypes = [P, ct.POINTER(I64), ct.POINTER(D)]
     lib.mlmc_export_proposal.argtypes = [P] + [P] * 7
     lib.mlmc_mlp_create.argtypes = [ct.POINTER(P), ct.c_uint64, P]
     lib.mlmc_mlp_destroy.argtypes = [P]
@@ -112,7 +114,8 @@ def load(build_if_missing: bool = False):
                  "mlmc_stats", "mlmc_mlmcl", "mlmc_trace", "mlmc_trace_noalloc",
                  "mlmc_export_tables", "mlmc_batch_create", "mlmc_batch_expmv",
                  "mlmc_batch_stats", "mlmc_batch_info", "mlmc_batch_autotune",
-                 "mlmc_plan_set_proposal", "mlmc_plan_set_source", "mlmc_export_proposal",
+                 "mlmc_plan_set_proposal", "mlmc_plan_set_source", "mlmc_plan_l2_window",
+                 "mlmc_export_proposal",
                  "mlmc_mlp_create",
                  "mlmc_mlp_params", "mlmc_mlp_forward", "mlmc_mlp_loss_grad", "mlmc_mlp_train",
                  "mlmc_learn_proposal",
@@ -338,6 +341,12 @@ class Plan:
         _check(self._lib.mlmc_plan_info(self._h, ct.byref(n), ct.byref(nnz), ct.byref(l0),
                                         ct.byref(t)))
         return dict(n=n.value, nnz=nnz.value, l0=l0.value, t=t.value)
+
+    def l2_window(self) -> dict:
+        """The walk kernels' L2 access-policy window: bytes and hit ratio."""
+        b, r = ct.c_int64(), ct.c_double()
+        _check(self._lib.mlmc_plan_l2_window(self._h, ct.byref(b), ct.byref(r)))
+        return dict(bytes=b.value, hit_ratio=r.value)
 
     def launch_count(self) -> int:
         return int(self._lib.mlmc_launch_count(self._h))
