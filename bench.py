@@ -139,7 +139,7 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU baseline: the oracle walker on the host cores (bounded sample)
 # ---------------------------------------------------------------------------
-def _oracle_sample(w, l0: int, seconds: float = 15.0, seed: int = 1):
+def _oracle_sample(w, l0: int, seconds: float = 15.0, seed: int = 1, nthreads: int = 0):
     """Time the oracle's Algorithm 2 (OpenMP over rows) on a bounded sample
     of the workload: all levels l0..l0+3 on a growing prefix of the rows,
     one walk per row per level, until ~`seconds` of CPU work is done.
@@ -147,7 +147,7 @@ def _oracle_sample(w, l0: int, seconds: float = 15.0, seed: int = 1):
     from oracle import walker as W
     prec = W.FP32 if w.precision == "fp32" else W.FP64
     wk = W.Walker(w.a, w.t, w.v, seed=seed, precision=prec)
-    cores = W.max_threads()
+    cores = nthreads if nthreads > 0 else W.max_threads()
     levels = list(range(l0, l0 + w.num_levels))
     rows = min(w.a.n, 2048)
     events = 0
@@ -157,7 +157,7 @@ def _oracle_sample(w, l0: int, seconds: float = 15.0, seed: int = 1):
         t0 = time.perf_counter()
         ev = 0
         for l in levels:
-            _, _, jumps, _ = wk.mlmcl(l, l > l0, passes, 1, rows=(0, rows))
+            _, _, jumps, _ = wk.mlmcl(l, l > l0, passes, 1, rows=(0, rows), nthreads=nthreads)
             ev += jumps + rows
         dt = time.perf_counter() - t0
         events += ev
@@ -378,6 +378,8 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import reference as R
         cv, cores, sample = _oracle_sample(w, info["l0"], seconds=args.ref_seconds)
+        cv1, _, sample1 = _oracle_sample(w, info["l0"], seconds=5.0, seed=2, nthreads=1)
+        _oracle_sample(w, info["l0"], seconds=0.1, seed=3, nthreads=cores)  # restore the thread count
         t_ref = time.perf_counter()
         ref = R.expmv_taylor(w.a.scipy(), w.t, w.v)
         t_ref = time.perf_counter() - t_ref
@@ -385,7 +387,7 @@ def run_ours(args):
         ref_d = R.expmv_taylor(w.a.scipy(), t_dmax, w.v)
         err_dmax = float(np.linalg.norm(x_dmax - ref_d) / np.linalg.norm(ref_d))
         cpu = {"value": cv, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
-               "fp64_reference_s": t_ref}
+               "fp64_reference_s": t_ref, "single_thread_value": cv1, "single_thread_sample": sample1}
 
     if rank == 0:
         line = {
@@ -459,6 +461,7 @@ def walk_roofline(level_log, walk_s, clocks, peaks, total_ms):
     ops = 0.0
     events = 0
     launches = 0
+    gather = 0.0
     for lv in level_log:
         c = lv["coarse"]
         ev = lv["walks"] + lv["jumps"]
@@ -466,11 +469,16 @@ def walk_roofline(level_log, walk_s, clocks, peaks, total_ms):
         ops += OPS_DRAW * ev + OPS_HOLD * (ev - still) + OPS_STILL_TEST * still \
             + OPS_JUMP[c] * lv["jumps"] + OPS_END_JUMPED[c] * (lv["walks"] - still) \
             + OPS_END_STILL * still
+        # table gathers: alias entry + the new state's row record per jump,
+        # v at the end state per walk that jumped (FP32 layout)
+        gather += 32.0 * lv["jumps"] + 4.0 * (lv["walks"] - still)
         events += ev
         launches += lv.get("launches", 0)
     sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     peak = 152 * 128 * sm_mhz * 1e6 / 1e9
     achieved = ops / walk_s / 1e9 if walk_s > 0 else 0.0
+    hbm = peaks.get("hbm_gbs")
+    gather_gbs = gather / walk_s / 1e9 if walk_s > 0 else 0.0
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s",
             "frac": achieved / peak if peak else None,
             "traffic": TRAFFIC_CAPTURE,
@@ -480,7 +488,11 @@ def walk_roofline(level_log, walk_s, clocks, peaks, total_ms):
             "walk_launches": launches,
             "avg_launch_ms": 1e3 * walk_s / launches if launches else None,
             "walk_events_per_s": events / walk_s if walk_s > 0 else None,
-            "walk_kernel_share_of_step_time": (1e3 * walk_s / total_ms) if total_ms > 0 else None}
+            "walk_kernel_share_of_step_time": (1e3 * walk_s / total_ms) if total_ms > 0 else None,
+            "gather": {"achieved": gather_gbs, "unit": "GB/s", "peak": hbm,
+                       "peak_source": "HBM copy of measured (the tables are L2-resident here)",
+                       "frac": gather_gbs / hbm if hbm else None,
+                       "bytes_per_event": gather / events if events else None}}
 
 
 def log(msg: str):
@@ -987,6 +999,48 @@ def run_source_workload(args):
     print(json.dumps(out), flush=True)
 
 
+def run_forward_workload(args):
+    """Forward mode (Eq. 5: walks on A^T from starts drawn ~ |v|) against
+    backward mode (walks from every row) for the full vector x = exp(tA)v on
+    the convection-diffusion workload (nonsymmetric; v the Gaussian bump,
+    concentrated near the centre), FP32 walks, tolerance --tol, both against
+    the FP64 Taylor judge."""
+    import torch
+    import mlmc_inputs as I
+    import __graft_entry__ as g
+    g.build()
+    from paper_1904_12754_gb300 import mlmc as M
+    from oracle import reference as R  # FP64 judge
+    stream = torch.cuda.current_stream()
+    w = I.workload_c4()
+    ref = R.expmv_taylor(w.a.scipy(), w.t, w.v)
+    nref = np.linalg.norm(ref)
+    dv = torch.from_numpy(w.v).cuda()
+    dx = torch.zeros(w.a.n, dtype=torch.float64, device="cuda")
+    res = {}
+    for name, mode in (("backward", M.BACKWARD), ("forward", M.FORWARD)):
+        sched = M.schedule_default(precision=M.FP32_KAHAN, num_levels=4, max_levels=10, mode=mode,
+                                   time_budget_s=args.step_budget)
+        with M.Plan.from_csr(w.a, w.t, sched, rel_tol=args.tol, stream=stream.cuda_stream) as plan:
+            _timed_solve(plan, dv, dx, 40)  # warm-up
+            sec, est, conv, _ = _timed_solve(plan, dv, dx, 41)
+            lv, _ = plan.stats()
+            walks = sum(l["walks_per_row"] for l in lv) * (1 if mode == M.FORWARD else w.a.n)
+            events = walks + sum(l["jumps"] for l in lv)
+        x = dx.cpu().numpy()
+        res[name] = {"seconds": sec, "est_rel_err": est, "converged": conv, "walks": walks,
+                     "walk_steps_per_s": events / sec,
+                     "rel_err_vs_fp64_taylor": float(np.linalg.norm(x - ref) / nref)}
+        log(f"{name}: {sec:.3f} s, {walks:.3g} walks, est {est:.3g}, "
+            f"err {res[name]['rel_err_vs_fp64_taylor']:.3g}")
+    out = {"metric": "full vector exp(tA)v: forward vs backward mode, time to tolerance",
+           "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": w.name, "n": w.a.n, "nnz": w.a.nnz, "t": w.t, "tol": args.tol},
+           **res, "value": res["backward"]["seconds"] / res["forward"]["seconds"],
+           "unit": "x (backward time / forward time)", "higher_is_better": True}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -998,13 +1052,14 @@ def main():
     ap.add_argument("--step-budget", type=float, default=8.0,
                     help="controller wall-clock budget of one step (s)")
     ap.add_argument("--workload", choices=["tc", "batch", "learned", "precision", "kernel",
-                                           "levels", "complexity", "source"],
+                                           "levels", "complexity", "source", "forward"],
                     default="tc",
                     help="tc: the metric's workload (default); batch: batched vs plain; "
                          "learned: learned proposal vs plain; precision: FP32 vs FP64 walk; "
                          "kernel: the walk kernel alone; levels: m_l and V_l vs level; "
                          "complexity: MLMC vs single-level MC and the l0 sweep; "
-                         "source: the inhomogeneous problem (Algorithm 3)")
+                         "source: the inhomogeneous problem (Algorithm 3); "
+                         "forward: forward vs backward mode")
     ap.add_argument("--max-level", type=int, default=10, help="--workload levels: finest level")
     ap.add_argument("--kernel-reps", type=int, default=4096,
                     help="walks per row of one launch in --workload kernel")
@@ -1036,6 +1091,8 @@ def main():
         run_complexity_workload(args)
     elif args.workload == "source":
         run_source_workload(args)
+    elif args.workload == "forward":
+        run_forward_workload(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -82,6 +82,7 @@ void free_plan(mlmc_plan* p) {
   cudaFree(p->d_sumpair);
   cudaFree(p->d_wstart);
   cudaFree(p->d_cdf);
+  cudaFree(p->d_guide);
   cudaFree(p->d_scan_tmp);
   if (!p->levels.empty()) cudaFree(p->levels[0].sum_y);
   for (auto& L : p->levels) {
@@ -131,6 +132,8 @@ static mlmc_status prepare_starts(mlmc_plan* p, const double* v) {
                             p->stream), "read W");
   MLMC_CUDA(cudaStreamSynchronize(p->stream), "synchronize");
   p->start_total = static_cast<unsigned long long>(W);
+  if (W <= 0) return MLMC_OK;  // v = 0: no walks (launch_walk_forward makes none), x = 0
+  MLMC_CUDA(launch_start_guide(p, p->d_cdf, p->start_total, p->d_guide), "start guide");
   return MLMC_OK;
 }
 
@@ -444,6 +447,7 @@ mlmc_status mlmc_plan_create(mlmc_plan** out, int64_t n, int64_t nnz, const int6
     if (terr != cudaSuccess) return bail(cuda_fail(terr, "transpose"));
     PLAN_CUDA(dev_alloc(&p->d_wstart, n), "alloc start weights");
     PLAN_CUDA(dev_alloc(&p->d_cdf, n), "alloc start cdf");
+    PLAN_CUDA(dev_alloc(&p->d_guide, n), "alloc start guide");
     PLAN_CUDA(dev_alloc(&p->d_scan_tmp, scan_tmp), "alloc scan scratch");
   }
   mlmc_status st = mlmc_plan_rebuild(p);

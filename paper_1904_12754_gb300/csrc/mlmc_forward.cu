@@ -10,8 +10,9 @@
 //              v_s = 0), their inclusive int64 prefix sum C (exact, order
 //              independent) and W = C[n-1].  Walk g draws r = floor(u W / 2^64)
 //              from the 64-bit word u of its Philox block at draw index
-//              0xFFFFFFFF and starts at the smallest s with C[s] > r; its
-//              weight is v_s W / w_s, so E[weight * f(walk from s)] =
+//              0xFFFFFFFF and starts at the smallest s with C[s] > r, found
+//              from a guide table of n cutpoints and a short forward scan;
+//              its weight is v_s W / w_s, so E[weight * f(walk from s)] =
 //              sum_s v_s f(s) exactly for any positive w.
 #include <algorithm>
 #include <cmath>
@@ -119,6 +120,26 @@ __global__ void k_start_weights(int64_t n, const double* __restrict__ v,
   }
 }
 
+// Guide table of the start draw (the cutpoint method of Chen and Asau):
+// bucket b < n holds the answer for r = floor(b W / n).  A draw whose 64-bit
+// word is u has r = floor(u W / 2^64) >= floor(b W / n) for b = floor(u n /
+// 2^64), so its start is found by scanning forward from guide[b]; with n
+// buckets the scan takes one or two steps on average.
+__global__ void k_start_guide(int64_t n, const int64_t* __restrict__ cdf, unsigned long long W,
+                              int32_t* __restrict__ guide) {
+  for (int64_t b = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; b < n;
+       b += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const unsigned long long r = static_cast<unsigned long long>(
+        (static_cast<unsigned __int128>(b) * W) / static_cast<unsigned __int128>(n));
+    int64_t lo = 0, hi = n - 1;  // smallest s with cdf[s] > r
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (static_cast<unsigned long long>(cdf[mid]) > r) hi = mid; else lo = mid + 1;
+    }
+    guide[b] = static_cast<int32_t>(lo);
+  }
+}
+
 int grid_of(const mlmc_plan* p, int64_t items) {
   const int64_t want = (items + kBlock - 1) / kBlock;
   const int64_t cap = static_cast<int64_t>(p->num_sms) * 16;
@@ -158,6 +179,12 @@ cudaError_t launch_transpose(mlmc_plan* p, const int64_t* rp, const int32_t* col
   k_scatter_t<<<grid_of(p, n), kBlock, 0, p->stream>>>(n, rp, col, val, rp_t, fill, col_t, val_t);
   k_sort_rows<<<grid_of(p, n), 64, 0, p->stream>>>(n, rp_t, col_t, val_t);
   p->launches += 3;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_start_guide(mlmc_plan* p, const int64_t* cdf, unsigned long long W, int32_t* guide) {
+  k_start_guide<<<grid_of(p, p->n), kBlock, 0, p->stream>>>(p->n, cdf, W, guide);
+  p->launches++;
   return cudaGetLastError();
 }
 

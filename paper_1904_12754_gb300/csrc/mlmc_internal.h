@@ -122,6 +122,7 @@ struct mlmc_plan {
   // their prefix sums and total, scan scratch.
   int64_t* d_wstart = nullptr;
   int64_t* d_cdf = nullptr;
+  int32_t* d_guide = nullptr;  // [n] guide table of the start draw (cutpoints)
   int64_t* d_scan_tmp = nullptr;
   unsigned long long start_total = 0;
   float* d_h = nullptr;
@@ -185,13 +186,14 @@ cudaError_t launch_transpose(mlmc_plan* p, const int64_t* rp, const int32_t* col
 cudaError_t launch_start_table(mlmc_plan* p, const double* v, int64_t* w, int64_t* cdf,
                                int64_t* tmp, unsigned long long* vmax_bits);
 cudaError_t scan_int64(mlmc_plan* p, int64_t n, const int64_t* in, int64_t* out, int64_t* tmp);
+// guide[b] = the smallest s with cdf[s] > floor(b W / n), b < n (W = cdf[n-1]).
+cudaError_t launch_start_guide(mlmc_plan* p, const int64_t* cdf, unsigned long long W, int32_t* guide);
 // As launch_walk, with the work counter and the FP32 copy of v in the given
 // device memory instead of the plan's buffers.
 cudaError_t launch_walk_scratch(mlmc_plan* p, const WalkLaunch& w, unsigned long long* work,
                                 float* v32, int64_t* launches = nullptr);
 
 // Reductions (mlmc_reduce.cu).
-cudaError_t launch_sumsq(mlmc_plan* p, const double* a, double* out, double scale);
 // out[0] += sum_i a_i, out[1] += sum_i a_i^2 (out must be zeroed by the caller).
 cudaError_t launch_sum_sumsq(mlmc_plan* p, const double* a, double* out);
 cudaError_t launch_finalize(mlmc_plan* p, int num_levels, double* x, double* norm2);

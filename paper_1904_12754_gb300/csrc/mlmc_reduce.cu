@@ -1,5 +1,5 @@
-// FP64 reductions of the controller: sum of squares of a level's per-row
-// sums (for V_l and ||m_l||), and the final cross-level sum
+// FP64 reductions of the controller: sum and sum of squares of a level's
+// per-row sums (for V_l and ||m_l||), and the final cross-level sum
 // x = sum_l S_l / M_l (Eq. 10) with ||x||^2.
 #include "mlmc_internal.h"
 
@@ -27,18 +27,6 @@ __device__ __forceinline__ double block_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
   }
   return v;
-}
-
-__global__ void __launch_bounds__(kRedBlock) k_sumsq(int64_t n, const double* __restrict__ a,
-                                                     double* __restrict__ out, double scale) {
-  double acc = 0.0;
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(kRedBlock) + threadIdx.x; i < n;
-       i += static_cast<int64_t>(gridDim.x) * kRedBlock) {
-    const double x = a[i];
-    acc += x * x;
-  }
-  acc = block_sum(acc);
-  if (threadIdx.x == 0) atomicAdd(out, acc * scale);
 }
 
 __global__ void __launch_bounds__(kRedBlock) k_sum_sumsq(int64_t n, const double* __restrict__ a,
@@ -81,12 +69,6 @@ int red_grid(const mlmc_plan* p) {
 }
 
 }  // namespace
-
-cudaError_t launch_sumsq(mlmc_plan* p, const double* a, double* out, double scale) {
-  k_sumsq<<<red_grid(p), kRedBlock, 0, p->stream>>>(p->n, a, out, scale);
-  p->launches++;
-  return cudaGetLastError();
-}
 
 cudaError_t launch_sum_sumsq(mlmc_plan* p, const double* a, double* out) {
   k_sum_sumsq<<<red_grid(p), kRedBlock, 0, p->stream>>>(p->n, a, out);

@@ -998,6 +998,7 @@ struct FwdArgs {
   const void* alias;
   const double* v;              // right-hand side (start weights use FP64 v)
   const int64_t* cdf;           // inclusive prefix sums of the integer weights
+  const int32_t* guide;         // guide table (cutpoints) over cdf
   const int64_t* w;             // integer weights
   int64_t n;
   unsigned long long W;         // cdf[n-1]
@@ -1059,12 +1060,11 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk_fwd(const __grid_con
                                     a.rk);
       const unsigned long long u = (static_cast<unsigned long long>(x.x) << 32) | x.y;
       const unsigned long long rr = __umul64hi(u, a.W);
-      int64_t lo = 0, hi = a.n - 1;  // smallest index with cdf > rr
-      while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (static_cast<unsigned long long>(__ldg(a.cdf + mid)) > rr) hi = mid; else lo = mid + 1;
-      }
-      start = static_cast<int32_t>(lo);
+      // smallest index with cdf > rr: from the guide table's cutpoint for
+      // bucket floor(u n / 2^64), scanning forward
+      int64_t k = __ldg(a.guide + __umul64hi(u, static_cast<unsigned long long>(a.n)));
+      while (static_cast<unsigned long long>(__ldg(a.cdf + k)) <= rr) ++k;
+      start = static_cast<int32_t>(k);
       j = start;
       m = load_meta(meta, j);
       dl0 = static_cast<T>(m.dl);
@@ -1302,7 +1302,8 @@ cudaError_t dispatch_fwd(mlmc_plan* p, const FwdArgs& a, int block, bool fp64, b
 // start table (cdf, weights, W) must be current for w.v (launch_start_table).
 cudaError_t launch_walk_forward(mlmc_plan* p, const WalkLaunch& w, int64_t* launches) {
   if (launches) *launches = 0;
-  if (w.reps <= 0 || p->n <= 0) return cudaSuccess;
+  // v = 0 (W = 0): every sample is 0 and no walk is made
+  if (w.reps <= 0 || p->n <= 0 || p->start_total == 0) return cudaSuccess;
   const bool fp64 = p->sched.precision == MLMC_FP64;
   FwdArgs a{};
   a.meta = fp64 ? static_cast<const void*>(p->d_meta64) : static_cast<const void*>(p->d_meta32);
@@ -1310,6 +1311,7 @@ cudaError_t launch_walk_forward(mlmc_plan* p, const WalkLaunch& w, int64_t* laun
                                : static_cast<const void*>(p->d_alias);
   a.v = w.v;
   a.cdf = p->d_cdf;
+  a.guide = p->d_guide;
   a.w = p->d_wstart;
   a.n = p->n;
   a.W = p->start_total;

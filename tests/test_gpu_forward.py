@@ -174,3 +174,12 @@ def test_forward_plans_rejected_where_rows_are_needed():
         with pytest.raises(RuntimeError):
             plan.trace_noalloc(2, False, 0, 4, dv, 1, rec)
         torch.cuda.synchronize()
+
+
+def test_forward_zero_rhs_gives_zero():
+    from paper_1904_12754_gb300 import mlmc as M
+    a, t, _ = PROBLEMS["signed_301"]
+    with _fwd_plan(a, t, 1) as plan:
+        x = np.full(a.n, 7.0)
+        plan.expmv(np.zeros(a.n), x, seed=1)
+    assert np.all(x == 0.0)
