@@ -16,6 +16,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmlmc.so")
+# The checked build (-DMLMC_CHECKED: every table index a walk uses is
+# compared with the table sizes; see the walk kernels) in its own folder.
+BUILD_CHECKED = os.path.join(HERE, "_build_checked")
+LIB_CHECKED = os.path.join(BUILD_CHECKED, "libmlmc_checked.so")
 SOURCES = ["mlmc_abi.cu", "mlmc_tables.cu", "mlmc_walk.cu", "mlmc_reduce.cu", "mlmc_noalloc.cu",
            "mlmc_batch.cu", "mlmc_mlp.cu",
            "mlmc_forward.cu"]
@@ -39,15 +43,18 @@ def _stale(obj: str, src: str) -> bool:
     return any(os.path.getmtime(d) > os.path.getmtime(obj) for d in deps)
 
 
-def build(verbose: bool = False, force: bool = False, extra_flags=None) -> str:
-    """Compile (if needed) and return the path of libmlmc.so."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, force: bool = False, extra_flags=None,
+          checked: bool = False) -> str:
+    """Compile (if needed) and return the path of libmlmc.so (or, with
+    checked=True, of the checked build libmlmc_checked.so)."""
+    out_dir, lib_path = (BUILD_CHECKED, LIB_CHECKED) if checked else (BUILD, LIB)
+    os.makedirs(out_dir, exist_ok=True)
     nvcc = _nvcc()
-    flags = FLAGS + list(extra_flags or [])
+    flags = FLAGS + (["-DMLMC_CHECKED"] if checked else []) + list(extra_flags or [])
     jobs = []
     for src in SOURCES:
         path = os.path.join(CSRC, src)
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+        obj = os.path.join(out_dir, src.replace(".cu", ".o"))
         if force or _stale(obj, path):
             jobs.append([nvcc, *ARCH, *flags, "-c", path, "-o", obj])
     def run(cmd):
@@ -61,12 +68,12 @@ def build(verbose: bool = False, force: bool = False, extra_flags=None) -> str:
         return r
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         list(ex.map(run, jobs))
-    objs = [os.path.join(BUILD, s.replace(".cu", ".o")) for s in SOURCES]
-    if jobs or not os.path.exists(LIB):
-        tmp = LIB + f".tmp{os.getpid()}"
-        run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
-        os.replace(tmp, LIB)
-    return LIB
+    objs = [os.path.join(out_dir, s.replace(".cu", ".o")) for s in SOURCES]
+    if jobs or not os.path.exists(lib_path):
+        tmp = lib_path + f".tmp{os.getpid()}"
+        run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-ldl"])
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

@@ -109,6 +109,7 @@ std::string flag_text(uint32_t f) {
   if (f & kFlagNonFinite) s += " non-finite matrix value;";
   if (f & kFlagWalkLimit) s += " a walk exceeded max_jumps_per_walk;";
   if (f & kFlagNonFiniteY) s += " non-finite walk weight;";
+  if (f & kFlagBounds) s += " table index out of range (checked build);";
   return s;
 }
 
@@ -170,6 +171,7 @@ static mlmc_status run_level(mlmc_plan* p, int slot, int64_t extra, uint64_t see
     w.sum_y = L.sum_y;
     w.totals = totals_of(p, slot);
     int64_t nl = 0;
+    NvtxRange range("mlmc level walks");
     MLMC_CUDA(cudaEventRecord(L.ev0, p->stream), "event record");
     MLMC_CUDA(launch_any(p, w, &nl), "walk kernel launch");
     MLMC_CUDA(cudaEventRecord(L.ev1, p->stream), "event record");
@@ -672,6 +674,7 @@ mlmc_status mlmc_trace(mlmc_plan* p, int32_t level, int32_t coarse, int64_t rep_
 static mlmc_status controller(mlmc_plan* p, const double* v, double* x, double* scalar,
                               uint64_t seed, Target target) {
   const auto t_start = std::chrono::steady_clock::now();
+  NvtxRange whole("mlmc controller");
   const mlmc_schedule& s = p->sched;
   MLMC_CUDA(cudaMemcpyAsync(p->d_v, v, sizeof(double) * p->n, cudaMemcpyDefault, p->stream), "copy v");
   MLMC_CUDA(cudaMemsetAsync(p->d_flags, 0, sizeof(uint32_t) * 4, p->stream), "memset flags");
@@ -709,6 +712,7 @@ static mlmc_status controller(mlmc_plan* p, const double* v, double* x, double* 
   bool converged = false;
   mlmc_status result = MLMC_OK;
   for (int iter = 0; iter < 64; ++iter) {
+    NvtxRange range("mlmc controller iteration");
     if ((st = collect(p, nl, h, &norm2)) != MLMC_OK) return st;
     auto size_of_x = [&]() {
       if (target == kFull) return std::sqrt(norm2);
@@ -803,6 +807,7 @@ static mlmc_status controller(mlmc_plan* p, const double* v, double* x, double* 
   }
   if (flags & kFlagWalkLimit) return fail(MLMC_ERR_WALK_LIMIT, "walk limit:" + flag_text(flags));
   if (flags & kFlagNonFiniteY) return fail(MLMC_ERR_NUMERIC, "numeric:" + flag_text(flags));
+  if (flags & kFlagBounds) return fail(MLMC_ERR_NUMERIC, "tables:" + flag_text(flags));
   return result;
 }
 

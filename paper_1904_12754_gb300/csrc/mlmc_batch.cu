@@ -365,6 +365,7 @@ mlmc_status mlmc_batch_create(mlmc_batch** out, mlmc_plan* const* plans, int32_t
     d.sums = b->d_sums + b->offset[k] * L;
     d.totals = b->d_totals + static_cast<int64_t>(k) * L * kTotSlots;
     d.n = p->n;
+    d.nnz = p->nnz;
     d.max_jumps = b->sched.max_jumps_per_walk;
     d.l0 = p->l0;
     d.key0 = d.key1 = 0;
@@ -517,6 +518,7 @@ mlmc_status mlmc_batch_expmv(mlmc_batch* b, const double* const* v, double* cons
     th->hdr.total_items = items;
     th->hdr.segments = nseg;
     th->ntasks = ntask;
+    NvtxRange range("mlmc batch round");
     BATCH_CUDA(cudaEventRecord(b->ev0, b->stream), "event");
     BATCH_CUDA(cudaGraphLaunch(b->exec, b->stream), "graph launch");
     BATCH_CUDA(cudaEventRecord(b->ev1, b->stream), "event");

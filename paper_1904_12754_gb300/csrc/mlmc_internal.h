@@ -5,6 +5,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <cuda_runtime.h>
 
 #include "../../include/mlmc.h"
@@ -20,6 +22,7 @@ enum : uint32_t {
   kFlagNonFinite = 1u << 3,
   kFlagWalkLimit = 1u << 4,
   kFlagNonFiniteY = 1u << 5,
+  kFlagBounds = 1u << 6,      // checked build: a table index out of range
 };
 
 // Device accumulators of one level: sums of Y per row, and totals.
@@ -59,6 +62,7 @@ struct BatchProblemDev {
   double* sums;           // [max_levels][n] per-level row sums of Y
   double* totals;         // [max_levels][kTotSlots]
   int64_t n;
+  int64_t nnz;
   int64_t max_jumps;
   int32_t l0;
   uint32_t key0, key1;
@@ -163,6 +167,15 @@ struct mlmc_plan {
 };
 
 namespace mlmc {
+
+// NVTX range for the timeline of a profiler (header-only NVTX 3; a no-op
+// unless a tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Thread-local error message.
 void set_error(const std::string& msg);

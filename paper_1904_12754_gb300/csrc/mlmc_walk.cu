@@ -42,11 +42,21 @@ namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
+// Checked build (-DMLMC_CHECKED): every alias-entry index and every state a
+// jump picks is compared with the table sizes before it is used; a walk that
+// would leave them ends (status 2, sample 0) and sets kFlagBounds.
+#ifdef MLMC_CHECKED
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
+
 struct WalkArgs {
   const void* meta;
   const void* alias;       // AliasEntry, or AliasEntryIS with a proposal
   const void* v_walk;      // right-hand side in the walk precision
   int64_t n;
+  int64_t nnz;
   int64_t rep_begin;
   int64_t reps;
   int64_t chunk;           // walks per item (multiple of 32)
@@ -224,6 +234,7 @@ struct ItemArgs {
   int64_t trace_base;
   const void* f_walk;     // source vector (source walks only)
   double t;               // the time t (source walks only)
+  int64_t n, nnz;         // table sizes (checked build)
 };
 
 // Per-warp running totals of the walks a warp has finished.
@@ -531,7 +542,7 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
   // Jump at time s_new (after fine grid point g) with bucket word xz and
   // alias coin xw: count the grid points of the segment that ends, pick the
   // next state from the alias table of the current one.
-  auto jump = [&](T s_new, uint32_t xz, uint32_t xw) {
+  auto jump = [&](T s_new, uint32_t xz, uint32_t xw) -> bool {
     const int g = P::floor_int(P::mul(s_new, n_fine));
     if (SRC) source_segment(g);
     const T dlj = static_cast<T>(m.dl);
@@ -544,6 +555,7 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
     }
     kprev = g;
     const uint32_t bucket = __umulhi(xz, static_cast<uint32_t>(m.deg));
+    if (kChecked && (m.start < 0 || static_cast<int64_t>(m.start) + bucket >= a.nnz)) return false;
     uint32_t pick;
     if (IS) {
       const uint4* ep = reinterpret_cast<const uint4*>(
@@ -558,12 +570,14 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
                                   static_cast<const AliasEntry*>(a.alias) + m.start) + bucket);
       pick = (xw < ent.x) ? ent.y : ent.z;
     }
+    if (kChecked && static_cast<int64_t>(pick & kColMask) >= a.n) return false;
     neg ^= pick >> 31;
     j = static_cast<int32_t>(pick & kColMask);
     if (TRACE) hash = (hash ^ static_cast<uint32_t>(j)) * 16777619u;
     m = load_meta(meta, j);
     s = s_new;
     ++e;
+    return true;
   };
   // Sample of a walk that ended at s = 1 after e >= 1 jumps, from its
   // exponents: x1 = E_f (l0) or E_c (above), plus the proposal's log-ratio;
@@ -624,7 +638,7 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
       return;
     }
     if (status != 0) {
-      tot.bad |= kFlagWalkLimit;
+      tot.bad |= (status == 2) ? kFlagBounds : kFlagWalkLimit;
       ++n_limit;
       acc_y.add(static_cast<T>(0));
       tot.y2.add_square(static_cast<T>(0));
@@ -753,9 +767,10 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
           const uint32_t xz = q->xz[slot], xw = q->xw[slot];
           if (static_cast<int64_t>(e) >= a.max_jumps) {
             finish(1, false);
-          } else {
-            jump(s1, xz, xw);
+          } else if (jump(s1, xz, xw)) {
             live = true;
+          } else {
+            finish(2, false);
           }
         }
       }
@@ -772,8 +787,8 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
           finish(0, false);
         } else if (static_cast<int64_t>(e) >= a.max_jumps) {
           finish(1, false);
-        } else {
-          jump(s_new, x.z, x.w);
+        } else if (!jump(s_new, x.z, x.w)) {
+          finish(2, false);
         }
       }
     } else {
@@ -798,8 +813,8 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
           finish(0, true);
         } else if (static_cast<int64_t>(e) >= a.max_jumps) {
           finish(1, true);
-        } else {
-          jump(s_new, x.z, x.w);
+        } else if (!jump(s_new, x.z, x.w)) {
+          finish(2, true);
         }
       }
       settle_ends(false);
@@ -844,6 +859,8 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk(const __grid_constan
   ia.trace_base = a.trace_base;
   ia.f_walk = a.f_walk;
   ia.t = a.t;
+  ia.n = a.n;
+  ia.nnz = a.nnz;
   __shared__ WarpQueue<FP64> queues[kMaxWarps];
   __shared__ WarpCounters counters[kMaxWarps];
   __shared__ EndQueue<FP64> ends[kMaxWarps];
@@ -952,6 +969,8 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4)
         st.ia.trace_base = 0;
         st.ia.f_walk = nullptr;
         st.ia.t = 0.0;
+        st.ia.n = pb.n;
+        st.ia.nnz = pb.nnz;
         st.totals = pb.totals + static_cast<int64_t>(sg.slot) * kTotSlots;
         st.n = pb.n;
         st.reps = sg.reps;
@@ -999,6 +1018,7 @@ struct FwdArgs {
   const double* v;              // right-hand side (start weights use FP64 v)
   const int64_t* cdf;           // inclusive prefix sums of the integer weights
   const int32_t* guide;         // guide table (cutpoints) over cdf
+  int64_t nnz;                  // alias entries (checked build)
   const int64_t* w;             // integer weights
   int64_t n;
   unsigned long long W;         // cdf[n-1]
@@ -1094,6 +1114,24 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk_fwd(const __grid_con
           done = true;
           status = 1;
         }
+        if (kChecked && !done) {
+          // the alias entry and the state it picks must lie inside the tables
+          const uint32_t bk = __umulhi(x.z, static_cast<uint32_t>(m.deg));
+          if (m.start < 0 || static_cast<int64_t>(m.start) + bk >= a.nnz) {
+            done = true;
+            status = 2;
+          } else {
+            const uint4 ent = IS ? __ldg(reinterpret_cast<const uint4*>(
+                                       static_cast<const AliasEntryIS*>(a.alias) + m.start + bk))
+                                 : __ldg(reinterpret_cast<const uint4*>(
+                                       static_cast<const AliasEntry*>(a.alias) + m.start) + bk);
+            const uint32_t pk = (x.w < ent.x) ? ent.y : ent.z;
+            if (static_cast<int64_t>(pk & kColMask) >= a.n) {
+              done = true;
+              status = 2;
+            }
+          }
+        }
         if (!done) {
           const int gi = P::floor_int(P::mul(s_new, n_fine));
           const T dlj = static_cast<T>(m.dl);
@@ -1150,7 +1188,7 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk_fwd(const __grid_con
               y = 0;
             }
           } else {
-            tot.bad |= kFlagWalkLimit;
+            tot.bad |= (status == 2) ? kFlagBounds : kFlagWalkLimit;
             ++tot.limit;
           }
           if (e == 0) ++tot.still;
@@ -1312,6 +1350,7 @@ cudaError_t launch_walk_forward(mlmc_plan* p, const WalkLaunch& w, int64_t* laun
   a.v = w.v;
   a.cdf = p->d_cdf;
   a.guide = p->d_guide;
+  a.nnz = p->nnz;
   a.w = p->d_wstart;
   a.n = p->n;
   a.W = p->start_total;
@@ -1371,6 +1410,7 @@ cudaError_t launch_walk(mlmc_plan* p, const WalkLaunch& w, int64_t* launches) {
     a.t = p->t;
   }
   a.n = p->n;
+  a.nnz = p->nnz;
   a.level = w.level;
   a.ctr3 = static_cast<uint32_t>(w.level) & 0x3Fu;
   a.key0 = static_cast<uint32_t>(w.seed & 0xFFFFFFFFull);
@@ -1444,6 +1484,7 @@ cudaError_t launch_walk_scratch(mlmc_plan* p, const WalkLaunch& w, unsigned long
     a.t = p->t;
   }
   a.n = p->n;
+  a.nnz = p->nnz;
   a.level = w.level;
   a.ctr3 = static_cast<uint32_t>(w.level) & 0x3Fu;
   a.key0 = static_cast<uint32_t>(w.seed & 0xFFFFFFFFull);

@@ -54,20 +54,27 @@ WALK_RECORD_DTYPE = np.dtype([("end", np.int32), ("jumps", np.int32), ("sign", n
 _lib = None
 
 
+def _checked() -> bool:
+    return os.environ.get("MLMC_CHECKED", "0") == "1"
+
+
 def library_path() -> str:
-    return _build.LIB
+    """The library this process loads: libmlmc.so, or the checked build
+    libmlmc_checked.so when the environment sets MLMC_CHECKED=1."""
+    return _build.LIB_CHECKED if _checked() else _build.LIB
 
 
 def load(build_if_missing: bool = False):
-    """Load libmlmc.so (building it first if asked).  Raises if absent."""
+    """Load libmlmc.so (building it first if asked; the checked build is
+    always built on demand).  Raises if absent."""
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB
+    path = library_path()
     if not os.path.exists(path):
-        if not build_if_missing:
+        if not (build_if_missing or _checked()):
             raise ImportError(f"libmlmc.so not built ({path}); run __graft_entry__.build()")
-        _build.build()
+        _build.build(checked=_checked())
     lib = ct.CDLL(path)
     P, I64, I32, D = ct.c_void_p, ct.c_int64, ct.c_int32, ct.c_double
     lib.mlmc_schedule_default.argtypes = [ct.POINTER(Schedule)]
