@@ -185,6 +185,23 @@ mlmc_status mlmc_plan_rebuild(mlmc_plan *plan);
  * once (the call synchronises the plan's stream to validate it). */
 mlmc_status mlmc_plan_set_proposal(mlmc_plan *plan, const float *h, double alpha);
 
+/* Checkpoint and resume of a solve (the paper has no counterpart).  The
+ * state of the last mlmc_expmv / mlmc_expmv_entry / mlmc_expmv_sum call is
+ * small: per level the row sums of Y, the totals (sum Y^2, jumps, walks) and
+ * M_l, plus v and the seed.  mlmc_plan_save_state writes it to host memory
+ * (buf NULL or cap too small: *bytes receives the size needed, and a too
+ * small cap is an error); mlmc_plan_load_state restores it into a plan made
+ * from the same matrix size, t, l0, precision and mode, with the same source
+ * and proposal settings (anything else is INVALID_ARG).  mlmc_expmv_resume
+ * continues a saved or interrupted mlmc_expmv (for example one that returned
+ * MLMC_ERR_NOT_CONVERGED at its time budget) with a fresh budget: no pilot,
+ * and each level's walks continue from index M_l, so with the counter-based
+ * generator no walk is repeated and the samples are those an uninterrupted
+ * solve would draw.  x: host or device, n doubles.  All three synchronise. */
+mlmc_status mlmc_plan_save_state(const mlmc_plan *plan, void *buf, size_t cap, size_t *bytes);
+mlmc_status mlmc_plan_load_state(mlmc_plan *plan, const void *buf, size_t bytes);
+mlmc_status mlmc_expmv_resume(mlmc_plan *plan, double *x);
+
 /* Source term of an inhomogeneous system du/dt = A u + F with constant F
  * (Sec. 5: the solution exp(tA) u0 + int_0^t exp(sA) F ds, the integral by
  * Simpson's rule on each level's time grid, evaluated along the same walks as

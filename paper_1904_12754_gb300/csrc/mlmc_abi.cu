@@ -273,6 +273,32 @@ int l2_window_attr(const mlmc_plan* p, const void* base, size_t bytes, cudaLaunc
 }
 }  // namespace mlmc
 
+// Saved controller state: a header, per level (M_l, seconds, launches), then
+// the level totals, the per-level row sums and v (doubles).
+namespace {
+constexpr uint64_t kStateMagic = 0x54415453434D4C4Dull;  // "MLMCSTAT"
+struct StateHeader {
+  uint64_t magic;
+  uint32_t version;
+  int32_t nl;
+  int64_t n, nnz;
+  double t;
+  int32_t l0, precision, mode, target;
+  int64_t row_begin, row_count;
+  uint64_t seed;
+  int32_t source, proposal;
+};
+struct StateLevel {
+  int64_t reps;
+  double seconds;
+  int64_t launches;
+};
+size_t state_bytes(const mlmc_plan* p, int nl) {
+  return sizeof(StateHeader) + sizeof(StateLevel) * nl +
+         sizeof(double) * (static_cast<size_t>(nl) * kTotSlots + static_cast<size_t>(nl) * p->n + p->n);
+}
+}  // namespace
+
 extern "C" {
 
 mlmc_status mlmc_schedule_default(mlmc_schedule* s) {
@@ -672,24 +698,31 @@ mlmc_status mlmc_trace(mlmc_plan* p, int32_t level, int32_t coarse, int64_t rep_
 // mode, in V_l.
 
 static mlmc_status controller(mlmc_plan* p, const double* v, double* x, double* scalar,
-                              uint64_t seed, Target target) {
+                              uint64_t seed, Target target, bool resume = false) {
   const auto t_start = std::chrono::steady_clock::now();
   NvtxRange whole("mlmc controller");
   const mlmc_schedule& s = p->sched;
-  MLMC_CUDA(cudaMemcpyAsync(p->d_v, v, sizeof(double) * p->n, cudaMemcpyDefault, p->stream), "copy v");
   MLMC_CUDA(cudaMemsetAsync(p->d_flags, 0, sizeof(uint32_t) * 4, p->stream), "memset flags");
-  MLMC_CUDA(cudaMemsetAsync(p->levels[0].sum_y, 0, sizeof(double) * p->n * s.max_levels, p->stream),
-            "memset sums");
-  MLMC_CUDA(cudaMemsetAsync(p->d_totals, 0, sizeof(double) * kTotSlots * s.max_levels, p->stream),
-            "memset totals");
-  for (auto& L : p->levels) {
-    L.reps = 0;
-    L.seconds = 0.0;
-    L.launches = 0;
-    L.pending = false;
+  if (!resume) {
+    MLMC_CUDA(cudaMemcpyAsync(p->d_v, v, sizeof(double) * p->n, cudaMemcpyDefault, p->stream), "copy v");
+    MLMC_CUDA(cudaMemsetAsync(p->levels[0].sum_y, 0, sizeof(double) * p->n * s.max_levels, p->stream),
+              "memset sums");
+    MLMC_CUDA(cudaMemsetAsync(p->d_totals, 0, sizeof(double) * kTotSlots * s.max_levels, p->stream),
+              "memset totals");
+    for (auto& L : p->levels) {
+      L.reps = 0;
+      L.seconds = 0.0;
+      L.launches = 0;
+      L.pending = false;
+    }
   }
   std::vector<char> timed(s.max_levels, 0);
-  int nl = s.num_levels;
+  // A resumed solve continues the saved levels, sums and sample counts
+  // (walk indices continue from M_l, so no walk is repeated).
+  int nl = resume ? p->ctl_nl : s.num_levels;
+  p->ctl_nl = nl;
+  p->ctl_seed = seed;
+  p->ctl_target = target;
   // Forward mode counts walks, not walks per row: the pilot and the budget
   // are scaled by n so that both modes spend the same effort.
   const int64_t unit = forward_mode(p) ? p->n : 1;
@@ -703,7 +736,7 @@ static mlmc_status controller(mlmc_plan* p, const double* v, double* x, double* 
   const auto deadline = t_start + std::chrono::duration_cast<std::chrono::steady_clock::duration>(
                                       std::chrono::duration<double>(s.time_budget_s));
   bool out_of_time = false;
-  for (int k = 0; k < nl && st == MLMC_OK; ++k)
+  for (int k = 0; k < nl && st == MLMC_OK && !resume; ++k)
     st = run_level(p, k, pilot, seed, timed, deadline, nullptr);
   if (st != MLMC_OK) return st;
 
@@ -769,6 +802,7 @@ static mlmc_status controller(mlmc_plan* p, const double* v, double* x, double* 
       if ((st = run_level(p, nl, pilot, seed, timed, deadline, nullptr)) != MLMC_OK)
         return st;
       ++nl;
+      p->ctl_nl = nl;
       continue;
     }
     bool capped = true;
@@ -839,6 +873,112 @@ mlmc_status mlmc_expmv_sum(mlmc_plan* p, const double* v, double* total, uint64_
   p->ctl_row_begin = 0;
   p->ctl_row_count = -1;
   return controller(p, v, nullptr, total, seed, kSum);
+}
+
+
+mlmc_status mlmc_plan_save_state(const mlmc_plan* p, void* buf, size_t cap, size_t* bytes) {
+  if (!p || !bytes) return fail(MLMC_ERR_INVALID_ARG, "NULL argument");
+  if (p->ctl_target < 0) return fail(MLMC_ERR_INVALID_ARG, "mlmc_plan_save_state: no solve to save");
+  const int nl = p->ctl_nl;
+  const size_t need = state_bytes(p, nl);
+  *bytes = need;
+  if (!buf) return MLMC_OK;
+  if (cap < need) return fail(MLMC_ERR_INVALID_ARG, "mlmc_plan_save_state: buffer too small");
+  unsigned char* out = static_cast<unsigned char*>(buf);
+  StateHeader h{};
+  h.magic = kStateMagic;
+  h.version = 1;
+  h.nl = nl;
+  h.n = p->n;
+  h.nnz = p->nnz;
+  h.t = p->t;
+  h.l0 = p->l0;
+  h.precision = p->sched.precision;
+  h.mode = p->sched.mode;
+  h.target = p->ctl_target;
+  h.row_begin = p->ctl_row_begin;
+  h.row_count = p->ctl_row_count;
+  h.seed = p->ctl_seed;
+  h.source = p->source_active ? 1 : 0;
+  h.proposal = p->proposal_active ? 1 : 0;
+  std::memcpy(out, &h, sizeof(h));
+  out += sizeof(h);
+  for (int k = 0; k < nl; ++k) {
+    const StateLevel L{p->levels[k].reps, p->levels[k].seconds, p->levels[k].launches};
+    std::memcpy(out, &L, sizeof(L));
+    out += sizeof(L);
+  }
+  const size_t nt = static_cast<size_t>(nl) * kTotSlots;
+  const size_t ns = static_cast<size_t>(nl) * p->n;
+  MLMC_CUDA(cudaMemcpyAsync(out, p->d_totals, sizeof(double) * nt, cudaMemcpyDeviceToHost, p->stream), "save totals");
+  out += sizeof(double) * nt;
+  if (ns) MLMC_CUDA(cudaMemcpyAsync(out, p->levels[0].sum_y, sizeof(double) * ns, cudaMemcpyDeviceToHost, p->stream), "save sums");
+  out += sizeof(double) * ns;
+  MLMC_CUDA(cudaMemcpyAsync(out, p->d_v, sizeof(double) * p->n, cudaMemcpyDeviceToHost, p->stream), "save v");
+  MLMC_CUDA(cudaStreamSynchronize(p->stream), "synchronize");
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_plan_load_state(mlmc_plan* p, const void* buf, size_t bytes) {
+  if (!p || !buf) return fail(MLMC_ERR_INVALID_ARG, "NULL argument");
+  if (bytes < sizeof(StateHeader)) return fail(MLMC_ERR_INVALID_ARG, "mlmc_plan_load_state: truncated state");
+  StateHeader h;
+  std::memcpy(&h, buf, sizeof(h));
+  if (h.magic != kStateMagic || h.version != 1)
+    return fail(MLMC_ERR_INVALID_ARG, "mlmc_plan_load_state: not a saved state");
+  if (h.n != p->n || h.nnz != p->nnz || h.t != p->t || h.l0 != p->l0 ||
+      h.precision != p->sched.precision || h.mode != p->sched.mode ||
+      h.source != (p->source_active ? 1 : 0) || h.proposal != (p->proposal_active ? 1 : 0))
+    return fail(MLMC_ERR_INVALID_ARG,
+                "mlmc_plan_load_state: the plan differs from the saved one (matrix size, t, l0, "
+                "precision, mode, source or proposal)");
+  if (h.nl < 1 || h.nl > p->sched.max_levels || h.target < 0 || h.target > 2)
+    return fail(MLMC_ERR_INVALID_ARG, "mlmc_plan_load_state: levels or target out of range");
+  if (bytes != state_bytes(p, h.nl)) return fail(MLMC_ERR_INVALID_ARG, "mlmc_plan_load_state: size mismatch");
+  const unsigned char* in = static_cast<const unsigned char*>(buf) + sizeof(h);
+  MLMC_CUDA(cudaMemsetAsync(p->levels[0].sum_y, 0, sizeof(double) * p->n * p->sched.max_levels, p->stream),
+            "memset sums");
+  MLMC_CUDA(cudaMemsetAsync(p->d_totals, 0, sizeof(double) * kTotSlots * p->sched.max_levels, p->stream),
+            "memset totals");
+  for (auto& L : p->levels) {
+    L.reps = 0;
+    L.seconds = 0.0;
+    L.launches = 0;
+    L.pending = false;
+  }
+  for (int k = 0; k < h.nl; ++k) {
+    StateLevel L;
+    std::memcpy(&L, in, sizeof(L));
+    in += sizeof(L);
+    if (L.reps < 0) return fail(MLMC_ERR_INVALID_ARG, "mlmc_plan_load_state: negative sample count");
+    p->levels[k].reps = L.reps;
+    p->levels[k].seconds = L.seconds;
+    p->levels[k].launches = L.launches;
+  }
+  const size_t nt = static_cast<size_t>(h.nl) * kTotSlots;
+  const size_t ns = static_cast<size_t>(h.nl) * p->n;
+  MLMC_CUDA(cudaMemcpyAsync(p->d_totals, in, sizeof(double) * nt, cudaMemcpyHostToDevice, p->stream), "load totals");
+  in += sizeof(double) * nt;
+  if (ns) MLMC_CUDA(cudaMemcpyAsync(p->levels[0].sum_y, in, sizeof(double) * ns, cudaMemcpyHostToDevice, p->stream), "load sums");
+  in += sizeof(double) * ns;
+  MLMC_CUDA(cudaMemcpyAsync(p->d_v, in, sizeof(double) * p->n, cudaMemcpyHostToDevice, p->stream), "load v");
+  MLMC_CUDA(cudaStreamSynchronize(p->stream), "synchronize");
+  p->ctl_nl = h.nl;
+  p->ctl_seed = h.seed;
+  p->ctl_target = h.target;
+  p->ctl_row_begin = h.row_begin;
+  p->ctl_row_count = h.row_count;
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_expmv_resume(mlmc_plan* p, double* x) {
+  g_last_error.clear();
+  if (!p || !x) return fail(MLMC_ERR_INVALID_ARG, "NULL argument");
+  if (p->ctl_target != kFull)
+    return fail(MLMC_ERR_INVALID_ARG, "mlmc_expmv_resume: the last solve (or loaded state) is not an mlmc_expmv");
+  p->ctl_row_begin = 0;
+  p->ctl_row_count = -1;
+  return controller(p, nullptr, x, nullptr, p->ctl_seed, kFull, true);
 }
 
 mlmc_status mlmc_stats(const mlmc_plan* p, mlmc_level_stats* out, int32_t cap, int32_t* n_levels,

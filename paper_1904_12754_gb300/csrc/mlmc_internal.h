@@ -162,6 +162,11 @@ struct mlmc_plan {
   // Rows walked by the controller (ENTRY mode: one row); -1 = every row.
   int64_t ctl_row_begin = 0;
   int64_t ctl_row_count = -1;
+  // The last controller call (mlmc_plan_save_state, mlmc_expmv_resume):
+  // levels in use, seed and target (-1: no solve yet).
+  int32_t ctl_nl = 0;
+  uint64_t ctl_seed = 0;
+  int32_t ctl_target = -1;
   double last_est_rel_err = 0.0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };

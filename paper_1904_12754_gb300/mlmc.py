@@ -104,6 +104,9 @@ def load(build_if_missing: bool = False):
     lib.mlmc_plan_set_proposal.argtypes = [P, P, D]
     lib.mlmc_plan_set_source.argtypes = [P, P]
     lib.mlmc_plan_l2_window.argtypes = [P, ct.POINTER(I64), ct.POINTER(D)]
+    lib.mlmc_plan_save_state.argtypes = [P, P, ct.c_size_t, ct.POINTER(ct.c_size_t)]
+    lib.mlmc_plan_load_state.argtypes = [P, P, ct.c_size_t]
+    lib.mlmc_expmv_resume.argtypes = [P, P]
     lib.mlmc_export_proposal.argtypes = [P] + [P] * 7
     lib.mlmc_mlp_create.argtypes = [ct.POINTER(P), ct.c_uint64, P]
     lib.mlmc_mlp_destroy.argtypes = [P]
@@ -122,6 +125,7 @@ def load(build_if_missing: bool = False):
                  "mlmc_export_tables", "mlmc_batch_create", "mlmc_batch_expmv",
                  "mlmc_batch_stats", "mlmc_batch_info", "mlmc_batch_autotune",
                  "mlmc_plan_set_proposal", "mlmc_plan_set_source", "mlmc_plan_l2_window",
+                 "mlmc_plan_save_state", "mlmc_plan_load_state", "mlmc_expmv_resume",
                  "mlmc_export_proposal",
                  "mlmc_mlp_create",
                  "mlmc_mlp_params", "mlmc_mlp_forward", "mlmc_mlp_loss_grad", "mlmc_mlp_train",
@@ -348,6 +352,26 @@ class Plan:
         _check(self._lib.mlmc_plan_info(self._h, ct.byref(n), ct.byref(nnz), ct.byref(l0),
                                         ct.byref(t)))
         return dict(n=n.value, nnz=nnz.value, l0=l0.value, t=t.value)
+
+    def save_state(self) -> bytes:
+        """The state of the last solve (row sums, totals and M_l per level,
+        v, seed) as bytes, for mlmc_plan_load_state on a plan of the same
+        matrix, t and schedule."""
+        need = ct.c_size_t()
+        _check(self._lib.mlmc_plan_save_state(self._h, None, 0, ct.byref(need)))
+        buf = ct.create_string_buffer(need.value)
+        _check(self._lib.mlmc_plan_save_state(self._h, buf, need.value, ct.byref(need)))
+        return buf.raw[:need.value]
+
+    def load_state(self, state: bytes):
+        buf = ct.create_string_buffer(state, len(state))
+        _check(self._lib.mlmc_plan_load_state(self._h, buf, len(state)))
+
+    def expmv_resume(self, x, allow_not_converged: bool = False) -> int:
+        """Continue the last (or loaded) mlmc_expmv with a fresh budget."""
+        _need(x, 8 * self.n, "x")
+        allow = (MLMC_ERR_NOT_CONVERGED,) if allow_not_converged else ()
+        return _check(self._lib.mlmc_expmv_resume(self._h, _ptr(x)), allow)
 
     def l2_window(self) -> dict:
         """The walk kernels' L2 access-policy window: bytes and hit ratio."""
