@@ -500,7 +500,7 @@ static int orc_before(const orc_ctx *c, double t_next, int64_t n_step, int64_t N
  *           Lemma 2), so y = sign u_end e^{log_c} expm1(diff) avoids the
  *           cancellation in eta_2 - eta_1. */
 static int orc_walk_core(const orc_ctx *c, int64_t row, orc_ctr kc, int level, int coarse,
-                         int use_v_end, orc_walk_rec *out)
+                         int use_v_end, int backward, int64_t rep, orc_walk_rec *out)
 {
     const int64_t N = (int64_t)1 << level;
     int64_t j = row;
@@ -524,6 +524,25 @@ static int orc_walk_core(const orc_ctx *c, int64_t row, orc_ctr kc, int level, i
     double integ1 = integ2;
 
     orc_draw_k(c, kc, ndraw++, x);
+    /* Stream layout of the FP32 backward walk in a row with 1/(t L) >= 1
+     * (rows where most walks never jump): the first holding time takes its
+     * uniform from word (rep mod 4) of the shared block of the four walks
+     * 4g..4g+3, g = floor(rep/4), counter (g bits 0-31, row, 0xFFFFFFFE,
+     * level | variant << 6 | g bits 32-55 << 8); the first jump keeps words
+     * 2 and 3 of the walk's own draw 0.  The law is unchanged: the four words
+     * of one block are independent uniforms. */
+    if (backward && c->precision == ORC_FP32 && c->variant == ORC_RESIDUAL &&
+        c->inv_rate32[row] >= 1.0f) {
+        const uint64_t g = (uint64_t)rep >> 2;
+        orc_ctr kg;
+        kg.w0 = (uint32_t)(g & 0xFFFFFFFFull);
+        kg.w1 = (uint32_t)row;
+        kg.w3 = (uint32_t)level | ((uint32_t)c->variant << 6) |
+                ((uint32_t)((g >> 32) & 0xFFFFFFull) << 8);
+        uint32_t xg[4];
+        orc_draw_k(c, kg, 0xFFFFFFFEu, xg);
+        x[0] = xg[(uint64_t)rep & 3u];
+    }
     double t_next = orc_hold(c, j, x, 0.0);
 
     for (int64_t step = 1; step <= N; ++step) {
@@ -619,7 +638,8 @@ done:
 int orc_walk(const orc_ctx *c, int64_t row, int64_t rep, int level, int coarse,
              orc_walk_rec *out)
 {
-    return orc_walk_core(c, row, orc_ctr_backward(c, row, rep, level), level, coarse, 1, out);
+    return orc_walk_core(c, row, orc_ctr_backward(c, row, rep, level), level, coarse, 1, 1, rep,
+                         out);
 }
 
 /* Forward mode (Eq. 5; reading R6): the tables in c are those of B = A^T.
@@ -640,7 +660,7 @@ int orc_walk_fwd(const orc_ctx *c, const int64_t *cdf, const int64_t *w, uint64_
         int64_t mid = (lo + hi) / 2;
         if ((uint64_t)cdf[mid] > r) hi = mid; else lo = mid + 1;
     }
-    int status = orc_walk_core(c, lo, kc, level, coarse, 0, out);
+    int status = orc_walk_core(c, lo, kc, level, coarse, 0, 0, 0, out);
     double f = c->v[lo] * ((double)W / (double)w[lo]);
     out->y = out->y * f;
     out->y_alg2 = out->y_alg2 * f;

@@ -359,7 +359,7 @@ mlmc_status mlmc_batch_create(mlmc_batch** out, mlmc_plan* const* plans, int32_t
     mlmc_plan* p = plans[k];
     BatchProblemDev& d = probs[k];
     d.meta = b->fp64 ? static_cast<const void*>(p->d_meta64) : static_cast<const void*>(p->d_meta32);
-    d.alias = p->d_alias;
+    d.alias = p->d_fused;
     d.v_walk = b->fp64 ? static_cast<const void*>(b->d_v + b->offset[k])
                        : static_cast<const void*>(b->d_v32 + b->offset[k]);
     d.sums = b->d_sums + b->offset[k] * L;

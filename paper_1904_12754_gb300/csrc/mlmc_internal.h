@@ -57,7 +57,7 @@ struct WalkLaunch {
 // One problem = one plan's tables with one right-hand side.
 struct BatchProblemDev {
   const void* meta;       // Meta32 or Meta64 records of the problem's plan
-  const AliasEntry* alias;
+  const void* alias;      // FusedEntry32 or FusedEntry64 entries of the plan
   const void* v_walk;     // right-hand side in the walk precision
   double* sums;           // [max_levels][n] per-level row sums of Y
   double* totals;         // [max_levels][kTotSlots]
@@ -116,6 +116,9 @@ struct mlmc_plan {
   unsigned char* d_tables = nullptr;
   mlmc::Meta32* d_meta32 = nullptr;
   mlmc::Meta64* d_meta64 = nullptr;
+  // Fused entries of the plan's precision (FusedEntry32 or FusedEntry64),
+  // at the same positions as the alias entries.
+  void* d_fused = nullptr;
   double* d_lii = nullptr;
   mlmc::AliasEntry* d_alias = nullptr;
   double dmax_scaled = 0.0;  // max_i max(|t d_i|, t L_ii)

@@ -266,6 +266,29 @@ cudaError_t launch_validate(mlmc_plan* p) {
   return cudaGetLastError();
 }
 
+// Fused entries (the walk's table): each row's alias entries followed by the
+// row records of their kept and alias columns.
+template <typename Fused, typename Meta>
+__global__ void k_fuse(int64_t n, const Meta* __restrict__ meta, const AliasEntry* __restrict__ alias,
+                       Fused* __restrict__ fused) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t start = meta[i].start;
+    const int32_t deg = meta[i].deg;
+    for (int32_t b = 0; b < deg; ++b) {
+      const AliasEntry e = alias[start + b];
+      Fused f;
+      f.thr = e.thr;
+      f.keep = e.keep;
+      f.alias = e.alias;
+      f.pad = 0;
+      f.mk = meta[e.keep & kColMask];
+      f.ma = meta[e.alias & kColMask];
+      fused[start + b] = f;
+    }
+  }
+}
+
 cudaError_t launch_build_tables(mlmc_plan* p) {
   cudaError_t err = cudaMemsetAsync(p->d_norm2, 0, sizeof(double), p->stream);
   if (err != cudaSuccess) return err;
@@ -274,6 +297,13 @@ cudaError_t launch_build_tables(mlmc_plan* p) {
   k_build_tables<<<grid_for(p, p->n, kBuildBlock), kBuildBlock, 0, p->stream>>>(
       p->n, p->t, p->d_row_ptr, p->d_col, p->d_val, p->d_meta32, p->d_meta64, p->d_lii,
       p->d_alias, reinterpret_cast<unsigned long long*>(p->d_norm2));
+  p->launches++;
+  if (p->sched.precision == MLMC_FP64)
+    k_fuse<<<grid_for(p, p->n, kBuildBlock), kBuildBlock, 0, p->stream>>>(
+        p->n, p->d_meta64, p->d_alias, static_cast<FusedEntry64*>(p->d_fused));
+  else
+    k_fuse<<<grid_for(p, p->n, kBuildBlock), kBuildBlock, 0, p->stream>>>(
+        p->n, p->d_meta32, p->d_alias, static_cast<FusedEntry32*>(p->d_fused));
   p->launches++;
   return cudaGetLastError();
 }

@@ -21,11 +21,12 @@
 // the time, words 2-3 the bucket and the alias coin of the jump that ends it.
 //
 // Work decomposition: a warp takes one (row, chunk of walks) item at a time
-// from a global counter.  Its lanes first screen the chunk's walks 32 at a
-// time (first holding time only): walks that never jump are counted, the
-// others go to a per-warp queue in shared memory, from which a lane whose
-// walk ends takes the next one at once, so lanes stay busy although walk
-// lengths are geometric.  Per-row sums are reduced across the warp and added
+// from a global counter.  Its lanes first screen the chunk's walks (first
+// holding time only; FP32: 128 walks per round from 32 Philox blocks, four
+// walks per block): walks that never jump are counted, the others go to a
+// per-warp queue in shared memory, from which a lane whose walk ends takes
+// the next one at once, so lanes stay busy although walk lengths are
+// geometric.  Per-row sums are reduced across the warp and added
 // with one FP64 atomic per item; totals are flushed once per warp.
 // The FP32 variant keeps times, exponents and weights in FP32 and sums Y per
 // row with Kahan compensation and sum Y^2 (which sets the sample sizes through
@@ -309,20 +310,31 @@ __device__ __forceinline__ void flush_warp(LaneTotals<T>& t, WarpCounters* wc, d
   t = LaneTotals<T>();
 }
 
-// Per-warp queue of screened walks that jump at least once: replica offset,
-// the bucket and coin words of the first jump and either the first holding
-// time (FP64) or the Philox word it is drawn from (FP32).  A ring of
-// kQueueCap slots; a screening round adds at most 64 entries (two walks per
-// lane) and runs only while fewer than 32 are queued, so it never holds more
-// than 95.
-constexpr uint32_t kQueueCap = 128;
+// Per-warp queue of screened walks that jump at least once, a ring of
+// WarpQueue<FP64>::kCap slots.  FP32: replica offset and the Philox word of the first
+// holding time (the first jump's words come from the walk's own draw 0 when
+// it is taken); a screening round adds at most 128 entries (32 blocks of 4
+// walks) and runs only while fewer than 32 are queued, so it never holds more
+// than 159.  FP64: replica offset, the first holding time and the first
+// jump's bucket and coin words; at most 64 per round, never more than 95.
 template <bool FP64>
-struct WarpQueue {
-  uint32_t r[kQueueCap];
-  uint32_t xz[kQueueCap];
-  uint32_t xw[kQueueCap];
-  typename std::conditional<FP64, double, uint32_t>::type first[kQueueCap];
+struct WarpQueue;
+template <>
+struct WarpQueue<false> {
+  static constexpr uint32_t kCap = 256;
+  uint32_t r[kCap];
+  uint32_t first[kCap];
 };
+template <>
+struct WarpQueue<true> {
+  static constexpr uint32_t kCap = 128;
+  uint32_t r[kCap];
+  uint32_t xz[kCap];
+  uint32_t xw[kCap];
+  double first[kCap];
+};
+constexpr uint32_t kQueueCap = 64;  // the end queue's ring
+
 // Per-warp queue of walks that ended at s = 1 (their samples are evaluated 32
 // at a time): the exponents and the end state with the sign in bit 31.  At
 // most 32 are added per iteration and fewer than 32 are left after one, so
@@ -557,6 +569,7 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
     const uint32_t bucket = __umulhi(xz, static_cast<uint32_t>(m.deg));
     if (kChecked && (m.start < 0 || static_cast<int64_t>(m.start) + bucket >= a.nnz)) return false;
     uint32_t pick;
+    Meta mnext{};
     if (IS) {
       const uint4* ep = reinterpret_cast<const uint4*>(
           static_cast<const AliasEntryIS*>(a.alias) + m.start + bucket);
@@ -566,15 +579,21 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
       pick = keep ? e0.y : e0.z;
       lw = P::add(lw, static_cast<T>(__uint_as_float(keep ? e1.x : e1.y)));
     } else {
-      const uint4 ent = __ldg(reinterpret_cast<const uint4*>(
-                                  static_cast<const AliasEntry*>(a.alias) + m.start) + bucket);
-      pick = (xw < ent.x) ? ent.y : ent.z;
+      // the fused entry: both candidates' row records arrive with it
+      using Fused = typename std::conditional<FP64, FusedEntry64, FusedEntry32>::type;
+      const Fused* fe = static_cast<const Fused*>(a.alias) + m.start + bucket;
+      const uint4 ent = __ldg(reinterpret_cast<const uint4*>(fe));
+      const Meta mk = load_meta(&fe->mk, 0);
+      const Meta ma = load_meta(&fe->ma, 0);
+      const bool keep = xw < ent.x;
+      pick = keep ? ent.y : ent.z;
+      mnext = keep ? mk : ma;
     }
     if (kChecked && static_cast<int64_t>(pick & kColMask) >= a.n) return false;
     neg ^= pick >> 31;
     j = static_cast<int32_t>(pick & kColMask);
     if (TRACE) hash = (hash ^ static_cast<uint32_t>(j)) * 16777619u;
-    m = load_meta(meta, j);
+    m = IS ? load_meta(meta, j) : mnext;
     s = s_new;
     ++e;
     return true;
@@ -696,75 +715,120 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
     }
   };
 
+  // Record of a walk screened as never jumping (trace only).
+  auto trace_still = [&](uint32_t rs) {
+    mlmc_walk_record rec;
+    rec.end = static_cast<int32_t>(row);
+    rec.jumps = 0;
+    rec.sign = 1;
+    rec.hash = 2166136261u;
+    rec.y = static_cast<double>(y_still);
+    rec.status = 0;
+    rec.pad = 0;
+    a.trace[row * a.trace_stride + a.trace_base + (r_lo + rs)] = rec;
+  };
+  // FP32 screening: the blocks of four walks (groups rep/4) that meet the
+  // item's replica range [rep_base, rep_base + span).
+  uint64_t gnext = rep_base >> 2;
+  const uint64_t g_end = (rep_base + span + 3) >> 2;
+  // FP32 rows with 1/(t L) >= 1 take a walk's first uniform from its group's
+  // block (the walks the one-wave path runs in such rows, too).
+  const bool group_first = !FP64 && static_cast<float>(m0.inv_rate) >= 1.0f;
+
   for (;;) {
     if (two_wave) {
-      // Screen the first holding times of the next 64 walks (two per lane:
-      // independent Philox chains that the lane's instructions interleave).
-      while (qtail - qhead < 32u && screened < span) {
-        uint4 x[kWays];
-        T h1[kWays] = {};
-        bool push[kWays];
+      constexpr uint32_t kCap = WarpQueue<FP64>::kCap;
+      // Screen first holding times while fewer than 32 walks are queued.
+      if constexpr (FP64) {
+        // 64 walks per round (two per lane: independent Philox chains that
+        // the lane's instructions interleave), each from its own draw 0.
+        while (qtail - qhead < 32u && screened < span) {
+          uint4 x[kWays];
+          T h1[kWays] = {};
+          bool push[kWays];
 #pragma unroll
-        for (int w = 0; w < kWays; ++w) {
-          const uint64_t rep = rep_base + screened + static_cast<uint32_t>(32 * w + lane);
-          x[w] = keys.draw(make_uint4(static_cast<uint32_t>(rep), row32, 0u,
-                                      a.ctr3 | (static_cast<uint32_t>(rep >> 32) << 8)));
-        }
+          for (int w = 0; w < kWays; ++w) {
+            const uint64_t rep = rep_base + screened + static_cast<uint32_t>(32 * w + lane);
+            x[w] = keys.draw(make_uint4(static_cast<uint32_t>(rep), row32, 0u,
+                                        a.ctr3 | (static_cast<uint32_t>(rep >> 32) << 8)));
+          }
 #pragma unroll
-        for (int w = 0; w < kWays; ++w) {
-          const uint32_t rs = screened + static_cast<uint32_t>(32 * w + lane);
-          if (FP64) {
+          for (int w = 0; w < kWays; ++w) {
+            const uint32_t rs = screened + static_cast<uint32_t>(32 * w + lane);
             h1[w] = P::mul(P::neglog(P::uniform(x[w])), inv_rate0);
             push[w] = rs < span && h1[w] < static_cast<T>(1);
-          } else {
-            push[w] = rs < span && static_cast<int32_t>(x[w].x >> 9) > still_max;  // uniform index
-          }
-          if (rs < span && !push[w]) {
-            ++n_still;
-            if (TRACE) {
-              mlmc_walk_record rec;
-              rec.end = static_cast<int32_t>(row);
-              rec.jumps = 0;
-              rec.sign = 1;
-              rec.hash = 2166136261u;
-              rec.y = static_cast<double>(y_still);
-              rec.status = 0;
-              rec.pad = 0;
-              a.trace[row * a.trace_stride + a.trace_base + (r_lo + rs)] = rec;
+            if (rs < span && !push[w]) {
+              ++n_still;
+              if (TRACE) trace_still(rs);
             }
+            const unsigned pm = __ballot_sync(kFull, push[w]);
+            if (push[w]) {
+              const uint32_t slot = (qtail + static_cast<uint32_t>(__popc(pm & lanes_below))) & (kCap - 1);
+              q->r[slot] = rs;
+              q->xz[slot] = x[w].z;
+              q->xw[slot] = x[w].w;
+              q->first[slot] = h1[w];
+            }
+            qtail += static_cast<uint32_t>(__popc(pm));
           }
-          const unsigned pm = __ballot_sync(kFull, push[w]);
-          if (push[w]) {
-            const uint32_t slot =
-                (qtail + static_cast<uint32_t>(__popc(pm & lanes_below))) & (kQueueCap - 1);
-            q->r[slot] = rs;
-            q->xz[slot] = x[w].z;
-            q->xw[slot] = x[w].w;
-            if constexpr (FP64) q->first[slot] = h1[w];
-            else q->first[slot] = x[w].x;
-          }
-          qtail += static_cast<uint32_t>(__popc(pm));
+          screened += 32u * kWays;
         }
-        screened += 32u * kWays;
+      } else {
+        // 32 blocks of four walks per round: walk rep takes word (rep mod 4)
+        // of the block of group rep/4 (draw index 0xFFFFFFFE); the still test
+        // is the uniform's index against the row's threshold index.
+        while (qtail - qhead < 32u && gnext < g_end) {
+          const uint64_t g = gnext + static_cast<uint32_t>(lane);
+          uint4 xg = make_uint4(0u, 0u, 0u, 0u);
+          if (g < g_end)
+            xg = keys.draw(make_uint4(static_cast<uint32_t>(g), row32, 0xFFFFFFFEu,
+                                      a.ctr3 | (static_cast<uint32_t>(g >> 32) << 8)));
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const uint64_t rep = 4 * g + static_cast<uint64_t>(k);
+            const bool valid = g < g_end && rep >= rep_base && rep < rep_base + span;
+            const uint32_t word = k == 0 ? xg.x : (k == 1 ? xg.y : (k == 2 ? xg.z : xg.w));
+            const uint32_t rs = static_cast<uint32_t>(rep - rep_base);
+            const bool push = valid && static_cast<int32_t>(word >> 9) > still_max;
+            if (valid && !push) {
+              ++n_still;
+              if (TRACE) trace_still(rs);
+            }
+            const unsigned pm = __ballot_sync(kFull, push);
+            if (push) {
+              const uint32_t slot = (qtail + static_cast<uint32_t>(__popc(pm & lanes_below))) & (kCap - 1);
+              q->r[slot] = rs;
+              q->first[slot] = word;
+            }
+            qtail += static_cast<uint32_t>(__popc(pm));
+          }
+          gnext += 32u;
+        }
       }
       __syncwarp();
       // Refill wave: lanes without a walk take queued ones and make their
-      // first jump with the queued draw.
+      // first jump.
       const unsigned idle = __ballot_sync(kFull, !live);
       if (!live) {
         const uint32_t k = qhead + static_cast<uint32_t>(__popc(idle & lanes_below));
         if (k < qtail) {
-          const uint32_t slot = k & (kQueueCap - 1);
+          const uint32_t slot = k & (kCap - 1);
           start_walk(q->r[slot]);
           T s1;
+          uint32_t xz, xw;
           if constexpr (FP64) {
             s1 = q->first[slot];  // drawn at screening
+            xz = q->xz[slot];
+            xw = q->xw[slot];
           } else {
-            // s = 0 and m = m0: the first event's time from the queued word
+            // s = 0 and m = m0: the first holding time from the queued word,
+            // the first jump from the walk's own draw 0
+            const uint4 x0 = keys.draw(make_uint4(c_lo, row32, 0u, c_hi));
             s1 = P::add(s, P::mul(P::neglog(P::uniform(make_uint4(q->first[slot], 0u, 0u, 0u))),
                                   static_cast<T>(m.inv_rate)));
+            xz = x0.z;
+            xw = x0.w;
           }
-          const uint32_t xz = q->xz[slot], xw = q->xw[slot];
           if (static_cast<int64_t>(e) >= a.max_jumps) {
             finish(1, false);
           } else if (jump(s1, xz, xw)) {
@@ -807,7 +871,16 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
       claimed = min(claimed + static_cast<uint32_t>(__popc(idle)), span);
       if (!__any_sync(kFull, live)) break;  // every walk of the item done
       if (live) {
-        const uint4 x = keys.draw(make_uint4(c_lo, row32, e, c_hi));
+        uint4 x = keys.draw(make_uint4(c_lo, row32, e, c_hi));
+        if (!FP64 && group_first && e == 0) {
+          // the first uniform from word (rep mod 4) of the group's block
+          const uint64_t rep = rep_base + r;
+          const uint64_t g = rep >> 2;
+          const uint4 xg = keys.draw(make_uint4(static_cast<uint32_t>(g), row32, 0xFFFFFFFEu,
+                                                a.ctr3 | (static_cast<uint32_t>(g >> 32) << 8)));
+          const uint32_t k = static_cast<uint32_t>(rep & 3u);
+          x.x = k == 0 ? xg.x : (k == 1 ? xg.y : (k == 2 ? xg.z : xg.w));
+        }
         const T s_new = P::add(s, P::mul(P::neglog(P::uniform(x)), static_cast<T>(m.inv_rate)));
         if (!(s_new < static_cast<T>(1))) {
           finish(0, true);
@@ -1121,10 +1194,11 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk_fwd(const __grid_con
             done = true;
             status = 2;
           } else {
+            using Fused = typename std::conditional<FP64, FusedEntry64, FusedEntry32>::type;
             const uint4 ent = IS ? __ldg(reinterpret_cast<const uint4*>(
                                        static_cast<const AliasEntryIS*>(a.alias) + m.start + bk))
                                  : __ldg(reinterpret_cast<const uint4*>(
-                                       static_cast<const AliasEntry*>(a.alias) + m.start) + bk);
+                                       static_cast<const Fused*>(a.alias) + m.start + bk));
             const uint32_t pk = (x.w < ent.x) ? ent.y : ent.z;
             if (static_cast<int64_t>(pk & kColMask) >= a.n) {
               done = true;
@@ -1145,6 +1219,7 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk_fwd(const __grid_con
           kprev = gi;
           const uint32_t bucket = __umulhi(x.z, static_cast<uint32_t>(m.deg));
           uint32_t pick;
+          Meta mnext{};
           if (IS) {
             const uint4* ep = reinterpret_cast<const uint4*>(
                 static_cast<const AliasEntryIS*>(a.alias) + m.start + bucket);
@@ -1154,14 +1229,19 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk_fwd(const __grid_con
             pick = keep ? e0.y : e0.z;
             lw = P::add(lw, static_cast<T>(__uint_as_float(keep ? e1.x : e1.y)));
           } else {
-            const uint4 ent = __ldg(reinterpret_cast<const uint4*>(
-                                        static_cast<const AliasEntry*>(a.alias) + m.start) + bucket);
-            pick = (x.w < ent.x) ? ent.y : ent.z;
+            using Fused = typename std::conditional<FP64, FusedEntry64, FusedEntry32>::type;
+            const Fused* fe = static_cast<const Fused*>(a.alias) + m.start + bucket;
+            const uint4 ent = __ldg(reinterpret_cast<const uint4*>(fe));
+            const Meta mk = load_meta(&fe->mk, 0);
+            const Meta ma = load_meta(&fe->ma, 0);
+            const bool keep = x.w < ent.x;
+            pick = keep ? ent.y : ent.z;
+            mnext = keep ? mk : ma;
           }
           neg ^= pick >> 31;
           j = static_cast<int32_t>(pick & kColMask);
           if (TRACE) hash = (hash ^ static_cast<uint32_t>(j)) * 16777619u;
-          m = load_meta(meta, j);
+          m = IS ? load_meta(meta, j) : mnext;
           s = s_new;
           ++e;
         } else {
@@ -1346,7 +1426,7 @@ cudaError_t launch_walk_forward(mlmc_plan* p, const WalkLaunch& w, int64_t* laun
   FwdArgs a{};
   a.meta = fp64 ? static_cast<const void*>(p->d_meta64) : static_cast<const void*>(p->d_meta32);
   a.alias = p->proposal_active ? static_cast<const void*>(p->d_alias_is)
-                               : static_cast<const void*>(p->d_alias);
+                               : static_cast<const void*>(p->d_fused);
   a.v = w.v;
   a.cdf = p->d_cdf;
   a.guide = p->d_guide;
@@ -1391,7 +1471,7 @@ cudaError_t launch_walk(mlmc_plan* p, const WalkLaunch& w, int64_t* launches) {
   WalkArgs a{};
   a.meta = fp64 ? static_cast<const void*>(p->d_meta64) : static_cast<const void*>(p->d_meta32);
   a.alias = p->proposal_active ? static_cast<const void*>(p->d_alias_is)
-                               : static_cast<const void*>(p->d_alias);
+                               : static_cast<const void*>(p->d_fused);
   if (fp64) {
     a.v_walk = w.v;
   } else {
@@ -1465,7 +1545,7 @@ cudaError_t launch_walk_scratch(mlmc_plan* p, const WalkLaunch& w, unsigned long
   WalkArgs a{};
   a.meta = fp64 ? static_cast<const void*>(p->d_meta64) : static_cast<const void*>(p->d_meta32);
   a.alias = p->proposal_active ? static_cast<const void*>(p->d_alias_is)
-                               : static_cast<const void*>(p->d_alias);
+                               : static_cast<const void*>(p->d_fused);
   if (fp64) {
     a.v_walk = w.v;
   } else {

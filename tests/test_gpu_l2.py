@@ -26,16 +26,16 @@ def test_window_covers_the_tables(prec):
     with make_plan(a, t, prec, l2_persist=0) as plan:
         assert plan.l2_window() == {"bytes": 0, "hit_ratio": 0.0}
     assert w["bytes"] > 0          # GB300: persisting L2 and access-policy windows
-    row = 16 if prec == 1 else 32
-    assert w["bytes"] >= row * a.n + 16 * a.nnz
-    assert w["bytes"] < row * a.n + 16 * a.nnz + 1024
+    row, entry = (16, 48) if prec == 1 else (32, 80)   # row record, fused alias entry
+    assert w["bytes"] >= row * a.n + entry * a.nnz
+    assert w["bytes"] < row * a.n + entry * a.nnz + 1024
     assert w["hit_ratio"] == 1.0
 
 
 def test_window_larger_than_the_set_aside_has_partial_hit_ratio():
-    # ~6.4e6 alias entries: ~109 MB of FP32 tables, above GB300's persisting
-    # set-aside (about 85 MB) and below its 128 MB window limit
-    a = I.ba_graph(400_000, 8, seed=3)
+    # ~2.2e6 fused entries of 48 B: ~110 MB of FP32 tables, above GB300's
+    # persisting set-aside (about 85 MB) and below its 128 MB window limit
+    a = I.ba_graph(140_000, 8, seed=3)
     with make_plan(a, 0.01, 1, l2_persist=1) as plan:
         w = plan.l2_window()
     assert 100e6 < w["bytes"] < 128 * 2 ** 20

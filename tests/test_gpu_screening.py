@@ -1,6 +1,6 @@
 """The FP32 walk decides whether a walk ever leaves its start row by comparing
-the index of its first uniform with a per-row threshold index instead of
-evaluating -ln(u).  These tests put one walk's first draw exactly on that
+the index of its first uniform (a word of the block shared by four walks)
+with a per-row threshold index instead of evaluating -ln(u).  These tests put one walk's first draw exactly on that
 threshold (from either side) by choosing t, and check the GPU trajectory and
 value against the oracle, which evaluates the holding time directly."""
 import numpy as np
@@ -24,9 +24,12 @@ def _built():
 
 
 def _first_draw_index(seed, row, rep, level):
-    x = W.philox([rep & 0xFFFFFFFF, row, 0, level | ((rep >> 32) << 8)],
+    # FP32 rows with 1/(tL) >= 1: the first uniform is word (rep mod 4) of
+    # the block of group rep // 4 (draw index 0xFFFFFFFE)
+    g = rep >> 2
+    x = W.philox([g & 0xFFFFFFFF, row, 0xFFFFFFFE, level | ((g >> 32) << 8)],
                  [seed & 0xFFFFFFFF, seed >> 32])
-    return int(x[0]) >> 9
+    return int(x[rep & 3]) >> 9
 
 
 def _u(i):

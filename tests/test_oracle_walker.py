@@ -236,3 +236,40 @@ def test_value_function_proposal_reduces_variance():
     plain = rel_var(W.build_tables(a, t))
     learned = rel_var(W.build_tables(a, t, x.astype(np.float32), 0.1))
     assert learned < 0.8 * plain
+
+
+def test_fp32_first_uniform_comes_from_the_shared_block():
+    # FP32 walks in rows with 1/(tL) >= 1 take their first uniform from word
+    # (rep mod 4) of the block (rep // 4, row, 0xFFFFFFFE, level | rep_hi..);
+    # the walk never jumps exactly when that uniform's holding time reaches 1.
+    a = I.ring_graph(16)                     # L = 2 everywhere
+    t = 0.3                                  # 1/(tL) = 1.67 >= 1
+    seed, level = 99, 3
+    wk = W.Walker(a, t, np.ones(a.n), seed=seed, precision=W.FP32)
+    ir = wk.tables.inv_rate32
+    assert ir[0] >= 1.0
+    reps = np.arange(400)
+    rows = np.zeros(reps.size, np.int64)
+    rec = wk.walks(rows, reps, level, False)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    differ = 0
+    for r, jumps in zip(reps, rec["jumps"]):
+        xg = W.philox([r >> 2, 0, 0xFFFFFFFE, level], key)
+        x0 = W.philox([r, 0, 0, level], key)
+        def still(word):
+            u = np.float32(((int(word) >> 8) | 1) * 2.0 ** -24)
+            return np.float32(W.neglog32(np.array([u], np.float32))[0] * ir[0]) >= 1.0
+        assert (jumps == 0) == still(xg[r & 3])
+        differ += still(xg[r & 3]) != still(x0[0])
+    assert differ > 20                       # the test tells the two layouts apart
+
+
+def test_fp32_shared_block_keeps_the_still_probability():
+    a = I.ring_graph(8)
+    t = 0.4                                  # t L = 0.8: P(no jump) = e^-0.8
+    wk = W.Walker(a, t, np.ones(a.n), seed=5, precision=W.FP32)
+    m = 200000
+    rec = wk.walks(np.zeros(m, np.int64), np.arange(m), 2, False)
+    p = np.exp(-0.8)
+    frac = (rec["jumps"] == 0).mean()
+    assert abs(frac - p) < 5 * np.sqrt(p * (1 - p) / m)
