@@ -452,9 +452,9 @@ OPS_JUMP = {True: 22, False: 15}
 OPS_END_JUMPED = {True: 31, False: 24}
 OPS_END_STILL = 1
 # DRAM bytes of one captured walk launch (ncu, profiles/walk_fp32_ba_n1e5_l0.md:
-# 4.1e8 walks at l0 after an L2 flush; the tables are read once, everything
-# else hits L2); None when the kernel changed after the capture.
-TRAFFIC_CAPTURE = 15655936
+# 4.1e8 walks at l0 after an L2 flush; the fused tables, 40 MB, are read once
+# and everything else hits L2); None when the kernel changed after the capture.
+TRAFFIC_CAPTURE = 41288448
 
 
 def walk_roofline(level_log, walk_s, clocks, peaks, total_ms):
