@@ -783,12 +783,15 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
           if (g < g_end)
             xg = keys.draw(make_uint4(static_cast<uint32_t>(g), row32, 0xFFFFFFFEu,
                                       a.ctr3 | (static_cast<uint32_t>(g >> 32) << 8)));
+          // offset of the block's first walk in the item (wraps below 0: the
+          // unsigned compare with span rejects it)
+          const uint32_t rs0 = 4u * static_cast<uint32_t>(g - (rep_base >> 2)) -
+                               static_cast<uint32_t>(rep_base & 3u);
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
-            const uint64_t rep = 4 * g + static_cast<uint64_t>(k);
-            const bool valid = g < g_end && rep >= rep_base && rep < rep_base + span;
+            const uint32_t rs = rs0 + static_cast<uint32_t>(k);
+            const bool valid = rs < span;
             const uint32_t word = k == 0 ? xg.x : (k == 1 ? xg.y : (k == 2 ? xg.z : xg.w));
-            const uint32_t rs = static_cast<uint32_t>(rep - rep_base);
             const bool push = valid && static_cast<int32_t>(word >> 9) > still_max;
             if (valid && !push) {
               ++n_still;
