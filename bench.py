@@ -512,7 +512,7 @@ def run_batch_workload(args):
     g.build()
     from paper_1904_12754_gb300 import mlmc as M
     stream = torch.cuda.current_stream()
-    inst = I.workload_c3()
+    inst = I.workload_c3(n_hi=args.batch_nmax)
     tol = args.tol
     sched = M.schedule_default(precision=M.FP32_KAHAN, num_levels=3, max_levels=10, pilot_walks=64,
                                time_budget_s=600.0)
@@ -562,8 +562,9 @@ def run_batch_workload(args):
     line = {"metric": "time to per-instance rel. RMS tolerance, batched vs plain", "unit": "s",
             "value": t_batch, "higher_is_better": False, "n_gpus": 1, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": "256 Laplacian instances (2D/3D), n log-uniform in [1e3, 1e6], "
-                                   "t ~ U[0.1, 2], 1-8 right-hand sides", "tol": tol,
+            "config": {"workload": f"256 Laplacian instances (2D/3D), n log-uniform in "
+                                   f"[1e3, {args.batch_nmax:g}], t ~ U[0.1, 2], 1-8 right-hand sides",
+                       "tol": tol,
                        "problems": len(probs), "rows": rows},
             "batched": {"seconds": t_batch, "walk_steps_per_s": batch_events / t_batch,
                         "rounds": info["rounds"], "gpu_seconds": info["gpu_seconds"],
@@ -1074,6 +1075,9 @@ def main():
     ap.add_argument("--block", type=int, default=0,
                     help="--workload kernel: threads per block (0 = library default)")
     ap.add_argument("--tol", type=float, default=1e-2, help="tolerance of --workload batch")
+    ap.add_argument("--batch-nmax", type=float, default=1e6,
+                    help="--workload batch: largest instance size (1e6: the batching workload; "
+                         "smaller: many small problems)")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
