@@ -402,8 +402,14 @@ typedef struct {
 } orc_walk_rec;
 
 /* Counter layout: (rep bits 0-31, row, draw index, level | variant<<6 |
- * rep bits 32-55 << 8); key = seed.  In the residual-clock walk the draw
- * index equals the number of jumps taken so far. */
+ * rep bits 32-55 << 8); key = seed.  Which words of which draw a walk uses:
+ *   FP64 (and the per-interval variant ORC_REDRAW): draw k gives the k-th
+ *     holding time (words 0, 1) and the (k+1)-th jump (words 2, 3), so the
+ *     draw index equals the number of jumps taken so far.
+ *   FP32 (one 32-bit word per uniform): draw k gives the (k+1)-th jump
+ *     (words 2, 3) and the holding time that follows it (word 0); the first
+ *     holding time takes word 1 of draw 0, or the shared block word below.
+ *     A walk with J >= 1 jumps then uses draws 0 .. J-1 and no word twice. */
 /* The three fixed counter words of one walk.  Backward: (rep bits 0-31,
  * row, -, level | variant << 6 | rep bits 32-55 << 8).  Forward walk g:
  * (g bits 0-31, g bits 32-63, -, level | 1 << 6). */
@@ -452,6 +458,13 @@ static double orc_hold(const orc_ctx *c, int64_t j, const uint32_t x[4], double 
     }
     double s = orc_neglog64(orc_uniform64(x[0], x[1])) * c->inv_rate[j];
     return from + s;
+}
+
+/* FP32 holding time in state j from the single uniform word w. */
+static double orc_hold32_word(const orc_ctx *c, int64_t j, uint32_t w, double from)
+{
+    float s = orc_neglog32(orc_uniform32(w)) * c->inv_rate32[j];
+    return (double)((float)from + s);
 }
 
 /* Choose the next state from row j's alias table with draw words x2, x3;
@@ -523,27 +536,35 @@ static int orc_walk_core(const orc_ctx *c, int64_t row, orc_ctr kc, int level, i
     double integ2 = src_on ? c->f[row] : 0.0;
     double integ1 = integ2;
 
+    /* FP32 walks pack the holding time that follows a jump into the jump's
+     * draw (the counter layout above); the per-interval variant keeps one
+     * draw per clock. */
+    const int packed = c->precision == ORC_FP32 && c->variant != ORC_REDRAW;
     orc_draw_k(c, kc, ndraw++, x);
-    /* Stream layout of the FP32 backward walk in a row with 1/(t L) >= 1
-     * (rows where most walks never jump): the first holding time takes its
-     * uniform from word (rep mod 4) of the shared block of the four walks
-     * 4g..4g+3, g = floor(rep/4), counter (g bits 0-31, row, 0xFFFFFFFE,
-     * level | variant << 6 | g bits 32-55 << 8); the first jump keeps words
-     * 2 and 3 of the walk's own draw 0.  The law is unchanged: the four words
-     * of one block are independent uniforms. */
-    if (backward && c->precision == ORC_FP32 && c->variant == ORC_RESIDUAL &&
-        c->inv_rate32[row] >= 1.0f) {
-        const uint64_t g = (uint64_t)rep >> 2;
-        orc_ctr kg;
-        kg.w0 = (uint32_t)(g & 0xFFFFFFFFull);
-        kg.w1 = (uint32_t)row;
-        kg.w3 = (uint32_t)level | ((uint32_t)c->variant << 6) |
-                ((uint32_t)((g >> 32) & 0xFFFFFFull) << 8);
-        uint32_t xg[4];
-        orc_draw_k(c, kg, 0xFFFFFFFEu, xg);
-        x[0] = xg[(uint64_t)rep & 3u];
+    double t_next;
+    if (packed) {
+        uint32_t w_first = x[1];
+        /* FP32 backward walk in a row with 1/(t L) >= 1 (rows where most
+         * walks never jump): the first holding time takes its uniform from
+         * word (rep mod 4) of the shared block of the four walks 4g..4g+3,
+         * g = floor(rep/4), counter (g bits 0-31, row, 0xFFFFFFFE, level |
+         * variant << 6 | g bits 32-55 << 8).  The law is unchanged: the
+         * four words of one block are independent uniforms. */
+        if (backward && c->variant == ORC_RESIDUAL && c->inv_rate32[row] >= 1.0f) {
+            const uint64_t g = (uint64_t)rep >> 2;
+            orc_ctr kg;
+            kg.w0 = (uint32_t)(g & 0xFFFFFFFFull);
+            kg.w1 = (uint32_t)row;
+            kg.w3 = (uint32_t)level | ((uint32_t)c->variant << 6) |
+                    ((uint32_t)((g >> 32) & 0xFFFFFFull) << 8);
+            uint32_t xg[4];
+            orc_draw_k(c, kg, 0xFFFFFFFEu, xg);
+            w_first = xg[(uint64_t)rep & 3u];
+        }
+        t_next = orc_hold32_word(c, j, w_first, 0.0);
+    } else {
+        t_next = orc_hold(c, j, x, 0.0);
     }
-    double t_next = orc_hold(c, j, x, 0.0);
 
     for (int64_t step = 1; step <= N; ++step) {
         double g = c->dl[j] / (double)N;
@@ -561,14 +582,21 @@ static int orc_walk_core(const orc_ctx *c, int64_t row, orc_ctr kc, int level, i
             }
             int64_t from = j;
             double lr = 0.0;
+            /* FP32: jump k + 1 takes draw k (draw 0 is already at hand). */
+            if (packed && jumps > 0) orc_draw_k(c, kc, ndraw++, x);
             j = orc_jump(c, j, x, &sign, &lr);
             log_is = log_is + lr;
             hash = (hash ^ (uint32_t)j) * 16777619u;
             jumps = jumps + 1;
-            orc_draw_k(c, kc, ndraw++, x);
             /* R1: the new holding time uses the new state's rate; the
              * literal reading uses the state just left. */
-            t_next = orc_hold(c, (c->variant == ORC_LITERAL_RATE) ? from : j, x, t_next);
+            const int64_t rate_state = (c->variant == ORC_LITERAL_RATE) ? from : j;
+            if (packed) {
+                t_next = orc_hold32_word(c, rate_state, x[0], t_next);
+            } else {
+                orc_draw_k(c, kc, ndraw++, x);
+                t_next = orc_hold(c, rate_state, x, t_next);
+            }
         }
         g = c->dl[j] / (double)N;
         eta2 = eta2 * exp(g / 2.0);

@@ -273,3 +273,59 @@ def test_fp32_shared_block_keeps_the_still_probability():
     p = np.exp(-0.8)
     frac = (rec["jumps"] == 0).mean()
     assert abs(frac - p) < 5 * np.sqrt(p * (1 - p) / m)
+
+
+def _hold_count(words_after_jump, first_word, ir):
+    """Jumps of a walk with constant rate: the number of partial sums of
+    FP32 holding times below 1, the first from `first_word`, the one after
+    jump k from words_after_jump(k) (k = 0, 1, ...)."""
+    def hold(word):
+        u = np.float32(((int(word) >> 8) | 1) * 2.0 ** -24)
+        return np.float32(W.neglog32(np.array([u], np.float32))[0] * ir)
+    s = hold(first_word)
+    jumps = 0
+    while s < np.float32(1.0):
+        s = np.float32(s + hold(words_after_jump(jumps)))
+        jumps += 1
+    return jumps
+
+
+@pytest.mark.parametrize("t", [0.3, 1.4])
+def test_fp32_holding_time_after_a_jump_comes_from_the_jump_draw(t):
+    # FP32 walks: jump k + 1 takes words 2, 3 of draw k and the holding
+    # time after it word 0 of the same draw; the first holding time takes
+    # word 1 of draw 0 (rows with 1/(tL) < 1, t = 1.4) or the shared block
+    # word (1/(tL) >= 1, t = 0.3).  On a ring every state has L = 2, so the
+    # jump count depends on the holding-time words alone.
+    a = I.ring_graph(16)
+    seed, level, row = 12345, 4, 3
+    wk = W.Walker(a, t, np.ones(a.n), seed=seed, precision=W.FP32)
+    ir = wk.tables.inv_rate32[row]
+    grouped = ir >= 1.0
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    reps = np.arange(300)
+    rec = wk.walks(np.full(reps.size, row, np.int64), reps, level, False)
+    old_layout_differs = 0
+    for r, jumps in zip(reps, rec["jumps"]):
+        draw = lambda k, r=r: W.philox([r, row, k, level], key)
+        first = (W.philox([r >> 2, row, 0xFFFFFFFE, level], key)[r & 3] if grouped
+                 else draw(0)[1])
+        assert jumps == _hold_count(lambda k: draw(k)[0], first, ir)
+        old_first = first if grouped else draw(0)[0]
+        old_layout_differs += jumps != _hold_count(lambda k: draw(k + 1)[0], old_first, ir)
+    assert rec["jumps"].max() >= 2
+    assert old_layout_differs > 20           # the test tells the layouts apart
+
+
+def test_fp32_forward_walk_uses_the_packed_layout():
+    # Forward walk g: counter (g lo, g hi, draw, level | 1 << 6); its first
+    # holding time is word 1 of draw 0, the one after jump k word 0 of draw k.
+    a = I.ring_graph(12)
+    t, seed, level = 1.2, 77, 3
+    fw = W.ForwardWalker(a, t, np.ones(a.n), seed=seed, precision=W.FP32)
+    ir = fw.tables.inv_rate32[0]
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    rec = fw.walks_fwd(0, 200, level, False)
+    for g, jumps in enumerate(rec["jumps"]):
+        draw = lambda k, g=g: W.philox([g, 0, k, level | (1 << 6)], key)
+        assert jumps == _hold_count(lambda k: draw(k)[0], draw(0)[1], ir)
