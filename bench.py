@@ -434,11 +434,16 @@ def run_ours(args):
 # Walk-kernel roofline: ALU (issue) bound with this workload's tables in L2.
 # Algorithmic operations of the FP32 walk, counted from the kernel source
 # (each integer/FP32 operation, compare, select, load, exp = 1):
-#   Philox draw   60  (10 rounds x 2 wide multiplies, 2 three-input xors, 2 key adds)
+#   Philox draw   60  (10 rounds x 2 wide multiplies, 2 three-input xors, 2 key
+#                     adds).  The FP32 layout needs one draw per jump plus one
+#                     block per four walks for their first holding times
+#                     (rows with 1/(tL) >= 1, nearly all rows here; a walk in
+#                     another row that never jumps also draws once, which
+#                     this count leaves out)
 #   holding time  37  (uniform 4, -ln(u) 30, scale + add + compare 3), for
-#                     every event except the first of a walk that never jumps:
-#                     that one is decided by comparing the uniform's index with
-#                     the row's threshold index (2)
+#                     every event except the first of a walk that never jumps
+#   still test     2  per walk: the first uniform's index against the row's
+#                     threshold index
 #   every jump    22 (levels above l0) / 15 (l0): grid index, counts, bucket,
 #                 alias gather and select, sign, next-state gather
 #   walk end      31 / 24 for a walk that jumped (exponents, exp/expm1, Kahan
@@ -454,7 +459,7 @@ OPS_END_STILL = 1
 # DRAM bytes of one captured walk launch (ncu, profiles/walk_fp32_ba_n1e5_l0.md:
 # 4.1e8 walks at l0 after an L2 flush; the fused tables, 40 MB, are read once
 # and everything else hits L2); None when the kernel changed after the capture.
-TRAFFIC_CAPTURE = 41288448
+TRAFFIC_CAPTURE = None
 
 
 def walk_roofline(level_log, walk_s, clocks, peaks, total_ms):
@@ -466,9 +471,9 @@ def walk_roofline(level_log, walk_s, clocks, peaks, total_ms):
         c = lv["coarse"]
         ev = lv["walks"] + lv["jumps"]
         still = lv.get("still_walks", 0)
-        ops += OPS_DRAW * ev + OPS_HOLD * (ev - still) + OPS_STILL_TEST * still \
-            + OPS_JUMP[c] * lv["jumps"] + OPS_END_JUMPED[c] * (lv["walks"] - still) \
-            + OPS_END_STILL * still
+        ops += OPS_DRAW * (lv["jumps"] + lv["walks"] / 4.0) + OPS_HOLD * (ev - still) \
+            + OPS_STILL_TEST * lv["walks"] + OPS_JUMP[c] * lv["jumps"] \
+            + OPS_END_JUMPED[c] * (lv["walks"] - still) + OPS_END_STILL * still
         # table gathers: alias entry + the new state's row record per jump,
         # v at the end state per walk that jumped (FP32 layout)
         gather += 32.0 * lv["jumps"] + 4.0 * (lv["walks"] - still)

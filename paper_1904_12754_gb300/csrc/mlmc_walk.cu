@@ -16,9 +16,13 @@
 //   E_f = (acc_f - h)/N,  E_c = (acc_c - h)/(N/2),  E_f - E_c = (acc_d + h)/N
 // and the sample is Y = sign v_end e^{E_f} at the coarsest level and
 // Y = sign v_end e^{E_c} expm1(E_f - E_c) above it (Fig. 1; no cancellation).
-// Every walk draws one Philox4x32-10 block per holding time, counter
-// (rep_lo, row, jump index, level | rep_hi << 8), key = seed: words 0-1 give
-// the time, words 2-3 the bucket and the alias coin of the jump that ends it.
+// Draws are Philox4x32-10 blocks, counter (rep_lo, row, draw index, level |
+// rep_hi << 8), key = seed.  FP64 walks: draw k gives the k-th holding time
+// (words 0-1) and the bucket and alias coin of the jump that ends it (words
+// 2-3).  FP32 walks (one word per uniform): draw k gives the (k+1)-th jump
+// (words 2-3) and the holding time after it (word 0); the first holding time
+// is word 1 of draw 0, or a word of a block shared by four walks in rows
+// whose walks rarely jump.  An FP32 walk thus draws once per jump.
 //
 // Work decomposition: a warp takes one (row, chunk of walks) item at a time
 // from a global counter.  Its lanes first screen the chunk's walks (first
@@ -417,15 +421,17 @@ __device__ __forceinline__ int32_t still_index32(float inv_rate, int lane) {
 
 // One work item: walks r_lo .. r_hi-1 (replica offsets relative to
 // a.rep_begin) of row `row`, run by the whole warp in two interleaved stages.
-//   screen  the 32 lanes draw the first holding time of 64 new walks; a walk
-//           whose first time reaches s = 1 never leaves the row (its sample
-//           is the same for every such walk: it is only counted), the others
-//           are queued;
-//   walk    lanes without a walk take queued ones; an iteration has two
-//           waves: the refilled lanes make their first jump with the queued
-//           draw, then every live lane draws its next holding time and jumps
-//           or ends, so most walks finish in one iteration with the draw on
-//           (nearly) all lanes.
+//   screen  the 32 lanes draw the first holding time of 64 (FP64) or 128
+//           (FP32) new walks; a walk whose first time reaches s = 1 never
+//           leaves the row (its sample is the same for every such walk: it is
+//           only counted), the others are queued;
+//   walk    lanes without a walk take queued ones.  FP64: an iteration has
+//           two waves: the refilled lanes make their first jump with the
+//           queued draw, then every live lane draws its next holding time and
+//           jumps or ends.  FP32: every live lane takes its pending jump with
+//           one draw, which also gives the holding time after the jump, and
+//           ends if that time reaches s = 1.  Either way most walks finish in
+//           one iteration with the draw on (nearly) all lanes.
 // Rows whose walks are long (t L_row > 1) are not screened: an iteration is
 // one event per lane, a lane whose walk ends claims the next walk index at
 // once (ballot + prefix count), and the samples of ended walks are evaluated
@@ -519,6 +525,10 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
   T lw = 0;                // proposal only: sum of log(k/q) over the jumps
   uint32_t hash = 2166136261u;
   T src_f = 0, src_c = 0;  // source only: fine and coarse Simpson sums so far
+  // FP32: the walk's next jump time (< 1), known before the draw that gives
+  // the jump's words; `fresh`: claimed, first holding time not drawn yet.
+  T s_pend = 0;
+  bool fresh = false;
 
   // Start walk r of the item (state at s = 0 in the row).
   auto start_walk = [&](uint32_t r_new) {
@@ -809,53 +819,74 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
         }
       }
       __syncwarp();
-      // Refill wave: lanes without a walk take queued ones and make their
-      // first jump.
-      const unsigned idle = __ballot_sync(kFull, !live);
-      if (!live) {
-        const uint32_t k = qhead + static_cast<uint32_t>(__popc(idle & lanes_below));
-        if (k < qtail) {
-          const uint32_t slot = k & (kCap - 1);
-          start_walk(q->r[slot]);
-          T s1;
-          uint32_t xz, xw;
-          if constexpr (FP64) {
-            s1 = q->first[slot];  // drawn at screening
-            xz = q->xz[slot];
-            xw = q->xw[slot];
-          } else {
-            // s = 0 and m = m0: the first holding time from the queued word,
-            // the first jump from the walk's own draw 0
-            const uint4 x0 = keys.draw(make_uint4(c_lo, row32, 0u, c_hi));
-            s1 = P::add(s, P::mul(P::neglog(P::uniform(make_uint4(q->first[slot], 0u, 0u, 0u))),
-                                  static_cast<T>(m.inv_rate)));
-            xz = x0.z;
-            xw = x0.w;
+      if constexpr (FP64) {
+        // Refill wave: lanes without a walk take queued ones and make their
+        // first jump.
+        const unsigned idle = __ballot_sync(kFull, !live);
+        if (!live) {
+          const uint32_t k = qhead + static_cast<uint32_t>(__popc(idle & lanes_below));
+          if (k < qtail) {
+            const uint32_t slot = k & (kCap - 1);
+            start_walk(q->r[slot]);
+            const T s1 = q->first[slot];  // drawn at screening
+            if (static_cast<int64_t>(e) >= a.max_jumps) {
+              finish(1, false);
+            } else if (jump(s1, q->xz[slot], q->xw[slot])) {
+              live = true;
+            } else {
+              finish(2, false);
+            }
           }
-          if (static_cast<int64_t>(e) >= a.max_jumps) {
+        }
+        qhead = min(qhead + static_cast<uint32_t>(__popc(idle)), qtail);
+        __syncwarp();  // queue slots read above are free for the next screening
+        if (!__any_sync(kFull, live)) break;  // queue empty and every walk screened
+        // Draw wave: every live lane draws its next holding time, then jumps
+        // or ends (short walks: most lanes end here together, so the sample
+        // is evaluated at once).
+        if (live) {
+          const uint4 x = keys.draw(make_uint4(c_lo, row32, e, c_hi));
+          const T s_new = P::add(s, P::mul(P::neglog(P::uniform(x)), static_cast<T>(m.inv_rate)));
+          if (!(s_new < static_cast<T>(1))) {
+            finish(0, false);
+          } else if (static_cast<int64_t>(e) >= a.max_jumps) {
             finish(1, false);
-          } else if (jump(s1, xz, xw)) {
-            live = true;
-          } else {
+          } else if (!jump(s_new, x.z, x.w)) {
             finish(2, false);
           }
         }
-      }
-      qhead = min(qhead + static_cast<uint32_t>(__popc(idle)), qtail);
-      __syncwarp();  // queue slots read above are free for the next screening
-      if (!__any_sync(kFull, live)) break;  // queue empty and every walk screened
-      // Draw wave: every live lane draws its next holding time, then jumps
-      // or ends (short walks: most lanes end here together, so the sample
-      // is evaluated at once).
-      if (live) {
-        const uint4 x = keys.draw(make_uint4(c_lo, row32, e, c_hi));
-        const T s_new = P::add(s, P::mul(P::neglog(P::uniform(x)), static_cast<T>(m.inv_rate)));
-        if (!(s_new < static_cast<T>(1))) {
-          finish(0, false);
-        } else if (static_cast<int64_t>(e) >= a.max_jumps) {
-          finish(1, false);
-        } else if (!jump(s_new, x.z, x.w)) {
-          finish(2, false);
+      } else {
+        // Lanes without a walk take queued ones: the first jump time from
+        // the queued word (s = 0, m = m0).
+        const unsigned idle = __ballot_sync(kFull, !live);
+        if (!live) {
+          const uint32_t k = qhead + static_cast<uint32_t>(__popc(idle & lanes_below));
+          if (k < qtail) {
+            const uint32_t slot = k & (kCap - 1);
+            start_walk(q->r[slot]);
+            s_pend = P::mul(neglog32(uniform32(q->first[slot])), static_cast<T>(m0.inv_rate));
+            live = true;
+          }
+        }
+        qhead = min(qhead + static_cast<uint32_t>(__popc(idle)), qtail);
+        __syncwarp();  // queue slots read above are free for the next screening
+        if (!__any_sync(kFull, live)) break;  // queue empty and every walk screened
+        // Every live lane takes its pending jump with draw e (words 2, 3)
+        // and draws the holding time after it (word 0): one Philox call per
+        // jump.  Short walks: most lanes end here together, so the sample
+        // is evaluated at once.
+        if (live) {
+          if (static_cast<int64_t>(e) >= a.max_jumps) {
+            finish(1, false);
+          } else {
+            const uint4 x = keys.draw(make_uint4(c_lo, row32, e, c_hi));
+            if (!jump(s_pend, x.z, x.w)) {
+              finish(2, false);
+            } else {
+              s_pend = P::add(s, P::mul(neglog32(uniform32(x.x)), static_cast<T>(m.inv_rate)));
+              if (!(s_pend < static_cast<T>(1))) finish(0, false);
+            }
+          }
         }
       }
     } else {
@@ -869,28 +900,49 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
         if (k < span) {
           start_walk(k);
           live = true;
+          fresh = true;
         }
       }
       claimed = min(claimed + static_cast<uint32_t>(__popc(idle)), span);
       if (!__any_sync(kFull, live)) break;  // every walk of the item done
       if (live) {
-        uint4 x = keys.draw(make_uint4(c_lo, row32, e, c_hi));
-        if (!FP64 && group_first && e == 0) {
-          // the first uniform from word (rep mod 4) of the group's block
-          const uint64_t rep = rep_base + r;
-          const uint64_t g = rep >> 2;
-          const uint4 xg = keys.draw(make_uint4(static_cast<uint32_t>(g), row32, 0xFFFFFFFEu,
-                                                a.ctr3 | (static_cast<uint32_t>(g >> 32) << 8)));
-          const uint32_t k = static_cast<uint32_t>(rep & 3u);
-          x.x = k == 0 ? xg.x : (k == 1 ? xg.y : (k == 2 ? xg.z : xg.w));
-        }
-        const T s_new = P::add(s, P::mul(P::neglog(P::uniform(x)), static_cast<T>(m.inv_rate)));
-        if (!(s_new < static_cast<T>(1))) {
-          finish(0, true);
-        } else if (static_cast<int64_t>(e) >= a.max_jumps) {
-          finish(1, true);
-        } else if (!jump(s_new, x.z, x.w)) {
-          finish(2, true);
+        const uint4 x = keys.draw(make_uint4(c_lo, row32, e, c_hi));
+        if constexpr (FP64) {
+          const T s_new = P::add(s, P::mul(P::neglog(P::uniform(x)), static_cast<T>(m.inv_rate)));
+          if (!(s_new < static_cast<T>(1))) {
+            finish(0, true);
+          } else if (static_cast<int64_t>(e) >= a.max_jumps) {
+            finish(1, true);
+          } else if (!jump(s_new, x.z, x.w)) {
+            finish(2, true);
+          }
+        } else {
+          // Draw e gives the pending jump (words 2, 3) and the holding time
+          // after it (word 0); a fresh walk first draws its first holding
+          // time from word 1 (or from its group's block word).
+          if (fresh) {
+            uint32_t w = x.y;
+            if (group_first) {
+              const uint64_t rep = rep_base + r;
+              const uint64_t g = rep >> 2;
+              const uint4 xg = keys.draw(make_uint4(static_cast<uint32_t>(g), row32, 0xFFFFFFFEu,
+                                                    a.ctr3 | (static_cast<uint32_t>(g >> 32) << 8)));
+              const uint32_t k = static_cast<uint32_t>(rep & 3u);
+              w = k == 0 ? xg.x : (k == 1 ? xg.y : (k == 2 ? xg.z : xg.w));
+            }
+            s_pend = P::add(s, P::mul(neglog32(uniform32(w)), static_cast<T>(m.inv_rate)));
+            fresh = false;
+          }
+          if (!(s_pend < static_cast<T>(1))) {
+            finish(0, true);  // never jumped
+          } else if (static_cast<int64_t>(e) >= a.max_jumps) {
+            finish(1, true);
+          } else if (!jump(s_pend, x.z, x.w)) {
+            finish(2, true);
+          } else {
+            s_pend = P::add(s, P::mul(neglog32(uniform32(x.x)), static_cast<T>(m.inv_rate)));
+            if (!(s_pend < static_cast<T>(1))) finish(0, true);
+          }
         }
       }
       settle_ends(false);
@@ -1149,6 +1201,10 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk_fwd(const __grid_con
     int kprev = -1;
     int32_t start = 0;
     uint32_t hash = 2166136261u;
+    // FP32: the next jump time, drawn with the previous jump (word 0) or,
+    // for a fresh walk, from word 1 of draw 0.
+    T s_pend = 0;
+    bool fresh = false;
     auto begin_walk = [&]() {
       g = static_cast<uint64_t>(a.walk_begin + w_lo + r);
       const uint4 x = philox4x32_10(make_uint4(static_cast<uint32_t>(g), static_cast<uint32_t>(g >> 32),
@@ -1174,6 +1230,7 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk_fwd(const __grid_con
       lw = 0;
       kprev = -1;
       hash = 2166136261u;
+      fresh = true;
     };
     if (live) begin_walk();
     while (__any_sync(kFull, live)) {
@@ -1182,8 +1239,19 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk_fwd(const __grid_con
       if (live) {
         const uint4 x = philox4x32_10(
             make_uint4(static_cast<uint32_t>(g), static_cast<uint32_t>(g >> 32), e, a.ctr3), a.rk);
-        const T hold = P::mul(P::neglog(P::uniform(x)), static_cast<T>(m.inv_rate));
-        const T s_new = P::add(s, hold);
+        T s_new;
+        if constexpr (FP64) {
+          // draw e: the holding time (words 0, 1) and the jump after it
+          s_new = P::add(s, P::mul(P::neglog(P::uniform(x)), static_cast<T>(m.inv_rate)));
+        } else {
+          // draw e: the pending jump (words 2, 3) and the holding time after
+          // it (word 0); a fresh walk's first holding time is word 1
+          if (fresh) {
+            s_pend = P::add(s, P::mul(neglog32(uniform32(x.y)), static_cast<T>(m.inv_rate)));
+            fresh = false;
+          }
+          s_new = s_pend;
+        }
         bool done = !(s_new < static_cast<T>(1));
         int status = 0;
         if (!done && static_cast<int64_t>(e) >= a.max_jumps) {
@@ -1247,7 +1315,12 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk_fwd(const __grid_con
           m = IS ? load_meta(meta, j) : mnext;
           s = s_new;
           ++e;
-        } else {
+          if constexpr (!FP64) {
+            s_pend = P::add(s, P::mul(neglog32(uniform32(x.x)), static_cast<T>(m.inv_rate)));
+            done = !(s_pend < static_cast<T>(1));
+          }
+        }
+        if (done) {
           fin = true;
           if (status == 0) {
             const T dle = static_cast<T>(m.dl);
