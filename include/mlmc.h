@@ -319,27 +319,29 @@ typedef struct mlmc_batch mlmc_batch;
  * stream: mlmc_batch_expmv orders its work after work queued there.
  * Creation runs the launch-shape autotuner (walks per lane of a work item,
  * per problem-size bucket n < 1e4, < 1e5, >= 1e5; a few short walk
- * launches) and captures the CUDA graph of one controller round. */
+ * launches) and captures the CUDA graph of one round's reductions. */
 mlmc_status mlmc_batch_create(mlmc_batch **out, mlmc_plan *const *plans, int32_t count,
                               const mlmc_schedule *sched, double rel_tol, void *cuda_stream);
 
 /* x_k = exp(t_k A_k) v_k for every problem k, by Algorithm 1 run for all
- * problems in lockstep rounds; each round is one graph launch (all walks of
- * the round in one persistent kernel, then the batched reductions) and one
- * synchronisation.  v[k], x[k]: host or device pointers to n_k doubles;
- * seeds[k]: Philox key of problem k.  Returns NOT_CONVERGED if any problem
- * stopped on a budget (every x is still written). */
+ * problems in lockstep rounds.  A round launches the walk kernel once per
+ * (problem, level, replica range) segment, spread over the batch's streams
+ * so that small problems run side by side, then one graph launch does the
+ * batched reductions, and the host synchronises once.  v[k], x[k]: host or
+ * device pointers to n_k doubles; seeds[k]: Philox key of problem k (the
+ * walks are those a single-plan solve with that seed draws).  Returns
+ * NOT_CONVERGED if any problem stopped on a budget (every x is still
+ * written). */
 mlmc_status mlmc_batch_expmv(mlmc_batch *batch, const double *const *v, double *const *x,
                              const uint64_t *seeds);
 
 /* Per-level statistics of problem `problem` after mlmc_batch_expmv (as
- * mlmc_stats; seconds and launches are 0: walks of all problems share
- * launches). */
+ * mlmc_stats; seconds is 0: the launches of different problems overlap). */
 mlmc_status mlmc_batch_stats(const mlmc_batch *batch, int32_t problem, mlmc_level_stats *out,
                              int32_t cap, int32_t *n_levels, double *est_rel_err);
 
-/* Rounds (graph launches), GPU seconds of the rounds and number of converged
- * problems of the last mlmc_batch_expmv; any pointer may be NULL. */
+/* Rounds, GPU seconds of the rounds and number of converged problems of the
+ * last mlmc_batch_expmv; any pointer may be NULL. */
 mlmc_status mlmc_batch_info(const mlmc_batch *batch, int64_t *rounds, double *gpu_seconds,
                             int32_t *converged);
 

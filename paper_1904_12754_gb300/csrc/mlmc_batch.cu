@@ -2,22 +2,24 @@
 // of different sizes, several right-hand sides per plan) solved together.
 //
 // The controller of Algorithm 1 runs for every problem in lockstep rounds.
-// A round is one CUDA graph, captured once when the batch is created:
-//   H2D  segment table + reduction tasks (pinned host buffer, fixed size)
-//   memset of the work counter
-//   k_walk_batch: one persistent launch over every (problem, level, replica
-//                 range) segment of the round
+// A round launches, for every (problem, level, replica range) segment, the
+// plan's own walk kernel (the single-plan launch sequence, with the problem's
+// Philox round keys as a launch constant and the screened path for short
+// walks) on one of kStreams streams, so that the segments of small problems
+// run side by side; then, after the streams join, one captured graph does
+//   H2D  reduction tasks (pinned host buffer, fixed size)
 //   k_batch_reduce: sum_i S_l,i^2 for every active (problem, level) and
 //                 ||x||^2 for every active problem
 //   D2H  per-(problem, level) totals and per-problem norms (pinned)
-// so a round costs one graph launch and one synchronisation whatever the
-// number of problems.  Between rounds the host applies each problem's
-// sample-size rule (the same readings as the single-plan controller) and
-// writes the next segment table.
+// and the host synchronises once.  Between rounds the host applies each
+// problem's sample-size rule (the same readings as the single-plan
+// controller) and forms the next segments.  A segment costs one kernel
+// launch (a few microseconds of host time), so a round of thousands of
+// segments is still far shorter than its walks.
 //
 // Launch shape: walks per lane of a work item (the item is 32 x that many
 // walks of one row) is picked per problem-size bucket by a short timing
-// trial at batch creation (autotuner); blocks are 256 threads.
+// trial at batch creation (autotuner); blocks are the plans' block size.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -34,6 +36,8 @@ constexpr int kRedBlock = 256;
 constexpr int kBuckets = 3;  // n < 1e4, 1e4 <= n < 1e5, n >= 1e5
 constexpr int64_t kRoundWalks = int64_t{1} << 35;  // walks per round, at most
 
+constexpr int kStreams = 8;  // streams the segments of a round are spread over
+
 struct ReduceTask {
   const double* vec;    // level sums S (sumsq task) or unused (norm task)
   double* out;          // where the result goes
@@ -42,8 +46,13 @@ struct ReduceTask {
   int32_t pad;
 };
 
+// What the reduction kernels read of a problem: its per-level row sums.
+struct BatchProblemDev {
+  double* sums;         // [max_levels][n] per-level row sums of Y
+  int64_t n;
+};
+
 struct BatchTables {
-  BatchHeaderDev hdr;
   int32_t ntasks;
   int32_t pad;
 };
@@ -131,7 +140,7 @@ struct ProblemState {
   bool done = false;
   bool converged = false;
   std::vector<int64_t> reps;      // per slot
-  std::vector<double> seconds;
+  std::vector<int64_t> launches;  // per slot
   double est_rel_err = 0.0;
 };
 
@@ -149,8 +158,11 @@ struct mlmc_batch {
   bool fp64 = false;
   int num_sms = 0;
   int device = 0;
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;   // controller stream: copies, reductions, graph
   cudaStream_t caller = nullptr;
+  cudaStream_t seg_streams[kStreams] = {};  // the rounds' walk launches
+  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_join[kStreams] = {};
   std::vector<int64_t> n;          // per problem
   std::vector<int64_t> offset;     // row offset of each problem in the contiguous buffers
   int64_t total_rows = 0;
@@ -165,19 +177,20 @@ struct mlmc_batch {
   float* d_v32 = nullptr;          // total_rows
   double* d_x = nullptr;           // total_rows
   double** d_xptr = nullptr;       // nprob pointers into d_x
-  unsigned long long* d_work = nullptr;
+  unsigned long long* d_work = nullptr;  // one work counter per segment stream
   uint32_t* d_flags = nullptr;
-  // Round table (device + pinned host mirror): [BatchTables][segments][tasks][inv_m]
+  // Round table (device + pinned host mirror): [BatchTables][tasks][inv_m]
   unsigned char* d_tab = nullptr;
   unsigned char* h_tab = nullptr;
-  size_t tab_bytes = 0, off_segs = 0, off_tasks = 0, off_invm = 0;
-  int max_segs = 0, max_tasks = 0;
+  size_t tab_bytes = 0, off_tasks = 0, off_invm = 0;
+  int max_tasks = 0;
   double* h_totals = nullptr;      // pinned
   double* h_norm = nullptr;        // pinned
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   int64_t rounds = 0;
+  int64_t launches = 0;            // walk launches of the last mlmc_batch_expmv
   std::vector<ProblemState> state;
   double last_seconds = 0.0;
 };
@@ -204,28 +217,27 @@ void free_batch(mlmc_batch* b) {
   if (b->h_norm) cudaFreeHost(b->h_norm);
   if (b->ev0) cudaEventDestroy(b->ev0);
   if (b->ev1) cudaEventDestroy(b->ev1);
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  for (int i = 0; i < kStreams; ++i) {
+    if (b->ev_join[i]) cudaEventDestroy(b->ev_join[i]);
+    if (b->seg_streams[i]) cudaStreamDestroy(b->seg_streams[i]);
+  }
   if (b->stream) cudaStreamDestroy(b->stream);
   delete b;
 }
 
 BatchTables* tab_hdr(mlmc_batch* b) { return reinterpret_cast<BatchTables*>(b->h_tab); }
-BatchSegmentDev* tab_segs(mlmc_batch* b) {
-  return reinterpret_cast<BatchSegmentDev*>(b->h_tab + b->off_segs);
-}
 ReduceTask* tab_tasks(mlmc_batch* b) { return reinterpret_cast<ReduceTask*>(b->h_tab + b->off_tasks); }
 double* tab_invm(mlmc_batch* b) { return reinterpret_cast<double*>(b->h_tab + b->off_invm); }
 
+// The graph of a round's reductions: upload the task table, reduce, read the
+// totals and norms back.
 mlmc_status capture_round_graph(mlmc_batch* b) {
   const BatchTables* dt = reinterpret_cast<const BatchTables*>(b->d_tab);
-  const BatchSegmentDev* dsegs = reinterpret_cast<const BatchSegmentDev*>(b->d_tab + b->off_segs);
   const ReduceTask* dtasks = reinterpret_cast<const ReduceTask*>(b->d_tab + b->off_tasks);
   const double* dinvm = reinterpret_cast<const double*>(b->d_tab + b->off_invm);
   BATCH_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
   cudaError_t err = cudaMemcpyAsync(b->d_tab, b->h_tab, b->tab_bytes, cudaMemcpyHostToDevice, b->stream);
-  if (err == cudaSuccess) err = cudaMemsetAsync(b->d_work, 0, sizeof(unsigned long long), b->stream);
-  if (err == cudaSuccess)
-    err = launch_walk_batch(b->fp64, b->d_probs, &dt->hdr, dsegs, b->d_work, b->d_flags, b->num_sms,
-                            256, b->stream);
   if (err == cudaSuccess) {
     k_batch_reduce<<<b->num_sms * 8, kRedBlock, 0, b->stream>>>(dt, dtasks, b->d_probs, dinvm,
                                                                   b->max_levels);
@@ -331,6 +343,11 @@ mlmc_status mlmc_batch_create(mlmc_batch** out, mlmc_plan* const* plans, int32_t
   BC(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking), "stream");
   BC(cudaEventCreate(&b->ev0), "event");
   BC(cudaEventCreate(&b->ev1), "event");
+  BC(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming), "event");
+  for (int i = 0; i < kStreams; ++i) {
+    BC(cudaStreamCreateWithFlags(&b->seg_streams[i], cudaStreamNonBlocking), "stream");
+    BC(cudaEventCreateWithFlags(&b->ev_join[i], cudaEventDisableTiming), "event");
+  }
   const int64_t L = b->max_levels;
   BC(cudaMalloc(&b->d_probs, sizeof(BatchProblemDev) * count), "alloc");
   BC(cudaMalloc(&b->d_sums, sizeof(double) * b->total_rows * L), "alloc sums");
@@ -340,12 +357,10 @@ mlmc_status mlmc_batch_create(mlmc_batch** out, mlmc_plan* const* plans, int32_t
   BC(cudaMalloc(&b->d_v32, sizeof(float) * b->total_rows), "alloc");
   BC(cudaMalloc(&b->d_x, sizeof(double) * b->total_rows), "alloc");
   BC(cudaMalloc(&b->d_xptr, sizeof(double*) * count), "alloc");
-  BC(cudaMalloc(&b->d_work, sizeof(unsigned long long)), "alloc");
+  BC(cudaMalloc(&b->d_work, sizeof(unsigned long long) * kStreams), "alloc");
   BC(cudaMalloc(&b->d_flags, sizeof(uint32_t) * 4), "alloc");
-  b->max_segs = static_cast<int>(count * L);
   b->max_tasks = static_cast<int>(count * L + count);
-  b->off_segs = 256;
-  b->off_tasks = b->off_segs + ((sizeof(BatchSegmentDev) * b->max_segs + 255) / 256) * 256;
+  b->off_tasks = 256;
   b->off_invm = b->off_tasks + ((sizeof(ReduceTask) * b->max_tasks + 255) / 256) * 256;
   b->tab_bytes = b->off_invm + sizeof(double) * count * L;
   BC(cudaMalloc(&b->d_tab, b->tab_bytes), "alloc table");
@@ -356,20 +371,8 @@ mlmc_status mlmc_batch_create(mlmc_batch** out, mlmc_plan* const* plans, int32_t
   std::vector<BatchProblemDev> probs(count);
   std::vector<double*> xptr(count);
   for (int k = 0; k < count; ++k) {
-    mlmc_plan* p = plans[k];
-    BatchProblemDev& d = probs[k];
-    d.meta = b->fp64 ? static_cast<const void*>(p->d_meta64) : static_cast<const void*>(p->d_meta32);
-    d.alias = p->d_fused;
-    d.v_walk = b->fp64 ? static_cast<const void*>(b->d_v + b->offset[k])
-                       : static_cast<const void*>(b->d_v32 + b->offset[k]);
-    d.sums = b->d_sums + b->offset[k] * L;
-    d.totals = b->d_totals + static_cast<int64_t>(k) * L * kTotSlots;
-    d.n = p->n;
-    d.nnz = p->nnz;
-    d.max_jumps = b->sched.max_jumps_per_walk;
-    d.l0 = p->l0;
-    d.key0 = d.key1 = 0;
-    d.pad = 0;
+    probs[k].sums = b->d_sums + b->offset[k] * L;
+    probs[k].n = b->n[k];
     xptr[k] = b->d_x + b->offset[k];
   }
   BC(cudaMemcpy(b->d_probs, probs.data(), sizeof(BatchProblemDev) * count, cudaMemcpyHostToDevice),
@@ -439,63 +442,74 @@ mlmc_status mlmc_batch_expmv(mlmc_batch* b, const double* const* v, double* cons
   BATCH_CUDA(cudaMemsetAsync(b->d_sums, 0, sizeof(double) * b->total_rows * L, b->stream), "memset");
   BATCH_CUDA(cudaMemsetAsync(b->d_totals, 0, sizeof(double) * K * L * kTotSlots, b->stream), "memset");
   BATCH_CUDA(cudaMemsetAsync(b->d_flags, 0, sizeof(uint32_t) * 4, b->stream), "memset");
-  // Per-problem Philox keys.
-  std::vector<BatchProblemDev> probs(K);
-  BATCH_CUDA(cudaMemcpyAsync(probs.data(), b->d_probs, sizeof(BatchProblemDev) * K,
-                             cudaMemcpyDeviceToHost, b->stream), "read problems");
-  BATCH_CUDA(cudaStreamSynchronize(b->stream), "sync");
-  for (int k = 0; k < K; ++k) {
-    probs[k].key0 = static_cast<uint32_t>(seeds[k] & 0xFFFFFFFFull);
-    probs[k].key1 = static_cast<uint32_t>(seeds[k] >> 32);
-  }
-  BATCH_CUDA(cudaMemcpyAsync(b->d_probs, probs.data(), sizeof(BatchProblemDev) * K,
-                             cudaMemcpyHostToDevice, b->stream), "write problems");
   b->state.assign(K, ProblemState());
   for (auto& s : b->state) {
     s.nl = b->sched.num_levels;
     s.reps.assign(L, 0);
-    s.seconds.assign(L, 0.0);
+    s.launches.assign(L, 0);
   }
   // Pending work per (problem, slot): walks per row still to launch.
   std::vector<int64_t> want(K * L, 0);
   for (int k = 0; k < K; ++k)
     for (int l = 0; l < b->sched.num_levels; ++l) want[k * L + l] = b->sched.pilot_walks;
   b->rounds = 0;
+  b->launches = 0;
   double gpu_s = 0.0;
   bool out_of_time = false;
   for (;;) {
-    // Build the round: segments (bounded walks per round) and reduction tasks.
-    BatchTables* th = tab_hdr(b);
-    BatchSegmentDev* segs = tab_segs(b);
-    ReduceTask* tasks = tab_tasks(b);
-    double* invm = tab_invm(b);
-    int nseg = 0, ntask = 0;
-    unsigned long long items = 0;
+    NvtxRange range("mlmc batch round");
+    // The round's walks: segments of bounded total size, each launched on
+    // one of the segment streams after the work queued so far.
+    BATCH_CUDA(cudaEventRecord(b->ev0, b->stream), "event");
+    BATCH_CUDA(cudaEventRecord(b->ev_fork, b->stream), "event");
+    for (int i = 0; i < kStreams; ++i)
+      BATCH_CUDA(cudaStreamWaitEvent(b->seg_streams[i], b->ev_fork, 0), "wait");
+    int nseg = 0;
     int64_t walks = 0;
     for (int k = 0; k < K; ++k) {
       ProblemState& s = b->state[k];
       if (s.done) continue;
+      mlmc_plan* p = b->plans[k];
       for (int l = 0; l < s.nl; ++l) {
         int64_t reps = want[k * L + l];
         if (reps <= 0) continue;
         if (walks >= kRoundWalks) break;
         const int64_t room = std::max<int64_t>(1, (kRoundWalks - walks) / b->n[k]);
         reps = std::min(reps, room);
-        BatchSegmentDev& g = segs[nseg++];
-        g.problem = k;
-        g.slot = l;
-        g.rep_begin = s.reps[l];
-        g.reps = reps;
-        const int64_t per_lane = std::min<int64_t>(b->per_lane[bucket_of(b->n[k])], (reps + 31) / 32);
-        g.chunk = 32 * std::max<int64_t>(1, per_lane);
-        g.chunks_per_row = (reps + g.chunk - 1) / g.chunk;
-        g.item_begin = items;
-        items += static_cast<unsigned long long>(b->n[k]) * g.chunks_per_row;
+        WalkLaunch w;
+        w.level = p->l0 + l;
+        w.coarse = l > 0;
+        w.rep_begin = s.reps[l];
+        w.reps = reps;
+        w.seed = seeds[k];
+        w.sum_y = b->d_sums + b->offset[k] * L + static_cast<int64_t>(l) * b->n[k];
+        w.totals = b->d_totals + (static_cast<int64_t>(k) * L + l) * kTotSlots;
+        const void* v_walk = b->fp64 ? static_cast<const void*>(b->d_v + b->offset[k])
+                                     : static_cast<const void*>(b->d_v32 + b->offset[k]);
+        const int64_t per_lane =
+            std::max<int64_t>(1, std::min<int64_t>(b->per_lane[bucket_of(b->n[k])], (reps + 31) / 32));
+        const int si = nseg % kStreams;
+        int64_t nl = 0;
+        BATCH_CUDA(launch_walk_segment(p, w, v_walk, per_lane, b->d_work + si, b->d_flags,
+                                       b->seg_streams[si], &nl),
+                   "walk launch");
+        s.launches[l] += nl;
+        b->launches += nl;
+        ++nseg;
         walks += reps * b->n[k];
         want[k * L + l] -= reps;
         s.reps[l] += reps;
       }
     }
+    for (int i = 0; i < kStreams; ++i) {
+      BATCH_CUDA(cudaEventRecord(b->ev_join[i], b->seg_streams[i]), "event");
+      BATCH_CUDA(cudaStreamWaitEvent(b->stream, b->ev_join[i], 0), "wait");
+    }
+    // Reduction tasks of every active problem.
+    BatchTables* th = tab_hdr(b);
+    ReduceTask* tasks = tab_tasks(b);
+    double* invm = tab_invm(b);
+    int ntask = 0;
     for (int k = 0; k < K; ++k) {
       ProblemState& s = b->state[k];
       for (int l = 0; l < L; ++l)
@@ -503,7 +517,7 @@ mlmc_status mlmc_batch_expmv(mlmc_batch* b, const double* const* v, double* cons
       if (s.done) continue;
       for (int l = 0; l < s.nl; ++l) {
         ReduceTask& t = tasks[ntask++];
-        t.vec = probs[k].sums + static_cast<int64_t>(l) * b->n[k];
+        t.vec = b->d_sums + b->offset[k] * L + static_cast<int64_t>(l) * b->n[k];
         t.out = b->d_totals + (static_cast<int64_t>(k) * L + l) * kTotSlots + kTotSumSq;
         t.n = b->n[k];
         t.problem = -1;
@@ -515,11 +529,7 @@ mlmc_status mlmc_batch_expmv(mlmc_batch* b, const double* const* v, double* cons
       t.problem = k;
     }
     if (nseg == 0 && ntask == 0) break;
-    th->hdr.total_items = items;
-    th->hdr.segments = nseg;
     th->ntasks = ntask;
-    NvtxRange range("mlmc batch round");
-    BATCH_CUDA(cudaEventRecord(b->ev0, b->stream), "event");
     BATCH_CUDA(cudaGraphLaunch(b->exec, b->stream), "graph launch");
     BATCH_CUDA(cudaEventRecord(b->ev1, b->stream), "event");
     BATCH_CUDA(cudaStreamSynchronize(b->stream), "sync");
@@ -619,6 +629,7 @@ mlmc_status mlmc_batch_expmv(mlmc_batch* b, const double* const* v, double* cons
     b->last_seconds = gpu_s;
     if (flags & kFlagWalkLimit) return bfail(MLMC_ERR_WALK_LIMIT, "batch: a walk exceeded max_jumps_per_walk");
     if (flags & kFlagNonFiniteY) return bfail(MLMC_ERR_NUMERIC, "batch: non-finite walk weight");
+    if (flags & kFlagBounds) return bfail(MLMC_ERR_NUMERIC, "batch: table index out of range");
   }
   for (auto& s : b->state)
     if (!s.converged) return bfail(MLMC_ERR_NOT_CONVERGED, "batch: budget exhausted before the tolerance");
@@ -643,7 +654,7 @@ mlmc_status mlmc_batch_stats(const mlmc_batch* b, int32_t problem, mlmc_level_st
     ls.cost_events_per_walk = t[kTotWalks] > 0 ? 1.0 + t[kTotJumps] / t[kTotWalks] : 1.0;
     ls.jumps = static_cast<int64_t>(t[kTotJumps]);
     ls.seconds = 0.0;
-    ls.launches = 0;
+    ls.launches = s.launches[l];
     ls.still_walks = static_cast<int64_t>(t[kTotStill]);
     out[l] = ls;
   }

@@ -53,44 +53,6 @@ struct WalkLaunch {
   mlmc_walk_record* trace = nullptr;  // non-null selects the recording kernel
 };
 
-// Batched walks (mlmc_batch.cu drives them; the kernel is in mlmc_walk.cu).
-// One problem = one plan's tables with one right-hand side.
-struct BatchProblemDev {
-  const void* meta;       // Meta32 or Meta64 records of the problem's plan
-  const void* alias;      // FusedEntry32 or FusedEntry64 entries of the plan
-  const void* v_walk;     // right-hand side in the walk precision
-  double* sums;           // [max_levels][n] per-level row sums of Y
-  double* totals;         // [max_levels][kTotSlots]
-  int64_t n;
-  int64_t nnz;
-  int64_t max_jumps;
-  int32_t l0;
-  uint32_t key0, key1;
-  int32_t pad;
-};
-
-// A contiguous replica range of one (problem, level slot): items
-// item_begin .. item_begin + n * chunks_per_row - 1 of the launch.
-struct BatchSegmentDev {
-  int32_t problem;
-  int32_t slot;
-  int64_t rep_begin;
-  int64_t reps;
-  int64_t chunk;
-  int64_t chunks_per_row;
-  unsigned long long item_begin;
-};
-
-struct BatchHeaderDev {
-  unsigned long long total_items;
-  int32_t segments;
-  int32_t pad;
-};
-
-cudaError_t launch_walk_batch(bool fp64, const BatchProblemDev* probs, const BatchHeaderDev* hdr,
-                              const BatchSegmentDev* segs, unsigned long long* work,
-                              uint32_t* flags, int num_sms, int block, cudaStream_t stream);
-
 }  // namespace mlmc
 
 struct mlmc_plan {
@@ -213,6 +175,13 @@ cudaError_t launch_start_guide(mlmc_plan* p, const int64_t* cdf, unsigned long l
 // device memory instead of the plan's buffers.
 cudaError_t launch_walk_scratch(mlmc_plan* p, const WalkLaunch& w, unsigned long long* work,
                                 float* v32, int64_t* launches = nullptr);
+// One segment of a batch round: launch_walk's launches with v already in the
+// walk precision (v_walk), on `stream`, with their own work counter and flags
+// word; per_lane > 0 fixes the walks per lane of an item.  Plans with a source
+// term are refused (cudaErrorInvalidValue).
+cudaError_t launch_walk_segment(mlmc_plan* p, const WalkLaunch& w, const void* v_walk,
+                                int64_t per_lane, unsigned long long* work, uint32_t* flags,
+                                cudaStream_t stream, int64_t* launches = nullptr);
 
 // Reductions (mlmc_reduce.cu).
 // out[0] += sum_i a_i, out[1] += sum_i a_i^2 (out must be zeroed by the caller).

@@ -84,16 +84,11 @@ struct WalkArgs {
   double t;                // the time t (source walks only)
 };
 
-// Key sources of the walk's draws: the round keys of a launch-constant
-// parameter (single-plan launches), or formed from the key on the fly (the
-// batch kernel, whose key changes with the problem).
+// Key source of the walk's draws: the round keys of a launch-constant
+// parameter, so that every round's key add is an operand of the constant bank.
 struct KeysFromParam {
   const PhiloxRoundKeys* rk;
   __device__ __forceinline__ uint4 draw(uint4 c) const { return philox4x32_10(c, *rk); }
-};
-struct KeysOnTheFly {
-  uint32_t k0, k1;
-  __device__ __forceinline__ uint4 draw(uint4 c) const { return philox4x32_10(c, k0, k1); }
 };
 
 template <bool FP64>
@@ -443,8 +438,7 @@ __device__ __forceinline__ int32_t still_index32(float inv_rate, int lane) {
 // counter, so the trajectories are those of the walk-by-walk definition.
 // Adds the item's sum of Y to a.sum_y[row] (one atomic) and its totals to
 // `tot`.
-template <bool FP64, bool COARSE, bool TRACE, bool IS, class Keys, bool kScreen = true,
-          bool SRC = false>
+template <bool FP64, bool COARSE, bool TRACE, bool IS, class Keys, bool SRC = false>
 __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, int64_t row,
                                           int64_t r_lo, int64_t r_hi,
                                           LaneTotals<typename Prec<FP64>::T>& tot,
@@ -468,7 +462,7 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
   // (t L_row <= 1: few events per walk, the first jump and the end usually
   // fall in the same iteration); one wave without screening for the others.
   constexpr int kWays = 2;
-  const bool two_wave = kScreen && static_cast<T>(m0.inv_rate) >= static_cast<T>(1);
+  const bool two_wave = static_cast<T>(m0.inv_rate) >= static_cast<T>(1);
   const int32_t still_max =
       (FP64 || !two_wave) ? 0 : still_index32(static_cast<float>(m0.inv_rate), lane);
   // A walk that never jumps stays at the row for the whole interval: its
@@ -501,7 +495,7 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
 
   Kahan<T> acc_y;
   uint32_t item_jumps = 0;  // this lane's jumps in this item (< 2^32)
-  uint32_t n_still = 0;     // walks without a jump screened by this lane
+  uint32_t n_still = 0;     // walks of one-wave rows that ended without a jump
   uint32_t n_limit = 0;     // this lane's walks stopped at the jump limit
   const uint32_t row32 = static_cast<uint32_t>(row);
   const uint32_t span = static_cast<uint32_t>(r_hi - r_lo);
@@ -741,9 +735,6 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
   // item's replica range [rep_base, rep_base + span).
   uint64_t gnext = rep_base >> 2;
   const uint64_t g_end = (rep_base + span + 3) >> 2;
-  // FP32 rows with 1/(t L) >= 1 take a walk's first uniform from its group's
-  // block (the walks the one-wave path runs in such rows, too).
-  const bool group_first = !FP64 && static_cast<float>(m0.inv_rate) >= 1.0f;
 
   for (;;) {
     if (two_wave) {
@@ -767,10 +758,7 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
             const uint32_t rs = screened + static_cast<uint32_t>(32 * w + lane);
             h1[w] = P::mul(P::neglog(P::uniform(x[w])), inv_rate0);
             push[w] = rs < span && h1[w] < static_cast<T>(1);
-            if (rs < span && !push[w]) {
-              ++n_still;
-              if (TRACE) trace_still(rs);
-            }
+            if (TRACE && rs < span && !push[w]) trace_still(rs);
             const unsigned pm = __ballot_sync(kFull, push[w]);
             if (push[w]) {
               const uint32_t slot = (qtail + static_cast<uint32_t>(__popc(pm & lanes_below))) & (kCap - 1);
@@ -803,10 +791,7 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
             const bool valid = rs < span;
             const uint32_t word = k == 0 ? xg.x : (k == 1 ? xg.y : (k == 2 ? xg.z : xg.w));
             const bool push = valid && static_cast<int32_t>(word >> 9) > still_max;
-            if (valid && !push) {
-              ++n_still;
-              if (TRACE) trace_still(rs);
-            }
+            if (TRACE && valid && !push) trace_still(rs);
             const unsigned pm = __ballot_sync(kFull, push);
             if (push) {
               const uint32_t slot = (qtail + static_cast<uint32_t>(__popc(pm & lanes_below))) & (kCap - 1);
@@ -919,18 +904,9 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
         } else {
           // Draw e gives the pending jump (words 2, 3) and the holding time
           // after it (word 0); a fresh walk first draws its first holding
-          // time from word 1 (or from its group's block word).
+          // time from word 1 (rows with 1/(tL) < 1: no shared block word).
           if (fresh) {
-            uint32_t w = x.y;
-            if (group_first) {
-              const uint64_t rep = rep_base + r;
-              const uint64_t g = rep >> 2;
-              const uint4 xg = keys.draw(make_uint4(static_cast<uint32_t>(g), row32, 0xFFFFFFFEu,
-                                                    a.ctr3 | (static_cast<uint32_t>(g >> 32) << 8)));
-              const uint32_t k = static_cast<uint32_t>(rep & 3u);
-              w = k == 0 ? xg.x : (k == 1 ? xg.y : (k == 2 ? xg.z : xg.w));
-            }
-            s_pend = P::add(s, P::mul(neglog32(uniform32(w)), static_cast<T>(m.inv_rate)));
+            s_pend = P::add(s, P::mul(neglog32(uniform32(x.y)), static_cast<T>(m.inv_rate)));
             fresh = false;
           }
           if (!(s_pend < static_cast<T>(1))) {
@@ -951,7 +927,10 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
   settle_ends(true);
   double ys = warp_sum(acc_y);
   const unsigned long long jumps = warp_sum_u64(item_jumps);
-  const unsigned long long still = warp_sum_u64(n_still);
+  // Screened rows: every screened walk that was not queued never jumps
+  // (qtail counts the queued ones); other rows count them as they end.
+  const unsigned long long still =
+      warp_sum_u64(n_still) + (two_wave ? static_cast<unsigned long long>(span - qtail) : 0ull);
   const unsigned long long limit = warp_sum_u64(n_limit);
   // Walks that never jump: y_still each (0 above l0 unless a source term
   // adds its fixed Simpson part).
@@ -1007,128 +986,11 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk(const __grid_constan
     const int64_t chunk = static_cast<int64_t>(item) - rel * a.chunks_per_row;
     const int64_t r_lo = chunk * a.chunk;
     const int64_t r_hi = min(r_lo + a.chunk, a.reps);
-    walk_item<FP64, COARSE, TRACE, IS, KeysFromParam, true, SRC>(ia, KeysFromParam{&a.rk},
+    walk_item<FP64, COARSE, TRACE, IS, KeysFromParam, SRC>(ia, KeysFromParam{&a.rk},
                                                                 a.row_begin + rel, r_lo, r_hi,
                                        tot, wc, q, eq, lane);
   }
   flush_warp(tot, wc, a.totals, a.flags, lane);
-}
-
-// Batched walks: the items of many (problem, level, replica range) segments
-// in one persistent launch.  A warp maps its item to a segment by binary
-// search over the segments' first items, then runs the same per-item walk as
-// k_walk with that problem's tables and adds its totals to the problem's
-// level totals.
-// Per-warp copy of the current segment's walk parameters (shared memory, so
-// that they are not held in registers across the walk loop).
-struct BatchWarpState {
-  ItemArgs ia;
-  double* totals;          // the segment's level totals
-  int64_t n;               // rows of the segment's problem
-  int64_t reps;            // replicas of the segment
-  int64_t chunk;           // walks per item
-  int64_t chunks_per_row;
-  int32_t slot;            // level slot (0 = l0, coarse above)
-  uint32_t key0, key1;
-};
-
-template <bool FP64>
-__global__ void __launch_bounds__(256, FP64 ? 3 : 4)
-    k_walk_batch(const BatchProblemDev* __restrict__ probs, const BatchHeaderDev* __restrict__ hdr,
-                 const BatchSegmentDev* __restrict__ segs, unsigned long long* __restrict__ work,
-                 uint32_t* __restrict__ flags) {
-  using T = typename Prec<FP64>::T;
-  const int lane = threadIdx.x & 31;
-  const unsigned long long total = hdr->total_items;
-  const int nseg = hdr->segments;
-  __shared__ BatchWarpState states[kMaxWarps];
-  __shared__ WarpCounters counters[kMaxWarps];
-  __shared__ EndQueue<FP64> ends[kMaxWarps];
-  WarpQueue<FP64>* q = nullptr;  // no screening in this kernel
-  EndQueue<FP64>* eq = &ends[threadIdx.x >> 5];
-  BatchWarpState& st = states[threadIdx.x >> 5];
-  WarpCounters* wc = &counters[threadIdx.x >> 5];
-  if (lane == 0) *wc = WarpCounters{};
-  __syncwarp();
-  LaneTotals<T> tot;
-  // The warp's current segment; its totals are flushed when the warp's next
-  // item falls in another segment (items come in segment order, so a warp
-  // usually stays in one segment for many items).
-  bool have = false;
-  unsigned long long seg_lo = 0, seg_hi = 0;
-  // A warp claims kGrab consecutive items per atomic, so that it crosses a
-  // segment boundary (search + flush) at most about once per claim.
-  constexpr unsigned kGrab = 8;
-  unsigned long long base = 0;
-  unsigned left = 0;
-  for (;;) {
-    if (left == 0) {
-      if (lane == 0) base = atomicAdd(work, static_cast<unsigned long long>(kGrab));
-      base = __shfl_sync(kFull, base, 0);
-      left = kGrab;
-    }
-    const unsigned long long item = base + (kGrab - left);
-    --left;
-    if (item >= total) break;
-    if (item < seg_lo || item >= seg_hi) {
-      if (have) flush_warp(tot, wc, st.totals, flags, lane);
-      int lo = 0, hi = nseg - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (segs[mid].item_begin <= item) lo = mid; else hi = mid - 1;
-      }
-      __syncwarp();
-      if (lane == 0) {
-        const BatchSegmentDev sg = segs[lo];
-        const BatchProblemDev pb = probs[sg.problem];
-        const int level = pb.l0 + sg.slot;
-        st.ia.meta = pb.meta;
-        st.ia.alias = pb.alias;
-        st.ia.v_walk = pb.v_walk;
-        st.ia.level = level;
-        st.ia.ctr3 = static_cast<uint32_t>(level) & 0x3Fu;
-        st.ia.key0 = pb.key0;
-        st.ia.key1 = pb.key1;
-        st.ia.max_jumps = pb.max_jumps;
-        st.ia.sum_y = pb.sums + static_cast<int64_t>(sg.slot) * pb.n;
-        st.ia.rep_begin = sg.rep_begin;
-        st.ia.trace = nullptr;
-        st.ia.trace_stride = 0;
-        st.ia.trace_base = 0;
-        st.ia.f_walk = nullptr;
-        st.ia.t = 0.0;
-        st.ia.n = pb.n;
-        st.ia.nnz = pb.nnz;
-        st.totals = pb.totals + static_cast<int64_t>(sg.slot) * kTotSlots;
-        st.n = pb.n;
-        st.reps = sg.reps;
-        st.chunk = sg.chunk;
-        st.chunks_per_row = sg.chunks_per_row;
-        st.slot = sg.slot;
-        st.key0 = pb.key0;
-        st.key1 = pb.key1;
-      }
-      __syncwarp();
-      seg_lo = segs[lo].item_begin;
-      seg_hi = seg_lo + static_cast<unsigned long long>(st.n) *
-                            static_cast<unsigned long long>(st.chunks_per_row);
-      have = true;
-    }
-    const unsigned long long local = item - seg_lo;
-    const int64_t row = static_cast<int64_t>(local / static_cast<unsigned long long>(st.chunks_per_row));
-    const int64_t chunk = static_cast<int64_t>(local) - row * st.chunks_per_row;
-    const int64_t r_lo = chunk * st.chunk;
-    const int64_t r_hi = min(r_lo + st.chunk, st.reps);
-    const KeysOnTheFly keys{st.key0, st.key1};
-    // Without screening (one event per lane per iteration for every row):
-    // the batched instances' walks are mostly long, and the screening stage
-    // would hold more state than this kernel's registers allow.
-    if (st.slot > 0)
-      walk_item<FP64, true, false, false, KeysOnTheFly, false>(st.ia, keys, row, r_lo, r_hi, tot, wc, q, eq, lane);
-    else
-      walk_item<FP64, false, false, false, KeysOnTheFly, false>(st.ia, keys, row, r_lo, r_hi, tot, wc, q, eq, lane);
-  }
-  if (have) flush_warp(tot, wc, st.totals, flags, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -1400,7 +1262,7 @@ cudaError_t launch_to_float(mlmc_plan* p, const double* in, float* out) {
 }
 
 template <bool FP64, bool COARSE, bool TRACE, bool IS, bool SRC>
-cudaError_t launch_one(mlmc_plan* p, const WalkArgs& args, int block) {
+cudaError_t launch_one(mlmc_plan* p, const WalkArgs& args, int block, cudaStream_t stream) {
   auto kern = k_walk<FP64, COARSE, TRACE, IS, SRC>;
   int per_sm = 0;
   cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, 0);
@@ -1416,7 +1278,7 @@ cudaError_t launch_one(mlmc_plan* p, const WalkArgs& args, int block) {
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(static_cast<unsigned>(grid));
   cfg.blockDim = dim3(static_cast<unsigned>(block));
-  cfg.stream = p->stream;
+  cfg.stream = stream;
   cfg.attrs = attr;
   if (IS)
     cfg.numAttrs = l2_window_attr(p, p->d_alias_is, sizeof(AliasEntryIS) * static_cast<size_t>(p->nnz), attr);
@@ -1431,20 +1293,21 @@ cudaError_t launch_one(mlmc_plan* p, const WalkArgs& args, int block) {
 
 // Proposal and source term are exclusive (checked when either is set).
 template <bool FP64, bool COARSE, bool TRACE>
-cudaError_t dispatch_is(mlmc_plan* p, const WalkArgs& a, int block, bool is, bool src) {
-  if (src) return launch_one<FP64, COARSE, TRACE, false, true>(p, a, block);
-  return is ? launch_one<FP64, COARSE, TRACE, true, false>(p, a, block)
-            : launch_one<FP64, COARSE, TRACE, false, false>(p, a, block);
+cudaError_t dispatch_is(mlmc_plan* p, const WalkArgs& a, int block, bool is, bool src,
+                        cudaStream_t st) {
+  if (src) return launch_one<FP64, COARSE, TRACE, false, true>(p, a, block, st);
+  return is ? launch_one<FP64, COARSE, TRACE, true, false>(p, a, block, st)
+            : launch_one<FP64, COARSE, TRACE, false, false>(p, a, block, st);
 }
 
 cudaError_t dispatch_walk(mlmc_plan* p, const WalkArgs& a, int block, bool fp64, bool coarse,
-                          bool trace, bool is, bool src) {
+                          bool trace, bool is, bool src, cudaStream_t st) {
   if (fp64) {
-    if (coarse) return trace ? dispatch_is<true, true, true>(p, a, block, is, src) : dispatch_is<true, true, false>(p, a, block, is, src);
-    return trace ? dispatch_is<true, false, true>(p, a, block, is, src) : dispatch_is<true, false, false>(p, a, block, is, src);
+    if (coarse) return trace ? dispatch_is<true, true, true>(p, a, block, is, src, st) : dispatch_is<true, true, false>(p, a, block, is, src, st);
+    return trace ? dispatch_is<true, false, true>(p, a, block, is, src, st) : dispatch_is<true, false, false>(p, a, block, is, src, st);
   }
-  if (coarse) return trace ? dispatch_is<false, true, true>(p, a, block, is, src) : dispatch_is<false, true, false>(p, a, block, is, src);
-  return trace ? dispatch_is<false, false, true>(p, a, block, is, src) : dispatch_is<false, false, false>(p, a, block, is, src);
+  if (coarse) return trace ? dispatch_is<false, true, true>(p, a, block, is, src, st) : dispatch_is<false, true, false>(p, a, block, is, src, st);
+  return trace ? dispatch_is<false, false, true>(p, a, block, is, src, st) : dispatch_is<false, false, false>(p, a, block, is, src, st);
 }
 
 template <bool FP64, bool COARSE, bool TRACE, bool IS>
@@ -1540,103 +1403,25 @@ cudaError_t launch_walk_forward(mlmc_plan* p, const WalkLaunch& w, int64_t* laun
   return cudaSuccess;
 }
 
-cudaError_t launch_walk(mlmc_plan* p, const WalkLaunch& w, int64_t* launches) {
-  if (launches) *launches = 0;
-  if (w.reps <= 0 || p->n <= 0) return cudaSuccess;
-  const bool fp64 = p->sched.precision == MLMC_FP64;
-  WalkArgs a{};
-  a.meta = fp64 ? static_cast<const void*>(p->d_meta64) : static_cast<const void*>(p->d_meta32);
-  a.alias = p->proposal_active ? static_cast<const void*>(p->d_alias_is)
-                               : static_cast<const void*>(p->d_fused);
-  if (fp64) {
-    a.v_walk = w.v;
-  } else {
-    cudaError_t cerr = launch_to_float(p, w.v, p->d_v32);
-    if (cerr != cudaSuccess) return cerr;
-    a.v_walk = p->d_v32;
-  }
-  const bool src = p->source_active;
-  if (src) {
-    if (w.level < 1 || (w.coarse && w.level < 2)) return cudaErrorInvalidValue;
-    if (!fp64) {
-      cudaError_t cerr = launch_to_float(p, p->d_src, p->d_src32);
-      if (cerr != cudaSuccess) return cerr;
-    }
-    a.f_walk = fp64 ? static_cast<const void*>(p->d_src) : static_cast<const void*>(p->d_src32);
-    a.t = p->t;
-  }
-  a.n = p->n;
-  a.nnz = p->nnz;
-  a.level = w.level;
-  a.ctr3 = static_cast<uint32_t>(w.level) & 0x3Fu;
-  a.key0 = static_cast<uint32_t>(w.seed & 0xFFFFFFFFull);
-  a.key1 = static_cast<uint32_t>(w.seed >> 32);
-  a.rk = philox_round_keys(a.key0, a.key1);
-  a.max_jumps = p->sched.max_jumps_per_walk;
-  a.sum_y = w.sum_y;
-  a.totals = w.totals;
-  a.flags = p->d_flags;
-  a.work = p->d_work;
-  a.trace = w.trace;
-  a.trace_stride = w.reps;
-  const int block = p->sched.block_threads > 0 ? p->sched.block_threads : 256;
-  const bool trace = w.trace != nullptr;
-  // Bounded launches (about 2^31 walks each, tens of milliseconds): the
-  // controller's time budget is checked between them and no single kernel
-  // runs for seconds.
-  const int64_t cap = std::max<int64_t>(32, (int64_t{1} << 31) / p->n);
-  for (int64_t done = 0; done < w.reps; done += cap) {
-    const int64_t reps = std::min(cap, w.reps - done);
-    a.rep_begin = w.rep_begin + done;
-    a.reps = reps;
-    a.trace_base = done;
-    int64_t per_lane = p->sched.walks_per_lane;
-    if (per_lane <= 0) {
-      // Enough walks per item to amortise the item fetch and the pool's tail.
-      per_lane = (reps + 31) / 32;
-      if (per_lane > 128) per_lane = 128;
-    }
-    a.chunk = 32 * per_lane;
-    a.chunks_per_row = (reps + a.chunk - 1) / a.chunk;
-    a.row_begin = w.row_count < 0 ? 0 : w.row_begin;
-    a.total_items = static_cast<unsigned long long>(w.row_count < 0 ? p->n : w.row_count) *
-                    static_cast<unsigned long long>(a.chunks_per_row);
-    cudaError_t err = cudaMemsetAsync(p->d_work, 0, sizeof(unsigned long long), p->stream);
-    if (err != cudaSuccess) return err;
-    err = dispatch_walk(p, a, block, fp64, w.coarse, trace, p->proposal_active, src);
-    if (err != cudaSuccess) return err;
-    if (launches) ++*launches;
-  }
-  return cudaSuccess;
-}
+namespace {
 
-// The same launch sequence as launch_walk, with the work counter and the FP32
-// copy of v taken from caller-supplied device memory instead of the plan's
-// buffers (used by the entry point whose scratch is static device memory).
-cudaError_t launch_walk_scratch(mlmc_plan* p, const WalkLaunch& w, unsigned long long* work,
-                                float* v32, int64_t* launches) {
-  if (launches) *launches = 0;
-  if (w.reps <= 0 || p->n <= 0) return cudaSuccess;
+// The launches of one walk request on `stream`: bounded launches of about
+// 2^31 walks (tens of milliseconds each: the controller checks its time
+// budget between them and no kernel runs for seconds), each after resetting
+// the work counter `work`.  v_walk / f_walk: right-hand side and source in
+// the walk precision; per_lane_fixed > 0 fixes the walks per lane of an item.
+cudaError_t launch_walk_core(mlmc_plan* p, const WalkLaunch& w, const void* v_walk,
+                             const void* f_walk, unsigned long long* work, uint32_t* flags,
+                             int64_t per_lane_fixed, cudaStream_t stream, int64_t* launches) {
   const bool fp64 = p->sched.precision == MLMC_FP64;
   WalkArgs a{};
   a.meta = fp64 ? static_cast<const void*>(p->d_meta64) : static_cast<const void*>(p->d_meta32);
   a.alias = p->proposal_active ? static_cast<const void*>(p->d_alias_is)
                                : static_cast<const void*>(p->d_fused);
-  if (fp64) {
-    a.v_walk = w.v;
-  } else {
-    cudaError_t cerr = launch_to_float(p, w.v, v32);
-    if (cerr != cudaSuccess) return cerr;
-    a.v_walk = v32;
-  }
-  const bool src = p->source_active;
+  a.v_walk = v_walk;
+  const bool src = f_walk != nullptr;
   if (src) {
-    if (w.level < 1 || (w.coarse && w.level < 2)) return cudaErrorInvalidValue;
-    if (!fp64) {
-      cudaError_t cerr = launch_to_float(p, p->d_src, p->d_src32);
-      if (cerr != cudaSuccess) return cerr;
-    }
-    a.f_walk = fp64 ? static_cast<const void*>(p->d_src) : static_cast<const void*>(p->d_src32);
+    a.f_walk = f_walk;
     a.t = p->t;
   }
   a.n = p->n;
@@ -1649,7 +1434,7 @@ cudaError_t launch_walk_scratch(mlmc_plan* p, const WalkLaunch& w, unsigned long
   a.max_jumps = p->sched.max_jumps_per_walk;
   a.sum_y = w.sum_y;
   a.totals = w.totals;
-  a.flags = p->d_flags;
+  a.flags = flags;
   a.work = work;
   a.trace = w.trace;
   a.trace_stride = w.reps;
@@ -1661,8 +1446,9 @@ cudaError_t launch_walk_scratch(mlmc_plan* p, const WalkLaunch& w, unsigned long
     a.rep_begin = w.rep_begin + done;
     a.reps = reps;
     a.trace_base = done;
-    int64_t per_lane = p->sched.walks_per_lane;
+    int64_t per_lane = per_lane_fixed;
     if (per_lane <= 0) {
+      // Enough walks per item to amortise the item fetch and the pool's tail.
       per_lane = (reps + 31) / 32;
       if (per_lane > 128) per_lane = 128;
     }
@@ -1671,26 +1457,75 @@ cudaError_t launch_walk_scratch(mlmc_plan* p, const WalkLaunch& w, unsigned long
     a.row_begin = w.row_count < 0 ? 0 : w.row_begin;
     a.total_items = static_cast<unsigned long long>(w.row_count < 0 ? p->n : w.row_count) *
                     static_cast<unsigned long long>(a.chunks_per_row);
-    cudaError_t err = cudaMemsetAsync(work, 0, sizeof(unsigned long long), p->stream);
+    cudaError_t err = cudaMemsetAsync(work, 0, sizeof(unsigned long long), stream);
     if (err != cudaSuccess) return err;
-    err = dispatch_walk(p, a, block, fp64, w.coarse, trace, p->proposal_active, src);
+    err = dispatch_walk(p, a, block, fp64, w.coarse, trace, p->proposal_active, src, stream);
     if (err != cudaSuccess) return err;
     if (launches) ++*launches;
   }
   return cudaSuccess;
 }
 
-cudaError_t launch_walk_batch(bool fp64, const BatchProblemDev* probs, const BatchHeaderDev* hdr,
-                              const BatchSegmentDev* segs, unsigned long long* work,
-                              uint32_t* flags, int num_sms, int block, cudaStream_t stream) {
-  int per_sm = 0;
-  cudaError_t err = fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_batch<true>, block, 0)
-                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_batch<false>, block, 0);
+// The source term in the walk precision (FP32 walks: converted into the
+// plan's buffer), or null without one.
+cudaError_t source_for_walk(mlmc_plan* p, const WalkLaunch& w, const void** f_walk) {
+  *f_walk = nullptr;
+  if (!p->source_active) return cudaSuccess;
+  if (w.level < 1 || (w.coarse && w.level < 2)) return cudaErrorInvalidValue;
+  if (p->sched.precision == MLMC_FP64) {
+    *f_walk = p->d_src;
+    return cudaSuccess;
+  }
+  cudaError_t err = launch_to_float(p, p->d_src, p->d_src32);
+  *f_walk = p->d_src32;
+  return err;
+}
+
+}  // namespace
+
+cudaError_t launch_walk(mlmc_plan* p, const WalkLaunch& w, int64_t* launches) {
+  if (launches) *launches = 0;
+  if (w.reps <= 0 || p->n <= 0) return cudaSuccess;
+  const void* v_walk = w.v;
+  if (p->sched.precision != MLMC_FP64) {
+    cudaError_t err = launch_to_float(p, w.v, p->d_v32);
+    if (err != cudaSuccess) return err;
+    v_walk = p->d_v32;
+  }
+  const void* f_walk = nullptr;
+  cudaError_t err = source_for_walk(p, w, &f_walk);
   if (err != cudaSuccess) return err;
-  const unsigned grid = static_cast<unsigned>(num_sms * (per_sm > 0 ? per_sm : 1));
-  if (fp64) k_walk_batch<true><<<grid, block, 0, stream>>>(probs, hdr, segs, work, flags);
-  else k_walk_batch<false><<<grid, block, 0, stream>>>(probs, hdr, segs, work, flags);
-  return cudaGetLastError();
+  return launch_walk_core(p, w, v_walk, f_walk, p->d_work, p->d_flags, p->sched.walks_per_lane,
+                          p->stream, launches);
+}
+
+// The same launch sequence as launch_walk, with the work counter and the FP32
+// copy of v taken from caller-supplied device memory instead of the plan's
+// buffers (used by the entry point whose scratch is static device memory).
+cudaError_t launch_walk_scratch(mlmc_plan* p, const WalkLaunch& w, unsigned long long* work,
+                                float* v32, int64_t* launches) {
+  if (launches) *launches = 0;
+  if (w.reps <= 0 || p->n <= 0) return cudaSuccess;
+  const void* v_walk = w.v;
+  if (p->sched.precision != MLMC_FP64) {
+    cudaError_t err = launch_to_float(p, w.v, v32);
+    if (err != cudaSuccess) return err;
+    v_walk = v32;
+  }
+  const void* f_walk = nullptr;
+  cudaError_t err = source_for_walk(p, w, &f_walk);
+  if (err != cudaSuccess) return err;
+  return launch_walk_core(p, w, v_walk, f_walk, work, p->d_flags, p->sched.walks_per_lane,
+                          p->stream, launches);
+}
+
+cudaError_t launch_walk_segment(mlmc_plan* p, const WalkLaunch& w, const void* v_walk,
+                                int64_t per_lane, unsigned long long* work, uint32_t* flags,
+                                cudaStream_t stream, int64_t* launches) {
+  if (launches) *launches = 0;
+  if (w.reps <= 0 || p->n <= 0) return cudaSuccess;
+  if (p->source_active) return cudaErrorInvalidValue;
+  return launch_walk_core(p, w, v_walk, nullptr, work, flags, per_lane, stream, launches);
 }
 
 }  // namespace mlmc
