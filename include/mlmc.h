@@ -329,7 +329,8 @@ mlmc_status mlmc_batch_create(mlmc_batch **out, mlmc_plan *const *plans, int32_t
  * so that small problems run side by side, then one graph launch does the
  * batched reductions, and the host synchronises once.  v[k], x[k]: host or
  * device pointers to n_k doubles; seeds[k]: Philox key of problem k (the
- * walks are those a single-plan solve with that seed draws).  Returns
+ * walks are those a single-plan solve with that seed draws, with the plan's
+ * jump law: its proposal when one is set).  Returns
  * NOT_CONVERGED if any problem stopped on a budget (every x is still
  * written). */
 mlmc_status mlmc_batch_expmv(mlmc_batch *batch, const double *const *v, double *const *x,
