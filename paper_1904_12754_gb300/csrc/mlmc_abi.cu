@@ -382,8 +382,9 @@ mlmc_status mlmc_plan_create(mlmc_plan** out, int64_t n, int64_t nnz, const int6
   PLAN_CUDA(dev_alloc(&p->d_val, nnz), "alloc val");
   {
     // [records of the plan's precision | its fused entries | plain alias |
-    // records of the other precision], each part 256-byte aligned: the
-    // walk reads the first two parts (one contiguous L2 window).
+    // records of the other precision | FP32 still thresholds], each part
+    // 256-byte aligned: the walk reads the first two parts (one contiguous
+    // L2 window) and one threshold per work item.
     auto up = [](size_t b) { return (b + 255) & ~size_t{255}; };
     const bool fp64 = s.precision == MLMC_FP64;
     const size_t ent = static_cast<size_t>(nnz > 0 ? nnz : 1);
@@ -392,13 +393,15 @@ mlmc_status mlmc_plan_create(mlmc_plan** out, int64_t n, int64_t nnz, const int6
     const size_t ba = up(sizeof(AliasEntry) * ent);
     const size_t bf = up((fp64 ? sizeof(FusedEntry64) : sizeof(FusedEntry32)) * ent);
     const size_t bown = fp64 ? b64 : b32, bother = fp64 ? b32 : b64;
-    PLAN_CUDA(dev_alloc(&p->d_tables, bown + bf + ba + bother), "alloc tables");
+    const size_t bstill = up(sizeof(int32_t) * static_cast<size_t>(n > 0 ? n : 1));
+    PLAN_CUDA(dev_alloc(&p->d_tables, bown + bf + ba + bother + bstill), "alloc tables");
     unsigned char* own = p->d_tables;
     p->d_fused = p->d_tables + bown;
     p->d_alias = reinterpret_cast<AliasEntry*>(p->d_tables + bown + bf);
     unsigned char* other = p->d_tables + bown + bf + ba;
     p->d_meta32 = reinterpret_cast<Meta32*>(fp64 ? other : own);
     p->d_meta64 = reinterpret_cast<Meta64*>(fp64 ? own : other);
+    p->d_still32 = reinterpret_cast<int32_t*>(other + bother);
     p->l2_base32 = p->d_tables;
     p->l2_bytes32 = bown + bf;
     p->l2_base64 = p->d_tables;

@@ -216,4 +216,36 @@ __device__ __forceinline__ float neglog32(float u) {
   return -lnu;
 }
 
+// FP32 walks: the largest uniform index i (u = (2i+1) 2^-24, i < 2^23) whose
+// first holding time fl(-ln(u)) / (t L_row) reaches s = 1, or -1 if none.  The
+// holding time is non-increasing in i (the FP32 -ln(u) is strictly
+// decreasing over all 2^23 uniforms, an exhaustive host check of the same
+// arithmetic, and rounding a product with a positive factor is monotone), so
+// a walk never jumps exactly when its index is <= the returned one.  The 32
+// lanes test 32 points of the open interval per round: the passing points
+// form a prefix, and an interval of at most 33 points is settled in one
+// round (5 rounds from 2^23).
+__device__ __forceinline__ int32_t still_index32(float inv_rate, int lane) {
+  int32_t lo = -1, hi = 1 << 23;  // the test holds at lo (or lo = -1), fails at hi (or hi = 2^23)
+  while (hi - lo > 1) {
+    const int64_t width = hi - lo;
+    const int32_t c = lo + static_cast<int32_t>((static_cast<int64_t>(lane + 1) * width) / 33);
+    bool pass;
+    if (c <= lo) {
+      pass = true;
+    } else if (c >= hi) {
+      pass = false;
+    } else {
+      const float u = __fmul_rn(__uint2float_rn(2u * static_cast<uint32_t>(c) + 1u), 0x1p-24f);
+      pass = !(__fmul_rn(neglog32(u), inv_rate) < 1.0f);
+    }
+    const int t = __popc(__ballot_sync(0xFFFFFFFFu, pass));
+    const int32_t c_last = __shfl_sync(0xFFFFFFFFu, c, t > 0 ? t - 1 : 0);
+    const int32_t c_first_fail = __shfl_sync(0xFFFFFFFFu, c, t < 32 ? t : 31);
+    if (t > 0 && c_last > lo) lo = c_last;
+    if (t < 32 && c_first_fail < hi) hi = c_first_fail;
+  }
+  return lo;
+}
+
 }  // namespace mlmc

@@ -73,11 +73,13 @@ struct mlmc_plan {
   double* d_val = nullptr;
 
   // Tables (Eq. 1 split, Eq. 12 alias), carved from one allocation in the
-  // order meta32 | alias | meta64 so that each precision's walk reads one
-  // contiguous range (its L2 access-policy window).
+  // order: records of the plan's precision | its fused entries | plain alias
+  // | records of the other precision | FP32 still thresholds, so that the
+  // walk reads one contiguous range (its L2 access-policy window).
   unsigned char* d_tables = nullptr;
   mlmc::Meta32* d_meta32 = nullptr;
   mlmc::Meta64* d_meta64 = nullptr;
+  int32_t* d_still32 = nullptr;   // FP32: per-row still threshold index (in d_tables)
   // Fused entries of the plan's precision (FusedEntry32 or FusedEntry64),
   // at the same positions as the alias entries.
   void* d_fused = nullptr;

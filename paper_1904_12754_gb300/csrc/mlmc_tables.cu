@@ -289,6 +289,21 @@ __global__ void k_fuse(int64_t n, const Meta* __restrict__ meta, const AliasEntr
   }
 }
 
+// FP32 walks: per row with 1/(t L) >= 1 (the rows the walk kernel screens),
+// the largest first-uniform index whose holding time reaches s = 1
+// (still_index32); other rows get -1 (never read).  One warp per row.
+__global__ void __launch_bounds__(256) k_still_index(int64_t n, const Meta32* __restrict__ meta,
+                                                     int32_t* __restrict__ still) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x >> 5) + (threadIdx.x >> 5); i < n;
+       i += warps) {
+    const float ir = meta[i].inv_rate;
+    const int32_t k = ir >= 1.0f ? still_index32(ir, lane) : -1;  // warp-uniform branch
+    if (lane == 0) still[i] = k;
+  }
+}
+
 cudaError_t launch_build_tables(mlmc_plan* p) {
   cudaError_t err = cudaMemsetAsync(p->d_norm2, 0, sizeof(double), p->stream);
   if (err != cudaSuccess) return err;
@@ -305,6 +320,12 @@ cudaError_t launch_build_tables(mlmc_plan* p) {
     k_fuse<<<grid_for(p, p->n, kBuildBlock), kBuildBlock, 0, p->stream>>>(
         p->n, p->d_meta32, p->d_alias, static_cast<FusedEntry32*>(p->d_fused));
   p->launches++;
+  if (p->sched.precision != MLMC_FP64) {
+    const int64_t blocks = (p->n + 7) / 8;
+    const int grid = static_cast<int>(blocks < p->num_sms * 16 ? blocks : p->num_sms * 16);
+    k_still_index<<<grid > 0 ? grid : 1, 256, 0, p->stream>>>(p->n, p->d_meta32, p->d_still32);
+    p->launches++;
+  }
   return cudaGetLastError();
 }
 

@@ -82,6 +82,7 @@ struct WalkArgs {
   int64_t trace_base;      // offset of this launch's first replica
   const void* f_walk;      // source vector in the walk precision (source walks only)
   double t;                // the time t (source walks only)
+  const int32_t* still32;  // FP32: per-row still threshold index (still_index32)
 };
 
 // Key source of the walk's draws: the round keys of a launch-constant
@@ -235,6 +236,7 @@ struct ItemArgs {
   const void* f_walk;     // source vector (source walks only)
   double t;               // the time t (source walks only)
   int64_t n, nnz;         // table sizes (checked build)
+  const int32_t* still32; // FP32: per-row still threshold index
 };
 
 // Per-warp running totals of the walks a warp has finished.
@@ -312,9 +314,9 @@ __device__ __forceinline__ void flush_warp(LaneTotals<T>& t, WarpCounters* wc, d
 // Per-warp queue of screened walks that jump at least once, a ring of
 // WarpQueue<FP64>::kCap slots.  FP32: replica offset and the Philox word of the first
 // holding time (the first jump's words come from the walk's own draw 0 when
-// it is taken); a screening round adds at most 128 entries (32 blocks of 4
+// it is taken); a screening round adds at most 256 entries (64 blocks of 4
 // walks) and runs only while fewer than 32 are queued, so it never holds more
-// than 159.  FP64: replica offset, the first holding time and the first
+// than 287.  FP64: replica offset, the first holding time and the first
 // jump's bucket and coin words; at most 64 per round, never more than 95.
 template <bool FP64>
 struct WarpQueue;
@@ -382,38 +384,6 @@ __device__ __forceinline__ typename Prec<FP64>::T simpson_segment(
   return total;
 }
 
-// FP32 walks: the largest uniform index i (u = (2i+1) 2^-24, i < 2^23) whose
-// first holding time fl(-ln(u)) / (t L_row) reaches s = 1, or -1 if none.  The
-// holding time is non-increasing in i (the FP32 -ln(u) is strictly
-// decreasing over all 2^23 uniforms, an exhaustive host check of the same
-// arithmetic, and rounding a product with a positive factor is monotone), so
-// a walk never jumps exactly when its index is <= the returned one.  The 32
-// lanes test 32 points of the open interval per round: the passing points
-// form a prefix, and an interval of at most 33 points is settled in one
-// round (5 rounds from 2^23).
-__device__ __forceinline__ int32_t still_index32(float inv_rate, int lane) {
-  int32_t lo = -1, hi = 1 << 23;  // the test holds at lo (or lo = -1), fails at hi (or hi = 2^23)
-  while (hi - lo > 1) {
-    const int64_t width = hi - lo;
-    const int32_t c = lo + static_cast<int32_t>((static_cast<int64_t>(lane + 1) * width) / 33);
-    bool pass;
-    if (c <= lo) {
-      pass = true;
-    } else if (c >= hi) {
-      pass = false;
-    } else {
-      const float u = __fmul_rn(__uint2float_rn(2u * static_cast<uint32_t>(c) + 1u), 0x1p-24f);
-      pass = !(__fmul_rn(neglog32(u), inv_rate) < 1.0f);
-    }
-    const int t = __popc(__ballot_sync(kFull, pass));
-    const int32_t c_last = __shfl_sync(kFull, c, t > 0 ? t - 1 : 0);
-    const int32_t c_first_fail = __shfl_sync(kFull, c, t < 32 ? t : 31);
-    if (t > 0 && c_last > lo) lo = c_last;
-    if (t < 32 && c_first_fail < hi) hi = c_first_fail;
-  }
-  return lo;
-}
-
 // One work item: walks r_lo .. r_hi-1 (replica offsets relative to
 // a.rep_begin) of row `row`, run by the whole warp in two interleaved stages.
 //   screen  the 32 lanes draw the first holding time of 64 (FP64) or 128
@@ -463,8 +433,9 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
   // fall in the same iteration); one wave without screening for the others.
   constexpr int kWays = 2;
   const bool two_wave = static_cast<T>(m0.inv_rate) >= static_cast<T>(1);
-  const int32_t still_max =
-      (FP64 || !two_wave) ? 0 : still_index32(static_cast<float>(m0.inv_rate), lane);
+  // FP32: a screened walk never jumps exactly when its first uniform's index
+  // is <= the row's threshold index (computed once per row with the tables).
+  const int32_t still_max = (FP64 || !two_wave) ? 0 : __ldg(a.still32 + row);
   // A walk that never jumps stays at the row for the whole interval: its
   // sample is 0 above l0 and v_row e^{dl_row} at l0 (E_f = dl_row exactly
   // as the grid weights sum to 1), the same for every such walk.
@@ -968,6 +939,7 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk(const __grid_constan
   ia.t = a.t;
   ia.n = a.n;
   ia.nnz = a.nnz;
+  ia.still32 = a.still32;
   __shared__ WarpQueue<FP64> queues[kMaxWarps];
   __shared__ WarpCounters counters[kMaxWarps];
   __shared__ EndQueue<FP64> ends[kMaxWarps];
@@ -1419,6 +1391,7 @@ cudaError_t launch_walk_core(mlmc_plan* p, const WalkLaunch& w, const void* v_wa
   a.alias = p->proposal_active ? static_cast<const void*>(p->d_alias_is)
                                : static_cast<const void*>(p->d_fused);
   a.v_walk = v_walk;
+  a.still32 = p->d_still32;
   const bool src = f_walk != nullptr;
   if (src) {
     a.f_walk = f_walk;
