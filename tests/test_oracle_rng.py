@@ -72,13 +72,26 @@ def test_neglog32_accuracy():
     rng = np.random.default_rng(2)
     u = np.concatenate([rng.random(200_000).astype(np.float32),
                         (2.0 ** -np.arange(1, 25)).astype(np.float32),
-                        (1.0 - 2.0 ** -np.arange(1, 25)).astype(np.float32)])
+                        (1.0 - 2.0 ** -np.arange(1, 25)).astype(np.float32),
+                        np.array([np.sqrt(0.5), np.nextafter(np.float32(np.sqrt(0.5)), 0)],
+                                 np.float32)])
     u = u[(u > 0) & (u < 1)]
     ref = -np.log(u.astype(np.float64))
     got = W.neglog32(u).astype(np.float64)
     assert np.all(got > 0)
     ulp = np.abs(got - ref) / np.spacing(ref.astype(np.float32)).astype(np.float64)
-    assert ulp.max() <= 4.0
+    assert ulp.max() <= 1.0
+
+
+def test_neglog32_within_one_ulp_on_every_fp32_uniform():
+    # The walk's FP32 -ln(u) against the FP64 logarithm on all 2^23 uniforms
+    # u = (2i+1) 2^-24 it is ever called with.
+    i = np.arange(1 << 23, dtype=np.float64)
+    u = ((2.0 * i + 1.0) * 2.0 ** -24).astype(np.float32)
+    ref = -np.log(u.astype(np.float64))
+    got = W.neglog32(u).astype(np.float64)
+    ulp = np.abs(got - ref) / np.spacing(ref.astype(np.float32)).astype(np.float64)
+    assert ulp.max() <= 1.0
 
 
 def test_exponential_law_of_holding_draws():
