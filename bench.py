@@ -459,7 +459,7 @@ OPS_END_STILL = 1
 # DRAM bytes of one captured walk launch (ncu, profiles/walk_fp32_ba_n1e5_l0.md:
 # 4.1e8 walks at l0 after an L2 flush; the fused tables, 40 MB, are read once
 # and everything else hits L2); None when the kernel changed after the capture.
-TRAFFIC_CAPTURE = None
+TRAFFIC_CAPTURE = 41644800
 
 
 def walk_roofline(level_log, walk_s, clocks, peaks, total_ms):
