@@ -434,13 +434,15 @@ def run_ours(args):
 # Walk-kernel roofline: ALU (issue) bound with this workload's tables in L2.
 # Algorithmic operations of the FP32 walk, counted from the kernel source
 # (each integer/FP32 operation, compare, select, load, exp = 1):
-#   Philox draw   60  (10 rounds x 2 wide multiplies, 2 three-input xors, 2 key
-#                     adds).  The FP32 layout needs one draw per jump plus one
+#   Philox draw   42  (10 rounds x 2 wide multiplies and 2 three-input xors, 2
+#                     counter words; the round keys are formed once per launch).
+#                     The FP32 layout needs one draw per jump plus one
 #                     block per four walks for their first holding times
 #                     (rows with 1/(tL) >= 1, nearly all rows here; a walk in
 #                     another row that never jumps also draws once, which
 #                     this count leaves out)
-#   holding time  37  (uniform 4, -ln(u) 30, scale + add + compare 3), for
+#   holding time  31  (uniform 4; -ln(u) 24: range reduction 10, degree-8
+#                     polynomial 10, ln 2 terms 4; scale + add + compare 3), for
 #                     every event except the first of a walk that never jumps
 #   still test     2  per walk: the first uniform's index against the row's
 #                     threshold index
@@ -450,8 +452,8 @@ def run_ours(args):
 #                 and pair sums); 1 for a walk that never jumped
 # peak = 152 SMs x 128 lanes x SM clock (one operation per lane per clock).
 # ---------------------------------------------------------------------------
-OPS_DRAW = 60
-OPS_HOLD = 37
+OPS_DRAW = 42
+OPS_HOLD = 31
 OPS_STILL_TEST = 2
 OPS_JUMP = {True: 22, False: 15}
 OPS_END_JUMPED = {True: 31, False: 24}
