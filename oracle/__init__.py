@@ -15,6 +15,8 @@ Modules
              of the level corrections, and brute-force path enumeration.
   mlmc       the driver of Algorithm 1 with Giles' optimal sample sizes
              (Eq. 11), running the oracle walker.
+  mlp        numpy forward pass, loss and gradients of the proposal network
+             with the GPU's BF16 rounding points, pinned by finite differences.
 
 Every function whose result is not pinned by a test against something other
 than itself says "parity unpinned" in its docstring.
