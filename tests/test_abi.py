@@ -53,3 +53,27 @@ def test_host_only_calls(lib):
         st = lib.mlmc_plan_create(ct.byref(h), n, 0, rp, None, None, t, None, tol, None)
         assert st == mlmc.MLMC_ERR_INVALID_ARG
     lib.mlmc_plan_destroy(None)
+
+
+def test_schedule_checks_come_before_device_work(lib):
+    # Every bad schedule is refused with INVALID_ARG and a message, before the
+    # plan touches the device (this runs without a GPU).
+    from paper_1904_12754_gb300 import mlmc
+    rp = (ct.c_int64 * 2)(0, 0)
+    h = ct.c_void_p()
+
+    def create(**fields):
+        s = mlmc.schedule_default()
+        for k, v in fields.items():
+            setattr(s, k, v)
+        return lib.mlmc_plan_create(ct.byref(h), 1, 0, rp, None, None, 1.0, ct.byref(s), 1e-3, None)
+
+    bad = [dict(num_levels=0), dict(num_levels=4, max_levels=3), dict(max_levels=33),
+           dict(precision=7), dict(mode=5), dict(proposal=1), dict(pilot_walks=1),
+           dict(max_walks_per_row=1), dict(max_jumps_per_walk=-1), dict(l0=25),
+           dict(l0=20, num_levels=3, max_levels=6), dict(l2_persist=2),
+           dict(block_threads=48), dict(block_threads=512), dict(walks_per_lane=-1)]
+    for fields in bad:
+        assert create(**fields) == mlmc.MLMC_ERR_INVALID_ARG, fields
+        assert lib.mlmc_last_error(), fields
+        assert not h.value
