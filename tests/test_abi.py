@@ -77,3 +77,29 @@ def test_schedule_checks_come_before_device_work(lib):
         assert create(**fields) == mlmc.MLMC_ERR_INVALID_ARG, fields
         assert lib.mlmc_last_error(), fields
         assert not h.value
+
+
+def test_every_entry_point_refuses_null_handles(lib):
+    # Each status-returning call of the header, given NULL handles and zero
+    # sizes, returns INVALID_ARG with a message and does no device work.
+    from paper_1904_12754_gb300 import mlmc
+    skip = {"mlmc_last_error", "mlmc_launch_count", "mlmc_plan_destroy", "mlmc_batch_destroy",
+            "mlmc_mlp_destroy"}
+    called = 0
+    for name in _declared():
+        fn = getattr(lib, name)
+        if name in skip or fn.argtypes is None or fn.restype not in (ct.c_int, ct.c_int32):
+            continue
+        args = []
+        for t in fn.argtypes:
+            if t in (ct.c_double, ct.c_float):
+                args.append(t(0.0))
+            elif isinstance(t, type) and issubclass(t, (ct.c_int, ct.c_int32, ct.c_int64, ct.c_uint32,
+                                                        ct.c_uint64, ct.c_bool)):
+                args.append(t(0))
+            else:
+                args.append(None)
+        assert fn(*args) == mlmc.MLMC_ERR_INVALID_ARG, name
+        assert lib.mlmc_last_error(), name
+        called += 1
+    assert called >= 20
