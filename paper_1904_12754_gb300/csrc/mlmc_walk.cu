@@ -428,14 +428,14 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
   const Meta m0 = load_meta(meta, row);
   const T dl0 = static_cast<T>(m0.dl);
   const T inv_rate0 = static_cast<T>(m0.inv_rate);
-  // Two waves per iteration (with screening) for rows whose walks are short
-  // (t L_row <= 1: few events per walk, the first jump and the end usually
-  // fall in the same iteration); one wave without screening for the others.
-  constexpr int kWays = 2;
-  const bool two_wave = static_cast<T>(m0.inv_rate) >= static_cast<T>(1);
+  // Rows whose walks are short (t L_row <= 1: few events per walk, the
+  // first jump and the end usually fall in the same iteration) are screened;
+  // the others run one event per lane per iteration without screening.
+  constexpr int kWays = 2;  // FP64 screening: walks per lane per round
+  const bool screened_row = static_cast<T>(m0.inv_rate) >= static_cast<T>(1);
   // FP32: a screened walk never jumps exactly when its first uniform's index
   // is <= the row's threshold index (computed once per row with the tables).
-  const int32_t still_max = (FP64 || !two_wave) ? 0 : __ldg(a.still32 + row);
+  const int32_t still_max = (FP64 || !screened_row) ? 0 : __ldg(a.still32 + row);
   // A walk that never jumps stays at the row for the whole interval: its
   // sample is 0 above l0 and v_row e^{dl_row} at l0 (E_f = dl_row exactly
   // as the grid weights sum to 1), the same for every such walk.
@@ -708,7 +708,7 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
   const uint64_t g_end = (rep_base + span + 3) >> 2;
 
   for (;;) {
-    if (two_wave) {
+    if (screened_row) {
       constexpr uint32_t kCap = WarpQueue<FP64>::kCap;
       // Screen first holding times while fewer than 32 walks are queued.
       if constexpr (FP64) {
@@ -901,7 +901,7 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
   // Screened rows: every screened walk that was not queued never jumps
   // (qtail counts the queued ones); other rows count them as they end.
   const unsigned long long still =
-      warp_sum_u64(n_still) + (two_wave ? static_cast<unsigned long long>(span - qtail) : 0ull);
+      warp_sum_u64(n_still) + (screened_row ? static_cast<unsigned long long>(span - qtail) : 0ull);
   const unsigned long long limit = warp_sum_u64(n_limit);
   // Walks that never jump: y_still each (0 above l0 unless a source term
   // adds its fixed Simpson part).
