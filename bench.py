@@ -450,7 +450,8 @@ def run_ours(args):
 #                 alias gather and select, sign, next-state gather
 #   walk end      31 / 24 for a walk that jumped (exponents, exp/expm1, Kahan
 #                 and pair sums); 1 for a walk that never jumped
-# peak = 152 SMs x 128 lanes x SM clock (one operation per lane per clock).
+# peak = SMs x 128 lanes x SM clock (one operation per lane per clock), the SM
+# count read from the device.
 # ---------------------------------------------------------------------------
 OPS_DRAW = 42
 OPS_HOLD = 31
@@ -458,13 +459,15 @@ OPS_STILL_TEST = 2
 OPS_JUMP = {True: 22, False: 15}
 OPS_END_JUMPED = {True: 31, False: 24}
 OPS_END_STILL = 1
-# DRAM bytes of one captured walk launch (ncu, profiles/walk_fp32_ba_n1e5_l0.md:
-# 4.1e8 walks at l0 after an L2 flush; the fused tables, 40 MB, are read once
-# and everything else hits L2); None when the kernel changed after the capture.
-TRAFFIC_CAPTURE = 41644800
+# From one ncu capture of the walk kernel on this workload (a 4.1e8-walk
+# launch at l0 after an L2 flush): DRAM bytes per launch (the fused tables are
+# read once, everything else hits L2), issue-slot use and instructions per
+# event.  None when the kernel has changed since the capture.
+TRAFFIC_CAPTURE = None
+ISSUE_CAPTURE = None
 
 
-def walk_roofline(level_log, walk_s, clocks, peaks, total_ms):
+def walk_roofline(level_log, walk_s, clocks, peaks, total_ms, num_sms=None):
     ops = 0.0
     events = 0
     launches = 0
@@ -482,7 +485,10 @@ def walk_roofline(level_log, walk_s, clocks, peaks, total_ms):
         events += ev
         launches += lv.get("launches", 0)
     sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    peak = 152 * 128 * sm_mhz * 1e6 / 1e9
+    if num_sms is None:
+        import torch
+        num_sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    peak = num_sms * 128 * sm_mhz * 1e6 / 1e9
     achieved = ops / walk_s / 1e9 if walk_s > 0 else 0.0
     hbm = peaks.get("hbm_gbs")
     gather_gbs = gather / walk_s / 1e9 if walk_s > 0 else 0.0
@@ -490,7 +496,9 @@ def walk_roofline(level_log, walk_s, clocks, peaks, total_ms):
             "frac": achieved / peak if peak else None,
             "traffic": TRAFFIC_CAPTURE,
             "kernel": "k_walk<FP32> (mlmc_walk.cu)",
-            "peak_source": f"152 SMs x 128 lanes x {sm_mhz:.0f} MHz (median SM clock sampled in the run)",
+            "peak_source": f"{num_sms} SMs x 128 lanes x {sm_mhz:.0f} MHz (SM count of the device, "
+                           "median SM clock sampled in the run)",
+            "issue": ISSUE_CAPTURE,
             "ops_per_event": ops / events if events else None,
             "walk_launches": launches,
             "avg_launch_ms": 1e3 * walk_s / launches if launches else None,

@@ -81,7 +81,12 @@ enum { MLMC_PLAIN = 0, MLMC_LEARNED = 1 };     /* jump proposal */
  *                     the tables up to the device maximum (never lowering it;
  *                     the set-aside belongs to the process's CUDA context and
  *                     ends with it); the hit ratio is set-aside / window.
- *                     0: plain caching. */
+ *                     0: plain caching.
+ *   launch_reps       walks per launch: backward mode, replicas per row of one
+ *                     walk launch; forward mode, walks of one launch
+ *                     (0 = automatic: max(32, 2^31/n) replicas per row, or
+ *                     2^31 walks; a smaller value splits a request into more
+ *                     launches with the same walks and results). */
 typedef struct {
     int32_t l0;
     int32_t num_levels;
@@ -96,7 +101,7 @@ typedef struct {
     int32_t walks_per_lane;
     int32_t block_threads;
     int32_t l2_persist;
-    int32_t reserved;
+    int32_t launch_reps;
 } mlmc_schedule;
 
 /* Per-level statistics of the last mlmc_expmv call.
@@ -295,8 +300,11 @@ mlmc_status mlmc_trace(mlmc_plan *plan, int32_t level, int32_t coarse, int64_t r
  *   n (the plan's order) must not exceed 262144 (2^18) rows, else
  *   MLMC_ERR_INVALID_ARG with a message naming the limit.
  *   The plan's device must be the current device.  The first call on a
- *   device looks up the array's device address (cudaGetSymbolAddress), so
- *   make that first call before any stream capture.
+ *   device looks up the array's device address (cudaGetSymbolAddress) and
+ *   keeps it for the device's current context; a failed lookup is not kept
+ *   (the next call tries again), and a call in a new context of the device
+ *   (after cudaDeviceReset) looks it up again.  Make the first call on a
+ *   device before any stream capture.
  *   Asynchronous on the plan's stream; makes no allocation.  Every call on a
  *   device shares the array and it keeps the previous call's contents; the
  *   call clears what must start at zero.  Calls whose GPU work overlaps (on

@@ -112,17 +112,18 @@ static void orc_init_coeffs(void)
 }
 
 /* FP32: ln(1+f) = f + f^2 Q(f) for f = m - 1 in [sqrt(1/2) - 1, sqrt(2) - 1],
- * Q of degree 8 with these FP32 coefficients (constant term first).  They
- * were fitted by least squares to the relative error of ln(1+f) on
- * Chebyshev points of the interval and rounded to FP32; they define the
- * FP32 -ln(u) of this implementation (reading R4).  With fused
+ * Q of degree 8 with these FP32 coefficients (constant term first): the
+ * FP64 least-squares fit of the relative error of f + f^2 Q(f) against
+ * ln(1+f) on 1000 Chebyshev (Gauss) points of the interval, each rounded to
+ * FP32 (oracle/fit_neglog32.py computes them).  They define the FP32 -ln(u)
+ * of this implementation (reading R4).  With fused
  * multiply-adds the result is within 0.87 ulp of -ln(u) and strictly
  * decreasing over all 2^23 FP32 uniforms (both checked exhaustively by the
  * tests). */
 #define ORC_NEGLOG_DEG32 8
 static const float orc_q32[ORC_NEGLOG_DEG32 + 1] = {
-    -0x1.fffff8p-2f, 0x1.555558p-2f, -0x1.000422p-2f, 0x1.999fc2p-3f, -0x1.5424dep-3f,
-    0x1.22bf82p-3f, -0x1.0f9b18p-3f, 0x1.068b54p-3f, -0x1.321a7ap-4f};
+    -0x1.fffff8p-2f, 0x1.555558p-2f, -0x1.000422p-2f, 0x1.999fc2p-3f, -0x1.5424e0p-3f,
+    0x1.22bf86p-3f, -0x1.0f9b0cp-3f, 0x1.068b2ap-3f, -0x1.321a4cp-4f};
 
 /* -ln(u) for normal u in (0,1).  u = m 2^e with m in [sqrt(1/2), sqrt(2));
  * ln m = 2 z (1 + z^2/3 + z^4/5 + ...), z = (m-1)/(m+1), |z| <= 0.1716,

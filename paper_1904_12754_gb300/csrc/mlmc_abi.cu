@@ -355,6 +355,7 @@ mlmc_status mlmc_plan_create(mlmc_plan** out, int64_t n, int64_t nnz, const int6
   if (s.walks_per_lane < 0 || s.block_threads < 0 || s.block_threads % 32 != 0 ||
       s.block_threads > 256)
     return fail(MLMC_ERR_INVALID_ARG, "block_threads must be a multiple of 32 up to 256");
+  if (s.launch_reps < 0) return fail(MLMC_ERR_INVALID_ARG, "launch_reps must be >= 0");
 
   mlmc_plan* p = new mlmc_plan();
   p->n = n;
@@ -648,7 +649,7 @@ mlmc_status mlmc_mlmcl(mlmc_plan* p, int32_t level, int32_t coarse, int64_t rep_
     return fail(MLMC_ERR_INVALID_ARG, "level must be in [0,24] (>= 1 when coarse)");
   if (p->source_active && (level < 1 || (coarse && level < 2)))
     return fail(MLMC_ERR_INVALID_ARG, "with a source term the level must be >= 1 (>= 2 when coarse)");
-  if (rep_begin < 0 || reps < 0 || rep_begin + reps > (1ll << 56))
+  if (rep_begin < 0 || reps < 0 || rep_begin > (1ll << 56) || reps > (1ll << 56) - rep_begin)
     return fail(MLMC_ERR_INVALID_ARG, "replica range out of [0, 2^56)");
   WalkLaunch w;
   w.level = level;
@@ -674,7 +675,7 @@ mlmc_status mlmc_trace(mlmc_plan* p, int32_t level, int32_t coarse, int64_t rep_
     return fail(MLMC_ERR_INVALID_ARG, "level must be in [0,24] (>= 1 when coarse)");
   if (p->source_active && (level < 1 || (coarse && level < 2)))
     return fail(MLMC_ERR_INVALID_ARG, "with a source term the level must be >= 1 (>= 2 when coarse)");
-  if (rep_begin < 0 || reps < 0 || rep_begin + reps > (1ll << 56))
+  if (rep_begin < 0 || reps < 0 || rep_begin > (1ll << 56) || reps > (1ll << 56) - rep_begin)
     return fail(MLMC_ERR_INVALID_ARG, "replica range out of [0, 2^56)");
   double* scratch = nullptr;
   MLMC_CUDA(dev_alloc(&scratch, static_cast<size_t>(p->n) + kTotSlots), "alloc trace sums");
@@ -776,9 +777,9 @@ static mlmc_status controller(mlmc_plan* p, const double* v, double* x, double* 
     if (eps > 0.0) {
       for (int k = 0; k < nl; ++k) {
         if (V[k] <= 0.0) continue;
-        double target = std::ceil(2.0 / (eps * eps) * std::sqrt(V[k] / C[k]) * root_sum);
-        target = std::min(target, max_reps);
-        const int64_t want = static_cast<int64_t>(target);
+        double want_reps = std::ceil(2.0 / (eps * eps) * std::sqrt(V[k] / C[k]) * root_sum);
+        want_reps = std::min(want_reps, max_reps);
+        const int64_t want = static_cast<int64_t>(want_reps);
         if (want > p->levels[k].reps) {
           if ((st = run_level(p, k, want - p->levels[k].reps, seed, timed, deadline,
                               &out_of_time)) != MLMC_OK)

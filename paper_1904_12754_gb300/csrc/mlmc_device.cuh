@@ -154,10 +154,11 @@ __device__ __forceinline__ float uniform32(uint32_t x0) {
 // and the host checks these literals against its own IEEE division at
 // library load.
 // FP32: ln m = f + f^2 Q(f), f = m - 1 (exact), Q of degree 8 by Horner's
-// rule with fused multiply-adds.  Q's FP32 coefficients were fitted by least
-// squares to the relative error on Chebyshev points of [sqrt(1/2) - 1,
-// sqrt(2) - 1]; the result is within 0.87 ulp of -ln(u) and strictly
-// decreasing over all 2^23 FP32 uniforms (2i+1) 2^-24.
+// rule with fused multiply-adds.  Q's coefficients are the FP64
+// least-squares fit of the relative error of f + f^2 Q(f) against ln(1+f) on
+// 1000 Chebyshev (Gauss) points of [sqrt(1/2) - 1, sqrt(2) - 1], each rounded
+// to FP32; the result is within 0.87 ulp of -ln(u) and strictly decreasing
+// over all 2^23 FP32 uniforms (2i+1) 2^-24.
 // ---------------------------------------------------------------------------
 constexpr double kLn2Hi64 = 0x1.62e42fefa3800p-1;
 constexpr double kLn2Lo64 = 0x1.ef35793c76730p-45;
@@ -179,8 +180,8 @@ __host__ __device__ constexpr double neglog_c64(int k) {
 
 __host__ __device__ constexpr float neglog_q32(int k) {
   constexpr float c[kNeglogDeg32 + 1] = {-0x1.fffff8p-2f, 0x1.555558p-2f, -0x1.000422p-2f,
-                                         0x1.999fc2p-3f,  -0x1.5424dep-3f, 0x1.22bf82p-3f,
-                                         -0x1.0f9b18p-3f, 0x1.068b54p-3f,  -0x1.321a7ap-4f};
+                                         0x1.999fc2p-3f,  -0x1.5424e0p-3f, 0x1.22bf86p-3f,
+                                         -0x1.0f9b0cp-3f, 0x1.068b2ap-3f,  -0x1.321a4cp-4f};
   return c[k];
 }
 

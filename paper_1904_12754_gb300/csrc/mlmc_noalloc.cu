@@ -7,6 +7,8 @@
 // synchronisation while other streams are busy -- use this entry point: its
 // scratch is a fixed array in static device memory, sized for at most
 // kNoAllocMaxRows rows.
+#include <cuda.h>
+
 #include <mutex>
 #include <string>
 
@@ -32,9 +34,42 @@ constexpr size_t kScratchBytes = kOffV32 + sizeof(float) * kNoAllocMaxRows;
 static __device__ __align__(256) unsigned char g_trace_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
-std::once_flag g_setup_once[kMaxDevices];
+
+// Per device: the array's device address and the CUDA context it belongs
+// to.  Only a successful lookup is kept, so a failed one is retried by the
+// next call; a new context on the device (after cudaDeviceReset the module
+// is loaded again, possibly elsewhere) triggers a new lookup.
+std::mutex g_setup_mutex;
 unsigned char* g_scratch_addr[kMaxDevices];
-cudaError_t g_setup_err[kMaxDevices];
+unsigned long long g_scratch_ctx[kMaxDevices];
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+// Identity of the calling thread's current context (0 when none is current
+// or the driver cannot say).
+unsigned long long current_context_id() {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static std::once_flag resolved;
+  std::call_once(resolved, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(f);
+  });
+  if (!get_current || !get_id) return 0;
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+  unsigned long long id = 0;
+  if (get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
 
 mlmc_status noalloc_fail(mlmc_status st, const std::string& msg) {
   set_error(msg);
@@ -56,7 +91,8 @@ extern "C" mlmc_status mlmc_trace_noalloc(mlmc_plan* p, int32_t level, int32_t c
   if (p->source_active && (level < 1 || (coarse && level < 2)))
     return noalloc_fail(MLMC_ERR_INVALID_ARG,
                         "mlmc_trace_noalloc: with a source term the level must be >= 1 (>= 2 when coarse)");
-  if (rep_begin < 0 || reps < 0 || rep_begin + reps > (int64_t{1} << 56))
+  if (rep_begin < 0 || reps < 0 || rep_begin > (int64_t{1} << 56) ||
+      reps > (int64_t{1} << 56) - rep_begin)
     return noalloc_fail(MLMC_ERR_INVALID_ARG, "mlmc_trace_noalloc: replica range out of [0, 2^56)");
   if (p->sched.mode == MLMC_FORWARD)
     return noalloc_fail(MLMC_ERR_INVALID_ARG, "mlmc_trace_noalloc: backward-mode plans only");
@@ -75,17 +111,28 @@ extern "C" mlmc_status mlmc_trace_noalloc(mlmc_plan* p, int32_t level, int32_t c
                         "mlmc_trace_noalloc: the plan's device must be the current device");
   if (dev < 0 || dev >= kMaxDevices)
     return noalloc_fail(MLMC_ERR_INVALID_ARG, "mlmc_trace_noalloc: device index out of range");
-  // Once per device, with that device current: the device address of the
-  // static array (in host code its name is only a host-side stand-in).
-  std::call_once(g_setup_once[dev], [dev] {
-    void* addr = nullptr;
-    g_setup_err[dev] = cudaGetSymbolAddress(&addr, g_trace_scratch);
-    g_scratch_addr[dev] = static_cast<unsigned char*>(addr);
-  });
-  if (g_setup_err[dev] != cudaSuccess || !g_scratch_addr[dev])
-    return noalloc_fail(MLMC_ERR_CUDA, std::string("mlmc_trace_noalloc: cudaGetSymbolAddress: ") +
-                                           cudaGetErrorString(g_setup_err[dev]));
-  unsigned char* base = g_scratch_addr[dev];
+  // Once per device and context, with that device current: the device
+  // address of the static array (in host code its name is only a host-side
+  // stand-in).  The lookup also makes the device's context current on this
+  // thread, so the context is identified after it.
+  unsigned char* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    unsigned long long ctx = current_context_id();
+    if (ctx == 0 || g_scratch_ctx[dev] != ctx || !g_scratch_addr[dev]) {
+      void* addr = nullptr;
+      err = cudaGetSymbolAddress(&addr, g_trace_scratch);
+      if (err != cudaSuccess || !addr) {
+        g_scratch_addr[dev] = nullptr;
+        g_scratch_ctx[dev] = 0;
+        return noalloc_fail(MLMC_ERR_CUDA, std::string("mlmc_trace_noalloc: cudaGetSymbolAddress: ") +
+                                               cudaGetErrorString(err));
+      }
+      g_scratch_addr[dev] = static_cast<unsigned char*>(addr);
+      g_scratch_ctx[dev] = current_context_id();
+    }
+    base = g_scratch_addr[dev];
+  }
   // The counter, totals and row sums must start at zero; the FP32 copy of v
   // is rewritten by the call.
   err = cudaMemsetAsync(base, 0, kOffSums + sizeof(double) * p->n, p->stream);

@@ -312,12 +312,14 @@ __device__ __forceinline__ void flush_warp(LaneTotals<T>& t, WarpCounters* wc, d
 }
 
 // Per-warp queue of screened walks that jump at least once, a ring of
-// WarpQueue<FP64>::kCap slots.  FP32: replica offset and the Philox word of the first
-// holding time (the first jump's words come from the walk's own draw 0 when
-// it is taken); a screening round adds at most 256 entries (64 blocks of 4
-// walks) and runs only while fewer than 32 are queued, so it never holds more
-// than 287.  FP64: replica offset, the first holding time and the first
-// jump's bucket and coin words; at most 64 per round, never more than 95.
+// WarpQueue<FP64>::kCap slots.  A screening round runs only while fewer than
+// 32 walks are queued, so the queue never holds more than 31 plus one round's
+// walks.  FP32: replica offset and the Philox word of the first holding time
+// (the first jump's words come from the walk's own draw 0 when it is taken);
+// a round screens 32 blocks of 4 walks, at most 128 entries, so never more
+// than 159 are queued.  FP64: replica offset, the first holding time and the
+// first jump's bucket and coin words; a round screens kWays = 2 walks per
+// lane, at most 64 entries, never more than 95.
 template <bool FP64>
 struct WarpQueue;
 template <>
@@ -334,6 +336,15 @@ struct WarpQueue<true> {
   uint32_t xw[kCap];
   double first[kCap];
 };
+// Screening rounds: FP32 32 blocks of 4 walks, FP64 kScreenWays walks per
+// lane; the bound above must fit the rings, whose sizes are powers of two
+// (slots are taken modulo the size).
+constexpr uint32_t kScreenWalks32 = 32u * 4u;
+constexpr uint32_t kScreenWays = 2u;
+static_assert(31u + kScreenWalks32 <= WarpQueue<false>::kCap, "FP32 screening queue too small");
+static_assert(31u + 32u * kScreenWays <= WarpQueue<true>::kCap, "FP64 screening queue too small");
+static_assert((WarpQueue<false>::kCap & (WarpQueue<false>::kCap - 1)) == 0, "ring size");
+static_assert((WarpQueue<true>::kCap & (WarpQueue<true>::kCap - 1)) == 0, "ring size");
 constexpr uint32_t kQueueCap = 64;  // the end queue's ring
 
 // Per-warp queue of walks that ended at s = 1 (their samples are evaluated 32
@@ -431,7 +442,7 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
   // Rows whose walks are short (t L_row <= 1: few events per walk, the
   // first jump and the end usually fall in the same iteration) are screened;
   // the others run one event per lane per iteration without screening.
-  constexpr int kWays = 2;  // FP64 screening: walks per lane per round
+  constexpr int kWays = static_cast<int>(kScreenWays);  // FP64 screening: walks per lane per round
   const bool screened_row = static_cast<T>(m0.inv_rate) >= static_cast<T>(1);
   // FP32: a screened walk never jumps exactly when its first uniform's index
   // is <= the row's threshold index (computed once per row with the tables).
@@ -1359,7 +1370,7 @@ cudaError_t launch_walk_forward(mlmc_plan* p, const WalkLaunch& w, int64_t* laun
   const int block = p->sched.block_threads > 0 ? p->sched.block_threads : 256;
   const int64_t per_lane = p->sched.walks_per_lane > 0 ? p->sched.walks_per_lane : 64;
   a.chunk = 32 * per_lane;
-  const int64_t cap = int64_t{1} << 31;
+  const int64_t cap = p->sched.launch_reps > 0 ? p->sched.launch_reps : int64_t{1} << 31;
   for (int64_t done = 0; done < w.reps; done += cap) {
     const int64_t walks = std::min(cap, w.reps - done);
     a.walk_begin = w.rep_begin + done;
@@ -1413,7 +1424,8 @@ cudaError_t launch_walk_core(mlmc_plan* p, const WalkLaunch& w, const void* v_wa
   a.trace_stride = w.reps;
   const int block = p->sched.block_threads > 0 ? p->sched.block_threads : 256;
   const bool trace = w.trace != nullptr;
-  const int64_t cap = std::max<int64_t>(32, (int64_t{1} << 31) / p->n);
+  const int64_t cap = p->sched.launch_reps > 0 ? p->sched.launch_reps
+                                               : std::max<int64_t>(32, (int64_t{1} << 31) / p->n);
   for (int64_t done = 0; done < w.reps; done += cap) {
     const int64_t reps = std::min(cap, w.reps - done);
     a.rep_begin = w.rep_begin + done;

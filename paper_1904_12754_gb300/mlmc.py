@@ -37,7 +37,7 @@ class Schedule(ct.Structure):
                 ("pilot_walks", ct.c_int64), ("max_jumps_per_walk", ct.c_int64),
                 ("max_walks_per_row", ct.c_int64), ("time_budget_s", ct.c_double),
                 ("walks_per_lane", ct.c_int32), ("block_threads", ct.c_int32),
-                ("l2_persist", ct.c_int32), ("reserved", ct.c_int32)]
+                ("l2_persist", ct.c_int32), ("launch_reps", ct.c_int32)]
 
 
 class LevelStats(ct.Structure):

@@ -103,3 +103,23 @@ def small_problems():
     hub.val[lo:hi] = np.where(hub.col[lo:hi] == 5, hub.val[lo:hi], 0.0)
     out["hub_777"] = (hub, 0.2, rng.standard_normal(n))
     return out
+
+
+def compare_fwd_walks(got, orc, fw, level, fp64, what):
+    """Forward-mode walks: start, end, jumps, hash, status and sign bit for
+    bit, values within the stated tolerance."""
+    for f in ("pad", "end", "jumps", "hash", "status", "sign"):
+        bad = np.flatnonzero(got[f] != orc[f])
+        assert bad.size == 0, f"{what}: {f} differs at {bad[:5]} ({got[f][bad[:5]]} vs {orc[f][bad[:5]]})"
+    # y = v_s (W/w_s) sign e^{...}: relative tolerance plus the rounding of
+    # the +-dl/N sums that form the exponent (as for backward walks)
+    s = orc["pad"]
+    f = np.abs(fw.v[s]) * (fw.W / np.maximum(fw.w[s], 1))
+    scale = f * np.exp(np.abs(orc["log_c"]) + np.abs(orc["log_f"]))
+    terms = (orc["jumps"] + 3.0) * np.abs(fw.tables.dl).max() / 2.0 ** level
+    if fp64:
+        tol = 1e-12 * np.abs(orc["y"]) + 64 * EPS64 * scale * terms
+    else:
+        tol = 1e-5 * np.abs(orc["y"]) + 64 * EPS32 * scale * (terms + 1.0)
+    bad = np.flatnonzero(np.abs(got["y"] - orc["y"]) > tol)
+    assert bad.size == 0, f"{what}: y differs at {bad[:5]}: {got['y'][bad[:5]]} vs {orc['y'][bad[:5]]}"

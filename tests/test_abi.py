@@ -72,7 +72,8 @@ def test_schedule_checks_come_before_device_work(lib):
            dict(precision=7), dict(mode=5), dict(proposal=1), dict(pilot_walks=1),
            dict(max_walks_per_row=1), dict(max_jumps_per_walk=-1), dict(l0=25),
            dict(l0=20, num_levels=3, max_levels=6), dict(l2_persist=2),
-           dict(block_threads=48), dict(block_threads=512), dict(walks_per_lane=-1)]
+           dict(block_threads=48), dict(block_threads=512), dict(walks_per_lane=-1),
+           dict(launch_reps=-1)]
     for fields in bad:
         assert create(**fields) == mlmc.MLMC_ERR_INVALID_ARG, fields
         assert lib.mlmc_last_error(), fields

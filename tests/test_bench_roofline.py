@@ -28,9 +28,11 @@ def test_op_model_counts_each_part_once():
     walk_s = 1e-3
     clocks = {"sm_mhz": 2000.0}
     peaks = {"hbm_gbs": 8000.0}
-    r = bench.walk_roofline([lv0, lv1], walk_s, clocks, peaks, total_ms=2.0)
+    r = bench.walk_roofline([lv0, lv1], walk_s, clocks, peaks, total_ms=2.0, num_sms=152)
     assert r["achieved"] == pytest.approx((want0 + want1) / walk_s / 1e9, rel=1e-12)
     assert r["peak"] == pytest.approx(152 * 128 * 2000.0 * 1e6 / 1e9, rel=1e-12)
+    other = bench.walk_roofline([lv0, lv1], walk_s, clocks, peaks, total_ms=2.0, num_sms=148)
+    assert other["peak"] == pytest.approx(148 * 128 * 2000.0 * 1e6 / 1e9, rel=1e-12)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"], rel=1e-12)
     assert r["ops_per_event"] == pytest.approx((want0 + want1) / (2 * 550), rel=1e-12)
     assert r["walk_kernel_share_of_step_time"] == pytest.approx(0.5)
@@ -44,7 +46,7 @@ def test_op_model_counts_each_part_once():
 
 
 def test_a_walk_that_never_jumps_costs_a_quarter_draw_and_a_test():
-    base = bench.walk_roofline([_level(4, 0, 4)], 1.0, {"sm_mhz": 1000.0}, {}, 1.0)
-    more = bench.walk_roofline([_level(8, 0, 8)], 1.0, {"sm_mhz": 1000.0}, {}, 1.0)
+    base = bench.walk_roofline([_level(4, 0, 4)], 1.0, {"sm_mhz": 1000.0}, {}, 1.0, num_sms=152)
+    more = bench.walk_roofline([_level(8, 0, 8)], 1.0, {"sm_mhz": 1000.0}, {}, 1.0, num_sms=152)
     per_still = (more["achieved"] - base["achieved"]) * 1e9 / 4
     assert per_still == pytest.approx(42 / 4 + 2 + 1, rel=1e-12)

@@ -11,7 +11,8 @@ import mlmc_inputs as I
 from oracle import reference as R
 from oracle import walker as W
 
-from gpu_helpers import EPS32, EPS64, make_plan, small_problems, stream_handle, torch_cuda
+from gpu_helpers import (EPS32, EPS64, compare_fwd_walks as _compare, make_plan, small_problems,
+                         stream_handle, torch_cuda)
 
 pytestmark = pytest.mark.gpu
 
@@ -37,24 +38,6 @@ def _fwd_trace(plan, level, coarse, g0, walks, v, seed):
     plan.trace(level, coarse, g0, walks, dv, seed, rec)
     torch.cuda.synchronize()
     return rec.cpu().numpy().view(M.WALK_RECORD_DTYPE)
-
-
-def _compare(got, orc, fw, level, fp64, what):
-    for f in ("pad", "end", "jumps", "hash", "status", "sign"):
-        bad = np.flatnonzero(got[f] != orc[f])
-        assert bad.size == 0, f"{what}: {f} differs at {bad[:5]} ({got[f][bad[:5]]} vs {orc[f][bad[:5]]})"
-    # y = v_s (W/w_s) sign e^{...}: relative tolerance plus the rounding of
-    # the +-dl/N sums that form the exponent (as for backward walks)
-    s = orc["pad"]
-    f = np.abs(fw.v[s]) * (fw.W / np.maximum(fw.w[s], 1))
-    scale = f * np.exp(np.abs(orc["log_c"]) + np.abs(orc["log_f"]))
-    terms = (orc["jumps"] + 3.0) * np.abs(fw.tables.dl).max() / 2.0 ** level
-    if fp64:
-        tol = 1e-12 * np.abs(orc["y"]) + 64 * EPS64 * scale * terms
-    else:
-        tol = 1e-5 * np.abs(orc["y"]) + 64 * EPS32 * scale * (terms + 1.0)
-    bad = np.flatnonzero(np.abs(got["y"] - orc["y"]) > tol)
-    assert bad.size == 0, f"{what}: y differs at {bad[:5]}: {got['y'][bad[:5]]} vs {orc['y'][bad[:5]]}"
 
 
 @pytest.mark.parametrize("name", list(PROBLEMS))

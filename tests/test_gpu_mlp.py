@@ -48,7 +48,58 @@ def test_forward_matches_oracle(n):
     assert np.all(np.abs(z - zo) <= 2e-3 * (1.0 + np.abs(zo)))
 
 
+def _gradient_bounds(p, x, y):
+    """Per-element error bound of the GPU gradient against the oracle's.
+
+    Every gradient entry is a sum over rows of products; the GPU forms them
+    from BF16 operands with FP32 accumulation, the oracle in FP64 with the
+    same BF16 rounding points.  Two effects separate them:
+      - rounding: FP32 accumulation (relative 2^-24 per add, 2^-16 over a
+        few hundred terms is generous) and a BF16 rounding of dA2 that can
+        land on the other neighbour when the FP32 and FP64 values straddle a
+        rounding boundary (relative 2^-8 on that term): bounded by
+        2^-7 x (the same sum with every term in absolute value);
+      - relu decisions: a pre-activation within rounding of 0 can take the
+        other sign on the GPU, which moves that row's whole term: added in
+        full for those rows (|a| below 1e-5 x the sum of |terms| of a).
+    """
+    q = OM.unpack(p.astype(np.float64))
+    r = OM.round_bf16
+    xb, W1, W2 = r(x), r(q["W1"]), r(q["W2"])
+    a1 = xb @ W1 + q["b1"]
+    s1 = np.abs(xb) @ np.abs(W1) + np.abs(q["b1"])
+    h1 = r(np.maximum(a1, 0.0))
+    a2 = h1 @ W2 + q["b2"]
+    s2 = np.abs(h1) @ np.abs(W2) + np.abs(q["b2"])
+    h2 = np.maximum(a2, 0.0)
+    z = h2 @ q["w3"] + q["b3"][0]
+    B = x.shape[0]
+    dz = 2.0 * (z - y) / B
+    u1 = np.abs(a1) <= 1e-5 * s1          # relu decisions that rounding can flip
+    u2 = np.abs(a2) <= 1e-5 * s2
+    m1, m2 = (a1 > 0) | u1, (a2 > 0) | u2  # every term that may be present
+    da2a = np.abs(np.outer(dz, q["w3"])) * m2
+    dh1a = np.abs(r(da2a)) @ np.abs(W2).T * 1.01
+    da1a = dh1a * m1
+    # rounding part (all terms in absolute value)
+    absg = {"w3": np.abs(h2).T @ np.abs(dz), "b3": np.array([np.abs(dz).sum()]),
+            "W2": np.abs(h1).T @ da2a, "b2": da2a.sum(axis=0),
+            "W1": np.abs(xb).T @ da1a, "b1": da1a.sum(axis=0)}
+    tol = {k: 2.0 ** -7 * v for k, v in absg.items()}
+    # flip part: the full term of each row whose decision is uncertain
+    flip2 = np.abs(np.outer(dz, q["w3"])) * u2
+    tol["W2"] = tol["W2"] + np.abs(h1).T @ flip2
+    tol["b2"] = tol["b2"] + flip2.sum(axis=0)
+    flip1 = dh1a * u1
+    tol["W1"] = tol["W1"] + np.abs(xb).T @ flip1
+    tol["b1"] = tol["b1"] + flip1.sum(axis=0)
+    return OM.pack(tol)
+
+
 def test_gradients_match_oracle():
+    # element by element: every one of the 5,441 parameters' gradient within
+    # its own bound (rounding and relu decisions, _gradient_bounds) of the
+    # oracle's; the bound is far below the gradient for nearly every entry
     torch = torch_cuda()
     from paper_1904_12754_gb300 import mlmc as M
     n = 777
@@ -58,12 +109,19 @@ def test_gradients_match_oracle():
         loss, g = net.loss_grad(_to_device_bf16(x), torch.from_numpy(y).cuda(), n)
     _, lo, go = OM.loss_and_grad(p.astype(np.float64), x, y.astype(np.float64))
     assert abs(loss - lo) <= 1e-3 * abs(lo)
+    tol = _gradient_bounds(p, x, y.astype(np.float64)) + 1e-7
+    g = g.astype(np.float64)
     o = 0
     for name, shape in OM.SIZES:
         size = int(np.prod(shape))
-        a, b = g[o:o + size].astype(np.float64), go[o:o + size]
-        assert np.linalg.norm(a - b) <= 2e-2 * np.linalg.norm(b) + 1e-6, name
+        a, b, t = g[o:o + size], go[o:o + size], tol[o:o + size]
+        bad = np.flatnonzero(np.abs(a - b) > t)
+        assert bad.size == 0, (name, bad[:5], a[bad[:5]], b[bad[:5]], t[bad[:5]])
         o += size
+    # the bound is informative: most entries are held to a small fraction of
+    # their own magnitude
+    big = np.abs(go) > 1e-4
+    assert np.median(tol[big] / np.abs(go[big])) < 0.05
 
 
 def test_training_reduces_loss():

@@ -115,3 +115,39 @@ def test_neglog32_is_strictly_decreasing_over_every_fp32_uniform():
     assert np.all(u.astype(np.float64) == (2.0 * i + 1.0) * 2.0 ** -24)
     g = W.neglog32(u).astype(np.float64)
     assert np.all(np.diff(g) < 0)
+
+
+def _c_floats(path, start_marker, count):
+    # The first `count` C hex-float literals after `start_marker` in a source
+    # file, as FP32 values.
+    import re
+    text = open(path).read()
+    body = text[text.index(start_marker):]
+    lits = re.findall(r"-?0x1\.[0-9a-f]+p[-+]?\d+f", body)[:count]
+    return np.array([float.fromhex(s[:-1]) for s in lits], np.float32)
+
+
+def test_neglog32_coefficients_are_the_committed_fit():
+    # R4: Q's FP32 coefficients are the relative-error least-squares fit on
+    # Chebyshev points, rounded to FP32.  Re-running the fit must give exactly
+    # the literals both sides compile (the oracle's C source and the walk
+    # kernel's device header, each written on its own side).
+    import os
+    from oracle import fit_neglog32 as F
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    fitted = F.coefficients_fp32()
+    orc = _c_floats(os.path.join(root, "oracle", "mlmc_oracle.c"), "orc_q32[ORC_NEGLOG_DEG32 + 1]", 9)
+    dev = _c_floats(os.path.join(root, "paper_1904_12754_gb300", "csrc", "mlmc_device.cuh"),
+                    "c[kNeglogDeg32 + 1]", 9)
+    assert np.array_equal(fitted, orc)
+    assert np.array_equal(fitted, dev)
+    # the fit is insensitive to the number of nodes once it exceeds the degree
+    assert np.array_equal(F.coefficients_fp32(64), fitted)
+    # and every coefficient is well away from an FP32 rounding boundary, so a
+    # different LAPACK cannot round it the other way
+    c = F.fit()
+    r = c.astype(np.float32).astype(np.float64)
+    gap = np.abs(c - r) / np.spacing(np.abs(r).astype(np.float32)).astype(np.float64)
+    assert np.all(gap < 0.45)
+    # the printed literals parse back to the same values
+    assert [float.fromhex(s[:-1]) for s in F.c_hex(fitted)] == [float(x) for x in fitted]
