@@ -287,8 +287,8 @@ static uint32_t orc_threshold(double prob)
  * which keeps the estimator unbiased whatever h > 0 is. */
 static int orc_alias_impl(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
                           const double *L, const int32_t *deg, const float *h, double alpha,
-                          uint32_t *thr, int32_t *keep_col, uint8_t *keep_neg, int32_t *alias_col,
-                          uint8_t *alias_neg, float *lr_keep, float *lr_alias)
+                          const double *lam, uint32_t *thr, int32_t *keep_col, uint8_t *keep_neg,
+                          int32_t *alias_col, uint8_t *alias_neg, float *lr_keep, float *lr_alias)
 {
     int64_t max_deg = 0;
     for (int64_t i = 0; i < n; ++i)
@@ -316,6 +316,8 @@ static int orc_alias_impl(int64_t n, const int64_t *row_ptr, const int32_t *col,
             if (h) hsum = hsum + fabs(val[q]) * (double)h[col[q]];
             ++b;
         }
+        /* clock tilt: every jump out of row i also carries log(L_ii / lambda_i) */
+        double lr_clock = (lam && L[i] > 0.0 && lam[i] > 0.0) ? log(L[i] / lam[i]) : 0.0;
         b = 0;
         for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q) {
             if ((int64_t)col[q] == i) continue;
@@ -325,12 +327,12 @@ static int orc_alias_impl(int64_t n, const int64_t *row_ptr, const int32_t *col,
                 lr[b] = 0.0;
             } else if (!h || !(hsum > 0.0)) {
                 p[b] = (w * (double)k) / L[i];
-                lr[b] = 0.0;
+                lr[b] = lr_clock;
             } else {
                 double kb = w / L[i];
                 double qb = (1.0 - alpha) * ((w * (double)h[col[q]]) / hsum) + alpha * kb;
                 p[b] = qb * (double)k;
-                lr[b] = (qb > 0.0) ? log(kb / qb) : 0.0;
+                lr[b] = ((qb > 0.0) ? log(kb / qb) : 0.0) + lr_clock;
             }
             ++b;
         }
@@ -354,7 +356,7 @@ int orc_alias(int64_t n, const int64_t *row_ptr, const int32_t *col, const doubl
               const double *L, const int32_t *deg, uint32_t *thr, int32_t *keep_col,
               uint8_t *keep_neg, int32_t *alias_col, uint8_t *alias_neg)
 {
-    return orc_alias_impl(n, row_ptr, col, val, L, deg, NULL, 0.0, thr, keep_col, keep_neg,
+    return orc_alias_impl(n, row_ptr, col, val, L, deg, NULL, 0.0, NULL, thr, keep_col, keep_neg,
                           alias_col, alias_neg, NULL, NULL);
 }
 
@@ -363,7 +365,81 @@ int orc_alias_is(int64_t n, const int64_t *row_ptr, const int32_t *col, const do
                  int32_t *keep_col, uint8_t *keep_neg, int32_t *alias_col, uint8_t *alias_neg,
                  float *lr_keep, float *lr_alias)
 {
-    return orc_alias_impl(n, row_ptr, col, val, L, deg, h, alpha, thr, keep_col, keep_neg,
+    return orc_alias_impl(n, row_ptr, col, val, L, deg, h, alpha, NULL, thr, keep_col, keep_neg,
+                          alias_col, alias_neg, lr_keep, lr_alias);
+}
+
+/* ------------------------------------------------------------------ */
+/* Tilted clocks: the h-transform of the walk (importance sampling of  */
+/* the holding times; not in the paper)                                */
+/* ------------------------------------------------------------------ */
+/* Any walk with rates lambda_j > 0 (where row j has off-diagonals), jump
+ * law q and, per jump j -> k, the factor a_jk / (lambda_j q_jk) (sign
+ * included), weighted by exp(int beta (a_XX + lambda_X) ds), has the
+ * expectation of the level-l Strang product of the split
+ *   A = D' - T',  D' = diag(a_ii + lambda_i),  T' = diag(lambda) - (A - diag(a)),
+ * which tends to exp(tA) v like the paper's split (D' = D, T' = T when
+ * lambda = L).  The paper's walk has lambda = L and q = k (Eq. 1, Eq. 12).
+ * The h-transform takes, for h > 0,
+ *   lambda_i = sum_{j != i} |a_ij| h_j / h_i
+ * (clamped to [L_ii / 1024, 4 L_ii]: a faster clock than 4 L_ii would let the
+ * weight grow like e^{t lambda s} where h is poor) and the proposal q of
+ * orc_alias_is,
+ * so that with h = the exact solution the factors of a path telescope to
+ * h(start) / h(end) and the exponent stays near its mean: the variance that
+ * the hubs' holding times give the paper's walk (weight e^{t d_j S} against an
+ * Exp(t L_jj) clock with d = L) disappears.  In the walk this changes only
+ * the tables: rate t lambda_i, dl_i = t (a_ii + lambda_i), and each jump out
+ * of row i adds log(L_ii / lambda_i) to the exponent on top of log(k / q).
+ * The sum over the row runs in stored order with separate multiply and add
+ * (the GPU builds the same tables with the same operations). */
+#define ORC_TILT_MIN (1.0 / 1024.0)
+#define ORC_TILT_MAX 4.0
+
+int orc_tilt_rates(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
+                   const double *L, const float *h, double *lam)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double hsum = 0.0;
+        for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q) {
+            if ((int64_t)col[q] == i) continue;
+            hsum = hsum + fabs(val[q]) * (double)h[col[q]];
+        }
+        if (!(L[i] > 0.0)) {
+            lam[i] = 0.0;
+            continue;
+        }
+        double r = hsum / (double)h[i];
+        double lo = L[i] * ORC_TILT_MIN, hi = L[i] * ORC_TILT_MAX;
+        lam[i] = r < lo ? lo : (r > hi ? hi : r);
+    }
+    return 0;
+}
+
+/* The walk's scaled row quantities for rates lambda (as orc_split does for
+ * lambda = L): rate_i = t lambda_i, dl_i = t (a_ii + lambda_i),
+ * inv_rate_i = 1/rate_i (inf if 0), and their FP32 copies. */
+int orc_tilted_split(int64_t n, double t, const double *a_ii, const double *lam, double *dl,
+                     double *inv_rate, float *inv_rate32, float *dl32)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double rate = t * lam[i];
+        dl[i] = t * (a_ii[i] + lam[i]);
+        inv_rate[i] = (rate > 0.0) ? 1.0 / rate : INFINITY;
+        inv_rate32[i] = (float)inv_rate[i];
+        dl32[i] = (float)dl[i];
+    }
+    return 0;
+}
+
+/* Proposal tables of the h-transform: the jump law of orc_alias_is and, per
+ * entry, lr = log(k/q) + log(L_ii / lambda_i). */
+int orc_alias_tilt(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
+                   const double *L, const int32_t *deg, const float *h, double alpha,
+                   const double *lam, uint32_t *thr, int32_t *keep_col, uint8_t *keep_neg,
+                   int32_t *alias_col, uint8_t *alias_neg, float *lr_keep, float *lr_alias)
+{
+    return orc_alias_impl(n, row_ptr, col, val, L, deg, h, alpha, lam, thr, keep_col, keep_neg,
                           alias_col, alias_neg, lr_keep, lr_alias);
 }
 

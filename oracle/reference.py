@@ -152,23 +152,27 @@ def expmv(a, t: float, v: np.ndarray) -> np.ndarray:
 # ---------------------------------------------------------------------------
 # Strang levels (Eq. 2) and the telescoping corrections (Eq. 8-9)
 # ---------------------------------------------------------------------------
-def _split_sparse(a):
-    """Sparse splitting: returns (d, -T as sparse) of Eq. 1."""
+def _split_sparse(a, lam=None):
+    """Sparse splitting: returns (d, -T as sparse) of Eq. 1.  With ``lam``
+    (the rates of a walk with tilted clocks) the split A = D' - T' with
+    D' = diag(a_ii + lam_i) and -T' = (A - diag(a)) - diag(lam)."""
     a = sp.csr_matrix(a, dtype=np.float64)
     diag = a.diagonal()
     off = a - sp.diags(diag)
     off.eliminate_zeros()
-    lii = np.asarray(abs(off).sum(axis=1)).ravel()
+    lii = np.asarray(abs(off).sum(axis=1)).ravel() if lam is None else np.asarray(lam, float)
     minus_t = (off - sp.diags(lii)).tocsr()      # off-diagonals a_ij, diagonal -L_ii
     return diag + lii, minus_t
 
 
-def strang(a, t: float, v: np.ndarray, level: int) -> np.ndarray:
+def strang(a, t: float, v: np.ndarray, level: int, lam=None) -> np.ndarray:
     """x-bar of Eq. 2 with N = 2^level steps of dt = t/N:
-    apply e^{dt D/2} e^{-dt T} e^{dt D/2} N times to v."""
+    apply e^{dt D/2} e^{-dt T} e^{dt D/2} N times to v.  With ``lam``: the
+    same product for the split of a walk with rates lam (_split_sparse),
+    which is what a walk with tilted clocks estimates at level l."""
     n_steps = 1 << level
     dt = t / n_steps
-    d, minus_t = _split_sparse(a)
+    d, minus_t = _split_sparse(a, lam)
     half = np.exp(dt * d / 2.0)
     dense = None
     if a.shape[0] <= 2048:
@@ -259,10 +263,11 @@ def expmv_source_taylor(a, t: float, f: np.ndarray) -> np.ndarray:
     return expmv_taylor(b, t, e)[:n]
 
 
-def level_means(a, t: float, v: np.ndarray, l0: int, top: int):
+def level_means(a, t: float, v: np.ndarray, l0: int, top: int, lam=None):
     """Exact per-level corrections m_l of Eq. 9 for l = l0..top:
-    m_l0 = x-bar^(l0), m_l = x-bar^(l) - x-bar^(l-1)."""
-    xs = {l: strang(a, t, v, l) for l in range(max(0, l0 - 1) if l0 > 0 else 0, top + 1)}
+    m_l0 = x-bar^(l0), m_l = x-bar^(l) - x-bar^(l-1) (``lam``: the split of
+    a walk with tilted clocks)."""
+    xs = {l: strang(a, t, v, l, lam) for l in range(max(0, l0 - 1) if l0 > 0 else 0, top + 1)}
     out = {l0: xs[l0]}
     for l in range(l0 + 1, top + 1):
         out[l] = xs[l] - xs[l - 1]
@@ -296,16 +301,73 @@ def _functional(kernel: np.ndarray, dl: np.ndarray, c: np.ndarray, g: np.ndarray
     return w
 
 
-def level_moments(a_dense: np.ndarray, t: float, v: np.ndarray, level: int, coarse: bool):
+def tilt_law(a_dense: np.ndarray, h: np.ndarray, alpha: float):
+    """The h-transform walk's law in FP64 (no table rounding): rates
+    lam_i = sum_{j != i} |a_ij| h_j / h_i clamped to [L_ii/1024, 4 L_ii]
+    (0 where L_ii = 0) and jump law q_ij = (1 - alpha) |a_ij| h_j / sum_k
+    |a_ik| h_k + alpha |a_ij| / L_ii (rows with L_ii = 0: zero)."""
+    a = np.asarray(a_dense, dtype=np.float64)
+    off = np.abs(a.copy())
+    np.fill_diagonal(off, 0.0)
+    h = np.asarray(h, dtype=np.float64)
+    lii = off.sum(axis=1)
+    hs = off @ h
+    q = np.zeros_like(off)
+    lam = np.zeros(a.shape[0])
+    rows = lii > 0
+    q[rows] = ((1.0 - alpha) * off[rows] * h[None, :] / hs[rows, None]
+               + alpha * off[rows] / lii[rows, None])
+    lam[rows] = np.clip(hs[rows] / h[rows], lii[rows] / 1024.0, lii[rows] * 4.0)
+    return lam, q
+
+
+def walk_generators(a_dense: np.ndarray, t: float, lam=None, q=None):
+    """Scaled-time generators of a walk with rates lam and jump law q that
+    carries the factor a_jk / (lam_j q_jk) per jump (lam = L, q = k: the
+    paper's walk, generators()): the mean's kernel generator t (N - diag lam)
+    with N the off-diagonal part of A (signed), the second moment's
+    t (R2 - diag lam) with R2_jk = a_jk^2 / (lam_j q_jk) (the squared factor
+    times the jump rate), and dl = t (a_ii + lam_i)."""
+    a = np.asarray(a_dense, dtype=np.float64)
+    n = a.shape[0]
+    off = a.copy()
+    np.fill_diagonal(off, 0.0)
+    if lam is None:
+        lam = np.abs(off).sum(axis=1)
+    if q is None:
+        with np.errstate(divide="ignore", invalid="ignore"):
+            q = np.where(lam[:, None] > 0, np.abs(off) / lam[:, None], 0.0)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        r2 = np.where((off != 0) & (q > 0), off * off / (lam[:, None] * q), 0.0)
+    g1 = t * (off - np.diag(lam))
+    g2 = t * (r2 - np.diag(lam))
+    return g1, g2, t * (np.diag(a) + lam)
+
+
+def level_moments(a_dense: np.ndarray, t: float, v: np.ndarray, level: int, coarse: bool,
+                  lam=None, q=None):
     """Exact (E[Y], E[Y^2]) per start row for the level-``level`` sample of
     Algorithm 2: Y = phi v_{X_N} (e^{E_f} - e^{E_c}) when ``coarse``, else
     phi v_{X_N} e^{E_f}.  The mean uses the signed kernel exp(dt Qs); the
     second moment uses the unsigned exp(dt Q), since phi^2 = 1 and fine and
-    coarse share phi."""
+    coarse share phi.  With ``lam`` and ``q`` the walk has tilted clocks and
+    jumps (walk_generators): the kernels are exp(dt G1) and exp(dt G2)."""
+    if lam is not None or q is not None:
+        g1, g2, dl = walk_generators(a_dense, t, lam, q)
+        n_steps = 1 << level
+        ks = expm_pade13(g1 / n_steps)
+        ku = expm_pade13(g2 / n_steps)
+        return _moments_from_kernels(ks, ku, dl, v, level, coarse)
     q, qs, dl = generators(a_dense, t)
     n_steps = 1 << level
     ks = expm_pade13(qs / n_steps)
     ku = expm_pade13(q / n_steps)
+    return _moments_from_kernels(ks, ku, dl, v, level, coarse)
+
+
+def _moments_from_kernels(ks, ku, dl, v, level: int, coarse: bool):
+    """(E[Y], E[Y^2]) from the one-step kernels of the mean and of the
+    second moment over the N = 2^level grid steps."""
     v = np.asarray(v, dtype=np.float64)
     cf, cc = _weights(level, coarse)
     if not coarse:

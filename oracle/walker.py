@@ -83,6 +83,13 @@ def lib():
         _lib.orc_alias_is.argtypes = [ct.c_int64, P, P, P, P, P, P, ct.c_double, P, P, P, P, P, P,
                                       P]
         _lib.orc_alias_is.restype = ct.c_int
+        _lib.orc_tilt_rates.argtypes = [ct.c_int64, P, P, P, P, P, P]
+        _lib.orc_tilt_rates.restype = ct.c_int
+        _lib.orc_tilted_split.argtypes = [ct.c_int64, ct.c_double, P, P, P, P, P, P]
+        _lib.orc_tilted_split.restype = ct.c_int
+        _lib.orc_alias_tilt.argtypes = [ct.c_int64, P, P, P, P, P, P, ct.c_double, P, P, P, P, P,
+                                        P, P, P]
+        _lib.orc_alias_tilt.restype = ct.c_int
         _lib.orc_walk.argtypes = [ct.POINTER(Ctx), ct.c_int64, ct.c_int64, ct.c_int, ct.c_int,
                                   ct.POINTER(WalkRec)]
         _lib.orc_walk_many.argtypes = [ct.POINTER(Ctx), ct.c_int64, P, P, ct.c_int, ct.c_int, P]
@@ -142,14 +149,19 @@ class Tables:
     alias_neg: np.ndarray
     lr_keep: np.ndarray = None   # proposal tables only: log(k/q) of the kept column
     lr_alias: np.ndarray = None  # ... and of the alias column
+    lam: np.ndarray = None       # tilted clocks only: the walk's rates lambda_i
 
 
-def build_tables(a, t: float, h=None, alpha: float = 0.1) -> Tables:
+def build_tables(a, t: float, h=None, alpha: float = 0.1, clocks: bool = False) -> Tables:
     """Splitting (Eq. 1) and alias tables (Eq. 12) of the CSR matrix ``a``
     for time ``t``.  ``a`` has fields n, row_ptr, col, val.  With ``h`` (n
     positive float32 values) the tables sample the importance-sampling
     proposal q = (1-alpha) |a_ij| h_j / sum + alpha k_ij instead, and record
-    log(k/q) per entry."""
+    log(k/q) per entry.  With ``clocks`` as well, the holding times are
+    tilted too (the h-transform, orc_tilt_rates): the walk's rates are
+    lambda_i = sum_j |a_ij| h_j / h_i (clamped to [L_ii/1024, 4 L_ii]),
+    dl_i = t (a_ii + lambda_i), and every entry of row i also records
+    log(L_ii / lambda_i)."""
     n = a.n
     rp = np.ascontiguousarray(a.row_ptr, dtype=np.int64)
     col = np.ascontiguousarray(a.col, dtype=np.int32)
@@ -170,10 +182,24 @@ def build_tables(a, t: float, h=None, alpha: float = 0.1) -> Tables:
     keep_neg = np.zeros(m, dtype=np.uint8)
     alias_col = np.full(m, -1, dtype=np.int32)
     alias_neg = np.zeros(m, dtype=np.uint8)
+    lam = None
     if h is None:
+        if clocks:
+            raise ValueError("tilted clocks need h")
         rc = lib().orc_alias(n, _p(rp), _p(col), _p(val), _p(L), _p(deg), _p(thr), _p(keep_col),
                              _p(keep_neg), _p(alias_col), _p(alias_neg))
         lr_keep = lr_alias = None
+    elif clocks:
+        hh = np.ascontiguousarray(h, dtype=np.float32)
+        lam = np.zeros(n)
+        lib().orc_tilt_rates(n, _p(rp), _p(col), _p(val), _p(L), _p(hh), _p(lam))
+        lib().orc_tilted_split(n, float(t), _p(a_ii), _p(lam), _p(dl), _p(inv_rate),
+                               _p(inv_rate32), _p(dl32))
+        lr_keep = np.zeros(m, dtype=np.float32)
+        lr_alias = np.zeros(m, dtype=np.float32)
+        rc = lib().orc_alias_tilt(n, _p(rp), _p(col), _p(val), _p(L), _p(deg), _p(hh),
+                                  float(alpha), _p(lam), _p(thr), _p(keep_col), _p(keep_neg),
+                                  _p(alias_col), _p(alias_neg), _p(lr_keep), _p(lr_alias))
     else:
         hh = np.ascontiguousarray(h, dtype=np.float32)
         lr_keep = np.zeros(m, dtype=np.float32)
@@ -184,7 +210,7 @@ def build_tables(a, t: float, h=None, alpha: float = 0.1) -> Tables:
     if rc != 0:
         raise MemoryError("oracle alias build failed")
     return Tables(n, rp, a_ii, L, deg, dl, inv_rate, inv_rate32, dl32, thr, keep_col, keep_neg,
-                  alias_col, alias_neg, lr_keep, lr_alias)
+                  alias_col, alias_neg, lr_keep, lr_alias, lam)
 
 
 class Walker:
@@ -265,9 +291,9 @@ class ForwardWalker(Walker):
     """Forward-mode walks (Eq. 5): tables of A^T, starts drawn ~ |v|."""
 
     def __init__(self, a, t: float, v: np.ndarray, seed: int, precision: int = FP64,
-                 max_jumps: int = 1 << 30, h=None, alpha: float = 0.1):
+                 max_jumps: int = 1 << 30, h=None, alpha: float = 0.1, clocks: bool = False):
         b = transpose(a)
-        tables = build_tables(b, t, h, alpha) if h is not None else build_tables(b, t)
+        tables = build_tables(b, t, h, alpha, clocks) if h is not None else build_tables(b, t)
         super().__init__(b, t, v, seed, precision=precision, max_jumps=max_jumps, tables=tables)
         self.w, self.cdf, self.W = start_weights(v)
 

@@ -100,7 +100,10 @@ def test_launch_and_item_split_together_fp32_l0():
 
 def test_launch_split_row_sums_equal_one_launch():
     # mlmcl per-row sums and totals do not depend on how the request is split
-    # (same walks; sums within rounding of a different addition order)
+    # (same walks, FP32 values; the sums differ only by the rounding of a
+    # different grouping: each lane's FP32 Kahan sum over its walks of an item
+    # is exact to a few FP32 ulps of the item's sum, so 1e-6 of the largest
+    # row sum bounds the difference)
     torch = torch_cuda()
     a, t, v = PROBLEMS["ba_240"]
     res = []
@@ -114,8 +117,8 @@ def test_launch_split_row_sums_equal_one_launch():
             res.append((s.cpu().numpy(), tot.cpu().numpy()))
     (s0, t0), (s1, t1) = res
     assert np.all(t0[1:5] == t1[1:5])
-    assert np.abs(s0 - s1).max() <= 1e-9 * np.abs(s0).max()
-    assert abs(t0[0] - t1[0]) <= 1e-9 * t0[0]
+    assert np.abs(s0 - s1).max() <= 1e-6 * np.abs(s0).max()
+    assert abs(t0[0] - t1[0]) <= 1e-6 * t0[0]
 
 
 @pytest.mark.parametrize("prec", [0, 1])
