@@ -190,6 +190,40 @@ mlmc_status mlmc_plan_rebuild(mlmc_plan *plan);
  * once (the call synchronises the plan's stream to validate it). */
 mlmc_status mlmc_plan_set_proposal(mlmc_plan *plan, const float *h, double alpha);
 
+/* What a proposal tilts (mlmc_plan_set_tilt, mlmc_learn_tilt). */
+enum { MLMC_TILT_JUMPS = 1, MLMC_TILT_CLOCKS = 2 };
+
+/* Proposal with the jumps alone tilted (tilt = MLMC_TILT_JUMPS: exactly
+ * mlmc_plan_set_proposal) or with the holding times tilted as well
+ * (tilt = MLMC_TILT_JUMPS | MLMC_TILT_CLOCKS: the h-transform of the walk;
+ * the paper has no counterpart, its clocks run at the rates L_ii of Sec. 3,
+ * Eq. 12).  With tilted clocks the walk holds row i for an
+ * Exp(t lambda_i) time with
+ *   lambda_i = sum_{j != i} |a_ij| h_j / h_i, clamped to [L_ii/1024, 4 L_ii]
+ * (0 where L_ii = 0), weights its path by exp(t int (a_ii + lambda_X) ds)
+ * instead of exp(t int d_X ds), and every jump out of row i adds
+ * log(L_ii / lambda_i) + log(k/q) to the exponent.  Every level then
+ * estimates, without bias, the Strang product (Eq. 2) of the split
+ * D' = diag(a_ii + lambda_i), T' = diag(lambda) - (A - diag(a)); like the
+ * paper's split it tends to exp(tA)v as the level grows, and the
+ * controller's level corrections and bias test apply unchanged.  With h
+ * close to the solution the path weights nearly telescope to h(start)/h(end):
+ * this removes the variance that long holding times in rows with large
+ * t d_ii give the paper's walk (the hubs of a scale-free graph).  h, alpha
+ * and the synchronisation as mlmc_plan_set_proposal; h = NULL returns to the
+ * plain walk.  Tables: the proposal entries plus row records of the rates
+ * lambda (48 bytes per row and 32 per entry in all). */
+mlmc_status mlmc_plan_set_tilt(mlmc_plan *plan, const float *h, double alpha, int32_t tilt);
+
+/* The tilted clocks' tables (after mlmc_plan_set_tilt with
+ * MLMC_TILT_CLOCKS), as mlmc_export_tables exports the plain ones: lambda,
+ * dl = t (a_ii + lambda), inv_rate = 1/(t lambda) (n doubles), their FP32
+ * copies (n floats), and for FP32 plans the still thresholds of the FP32
+ * walk (n int32; -1 for FP64 plans and rows that are not screened).  Any
+ * pointer may be NULL.  Synchronises. */
+mlmc_status mlmc_export_tilt(const mlmc_plan *plan, double *lam, double *dl, double *inv_rate,
+                             float *inv_rate32, float *dl32, int32_t *still32);
+
 /* Checkpoint and resume of a solve (the paper has no counterpart).  The
  * state of the last mlmc_expmv / mlmc_expmv_entry / mlmc_expmv_sum call is
  * small: per level the row sums of Y, the totals (sum Y^2, jumps, walks) and
@@ -404,6 +438,18 @@ mlmc_status mlmc_mlp_train(mlmc_mlp *mlp, const uint16_t *x, const float *y, int
 mlmc_status mlmc_learn_proposal(mlmc_plan *plan, mlmc_mlp *mlp, const double *v, uint64_t seed,
                                 int64_t pilot_walks, int32_t steps, int32_t batch, float lr,
                                 double alpha, float *final_loss);
+
+/* mlmc_learn_proposal generalised: `tilt` as in mlmc_plan_set_tilt, and
+ * `rounds` (1..8) pilot-train-install rounds, each round after the first
+ * drawing its pilot (walk indices round*pilot_walks onward) with the
+ * proposal installed by the previous one.  With tilted clocks the MLP's
+ * target is 0.5 (log(|x-hat| + 1e-3 max|x-hat|) + log(|v| + 1e-3 max|v|)):
+ * the zero-variance h of a walk at scaled time s is exp((1-s)tA)v, from x at
+ * the start to v at the end, and this is its geometric mean.  final_loss is
+ * the last round's.  Backward-mode plans only. */
+mlmc_status mlmc_learn_tilt(mlmc_plan *plan, mlmc_mlp *mlp, const double *v, uint64_t seed,
+                            int64_t pilot_walks, int32_t steps, int32_t batch, float lr,
+                            double alpha, int32_t tilt, int32_t rounds, float *final_loss);
 
 /* Copy the device tables to host arrays (any pointer may be NULL):
  *   l_ii, dl (= t d_i), inv_rate (1/(t L_ii), +inf when L_ii = 0): n doubles

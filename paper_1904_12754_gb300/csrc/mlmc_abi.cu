@@ -66,7 +66,7 @@ void free_plan(mlmc_plan* p) {
   cudaFree(p->d_val);
   cudaFree(p->d_tables);
   cudaFree(p->d_lii);
-  cudaFree(p->d_alias_is);
+  cudaFree(p->d_is_block);
   cudaFree(p->d_h);
   cudaFree(p->d_src);
   cudaFree(p->d_src32);
@@ -563,20 +563,39 @@ mlmc_status mlmc_plan_set_source(mlmc_plan* p, const double* f) {
 }
 
 mlmc_status mlmc_plan_set_proposal(mlmc_plan* p, const float* h, double alpha) {
+  return mlmc_plan_set_tilt(p, h, alpha, MLMC_TILT_JUMPS);
+}
+
+mlmc_status mlmc_plan_set_tilt(mlmc_plan* p, const float* h, double alpha, int32_t tilt) {
   if (!p) return fail(MLMC_ERR_INVALID_ARG, "NULL plan");
   if (!h) {
     p->proposal_active = false;
+    p->clock_tilt = false;
     p->sched.proposal = MLMC_PLAIN;
     return MLMC_OK;
   }
+  if (tilt != MLMC_TILT_JUMPS && tilt != (MLMC_TILT_JUMPS | MLMC_TILT_CLOCKS))
+    return fail(MLMC_ERR_INVALID_ARG,
+                "mlmc_plan_set_tilt: tilt must be MLMC_TILT_JUMPS or MLMC_TILT_JUMPS | MLMC_TILT_CLOCKS");
   if (p->source_active)
     return fail(MLMC_ERR_INVALID_ARG, "mlmc_plan_set_proposal: the plan has a source term");
   if (!(alpha > 0.0) || !(alpha <= 1.0))
     return fail(MLMC_ERR_INVALID_ARG, "alpha must be in (0, 1]: the proposal mixes in the plain law");
-  if (!p->d_alias_is) {
-    MLMC_CUDA(dev_alloc(&p->d_alias_is, static_cast<size_t>(p->nnz)), "alloc proposal tables");
-    MLMC_CUDA(dev_alloc(&p->d_h, static_cast<size_t>(p->n)), "alloc h");
+  if (!p->d_is_block) {
+    // [proposal entries | Meta32 | Meta64 | still thresholds | lambda]
+    auto up = [](size_t b) { return (b + 255) & ~size_t{255}; };
+    const size_t n = static_cast<size_t>(p->n);
+    const size_t be = up(sizeof(AliasEntryIS) * static_cast<size_t>(p->nnz > 0 ? p->nnz : 1));
+    const size_t b32 = up(sizeof(Meta32) * n), b64 = up(sizeof(Meta64) * n);
+    const size_t bs = up(sizeof(int32_t) * n), bl = up(sizeof(double) * n);
+    MLMC_CUDA(dev_alloc(&p->d_is_block, be + b32 + b64 + bs + bl), "alloc proposal tables");
+    p->d_alias_is = reinterpret_cast<AliasEntryIS*>(p->d_is_block);
+    p->d_meta32_t = reinterpret_cast<Meta32*>(p->d_is_block + be);
+    p->d_meta64_t = reinterpret_cast<Meta64*>(p->d_is_block + be + b32);
+    p->d_still32_t = reinterpret_cast<int32_t*>(p->d_is_block + be + b32 + b64);
+    p->d_lam = reinterpret_cast<double*>(p->d_is_block + be + b32 + b64 + bs);
   }
+  if (!p->d_h) MLMC_CUDA(dev_alloc(&p->d_h, static_cast<size_t>(p->n)), "alloc h");
   MLMC_CUDA(cudaMemcpyAsync(p->d_h, h, sizeof(float) * p->n, cudaMemcpyDefault, p->stream), "copy h");
   // h must be positive and finite on every row (checked on the host copy).
   std::vector<float> hh(p->n);
@@ -587,9 +606,38 @@ mlmc_status mlmc_plan_set_proposal(mlmc_plan* p, const float* h, double alpha) {
     if (!(hh[i] > 0.0f) || !std::isfinite(hh[i]))
       return fail(MLMC_ERR_INVALID_ARG, "h must be positive and finite (row " + std::to_string(i) + ")");
   p->alpha = alpha;
+  p->clock_tilt = (tilt & MLMC_TILT_CLOCKS) != 0;
   MLMC_CUDA(launch_build_is_tables(p), "proposal table build");
   p->proposal_active = true;
   p->sched.proposal = MLMC_LEARNED;
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_export_tilt(const mlmc_plan* pc, double* lam, double* dl, double* inv_rate,
+                             float* inv_rate32, float* dl32, int32_t* still32) {
+  mlmc_plan* p = const_cast<mlmc_plan*>(pc);
+  if (!p) return fail(MLMC_ERR_INVALID_ARG, "NULL plan");
+  if (!p->proposal_active || !p->clock_tilt)
+    return fail(MLMC_ERR_INVALID_ARG, "mlmc_export_tilt: no proposal with tilted clocks on this plan");
+  const size_t n = static_cast<size_t>(p->n);
+  std::vector<Meta32> m32(n);
+  std::vector<Meta64> m64(n);
+  std::vector<double> lm(n);
+  std::vector<int32_t> st(n);
+  MLMC_CUDA(cudaMemcpyAsync(m32.data(), p->d_meta32_t, sizeof(Meta32) * n, cudaMemcpyDeviceToHost, p->stream), "copy");
+  MLMC_CUDA(cudaMemcpyAsync(m64.data(), p->d_meta64_t, sizeof(Meta64) * n, cudaMemcpyDeviceToHost, p->stream), "copy");
+  MLMC_CUDA(cudaMemcpyAsync(lm.data(), p->d_lam, sizeof(double) * n, cudaMemcpyDeviceToHost, p->stream), "copy");
+  if (p->sched.precision != MLMC_FP64)
+    MLMC_CUDA(cudaMemcpyAsync(st.data(), p->d_still32_t, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, p->stream), "copy");
+  MLMC_CUDA(cudaStreamSynchronize(p->stream), "synchronize");
+  for (size_t i = 0; i < n; ++i) {
+    if (lam) lam[i] = lm[i];
+    if (dl) dl[i] = m64[i].dl;
+    if (inv_rate) inv_rate[i] = m64[i].inv_rate;
+    if (inv_rate32) inv_rate32[i] = m32[i].inv_rate;
+    if (dl32) dl32[i] = m32[i].dl;
+    if (still32) still32[i] = p->sched.precision != MLMC_FP64 ? st[i] : -1;
+  }
   return MLMC_OK;
 }
 
@@ -911,7 +959,7 @@ mlmc_status mlmc_plan_save_state(const mlmc_plan* p, void* buf, size_t cap, size
   h.row_count = p->ctl_row_count;
   h.seed = p->ctl_seed;
   h.source = p->source_active ? 1 : 0;
-  h.proposal = p->proposal_active ? 1 : 0;
+  h.proposal = p->proposal_active ? (p->clock_tilt ? 2 : 1) : 0;
   std::memcpy(out, &h, sizeof(h));
   out += sizeof(h);
   for (int k = 0; k < nl; ++k) {
@@ -939,7 +987,7 @@ mlmc_status mlmc_plan_load_state(mlmc_plan* p, const void* buf, size_t bytes) {
     return fail(MLMC_ERR_INVALID_ARG, "mlmc_plan_load_state: not a saved state");
   if (h.n != p->n || h.nnz != p->nnz || h.t != p->t || h.l0 != p->l0 ||
       h.precision != p->sched.precision || h.mode != p->sched.mode ||
-      h.source != (p->source_active ? 1 : 0) || h.proposal != (p->proposal_active ? 1 : 0))
+      h.source != (p->source_active ? 1 : 0) || h.proposal != (p->proposal_active ? (p->clock_tilt ? 2 : 1) : 0))
     return fail(MLMC_ERR_INVALID_ARG,
                 "mlmc_plan_load_state: the plan differs from the saved one (matrix size, t, l0, "
                 "precision, mode, source or proposal)");

@@ -86,9 +86,20 @@ struct mlmc_plan {
   double* d_lii = nullptr;
   mlmc::AliasEntry* d_alias = nullptr;
   double dmax_scaled = 0.0;  // max_i max(|t d_i|, t L_ii)
-  // Importance-sampling proposal (mlmc_plan_set_proposal): when active the
-  // walks use d_alias_is and carry log(k/q) in their exponent.
+  // Importance-sampling proposal (mlmc_plan_set_tilt): when active the
+  // walks use d_alias_is and carry log(k/q) in their exponent; with tilted
+  // clocks (clock_tilt) they also read the row records and FP32 still
+  // thresholds of the rates lambda (d_meta32_t / d_meta64_t / d_still32_t),
+  // and every jump carries log(L/lambda).  One allocation (d_is_block):
+  // [proposal entries | Meta32 | Meta64 | still thresholds | lambda], each
+  // part 256-byte aligned, so the walk's tables form one L2 window.
+  unsigned char* d_is_block = nullptr;
   mlmc::AliasEntryIS* d_alias_is = nullptr;
+  mlmc::Meta32* d_meta32_t = nullptr;
+  mlmc::Meta64* d_meta64_t = nullptr;
+  int32_t* d_still32_t = nullptr;
+  double* d_lam = nullptr;
+  bool clock_tilt = false;
   // Forward mode (the tables above are then built from A^T): start weights,
   // their prefix sums and total, scan scratch.
   int64_t* d_wstart = nullptr;
@@ -160,6 +171,27 @@ int l2_window_attr(const mlmc_plan* p, const void* base, size_t bytes, cudaLaunc
 cudaError_t launch_validate(mlmc_plan* p);
 cudaError_t launch_build_tables(mlmc_plan* p);
 cudaError_t launch_build_is_tables(mlmc_plan* p);
+
+// The row records and FP32 still thresholds the walks of the plan read: the
+// tilted ones when a proposal with tilted clocks is active.
+inline const void* walk_meta(const mlmc_plan* p, bool fp64) {
+  if (p->proposal_active && p->clock_tilt)
+    return fp64 ? static_cast<const void*>(p->d_meta64_t) : static_cast<const void*>(p->d_meta32_t);
+  return fp64 ? static_cast<const void*>(p->d_meta64) : static_cast<const void*>(p->d_meta32);
+}
+inline const int32_t* walk_still32(const mlmc_plan* p) {
+  return (p->proposal_active && p->clock_tilt) ? p->d_still32_t : p->d_still32;
+}
+// The L2 window of proposal walks: their alias entries and row records.
+inline size_t is_window_bytes(const mlmc_plan* p, bool fp64) {
+  const size_t ent = static_cast<size_t>(p->nnz > 0 ? p->nnz : 1);
+  size_t b = (sizeof(AliasEntryIS) * ent + 255) & ~size_t{255};
+  if (p->clock_tilt) {
+    b += (sizeof(Meta32) * static_cast<size_t>(p->n) + 255) & ~size_t{255};
+    if (fp64) b += sizeof(Meta64) * static_cast<size_t>(p->n);
+  }
+  return b;
+}
 
 // Walk kernels (mlmc_walk.cu).  Splits the replica range into launches of at
 // most about 2^31 walks; returns the number of launches in *launches.

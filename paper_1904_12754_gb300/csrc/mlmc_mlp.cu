@@ -396,11 +396,15 @@ __global__ void k_mlp_features(int64_t n, const int64_t* __restrict__ row_ptr,
 }
 
 // log(|x| + eps) targets and, for the proposal, h = exp(z) clamped.
+// y_i = log(|x-hat_i| + floor_x), or, with v, the mean of that and
+// log(|v_i| + floor_v).
 __global__ void k_log_target(int64_t n, const double* __restrict__ xhat, float floor_abs,
-                             float* __restrict__ y) {
+                             const double* __restrict__ v, float floor_v, float* __restrict__ y) {
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
-       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
-    y[i] = logf(fabsf(static_cast<float>(xhat[i])) + floor_abs);
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const float lx = logf(fabsf(static_cast<float>(xhat[i])) + floor_abs);
+    y[i] = v ? 0.5f * (lx + logf(fabsf(static_cast<float>(v[i])) + floor_v)) : lx;
+  }
 }
 
 __global__ void k_exp_h(int64_t n, const float* __restrict__ z, float* __restrict__ h) {
@@ -699,18 +703,36 @@ mlmc_status mlmc_mlp_train(mlmc_mlp* m, const uint16_t* x, const float* y, int64
 
 // Learn a proposal for `plan`: a pilot of `pilot_walks` walks per row at
 // l0 gives per-row estimates x-hat (the method's own statistics); the MLP
-// is trained on features -> log|x-hat|; h = exp(z) becomes the plan's
-// importance-sampling proposal (mlmc_plan_set_proposal with alpha).
+// is trained on features -> a log-value target; h = exp(z) becomes the
+// plan's importance-sampling proposal (mlmc_plan_set_tilt with alpha).
+// Jumps only: target log|x-hat|.  Jumps and clocks (the h-transform): the
+// zero-variance h of a walk at time s is exp((1-s)tA)v, which runs from x at
+// the start to v at the end; its geometric mean over the walk,
+// sqrt(|x-hat| |v|), is the target (0.5 (log|x-hat| + log|v|)).  Each round
+// after the first draws its pilot with the previous round's proposal, whose
+// estimates are less noisy.
 mlmc_status mlmc_learn_proposal(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t seed,
                                 int64_t pilot_walks, int32_t steps, int32_t batch, float lr,
                                 double alpha, float* final_loss) {
-  if (!p || !m || !v || pilot_walks < 1) return mfail(MLMC_ERR_INVALID_ARG, "mlmc_learn_proposal: bad argument");
+  return mlmc_learn_tilt(p, m, v, seed, pilot_walks, steps, batch, lr, alpha, MLMC_TILT_JUMPS, 1,
+                         final_loss);
+}
+
+mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t seed,
+                            int64_t pilot_walks, int32_t steps, int32_t batch, float lr,
+                            double alpha, int32_t tilt, int32_t rounds, float* final_loss) {
+  if (!p || !m || !v || pilot_walks < 1 || rounds < 1 || rounds > 8)
+    return mfail(MLMC_ERR_INVALID_ARG, "mlmc_learn_tilt: bad argument");
+  if (tilt != MLMC_TILT_JUMPS && tilt != (MLMC_TILT_JUMPS | MLMC_TILT_CLOCKS))
+    return mfail(MLMC_ERR_INVALID_ARG, "mlmc_learn_tilt: tilt must be MLMC_TILT_JUMPS or "
+                                       "MLMC_TILT_JUMPS | MLMC_TILT_CLOCKS");
   // The targets are backward value estimates (x-hat per start row); a
   // forward walk's value would be the adjoint problem's.
   if (p->sched.mode != MLMC_BACKWARD)
-    return mfail(MLMC_ERR_INVALID_ARG, "mlmc_learn_proposal: backward-mode plans only");
+    return mfail(MLMC_ERR_INVALID_ARG, "mlmc_learn_tilt: backward-mode plans only");
+  const bool clocks = (tilt & MLMC_TILT_CLOCKS) != 0;
   const bool was = p->proposal_active;
-  p->proposal_active = false;  // the pilot uses the paper's jump law
+  p->proposal_active = false;  // the first pilot uses the paper's jump law
   double* sums = nullptr;
   double* dv = nullptr;
   __nv_bfloat16* feat = nullptr;
@@ -745,31 +767,8 @@ mlmc_status mlmc_learn_proposal(mlmc_plan* p, mlmc_mlp* m, const double* v, uint
   LP_CUDA(cudaMalloc(&h, sizeof(float) * p->n), "alloc");
   LP_CUDA(cudaMalloc(&pv, sizeof(float) * p->n * 5), "alloc");
   LP_CUDA(cudaMemcpyAsync(dv, v, sizeof(double) * p->n, cudaMemcpyDefault, p->stream), "copy v");
-  LP_CUDA(cudaMemsetAsync(sums, 0, sizeof(double) * (p->n + kTotSlots), p->stream), "memset");
-  WalkLaunch w;
-  w.level = p->l0;
-  w.coarse = false;
-  w.rep_begin = 0;
-  w.reps = pilot_walks;
-  w.seed = seed;
-  w.v = dv;
-  w.sum_y = sums;
-  w.totals = sums + p->n;
-  LP_CUDA(launch_walk(p, w), "pilot walks");
-  // x-hat = sums / pilot, in place
-  const double scale = 1.0 / static_cast<double>(pilot_walks);
-  double xmax = 0.0;
-  {
-    std::vector<double> hsum(p->n);
-    LP_CUDA(cudaMemcpyAsync(hsum.data(), sums, sizeof(double) * p->n, cudaMemcpyDeviceToHost, p->stream), "read");
-    LP_CUDA(cudaStreamSynchronize(p->stream), "sync");
-    for (auto& q : hsum) {
-      q *= scale;
-      xmax = std::max(xmax, std::fabs(q));
-    }
-    LP_CUDA(cudaMemcpyAsync(sums, hsum.data(), sizeof(double) * p->n, cudaMemcpyHostToDevice, p->stream), "write");
-  }
   const unsigned g = static_cast<unsigned>(std::min<int64_t>((p->n + 255) / 256, p->num_sms * 8));
+  // Features (fixed over the rounds: they use the paper's jump law).
   k_to_float32<<<g, 256, 0, p->stream>>>(p->n, dv, pv);
   for (int mstep = 1; mstep <= 4; ++mstep)
     k_jump_mean<<<g, 256, 0, p->stream>>>(p->n, p->d_row_ptr, p->d_col, p->d_val, p->d_lii,
@@ -778,24 +777,58 @@ mlmc_status mlmc_learn_proposal(mlmc_plan* p, mlmc_mlp* m, const double* v, uint
                                             pv, pv + p->n, pv + 2 * p->n, pv + 3 * p->n,
                                             pv + 4 * p->n, feat);
   LP_CUDA(cudaGetLastError(), "features");
-  // Targets log(|x-hat| + 1e-3 max|x-hat|): rows the pilot never reached do
-  // not get arbitrarily small h.
-  k_log_target<<<g, 256, 0, p->stream>>>(p->n, sums, static_cast<float>(1e-3 * xmax + 1e-30), y);
-  LP_CUDA(cudaGetLastError(), "targets");
-  LP_CUDA(cudaStreamSynchronize(p->stream), "sync");
-  m->stream = p->stream;
-  mlmc_status st = mlmc_mlp_train(m, reinterpret_cast<const uint16_t*>(feat), y, p->n, steps, batch,
-                                  lr, seed ^ 0xABCDEFull, final_loss);
-  if (st == MLMC_OK) st = forward(m, feat, p->n, z, nullptr, false);
-  if (st == MLMC_OK) st = check_err(m);
-  if (st != MLMC_OK) {
-    cleanup();
-    p->proposal_active = was;
-    return st;
+  double vmax = 0.0;
+  {
+    std::vector<double> hv(p->n);
+    LP_CUDA(cudaMemcpyAsync(hv.data(), dv, sizeof(double) * p->n, cudaMemcpyDeviceToHost, p->stream), "read v");
+    LP_CUDA(cudaStreamSynchronize(p->stream), "sync");
+    for (double q : hv) vmax = std::max(vmax, std::fabs(q));
   }
-  k_exp_h<<<g, 256, 0, p->stream>>>(p->n, z, h);
-  LP_CUDA(cudaGetLastError(), "h");
-  st = mlmc_plan_set_proposal(p, h, alpha);
+  mlmc_status st = MLMC_OK;
+  for (int32_t round = 0; round < rounds; ++round) {
+    LP_CUDA(cudaMemsetAsync(sums, 0, sizeof(double) * (p->n + kTotSlots), p->stream), "memset");
+    WalkLaunch w;
+    w.level = p->l0;
+    w.coarse = false;
+    w.rep_begin = static_cast<int64_t>(round) * pilot_walks;
+    w.reps = pilot_walks;
+    w.seed = seed;
+    w.v = dv;
+    w.sum_y = sums;
+    w.totals = sums + p->n;
+    LP_CUDA(launch_walk(p, w), "pilot walks");
+    // x-hat = sums / pilot, in place
+    const double scale = 1.0 / static_cast<double>(pilot_walks);
+    double xmax = 0.0;
+    {
+      std::vector<double> hsum(p->n);
+      LP_CUDA(cudaMemcpyAsync(hsum.data(), sums, sizeof(double) * p->n, cudaMemcpyDeviceToHost, p->stream), "read");
+      LP_CUDA(cudaStreamSynchronize(p->stream), "sync");
+      for (auto& q : hsum) {
+        q *= scale;
+        xmax = std::max(xmax, std::fabs(q));
+      }
+      LP_CUDA(cudaMemcpyAsync(sums, hsum.data(), sizeof(double) * p->n, cudaMemcpyHostToDevice, p->stream), "write");
+    }
+    // Targets log(|x-hat| + 1e-3 max|x-hat|) (rows the pilot never reached
+    // do not get arbitrarily small h), averaged with log(|v| + 1e-3 max|v|)
+    // for tilted clocks.
+    k_log_target<<<g, 256, 0, p->stream>>>(p->n, sums, static_cast<float>(1e-3 * xmax + 1e-30),
+                                           clocks ? dv : nullptr,
+                                           static_cast<float>(1e-3 * vmax + 1e-30), y);
+    LP_CUDA(cudaGetLastError(), "targets");
+    LP_CUDA(cudaStreamSynchronize(p->stream), "sync");
+    m->stream = p->stream;
+    st = mlmc_mlp_train(m, reinterpret_cast<const uint16_t*>(feat), y, p->n, steps, batch, lr,
+                        seed ^ (0xABCDEFull + static_cast<uint64_t>(round)), final_loss);
+    if (st == MLMC_OK) st = forward(m, feat, p->n, z, nullptr, false);
+    if (st == MLMC_OK) st = check_err(m);
+    if (st != MLMC_OK) break;
+    k_exp_h<<<g, 256, 0, p->stream>>>(p->n, z, h);
+    LP_CUDA(cudaGetLastError(), "h");
+    st = mlmc_plan_set_tilt(p, h, alpha, tilt);
+    if (st != MLMC_OK) break;
+  }
   cleanup();
   if (st != MLMC_OK) p->proposal_active = was;
   return st;

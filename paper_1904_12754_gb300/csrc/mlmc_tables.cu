@@ -158,26 +158,67 @@ __global__ void k_build_tables(int64_t n, double t, const int64_t* __restrict__ 
 // entry also stores lr = log(k/q) of its kept and alias columns.  During the
 // build an entry holds its working probability (bytes 0-7), its FIFO link
 // (bytes 8-11) and its own lr (bytes 16-19, which is also its final lr_keep).
+// Tilted clocks (clocks = true, the h-transform): the row's rate becomes
+//   lambda_i = sum_{j != i} |a_ij| h_j / h_i, clamped to [L_ii/1024, 4 L_ii]
+// (0 where L_ii = 0), its records m32t/m64t get rate t lambda_i and
+// dl_i = t (a_ii + lambda_i) (the split D' = diag(a + lambda),
+// T' = diag(lambda) - N, whose Strang product the walk then estimates), and
+// every entry's lr gains log(L_ii / lambda_i), the clock's likelihood ratio
+// per jump.  The same IEEE operations in the same order as the host
+// definition, so the records are identical bit for bit.
 __global__ void k_build_is_tables(int64_t n, const int64_t* __restrict__ row_ptr,
                                   const int32_t* __restrict__ col, const double* __restrict__ val,
                                   const double* __restrict__ lii, const float* __restrict__ h,
-                                  double alpha, AliasEntryIS* __restrict__ alias) {
+                                  double alpha, AliasEntryIS* __restrict__ alias, bool clocks,
+                                  double t, Meta32* __restrict__ m32t, Meta64* __restrict__ m64t,
+                                  double* __restrict__ lam_out) {
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int64_t rb = row_ptr[i];
     const int64_t re = row_ptr[i + 1];
     int64_t dpos = -1;
-    double hsum = 0.0;
+    double hsum = 0.0, diag = 0.0;
     for (int64_t q = rb; q < re; ++q) {
       if (col[q] == i) {
         dpos = q - rb;
+        diag = val[q];
       } else {
         hsum = __dadd_rn(hsum, __dmul_rn(fabs(val[q]), static_cast<double>(h[col[q]])));
       }
     }
     const int32_t k = static_cast<int32_t>((re - rb) - (dpos >= 0 ? 1 : 0));
-    if (k == 0) continue;
     const double L = lii[i];
+    double lr_clock = 0.0;
+    if (clocks) {
+      double lam = 0.0;
+      if (L > 0.0) {
+        const double r = __ddiv_rn(hsum, static_cast<double>(h[i]));
+        const double lo = __dmul_rn(L, 1.0 / 1024.0);
+        const double hi = __dmul_rn(L, 4.0);
+        lam = r < lo ? lo : (r > hi ? hi : r);
+        lr_clock = lam > 0.0 ? log(L / lam) : 0.0;
+      }
+      const double rate = __dmul_rn(t, lam);
+      const double dl = __dmul_rn(t, __dadd_rn(diag, lam));
+      const double inv_rate =
+          rate > 0.0 ? __ddiv_rn(1.0, rate) : __longlong_as_double(0x7ff0000000000000ll);
+      Meta32 m32;
+      m32.start = static_cast<int32_t>(rb);
+      m32.deg = k;
+      m32.inv_rate = __double2float_rn(inv_rate);
+      m32.dl = __double2float_rn(dl);
+      m32t[i] = m32;
+      Meta64 m64;
+      m64.start = static_cast<int32_t>(rb);
+      m64.deg = k;
+      m64.pad0 = 0;
+      m64.pad1 = 0;
+      m64.inv_rate = inv_rate;
+      m64.dl = dl;
+      m64t[i] = m64;
+      lam_out[i] = lam;
+    }
+    if (k == 0) continue;
     AliasEntryIS* row = alias + rb;
     auto csr_of = [&](int32_t b) -> int64_t { return rb + b + ((dpos >= 0 && b >= dpos) ? 1 : 0); };
     auto col_word = [&](int32_t b) -> uint32_t {
@@ -222,9 +263,10 @@ __global__ void k_build_is_tables(int64_t n, const int64_t* __restrict__ row_ptr
               __dmul_rn(keep_mix, __ddiv_rn(__dmul_rn(w, static_cast<double>(h[col[q]])), hsum)),
               __dmul_rn(alpha, kb));
           p = __dmul_rn(qb, kd);
-          lr = qb > 0.0 ? log(kb / qb) : 0.0;
+          lr = __dadd_rn(qb > 0.0 ? log(kb / qb) : 0.0, lr_clock);
         } else {
           p = __ddiv_rn(__dmul_rn(w, kd), L);
+          lr = lr_clock;
         }
       }
       p_of(b) = p;
@@ -332,8 +374,15 @@ cudaError_t launch_build_tables(mlmc_plan* p) {
 cudaError_t launch_build_is_tables(mlmc_plan* p) {
   constexpr int kBuildBlock = 64;
   k_build_is_tables<<<grid_for(p, p->n, kBuildBlock), kBuildBlock, 0, p->stream>>>(
-      p->n, p->d_row_ptr, p->d_col, p->d_val, p->d_lii, p->d_h, p->alpha, p->d_alias_is);
+      p->n, p->d_row_ptr, p->d_col, p->d_val, p->d_lii, p->d_h, p->alpha, p->d_alias_is,
+      p->clock_tilt, p->t, p->d_meta32_t, p->d_meta64_t, p->d_lam);
   p->launches++;
+  if (p->clock_tilt && p->sched.precision != MLMC_FP64) {
+    const int64_t blocks = (p->n + 7) / 8;
+    const int grid = static_cast<int>(blocks < p->num_sms * 16 ? blocks : p->num_sms * 16);
+    k_still_index<<<grid > 0 ? grid : 1, 256, 0, p->stream>>>(p->n, p->d_meta32_t, p->d_still32_t);
+    p->launches++;
+  }
   return cudaGetLastError();
 }
 

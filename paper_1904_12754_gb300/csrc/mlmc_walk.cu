@@ -1264,7 +1264,7 @@ cudaError_t launch_one(mlmc_plan* p, const WalkArgs& args, int block, cudaStream
   cfg.stream = stream;
   cfg.attrs = attr;
   if (IS)
-    cfg.numAttrs = l2_window_attr(p, p->d_alias_is, sizeof(AliasEntryIS) * static_cast<size_t>(p->nnz), attr);
+    cfg.numAttrs = l2_window_attr(p, p->d_alias_is, is_window_bytes(p, FP64), attr);
   else
     cfg.numAttrs = FP64 ? l2_window_attr(p, p->l2_base64, p->l2_bytes64, attr)
                         : l2_window_attr(p, p->l2_base32, p->l2_bytes32, attr);
@@ -1310,7 +1310,7 @@ cudaError_t launch_fwd_one(mlmc_plan* p, const FwdArgs& args, int block) {
   cfg.stream = p->stream;
   cfg.attrs = attr;
   if (IS)
-    cfg.numAttrs = l2_window_attr(p, p->d_alias_is, sizeof(AliasEntryIS) * static_cast<size_t>(p->nnz), attr);
+    cfg.numAttrs = l2_window_attr(p, p->d_alias_is, is_window_bytes(p, FP64), attr);
   else
     cfg.numAttrs = FP64 ? l2_window_attr(p, p->l2_base64, p->l2_bytes64, attr)
                         : l2_window_attr(p, p->l2_base32, p->l2_bytes32, attr);
@@ -1346,7 +1346,7 @@ cudaError_t launch_walk_forward(mlmc_plan* p, const WalkLaunch& w, int64_t* laun
   if (w.reps <= 0 || p->n <= 0 || p->start_total == 0) return cudaSuccess;
   const bool fp64 = p->sched.precision == MLMC_FP64;
   FwdArgs a{};
-  a.meta = fp64 ? static_cast<const void*>(p->d_meta64) : static_cast<const void*>(p->d_meta32);
+  a.meta = walk_meta(p, fp64);
   a.alias = p->proposal_active ? static_cast<const void*>(p->d_alias_is)
                                : static_cast<const void*>(p->d_fused);
   a.v = w.v;
@@ -1398,11 +1398,11 @@ cudaError_t launch_walk_core(mlmc_plan* p, const WalkLaunch& w, const void* v_wa
                              int64_t per_lane_fixed, cudaStream_t stream, int64_t* launches) {
   const bool fp64 = p->sched.precision == MLMC_FP64;
   WalkArgs a{};
-  a.meta = fp64 ? static_cast<const void*>(p->d_meta64) : static_cast<const void*>(p->d_meta32);
+  a.meta = walk_meta(p, fp64);
   a.alias = p->proposal_active ? static_cast<const void*>(p->d_alias_is)
                                : static_cast<const void*>(p->d_fused);
   a.v_walk = v_walk;
-  a.still32 = p->d_still32;
+  a.still32 = walk_still32(p);
   const bool src = f_walk != nullptr;
   if (src) {
     a.f_walk = f_walk;

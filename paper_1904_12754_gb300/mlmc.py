@@ -20,6 +20,7 @@ MLMC_ERR_NOT_CONVERGED, MLMC_ERR_WALK_LIMIT, MLMC_ERR_NUMERIC = 4, 5, 6
 FP64, FP32_KAHAN = 0, 1
 BACKWARD, FORWARD = 0, 1
 PLAIN, LEARNED = 0, 1
+TILT_JUMPS, TILT_CLOCKS = 1, 2
 
 _STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "NOT_CONVERGED",
            5: "WALK_LIMIT", 6: "NUMERIC"}
@@ -102,6 +103,8 @@ def load(build_if_missing: bool = False):
     lib.mlmc_batch_destroy.argtypes = [P]
     lib.mlmc_batch_destroy.restype = None
     lib.mlmc_plan_set_proposal.argtypes = [P, P, D]
+    lib.mlmc_plan_set_tilt.argtypes = [P, P, D, I32]
+    lib.mlmc_export_tilt.argtypes = [P] + [P] * 6
     lib.mlmc_plan_set_source.argtypes = [P, P]
     lib.mlmc_plan_l2_window.argtypes = [P, ct.POINTER(I64), ct.POINTER(D)]
     lib.mlmc_plan_save_state.argtypes = [P, P, ct.c_size_t, ct.POINTER(ct.c_size_t)]
@@ -117,6 +120,8 @@ def load(build_if_missing: bool = False):
     lib.mlmc_mlp_loss_grad.argtypes = [P, P, P, I64, P, P]
     lib.mlmc_mlp_train.argtypes = [P, P, P, I64, I32, I32, ct.c_float, ct.c_uint64, P]
     lib.mlmc_learn_proposal.argtypes = [P, P, P, ct.c_uint64, I64, I32, I32, ct.c_float, D, P]
+    lib.mlmc_learn_tilt.argtypes = [P, P, P, ct.c_uint64, I64, I32, I32, ct.c_float, D, I32, I32,
+                                    P]
     lib.mlmc_launch_count.argtypes = [P]
     lib.mlmc_launch_count.restype = I64
     for name in ("mlmc_schedule_default", "mlmc_plan_create", "mlmc_plan_rebuild", "mlmc_expmv",
@@ -124,12 +129,13 @@ def load(build_if_missing: bool = False):
                  "mlmc_stats", "mlmc_mlmcl", "mlmc_trace", "mlmc_trace_noalloc",
                  "mlmc_export_tables", "mlmc_batch_create", "mlmc_batch_expmv",
                  "mlmc_batch_stats", "mlmc_batch_info", "mlmc_batch_autotune",
-                 "mlmc_plan_set_proposal", "mlmc_plan_set_source", "mlmc_plan_l2_window",
+                 "mlmc_plan_set_proposal", "mlmc_plan_set_tilt", "mlmc_export_tilt",
+                 "mlmc_plan_set_source", "mlmc_plan_l2_window",
                  "mlmc_plan_save_state", "mlmc_plan_load_state", "mlmc_expmv_resume",
                  "mlmc_export_proposal",
                  "mlmc_mlp_create",
                  "mlmc_mlp_params", "mlmc_mlp_forward", "mlmc_mlp_loss_grad", "mlmc_mlp_train",
-                 "mlmc_learn_proposal",
+                 "mlmc_learn_proposal", "mlmc_learn_tilt",
                  "mlmc_plan_info"):
         getattr(lib, name).restype = ct.c_int
     _lib = lib
@@ -337,6 +343,31 @@ class Plan:
         _check(self._lib.mlmc_plan_set_proposal(self._h, _ptr(h) if h is not None else None,
                                                 float(alpha)))
 
+    def set_tilt(self, h, alpha: float = 0.1, clocks: bool = True):
+        """Proposal with tilted jumps and, with ``clocks``, tilted holding
+        times (the h-transform: rates sum_j |a_ij| h_j / h_i clamped to
+        [L_ii/1024, 4 L_ii]); h as in set_proposal (None = plain walk)."""
+        if isinstance(h, np.ndarray):
+            h = np.ascontiguousarray(h, dtype=np.float32)
+        elif h is not None and hasattr(h, "dtype") and str(h.dtype) != "torch.float32":
+            raise TypeError("h must be float32")
+        if h is not None:
+            _need(h, 4 * self.n, "h")
+        tilt = TILT_JUMPS | (TILT_CLOCKS if clocks else 0)
+        _check(self._lib.mlmc_plan_set_tilt(self._h, _ptr(h) if h is not None else None,
+                                            float(alpha), tilt))
+
+    def export_tilt(self) -> dict:
+        """The tilted clocks' tables: lam, dl, inv_rate (float64), inv_rate32,
+        dl32 (float32), still32 (int32)."""
+        n = self.n
+        out = dict(lam=np.zeros(n), dl=np.zeros(n), inv_rate=np.zeros(n),
+                   inv_rate32=np.zeros(n, np.float32), dl32=np.zeros(n, np.float32),
+                   still32=np.zeros(n, np.int32))
+        keys = ["lam", "dl", "inv_rate", "inv_rate32", "dl32", "still32"]
+        _check(self._lib.mlmc_export_tilt(self._h, *[_ptr(out[k]) for k in keys]))
+        return out
+
     def export_proposal(self) -> dict:
         m = max(self.nnz, 1)
         out = dict(thr=np.zeros(m, np.uint32), keep_col=np.full(m, -1, np.int32),
@@ -515,4 +546,17 @@ class MLP:
         _check(self._lib.mlmc_learn_proposal(plan.handle, self._h, _ptr(v), ct.c_uint64(seed),
                                              pilot_walks, steps, batch, ct.c_float(lr),
                                              float(alpha), _ptr(loss)))
+        return float(loss[0])
+
+    def learn_tilt(self, plan, v, seed: int, pilot_walks: int = 256, steps: int = 300,
+                   batch: int = 8192, lr: float = 3e-3, alpha: float = 0.1,
+                   clocks: bool = True, rounds: int = 2) -> float:
+        """mlmc_learn_tilt: `rounds` pilot-train-install rounds of a proposal
+        with tilted jumps and (clocks) holding times; returns the last loss."""
+        _need(v, 8 * plan.n, "v")
+        loss = np.zeros(1, np.float32)
+        tilt = TILT_JUMPS | (TILT_CLOCKS if clocks else 0)
+        _check(self._lib.mlmc_learn_tilt(plan.handle, self._h, _ptr(v), ct.c_uint64(seed),
+                                         pilot_walks, steps, batch, ct.c_float(lr), float(alpha),
+                                         tilt, rounds, _ptr(loss)))
         return float(loss[0])
