@@ -44,7 +44,8 @@ typedef enum {
     MLMC_ERR_OOM = 3,           /* device allocation failed */
     MLMC_ERR_NOT_CONVERGED = 4, /* budget exhausted; x and stats still written */
     MLMC_ERR_WALK_LIMIT = 5,    /* a walk exceeded max_jumps_per_walk */
-    MLMC_ERR_NUMERIC = 6        /* a non-finite weight was produced */
+    MLMC_ERR_NUMERIC = 6,       /* a non-finite weight was produced */
+    MLMC_ERR_EXCHANGE = 7       /* a sharded solve's exchange callback failed */
 } mlmc_status;
 
 enum { MLMC_FP64 = 0, MLMC_FP32_KAHAN = 1 };   /* walk arithmetic */
@@ -224,6 +225,11 @@ mlmc_status mlmc_plan_set_tilt(mlmc_plan *plan, const float *h, double alpha, in
 mlmc_status mlmc_export_tilt(const mlmc_plan *plan, double *lam, double *dl, double *inv_rate,
                              float *inv_rate32, float *dl32, int32_t *still32);
 
+/* The h of the plan's proposal (n floats, host or device), e.g. to give
+ * every rank of a sharded solve the proposal one rank learned.
+ * Synchronises. */
+mlmc_status mlmc_export_h(const mlmc_plan *plan, float *h);
+
 /* Checkpoint and resume of a solve (the paper has no counterpart).  The
  * state of the last mlmc_expmv / mlmc_expmv_entry / mlmc_expmv_sum call is
  * small: per level the row sums of Y, the totals (sum Y^2, jumps, walks) and
@@ -348,6 +354,52 @@ mlmc_status mlmc_trace_noalloc(mlmc_plan *plan, int32_t level, int32_t coarse, i
                                mlmc_walk_record *rec);
 
 /* ---------------------------------------------------------------------
+ * Sharded solves: one problem over several ranks (one GPU each).  The
+ * paper's MPI runs (Sec. 4, Tables 6-7) give every process its share of the
+ * walks and reduce the level sums between levels; here every rank holds
+ * the whole plan (matrix, tables, proposal) and walks its part of each
+ * level's new walk indices, and the counter-based generator makes a walk's
+ * draws depend only on its index, so the union of the ranks' walks is
+ * exactly the walks a one-rank solve draws.  Before each controller
+ * decision (after the pilot, after each round of top-ups) the per-level row
+ * sums and totals of all ranks are summed by the caller's exchange, and
+ * every rank then takes the same decisions from the same numbers.
+ * --------------------------------------------------------------------- */
+
+/* Sum buf[0..count) over all ranks, in place, on every rank (an
+ * all-reduce of doubles; buf is the buffer given to mlmc_plan_set_shard).
+ * Called by the host thread that runs the solve, after the plan's stream
+ * has been synchronised; it must finish the reduction before it returns.
+ * Return 0 on success; anything else ends the solve with
+ * MLMC_ERR_EXCHANGE. */
+typedef int32_t (*mlmc_exchange_fn)(int64_t count, void *ctx);
+
+/* Doubles the exchange buffer of a sharded plan must hold:
+ * max_levels * (n + 8) + 1.  Returns -1 for a NULL plan. */
+int64_t mlmc_shard_buffer_doubles(const mlmc_plan *plan);
+
+/* The walk indices [*lo, *hi) of `extra` new ones that rank `rank` of
+ * `world` takes: an even split in rank order, the first extra % world ranks
+ * one more.  Host only (no device work). */
+mlmc_status mlmc_shard_range(int64_t extra, int32_t rank, int32_t world, int64_t *lo, int64_t *hi);
+
+/* Make later mlmc_expmv / mlmc_expmv_entry / mlmc_expmv_sum calls of this
+ * plan one rank of a sharded solve (world = 1 or exchange = NULL: back to
+ * an unsharded plan).
+ *   rank, world  0 <= rank < world <= 65536; every rank makes the same
+ *                calls with the same v, seed, schedule and proposal
+ *   exchange     the all-reduce above; ctx is passed to it
+ *   buf, cap     the exchange buffer, host or device memory owned by the
+ *                caller, at least mlmc_shard_buffer_doubles(plan) doubles
+ * Each rank's pilot and top-up walks of a level are its shard_range of the
+ * level's new walk indices.  The time budget is checked at the exchanges
+ * only (a top-up is not cut short) and a rank past its deadline stops every
+ * rank at the next one.  Saved states and mlmc_expmv_resume are not
+ * available on sharded plans.  mlmc_stats reports the whole solve. */
+mlmc_status mlmc_plan_set_shard(mlmc_plan *plan, int32_t rank, int32_t world,
+                                mlmc_exchange_fn exchange, void *ctx, double *buf, int64_t cap);
+
+/* ---------------------------------------------------------------------
  * Batches: many problems solved together.  A problem is a plan with one
  * right-hand side; a plan may appear several times (several right-hand
  * sides of one matrix) and plans may differ in size and in t.
@@ -432,8 +484,8 @@ mlmc_status mlmc_mlp_train(mlmc_mlp *mlp, const uint16_t *x, const float *y, int
 /* Learn and install a proposal: `pilot_walks` walks per row at l0 under the
  * plain law give per-row estimates x-hat; the MLP is trained on per-node
  * features (degree, t L_ii, t d_i, v, k^m v for m = 1..4 with k the jump
- * law, neighbour degree statistics) to predict log(|x-hat| + 1e-3
- * max|x-hat|), and h = exp(MLP) is installed with
+ * law, neighbour degree statistics, and the third-order Taylor value
+ * sum_{m<=3} (t|A|)^m |v| / m!) to predict log(|x-hat| + 1e-3 max|x-hat|), and h = exp(MLP) is installed with
  * mlmc_plan_set_proposal(plan, h, alpha).  v: host or device, n doubles. */
 mlmc_status mlmc_learn_proposal(mlmc_plan *plan, mlmc_mlp *mlp, const double *v, uint64_t seed,
                                 int64_t pilot_walks, int32_t steps, int32_t batch, float lr,
@@ -441,8 +493,8 @@ mlmc_status mlmc_learn_proposal(mlmc_plan *plan, mlmc_mlp *mlp, const double *v,
 
 /* mlmc_learn_proposal generalised: `tilt` as in mlmc_plan_set_tilt, and
  * `rounds` (1..8) pilot-train-install rounds, each round after the first
- * drawing its pilot (walk indices round*pilot_walks onward) with the
- * proposal installed by the previous one.  With tilted clocks the MLP's
+ * drawing a pilot of 4 * pilot_walks walks per row (walk indices after the
+ * earlier rounds' ones) with the proposal installed by the previous one.  With tilted clocks the MLP's
  * target is 0.5 (log(|x-hat| + 1e-3 max|x-hat|) + log(|v| + 1e-3 max|v|)):
  * the zero-variance h of a walk at scaled time s is exp((1-s)tA)v, from x at
  * the start to v at the end, and this is its geometric mean.  final_loss is

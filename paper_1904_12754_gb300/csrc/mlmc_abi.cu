@@ -67,6 +67,7 @@ void free_plan(mlmc_plan* p) {
   cudaFree(p->d_tables);
   cudaFree(p->d_lii);
   cudaFree(p->d_is_block);
+  cudaFree(p->d_glob);
   cudaFree(p->d_h);
   cudaFree(p->d_src);
   cudaFree(p->d_src32);
@@ -147,6 +148,8 @@ static double* totals_of(mlmc_plan* p, int slot) { return p->d_totals + slot * k
 // issued in batches of at most kBatchWalks, with a synchronisation after
 // each, so that a large top-up stops at the wall-clock deadline; *stopped is
 // set when it did.
+// A sharded plan walks only its shard_range of the `extra` new indices (and
+// is never cut short here: the ranks stop together at an exchange).
 static mlmc_status run_level(mlmc_plan* p, int slot, int64_t extra, uint64_t seed,
                              std::vector<char>& timed,
                              std::chrono::steady_clock::time_point deadline, bool* stopped) {
@@ -155,14 +158,18 @@ static mlmc_status run_level(mlmc_plan* p, int slot, int64_t extra, uint64_t see
   const int64_t rows = forward_mode(p) ? 1 : (p->ctl_row_count < 0 ? p->n : p->ctl_row_count);
   const int64_t batch_reps = std::max<int64_t>(32, kBatchWalks / rows);
   if (stopped) *stopped = false;
-  for (int64_t done = 0; done < extra;) {
-    const int64_t reps = std::min(batch_reps, extra - done);
+  int64_t my_lo = 0, my_hi = extra;
+  if (sharded(p)) shard_range(extra, p->shard_rank, p->shard_world, &my_lo, &my_hi);
+  const int64_t base = L.reps;
+  if (sharded(p)) L.reps = base + extra;  // the level's global count
+  for (int64_t done = my_lo; done < my_hi;) {
+    const int64_t reps = std::min(batch_reps, my_hi - done);
     WalkLaunch w;
     w.row_begin = p->ctl_row_begin;
     w.row_count = p->ctl_row_count;
     w.level = p->l0 + slot;
     w.coarse = slot > 0;
-    w.rep_begin = L.reps;
+    w.rep_begin = base + done;
     w.reps = reps;
     w.seed = seed;
     w.v = p->d_v;
@@ -174,10 +181,10 @@ static mlmc_status run_level(mlmc_plan* p, int slot, int64_t extra, uint64_t see
     MLMC_CUDA(launch_any(p, w, &nl), "walk kernel launch");
     MLMC_CUDA(cudaEventRecord(L.ev1, p->stream), "event record");
     L.launches += nl;
-    L.reps += reps;
+    if (!sharded(p)) L.reps += reps;
     done += reps;
     timed[slot] = 1;
-    if (done < extra) {
+    if (done < my_hi && !sharded(p)) {
       // Mid top-up: read this batch's time now and check the deadline.
       MLMC_CUDA(cudaEventSynchronize(L.ev1), "event synchronize");
       float ms = 0.f;
@@ -194,20 +201,60 @@ static mlmc_status run_level(mlmc_plan* p, int slot, int64_t extra, uint64_t see
   return MLMC_OK;
 }
 
+// Sharded plans: sum this rank's row sums and totals of levels 0..nl-1 over
+// the ranks through the caller's exchange (in its buffer: nl x n sums |
+// nl x kTotSlots totals | the deadline vote) into d_glob, and take the
+// vote: some rank is past its deadline.
+static mlmc_status exchange(mlmc_plan* p, int nl, bool past_deadline) {
+  const int64_t n = p->n;
+  const int64_t ns = static_cast<int64_t>(nl) * n;
+  const int64_t nt = static_cast<int64_t>(nl) * kTotSlots;
+  const int64_t count = ns + nt + 1;
+  const double vote = past_deadline ? 1.0 : 0.0;
+  double got_vote = 0.0;
+  MLMC_CUDA(cudaMemcpyAsync(p->exch_buf, p->levels[0].sum_y, sizeof(double) * ns,
+                            cudaMemcpyDefault, p->stream), "exchange: copy sums");
+  MLMC_CUDA(cudaMemcpyAsync(p->exch_buf + ns, p->d_totals, sizeof(double) * nt, cudaMemcpyDefault,
+                            p->stream), "exchange: copy totals");
+  MLMC_CUDA(cudaMemcpyAsync(p->exch_buf + ns + nt, &vote, sizeof(double), cudaMemcpyDefault,
+                            p->stream), "exchange: copy vote");
+  MLMC_CUDA(cudaStreamSynchronize(p->stream), "exchange: synchronize");
+  {
+    NvtxRange range("mlmc exchange");
+    if (p->exch_fn(count, p->exch_ctx) != 0)
+      return fail(MLMC_ERR_EXCHANGE, "the exchange callback of a sharded solve failed");
+  }
+  MLMC_CUDA(cudaMemcpyAsync(p->d_glob, p->exch_buf, sizeof(double) * ns, cudaMemcpyDefault,
+                            p->stream), "exchange: read sums");
+  MLMC_CUDA(cudaMemcpyAsync(p->d_glob + static_cast<int64_t>(p->sched.max_levels) * n,
+                            p->exch_buf + ns, sizeof(double) * nt, cudaMemcpyDefault, p->stream),
+            "exchange: read totals");
+  MLMC_CUDA(cudaMemcpyAsync(&got_vote, p->exch_buf + ns + nt, sizeof(double), cudaMemcpyDefault,
+                            p->stream), "exchange: read vote");
+  MLMC_CUDA(cudaStreamSynchronize(p->stream), "exchange: synchronize");
+  p->shard_stop = got_vote > 0.0;
+  return MLMC_OK;
+}
+
 // Reduce sum_i S_i^2 per level and ||x||^2, and read the scalars back.
-static mlmc_status collect(mlmc_plan* p, int nl, std::vector<HostLevel>& out, double* norm2) {
+static mlmc_status collect(mlmc_plan* p, int nl, std::vector<HostLevel>& out, double* norm2,
+                           bool past_deadline = false) {
+  if (sharded(p)) {
+    mlmc_status st = exchange(p, nl, past_deadline);
+    if (st != MLMC_OK) return st;
+  }
   for (int k = 0; k < nl; ++k) {
-    MLMC_CUDA(cudaMemsetAsync(totals_of(p, k) + kTotSumSq, 0, 2 * sizeof(double), p->stream), "memset");
-    MLMC_CUDA(launch_sum_sumsq(p, p->levels[k].sum_y, p->d_sumpair), "sum");
-    MLMC_CUDA(cudaMemcpyAsync(totals_of(p, k) + kTotSumSq, p->d_sumpair + 1, sizeof(double),
+    MLMC_CUDA(cudaMemsetAsync(level_totals(p, k) + kTotSumSq, 0, 2 * sizeof(double), p->stream), "memset");
+    MLMC_CUDA(launch_sum_sumsq(p, level_sums(p, k), p->d_sumpair), "sum");
+    MLMC_CUDA(cudaMemcpyAsync(level_totals(p, k) + kTotSumSq, p->d_sumpair + 1, sizeof(double),
                               cudaMemcpyDeviceToDevice, p->stream), "copy");
-    MLMC_CUDA(cudaMemcpyAsync(totals_of(p, k) + kTotSum, p->d_sumpair, sizeof(double),
+    MLMC_CUDA(cudaMemcpyAsync(level_totals(p, k) + kTotSum, p->d_sumpair, sizeof(double),
                               cudaMemcpyDeviceToDevice, p->stream), "copy");
     MLMC_CUDA(cudaMemsetAsync(p->d_sumpair, 0, 2 * sizeof(double), p->stream), "memset");
   }
   MLMC_CUDA(launch_finalize(p, nl, nullptr, p->d_norm2), "finalize");
   std::vector<double> h(static_cast<size_t>(nl) * kTotSlots + 1);
-  MLMC_CUDA(cudaMemcpyAsync(h.data(), p->d_totals, sizeof(double) * nl * kTotSlots,
+  MLMC_CUDA(cudaMemcpyAsync(h.data(), level_totals(p, 0), sizeof(double) * nl * kTotSlots,
                             cudaMemcpyDeviceToHost, p->stream), "read totals");
   MLMC_CUDA(cudaMemcpyAsync(h.data() + nl * kTotSlots, p->d_norm2, sizeof(double),
                             cudaMemcpyDeviceToHost, p->stream), "read norm");
@@ -668,6 +715,59 @@ mlmc_status mlmc_export_proposal(const mlmc_plan* pc, uint32_t* thr, int32_t* ke
   return MLMC_OK;
 }
 
+mlmc_status mlmc_export_h(const mlmc_plan* pc, float* h) {
+  mlmc_plan* p = const_cast<mlmc_plan*>(pc);
+  if (!p || !h) return fail(MLMC_ERR_INVALID_ARG, "NULL argument");
+  if (!p->proposal_active) return fail(MLMC_ERR_INVALID_ARG, "mlmc_export_h: no proposal set on this plan");
+  MLMC_CUDA(cudaMemcpyAsync(h, p->d_h, sizeof(float) * p->n, cudaMemcpyDefault, p->stream), "copy h");
+  MLMC_CUDA(cudaStreamSynchronize(p->stream), "synchronize");
+  return MLMC_OK;
+}
+
+int64_t mlmc_shard_buffer_doubles(const mlmc_plan* p) {
+  if (!p) return -1;
+  return static_cast<int64_t>(p->sched.max_levels) * (p->n + kTotSlots) + 1;
+}
+
+mlmc_status mlmc_shard_range(int64_t extra, int32_t rank, int32_t world, int64_t* lo, int64_t* hi) {
+  if (!lo || !hi) return fail(MLMC_ERR_INVALID_ARG, "mlmc_shard_range: NULL argument");
+  if (extra < 0 || world < 1 || world > 65536 || rank < 0 || rank >= world)
+    return fail(MLMC_ERR_INVALID_ARG, "mlmc_shard_range: need extra >= 0 and 0 <= rank < world <= 65536");
+  shard_range(extra, rank, world, lo, hi);
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_plan_set_shard(mlmc_plan* p, int32_t rank, int32_t world, mlmc_exchange_fn exchange,
+                                void* ctx, double* buf, int64_t cap) {
+  if (!p) return fail(MLMC_ERR_INVALID_ARG, "NULL plan");
+  if (world == 1 || !exchange) {
+    p->shard_rank = 0;
+    p->shard_world = 1;
+    p->exch_fn = nullptr;
+    p->exch_ctx = nullptr;
+    p->exch_buf = nullptr;
+    p->exch_cap = 0;
+    return MLMC_OK;
+  }
+  if (world < 1 || world > 65536 || rank < 0 || rank >= world)
+    return fail(MLMC_ERR_INVALID_ARG, "mlmc_plan_set_shard: need 0 <= rank < world <= 65536");
+  if (!buf || cap < mlmc_shard_buffer_doubles(p))
+    return fail(MLMC_ERR_INVALID_ARG, "mlmc_plan_set_shard: the exchange buffer needs " +
+                                          std::to_string(mlmc_shard_buffer_doubles(p)) + " doubles");
+  if (!p->d_glob)
+    MLMC_CUDA(dev_alloc(&p->d_glob, static_cast<size_t>(p->sched.max_levels) *
+                                        static_cast<size_t>(p->n + kTotSlots)),
+              "alloc sharded sums");
+  p->shard_rank = rank;
+  p->shard_world = world;
+  p->exch_fn = exchange;
+  p->exch_ctx = ctx;
+  p->exch_buf = buf;
+  p->exch_cap = cap;
+  p->shard_stop = false;
+  return MLMC_OK;
+}
+
 mlmc_status mlmc_plan_info(const mlmc_plan* p, int64_t* n, int64_t* nnz, int32_t* l0, double* t) {
   if (!p) return fail(MLMC_ERR_INVALID_ARG, "NULL plan");
   if (n) *n = p->n;
@@ -803,9 +903,10 @@ static mlmc_status controller(mlmc_plan* p, const double* v, double* x, double* 
   double norm2 = 0.0;
   bool converged = false;
   mlmc_status result = MLMC_OK;
+  auto past = [&]() { return std::chrono::steady_clock::now() > deadline; };
   for (int iter = 0; iter < 64; ++iter) {
     NvtxRange range("mlmc controller iteration");
-    if ((st = collect(p, nl, h, &norm2)) != MLMC_OK) return st;
+    if ((st = collect(p, nl, h, &norm2, past())) != MLMC_OK) return st;
     auto size_of_x = [&]() {
       if (target == kFull) return std::sqrt(norm2);
       double tsum = 0.0;
@@ -838,7 +939,7 @@ static mlmc_status controller(mlmc_plan* p, const double* v, double* x, double* 
       }
     }
     if (topped) {
-      if ((st = collect(p, nl, h, &norm2)) != MLMC_OK) return st;
+      if ((st = collect(p, nl, h, &norm2, past())) != MLMC_OK) return st;
       eps = p->rel_tol * size_of_x();
     }
     double var = 0.0;
@@ -856,7 +957,8 @@ static mlmc_status controller(mlmc_plan* p, const double* v, double* x, double* 
       converged = true;
       break;
     }
-    if (out_of_time || std::chrono::steady_clock::now() > deadline) break;
+    // Sharded: the ranks stop together, on the vote of the last exchange.
+    if (sharded(p) ? p->shard_stop : (out_of_time || past())) break;
     if (!bias_ok && nl < s.max_levels) {
       if ((st = run_level(p, nl, pilot, seed, timed, deadline, nullptr)) != MLMC_OK)
         return st;
@@ -937,6 +1039,7 @@ mlmc_status mlmc_expmv_sum(mlmc_plan* p, const double* v, double* total, uint64_
 
 mlmc_status mlmc_plan_save_state(const mlmc_plan* p, void* buf, size_t cap, size_t* bytes) {
   if (!p || !bytes) return fail(MLMC_ERR_INVALID_ARG, "NULL argument");
+  if (sharded(p)) return fail(MLMC_ERR_INVALID_ARG, "mlmc_plan_save_state: not available on a sharded plan");
   if (p->ctl_target < 0) return fail(MLMC_ERR_INVALID_ARG, "mlmc_plan_save_state: no solve to save");
   const int nl = p->ctl_nl;
   const size_t need = state_bytes(p, nl);
@@ -980,6 +1083,7 @@ mlmc_status mlmc_plan_save_state(const mlmc_plan* p, void* buf, size_t cap, size
 
 mlmc_status mlmc_plan_load_state(mlmc_plan* p, const void* buf, size_t bytes) {
   if (!p || !buf) return fail(MLMC_ERR_INVALID_ARG, "NULL argument");
+  if (sharded(p)) return fail(MLMC_ERR_INVALID_ARG, "mlmc_plan_load_state: not available on a sharded plan");
   if (bytes < sizeof(StateHeader)) return fail(MLMC_ERR_INVALID_ARG, "mlmc_plan_load_state: truncated state");
   StateHeader h;
   std::memcpy(&h, buf, sizeof(h));
@@ -1031,6 +1135,8 @@ mlmc_status mlmc_plan_load_state(mlmc_plan* p, const void* buf, size_t bytes) {
 }
 
 mlmc_status mlmc_expmv_resume(mlmc_plan* p, double* x) {
+  if (p && sharded(p))
+    return fail(MLMC_ERR_INVALID_ARG, "mlmc_expmv_resume: not available on a sharded plan");
   g_last_error.clear();
   if (!p || !x) return fail(MLMC_ERR_INVALID_ARG, "NULL argument");
   if (p->ctl_target != kFull)

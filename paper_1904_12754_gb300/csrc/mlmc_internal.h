@@ -1,6 +1,7 @@
 // Internal declarations shared by the library's translation units.
 #pragma once
 
+#include <algorithm>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -147,6 +148,20 @@ struct mlmc_plan {
   int32_t ctl_target = -1;
   double last_est_rel_err = 0.0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+  // Sharded solve (mlmc_plan_set_shard): this rank walks its part of every
+  // level's new walk indices; before each controller decision the caller's
+  // exchange sums the per-level row sums and totals over the ranks (in the
+  // caller's buffer exch_buf), and d_glob receives the sums of all ranks:
+  // [max_levels x n row sums | max_levels x kTotSlots totals].
+  int32_t shard_rank = 0;
+  int32_t shard_world = 1;
+  mlmc_exchange_fn exch_fn = nullptr;
+  void* exch_ctx = nullptr;
+  double* exch_buf = nullptr;
+  int64_t exch_cap = 0;
+  double* d_glob = nullptr;
+  bool shard_stop = false;  // the last exchange's vote: a rank is past its deadline
 };
 
 namespace mlmc {
@@ -171,6 +186,24 @@ int l2_window_attr(const mlmc_plan* p, const void* base, size_t bytes, cudaLaunc
 cudaError_t launch_validate(mlmc_plan* p);
 cudaError_t launch_build_tables(mlmc_plan* p);
 cudaError_t launch_build_is_tables(mlmc_plan* p);
+
+// A level's row sums and totals as the controller reads them: this rank's
+// own (unsharded) or the exchanged sums of every rank.
+inline bool sharded(const mlmc_plan* p) { return p->shard_world > 1; }
+inline double* level_sums(const mlmc_plan* p, int slot) {
+  return sharded(p) ? p->d_glob + static_cast<int64_t>(slot) * p->n : p->levels[slot].sum_y;
+}
+inline double* level_totals(const mlmc_plan* p, int slot) {
+  return sharded(p) ? p->d_glob + static_cast<int64_t>(p->sched.max_levels) * p->n + slot * kTotSlots
+                    : p->d_totals + slot * kTotSlots;
+}
+// Rank `rank` of `world` takes new walk indices [lo, hi) of `extra` (an
+// even split, the first extra % world ranks one more).
+inline void shard_range(int64_t extra, int32_t rank, int32_t world, int64_t* lo, int64_t* hi) {
+  const int64_t q = extra / world, r = extra % world;
+  *lo = rank * q + std::min<int64_t>(rank, r);
+  *hi = *lo + q + (rank < r ? 1 : 0);
+}
 
 // The row records and FP32 still thresholds the walks of the plan read: the
 // tilted ones when a proposal with tilted clocks is active.

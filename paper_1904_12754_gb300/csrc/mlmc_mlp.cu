@@ -339,6 +339,33 @@ __global__ void k_jump_mean(int64_t n, const int64_t* __restrict__ row_ptr,
   }
 }
 
+// out = |v| + sum_{m=1..3} (t |A|)^m |v| / m!  (the first Taylor terms of
+// exp(t |A|) |v|: the value of the walks' unsigned weights to order 3),
+// with `term` as scratch (n floats).
+__global__ void k_abs_taylor_step(int64_t n, const int64_t* __restrict__ row_ptr,
+                                  const int32_t* __restrict__ col, const double* __restrict__ val,
+                                  double scale, const float* __restrict__ in,
+                                  float* __restrict__ term_out, float* __restrict__ acc) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    double s = 0.0;
+    for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q)
+      if (col[q] != i) s += fabs(val[q]) * static_cast<double>(in[col[q]]);
+    const float tv = static_cast<float>(scale * s);
+    term_out[i] = tv;
+    acc[i] += tv;
+  }
+}
+
+__global__ void k_abs_float32(int64_t n, const double* __restrict__ in, float* __restrict__ out,
+                              float* __restrict__ acc) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    out[i] = fabsf(static_cast<float>(in[i]));
+    acc[i] = out[i];
+  }
+}
+
 __global__ void k_to_float32(int64_t n, const double* __restrict__ in, float* __restrict__ out) {
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x)
@@ -350,13 +377,14 @@ __global__ void k_to_float32(int64_t n, const double* __restrict__ in, float* __
 // noise.  With k = the jump law and p_m = k^m v (the mean of v after m
 // jumps): 1, log1p(deg), t L_ii, t d_i, v_i, p_1..p_4, neighbour mean and max
 // of log1p(deg), neighbour mean of t d, log(|v|+eps), log(|p_2|+eps),
-// log(|p_4|+eps); eps = 1e-6.
+// log(|p_4|+eps), log(T_3 + eps) with T_3 = sum_{m<=3} (t|A|)^m |v| / m!;
+// eps = 1e-6.
 __global__ void k_mlp_features(int64_t n, const int64_t* __restrict__ row_ptr,
                                const int32_t* __restrict__ col, const Meta64* __restrict__ meta,
                                const double* __restrict__ lii, double t, const float* __restrict__ v,
                                const float* __restrict__ p1, const float* __restrict__ p2,
                                const float* __restrict__ p3, const float* __restrict__ p4,
-                               __nv_bfloat16* __restrict__ x) {
+                               const float* __restrict__ taylor3, __nv_bfloat16* __restrict__ x) {
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     float f[kIn];
@@ -389,7 +417,7 @@ __global__ void k_mlp_features(int64_t n, const int64_t* __restrict__ row_ptr,
     f[12] = logf(fabsf(v[i]) + 1e-6f);
     f[13] = logf(fabsf(p2[i]) + 1e-6f);
     f[14] = logf(fabsf(p4[i]) + 1e-6f);
-    f[15] = 0.f;
+    f[15] = logf(taylor3[i] + 1e-6f);
 #pragma unroll
     for (int k = 0; k < kIn; ++k) x[i * kIn + k] = __float2bfloat16_rn(f[k]);
   }
@@ -739,7 +767,7 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
   float* y = nullptr;
   float* z = nullptr;
   float* h = nullptr;
-  float* pv = nullptr;  // v and k^m v, m = 1..4 (5 x n floats)
+  float* pv = nullptr;  // v, k^m v (m = 1..4), T_3 and two Taylor terms (8 x n floats)
   auto cleanup = [&]() {
     cudaFree(pv);
     cudaFree(sums);
@@ -765,7 +793,7 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
   LP_CUDA(cudaMalloc(&y, sizeof(float) * p->n), "alloc");
   LP_CUDA(cudaMalloc(&z, sizeof(float) * p->n), "alloc");
   LP_CUDA(cudaMalloc(&h, sizeof(float) * p->n), "alloc");
-  LP_CUDA(cudaMalloc(&pv, sizeof(float) * p->n * 5), "alloc");
+  LP_CUDA(cudaMalloc(&pv, sizeof(float) * p->n * 8), "alloc");
   LP_CUDA(cudaMemcpyAsync(dv, v, sizeof(double) * p->n, cudaMemcpyDefault, p->stream), "copy v");
   const unsigned g = static_cast<unsigned>(std::min<int64_t>((p->n + 255) / 256, p->num_sms * 8));
   // Features (fixed over the rounds: they use the paper's jump law).
@@ -773,9 +801,20 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
   for (int mstep = 1; mstep <= 4; ++mstep)
     k_jump_mean<<<g, 256, 0, p->stream>>>(p->n, p->d_row_ptr, p->d_col, p->d_val, p->d_lii,
                                            pv + (mstep - 1) * p->n, pv + mstep * p->n);
+  {
+    float* t3 = pv + 5 * p->n;
+    float* ta = pv + 6 * p->n;
+    float* tb = pv + 7 * p->n;
+    k_abs_float32<<<g, 256, 0, p->stream>>>(p->n, dv, ta, t3);
+    for (int mstep = 1; mstep <= 3; ++mstep) {
+      k_abs_taylor_step<<<g, 256, 0, p->stream>>>(p->n, p->d_row_ptr, p->d_col, p->d_val,
+                                                  p->t / mstep, ta, tb, t3);
+      std::swap(ta, tb);
+    }
+  }
   k_mlp_features<<<g, 256, 0, p->stream>>>(p->n, p->d_row_ptr, p->d_col, p->d_meta64, p->d_lii, p->t,
                                             pv, pv + p->n, pv + 2 * p->n, pv + 3 * p->n,
-                                            pv + 4 * p->n, feat);
+                                            pv + 4 * p->n, pv + 5 * p->n, feat);
   LP_CUDA(cudaGetLastError(), "features");
   double vmax = 0.0;
   {
@@ -790,15 +829,18 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
     WalkLaunch w;
     w.level = p->l0;
     w.coarse = false;
-    w.rep_begin = static_cast<int64_t>(round) * pilot_walks;
-    w.reps = pilot_walks;
+    // Later rounds walk with the previous tilt, whose samples are cheap and
+    // much less noisy: four times the first round's walks per row.
+    const int64_t round_walks = round == 0 ? pilot_walks : 4 * pilot_walks;
+    w.rep_begin = round == 0 ? 0 : pilot_walks + 4 * pilot_walks * (round - 1);
+    w.reps = round_walks;
     w.seed = seed;
     w.v = dv;
     w.sum_y = sums;
     w.totals = sums + p->n;
     LP_CUDA(launch_walk(p, w), "pilot walks");
     // x-hat = sums / pilot, in place
-    const double scale = 1.0 / static_cast<double>(pilot_walks);
+    const double scale = 1.0 / static_cast<double>(round_walks);
     double xmax = 0.0;
     {
       std::vector<double> hsum(p->n);

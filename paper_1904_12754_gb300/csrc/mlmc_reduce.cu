@@ -81,7 +81,7 @@ cudaError_t launch_finalize(mlmc_plan* p, int num_levels, double* x, double* nor
   FinalizeArgs f{};
   for (int k = 0; k < num_levels; ++k) {
     const LevelAcc& L = p->levels[k];
-    f.s[k] = L.sum_y;
+    f.s[k] = level_sums(p, k);
     f.inv_m[k] = L.reps > 0 ? 1.0 / static_cast<double>(L.reps) : 0.0;
   }
   f.count = num_levels;

@@ -17,19 +17,24 @@ from . import build as _build
 
 MLMC_OK, MLMC_ERR_INVALID_ARG, MLMC_ERR_CUDA, MLMC_ERR_OOM = 0, 1, 2, 3
 MLMC_ERR_NOT_CONVERGED, MLMC_ERR_WALK_LIMIT, MLMC_ERR_NUMERIC = 4, 5, 6
+MLMC_ERR_EXCHANGE = 7
 FP64, FP32_KAHAN = 0, 1
 BACKWARD, FORWARD = 0, 1
 PLAIN, LEARNED = 0, 1
 TILT_JUMPS, TILT_CLOCKS = 1, 2
 
 _STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "NOT_CONVERGED",
-           5: "WALK_LIMIT", 6: "NUMERIC"}
+           5: "WALK_LIMIT", 6: "NUMERIC", 7: "EXCHANGE"}
 
 
 class MlmcError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"mlmc {_STATUS.get(status, status)}: {msg}")
         self.status = status
+
+
+# int32_t (*mlmc_exchange_fn)(int64_t count, void *ctx)
+EXCHANGE_FN = ct.CFUNCTYPE(ct.c_int32, ct.c_int64, ct.c_void_p)
 
 
 class Schedule(ct.Structure):
@@ -105,6 +110,11 @@ def load(build_if_missing: bool = False):
     lib.mlmc_plan_set_proposal.argtypes = [P, P, D]
     lib.mlmc_plan_set_tilt.argtypes = [P, P, D, I32]
     lib.mlmc_export_tilt.argtypes = [P] + [P] * 6
+    lib.mlmc_export_h.argtypes = [P, P]
+    lib.mlmc_shard_buffer_doubles.argtypes = [P]
+    lib.mlmc_shard_buffer_doubles.restype = I64
+    lib.mlmc_shard_range.argtypes = [I64, I32, I32, ct.POINTER(I64), ct.POINTER(I64)]
+    lib.mlmc_plan_set_shard.argtypes = [P, I32, I32, P, P, P, I64]  # the exchange as a void*
     lib.mlmc_plan_set_source.argtypes = [P, P]
     lib.mlmc_plan_l2_window.argtypes = [P, ct.POINTER(I64), ct.POINTER(D)]
     lib.mlmc_plan_save_state.argtypes = [P, P, ct.c_size_t, ct.POINTER(ct.c_size_t)]
@@ -130,6 +140,7 @@ def load(build_if_missing: bool = False):
                  "mlmc_export_tables", "mlmc_batch_create", "mlmc_batch_expmv",
                  "mlmc_batch_stats", "mlmc_batch_info", "mlmc_batch_autotune",
                  "mlmc_plan_set_proposal", "mlmc_plan_set_tilt", "mlmc_export_tilt",
+                 "mlmc_export_h", "mlmc_shard_range", "mlmc_plan_set_shard",
                  "mlmc_plan_set_source", "mlmc_plan_l2_window",
                  "mlmc_plan_save_state", "mlmc_plan_load_state", "mlmc_expmv_resume",
                  "mlmc_export_proposal",
@@ -179,6 +190,14 @@ def _ptr(a) -> int:
     if isinstance(a, int):
         return a
     raise TypeError(f"cannot take the address of {type(a)}")
+
+
+def shard_range(extra: int, rank: int, world: int):
+    """The walk indices [lo, hi) of `extra` new ones that rank `rank` of
+    `world` takes in a sharded solve (mlmc_shard_range; no device work)."""
+    lo, hi = ct.c_int64(), ct.c_int64()
+    _check(load().mlmc_shard_range(int(extra), int(rank), int(world), ct.byref(lo), ct.byref(hi)))
+    return lo.value, hi.value
 
 
 def schedule_default(**overrides) -> Schedule:
@@ -356,6 +375,31 @@ class Plan:
         tilt = TILT_JUMPS | (TILT_CLOCKS if clocks else 0)
         _check(self._lib.mlmc_plan_set_tilt(self._h, _ptr(h) if h is not None else None,
                                             float(alpha), tilt))
+
+    def export_h(self) -> np.ndarray:
+        """The h of the plan's proposal (float32, n)."""
+        h = np.zeros(self.n, np.float32)
+        _check(self._lib.mlmc_export_h(self._h, _ptr(h)))
+        return h
+
+    def shard_buffer_doubles(self) -> int:
+        return int(self._lib.mlmc_shard_buffer_doubles(self._h))
+
+    def set_shard(self, rank: int, world: int, exchange=None, buf=None):
+        """Make the plan rank `rank` of a `world`-rank sharded solve.
+        exchange: an EXCHANGE_FN (kept alive by the plan) that sums
+        buf[0:count] over the ranks in place; buf: the exchange buffer (host
+        or device, float64, at least shard_buffer_doubles()).  world = 1 or
+        exchange = None: unsharded."""
+        self._exchange = (exchange, buf)
+        if exchange is None or world == 1:
+            _check(self._lib.mlmc_plan_set_shard(self._h, 0, 1, None, None, None, 0))
+            return
+        _need(buf, 8 * self.shard_buffer_doubles(), "exchange buffer")
+        cap = (buf.numel() if hasattr(buf, "numel") else buf.size)
+        _check(self._lib.mlmc_plan_set_shard(self._h, int(rank), int(world),
+                                             ct.cast(exchange, ct.c_void_p), None, _ptr(buf),
+                                             int(cap)))
 
     def export_tilt(self) -> dict:
         """The tilted clocks' tables: lam, dl, inv_rate (float64), inv_rate32,
