@@ -236,10 +236,14 @@ def run_ours(args):
     t_plan = time.perf_counter() - t_plan
     info = plan.info()
     n = w.a.n
+    exchange = None
+    if dist is not None:
+        from paper_1904_12754_gb300.shard import DistExchange
+        exchange = DistExchange(plan)        # one problem, sharded over the ranks
     dv = torch.from_numpy(w.v).cuda()
     dx = torch.zeros(n, dtype=torch.float64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    seed0 = 1_000_003 * (rank + 1)
+    seed0 = 1_000_003
 
     # table build alone (a1 + a2), for the record
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -249,17 +253,33 @@ def run_ours(args):
     torch.cuda.synchronize()
     table_ms = e0.elapsed_time(e1)
 
-    def step(seed):
-        plan.rebuild()
-        plan.expmv(dv, dx, seed, allow_not_converged=True)
-        levels, est = plan.stats()
-        return levels, est
+    mlp_launches = [0]
 
-    log(f"plan created in {t_plan:.2f} s (table build {table_ms:.2f} ms), l0 = {info['l0']}")
+    def step(seed, v_in, x_out):
+        """One pass of the hot path: tables, learned proposal with tilted
+        clocks (pilot walks, MLP training, proposal tables), the MLMC solve
+        to the tolerance.  Sharded runs learn on every rank and take rank
+        0's h, so that every rank walks the same law."""
+        plan.rebuild()
+        with M.MLP(seed=3, stream=stream.cuda_stream) as net:
+            net.learn_tilt(plan, v_in, seed=seed, pilot_walks=args.pilot, steps=300,
+                           batch=8192, clocks=True, rounds=args.rounds)
+            mlp_launches[0] += net.launch_count()
+        if dist is not None:
+            h = torch.from_numpy(plan.export_h()).cuda()
+            dist.broadcast(h, 0)
+            plan.set_tilt(h, 0.1, clocks=True)
+        rc = plan.expmv(v_in, x_out, seed, allow_not_converged=True)
+        levels, est = plan.stats()
+        plan.set_tilt(None)
+        return rc, levels, est
+
+    log(f"plan created in {t_plan:.2f} s (table build {table_ms:.2f} ms), l0 = {info['l0']}, "
+        f"ranks {world}")
     for k in range(args.warmup):
         t0 = time.perf_counter()
-        step(seed0 + 7919 * (k + 1))
-        log(f"warm-up {k}: {time.perf_counter() - t0:.2f} s")
+        rc, _, est = step(seed0 + 7919 * (k + 1), dv, dx)
+        log(f"warm-up {k}: {time.perf_counter() - t0:.2f} s, rc {rc}, est {est:.3g}")
     torch.cuda.synchronize()
 
     sampler = ClockSampler(local)
@@ -269,15 +289,15 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     launches0 = plan.launch_count()
-    step_ms, events, walk_s, ests, nlevels = [], 0, 0.0, [], []
+    mlp_launches[0] = 0
+    step_ms, events, walk_s, ests, nlevels, conv = [], 0, 0.0, [], [], []
     jumps_total, walks_total = 0, 0
     level_log = []
-    t_wall = time.perf_counter()
     for k in range(args.steps):
         flush.fill_(float(k))  # L2 flush between steps (256 MB write), outside the timing
         ev_s, ev_e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev_s.record(stream)
-        levels, est = step(seed0 + k)
+        rc, levels, est = step(seed0 + k, dv, dx)
         ev_e.record(stream)
         ev_e.synchronize()
         step_ms.append(ev_s.elapsed_time(ev_e))
@@ -288,26 +308,26 @@ def run_ours(args):
             walks_total += walks
             walk_s += lv["seconds"]
             level_log.append(dict(lv, coarse=k_l > 0, walks=walks))
-        log(f"step {k}: {step_ms[-1] / 1e3:.2f} s, levels {len(levels)}, est rel err {est:.2e}")
+        log(f"step {k}: {step_ms[-1] / 1e3:.3f} s, levels {len(levels)}, rc {rc}, "
+            f"est rel err {est:.2e}")
         ests.append(est)
         nlevels.append(len(levels))
-    t_wall = time.perf_counter() - t_wall
-    launches = plan.launch_count() - launches0
+        conv.append(rc == 0)
+    launches = plan.launch_count() - launches0 + mlp_launches[0]
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
     clocks = sampler.stop()
 
     total_ms = float(sum(step_ms))
-    # whole-job aggregate: sum of events over ranks / max time over ranks
-    total_ms_all, events_all = aggregate_over_ranks(dist, total_ms, events, "cuda")
-    value = events_all / (total_ms_all * 1e-3)
-
-    # accuracy of the last step against the FP64 judge (CPU baseline leg)
+    # whole-job aggregate.  Sharded: the walk-steps are counted once (every
+    # rank's stats describe the whole solve), the time is the slowest rank's.
+    total_ms_all, _ = aggregate_over_ranks(dist, total_ms, events, "cuda")
+    value = events / (total_ms_all * 1e-3)
     x_last = dx.cpu().numpy()
 
-    # end to end through the public API with host buffers (pinned): the
-    # library copies v in and x out inside mlmc_expmv.
+    # end to end through the public API with host buffers (pinned): v is
+    # copied in by the learning and the solve, x out by the solve
     vh = torch.from_numpy(w.v.copy()).pin_memory()
     xh = torch.zeros(n, dtype=torch.float64).pin_memory()
     if dist is not None:
@@ -316,65 +336,34 @@ def run_ours(args):
     e2e_events = 0
     t_e2e = time.perf_counter()
     for k in range(args.steps):
-        plan.rebuild()
-        plan.expmv(vh, xh, seed0 + 500 + k, allow_not_converged=True)
-        levels, _ = plan.stats()
+        _, levels, _ = step(seed0 + 500 + k, vh, xh)
         e2e_events += sum(lv["walks_per_row"] * n + lv["jumps"] for lv in levels)
     t_e2e = time.perf_counter() - t_e2e
-    e2e_value = e2e_events / t_e2e
     log(f"e2e: {t_e2e:.2f} s for {args.steps} step(s)")
-    t_e2e_all, e2e_events_all = aggregate_over_ranks(dist, t_e2e, e2e_events, "cuda")
-    e2e_value = e2e_events_all / t_e2e_all
+    t_e2e_all, _ = aggregate_over_ranks(dist, t_e2e, e2e_events, "cuda")
+    e2e_value = e2e_events / t_e2e_all
 
     peaks, peak_kind = _peaks()
-    roof = walk_roofline(level_log, walk_s, clocks, peaks, total_ms)
+    roof = walk_roofline(level_log, walk_s, clocks, peaks, total_ms, proposal=True)
 
-    # Learned proposal on the same workload and budget: per-walk variance at
-    # l0 and the error estimate one budget-bounded solve reaches.
-    var_plain, _ = _level0_variance(plan, dv, 256, 1234)
-    t0 = time.perf_counter()
-    with M.MLP(seed=3, stream=stream.cuda_stream) as net:
-        train_loss = net.learn_proposal(plan, dv, seed=99, pilot_walks=64, steps=300, batch=8192)
-    torch.cuda.synchronize()
-    t_learn = time.perf_counter() - t0
-    var_learned, _ = _level0_variance(plan, dv, 256, 1234)
-    sec_l, est_l, _, ev_l = _timed_solve(plan, dv, dx, seed0 + 777)
-    plan.set_proposal(None)
-    learned = {"level0_var_per_walk_plain": var_plain, "level0_var_per_walk_learned": var_learned,
-               "variance_ratio": var_learned / var_plain, "learn_seconds": t_learn,
-               "train_loss": train_loss, "step_seconds": sec_l, "est_rel_err": est_l,
-               "plain_est_rel_err_same_budget": float(np.mean(ests)),
-               "walk_steps_per_s": ev_l / sec_l}
-    log(f"learned proposal: variance ratio {var_learned / var_plain:.3f}, est err {est_l:.3g}")
+    # The plain walk on the same plan and budget: its error estimate after
+    # the budget, and the time 1e-3 would take at its measured variance
+    # (the error falls like 1/sqrt(time)).
+    sched_p = M.schedule_default(precision=M.FP32_KAHAN if w.precision == "fp32" else M.FP64,
+                                 num_levels=w.num_levels, max_levels=10, pilot_walks=64,
+                                 time_budget_s=args.plain_budget)
+    with M.Plan.from_csr(w.a, w.t, sched_p, rel_tol=w.tol, stream=stream.cuda_stream) as plan_p:
+        if exchange is not None:
+            exchange.attach(plan_p)
+        sec_p, est_p, conv_p, ev_p = _timed_solve(plan_p, dv, dx, seed0 + 777)
+    plain = {"budget_s": args.plain_budget, "seconds": sec_p, "est_rel_err": est_p,
+             "converged": conv_p, "walk_steps_per_s": ev_p / sec_p,
+             "projected_time_to_tol_s": sec_p * (est_p / w.tol) ** 2,
+             "projection": "seconds x (est_rel_err / tol)^2 at the measured variance"}
+    log(f"plain: {sec_p:.2f} s, est {est_p:.3g}, projected {plain['projected_time_to_tol_s']:.3g} s")
 
-    # Time to tolerance on the same graph with beta = 1/d_max (Sec. 5).
-    t_dmax = 1.0 / w.extra["d_max"]
-    sched_d = M.schedule_default(precision=M.FP32_KAHAN, num_levels=w.num_levels, max_levels=10,
-                                 pilot_walks=64, time_budget_s=120.0)
-    plan_d = M.Plan.from_csr(w.a, t_dmax, sched_d, rel_tol=w.tol, stream=stream.cuda_stream)
-    dx_d = torch.zeros(n, dtype=torch.float64, device="cuda")
-    tt, tt_events, tt_est, tt_conv = [], [], [], []
-    for k in range(4):
-        ev_s, ev_e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        flush.fill_(float(k))
-        ev_s.record(stream)
-        plan_d.rebuild()
-        rc = plan_d.expmv(dv, dx_d, seed0 + 900 + k, allow_not_converged=True)
-        ev_e.record(stream)
-        ev_e.synchronize()
-        lv_d, est_d = plan_d.stats()
-        if k == 0:
-            continue  # warm-up
-        tt.append(ev_s.elapsed_time(ev_e) / 1e3)
-        tt_events.append(sum(lv["walks_per_row"] * n + lv["jumps"] for lv in lv_d))
-        tt_est.append(est_d)
-        tt_conv.append(rc == 0)
-    x_dmax = dx_d.cpu().numpy()
-    plan_d.close()
-    log(f"time to 1e-3 at beta=1/d_max: {statistics.median(tt):.4f} s")
     cpu = None
     err = None
-    err_dmax = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import reference as R
         cv, cores, sample = _oracle_sample(w, info["l0"], seconds=args.ref_seconds)
@@ -384,37 +373,31 @@ def run_ours(args):
         ref = R.expmv_taylor(w.a.scipy(), w.t, w.v)
         t_ref = time.perf_counter() - t_ref
         err = float(np.linalg.norm(x_last - ref) / np.linalg.norm(ref))
-        ref_d = R.expmv_taylor(w.a.scipy(), t_dmax, w.v)
-        err_dmax = float(np.linalg.norm(x_dmax - ref_d) / np.linalg.norm(ref_d))
         cpu = {"value": cv, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
-               "fp64_reference_s": t_ref, "single_thread_value": cv1, "single_thread_sample": sample1}
+               "fp64_reference_s": t_ref, "single_thread_value": cv1,
+               "single_thread_sample": sample1}
 
     if rank == 0:
+        tt = [ms / 1e3 for ms in step_ms]
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
+            "higher_is_better": True, "scaling": "strong" if world > 1 else "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w.name, "n": n, "nnz": w.a.nnz, "t": w.t,
                        "lambda_max": w.extra.get("lambda_max"), "tol": w.tol, "l0": info["l0"],
                        "levels_used": nlevels, "precision": "fp32 walk + kahan, fp64 final",
+                       "step": "table build + learned tilted proposal (pilot walks, MLP "
+                               "training, proposal tables) + MLMC solve to the tolerance",
+                       "learning": {"rounds": args.rounds, "pilot_walks": args.pilot,
+                                    "mlp_steps": 300, "alpha": 0.1},
                        "l2": "flushed between steps (256 MB write outside the timed events)",
-                       "parallelism": f"replicas{world}" if world > 1 else "1 GPU"},
-            "time_to_tol": {
-                "beta_1_over_lambda_max": None,
-                "beta_1_over_lambda_max_note": (
-                    f"not reached: each step stops at its {args.step_budget:g} s budget with "
-                    f"estimated rel. RMS error {float(np.mean(ests)):.3g} (plain walk variance "
-                    "grows like e^(beta d_max), beta d_max = "
-                    f"{w.t * w.extra['d_max']:.1f})"),
-                "beta_1_over_d_max_s": statistics.median(tt),
-                "beta_1_over_d_max_runs_s": tt,
-                "beta_1_over_d_max_converged": all(tt_conv),
-                "beta_1_over_d_max_est_rel_err": float(np.mean(tt_est)),
-                "beta_1_over_d_max_rel_err_vs_fp64": err_dmax,
-                "beta_1_over_d_max_walk_steps_per_s": float(np.sum(tt_events) / np.sum(tt)),
-                "d_max": w.extra["d_max"]},
-            "learned_vs_plain": learned,
+                       "parallelism": f"shard{world}" if world > 1 else "1 GPU"},
+            "time_to_tol": {"learned_s": statistics.median(tt), "learned_runs_s": tt,
+                            "learned_converged": all(conv),
+                            "learned_est_rel_err": float(np.mean(ests)),
+                            "learned_rel_err_vs_fp64": err,
+                            "plain_s": None, "plain": plain},
             "est_rel_err": float(np.mean(ests)), "rel_err_vs_fp64": err,
             "table_build_ms": table_ms, "plan_create_s": t_plan,
             "walks_per_step": walks_total / args.steps, "jumps_per_step": jumps_total / args.steps,
@@ -459,6 +442,9 @@ OPS_STILL_TEST = 2
 OPS_JUMP = {True: 22, False: 15}
 OPS_END_JUMPED = {True: 31, False: 24}
 OPS_END_STILL = 1
+# A proposal walk's jump also loads the entry's log-ratios and adds one to
+# the exponent (the row record comes from the record table, not the entry).
+OPS_JUMP_PROPOSAL = 2
 # From one ncu capture of the walk kernel on this workload (a 4.1e8-walk
 # launch at l0 after an L2 flush): DRAM bytes per launch (the fused tables are
 # read once, everything else hits L2), issue-slot use and instructions per
@@ -467,7 +453,7 @@ TRAFFIC_CAPTURE = None
 ISSUE_CAPTURE = None
 
 
-def walk_roofline(level_log, walk_s, clocks, peaks, total_ms, num_sms=None):
+def walk_roofline(level_log, walk_s, clocks, peaks, total_ms, num_sms=None, proposal=False):
     ops = 0.0
     events = 0
     launches = 0
@@ -477,11 +463,13 @@ def walk_roofline(level_log, walk_s, clocks, peaks, total_ms, num_sms=None):
         ev = lv["walks"] + lv["jumps"]
         still = lv.get("still_walks", 0)
         ops += OPS_DRAW * (lv["jumps"] + lv["walks"] / 4.0) + OPS_HOLD * (ev - still) \
-            + OPS_STILL_TEST * lv["walks"] + OPS_JUMP[c] * lv["jumps"] \
+            + OPS_STILL_TEST * lv["walks"] \
+            + (OPS_JUMP[c] + (OPS_JUMP_PROPOSAL if proposal else 0)) * lv["jumps"] \
             + OPS_END_JUMPED[c] * (lv["walks"] - still) + OPS_END_STILL * still
         # table gathers: alias entry + the new state's row record per jump,
-        # v at the end state per walk that jumped (FP32 layout)
-        gather += 32.0 * lv["jumps"] + 4.0 * (lv["walks"] - still)
+        # v at the end state per walk that jumped (FP32 layout); a proposal
+        # entry adds its two log-ratios (8 B)
+        gather += (40.0 if proposal else 32.0) * lv["jumps"] + 4.0 * (lv["walks"] - still)
         events += ev
         launches += lv.get("launches", 0)
     sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
@@ -495,7 +483,7 @@ def walk_roofline(level_log, walk_s, clocks, peaks, total_ms, num_sms=None):
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s",
             "frac": achieved / peak if peak else None,
             "traffic": TRAFFIC_CAPTURE,
-            "kernel": "k_walk<FP32> (mlmc_walk.cu)",
+            "kernel": "k_walk<FP32%s> (mlmc_walk.cu)" % (", proposal" if proposal else ""),
             "peak_source": f"{num_sms} SMs x 128 lanes x {sm_mhz:.0f} MHz (SM count of the device, "
                            "median SM clock sampled in the run)",
             "issue": ISSUE_CAPTURE,
@@ -1065,8 +1053,15 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-seconds", type=float, default=15.0)
-    ap.add_argument("--step-budget", type=float, default=8.0,
-                    help="controller wall-clock budget of one step (s)")
+    ap.add_argument("--step-budget", type=float, default=60.0,
+                    help="controller wall-clock budget of one solve (s); the plain solve of the "
+                         "default workload runs to it")
+    ap.add_argument("--plain-budget", type=float, default=8.0,
+                    help="budget of the plain (untilted) comparison solve of the default workload")
+    ap.add_argument("--rounds", type=int, default=3,
+                    help="pilot-train-install rounds of the learned proposal (mlmc_learn_tilt)")
+    ap.add_argument("--pilot", type=int, default=64,
+                    help="first-round pilot walks per row of the learned proposal")
     ap.add_argument("--workload", choices=["tc", "batch", "learned", "precision", "kernel",
                                            "levels", "complexity", "source", "forward"],
                     default="tc",

@@ -200,7 +200,7 @@ enum { MLMC_TILT_JUMPS = 1, MLMC_TILT_CLOCKS = 2 };
  * the paper has no counterpart, its clocks run at the rates L_ii of Sec. 3,
  * Eq. 12).  With tilted clocks the walk holds row i for an
  * Exp(t lambda_i) time with
- *   lambda_i = sum_{j != i} |a_ij| h_j / h_i, clamped to [L_ii/1024, 4 L_ii]
+ *   lambda_i = sum_{j != i} |a_ij| h_j / h_i, clamped to [L_ii/1024, max(L_ii, 2/t)]
  * (0 where L_ii = 0), weights its path by exp(t int (a_ii + lambda_X) ds)
  * instead of exp(t int d_X ds), and every jump out of row i adds
  * log(L_ii / lambda_i) + log(k/q) to the exponent.  Every level then
@@ -462,6 +462,11 @@ void mlmc_mlp_destroy(mlmc_mlp *mlp);
  * W2[64][64] row = input, b2[64], w3[64], b3). */
 int32_t mlmc_mlp_param_count(void);
 
+/* Kernels the MLP has launched on its stream since creation (launch
+ * accounting; the feature, target and proposal kernels of
+ * mlmc_learn_proposal / mlmc_learn_tilt count on the plan). */
+int64_t mlmc_mlp_launch_count(const mlmc_mlp *mlp);
+
 /* Set (set != NULL) and/or read (get != NULL) the packed FP32 parameters
  * (host or device pointers).  Synchronises. */
 mlmc_status mlmc_mlp_params(mlmc_mlp *mlp, const float *set, float *get);
@@ -497,8 +502,11 @@ mlmc_status mlmc_learn_proposal(mlmc_plan *plan, mlmc_mlp *mlp, const double *v,
  * earlier rounds' ones) with the proposal installed by the previous one.  With tilted clocks the MLP's
  * target is 0.5 (log(|x-hat| + 1e-3 max|x-hat|) + log(|v| + 1e-3 max|v|)):
  * the zero-variance h of a walk at scaled time s is exp((1-s)tA)v, from x at
- * the start to v at the end, and this is its geometric mean.  final_loss is
- * the last round's.  Backward-mode plans only. */
+ * the start to v at the end, and this is its geometric mean.  The MLP's
+ * training rows are weighted by degree (row i counted 1 + floor(deg_i /
+ * mean degree) times, at most 4n rows): the few rows with many
+ * off-diagonals set the laws of every row around them.  final_loss is the
+ * last round's.  Backward-mode plans only. */
 mlmc_status mlmc_learn_tilt(mlmc_plan *plan, mlmc_mlp *mlp, const double *v, uint64_t seed,
                             int64_t pilot_walks, int32_t steps, int32_t batch, float lr,
                             double alpha, int32_t tilt, int32_t rounds, float *final_loss);

@@ -382,9 +382,11 @@ int orc_alias_is(int64_t n, const int64_t *row_ptr, const int32_t *col, const do
  * lambda = L).  The paper's walk has lambda = L and q = k (Eq. 1, Eq. 12).
  * The h-transform takes, for h > 0,
  *   lambda_i = sum_{j != i} |a_ij| h_j / h_i
- * (clamped to [L_ii / 1024, 4 L_ii]: a faster clock than 4 L_ii would let the
- * weight grow like e^{t lambda s} where h is poor) and the proposal q of
- * orc_alias_is,
+ * (clamped to [L_ii / 1024, max(L_ii, 2/t)]: a clock faster than the
+ * paper's only where its scaled rate t lambda stays below 2, because the
+ * weight grows like e^{t lambda s} wherever h misjudges the row, and at a
+ * row whose h is too small the unclamped rate would be large exactly where
+ * t L_ii is) and the proposal q of orc_alias_is,
  * so that with h = the exact solution the factors of a path telescope to
  * h(start) / h(end) and the exponent stays near its mean: the variance that
  * the hubs' holding times give the paper's walk (weight e^{t d_j S} against an
@@ -394,10 +396,10 @@ int orc_alias_is(int64_t n, const int64_t *row_ptr, const int32_t *col, const do
  * The sum over the row runs in stored order with separate multiply and add
  * (the GPU builds the same tables with the same operations). */
 #define ORC_TILT_MIN (1.0 / 1024.0)
-#define ORC_TILT_MAX 4.0
+#define ORC_TILT_SCALED_MAX 2.0
 
 int orc_tilt_rates(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
-                   const double *L, const float *h, double *lam)
+                   const double *L, const float *h, double t, double *lam)
 {
     for (int64_t i = 0; i < n; ++i) {
         double hsum = 0.0;
@@ -410,7 +412,9 @@ int orc_tilt_rates(int64_t n, const int64_t *row_ptr, const int32_t *col, const 
             continue;
         }
         double r = hsum / (double)h[i];
-        double lo = L[i] * ORC_TILT_MIN, hi = L[i] * ORC_TILT_MAX;
+        double lo = L[i] * ORC_TILT_MIN;
+        double cap = (t > 0.0) ? ORC_TILT_SCALED_MAX / t : 0.0;
+        double hi = L[i] > cap ? L[i] : cap;
         lam[i] = r < lo ? lo : (r > hi ? hi : r);
     }
     return 0;
@@ -601,8 +605,16 @@ static int orc_before(const orc_ctx *c, double t_next, int64_t n_step, int64_t N
  *   diff  = sum_j dt (-d_{X_{2j-2}}/2 + d_{X_{2j-1}} - d_{X_{2j}}/2) (xi_j of
  *           Lemma 2), so y = sign u_end e^{log_c} expm1(diff) avoids the
  *           cancellation in eta_2 - eta_1. */
+/* Intermediate times (the paper's Sec. 5 and Fig. 7 read the solution at
+ * the grid times of the same walks): with n_times > 0 the walk also writes
+ * y_times[k-1], k = 1..n_times-1, the sample of x(t k / n_times) from its
+ * prefix up to grid point g = k N / n_times: the same expression as y with
+ * the exponents summed over grid points 0..g (half weights at 0 and g; the
+ * coarse rule on the even points) and v at the state at g.  n_times divides
+ * N (and N/2 when coarse); the last time is y itself. */
 static int orc_walk_core(const orc_ctx *c, int64_t row, orc_ctr kc, int level, int coarse,
-                         int use_v_end, int backward, int64_t rep, orc_walk_rec *out)
+                         int use_v_end, int backward, int64_t rep, orc_walk_rec *out,
+                         int32_t n_times, double *y_times)
 {
     const int64_t N = (int64_t)1 << level;
     int64_t j = row;
@@ -711,6 +723,20 @@ static int orc_walk_core(const orc_ctx *c, int64_t row, orc_ctr kc, int level, i
         } else {
             x_prev1 = j;
         }
+        if (n_times > 1 && step < N && step % (N / n_times) == 0) {
+            /* prefix sample at grid point `step` (state j) */
+            double uj = use_v_end ? c->v[j] : 1.0;
+            double y;
+            if (coarse) {
+                y = (double)sign * uj * (exp(log_c + log_is) * expm1(diff));
+            } else {
+                double lf = log_f;
+                if (step % 2 != 0) /* the pairs end at step - 1 */
+                    lf = lf + (c->dl[x_prev2] / (double)N / 2.0 + c->dl[j] / (double)N / 2.0);
+                y = (double)sign * uj * exp(lf + log_is);
+            }
+            y_times[step / (N / n_times) - 1] = y;
+        }
     }
     if (N == 1) {
         /* Level 0 has one interval and no pair: the fine exponent is
@@ -731,6 +757,7 @@ done:
         out->y_alg2 = 0.0;
         out->log_f = 0.0;
         out->log_c = 0.0;
+        for (int32_t k = 0; k + 1 < n_times; ++k) y_times[k] = 0.0;
         return status;
     }
     if (src_on) {
@@ -756,7 +783,16 @@ int orc_walk(const orc_ctx *c, int64_t row, int64_t rep, int level, int coarse,
              orc_walk_rec *out)
 {
     return orc_walk_core(c, row, orc_ctr_backward(c, row, rep, level), level, coarse, 1, 1, rep,
-                         out);
+                         out, 0, NULL);
+}
+
+/* orc_walk with the samples of the intermediate times (see orc_walk_core):
+ * y_times[0 .. n_times-2]. */
+int orc_walk_times(const orc_ctx *c, int64_t row, int64_t rep, int level, int coarse,
+                   int32_t n_times, orc_walk_rec *out, double *y_times)
+{
+    return orc_walk_core(c, row, orc_ctr_backward(c, row, rep, level), level, coarse, 1, 1, rep,
+                         out, n_times, y_times);
 }
 
 /* Forward mode (Eq. 5; reading R6): the tables in c are those of B = A^T.
@@ -777,7 +813,7 @@ int orc_walk_fwd(const orc_ctx *c, const int64_t *cdf, const int64_t *w, uint64_
         int64_t mid = (lo + hi) / 2;
         if ((uint64_t)cdf[mid] > r) hi = mid; else lo = mid + 1;
     }
-    int status = orc_walk_core(c, lo, kc, level, coarse, 0, 0, 0, out);
+    int status = orc_walk_core(c, lo, kc, level, coarse, 0, 0, 0, out, 0, NULL);
     double f = c->v[lo] * ((double)W / (double)w[lo]);
     out->y = out->y * f;
     out->y_alg2 = out->y_alg2 * f;

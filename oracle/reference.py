@@ -301,11 +301,12 @@ def _functional(kernel: np.ndarray, dl: np.ndarray, c: np.ndarray, g: np.ndarray
     return w
 
 
-def tilt_law(a_dense: np.ndarray, h: np.ndarray, alpha: float):
+def tilt_law(a_dense: np.ndarray, h: np.ndarray, alpha: float, t: float):
     """The h-transform walk's law in FP64 (no table rounding): rates
-    lam_i = sum_{j != i} |a_ij| h_j / h_i clamped to [L_ii/1024, 4 L_ii]
-    (0 where L_ii = 0) and jump law q_ij = (1 - alpha) |a_ij| h_j / sum_k
-    |a_ik| h_k + alpha |a_ij| / L_ii (rows with L_ii = 0: zero)."""
+    lam_i = sum_{j != i} |a_ij| h_j / h_i clamped to [L_ii/1024,
+    max(L_ii, 2/t)] (0 where L_ii = 0) and jump law q_ij = (1 - alpha)
+    |a_ij| h_j / sum_k |a_ik| h_k + alpha |a_ij| / L_ii (rows with L_ii = 0:
+    zero)."""
     a = np.asarray(a_dense, dtype=np.float64)
     off = np.abs(a.copy())
     np.fill_diagonal(off, 0.0)
@@ -317,7 +318,8 @@ def tilt_law(a_dense: np.ndarray, h: np.ndarray, alpha: float):
     rows = lii > 0
     q[rows] = ((1.0 - alpha) * off[rows] * h[None, :] / hs[rows, None]
                + alpha * off[rows] / lii[rows, None])
-    lam[rows] = np.clip(hs[rows] / h[rows], lii[rows] / 1024.0, lii[rows] * 4.0)
+    cap = 2.0 / t if t > 0 else 0.0
+    lam[rows] = np.clip(hs[rows] / h[rows], lii[rows] / 1024.0, np.maximum(lii[rows], cap))
     return lam, q
 
 

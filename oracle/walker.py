@@ -83,7 +83,7 @@ def lib():
         _lib.orc_alias_is.argtypes = [ct.c_int64, P, P, P, P, P, P, ct.c_double, P, P, P, P, P, P,
                                       P]
         _lib.orc_alias_is.restype = ct.c_int
-        _lib.orc_tilt_rates.argtypes = [ct.c_int64, P, P, P, P, P, P]
+        _lib.orc_tilt_rates.argtypes = [ct.c_int64, P, P, P, P, P, ct.c_double, P]
         _lib.orc_tilt_rates.restype = ct.c_int
         _lib.orc_tilted_split.argtypes = [ct.c_int64, ct.c_double, P, P, P, P, P, P]
         _lib.orc_tilted_split.restype = ct.c_int
@@ -159,7 +159,7 @@ def build_tables(a, t: float, h=None, alpha: float = 0.1, clocks: bool = False) 
     proposal q = (1-alpha) |a_ij| h_j / sum + alpha k_ij instead, and record
     log(k/q) per entry.  With ``clocks`` as well, the holding times are
     tilted too (the h-transform, orc_tilt_rates): the walk's rates are
-    lambda_i = sum_j |a_ij| h_j / h_i (clamped to [L_ii/1024, 4 L_ii]),
+    lambda_i = sum_j |a_ij| h_j / h_i (clamped to [L_ii/1024, max(L_ii, 2/t)]),
     dl_i = t (a_ii + lambda_i), and every entry of row i also records
     log(L_ii / lambda_i)."""
     n = a.n
@@ -192,7 +192,7 @@ def build_tables(a, t: float, h=None, alpha: float = 0.1, clocks: bool = False) 
     elif clocks:
         hh = np.ascontiguousarray(h, dtype=np.float32)
         lam = np.zeros(n)
-        lib().orc_tilt_rates(n, _p(rp), _p(col), _p(val), _p(L), _p(hh), _p(lam))
+        lib().orc_tilt_rates(n, _p(rp), _p(col), _p(val), _p(L), _p(hh), float(t), _p(lam))
         lib().orc_tilted_split(n, float(t), _p(a_ii), _p(lam), _p(dl), _p(inv_rate),
                                _p(inv_rate32), _p(dl32))
         lr_keep = np.zeros(m, dtype=np.float32)

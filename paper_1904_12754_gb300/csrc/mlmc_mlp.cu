@@ -648,6 +648,8 @@ void mlmc_mlp_destroy(mlmc_mlp* m) {
 
 int32_t mlmc_mlp_param_count(void) { return kParams; }
 
+int64_t mlmc_mlp_launch_count(const mlmc_mlp* m) { return m ? m->launches : 0; }
+
 mlmc_status mlmc_mlp_params(mlmc_mlp* m, const float* set, float* get) {
   if (!m) return mfail(MLMC_ERR_INVALID_ARG, "NULL mlp");
   if (set) MLP_CUDA(cudaMemcpyAsync(m->d_p, set, kParams * 4, cudaMemcpyDefault, m->stream), "set");
@@ -768,7 +770,13 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
   float* z = nullptr;
   float* h = nullptr;
   float* pv = nullptr;  // v, k^m v (m = 1..4), T_3 and two Taylor terms (8 x n floats)
+  int64_t* widx = nullptr;        // training rows, weighted by degree (see below)
+  __nv_bfloat16* wfeat = nullptr;
+  float* wy = nullptr;
   auto cleanup = [&]() {
+    cudaFree(widx);
+    cudaFree(wfeat);
+    cudaFree(wy);
     cudaFree(pv);
     cudaFree(sums);
     cudaFree(dv);
@@ -798,23 +806,28 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
   const unsigned g = static_cast<unsigned>(std::min<int64_t>((p->n + 255) / 256, p->num_sms * 8));
   // Features (fixed over the rounds: they use the paper's jump law).
   k_to_float32<<<g, 256, 0, p->stream>>>(p->n, dv, pv);
+  p->launches++;
   for (int mstep = 1; mstep <= 4; ++mstep)
     k_jump_mean<<<g, 256, 0, p->stream>>>(p->n, p->d_row_ptr, p->d_col, p->d_val, p->d_lii,
                                            pv + (mstep - 1) * p->n, pv + mstep * p->n);
+    p->launches++;
   {
     float* t3 = pv + 5 * p->n;
     float* ta = pv + 6 * p->n;
     float* tb = pv + 7 * p->n;
     k_abs_float32<<<g, 256, 0, p->stream>>>(p->n, dv, ta, t3);
+    p->launches++;
     for (int mstep = 1; mstep <= 3; ++mstep) {
       k_abs_taylor_step<<<g, 256, 0, p->stream>>>(p->n, p->d_row_ptr, p->d_col, p->d_val,
                                                   p->t / mstep, ta, tb, t3);
+      p->launches++;
       std::swap(ta, tb);
     }
   }
   k_mlp_features<<<g, 256, 0, p->stream>>>(p->n, p->d_row_ptr, p->d_col, p->d_meta64, p->d_lii, p->t,
                                             pv, pv + p->n, pv + 2 * p->n, pv + 3 * p->n,
                                             pv + 4 * p->n, pv + 5 * p->n, feat);
+  p->launches++;
   LP_CUDA(cudaGetLastError(), "features");
   double vmax = 0.0;
   {
@@ -822,6 +835,31 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
     LP_CUDA(cudaMemcpyAsync(hv.data(), dv, sizeof(double) * p->n, cudaMemcpyDeviceToHost, p->stream), "read v");
     LP_CUDA(cudaStreamSynchronize(p->stream), "sync");
     for (double q : hv) vmax = std::max(vmax, std::fabs(q));
+  }
+  // Training rows weighted by degree: row i appears 1 + floor(deg_i / mean
+  // deg) times (at most 4n rows in all).  Rows with many off-diagonals are
+  // few, but their h sets the clocks and jump laws of every row around them,
+  // and an MLP fitted to rows drawn uniformly would fit them worst.
+  int64_t n_train = 0;
+  {
+    std::vector<int64_t> rp(p->n + 1);
+    LP_CUDA(cudaMemcpyAsync(rp.data(), p->d_row_ptr, sizeof(int64_t) * (p->n + 1),
+                            cudaMemcpyDeviceToHost, p->stream), "read row_ptr");
+    LP_CUDA(cudaStreamSynchronize(p->stream), "sync");
+    const double mean_deg = std::max(1.0, static_cast<double>(rp[p->n]) / static_cast<double>(p->n));
+    std::vector<int64_t> idx;
+    idx.reserve(static_cast<size_t>(2 * p->n));
+    for (int64_t i = 0; i < p->n; ++i) {
+      const int64_t c = 1 + static_cast<int64_t>(static_cast<double>(rp[i + 1] - rp[i]) / mean_deg);
+      for (int64_t k = 0; k < c && static_cast<int64_t>(idx.size()) < 4 * p->n; ++k) idx.push_back(i);
+    }
+    n_train = static_cast<int64_t>(idx.size());
+    LP_CUDA(cudaMalloc(&widx, sizeof(int64_t) * n_train), "alloc");
+    LP_CUDA(cudaMalloc(&wfeat, sizeof(__nv_bfloat16) * n_train * kIn), "alloc");
+    LP_CUDA(cudaMalloc(&wy, sizeof(float) * n_train), "alloc");
+    LP_CUDA(cudaMemcpyAsync(widx, idx.data(), sizeof(int64_t) * n_train, cudaMemcpyHostToDevice,
+                            p->stream), "write rows");
+    LP_CUDA(cudaStreamSynchronize(p->stream), "sync");
   }
   mlmc_status st = MLMC_OK;
   for (int32_t round = 0; round < rounds; ++round) {
@@ -858,15 +896,21 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
     k_log_target<<<g, 256, 0, p->stream>>>(p->n, sums, static_cast<float>(1e-3 * xmax + 1e-30),
                                            clocks ? dv : nullptr,
                                            static_cast<float>(1e-3 * vmax + 1e-30), y);
+    p->launches++;
     LP_CUDA(cudaGetLastError(), "targets");
     LP_CUDA(cudaStreamSynchronize(p->stream), "sync");
     m->stream = p->stream;
-    st = mlmc_mlp_train(m, reinterpret_cast<const uint16_t*>(feat), y, p->n, steps, batch, lr,
+    k_gather<<<p->num_sms * 2, 256, 0, p->stream>>>(n_train, widx, feat, y, wfeat, wy);
+    p->launches++;
+    LP_CUDA(cudaGetLastError(), "training rows");
+    LP_CUDA(cudaStreamSynchronize(p->stream), "sync");
+    st = mlmc_mlp_train(m, reinterpret_cast<const uint16_t*>(wfeat), wy, n_train, steps, batch, lr,
                         seed ^ (0xABCDEFull + static_cast<uint64_t>(round)), final_loss);
     if (st == MLMC_OK) st = forward(m, feat, p->n, z, nullptr, false);
     if (st == MLMC_OK) st = check_err(m);
     if (st != MLMC_OK) break;
     k_exp_h<<<g, 256, 0, p->stream>>>(p->n, z, h);
+    p->launches++;
     LP_CUDA(cudaGetLastError(), "h");
     st = mlmc_plan_set_tilt(p, h, alpha, tilt);
     if (st != MLMC_OK) break;

@@ -159,8 +159,9 @@ __global__ void k_build_tables(int64_t n, double t, const int64_t* __restrict__ 
 // build an entry holds its working probability (bytes 0-7), its FIFO link
 // (bytes 8-11) and its own lr (bytes 16-19, which is also its final lr_keep).
 // Tilted clocks (clocks = true, the h-transform): the row's rate becomes
-//   lambda_i = sum_{j != i} |a_ij| h_j / h_i, clamped to [L_ii/1024, 4 L_ii]
-// (0 where L_ii = 0), its records m32t/m64t get rate t lambda_i and
+//   lambda_i = sum_{j != i} |a_ij| h_j / h_i, clamped to
+//   [L_ii/1024, max(L_ii, 2/t)] (0 where L_ii = 0: a clock runs faster than
+//   the paper's only while its scaled rate t lambda stays below 2), its records m32t/m64t get rate t lambda_i and
 // dl_i = t (a_ii + lambda_i) (the split D' = diag(a + lambda),
 // T' = diag(lambda) - N, whose Strang product the walk then estimates), and
 // every entry's lr gains log(L_ii / lambda_i), the clock's likelihood ratio
@@ -194,7 +195,8 @@ __global__ void k_build_is_tables(int64_t n, const int64_t* __restrict__ row_ptr
       if (L > 0.0) {
         const double r = __ddiv_rn(hsum, static_cast<double>(h[i]));
         const double lo = __dmul_rn(L, 1.0 / 1024.0);
-        const double hi = __dmul_rn(L, 4.0);
+        const double cap = t > 0.0 ? __ddiv_rn(2.0, t) : 0.0;
+        const double hi = L > cap ? L : cap;
         lam = r < lo ? lo : (r > hi ? hi : r);
         lr_clock = lam > 0.0 ? log(L / lam) : 0.0;
       }

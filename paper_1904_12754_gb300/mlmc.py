@@ -132,6 +132,8 @@ def load(build_if_missing: bool = False):
     lib.mlmc_learn_proposal.argtypes = [P, P, P, ct.c_uint64, I64, I32, I32, ct.c_float, D, P]
     lib.mlmc_learn_tilt.argtypes = [P, P, P, ct.c_uint64, I64, I32, I32, ct.c_float, D, I32, I32,
                                     P]
+    lib.mlmc_mlp_launch_count.argtypes = [P]
+    lib.mlmc_mlp_launch_count.restype = I64
     lib.mlmc_launch_count.argtypes = [P]
     lib.mlmc_launch_count.restype = I64
     for name in ("mlmc_schedule_default", "mlmc_plan_create", "mlmc_plan_rebuild", "mlmc_expmv",
@@ -365,7 +367,7 @@ class Plan:
     def set_tilt(self, h, alpha: float = 0.1, clocks: bool = True):
         """Proposal with tilted jumps and, with ``clocks``, tilted holding
         times (the h-transform: rates sum_j |a_ij| h_j / h_i clamped to
-        [L_ii/1024, 4 L_ii]); h as in set_proposal (None = plain walk)."""
+        [L_ii/1024, max(L_ii, 2/t)]); h as in set_proposal (None = plain walk)."""
         if isinstance(h, np.ndarray):
             h = np.ascontiguousarray(h, dtype=np.float32)
         elif h is not None and hasattr(h, "dtype") and str(h.dtype) != "torch.float32":
@@ -591,6 +593,9 @@ class MLP:
                                              pilot_walks, steps, batch, ct.c_float(lr),
                                              float(alpha), _ptr(loss)))
         return float(loss[0])
+
+    def launch_count(self) -> int:
+        return int(self._lib.mlmc_mlp_launch_count(self._h))
 
     def learn_tilt(self, plan, v, seed: int, pilot_walks: int = 256, steps: int = 300,
                    batch: int = 8192, lr: float = 3e-3, alpha: float = 0.1,

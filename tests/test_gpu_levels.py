@@ -1,0 +1,103 @@
+"""GPU: the level structure the paper analyses, pinned on small-world networks
+(Newman-Watts, k = 2, p = 0.1, n = 1e4; total communicability, beta = 1,
+v = 1: the setting of Fig. 2, Fig. 4 and Fig. 5).
+
+  - Fig. 2 / Lemma 2 / Eq. 13: the coupled corrections m_l and their
+    variances V_l fall like 2^(-2l) (weak order 2 of the Strang splitting,
+    and the coupled fine/coarse pair's variance).  Least-squares slopes of
+    log2 |m_l| and log2 V_l over levels 3-8 lie in [-2.4, -1.6].
+  - Fig. 5: the MLMC work to an RMS tolerance eps grows like eps^-2 (the
+    slope of log10 walks against log10 eps lies in [-2.4, -1.6]).
+  - Fig. 4 with Eq. 14's cost model: the cost of a solve in the paper's units
+    (per level M_l walks of N_l intervals plus their jumps) against the
+    coarsest level l0 has its minimum at a small l0 and grows above it (the
+    optimum is asserted, and the cost at l0 = 6 is at least twice it).
+"""
+import numpy as np
+import pytest
+
+import mlmc_inputs as I
+
+from gpu_helpers import stream_handle, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+N = 10_000
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__ as g
+    g.build()
+
+
+@pytest.fixture(scope="module")
+def network():
+    return I.small_world(N, 2, 0.1, seed=20190429)
+
+
+def _slope(x, y):
+    x, y = np.asarray(x, float), np.asarray(y, float)
+    return float(np.polyfit(x, y, 1)[0])
+
+
+def test_corrections_and_variances_fall_like_4_to_the_minus_level(network):
+    torch = torch_cuda()
+    from paper_1904_12754_gb300 import mlmc as M
+    reps = 8192
+    sched = M.schedule_default(precision=M.FP64)
+    rows = []
+    with M.Plan.from_csr(network, 1.0, sched, rel_tol=1e-3, stream=stream_handle()) as plan:
+        dv = torch.ones(N, dtype=torch.float64, device="cuda")
+        sums = torch.zeros(N, dtype=torch.float64, device="cuda")
+        tot = torch.zeros(8, dtype=torch.float64, device="cuda")
+        for lvl in range(3, 9):
+            sums.zero_()
+            tot.zero_()
+            plan.mlmcl(lvl, True, 0, reps, dv, 77 + lvl, sums, tot)
+            torch.cuda.synchronize()
+            sv, t = sums.cpu().numpy(), tot.cpu().numpy()
+            mean = sv.sum() / (N * reps)
+            var = (t[0] - (sv * sv).sum() / reps) / (reps - 1) / N
+            rows.append((lvl, mean, var))
+    lv = [r[0] for r in rows]
+    sm = _slope(lv, [np.log2(abs(r[1])) for r in rows])
+    sv = _slope(lv, [np.log2(r[2]) for r in rows])
+    assert -2.4 <= sm <= -1.6, (sm, rows)
+    assert -2.4 <= sv <= -1.6, (sv, rows)
+
+
+def _solve_sum(network, tol, l0=-1, levels=3, seed=5):
+    from paper_1904_12754_gb300 import mlmc as M
+    sched = M.schedule_default(precision=M.FP32_KAHAN, num_levels=levels, max_levels=12,
+                               time_budget_s=60.0)
+    if l0 >= 0:
+        sched.l0 = l0
+    with M.Plan.from_csr(network, 1.0, sched, rel_tol=tol, stream=stream_handle()) as plan:
+        val = plan.expmv_sum(np.ones(N), seed=seed)
+        lv, est = plan.stats()
+    walks = sum(l["walks_per_row"] for l in lv) * N
+    paper_cost = sum(l["walks_per_row"] * N * (2 ** l["level"]) + l["jumps"] for l in lv)
+    return val, est, walks, paper_cost, lv
+
+
+def test_mlmc_work_grows_like_eps_to_the_minus_two(network):
+    tols = [8e-3, 4e-3, 2e-3, 1e-3]
+    walks = []
+    for tol in tols:
+        _, est, w, _, _ = _solve_sum(network, tol)
+        assert est <= tol
+        walks.append(w)
+    s = _slope(np.log10(tols), np.log10(walks))
+    assert -2.4 <= s <= -1.6, (s, walks)
+
+
+def test_cost_against_l0_has_its_optimum_at_a_small_level(network):
+    cost = {}
+    for l0 in range(0, 7):
+        _, est, _, c, lv = _solve_sum(network, 1e-3, l0=l0)
+        assert est <= 1e-3
+        cost[l0] = c
+    best = min(cost, key=cost.get)
+    assert best <= 3, cost
+    assert cost[6] >= 2 * cost[best], cost

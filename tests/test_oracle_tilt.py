@@ -74,7 +74,7 @@ def test_tilted_mean_is_the_tilted_strang_product(level):
     a, ad = _signed(12, 9)
     t = 0.9
     v = np.random.default_rng(2).standard_normal(a.n)
-    lam, q = R.tilt_law(ad, _h_clamped(ad, 3), 0.2)   # both clamps active
+    lam, q = R.tilt_law(ad, _h_clamped(ad, 3), 0.2, t)   # both clamps active
     m1, _ = R.level_moments(ad, t, v, level, False, lam=lam, q=q)
     xs = R.strang(a.scipy(), t, v, level, lam=lam)
     assert np.allclose(m1, xs, rtol=1e-11, atol=1e-13)
@@ -82,13 +82,14 @@ def test_tilted_mean_is_the_tilted_strang_product(level):
 
 def test_clamps_of_the_rates_are_active_in_the_pins():
     a, ad = _signed(12, 9)
-    lam, _ = R.tilt_law(ad, _h_clamped(ad, 3), 0.2)
+    t = 0.9
+    lam, _ = R.tilt_law(ad, _h_clamped(ad, 3), 0.2, t)
     off = np.abs(ad.copy())
     np.fill_diagonal(off, 0.0)
     lii = off.sum(axis=1)
     rows = lii > 0
     assert np.any(np.isclose(lam[rows], lii[rows] / 1024.0))
-    assert np.any(np.isclose(lam[rows], lii[rows] * 4.0))
+    assert np.any(np.isclose(lam[rows], np.maximum(lii[rows], 2.0 / t)))
 
 
 @pytest.mark.parametrize("level", [0, 2, 4])
@@ -102,7 +103,7 @@ def test_perron_h_makes_the_split_exact(level):
     phi = np.abs(vecs[:, -1])
     t = 1.0 / w[-1]
     v = np.random.default_rng(5).random(b.n)
-    lam, q = R.tilt_law(ad, phi, 0.0)
+    lam, q = R.tilt_law(ad, phi, 0.0, t)
     assert np.allclose(lam, w[-1], rtol=1e-10)
     exact = sla.expm(t * ad) @ v
     assert np.allclose(R.strang(b.scipy(), t, v, level, lam=lam), exact, rtol=1e-11)
@@ -117,7 +118,7 @@ def test_c_tables_reproduce_the_fp64_law():
     t = 0.6
     h = _h_clamped(ad, 8)
     tb = W.build_tables(a, t, h, 0.15, clocks=True)
-    lam, q = R.tilt_law(ad, h.astype(np.float64), 0.15)
+    lam, q = R.tilt_law(ad, h.astype(np.float64), 0.15, t)
     assert np.allclose(tb.lam, lam, rtol=1e-14, atol=0)
     rows = lam > 0
     assert np.allclose(tb.inv_rate[rows], 1.0 / (t * lam[rows]), rtol=1e-15)
@@ -156,7 +157,7 @@ def test_tilted_walks_match_exact_moments(precision, level, coarse):
     t = 0.8
     v = np.random.default_rng(2).random(7) - 0.4
     h = _h(a.n, 6, spread=1.0)
-    lam, q = R.tilt_law(ad, h.astype(np.float64), 0.1)
+    lam, q = R.tilt_law(ad, h.astype(np.float64), 0.1, t)
     m1, m2 = R.level_moments(ad, t, v, level, coarse, lam=lam, q=q)
     reps = 1 << 16
     tb = W.build_tables(a, t, h, 0.1, clocks=True)
@@ -194,7 +195,7 @@ def test_clock_tilt_removes_the_hub_variance(n, plain_min):
     t = 1.0 / I.lambda_max(b)
     v = np.ones(n)
     x = sla.expm(t * ad) @ v
-    lam, q = R.tilt_law(ad, x, 0.1)
+    lam, q = R.tilt_law(ad, x, 0.1, t)
     off = ad.copy()
     np.fill_diagonal(off, 0.0)
     lii = off.sum(axis=1)
@@ -209,5 +210,5 @@ def test_clock_tilt_removes_the_hub_variance(n, plain_min):
     assert plain > plain_min
     assert both < 0.2
     assert both < plain / 4 and both < jumps / 2
-    lam_g, q_g = R.tilt_law(ad, np.sqrt(x * v), 0.1)
+    lam_g, q_g = R.tilt_law(ad, np.sqrt(x * v), 0.1, t)
     assert relvar(lam_g, q_g) < 0.01
