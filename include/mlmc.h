@@ -282,6 +282,37 @@ mlmc_status mlmc_export_proposal(const mlmc_plan *plan, uint32_t *thr, int32_t *
  * Synchronises the plan's stream.  NOT_CONVERGED still writes x. */
 mlmc_status mlmc_expmv(mlmc_plan *plan, const double *v, double *x, uint64_t seed);
 
+/* The solution at intermediate times (Sec. 5 and Fig. 7: the paper reads the
+ * heat equation's solution at the grid times of one run, and Algorithm 3
+ * evaluates the Strang weight eta at every grid time of a walk):
+ * x(t_k) = exp(t_k A) v for t_k = t k / n_times, k = 1..n_times, from the
+ * same walks as mlmc_expmv.  A walk's sample for t_k is formed from its
+ * prefix up to the fine grid point k N / n_times, exactly as its final
+ * sample is from the whole path (exponents over the grid points up to it,
+ * half weights at both ends, the coarse rule on the even points, v at the
+ * state there); so each level's sum at t_k estimates the level-l Strang
+ * product of k N/n_times steps, and the sum over levels telescopes like
+ * Eq. 8.  The controller (Algorithm 1) sets M_l for the final time.
+ *   x_times  host or device, n_times x n doubles, row k-1 holds x(t_k) (the
+ *            last row is mlmc_expmv's x)
+ *   n_times  a power of two, 2 <= n_times <= 2^l0, and at most 16 (FP32
+ *            plans) or 8 (FP64 plans)
+ * Backward-mode plans without a source term, not sharded.  Time sums use
+ * (n_times - 1) x n doubles per level (allocated on the first call, for
+ * n_times = 16).  Synchronises; NOT_CONVERGED still writes x_times. */
+mlmc_status mlmc_expmv_times(mlmc_plan *plan, const double *v, double *x_times, int32_t n_times,
+                             uint64_t seed);
+
+/* mlmc_trace with the intermediate-time samples of every walk as well:
+ * y_times (device, n*reps*(n_times-1) doubles) receives, for the record at
+ * index r, its samples for k = 1..n_times-1 at y_times[r*(n_times-1) + k-1].
+ * n_times as for mlmc_expmv_times with `level` in place of l0 (level - 1 when
+ * coarse).  A walk stopped at the jump limit keeps the samples of the times
+ * it passed and has 0 at the later ones.  Synchronises. */
+mlmc_status mlmc_trace_times(mlmc_plan *plan, int32_t level, int32_t coarse, int64_t rep_begin,
+                             int64_t reps, const double *v, uint64_t seed, int32_t n_times,
+                             mlmc_walk_record *rec, double *y_times);
+
 /* One entry x_i = (exp(t A) v)_i: Algorithm 2 as printed, walks from row i
  * only, with the controller of Algorithm 1 on the scalar (eps = rel_tol
  * |x_i|).  v: host or device, n doubles; xi: host.  This is what the paper's

@@ -611,7 +611,9 @@ static int orc_before(const orc_ctx *c, double t_next, int64_t n_step, int64_t N
  * prefix up to grid point g = k N / n_times: the same expression as y with
  * the exponents summed over grid points 0..g (half weights at 0 and g; the
  * coarse rule on the even points) and v at the state at g.  n_times divides
- * N (and N/2 when coarse); the last time is y itself. */
+ * N (and N/2 when coarse); the last time is y itself.  A walk stopped at the
+ * jump limit keeps the samples of the times it passed (a sample depends only
+ * on the path up to its time) and has 0 at the later ones. */
 static int orc_walk_core(const orc_ctx *c, int64_t row, orc_ctr kc, int level, int coarse,
                          int use_v_end, int backward, int64_t rep, orc_walk_rec *out,
                          int32_t n_times, double *y_times)
@@ -634,6 +636,7 @@ static int orc_walk_core(const orc_ctx *c, int64_t row, orc_ctr kc, int level, i
      * N/2 steps of level l-1 (the even grid points).  Grid point 0: weight
      * 1, eta 1, the start row. */
     const int src_on = c->f != NULL && N >= 2;
+    for (int32_t k = 0; k + 1 < n_times; ++k) y_times[k] = 0.0;
     double integ2 = src_on ? c->f[row] : 0.0;
     double integ1 = integ2;
 
@@ -757,7 +760,6 @@ done:
         out->y_alg2 = 0.0;
         out->log_f = 0.0;
         out->log_c = 0.0;
-        for (int32_t k = 0; k + 1 < n_times; ++k) y_times[k] = 0.0;
         return status;
     }
     if (src_on) {
@@ -859,6 +861,20 @@ int orc_walk_many(const orc_ctx *c, int64_t count, const int64_t *rows, const in
  * [rep_begin, rep_begin + reps): per-row sums of y into sum_y[row], and the
  * totals sum y^2, jumps and walk-limit hits.  Rows are split over OpenMP
  * threads; each row's sum is formed in replica order. */
+/* Walks rows[k], reps[k] with their intermediate-time samples:
+ * y_times[k*(n_times-1) + j]. */
+int orc_walk_times_many(const orc_ctx *c, int64_t count, const int64_t *rows, const int64_t *reps,
+                        int level, int coarse, int32_t n_times, orc_walk_rec *out,
+                        double *y_times)
+{
+    int bad = 0;
+    for (int64_t k = 0; k < count; ++k)
+        if (orc_walk_times(c, rows[k], reps[k], level, coarse, n_times, &out[k],
+                           y_times + k * (int64_t)(n_times - 1)) != ORC_OK)
+            bad = 1;
+    return bad;
+}
+
 int orc_mlmcl(const orc_ctx *c, int64_t row_begin, int64_t row_end, int64_t rep_begin,
               int64_t reps, int level, int coarse, int nthreads, double *sum_y,
               double *sum_y2, int64_t *jumps, int64_t *limit_hits)

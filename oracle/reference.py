@@ -185,6 +185,29 @@ def strang(a, t: float, v: np.ndarray, level: int, lam=None) -> np.ndarray:
     return w
 
 
+def strang_times(a, t: float, v: np.ndarray, level: int, n_times: int, lam=None) -> np.ndarray:
+    """The level-l Strang product at the times t k / n_times, k = 1..n_times:
+    row k-1 holds (e^{dt D/2} e^{-dt T} e^{dt D/2})^{k N / n_times} v with
+    N = 2^level, dt = t/N (the mean of a walk's prefix sample at that time)."""
+    n_steps = 1 << level
+    if n_steps % n_times:
+        raise ValueError("n_times must divide 2^level")
+    dt = t / n_steps
+    d, minus_t = _split_sparse(a, lam)
+    half = np.exp(dt * d / 2.0)
+    dense = expm_pade13(dt * minus_t.toarray()) if a.shape[0] <= 2048 else None
+    w = np.array(v, dtype=np.float64, copy=True)
+    out = []
+    stride = n_steps // n_times
+    for step in range(1, n_steps + 1):
+        w = half * w
+        w = dense @ w if dense is not None else expmv_taylor(minus_t, dt, w)
+        w = half * w
+        if step % stride == 0:
+            out.append(w.copy())
+    return np.array(out)
+
+
 def strang_forward(a, t: float, v: np.ndarray, level: int) -> np.ndarray:
     """Mean of the forward-mode level-l estimate (Eq. 5 read on B = A^T):
     with B = D' - T' split by Eq. 1 (d'_i = a_ii + sum_{k != i} |a_ki|), the

@@ -83,6 +83,9 @@ def lib():
         _lib.orc_alias_is.argtypes = [ct.c_int64, P, P, P, P, P, P, ct.c_double, P, P, P, P, P, P,
                                       P]
         _lib.orc_alias_is.restype = ct.c_int
+        _lib.orc_walk_times_many.argtypes = [P, ct.c_int64, P, P, ct.c_int, ct.c_int, ct.c_int32,
+                                             P, P]
+        _lib.orc_walk_times_many.restype = ct.c_int
         _lib.orc_tilt_rates.argtypes = [ct.c_int64, P, P, P, P, P, ct.c_double, P]
         _lib.orc_tilt_rates.restype = ct.c_int
         _lib.orc_tilted_split.argtypes = [ct.c_int64, ct.c_double, P, P, P, P, P, P]
@@ -240,6 +243,17 @@ class Walker:
         r = WalkRec()
         lib().orc_walk(ct.byref(self.ctx), row, rep, level, int(coarse), ct.byref(r))
         return r
+
+    def walks_times(self, rows, reps, level: int, coarse: bool, n_times: int):
+        """walks() plus each walk's samples of the intermediate times t k /
+        n_times, k = 1..n_times-1 (array [count, n_times-1])."""
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        reps = np.ascontiguousarray(reps, dtype=np.int64)
+        out = np.zeros(rows.size, dtype=WALK_DTYPE)
+        yt = np.zeros((rows.size, n_times - 1))
+        lib().orc_walk_times_many(ct.byref(self.ctx), rows.size, _p(rows), _p(reps), level,
+                                  int(coarse), n_times, _p(out), _p(yt))
+        return out, yt
 
     def walks(self, rows, reps, level: int, coarse: bool) -> np.ndarray:
         rows = np.ascontiguousarray(rows, dtype=np.int64)

@@ -68,6 +68,8 @@ void free_plan(mlmc_plan* p) {
   cudaFree(p->d_lii);
   cudaFree(p->d_is_block);
   cudaFree(p->d_glob);
+  cudaFree(p->d_times);
+  cudaFree(p->d_xtimes);
   cudaFree(p->d_h);
   cudaFree(p->d_src);
   cudaFree(p->d_src32);
@@ -175,6 +177,10 @@ static mlmc_status run_level(mlmc_plan* p, int slot, int64_t extra, uint64_t see
     w.v = p->d_v;
     w.sum_y = L.sum_y;
     w.totals = totals_of(p, slot);
+    if (p->ctl_times > 1) {
+      w.n_times = p->ctl_times;
+      w.sum_times = p->d_times + static_cast<int64_t>(slot) * (kMaxTimesAll - 1) * p->n;
+    }
     int64_t nl = 0;
     NvtxRange range("mlmc level walks");
     MLMC_CUDA(cudaEventRecord(L.ev0, p->stream), "event record");
@@ -816,6 +822,54 @@ mlmc_status mlmc_mlmcl(mlmc_plan* p, int32_t level, int32_t coarse, int64_t rep_
   return MLMC_OK;
 }
 
+// Largest n_times of the plan's walk precision (the kernels' per-lane sums).
+static int max_times(const mlmc_plan* p) { return p->sched.precision == MLMC_FP64 ? 8 : 16; }
+
+static mlmc_status check_times(const mlmc_plan* p, int32_t n_times, int32_t level) {
+  if (forward_mode(p)) return fail(MLMC_ERR_INVALID_ARG, "intermediate times: backward-mode plans only");
+  if (p->source_active) return fail(MLMC_ERR_INVALID_ARG, "intermediate times: remove the source term first");
+  if (n_times < 2 || n_times > max_times(p) || (n_times & (n_times - 1)) != 0)
+    return fail(MLMC_ERR_INVALID_ARG, "n_times must be a power of two in [2, " +
+                                          std::to_string(max_times(p)) + "]");
+  if (n_times > (1 << level))
+    return fail(MLMC_ERR_INVALID_ARG, "n_times must not exceed 2^level (2^l0 for a solve)");
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_trace_times(mlmc_plan* p, int32_t level, int32_t coarse, int64_t rep_begin,
+                             int64_t reps, const double* v, uint64_t seed, int32_t n_times,
+                             mlmc_walk_record* rec, double* y_times) {
+  if (!p || !v || !rec || !y_times) return fail(MLMC_ERR_INVALID_ARG, "NULL argument");
+  if (level < 0 || level > 24 || (coarse && level < 2))
+    return fail(MLMC_ERR_INVALID_ARG, "level must be in [0,24] (>= 2 when coarse)");
+  mlmc_status cst = check_times(p, n_times, coarse ? level - 1 : level);
+  if (cst != MLMC_OK) return cst;
+  if (rep_begin < 0 || reps < 0 || rep_begin > (1ll << 56) || reps > (1ll << 56) - rep_begin)
+    return fail(MLMC_ERR_INVALID_ARG, "replica range out of [0, 2^56)");
+  double* scratch = nullptr;
+  const size_t ns = static_cast<size_t>(p->n) * static_cast<size_t>(n_times);
+  MLMC_CUDA(dev_alloc(&scratch, ns + kTotSlots), "alloc trace sums");
+  cudaError_t err = cudaMemsetAsync(scratch, 0, sizeof(double) * (ns + kTotSlots), p->stream);
+  WalkLaunch w;
+  w.level = level;
+  w.coarse = coarse != 0;
+  w.rep_begin = rep_begin;
+  w.reps = reps;
+  w.seed = seed;
+  w.v = v;
+  w.sum_y = scratch;
+  w.totals = scratch + ns;
+  w.sum_times = scratch + p->n;
+  w.n_times = n_times;
+  w.trace = rec;
+  w.trace_times = y_times;
+  if (err == cudaSuccess) err = launch_walk(p, w, nullptr);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(p->stream);
+  cudaFree(scratch);
+  if (err != cudaSuccess) return cuda_fail(err, "trace launch");
+  return MLMC_OK;
+}
+
 mlmc_status mlmc_trace(mlmc_plan* p, int32_t level, int32_t coarse, int64_t rep_begin,
                        int64_t reps, const double* v, uint64_t seed, mlmc_walk_record* rec) {
   if (!p || !v || !rec) return fail(MLMC_ERR_INVALID_ARG, "NULL argument");
@@ -868,6 +922,10 @@ static mlmc_status controller(mlmc_plan* p, const double* v, double* x, double* 
               "memset sums");
     MLMC_CUDA(cudaMemsetAsync(p->d_totals, 0, sizeof(double) * kTotSlots * s.max_levels, p->stream),
               "memset totals");
+    if (p->ctl_times > 1)
+      MLMC_CUDA(cudaMemsetAsync(p->d_times, 0, sizeof(double) * (kMaxTimesAll - 1) * p->n *
+                                                   static_cast<size_t>(s.max_levels), p->stream),
+                "memset time sums");
     for (auto& L : p->levels) {
       L.reps = 0;
       L.seconds = 0.0;
@@ -977,7 +1035,17 @@ static mlmc_status controller(mlmc_plan* p, const double* v, double* x, double* 
   // Final cross-level sum (Eq. 10) in FP64 and copy-out.
   if (target == kFull) {
     MLMC_CUDA(launch_finalize(p, nl, p->d_x, p->d_norm2), "finalize");
-    MLMC_CUDA(cudaMemcpyAsync(x, p->d_x, sizeof(double) * p->n, cudaMemcpyDefault, p->stream), "copy x");
+    if (p->ctl_times > 1) {
+      // x holds n_times rows: the intermediate times first, the final one last
+      const int64_t nt = static_cast<int64_t>(p->ctl_times - 1) * p->n;
+      MLMC_CUDA(launch_finalize_times(p, nl, p->ctl_times, p->d_xtimes), "finalize times");
+      MLMC_CUDA(cudaMemcpyAsync(x, p->d_xtimes, sizeof(double) * nt, cudaMemcpyDefault, p->stream),
+                "copy x(t_k)");
+      MLMC_CUDA(cudaMemcpyAsync(x + nt, p->d_x, sizeof(double) * p->n, cudaMemcpyDefault, p->stream),
+                "copy x");
+    } else {
+      MLMC_CUDA(cudaMemcpyAsync(x, p->d_x, sizeof(double) * p->n, cudaMemcpyDefault, p->stream), "copy x");
+    }
   } else {
     double tsum = 0.0;
     for (int k = 0; k < nl; ++k) tsum += h[k].sum / static_cast<double>(p->levels[k].reps);
@@ -1012,6 +1080,28 @@ mlmc_status mlmc_expmv(mlmc_plan* p, const double* v, double* x, uint64_t seed) 
   p->ctl_row_begin = 0;
   p->ctl_row_count = -1;
   return controller(p, v, x, nullptr, seed, kFull);
+}
+
+mlmc_status mlmc_expmv_times(mlmc_plan* p, const double* v, double* x_times, int32_t n_times,
+                             uint64_t seed) {
+  g_last_error.clear();
+  if (!p || !v || !x_times) return fail(MLMC_ERR_INVALID_ARG, "NULL argument");
+  mlmc_status cst = check_times(p, n_times, p->l0);
+  if (cst != MLMC_OK) return cst;
+  if (sharded(p)) return fail(MLMC_ERR_INVALID_ARG, "mlmc_expmv_times: not available on a sharded plan");
+  if (!p->d_times) {
+    MLMC_CUDA(dev_alloc(&p->d_times, static_cast<size_t>(kMaxTimesAll - 1) * static_cast<size_t>(p->n) *
+                                         static_cast<size_t>(p->sched.max_levels)),
+              "alloc time sums");
+    MLMC_CUDA(dev_alloc(&p->d_xtimes, static_cast<size_t>(kMaxTimesAll - 1) * static_cast<size_t>(p->n)),
+              "alloc x(t_k)");
+  }
+  p->ctl_row_begin = 0;
+  p->ctl_row_count = -1;
+  p->ctl_times = n_times;
+  const mlmc_status st = controller(p, v, x_times, nullptr, seed, kFull);
+  p->ctl_times = 0;
+  return st;
 }
 
 mlmc_status mlmc_expmv_entry(mlmc_plan* p, int64_t i, const double* v, double* xi, uint64_t seed) {

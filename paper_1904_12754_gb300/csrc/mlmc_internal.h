@@ -52,6 +52,12 @@ struct WalkLaunch {
   double* sum_y = nullptr;
   double* totals = nullptr;         // kTotSlots doubles
   mlmc_walk_record* trace = nullptr;  // non-null selects the recording kernel
+  // Intermediate times (backward walks): n_times > 1 also samples x(t k /
+  // n_times), k < n_times, into sum_times [(n_times-1) x n] (and, with trace,
+  // each record's samples into trace_times [(n_times-1) per record]).
+  int n_times = 0;
+  double* sum_times = nullptr;
+  double* trace_times = nullptr;
 };
 
 }  // namespace mlmc
@@ -162,6 +168,13 @@ struct mlmc_plan {
   int64_t exch_cap = 0;
   double* d_glob = nullptr;
   bool shard_stop = false;  // the last exchange's vote: a rank is past its deadline
+
+  // Intermediate times (mlmc_expmv_times): per level the row sums of the
+  // samples at t k / T, k < T ([max_levels][T_max - 1][n], allocated on first
+  // use for T_max = 16), and the T of the current solve (0: none).
+  double* d_times = nullptr;
+  double* d_xtimes = nullptr;   // [T_max - 1][n] the final sums of the times
+  int32_t ctl_times = 0;
 };
 
 namespace mlmc {
@@ -254,5 +267,8 @@ cudaError_t launch_walk_segment(mlmc_plan* p, const WalkLaunch& w, const void* v
 // out[0] += sum_i a_i, out[1] += sum_i a_i^2 (out must be zeroed by the caller).
 cudaError_t launch_sum_sumsq(mlmc_plan* p, const double* a, double* out);
 cudaError_t launch_finalize(mlmc_plan* p, int num_levels, double* x, double* norm2);
+// x_times[(k-1) n + i] = sum_l S_l,k[i] / M_l for k = 1..n_times-1.
+cudaError_t launch_finalize_times(mlmc_plan* p, int num_levels, int n_times, double* x_times);
+constexpr int kMaxTimesAll = 16;
 
 }  // namespace mlmc

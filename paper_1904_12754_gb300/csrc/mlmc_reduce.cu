@@ -68,7 +68,42 @@ int red_grid(const mlmc_plan* p) {
   return static_cast<int>(want < 1 ? 1 : (want > cap ? cap : want));
 }
 
+struct FinalizeTimesArgs {
+  const double* s[kMaxLevels];  // level sums [(T-1) x n]
+  double inv_m[kMaxLevels];
+  int count;
+};
+
+__global__ void __launch_bounds__(kRedBlock) k_finalize_times(int64_t total, FinalizeTimesArgs f,
+                                                              double* __restrict__ x) {
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(kRedBlock) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * kRedBlock) {
+    double xe = 0.0;
+    for (int l = 0; l < f.count; ++l) xe += f.s[l][e] * f.inv_m[l];
+    x[e] = xe;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_finalize_times(mlmc_plan* p, int num_levels, int n_times, double* x_times) {
+  if (num_levels > kMaxLevels || n_times < 2) return cudaErrorInvalidValue;
+  FinalizeTimesArgs f{};
+  const int64_t per_level = static_cast<int64_t>(kMaxTimesAll - 1) * p->n;
+  for (int k = 0; k < num_levels; ++k) {
+    f.s[k] = p->d_times + k * per_level;
+    const int64_t m = p->levels[k].reps;
+    f.inv_m[k] = m > 0 ? 1.0 / static_cast<double>(m) : 0.0;
+  }
+  f.count = num_levels;
+  const int64_t total = static_cast<int64_t>(n_times - 1) * p->n;
+  const int64_t want = (total + kRedBlock - 1) / kRedBlock;
+  const int64_t cap = static_cast<int64_t>(p->num_sms) * 8;
+  k_finalize_times<<<static_cast<int>(want < 1 ? 1 : (want > cap ? cap : want)), kRedBlock, 0,
+                     p->stream>>>(total, f, x_times);
+  p->launches++;
+  return cudaGetLastError();
+}
 
 cudaError_t launch_sum_sumsq(mlmc_plan* p, const double* a, double* out) {
   k_sum_sumsq<<<red_grid(p), kRedBlock, 0, p->stream>>>(p->n, a, out);

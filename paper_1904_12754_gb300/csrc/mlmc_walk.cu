@@ -83,6 +83,9 @@ struct WalkArgs {
   const void* f_walk;      // source vector in the walk precision (source walks only)
   double t;                // the time t (source walks only)
   const int32_t* still32;  // FP32: per-row still threshold index (still_index32)
+  int n_times;             // intermediate-time walks: output times (T), else 0
+  double* sum_times;       // [(T-1) x n] per-row sums of the samples at t k/T, k < T
+  double* trace_times;     // trace: [(T-1)] samples per record (or null)
 };
 
 // Key source of the walk's draws: the round keys of a launch-constant
@@ -237,6 +240,9 @@ struct ItemArgs {
   double t;               // the time t (source walks only)
   int64_t n, nnz;         // table sizes (checked build)
   const int32_t* still32; // FP32: per-row still threshold index
+  int n_times;            // intermediate times (T), 0 without
+  double* sum_times;
+  double* trace_times;
 };
 
 // Per-warp running totals of the walks a warp has finished.
@@ -359,6 +365,20 @@ struct EndQueue {
 };
 constexpr int kMaxWarps = 8;  // blocks of at most 256 threads
 
+// Intermediate times (mlmc_expmv_times): a walk also samples x(t k/T) at the
+// fine grid points g_k = k N/T, k = 1..T-1, from its prefix; each lane sums
+// its walks' samples per time here (per warp: [T-1][32]) and the warp adds
+// them to the row's sums once per work item.
+// At most 16 output times for FP32 walks and 8 for FP64 walks (the block's
+// static shared memory stays below 48 KB).
+constexpr int kMaxTimes32 = 16;
+constexpr int kMaxTimes64 = 8;
+template <bool FP64, bool TIMES>
+struct TimesAcc {
+  typename std::conditional<FP64, double, float>::type
+      v[TIMES ? (FP64 ? kMaxTimes64 : kMaxTimes32) - 1 : 1][32];
+};
+
 // Source term (Algorithm 3, Simpson's rule on a grid of K steps, K even): the
 // weighted sum over grid points k in (a, b] of w_k e^{W_k / K}, where the walk
 // holds one state (scaled rate term dl) on (a, b], W_k = P_a + (k - a) dl -
@@ -419,13 +439,15 @@ __device__ __forceinline__ typename Prec<FP64>::T simpson_segment(
 // counter, so the trajectories are those of the walk-by-walk definition.
 // Adds the item's sum of Y to a.sum_y[row] (one atomic) and its totals to
 // `tot`.
-template <bool FP64, bool COARSE, bool TRACE, bool IS, class Keys, bool SRC = false>
+template <bool FP64, bool COARSE, bool TRACE, bool IS, class Keys, bool SRC = false,
+          bool TIMES = false>
 __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, int64_t row,
                                           int64_t r_lo, int64_t r_hi,
                                           LaneTotals<typename Prec<FP64>::T>& tot,
                                           WarpCounters* __restrict__ wc,
                                           WarpQueue<FP64>* __restrict__ q,
-                                          EndQueue<FP64>* __restrict__ eq, int lane) {
+                                          EndQueue<FP64>* __restrict__ eq,
+                                          TimesAcc<FP64, TIMES>* __restrict__ ta, int lane) {
   using P = Prec<FP64>;
   using T = typename P::T;
   using Meta = typename P::Meta;
@@ -505,6 +527,9 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
   // the jump's words; `fresh`: claimed, first holding time not drawn yet.
   T s_pend = 0;
   bool fresh = false;
+  // Intermediate times: output k < T at fine grid point k * t_stride.
+  const int t_stride = TIMES ? n_grid / a.n_times : 1;
+  const int n_out = TIMES ? a.n_times - 1 : 0;
 
   // Start walk r of the item (state at s = 0 in the row).
   auto start_walk = [&](uint32_t r_new) {
@@ -537,12 +562,57 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
       src_c = P::add(src_c, P::mul(sfj, simpson_segment<FP64>(kprev >> 1, b >> 1, n_coarse, inv_nc,
                                                              acc, dlj, dl0)));
   };
+  // Intermediate times: the samples at the output grid points in (kprev, g],
+  // all held in the current state j (prefix exponents as in exponents()
+  // with the grid ending at the output point), added to this lane's sums.
+  auto emit_times = [&](int g) {
+    if constexpr (TIMES) {
+      const T dlj = static_cast<T>(m.dl);
+      const T vj = static_cast<T>(__ldg(vv + j));
+      const T h = P::mul(P::add(dl0, dlj), static_cast<T>(0.5));
+      int k = kprev / t_stride + 1;
+      const int k_hi = min(g / t_stride, n_out);
+      for (; k <= k_hi; ++k) {
+        const int gk = k * t_stride;
+        T y;
+        if (COARSE) {
+          const T acc_c = P::fma(P::from_int((gk >> 1) - (kprev >> 1)), dlj, acc);
+          const T accd = P::fma(P::from_int(-(kprev & 1)), dlj, acc_d);
+          T x1 = P::mul(P::sub(acc_c, h), P::mul(inv_n, static_cast<T>(2)));
+          if (IS) x1 = P::add(x1, lw);
+          const T x2 = P::mul(P::add(accd, h), inv_n);
+          y = P::mul(vj, P::mul(P::ex(x1), P::exm1(x2)));
+        } else {
+          const T acc_f = P::fma(P::from_int(gk - kprev), dlj, acc);
+          T x1 = P::mul(P::sub(acc_f, h), inv_n);
+          if (IS) x1 = P::add(x1, lw);
+          y = P::mul(vj, P::ex(x1));
+        }
+        if (neg) y = -y;
+        if (!isfinite(y)) {
+          tot.bad |= kFlagNonFiniteY;
+          y = 0;
+        }
+        ta->v[k - 1][lane] = P::add(ta->v[k - 1][lane], y);
+        if (TRACE)
+          a.trace_times[(row * a.trace_stride + a.trace_base + (r_lo + r)) * n_out + (k - 1)] =
+              static_cast<double>(y);
+      }
+    }
+  };
+  // The still sample at output k (a walk that never leaves the row).
+  auto still_time = [&](int k) -> T {
+    if (COARSE) return static_cast<T>(0);
+    return P::mul(static_cast<T>(__ldg(vv + row)),
+                  P::ex(P::mul(P::mul(P::from_int(k * t_stride), dl0), inv_n)));
+  };
   // Jump at time s_new (after fine grid point g) with bucket word xz and
   // alias coin xw: count the grid points of the segment that ends, pick the
   // next state from the alias table of the current one.
   auto jump = [&](T s_new, uint32_t xz, uint32_t xw) -> bool {
     const int g = P::floor_int(P::mul(s_new, n_fine));
     if (SRC) source_segment(g);
+    if (TIMES) emit_times(g);
     const T dlj = static_cast<T>(m.dl);
     if (COARSE) {
       const int kc_prev = kprev >> 1;   // floor(a/2), also for a = -1
@@ -629,6 +699,10 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
     if (status == 0 && e == 0) {
       // never jumped: counted, its sample y_still is added per item
       ++n_still;
+      if (TRACE && TIMES)
+        for (int k = 1; k <= n_out; ++k)
+          a.trace_times[(row * a.trace_stride + a.trace_base + (r_lo + r)) * n_out + (k - 1)] =
+              static_cast<double>(still_time(k));
       if (TRACE) {
         mlmc_walk_record rec;
         rec.end = j;
@@ -647,13 +721,14 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
       ++n_limit;
       acc_y.add(static_cast<T>(0));
       tot.y2.add_square(static_cast<T>(0));
-    } else if (!TRACE && !SRC && defer) {
+    } else if (!TRACE && !SRC && !TIMES && defer) {
       exponents(end_x1, end_x2);
       ending = true;
       return;
     }
     T y = 0;
     if (status == 0) {
+      if (TIMES) emit_times(n_grid);
       T x1, x2;
       exponents(x1, x2);
       T extra = 0;
@@ -701,8 +776,18 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
     }
   };
 
+  // A walk stopped at the jump limit with its pending jump at time s_at: the
+  // output times it passed keep their samples, the final time gets 0.
+  auto stop_limit = [&](T s_at, bool defer) {
+    if (TIMES) emit_times(P::floor_int(P::mul(s_at, n_fine)));
+    finish(1, defer);
+  };
   // Record of a walk screened as never jumping (trace only).
   auto trace_still = [&](uint32_t rs) {
+    if (TIMES)
+      for (int k = 1; k <= n_out; ++k)
+        a.trace_times[(row * a.trace_stride + a.trace_base + (r_lo + rs)) * n_out + (k - 1)] =
+            static_cast<double>(still_time(k));
     mlmc_walk_record rec;
     rec.end = static_cast<int32_t>(row);
     rec.jumps = 0;
@@ -797,7 +882,7 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
             start_walk(q->r[slot]);
             const T s1 = q->first[slot];  // drawn at screening
             if (static_cast<int64_t>(e) >= a.max_jumps) {
-              finish(1, false);
+              stop_limit(s1, false);
             } else if (jump(s1, q->xz[slot], q->xw[slot])) {
               live = true;
             } else {
@@ -817,7 +902,7 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
           if (!(s_new < static_cast<T>(1))) {
             finish(0, false);
           } else if (static_cast<int64_t>(e) >= a.max_jumps) {
-            finish(1, false);
+            stop_limit(s_new, false);
           } else if (!jump(s_new, x.z, x.w)) {
             finish(2, false);
           }
@@ -844,7 +929,7 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
         // is evaluated at once.
         if (live) {
           if (static_cast<int64_t>(e) >= a.max_jumps) {
-            finish(1, false);
+            stop_limit(s_pend, false);
           } else {
             const uint4 x = keys.draw(make_uint4(c_lo, row32, e, c_hi));
             if (!jump(s_pend, x.z, x.w)) {
@@ -879,7 +964,7 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
           if (!(s_new < static_cast<T>(1))) {
             finish(0, true);
           } else if (static_cast<int64_t>(e) >= a.max_jumps) {
-            finish(1, true);
+            stop_limit(s_new, true);
           } else if (!jump(s_new, x.z, x.w)) {
             finish(2, true);
           }
@@ -894,7 +979,7 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
           if (!(s_pend < static_cast<T>(1))) {
             finish(0, true);  // never jumped
           } else if (static_cast<int64_t>(e) >= a.max_jumps) {
-            finish(1, true);
+            stop_limit(s_pend, true);
           } else if (!jump(s_pend, x.z, x.w)) {
             finish(2, true);
           } else {
@@ -926,9 +1011,20 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
     if (!COARSE || SRC) wc->y2_fixed += static_cast<double>(still) * (yc * yc);
   }
   if (lane == 0 && ys != 0.0) atomicAdd(a.sum_y + row, ys);
+  if constexpr (TIMES) {
+    // per output time: the lanes' sums plus the walks that never jumped
+    for (int k = 1; k <= n_out; ++k) {
+      double yk = static_cast<double>(ta->v[k - 1][lane]);
+      ta->v[k - 1][lane] = 0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) yk += __shfl_xor_sync(kFull, yk, o);
+      if (!COARSE) yk += static_cast<double>(still) * static_cast<double>(still_time(k));
+      if (lane == 0 && yk != 0.0) atomicAdd(a.sum_times + static_cast<int64_t>(k - 1) * a.n + row, yk);
+    }
+  }
 }
 
-template <bool FP64, bool COARSE, bool TRACE, bool IS, bool SRC = false>
+template <bool FP64, bool COARSE, bool TRACE, bool IS, bool SRC = false, bool TIMES = false>
 __global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk(const __grid_constant__ WalkArgs a) {
   using T = typename Prec<FP64>::T;
   const int lane = threadIdx.x & 31;
@@ -951,13 +1047,22 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk(const __grid_constan
   ia.n = a.n;
   ia.nnz = a.nnz;
   ia.still32 = a.still32;
+  ia.n_times = a.n_times;
+  ia.sum_times = a.sum_times;
+  ia.trace_times = a.trace_times;
   __shared__ WarpQueue<FP64> queues[kMaxWarps];
   __shared__ WarpCounters counters[kMaxWarps];
   __shared__ EndQueue<FP64> ends[kMaxWarps];
+  __shared__ TimesAcc<FP64, TIMES> tacc[TIMES ? kMaxWarps : 1];
   WarpQueue<FP64>* q = &queues[threadIdx.x >> 5];
   EndQueue<FP64>* eq = &ends[threadIdx.x >> 5];
   WarpCounters* wc = &counters[threadIdx.x >> 5];
+  TimesAcc<FP64, TIMES>* ta = &tacc[TIMES ? (threadIdx.x >> 5) : 0];
   if (lane == 0) *wc = WarpCounters{};
+  if constexpr (TIMES) {
+    constexpr int kOut = (FP64 ? kMaxTimes64 : kMaxTimes32) - 1;
+    for (int k = 0; k < kOut; ++k) ta->v[k][lane] = 0;
+  }
   __syncwarp();
   LaneTotals<T> tot;
   for (;;) {
@@ -969,9 +1074,10 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk(const __grid_constan
     const int64_t chunk = static_cast<int64_t>(item) - rel * a.chunks_per_row;
     const int64_t r_lo = chunk * a.chunk;
     const int64_t r_hi = min(r_lo + a.chunk, a.reps);
-    walk_item<FP64, COARSE, TRACE, IS, KeysFromParam, SRC>(ia, KeysFromParam{&a.rk},
-                                                                a.row_begin + rel, r_lo, r_hi,
-                                       tot, wc, q, eq, lane);
+    walk_item<FP64, COARSE, TRACE, IS, KeysFromParam, SRC, TIMES>(ia, KeysFromParam{&a.rk},
+                                                                       a.row_begin + rel, r_lo,
+                                                                       r_hi, tot, wc, q, eq, ta,
+                                                                       lane);
   }
   flush_warp(tot, wc, a.totals, a.flags, lane);
 }
@@ -1244,9 +1350,9 @@ cudaError_t launch_to_float(mlmc_plan* p, const double* in, float* out) {
   return cudaGetLastError();
 }
 
-template <bool FP64, bool COARSE, bool TRACE, bool IS, bool SRC>
+template <bool FP64, bool COARSE, bool TRACE, bool IS, bool SRC, bool TIMES = false>
 cudaError_t launch_one(mlmc_plan* p, const WalkArgs& args, int block, cudaStream_t stream) {
-  auto kern = k_walk<FP64, COARSE, TRACE, IS, SRC>;
+  auto kern = k_walk<FP64, COARSE, TRACE, IS, SRC, TIMES>;
   int per_sm = 0;
   cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, 0);
   if (err != cudaSuccess) return err;
@@ -1274,11 +1380,15 @@ cudaError_t launch_one(mlmc_plan* p, const WalkArgs& args, int block, cudaStream
   return cudaGetLastError();
 }
 
-// Proposal and source term are exclusive (checked when either is set).
+// Proposal and source term are exclusive (checked when either is set), and
+// so are the source term and intermediate times.
 template <bool FP64, bool COARSE, bool TRACE>
 cudaError_t dispatch_is(mlmc_plan* p, const WalkArgs& a, int block, bool is, bool src,
                         cudaStream_t st) {
   if (src) return launch_one<FP64, COARSE, TRACE, false, true>(p, a, block, st);
+  if (a.n_times > 1)
+    return is ? launch_one<FP64, COARSE, TRACE, true, false, true>(p, a, block, st)
+              : launch_one<FP64, COARSE, TRACE, false, false, true>(p, a, block, st);
   return is ? launch_one<FP64, COARSE, TRACE, true, false>(p, a, block, st)
             : launch_one<FP64, COARSE, TRACE, false, false>(p, a, block, st);
 }
@@ -1422,6 +1532,9 @@ cudaError_t launch_walk_core(mlmc_plan* p, const WalkLaunch& w, const void* v_wa
   a.work = work;
   a.trace = w.trace;
   a.trace_stride = w.reps;
+  a.n_times = w.n_times > 1 ? w.n_times : 0;
+  a.sum_times = w.sum_times;
+  a.trace_times = w.trace_times;
   const int block = p->sched.block_threads > 0 ? p->sched.block_threads : 256;
   const bool trace = w.trace != nullptr;
   const int64_t cap = p->sched.launch_reps > 0 ? p->sched.launch_reps

@@ -94,6 +94,8 @@ def load(build_if_missing: bool = False):
     lib.mlmc_mlmcl.argtypes = [P, I32, I32, I64, I64, P, ct.c_uint64, P, P]
     lib.mlmc_trace.argtypes = [P, I32, I32, I64, I64, P, ct.c_uint64, P]
     lib.mlmc_trace_noalloc.argtypes = [P, I32, I32, I64, I64, P, ct.c_uint64, P]
+    lib.mlmc_trace_times.argtypes = [P, I32, I32, I64, I64, P, ct.c_uint64, I32, P, P]
+    lib.mlmc_expmv_times.argtypes = [P, P, P, I32, ct.c_uint64]
     lib.mlmc_export_tables.argtypes = [P] + [P] * 11
     lib.mlmc_plan_info.argtypes = [P, ct.POINTER(I64), ct.POINTER(I64), ct.POINTER(I32),
                                    ct.POINTER(D)]
@@ -139,6 +141,7 @@ def load(build_if_missing: bool = False):
     for name in ("mlmc_schedule_default", "mlmc_plan_create", "mlmc_plan_rebuild", "mlmc_expmv",
                  "mlmc_expmv_entry", "mlmc_expmv_sum",
                  "mlmc_stats", "mlmc_mlmcl", "mlmc_trace", "mlmc_trace_noalloc",
+                 "mlmc_trace_times", "mlmc_expmv_times",
                  "mlmc_export_tables", "mlmc_batch_create", "mlmc_batch_expmv",
                  "mlmc_batch_stats", "mlmc_batch_info", "mlmc_batch_autotune",
                  "mlmc_plan_set_proposal", "mlmc_plan_set_tilt", "mlmc_export_tilt",
@@ -270,6 +273,27 @@ class Plan:
         _need(x, 8 * self.n, "x")
         allow = (MLMC_ERR_NOT_CONVERGED,) if allow_not_converged else ()
         return _check(self._lib.mlmc_expmv(self._h, _ptr(v), _ptr(x), ct.c_uint64(seed)), allow)
+
+    def expmv_times(self, v, x_times, n_times: int, seed: int,
+                    allow_not_converged: bool = False) -> int:
+        """x(t k / n_times), k = 1..n_times, from the same walks (x_times:
+        n_times x n float64, host or device; the last row is x(t))."""
+        _need(v, 8 * self.n, "v")
+        _need(x_times, 8 * self.n * n_times, "x_times")
+        allow = (MLMC_ERR_NOT_CONVERGED,) if allow_not_converged else ()
+        return _check(self._lib.mlmc_expmv_times(self._h, _ptr(v), _ptr(x_times), int(n_times),
+                                                 ct.c_uint64(seed)), allow)
+
+    def trace_times(self, level: int, coarse: bool, rep_begin: int, reps: int, v, seed: int,
+                    n_times: int, rec, y_times):
+        """trace() plus each record's samples at the times t k / n_times,
+        k < n_times (y_times: device, n * reps * (n_times - 1) float64)."""
+        _need(v, 8 * self.n, "v")
+        _need(rec, WALK_RECORD_DTYPE.itemsize * self.n * reps, "rec")
+        _need(y_times, 8 * self.n * reps * (n_times - 1), "y_times")
+        _check(self._lib.mlmc_trace_times(self._h, level, int(coarse), rep_begin, reps, _ptr(v),
+                                          ct.c_uint64(seed), int(n_times), _ptr(rec),
+                                          _ptr(y_times)))
 
     def expmv_entry(self, i: int, v, seed: int, allow_not_converged: bool = False) -> float:
         """x_i = (exp(tA)v)_i by walks from row i only (Algorithm 2)."""
