@@ -750,9 +750,14 @@ def run_kernel_workload(args):
                                l2_persist=args.l2_persist)
     plan = M.Plan.from_csr(w.a, w.t, sched, rel_tol=w.tol, stream=stream.cuda_stream)
     l0 = plan.info()["l0"]
-    l2win = plan.l2_window()
     n = w.a.n
     dv = torch.from_numpy(w.v).cuda()
+    if args.kernel_tilt:
+        # the walk the default workload's solve runs: learned tilted clocks
+        with M.MLP(seed=3, stream=stream.cuda_stream) as net:
+            net.learn_tilt(plan, dv, seed=5, pilot_walks=args.pilot, steps=300, batch=8192,
+                           clocks=True, rounds=args.rounds)
+    l2win = plan.l2_window()
     sums = torch.zeros(n, dtype=torch.float64, device="cuda")
     tot = torch.zeros(5, dtype=torch.float64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -790,7 +795,7 @@ def run_kernel_workload(args):
     lv = [dict(coarse=False, walks=res["l0"]["walks"], jumps=res["l0"]["jumps"],
                still_walks=res["l0"]["still_walks"], launches=1)]
     roof = walk_roofline(lv, 1e-3 * statistics.mean(res["l0"]["launch_ms"]), clocks, peaks,
-                         statistics.mean(res["l0"]["launch_ms"]))
+                         statistics.mean(res["l0"]["launch_ms"]), proposal=args.kernel_tilt)
     out = {"metric": "walk kernel alone: walk-steps/s at l0 (one launch, L2 flushed before it)",
            "value": res["l0"]["events_per_s"], "unit": UNIT, "higher_is_better": True,
            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "dtype": "f32",
@@ -798,7 +803,8 @@ def run_kernel_workload(args):
            "config": {"workload": w.name, "n": n, "nnz": w.a.nnz, "t": w.t, "l0": l0,
                       "walks_per_row": reps, "l2": "flushed before each launch",
                       "walks_per_lane": args.walks_per_lane or "default",
-                      "block": args.block or "default", "l2_window": l2win},
+                      "block": args.block or "default", "l2_window": l2win,
+                      "walk": "learned tilted clocks and jumps" if args.kernel_tilt else "plain"},
            "levels": res, "roofline": roof, "clocks": clocks}
     print(json.dumps(out), flush=True)
     plan.close()
@@ -1078,6 +1084,9 @@ def main():
                     help="--workload kernel: ba = the metric's graph (short walks), "
                          "lap3d = 64^3 Laplacian at t = 1 (long walks), c4 = convection-diffusion "
                          "128^3, c5 = BA n = 1e6 m = 8 (tables larger than L2)")
+    ap.add_argument("--kernel-tilt", action="store_true",
+                    help="--workload kernel: time the walk with the learned tilted proposal "
+                         "(the default workload's solve)")
     ap.add_argument("--l2-persist", type=int, default=1, choices=[0, 1],
                     help="--workload kernel: L2 access-policy window over the tables")
     ap.add_argument("--walks-per-lane", type=int, default=0,

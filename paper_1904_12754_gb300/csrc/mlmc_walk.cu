@@ -570,7 +570,9 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
       const T dlj = static_cast<T>(m.dl);
       const T vj = static_cast<T>(__ldg(vv + j));
       const T h = P::mul(P::add(dl0, dlj), static_cast<T>(0.5));
-      int k = kprev / t_stride + 1;
+      // the first output after grid point kprev (kprev = -1 before the first
+      // jump: C++ division truncates toward zero, so that case is explicit)
+      int k = kprev < 0 ? 1 : kprev / t_stride + 1;
       const int k_hi = min(g / t_stride, n_out);
       for (; k <= k_hi; ++k) {
         const int gk = k * t_stride;

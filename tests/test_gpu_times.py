@@ -93,7 +93,8 @@ def test_solution_at_intermediate_times(prec):
     # every k against the FP64 judge
     w = I.workload_c1()
     from paper_1904_12754_gb300 import mlmc as M
-    sched = M.schedule_default(precision=prec, num_levels=3, max_levels=8, l0=2)
+    sched = M.schedule_default(precision=prec, num_levels=3, max_levels=8, l0=2,
+                               time_budget_s=60.0)
     n_times = 4
     xt = np.zeros((n_times, w.a.n))
     with M.Plan.from_csr(w.a, w.t, sched, rel_tol=1e-2, stream=torch_cuda().cuda.current_stream().cuda_stream) as plan:
