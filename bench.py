@@ -572,7 +572,8 @@ def run_batch_workload(args):
             "batched": {"seconds": t_batch, "walk_steps_per_s": batch_events / t_batch,
                         "rounds": info["rounds"], "gpu_seconds": info["gpu_seconds"],
                         "converged": info["converged"], "max_est_rel_err": max(ests),
-                        "create_s": t_create, "walks_per_lane_by_bucket": batch.autotune()},
+                        "create_s": t_create, "walks_per_lane_by_bucket": batch.autotune(),
+                        "round_kernel_block": batch.block()},
             "plain": {"seconds": t_plain, "walk_steps_per_s": plain_events / t_plain,
                       "converged": plain_conv},
             "speedup": t_plain / t_batch}

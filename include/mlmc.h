@@ -442,17 +442,21 @@ typedef struct mlmc_batch mlmc_batch;
  * schedule and budgets (NULL = the first plan's); each plan keeps its own
  * l0.  rel_tol is the per-problem target.  cuda_stream is the caller's
  * stream: mlmc_batch_expmv orders its work after work queued there.
- * Creation runs the launch-shape autotuner (walks per lane of a work item,
- * per problem-size bucket n < 1e4, < 1e5, >= 1e5; a few short walk
- * launches) and captures the CUDA graph of one round's reductions. */
+ * Creation runs the launch-shape autotuner (walks per lane of a work item
+ * from {4, 16, 64} per problem-size bucket n < 1e4, < 1e5, >= 1e5, then
+ * threads per block of the round kernel from {128, 256}; a few short trial
+ * launches of the round kernel on the batch's own problems) and captures the
+ * CUDA graph of one round. */
 mlmc_status mlmc_batch_create(mlmc_batch **out, mlmc_plan *const *plans, int32_t count,
                               const mlmc_schedule *sched, double rel_tol, void *cuda_stream);
 
 /* x_k = exp(t_k A_k) v_k for every problem k, by Algorithm 1 run for all
- * problems in lockstep rounds.  A round launches the walk kernel once per
- * (problem, level, replica range) segment, spread over the batch's streams
- * so that small problems run side by side, then one graph launch does the
- * batched reductions, and the host synchronises once.  v[k], x[k]: host or
+ * problems in lockstep rounds.  A round is one launch of one captured
+ * graph: the round's table of (problem, level, replica range) segments is
+ * uploaded, one persistent walk kernel walks every segment (warps pull
+ * (segment, row, chunk) items from a global counter and run the
+ * single-plan walk on the segment's tables), the batched reductions follow,
+ * and the host synchronises once.  v[k], x[k]: host or
  * device pointers to n_k doubles; seeds[k]: Philox key of problem k (the
  * walks are those a single-plan solve with that seed draws, with the plan's
  * jump law: its proposal when one is set).  Returns
@@ -471,7 +475,8 @@ mlmc_status mlmc_batch_stats(const mlmc_batch *batch, int32_t problem, mlmc_leve
 mlmc_status mlmc_batch_info(const mlmc_batch *batch, int64_t *rounds, double *gpu_seconds,
                             int32_t *converged);
 
-/* The autotuner's walks per lane for the three size buckets (cap >= 3). */
+/* The autotuner's walks per lane for the three size buckets (cap >= 3) and,
+ * with cap >= 4, the round kernel's threads per block in entry 3. */
 mlmc_status mlmc_batch_autotune(const mlmc_batch *batch, int32_t *walks_per_lane, int32_t cap);
 
 void mlmc_batch_destroy(mlmc_batch *batch);

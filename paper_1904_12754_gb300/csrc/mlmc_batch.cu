@@ -2,24 +2,24 @@
 // of different sizes, several right-hand sides per plan) solved together.
 //
 // The controller of Algorithm 1 runs for every problem in lockstep rounds.
-// A round launches, for every (problem, level, replica range) segment, the
-// plan's own walk kernel (the single-plan launch sequence, with the problem's
-// Philox round keys as a launch constant and the screened path for short
-// walks) on one of kStreams streams, so that the segments of small problems
-// run side by side; then, after the streams join, one captured graph does
-//   H2D  reduction tasks (pinned host buffer, fixed size)
-//   k_batch_reduce: sum_i S_l,i^2 for every active (problem, level) and
-//                 ||x||^2 for every active problem
+// A round is one launch of one captured graph:
+//   H2D  the round's segment table (pinned host buffer, fixed size): one
+//        segment per (problem, level, replica range) with work to do;
+//   k_walk_batch: one persistent walk kernel over every segment, warps
+//        pulling (segment, row, chunk of walks) items from a global counter
+//        and running the single-plan walk (screening, queues, the problem's
+//        Philox keys) on the segment's tables;
+//   H2D  reduction tasks; k_batch_reduce: sum_i S_l,i^2 for every active
+//        (problem, level) and ||x||^2 for every active problem;
 //   D2H  per-(problem, level) totals and per-problem norms (pinned)
 // and the host synchronises once.  Between rounds the host applies each
 // problem's sample-size rule (the same readings as the single-plan
-// controller) and forms the next segments.  A segment costs one kernel
-// launch (a few microseconds of host time), so a round of thousands of
-// segments is still far shorter than its walks.
+// controller) and writes the next segment table.
 //
-// Launch shape: walks per lane of a work item (the item is 32 x that many
-// walks of one row) is picked per problem-size bucket by a short timing
-// trial at batch creation (autotuner); blocks are the plans' block size.
+// Launch shape (autotuner at batch creation, timed on the batch's own
+// problems with the batch kernel): walks per lane of a work item (the item
+// is 32 x that many walks of one row) per problem-size bucket from {4, 16,
+// 64}, then threads per block from {128, 256} for the round kernel.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -36,7 +36,6 @@ constexpr int kRedBlock = 256;
 constexpr int kBuckets = 3;  // n < 1e4, 1e4 <= n < 1e5, n >= 1e5
 constexpr int64_t kRoundWalks = int64_t{1} << 35;  // walks per round, at most
 
-constexpr int kStreams = 8;  // streams the segments of a round are spread over
 
 struct ReduceTask {
   const double* vec;    // level sums S (sumsq task) or unused (norm task)
@@ -158,11 +157,9 @@ struct mlmc_batch {
   bool fp64 = false;
   int num_sms = 0;
   int device = 0;
-  cudaStream_t stream = nullptr;   // controller stream: copies, reductions, graph
+  cudaStream_t stream = nullptr;   // controller stream: the round graph, copies
   cudaStream_t caller = nullptr;
-  cudaStream_t seg_streams[kStreams] = {};  // the rounds' walk launches
-  cudaEvent_t ev_fork = nullptr;
-  cudaEvent_t ev_join[kStreams] = {};
+  int block = 256;                 // threads per block of the round kernel (autotuned)
   std::vector<int64_t> n;          // per problem
   std::vector<int64_t> offset;     // row offset of each problem in the contiguous buffers
   int64_t total_rows = 0;
@@ -177,7 +174,13 @@ struct mlmc_batch {
   float* d_v32 = nullptr;          // total_rows
   double* d_x = nullptr;           // total_rows
   double** d_xptr = nullptr;       // nprob pointers into d_x
-  unsigned long long* d_work = nullptr;  // one work counter per segment stream
+  unsigned long long* d_work = nullptr;  // the round kernel's work counter
+  // Segment table of a round (device + pinned host mirror):
+  // [BatchRound][max_segs x BatchSeg]
+  unsigned char* d_round = nullptr;
+  unsigned char* h_round = nullptr;
+  size_t round_bytes = 0;
+  int max_segs = 0;
   uint32_t* d_flags = nullptr;
   // Round table (device + pinned host mirror): [BatchTables][tasks][inv_m]
   unsigned char* d_tab = nullptr;
@@ -217,11 +220,8 @@ void free_batch(mlmc_batch* b) {
   if (b->h_norm) cudaFreeHost(b->h_norm);
   if (b->ev0) cudaEventDestroy(b->ev0);
   if (b->ev1) cudaEventDestroy(b->ev1);
-  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
-  for (int i = 0; i < kStreams; ++i) {
-    if (b->ev_join[i]) cudaEventDestroy(b->ev_join[i]);
-    if (b->seg_streams[i]) cudaStreamDestroy(b->seg_streams[i]);
-  }
+  cudaFree(b->d_round);
+  if (b->h_round) cudaFreeHost(b->h_round);
   if (b->stream) cudaStreamDestroy(b->stream);
   delete b;
 }
@@ -236,8 +236,17 @@ mlmc_status capture_round_graph(mlmc_batch* b) {
   const BatchTables* dt = reinterpret_cast<const BatchTables*>(b->d_tab);
   const ReduceTask* dtasks = reinterpret_cast<const ReduceTask*>(b->d_tab + b->off_tasks);
   const double* dinvm = reinterpret_cast<const double*>(b->d_tab + b->off_invm);
+  const BatchRound* dround = reinterpret_cast<const BatchRound*>(b->d_round);
+  const BatchSeg* dsegs = reinterpret_cast<const BatchSeg*>(b->d_round + 256);
   BATCH_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-  cudaError_t err = cudaMemcpyAsync(b->d_tab, b->h_tab, b->tab_bytes, cudaMemcpyHostToDevice, b->stream);
+  cudaError_t err = cudaMemcpyAsync(b->d_round, b->h_round, b->round_bytes, cudaMemcpyHostToDevice,
+                                    b->stream);
+  if (err == cudaSuccess) err = cudaMemsetAsync(b->d_work, 0, sizeof(unsigned long long), b->stream);
+  if (err == cudaSuccess)
+    err = launch_walk_batch(b->fp64, dround, dsegs, b->d_work, b->d_flags, b->num_sms, b->block,
+                            b->stream);
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(b->d_tab, b->h_tab, b->tab_bytes, cudaMemcpyHostToDevice, b->stream);
   if (err == cudaSuccess) {
     k_batch_reduce<<<b->num_sms * 8, kRedBlock, 0, b->stream>>>(dt, dtasks, b->d_probs, dinvm,
                                                                   b->max_levels);
@@ -262,30 +271,74 @@ mlmc_status capture_round_graph(mlmc_batch* b) {
   return MLMC_OK;
 }
 
-// Time k_walk on one plan with a given walks-per-lane setting (autotuner).
-double trial_ms(mlmc_plan* p, int per_lane, double* scratch, cudaEvent_t e0, cudaEvent_t e1) {
-  const int32_t saved = p->sched.walks_per_lane;
-  p->sched.walks_per_lane = per_lane;
-  WalkLaunch w;
-  w.level = p->l0;
-  w.coarse = false;
-  w.rep_begin = 0;
-  // Enough walks per row that every candidate's item size is reachable
-  // (32 x 64 = 2048), but at most ~2^31 walks.
-  w.reps = std::max<int64_t>(64, std::min<int64_t>(2048, (int64_t{1} << 31) / p->n));
-  w.seed = 0x5eedull;
-  w.v = p->d_v;
-  w.sum_y = scratch;
-  w.totals = scratch + p->n;
-  cudaMemsetAsync(p->d_v, 0, sizeof(double) * p->n, p->stream);
-  cudaEventRecord(e0, p->stream);
-  cudaError_t err = launch_walk(p, w);
-  cudaEventRecord(e1, p->stream);
-  cudaEventSynchronize(e1);
-  p->sched.walks_per_lane = saved;
+BatchRound* round_hdr(mlmc_batch* b) { return reinterpret_cast<BatchRound*>(b->h_round); }
+BatchSeg* round_segs(mlmc_batch* b) { return reinterpret_cast<BatchSeg*>(b->h_round + 256); }
+
+// Segment of problem k, level slot l: walks rep_begin .. rep_begin+reps-1 of
+// every row, walks per lane of an item per_lane; its items start at `first`.
+BatchSeg make_seg(mlmc_batch* b, int k, int l, int64_t rep_begin, int64_t reps, int64_t per_lane,
+                  uint64_t seed, unsigned long long first) {
+  mlmc_plan* p = b->plans[k];
+  const int64_t L = b->max_levels;
+  BatchSeg g{};
+  g.meta = walk_meta(p, b->fp64);
+  g.alias = p->proposal_active ? static_cast<const void*>(p->d_alias_is)
+                               : static_cast<const void*>(p->d_fused);
+  g.v_walk = b->fp64 ? static_cast<const void*>(b->d_v + b->offset[k])
+                     : static_cast<const void*>(b->d_v32 + b->offset[k]);
+  g.still32 = walk_still32(p);
+  g.sum_y = b->d_sums + b->offset[k] * L + static_cast<int64_t>(l) * b->n[k];
+  g.totals = b->d_totals + (static_cast<int64_t>(k) * L + l) * kTotSlots;
+  g.n = b->n[k];
+  g.nnz = p->nnz;
+  g.rep_begin = rep_begin;
+  g.reps = reps;
+  per_lane = std::max<int64_t>(1, std::min<int64_t>(per_lane, (reps + 31) / 32));
+  g.chunk = 32 * per_lane;
+  g.chunks_per_row = (reps + g.chunk - 1) / g.chunk;
+  g.item_begin = first;
+  g.max_jumps = p->sched.max_jumps_per_walk;
+  g.level = p->l0 + l;
+  g.coarse = l > 0 ? 1 : 0;
+  g.is = p->proposal_active ? 1 : 0;
+  g.ctr3 = static_cast<uint32_t>(g.level) & 0x3Fu;
+  g.rk = philox_round_keys(static_cast<uint32_t>(seed & 0xFFFFFFFFull), static_cast<uint32_t>(seed >> 32));
+  return g;
+}
+
+unsigned long long seg_items(const BatchSeg& g) {
+  return static_cast<unsigned long long>(g.n) * static_cast<unsigned long long>(g.chunks_per_row);
+}
+
+// Autotuner trial: one launch of the round kernel over the given problems'
+// l0 walks (reps per row each, into the batch's sums, which every
+// mlmc_batch_expmv clears), timed with events; ms per walk.
+double trial_round(mlmc_batch* b, const std::vector<int>& probs, int64_t reps, int64_t per_lane,
+                   int block) {
+  BatchSeg* segs = round_segs(b);
+  unsigned long long items = 0;
+  int nseg = 0;
+  int64_t walks = 0;
+  for (int k : probs) {
+    segs[nseg] = make_seg(b, k, 0, 0, reps, per_lane, 0x5eedull, items);
+    items += seg_items(segs[nseg]);
+    walks += reps * b->n[k];
+    ++nseg;
+  }
+  round_hdr(b)->total_items = items;
+  round_hdr(b)->nseg = nseg;
+  const BatchRound* dround = reinterpret_cast<const BatchRound*>(b->d_round);
+  const BatchSeg* dsegs = reinterpret_cast<const BatchSeg*>(b->d_round + 256);
+  cudaMemcpyAsync(b->d_round, b->h_round, b->round_bytes, cudaMemcpyHostToDevice, b->stream);
+  cudaMemsetAsync(b->d_work, 0, sizeof(unsigned long long), b->stream);
+  cudaEventRecord(b->ev0, b->stream);
+  cudaError_t err = launch_walk_batch(b->fp64, dround, dsegs, b->d_work, b->d_flags, b->num_sms,
+                                      block, b->stream);
+  cudaEventRecord(b->ev1, b->stream);
+  cudaEventSynchronize(b->ev1);
   float ms = 0.f;
-  if (err != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) return 1e30;
-  return static_cast<double>(ms) / static_cast<double>(w.reps * p->n);
+  if (err != cudaSuccess || cudaEventElapsedTime(&ms, b->ev0, b->ev1) != cudaSuccess) return 1e30;
+  return static_cast<double>(ms) / static_cast<double>(walks > 0 ? walks : 1);
 }
 
 }  // namespace
@@ -343,11 +396,6 @@ mlmc_status mlmc_batch_create(mlmc_batch** out, mlmc_plan* const* plans, int32_t
   BC(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking), "stream");
   BC(cudaEventCreate(&b->ev0), "event");
   BC(cudaEventCreate(&b->ev1), "event");
-  BC(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming), "event");
-  for (int i = 0; i < kStreams; ++i) {
-    BC(cudaStreamCreateWithFlags(&b->seg_streams[i], cudaStreamNonBlocking), "stream");
-    BC(cudaEventCreateWithFlags(&b->ev_join[i], cudaEventDisableTiming), "event");
-  }
   const int64_t L = b->max_levels;
   BC(cudaMalloc(&b->d_probs, sizeof(BatchProblemDev) * count), "alloc");
   BC(cudaMalloc(&b->d_sums, sizeof(double) * b->total_rows * L), "alloc sums");
@@ -357,7 +405,12 @@ mlmc_status mlmc_batch_create(mlmc_batch** out, mlmc_plan* const* plans, int32_t
   BC(cudaMalloc(&b->d_v32, sizeof(float) * b->total_rows), "alloc");
   BC(cudaMalloc(&b->d_x, sizeof(double) * b->total_rows), "alloc");
   BC(cudaMalloc(&b->d_xptr, sizeof(double*) * count), "alloc");
-  BC(cudaMalloc(&b->d_work, sizeof(unsigned long long) * kStreams), "alloc");
+  BC(cudaMalloc(&b->d_work, sizeof(unsigned long long)), "alloc");
+  b->max_segs = static_cast<int>(count * L);
+  b->round_bytes = 256 + sizeof(BatchSeg) * static_cast<size_t>(b->max_segs);
+  BC(cudaMalloc(&b->d_round, b->round_bytes), "alloc segment table");
+  BC(cudaMallocHost(&b->h_round, b->round_bytes), "alloc pinned segment table");
+  std::memset(b->h_round, 0, b->round_bytes);
   BC(cudaMalloc(&b->d_flags, sizeof(uint32_t) * 4), "alloc");
   b->max_tasks = static_cast<int>(count * L + count);
   b->off_tasks = 256;
@@ -379,29 +432,55 @@ mlmc_status mlmc_batch_create(mlmc_batch** out, mlmc_plan* const* plans, int32_t
      "upload problems");
   BC(cudaMemcpy(b->d_xptr, xptr.data(), sizeof(double*) * count, cudaMemcpyHostToDevice), "upload");
 
-  // Autotuner: walks per lane of a work item, per problem-size bucket, timed
-  // on the largest plan of each bucket at its l0 (candidates 4, 16, 64).
+  // Autotuner, timed with the round kernel on this batch's problems at their
+  // l0 (zero right-hand sides; the trial's sums are cleared by every solve):
+  // walks per lane of a work item per problem-size bucket from {4, 16, 64}
+  // (256 walks per row, the bucket's problems only), then threads per block
+  // of the round kernel from {128, 256} (every problem).  Blocks of 512 would
+  // need the walk's per-warp queues of 16 warps in one block's shared memory
+  // (over 48 KB for FP64 walks).
   {
-    double* scratch = nullptr;
-    int64_t nmax = 0;
-    for (int k = 0; k < count; ++k) nmax = std::max(nmax, b->n[k]);
-    BC(cudaMalloc(&scratch, sizeof(double) * (nmax + kTotSlots)), "alloc trial");
+    BC(cudaMemsetAsync(b->d_v, 0, sizeof(double) * b->total_rows, b->stream), "memset");
+    BC(cudaMemsetAsync(b->d_v32, 0, sizeof(float) * b->total_rows, b->stream), "memset");
+    BC(cudaMemsetAsync(b->d_sums, 0, sizeof(double) * b->total_rows * L, b->stream), "memset");
+    BC(cudaMemsetAsync(b->d_totals, 0, sizeof(double) * count * L * kTotSlots, b->stream), "memset");
+    std::vector<int> all;
     for (int bk = 0; bk < kBuckets; ++bk) {
-      int best_k = -1;
+      std::vector<int> members;
       for (int k = 0; k < count; ++k)
-        if (bucket_of(b->n[k]) == bk && (best_k < 0 || b->n[k] > b->n[best_k])) best_k = k;
-      if (best_k < 0) continue;
+        if (bucket_of(b->n[k]) == bk) members.push_back(k);
+      all.insert(all.end(), members.begin(), members.end());
+      if (members.empty()) continue;
       double best = 1e300;
       for (int cand : {4, 16, 64}) {
-        trial_ms(plans[best_k], cand, scratch, b->ev0, b->ev1);  // warm
-        const double t = trial_ms(plans[best_k], cand, scratch, b->ev0, b->ev1);
+        trial_round(b, members, 256, cand, 256);  // warm
+        const double t = trial_round(b, members, 256, cand, 256);
         if (t < best) {
           best = t;
           b->per_lane[bk] = cand;
         }
       }
     }
-    cudaFree(scratch);
+    double best = 1e300;
+    for (int blk : {128, 256}) {
+      BatchSeg* segs = round_segs(b);
+      (void)segs;
+      // per-bucket walks per lane as tuned: one trial per bucket's problems
+      double t = 0.0;
+      for (int bk = 0; bk < kBuckets; ++bk) {
+        std::vector<int> members;
+        for (int k = 0; k < count; ++k)
+          if (bucket_of(b->n[k]) == bk) members.push_back(k);
+        if (members.empty()) continue;
+        trial_round(b, members, 256, b->per_lane[bk], blk);  // warm
+        t += trial_round(b, members, 256, b->per_lane[bk], blk);
+      }
+      if (t < best) {
+        best = t;
+        b->block = blk;
+      }
+    }
+    BC(cudaStreamSynchronize(b->stream), "autotune");
   }
   {
     mlmc_status st = capture_round_graph(b);
@@ -417,6 +496,7 @@ void mlmc_batch_destroy(mlmc_batch* b) { free_batch(b); }
 mlmc_status mlmc_batch_autotune(const mlmc_batch* b, int32_t* walks_per_lane, int32_t cap) {
   if (!b || !walks_per_lane) return bfail(MLMC_ERR_INVALID_ARG, "NULL argument");
   for (int k = 0; k < kBuckets && k < cap; ++k) walks_per_lane[k] = b->per_lane[k];
+  if (cap > kBuckets) walks_per_lane[kBuckets] = b->block;
   return MLMC_OK;
 }
 
@@ -458,53 +538,35 @@ mlmc_status mlmc_batch_expmv(mlmc_batch* b, const double* const* v, double* cons
   bool out_of_time = false;
   for (;;) {
     NvtxRange range("mlmc batch round");
-    // The round's walks: segments of bounded total size, each launched on
-    // one of the segment streams after the work queued so far.
+    // The round's walks: a table of segments of bounded total size, walked
+    // by one launch of the round kernel inside the round graph.
     BATCH_CUDA(cudaEventRecord(b->ev0, b->stream), "event");
-    BATCH_CUDA(cudaEventRecord(b->ev_fork, b->stream), "event");
-    for (int i = 0; i < kStreams; ++i)
-      BATCH_CUDA(cudaStreamWaitEvent(b->seg_streams[i], b->ev_fork, 0), "wait");
+    BatchSeg* segs = round_segs(b);
     int nseg = 0;
     int64_t walks = 0;
+    unsigned long long items = 0;
     for (int k = 0; k < K; ++k) {
       ProblemState& s = b->state[k];
       if (s.done) continue;
-      mlmc_plan* p = b->plans[k];
       for (int l = 0; l < s.nl; ++l) {
         int64_t reps = want[k * L + l];
         if (reps <= 0) continue;
-        if (walks >= kRoundWalks) break;
+        if (walks >= kRoundWalks || nseg >= b->max_segs) break;
         const int64_t room = std::max<int64_t>(1, (kRoundWalks - walks) / b->n[k]);
         reps = std::min(reps, room);
-        WalkLaunch w;
-        w.level = p->l0 + l;
-        w.coarse = l > 0;
-        w.rep_begin = s.reps[l];
-        w.reps = reps;
-        w.seed = seeds[k];
-        w.sum_y = b->d_sums + b->offset[k] * L + static_cast<int64_t>(l) * b->n[k];
-        w.totals = b->d_totals + (static_cast<int64_t>(k) * L + l) * kTotSlots;
-        const void* v_walk = b->fp64 ? static_cast<const void*>(b->d_v + b->offset[k])
-                                     : static_cast<const void*>(b->d_v32 + b->offset[k]);
-        const int64_t per_lane =
-            std::max<int64_t>(1, std::min<int64_t>(b->per_lane[bucket_of(b->n[k])], (reps + 31) / 32));
-        const int si = nseg % kStreams;
-        int64_t nl = 0;
-        BATCH_CUDA(launch_walk_segment(p, w, v_walk, per_lane, b->d_work + si, b->d_flags,
-                                       b->seg_streams[si], &nl),
-                   "walk launch");
-        s.launches[l] += nl;
-        b->launches += nl;
+        segs[nseg] = make_seg(b, k, l, s.reps[l], reps, b->per_lane[bucket_of(b->n[k])], seeds[k],
+                              items);
+        items += seg_items(segs[nseg]);
         ++nseg;
+        s.launches[l] += 1;
         walks += reps * b->n[k];
         want[k * L + l] -= reps;
         s.reps[l] += reps;
       }
     }
-    for (int i = 0; i < kStreams; ++i) {
-      BATCH_CUDA(cudaEventRecord(b->ev_join[i], b->seg_streams[i]), "event");
-      BATCH_CUDA(cudaStreamWaitEvent(b->stream, b->ev_join[i], 0), "wait");
-    }
+    round_hdr(b)->total_items = items;
+    round_hdr(b)->nseg = nseg;
+    if (nseg > 0) ++b->launches;
     // Reduction tasks of every active problem.
     BatchTables* th = tab_hdr(b);
     ReduceTask* tasks = tab_tasks(b);

@@ -263,6 +263,40 @@ cudaError_t launch_walk_segment(mlmc_plan* p, const WalkLaunch& w, const void* v
                                 int64_t per_lane, unsigned long long* work, uint32_t* flags,
                                 cudaStream_t stream, int64_t* launches = nullptr);
 
+// Batched rounds (mlmc_batch.cu): one persistent walk launch over every
+// (problem, level, replica range) segment of a round.  A segment's items are
+// the global work items [item_begin, item_begin + n * chunks_per_row); the
+// kernel reads the round's header and segments from device memory, so one
+// captured graph serves every round.
+struct BatchSeg {
+  const void* meta;           // row records of the problem's plan (its walk precision)
+  const void* alias;          // fused entries, or proposal entries when is != 0
+  const void* v_walk;         // right-hand side in the walk precision
+  const int32_t* still32;     // FP32: per-row still threshold index
+  double* sum_y;              // per-row sums of the (problem, level)
+  double* totals;             // kTotSlots totals of the (problem, level)
+  int64_t n, nnz;
+  int64_t rep_begin, reps;    // replica range of every row
+  int64_t chunk;              // walks per item (32 x walks per lane)
+  int64_t chunks_per_row;
+  unsigned long long item_begin;
+  int64_t max_jumps;
+  int32_t level, coarse, is, pad;
+  uint32_t ctr3, pad2;
+  PhiloxRoundKeys rk;         // the problem's seed
+};
+struct BatchRound {
+  unsigned long long total_items;
+  int32_t nseg;
+  int32_t pad;
+};
+// Launch the persistent walk kernel of a round on `stream` (grid: every SM
+// at its occupancy for `block` threads); the header and segments are read
+// from device memory.
+cudaError_t launch_walk_batch(bool fp64, const BatchRound* round, const BatchSeg* segs,
+                              unsigned long long* work, uint32_t* flags, int num_sms, int block,
+                              cudaStream_t stream);
+
 // Reductions (mlmc_reduce.cu).
 // out[0] += sum_i a_i, out[1] += sum_i a_i^2 (out must be zeroed by the caller).
 cudaError_t launch_sum_sumsq(mlmc_plan* p, const double* a, double* out);

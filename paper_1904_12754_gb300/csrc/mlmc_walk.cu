@@ -1085,6 +1085,103 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk(const __grid_constan
 }
 
 // ---------------------------------------------------------------------------
+// Batched rounds: one persistent launch walks every segment of a round.  A
+// warp takes the next global work item, finds its segment (binary search of
+// the segments' first items), and runs the same walk_item as the single-plan
+// kernel with the segment's tables, right-hand side and Philox round keys
+// (copied to shared memory when the warp changes segment); its totals go to
+// the segment's (problem, level) after every item.
+// ---------------------------------------------------------------------------
+struct KeysFromShared {
+  const PhiloxRoundKeys* rk;  // in shared memory
+  __device__ __forceinline__ uint4 draw(uint4 c) const { return philox4x32_10(c, *rk); }
+};
+
+template <bool FP64>
+__global__ void __launch_bounds__(256, FP64 ? 3 : 4)
+    k_walk_batch(const BatchRound* __restrict__ round, const BatchSeg* __restrict__ segs,
+                 unsigned long long* __restrict__ work, uint32_t* __restrict__ flags) {
+  using T = typename Prec<FP64>::T;
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  __shared__ WarpQueue<FP64> queues[kMaxWarps];
+  __shared__ WarpCounters counters[kMaxWarps];
+  __shared__ EndQueue<FP64> ends[kMaxWarps];
+  __shared__ PhiloxRoundKeys keys[kMaxWarps];
+  WarpQueue<FP64>* q = &queues[warp];
+  EndQueue<FP64>* eq = &ends[warp];
+  WarpCounters* wc = &counters[warp];
+  if (lane == 0) *wc = WarpCounters{};
+  __syncwarp();
+  const unsigned long long total = round->total_items;
+  const int nseg = round->nseg;
+  LaneTotals<T> tot;
+  int loaded = -1;
+  for (;;) {
+    unsigned long long item = 0;
+    if (lane == 0) item = atomicAdd(work, 1ull);
+    item = __shfl_sync(kFull, item, 0);
+    if (item >= total) break;
+    // the last segment whose first item is <= item
+    int lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (segs[mid].item_begin <= item) lo = mid; else hi = mid - 1;
+    }
+    const BatchSeg& sg = segs[lo];
+    if (lo != loaded) {
+      if (lane < 10) {
+        keys[warp].k0[lane] = sg.rk.k0[lane];
+        keys[warp].k1[lane] = sg.rk.k1[lane];
+      }
+      __syncwarp();
+      loaded = lo;
+    }
+    ItemArgs ia;
+    ia.meta = sg.meta;
+    ia.alias = sg.alias;
+    ia.v_walk = sg.v_walk;
+    ia.level = sg.level;
+    ia.ctr3 = sg.ctr3;
+    ia.key0 = sg.rk.k0[0];
+    ia.key1 = sg.rk.k1[0];
+    ia.max_jumps = sg.max_jumps;
+    ia.sum_y = sg.sum_y;
+    ia.rep_begin = sg.rep_begin;
+    ia.trace = nullptr;
+    ia.trace_stride = 0;
+    ia.trace_base = 0;
+    ia.f_walk = nullptr;
+    ia.t = 0.0;
+    ia.n = sg.n;
+    ia.nnz = sg.nnz;
+    ia.still32 = sg.still32;
+    ia.n_times = 0;
+    ia.sum_times = nullptr;
+    ia.trace_times = nullptr;
+    const unsigned long long local = item - sg.item_begin;
+    const int64_t row = static_cast<int64_t>(local / static_cast<unsigned long long>(sg.chunks_per_row));
+    const int64_t chunk = static_cast<int64_t>(local) - row * sg.chunks_per_row;
+    const int64_t r_lo = chunk * sg.chunk;
+    const int64_t r_hi = min(r_lo + sg.chunk, sg.reps);
+    const KeysFromShared kk{&keys[warp]};
+    TimesAcc<FP64, false>* ta = nullptr;
+    if (sg.is) {
+      if (sg.coarse)
+        walk_item<FP64, true, false, true, KeysFromShared>(ia, kk, row, r_lo, r_hi, tot, wc, q, eq, ta, lane);
+      else
+        walk_item<FP64, false, false, true, KeysFromShared>(ia, kk, row, r_lo, r_hi, tot, wc, q, eq, ta, lane);
+    } else {
+      if (sg.coarse)
+        walk_item<FP64, true, false, false, KeysFromShared>(ia, kk, row, r_lo, r_hi, tot, wc, q, eq, ta, lane);
+      else
+        walk_item<FP64, false, false, false, KeysFromShared>(ia, kk, row, r_lo, r_hi, tot, wc, q, eq, ta, lane);
+    }
+    flush_warp(tot, wc, sg.totals, flags, lane);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Forward mode (Eq. 5): walk g starts at s ~ w_s / W (integer weights, see
 // mlmc_forward.cu), runs on the tables of B = A^T, and adds
 // y = (v_s W / w_s) sign e^{E} (level l0) or ... e^{E_c} expm1(E_f - E_c)
@@ -1617,6 +1714,21 @@ cudaError_t launch_walk_scratch(mlmc_plan* p, const WalkLaunch& w, unsigned long
   if (err != cudaSuccess) return err;
   return launch_walk_core(p, w, v_walk, f_walk, work, p->d_flags, p->sched.walks_per_lane,
                           p->stream, launches);
+}
+
+cudaError_t launch_walk_batch(bool fp64, const BatchRound* round, const BatchSeg* segs,
+                              unsigned long long* work, uint32_t* flags, int num_sms, int block,
+                              cudaStream_t stream) {
+  int per_sm = 0;
+  cudaError_t err = fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_batch<true>, block, 0)
+                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_batch<false>, block, 0);
+  if (err != cudaSuccess) return err;
+  const unsigned grid = static_cast<unsigned>(num_sms * (per_sm > 0 ? per_sm : 1));
+  if (fp64)
+    k_walk_batch<true><<<grid, block, 0, stream>>>(round, segs, work, flags);
+  else
+    k_walk_batch<false><<<grid, block, 0, stream>>>(round, segs, work, flags);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_walk_segment(mlmc_plan* p, const WalkLaunch& w, const void* v_walk,

@@ -544,9 +544,16 @@ class Batch:
         return dict(rounds=r.value, gpu_seconds=g.value, converged=c.value)
 
     def autotune(self):
-        out = (ct.c_int32 * 3)()
-        _check(self._lib.mlmc_batch_autotune(self._h, out, 3))
-        return list(out)
+        """Walks per lane for the three size buckets."""
+        out = (ct.c_int32 * 4)()
+        _check(self._lib.mlmc_batch_autotune(self._h, out, 4))
+        return list(out)[:3]
+
+    def block(self) -> int:
+        """Threads per block of the round kernel chosen by the autotuner."""
+        out = (ct.c_int32 * 4)()
+        _check(self._lib.mlmc_batch_autotune(self._h, out, 4))
+        return int(out[3])
 
 
 class MLP:

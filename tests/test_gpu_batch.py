@@ -84,6 +84,7 @@ def test_batch_pilot_samples_match_oracle(precision):
     with M.Batch(plans, sched, rel_tol=1e-6, stream=stream_handle()) as batch:
         batch.expmv([v for _, _, v in probs], xs, seeds, allow_not_converged=True)
         assert all(c in (4, 16, 64) for c in batch.autotune())
+        assert batch.block() in (128, 256)
     tol = 1e-11 if precision == 0 else 2e-5
     for k, (a, t, v) in enumerate(probs):
         l0 = plans[k].info()["l0"]
