@@ -1092,12 +1092,30 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk(const __grid_constan
 // (copied to shared memory when the warp changes segment); its totals go to
 // the segment's (problem, level) after every item.
 // ---------------------------------------------------------------------------
+// Round keys of the segment a warp is walking, interleaved (k0, k1) per
+// round so that each Philox round reads its pair with one shared load.
+struct SharedRoundKeys {
+  uint2 k[10];
+};
 struct KeysFromShared {
-  const PhiloxRoundKeys* rk;  // in shared memory
-  __device__ __forceinline__ uint4 draw(uint4 c) const { return philox4x32_10(c, *rk); }
+  const SharedRoundKeys* rk;  // in shared memory
+  __device__ __forceinline__ uint4 draw(uint4 c) const {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+      const uint2 kr = rk->k[r];
+      const unsigned long long p0 = static_cast<unsigned long long>(kPhiloxM0) * c.x;
+      const unsigned long long p1 = static_cast<unsigned long long>(kPhiloxM1) * c.z;
+      c = make_uint4(static_cast<uint32_t>(p1 >> 32) ^ c.y ^ kr.x, static_cast<uint32_t>(p1),
+                     static_cast<uint32_t>(p0 >> 32) ^ c.w ^ kr.y, static_cast<uint32_t>(p0));
+    }
+    return c;
+  }
 };
 
-template <bool FP64>
+// One kind of segment per kernel (fine or coupled level, plain or proposal
+// tables): the round's segments are grouped by kind, and each kind's kernel
+// walks its group with its own header and work counter.
+template <bool FP64, bool COARSE, bool IS>
 __global__ void __launch_bounds__(256, FP64 ? 3 : 4)
     k_walk_batch(const BatchRound* __restrict__ round, const BatchSeg* __restrict__ segs,
                  unsigned long long* __restrict__ work, uint32_t* __restrict__ flags) {
@@ -1107,78 +1125,77 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4)
   __shared__ WarpQueue<FP64> queues[kMaxWarps];
   __shared__ WarpCounters counters[kMaxWarps];
   __shared__ EndQueue<FP64> ends[kMaxWarps];
-  __shared__ PhiloxRoundKeys keys[kMaxWarps];
+  __shared__ SharedRoundKeys keys[kMaxWarps];
+  // the walking segment's arguments (read by walk_item from shared memory,
+  // as the single-plan kernel reads its own from the parameter bank)
+  __shared__ ItemArgs iargs[kMaxWarps];
   WarpQueue<FP64>* q = &queues[warp];
   EndQueue<FP64>* eq = &ends[warp];
   WarpCounters* wc = &counters[warp];
   if (lane == 0) *wc = WarpCounters{};
   __syncwarp();
   const unsigned long long total = round->total_items;
-  const int nseg = round->nseg;
+  const int seg0 = round->pad;           // the group's first segment
+  const int nseg = round->nseg;          // and its count
   LaneTotals<T> tot;
   int loaded = -1;
+  double* cur_totals = nullptr;
   for (;;) {
     unsigned long long item = 0;
     if (lane == 0) item = atomicAdd(work, 1ull);
     item = __shfl_sync(kFull, item, 0);
     if (item >= total) break;
-    // the last segment whose first item is <= item
-    int lo = 0, hi = nseg - 1;
+    // the group's last segment whose first item is <= item
+    int lo = seg0, hi = seg0 + nseg - 1;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
       if (segs[mid].item_begin <= item) lo = mid; else hi = mid - 1;
     }
     const BatchSeg& sg = segs[lo];
     if (lo != loaded) {
-      if (lane < 10) {
-        keys[warp].k0[lane] = sg.rk.k0[lane];
-        keys[warp].k1[lane] = sg.rk.k1[lane];
+      // the previous segment's totals, then this segment's round keys and
+      // arguments
+      if (cur_totals) flush_warp(tot, wc, cur_totals, flags, lane);
+      if (lane < 10) keys[warp].k[lane] = make_uint2(sg.rk.k0[lane], sg.rk.k1[lane]);
+      if (lane == 0) {
+        ItemArgs& ia = iargs[warp];
+        ia.meta = sg.meta;
+        ia.alias = sg.alias;
+        ia.v_walk = sg.v_walk;
+        ia.level = sg.level;
+        ia.ctr3 = sg.ctr3;
+        ia.key0 = sg.rk.k0[0];
+        ia.key1 = sg.rk.k1[0];
+        ia.max_jumps = sg.max_jumps;
+        ia.sum_y = sg.sum_y;
+        ia.rep_begin = sg.rep_begin;
+        ia.trace = nullptr;
+        ia.trace_stride = 0;
+        ia.trace_base = 0;
+        ia.f_walk = nullptr;
+        ia.t = 0.0;
+        ia.n = sg.n;
+        ia.nnz = sg.nnz;
+        ia.still32 = sg.still32;
+        ia.n_times = 0;
+        ia.sum_times = nullptr;
+        ia.trace_times = nullptr;
       }
       __syncwarp();
       loaded = lo;
+      cur_totals = sg.totals;
     }
-    ItemArgs ia;
-    ia.meta = sg.meta;
-    ia.alias = sg.alias;
-    ia.v_walk = sg.v_walk;
-    ia.level = sg.level;
-    ia.ctr3 = sg.ctr3;
-    ia.key0 = sg.rk.k0[0];
-    ia.key1 = sg.rk.k1[0];
-    ia.max_jumps = sg.max_jumps;
-    ia.sum_y = sg.sum_y;
-    ia.rep_begin = sg.rep_begin;
-    ia.trace = nullptr;
-    ia.trace_stride = 0;
-    ia.trace_base = 0;
-    ia.f_walk = nullptr;
-    ia.t = 0.0;
-    ia.n = sg.n;
-    ia.nnz = sg.nnz;
-    ia.still32 = sg.still32;
-    ia.n_times = 0;
-    ia.sum_times = nullptr;
-    ia.trace_times = nullptr;
     const unsigned long long local = item - sg.item_begin;
     const int64_t row = static_cast<int64_t>(local / static_cast<unsigned long long>(sg.chunks_per_row));
     const int64_t chunk = static_cast<int64_t>(local) - row * sg.chunks_per_row;
     const int64_t r_lo = chunk * sg.chunk;
     const int64_t r_hi = min(r_lo + sg.chunk, sg.reps);
-    const KeysFromShared kk{&keys[warp]};
     TimesAcc<FP64, false>* ta = nullptr;
-    if (sg.is) {
-      if (sg.coarse)
-        walk_item<FP64, true, false, true, KeysFromShared>(ia, kk, row, r_lo, r_hi, tot, wc, q, eq, ta, lane);
-      else
-        walk_item<FP64, false, false, true, KeysFromShared>(ia, kk, row, r_lo, r_hi, tot, wc, q, eq, ta, lane);
-    } else {
-      if (sg.coarse)
-        walk_item<FP64, true, false, false, KeysFromShared>(ia, kk, row, r_lo, r_hi, tot, wc, q, eq, ta, lane);
-      else
-        walk_item<FP64, false, false, false, KeysFromShared>(ia, kk, row, r_lo, r_hi, tot, wc, q, eq, ta, lane);
-    }
-    flush_warp(tot, wc, sg.totals, flags, lane);
+    walk_item<FP64, COARSE, false, IS, KeysFromShared>(iargs[warp], KeysFromShared{&keys[warp]},
+                                                       row, r_lo, r_hi, tot, wc, q, eq, ta, lane);
+    __syncwarp();  // iargs and keys stay put until every lane has finished the item
   }
+  if (cur_totals) flush_warp(tot, wc, cur_totals, flags, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -1716,19 +1733,40 @@ cudaError_t launch_walk_scratch(mlmc_plan* p, const WalkLaunch& w, unsigned long
                           p->stream, launches);
 }
 
-cudaError_t launch_walk_batch(bool fp64, const BatchRound* round, const BatchSeg* segs,
+namespace {
+template <bool FP64, bool COARSE, bool IS>
+cudaError_t launch_batch_kind(const BatchRound* round, const BatchSeg* segs,
                               unsigned long long* work, uint32_t* flags, int num_sms, int block,
                               cudaStream_t stream) {
   int per_sm = 0;
-  cudaError_t err = fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_batch<true>, block, 0)
-                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_batch<false>, block, 0);
+  cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &per_sm, k_walk_batch<FP64, COARSE, IS>, block, 0);
   if (err != cudaSuccess) return err;
   const unsigned grid = static_cast<unsigned>(num_sms * (per_sm > 0 ? per_sm : 1));
-  if (fp64)
-    k_walk_batch<true><<<grid, block, 0, stream>>>(round, segs, work, flags);
-  else
-    k_walk_batch<false><<<grid, block, 0, stream>>>(round, segs, work, flags);
+  k_walk_batch<FP64, COARSE, IS><<<grid, block, 0, stream>>>(round, segs, work, flags);
   return cudaGetLastError();
+}
+}  // namespace
+
+// The four kinds in the order of the round's groups: (fine, plain),
+// (coupled, plain), (fine, proposal), (coupled, proposal); round[k] and
+// work[k] belong to kind k.
+cudaError_t launch_walk_batch(bool fp64, const BatchRound* round, const BatchSeg* segs,
+                              unsigned long long* work, uint32_t* flags, int num_sms, int block,
+                              cudaStream_t stream) {
+  cudaError_t err = cudaSuccess;
+  if (fp64) {
+    if (err == cudaSuccess) err = launch_batch_kind<true, false, false>(round + 0, segs, work + 0, flags, num_sms, block, stream);
+    if (err == cudaSuccess) err = launch_batch_kind<true, true, false>(round + 1, segs, work + 1, flags, num_sms, block, stream);
+    if (err == cudaSuccess) err = launch_batch_kind<true, false, true>(round + 2, segs, work + 2, flags, num_sms, block, stream);
+    if (err == cudaSuccess) err = launch_batch_kind<true, true, true>(round + 3, segs, work + 3, flags, num_sms, block, stream);
+  } else {
+    if (err == cudaSuccess) err = launch_batch_kind<false, false, false>(round + 0, segs, work + 0, flags, num_sms, block, stream);
+    if (err == cudaSuccess) err = launch_batch_kind<false, true, false>(round + 1, segs, work + 1, flags, num_sms, block, stream);
+    if (err == cudaSuccess) err = launch_batch_kind<false, false, true>(round + 2, segs, work + 2, flags, num_sms, block, stream);
+    if (err == cudaSuccess) err = launch_batch_kind<false, true, true>(round + 3, segs, work + 3, flags, num_sms, block, stream);
+  }
+  return err;
 }
 
 cudaError_t launch_walk_segment(mlmc_plan* p, const WalkLaunch& w, const void* v_walk,
