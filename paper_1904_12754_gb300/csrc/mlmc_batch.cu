@@ -174,9 +174,9 @@ struct mlmc_batch {
   float* d_v32 = nullptr;          // total_rows
   double* d_x = nullptr;           // total_rows
   double** d_xptr = nullptr;       // nprob pointers into d_x
-  unsigned long long* d_work = nullptr;  // the round kernels' work counters (one per kind)
+  unsigned long long* d_work = nullptr;  // the round kernel's work counter
   // Segment table of a round (device + pinned host mirror):
-  // [4 x BatchRound (one per kind), padded to 256 B][max_segs x BatchSeg]
+  // [BatchRound][max_segs x BatchSeg]
   unsigned char* d_round = nullptr;
   unsigned char* h_round = nullptr;
   size_t round_bytes = 0;
@@ -241,7 +241,7 @@ mlmc_status capture_round_graph(mlmc_batch* b) {
   BATCH_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
   cudaError_t err = cudaMemcpyAsync(b->d_round, b->h_round, b->round_bytes, cudaMemcpyHostToDevice,
                                     b->stream);
-  if (err == cudaSuccess) err = cudaMemsetAsync(b->d_work, 0, 4 * sizeof(unsigned long long), b->stream);
+  if (err == cudaSuccess) err = cudaMemsetAsync(b->d_work, 0, sizeof(unsigned long long), b->stream);
   if (err == cudaSuccess)
     err = launch_walk_batch(b->fp64, dround, dsegs, b->d_work, b->d_flags, b->num_sms, b->block,
                             b->stream);
@@ -310,48 +310,27 @@ unsigned long long seg_items(const BatchSeg& g) {
   return static_cast<unsigned long long>(g.n) * static_cast<unsigned long long>(g.chunks_per_row);
 }
 
-// Segment kind: 0 fine plain, 1 coupled plain, 2 fine proposal, 3 coupled
-// proposal (the order of the round kernels).
-int seg_kind(const BatchSeg& g) { return (g.coarse ? 1 : 0) + (g.is ? 2 : 0); }
-
-// Write the round's table: the segments grouped by kind, each group's items
-// numbered from 0, one header per kind.
-void write_round(mlmc_batch* b, const std::vector<BatchSeg>& segs) {
-  BatchRound* hdr = round_hdr(b);
-  BatchSeg* out = round_segs(b);
-  int at = 0;
-  for (int kind = 0; kind < 4; ++kind) {
-    unsigned long long items = 0;
-    const int first = at;
-    for (const BatchSeg& g : segs) {
-      if (seg_kind(g) != kind) continue;
-      out[at] = g;
-      out[at].item_begin = items;
-      items += seg_items(g);
-      ++at;
-    }
-    hdr[kind].total_items = items;
-    hdr[kind].nseg = at - first;
-    hdr[kind].pad = first;
-  }
-}
-
 // Autotuner trial: one launch of the round kernel over the given problems'
 // l0 walks (reps per row each, into the batch's sums, which every
 // mlmc_batch_expmv clears), timed with events; ms per walk.
 double trial_round(mlmc_batch* b, const std::vector<int>& probs, int64_t reps, int64_t per_lane,
                    int block) {
-  std::vector<BatchSeg> segs;
+  BatchSeg* segs = round_segs(b);
+  unsigned long long items = 0;
+  int nseg = 0;
   int64_t walks = 0;
   for (int k : probs) {
-    segs.push_back(make_seg(b, k, 0, 0, reps, per_lane, 0x5eedull, 0));
+    segs[nseg] = make_seg(b, k, 0, 0, reps, per_lane, 0x5eedull, items);
+    items += seg_items(segs[nseg]);
     walks += reps * b->n[k];
+    ++nseg;
   }
-  write_round(b, segs);
+  round_hdr(b)->total_items = items;
+  round_hdr(b)->nseg = nseg;
   const BatchRound* dround = reinterpret_cast<const BatchRound*>(b->d_round);
   const BatchSeg* dsegs = reinterpret_cast<const BatchSeg*>(b->d_round + 256);
   cudaMemcpyAsync(b->d_round, b->h_round, b->round_bytes, cudaMemcpyHostToDevice, b->stream);
-  cudaMemsetAsync(b->d_work, 0, 4 * sizeof(unsigned long long), b->stream);
+  cudaMemsetAsync(b->d_work, 0, sizeof(unsigned long long), b->stream);
   cudaEventRecord(b->ev0, b->stream);
   cudaError_t err = launch_walk_batch(b->fp64, dround, dsegs, b->d_work, b->d_flags, b->num_sms,
                                       block, b->stream);
@@ -426,7 +405,7 @@ mlmc_status mlmc_batch_create(mlmc_batch** out, mlmc_plan* const* plans, int32_t
   BC(cudaMalloc(&b->d_v32, sizeof(float) * b->total_rows), "alloc");
   BC(cudaMalloc(&b->d_x, sizeof(double) * b->total_rows), "alloc");
   BC(cudaMalloc(&b->d_xptr, sizeof(double*) * count), "alloc");
-  BC(cudaMalloc(&b->d_work, 4 * sizeof(unsigned long long)), "alloc");
+  BC(cudaMalloc(&b->d_work, sizeof(unsigned long long)), "alloc");
   b->max_segs = static_cast<int>(count * L);
   b->round_bytes = 256 + sizeof(BatchSeg) * static_cast<size_t>(b->max_segs);
   BC(cudaMalloc(&b->d_round, b->round_bytes), "alloc segment table");
@@ -484,6 +463,8 @@ mlmc_status mlmc_batch_create(mlmc_batch** out, mlmc_plan* const* plans, int32_t
     }
     double best = 1e300;
     for (int blk : {128, 256}) {
+      BatchSeg* segs = round_segs(b);
+      (void)segs;
       // per-bucket walks per lane as tuned: one trial per bucket's problems
       double t = 0.0;
       for (int bk = 0; bk < kBuckets; ++bk) {
@@ -560,9 +541,10 @@ mlmc_status mlmc_batch_expmv(mlmc_batch* b, const double* const* v, double* cons
     // The round's walks: a table of segments of bounded total size, walked
     // by one launch of the round kernel inside the round graph.
     BATCH_CUDA(cudaEventRecord(b->ev0, b->stream), "event");
-    std::vector<BatchSeg> segs;
+    BatchSeg* segs = round_segs(b);
     int nseg = 0;
     int64_t walks = 0;
+    unsigned long long items = 0;
     for (int k = 0; k < K; ++k) {
       ProblemState& s = b->state[k];
       if (s.done) continue;
@@ -572,8 +554,9 @@ mlmc_status mlmc_batch_expmv(mlmc_batch* b, const double* const* v, double* cons
         if (walks >= kRoundWalks || nseg >= b->max_segs) break;
         const int64_t room = std::max<int64_t>(1, (kRoundWalks - walks) / b->n[k]);
         reps = std::min(reps, room);
-        segs.push_back(make_seg(b, k, l, s.reps[l], reps, b->per_lane[bucket_of(b->n[k])],
-                                seeds[k], 0));
+        segs[nseg] = make_seg(b, k, l, s.reps[l], reps, b->per_lane[bucket_of(b->n[k])], seeds[k],
+                              items);
+        items += seg_items(segs[nseg]);
         ++nseg;
         s.launches[l] += 1;
         walks += reps * b->n[k];
@@ -581,7 +564,8 @@ mlmc_status mlmc_batch_expmv(mlmc_batch* b, const double* const* v, double* cons
         s.reps[l] += reps;
       }
     }
-    write_round(b, segs);
+    round_hdr(b)->total_items = items;
+    round_hdr(b)->nseg = nseg;
     if (nseg > 0) ++b->launches;
     // Reduction tasks of every active problem.
     BatchTables* th = tab_hdr(b);

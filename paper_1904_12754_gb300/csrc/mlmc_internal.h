@@ -286,15 +286,13 @@ struct BatchSeg {
   PhiloxRoundKeys rk;         // the problem's seed
 };
 struct BatchRound {
-  unsigned long long total_items;   // items of the group
-  int32_t nseg;                     // segments of the group
-  int32_t pad;                      // index of the group's first segment
+  unsigned long long total_items;
+  int32_t nseg;
+  int32_t pad;
 };
-// Launch the persistent walk kernels of a round on `stream` (grid: every SM
-// at its occupancy for `block` threads): one per segment kind (fine/coupled
-// level x plain/proposal tables), round[k] the header of kind k's group of
-// segments and work[k] its work counter; headers and segments are read from
-// device memory.
+// Launch the persistent walk kernel of a round on `stream` (grid: every SM
+// at its occupancy for `block` threads); the header and segments are read
+// from device memory.
 cudaError_t launch_walk_batch(bool fp64, const BatchRound* round, const BatchSeg* segs,
                               unsigned long long* work, uint32_t* flags, int num_sms, int block,
                               cudaStream_t stream);

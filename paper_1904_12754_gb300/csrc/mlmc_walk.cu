@@ -351,6 +351,25 @@ static_assert(31u + kScreenWalks32 <= WarpQueue<false>::kCap, "FP32 screening qu
 static_assert(31u + 32u * kScreenWays <= WarpQueue<true>::kCap, "FP64 screening queue too small");
 static_assert((WarpQueue<false>::kCap & (WarpQueue<false>::kCap - 1)) == 0, "ring size");
 static_assert((WarpQueue<true>::kCap & (WarpQueue<true>::kCap - 1)) == 0, "ring size");
+// FP32 walks of rows that are not screened (t L_row > 1, long walks): the
+// next walks' draw 0 is computed 32 at a time at full width, before lanes
+// take them.  Its word 1 gives the first holding time (walks whose first
+// time reaches s = 1 never jump and are only counted), words 2-3 the first
+// jump and word 0 the holding time after it, so a lane starting a walk
+// needs no draw of its own and no divergent first holding time.  A ring of
+// 64: a round adds at most 32 entries and runs while fewer than 32 are
+// queued.  It shares the screened rows' queue memory (an item is one or
+// the other).
+struct FreshQueue {
+  static constexpr uint32_t kCap = 64;
+  uint32_t r[kCap];
+  uint32_t x0[kCap];
+  uint32_t x2[kCap];
+  uint32_t x3[kCap];
+  float s1[kCap];
+};
+static_assert(31u + 32u <= FreshQueue::kCap, "fresh queue too small");
+static_assert(sizeof(FreshQueue) <= sizeof(WarpQueue<false>), "fresh queue must fit the screening queue");
 constexpr uint32_t kQueueCap = 64;  // the end queue's ring
 
 // Per-warp queue of walks that ended at s = 1 (their samples are evaluated 32
@@ -948,20 +967,69 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
       // walk claim the next unclaimed walks of the item and every live lane
       // makes one event; few lanes end per iteration, so the samples of
       // ended walks go to the end queue.
-      const unsigned idle = __ballot_sync(kFull, !live);
-      if (!live) {
-        const uint32_t k = claimed + static_cast<uint32_t>(__popc(idle & lanes_below));
-        if (k < span) {
-          start_walk(k);
-          live = true;
-          fresh = true;
+      uint4 xq = make_uint4(0u, 0u, 0u, 0u);  // FP32: a fresh walk's draw 0
+      if constexpr (!FP64) {
+        // Draw 0 of the next walks, 32 at a time (see FreshQueue).
+        FreshQueue* fq = reinterpret_cast<FreshQueue*>(q);
+        while (qtail - qhead < 32u && claimed < span) {
+          const uint32_t rs = claimed + static_cast<uint32_t>(lane);
+          const bool valid = rs < span;
+          uint4 x = make_uint4(0u, 0u, 0u, 0u);
+          T s1 = static_cast<T>(1);
+          if (valid) {
+            const uint64_t rep = rep_base + rs;
+            x = keys.draw(make_uint4(static_cast<uint32_t>(rep), row32, 0u,
+                                     a.ctr3 | (static_cast<uint32_t>(rep >> 32) << 8)));
+            s1 = P::mul(neglog32(uniform32(x.y)), static_cast<T>(m0.inv_rate));
+          }
+          const bool push = valid && s1 < static_cast<T>(1);
+          if (valid && !push) {
+            ++n_still;  // never jumps: only counted
+            if (TRACE) trace_still(rs);
+          }
+          const unsigned pm = __ballot_sync(kFull, push);
+          if (push) {
+            const uint32_t slot = (qtail + static_cast<uint32_t>(__popc(pm & lanes_below))) &
+                                  (FreshQueue::kCap - 1);
+            fq->r[slot] = rs;
+            fq->x0[slot] = x.x;
+            fq->x2[slot] = x.z;
+            fq->x3[slot] = x.w;
+            fq->s1[slot] = s1;
+          }
+          qtail += static_cast<uint32_t>(__popc(pm));
+          claimed = min(claimed + 32u, span);
         }
+        __syncwarp();
+        const unsigned idle = __ballot_sync(kFull, !live);
+        if (!live) {
+          const uint32_t k = qhead + static_cast<uint32_t>(__popc(idle & lanes_below));
+          if (k < qtail) {
+            const uint32_t slot = k & (FreshQueue::kCap - 1);
+            start_walk(fq->r[slot]);
+            xq = make_uint4(fq->x0[slot], 0u, fq->x2[slot], fq->x3[slot]);
+            s_pend = static_cast<T>(fq->s1[slot]);
+            live = true;
+            fresh = true;
+          }
+        }
+        qhead = min(qhead + static_cast<uint32_t>(__popc(idle)), qtail);
+        __syncwarp();  // queue slots read above are free for the next round
+      } else {
+        const unsigned idle = __ballot_sync(kFull, !live);
+        if (!live) {
+          const uint32_t k = claimed + static_cast<uint32_t>(__popc(idle & lanes_below));
+          if (k < span) {
+            start_walk(k);
+            live = true;
+          }
+        }
+        claimed = min(claimed + static_cast<uint32_t>(__popc(idle)), span);
       }
-      claimed = min(claimed + static_cast<uint32_t>(__popc(idle)), span);
       if (!__any_sync(kFull, live)) break;  // every walk of the item done
       if (live) {
-        const uint4 x = keys.draw(make_uint4(c_lo, row32, e, c_hi));
         if constexpr (FP64) {
+          const uint4 x = keys.draw(make_uint4(c_lo, row32, e, c_hi));
           const T s_new = P::add(s, P::mul(P::neglog(P::uniform(x)), static_cast<T>(m.inv_rate)));
           if (!(s_new < static_cast<T>(1))) {
             finish(0, true);
@@ -972,14 +1040,13 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
           }
         } else {
           // Draw e gives the pending jump (words 2, 3) and the holding time
-          // after it (word 0); a fresh walk first draws its first holding
-          // time from word 1 (rows with 1/(tL) < 1: no shared block word).
-          if (fresh) {
-            s_pend = P::add(s, P::mul(neglog32(uniform32(x.y)), static_cast<T>(m.inv_rate)));
-            fresh = false;
-          }
+          // after it (word 0); a fresh walk's draw 0 (and its first holding
+          // time, from word 1) came from the queue.
+          uint4 x = xq;
+          if (!fresh) x = keys.draw(make_uint4(c_lo, row32, e, c_hi));
+          fresh = false;
           if (!(s_pend < static_cast<T>(1))) {
-            finish(0, true);  // never jumped
+            finish(0, true);  // never jumped (not reached: still walks are not queued)
           } else if (static_cast<int64_t>(e) >= a.max_jumps) {
             stop_limit(s_pend, true);
           } else if (!jump(s_pend, x.z, x.w)) {
@@ -1112,10 +1179,7 @@ struct KeysFromShared {
   }
 };
 
-// One kind of segment per kernel (fine or coupled level, plain or proposal
-// tables): the round's segments are grouped by kind, and each kind's kernel
-// walks its group with its own header and work counter.
-template <bool FP64, bool COARSE, bool IS>
+template <bool FP64>
 __global__ void __launch_bounds__(256, FP64 ? 3 : 4)
     k_walk_batch(const BatchRound* __restrict__ round, const BatchSeg* __restrict__ segs,
                  unsigned long long* __restrict__ work, uint32_t* __restrict__ flags) {
@@ -1126,76 +1190,75 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4)
   __shared__ WarpCounters counters[kMaxWarps];
   __shared__ EndQueue<FP64> ends[kMaxWarps];
   __shared__ SharedRoundKeys keys[kMaxWarps];
-  // the walking segment's arguments (read by walk_item from shared memory,
-  // as the single-plan kernel reads its own from the parameter bank)
-  __shared__ ItemArgs iargs[kMaxWarps];
   WarpQueue<FP64>* q = &queues[warp];
   EndQueue<FP64>* eq = &ends[warp];
   WarpCounters* wc = &counters[warp];
   if (lane == 0) *wc = WarpCounters{};
   __syncwarp();
   const unsigned long long total = round->total_items;
-  const int seg0 = round->pad;           // the group's first segment
-  const int nseg = round->nseg;          // and its count
+  const int nseg = round->nseg;
   LaneTotals<T> tot;
   int loaded = -1;
-  double* cur_totals = nullptr;
   for (;;) {
     unsigned long long item = 0;
     if (lane == 0) item = atomicAdd(work, 1ull);
     item = __shfl_sync(kFull, item, 0);
     if (item >= total) break;
-    // the group's last segment whose first item is <= item
-    int lo = seg0, hi = seg0 + nseg - 1;
+    // the last segment whose first item is <= item
+    int lo = 0, hi = nseg - 1;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
       if (segs[mid].item_begin <= item) lo = mid; else hi = mid - 1;
     }
     const BatchSeg& sg = segs[lo];
     if (lo != loaded) {
-      // the previous segment's totals, then this segment's round keys and
-      // arguments
-      if (cur_totals) flush_warp(tot, wc, cur_totals, flags, lane);
+      __syncwarp();  // the previous item's draws are done with the keys
       if (lane < 10) keys[warp].k[lane] = make_uint2(sg.rk.k0[lane], sg.rk.k1[lane]);
-      if (lane == 0) {
-        ItemArgs& ia = iargs[warp];
-        ia.meta = sg.meta;
-        ia.alias = sg.alias;
-        ia.v_walk = sg.v_walk;
-        ia.level = sg.level;
-        ia.ctr3 = sg.ctr3;
-        ia.key0 = sg.rk.k0[0];
-        ia.key1 = sg.rk.k1[0];
-        ia.max_jumps = sg.max_jumps;
-        ia.sum_y = sg.sum_y;
-        ia.rep_begin = sg.rep_begin;
-        ia.trace = nullptr;
-        ia.trace_stride = 0;
-        ia.trace_base = 0;
-        ia.f_walk = nullptr;
-        ia.t = 0.0;
-        ia.n = sg.n;
-        ia.nnz = sg.nnz;
-        ia.still32 = sg.still32;
-        ia.n_times = 0;
-        ia.sum_times = nullptr;
-        ia.trace_times = nullptr;
-      }
       __syncwarp();
       loaded = lo;
-      cur_totals = sg.totals;
     }
+    ItemArgs ia;
+    ia.meta = sg.meta;
+    ia.alias = sg.alias;
+    ia.v_walk = sg.v_walk;
+    ia.level = sg.level;
+    ia.ctr3 = sg.ctr3;
+    ia.key0 = sg.rk.k0[0];
+    ia.key1 = sg.rk.k1[0];
+    ia.max_jumps = sg.max_jumps;
+    ia.sum_y = sg.sum_y;
+    ia.rep_begin = sg.rep_begin;
+    ia.trace = nullptr;
+    ia.trace_stride = 0;
+    ia.trace_base = 0;
+    ia.f_walk = nullptr;
+    ia.t = 0.0;
+    ia.n = sg.n;
+    ia.nnz = sg.nnz;
+    ia.still32 = sg.still32;
+    ia.n_times = 0;
+    ia.sum_times = nullptr;
+    ia.trace_times = nullptr;
     const unsigned long long local = item - sg.item_begin;
     const int64_t row = static_cast<int64_t>(local / static_cast<unsigned long long>(sg.chunks_per_row));
     const int64_t chunk = static_cast<int64_t>(local) - row * sg.chunks_per_row;
     const int64_t r_lo = chunk * sg.chunk;
     const int64_t r_hi = min(r_lo + sg.chunk, sg.reps);
+    const KeysFromShared kk{&keys[warp]};
     TimesAcc<FP64, false>* ta = nullptr;
-    walk_item<FP64, COARSE, false, IS, KeysFromShared>(iargs[warp], KeysFromShared{&keys[warp]},
-                                                       row, r_lo, r_hi, tot, wc, q, eq, ta, lane);
-    __syncwarp();  // iargs and keys stay put until every lane has finished the item
+    if (sg.is) {
+      if (sg.coarse)
+        walk_item<FP64, true, false, true, KeysFromShared>(ia, kk, row, r_lo, r_hi, tot, wc, q, eq, ta, lane);
+      else
+        walk_item<FP64, false, false, true, KeysFromShared>(ia, kk, row, r_lo, r_hi, tot, wc, q, eq, ta, lane);
+    } else {
+      if (sg.coarse)
+        walk_item<FP64, true, false, false, KeysFromShared>(ia, kk, row, r_lo, r_hi, tot, wc, q, eq, ta, lane);
+      else
+        walk_item<FP64, false, false, false, KeysFromShared>(ia, kk, row, r_lo, r_hi, tot, wc, q, eq, ta, lane);
+    }
+    flush_warp(tot, wc, sg.totals, flags, lane);
   }
-  if (cur_totals) flush_warp(tot, wc, cur_totals, flags, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -1733,40 +1796,19 @@ cudaError_t launch_walk_scratch(mlmc_plan* p, const WalkLaunch& w, unsigned long
                           p->stream, launches);
 }
 
-namespace {
-template <bool FP64, bool COARSE, bool IS>
-cudaError_t launch_batch_kind(const BatchRound* round, const BatchSeg* segs,
-                              unsigned long long* work, uint32_t* flags, int num_sms, int block,
-                              cudaStream_t stream) {
-  int per_sm = 0;
-  cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &per_sm, k_walk_batch<FP64, COARSE, IS>, block, 0);
-  if (err != cudaSuccess) return err;
-  const unsigned grid = static_cast<unsigned>(num_sms * (per_sm > 0 ? per_sm : 1));
-  k_walk_batch<FP64, COARSE, IS><<<grid, block, 0, stream>>>(round, segs, work, flags);
-  return cudaGetLastError();
-}
-}  // namespace
-
-// The four kinds in the order of the round's groups: (fine, plain),
-// (coupled, plain), (fine, proposal), (coupled, proposal); round[k] and
-// work[k] belong to kind k.
 cudaError_t launch_walk_batch(bool fp64, const BatchRound* round, const BatchSeg* segs,
                               unsigned long long* work, uint32_t* flags, int num_sms, int block,
                               cudaStream_t stream) {
-  cudaError_t err = cudaSuccess;
-  if (fp64) {
-    if (err == cudaSuccess) err = launch_batch_kind<true, false, false>(round + 0, segs, work + 0, flags, num_sms, block, stream);
-    if (err == cudaSuccess) err = launch_batch_kind<true, true, false>(round + 1, segs, work + 1, flags, num_sms, block, stream);
-    if (err == cudaSuccess) err = launch_batch_kind<true, false, true>(round + 2, segs, work + 2, flags, num_sms, block, stream);
-    if (err == cudaSuccess) err = launch_batch_kind<true, true, true>(round + 3, segs, work + 3, flags, num_sms, block, stream);
-  } else {
-    if (err == cudaSuccess) err = launch_batch_kind<false, false, false>(round + 0, segs, work + 0, flags, num_sms, block, stream);
-    if (err == cudaSuccess) err = launch_batch_kind<false, true, false>(round + 1, segs, work + 1, flags, num_sms, block, stream);
-    if (err == cudaSuccess) err = launch_batch_kind<false, false, true>(round + 2, segs, work + 2, flags, num_sms, block, stream);
-    if (err == cudaSuccess) err = launch_batch_kind<false, true, true>(round + 3, segs, work + 3, flags, num_sms, block, stream);
-  }
-  return err;
+  int per_sm = 0;
+  cudaError_t err = fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_batch<true>, block, 0)
+                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_batch<false>, block, 0);
+  if (err != cudaSuccess) return err;
+  const unsigned grid = static_cast<unsigned>(num_sms * (per_sm > 0 ? per_sm : 1));
+  if (fp64)
+    k_walk_batch<true><<<grid, block, 0, stream>>>(round, segs, work, flags);
+  else
+    k_walk_batch<false><<<grid, block, 0, stream>>>(round, segs, work, flags);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_walk_segment(mlmc_plan* p, const WalkLaunch& w, const void* v_walk,
