@@ -612,76 +612,78 @@ def _timed_solve(plan, v_dev, x_dev, seed):
 
 
 def run_learned_workload(args):
-    """Plain jump law against the learned proposal on the same inputs."""
+    """The learned proposal with tilted clocks (mlmc_learn_tilt) against the
+    plain walk on the same inputs: time to the tolerance, learning included,
+    and the error against the FP64 judge.  A plain solve that stops at its
+    budget reports its projected time (budget x (estimated error / tol)^2)."""
     import torch
     import mlmc_inputs as I
     import __graft_entry__ as g
     g.build()
     from paper_1904_12754_gb300 import mlmc as M
-    st = torch.cuda.current_stream().cuda_stream
-    out = {"metric": "learned proposal vs plain MLMC", "n_gpus": 1, "dtype": "f32",
-           "data": "synthetic"}
-    # (1) the configured learned workload: BA n=1e6, m=8, beta=1/lambda_max
-    w = I.workload_c5()
-    log(f"{w.name}: n={w.a.n} nnz={w.a.nnz} lambda_max={w.extra['lambda_max']:.2f}")
-    sched = M.schedule_default(precision=M.FP32_KAHAN, num_levels=4, max_levels=10,
-                               time_budget_s=args.step_budget)
-    dv = torch.from_numpy(w.v).cuda()
-    dx = torch.zeros(w.a.n, dtype=torch.float64, device="cuda")
-    with M.Plan.from_csr(w.a, w.t, sched, rel_tol=1e-3, stream=st) as plan:
-        var_p, _ = _level0_variance(plan, dv, 256, 11)
-        tp, ep, cp, evp = _timed_solve(plan, dv, dx, 21)
-        t0 = time.perf_counter()
-        with M.MLP(seed=3, stream=st) as net:
-            loss = net.learn_proposal(plan, dv, seed=5, pilot_walks=64, steps=300, batch=8192)
-        torch.cuda.synchronize()
-        t_learn = time.perf_counter() - t0
-        var_l, _ = _level0_variance(plan, dv, 256, 11)
-        tl, el, cl, evl = _timed_solve(plan, dv, dx, 21)
-    out["ba_n1e6_m8_beta_inv_lambda_max"] = {
-        "level0_var_per_walk_plain": var_p, "level0_var_per_walk_learned": var_l,
-        "variance_ratio": var_l / var_p, "learn_seconds": t_learn, "train_loss": loss,
-        "budget_s": args.step_budget,
-        "plain": {"seconds": tp, "est_rel_err": ep, "converged": cp, "walk_steps_per_s": evp / tp},
-        "learned": {"seconds": tl, "est_rel_err": el, "converged": cl,
-                    "walk_steps_per_s": evl / tl},
-        "extrapolated_time_to_1e-3_s": {"plain": tp * (ep / 1e-3) ** 2,
-                                        "learned": t_learn + tl * (el / 1e-3) ** 2}}
-    log(f"BA: variance ratio {var_l / var_p:.3f}, est err plain {ep:.3g} learned {el:.3g}")
-    # (2) localized right-hand side: convection-diffusion 128^3, v = exp(-|x|^2)
-    w = I.workload_c4()
-    tol = args.tol
-    sched = M.schedule_default(precision=M.FP32_KAHAN, num_levels=4, max_levels=10,
-                               time_budget_s=300.0)
-    dv = torch.from_numpy(w.v).cuda()
-    dx = torch.zeros(w.a.n, dtype=torch.float64, device="cuda")
-    with M.Plan.from_csr(w.a, w.t, sched, rel_tol=tol, stream=st) as plan:
-        var_p, _ = _level0_variance(plan, dv, 64, 11)
-        tp, ep, cp, evp = _timed_solve(plan, dv, dx, 21)
-        xp = dx.cpu().numpy()
-        t0 = time.perf_counter()
-        with M.MLP(seed=3, stream=st) as net:
-            loss = net.learn_proposal(plan, dv, seed=5, pilot_walks=64, steps=300, batch=8192)
-        torch.cuda.synchronize()
-        t_learn = time.perf_counter() - t0
-        var_l, _ = _level0_variance(plan, dv, 64, 11)
-        tl, el, cl, evl = _timed_solve(plan, dv, dx, 21)
-        xl = dx.cpu().numpy()
     from oracle import reference as R  # FP64 judge (CPU baseline leg)
-    ref = R.expmv_taylor(w.a.scipy(), w.t, w.v)
-    nref = np.linalg.norm(ref)
-    out["convdiff3d_128_bump"] = {
-        "tol": tol, "level0_var_per_walk_plain": var_p, "level0_var_per_walk_learned": var_l,
-        "variance_ratio": var_l / var_p, "learn_seconds": t_learn, "train_loss": loss,
-        "plain": {"time_to_tol_s": tp, "est_rel_err": ep, "converged": cp,
-                  "rel_err_vs_fp64": float(np.linalg.norm(xp - ref) / nref)},
-        "learned": {"time_to_tol_s": tl, "time_incl_learning_s": tl + t_learn, "est_rel_err": el,
-                    "converged": cl, "rel_err_vs_fp64": float(np.linalg.norm(xl - ref) / nref)},
-        "speedup_excl_learning": tp / tl, "speedup_incl_learning": tp / (tl + t_learn)}
-    log(f"convdiff: plain {tp:.2f} s, learned {tl:.2f} s (+{t_learn:.2f} s learning)")
-    out["value"] = out["convdiff3d_128_bump"]["speedup_incl_learning"]
-    out["unit"] = "x (plain time / learned time incl. learning)"
-    out["higher_is_better"] = True
+    st = torch.cuda.current_stream().cuda_stream
+    out = {"metric": "time to rel. RMS tolerance, learned tilted proposal vs plain MLMC",
+           "n_gpus": 1, "dtype": "f32", "data": "synthetic", "workloads": {}}
+
+    def one(w, tol, plain_budget, learned_budget, name):
+        log(f"{name}: n={w.a.n} nnz={w.a.nnz}")
+        ref = R.expmv_taylor(w.a.scipy(), w.t, w.v)
+        nref = np.linalg.norm(ref)
+        dv = torch.from_numpy(w.v).cuda()
+        dx = torch.zeros(w.a.n, dtype=torch.float64, device="cuda")
+        res = {"tol": tol}
+        sched = M.schedule_default(precision=M.FP32_KAHAN, num_levels=4, max_levels=10,
+                                   time_budget_s=plain_budget)
+        with M.Plan.from_csr(w.a, w.t, sched, rel_tol=tol, stream=st) as plan:
+            var_p, _ = _level0_variance(plan, dv, 64, 11)
+            tp, ep, cp, evp = _timed_solve(plan, dv, dx, 21)
+            xp = dx.cpu().numpy()
+        res["plain"] = {"seconds": tp, "est_rel_err": ep, "converged": cp,
+                        "rel_err_vs_fp64": float(np.linalg.norm(xp - ref) / nref),
+                        "walk_steps_per_s": evp / tp, "level0_var_per_walk": var_p,
+                        "time_to_tol_s": tp if cp else None,
+                        "projected_time_to_tol_s": tp * (ep / tol) ** 2}
+        sched = M.schedule_default(precision=M.FP32_KAHAN, num_levels=4, max_levels=10,
+                                   time_budget_s=learned_budget)
+        runs = []
+        with M.Plan.from_csr(w.a, w.t, sched, rel_tol=tol, stream=st) as plan:
+            for rep in range(3):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                with M.MLP(seed=3, stream=st) as net:
+                    loss = net.learn_tilt(plan, dv, seed=5 + rep, pilot_walks=args.pilot, steps=300,
+                                          batch=8192, clocks=True, rounds=args.rounds)
+                torch.cuda.synchronize()
+                t_learn = time.perf_counter() - t0
+                var_l, _ = _level0_variance(plan, dv, 64, 11)
+                tl, el, cl, evl = _timed_solve(plan, dv, dx, 31 + rep)
+                xl = dx.cpu().numpy()
+                runs.append({"learn_s": t_learn, "solve_s": tl, "time_to_tol_s": t_learn + tl,
+                             "est_rel_err": el, "converged": cl, "train_loss": loss,
+                             "rel_err_vs_fp64": float(np.linalg.norm(xl - ref) / nref),
+                             "level0_var_per_walk": var_l, "walk_steps_per_s": evl / tl})
+                log(f"{name} learned run {rep}: {t_learn:.2f} + {tl:.2f} s, est {el:.3g}, "
+                    f"converged {cl}")
+                plan.set_tilt(None)
+        res["learned"] = runs
+        conv = [r["time_to_tol_s"] for r in runs if r["converged"]]
+        res["learned_median_time_to_tol_s"] = statistics.median(conv) if conv else None
+        res["learned_converged_runs"] = len(conv)
+        ref_t = res["plain"]["time_to_tol_s"] or res["plain"]["projected_time_to_tol_s"]
+        if conv:
+            res["speedup_incl_learning"] = ref_t / statistics.median(conv)
+        out["workloads"][name] = res
+        log(f"{name}: plain {tp:.2f} s (est {ep:.3g}), learned median "
+            f"{res['learned_median_time_to_tol_s']}")
+        return res
+
+    c5 = one(I.workload_c5(), 1e-3, args.plain_budget, args.step_budget,
+             "ba_n1e6_m8_beta_inv_lambda_max")
+    c4 = one(I.workload_c4(), 1e-3, 300.0, 300.0, "convdiff3d_128_bump")
+    out["value"] = c5.get("learned_median_time_to_tol_s")
+    out["unit"] = "s (learned time to 1e-3 on BA n=1e6 m=8, learning included)"
+    out["higher_is_better"] = False
     print(json.dumps(out), flush=True)
 
 
