@@ -255,13 +255,7 @@ cudaError_t launch_start_guide(mlmc_plan* p, const int64_t* cdf, unsigned long l
 // device memory instead of the plan's buffers.
 cudaError_t launch_walk_scratch(mlmc_plan* p, const WalkLaunch& w, unsigned long long* work,
                                 float* v32, int64_t* launches = nullptr);
-// One segment of a batch round: launch_walk's launches with v already in the
-// walk precision (v_walk), on `stream`, with their own work counter and flags
-// word; per_lane > 0 fixes the walks per lane of an item.  Plans with a source
-// term are refused (cudaErrorInvalidValue).
-cudaError_t launch_walk_segment(mlmc_plan* p, const WalkLaunch& w, const void* v_walk,
-                                int64_t per_lane, unsigned long long* work, uint32_t* flags,
-                                cudaStream_t stream, int64_t* launches = nullptr);
+
 
 // Batched rounds (mlmc_batch.cu): one persistent walk launch over every
 // (problem, level, replica range) segment of a round.  A segment's items are

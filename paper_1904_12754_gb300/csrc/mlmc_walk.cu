@@ -1811,13 +1811,5 @@ cudaError_t launch_walk_batch(bool fp64, const BatchRound* round, const BatchSeg
   return cudaGetLastError();
 }
 
-cudaError_t launch_walk_segment(mlmc_plan* p, const WalkLaunch& w, const void* v_walk,
-                                int64_t per_lane, unsigned long long* work, uint32_t* flags,
-                                cudaStream_t stream, int64_t* launches) {
-  if (launches) *launches = 0;
-  if (w.reps <= 0 || p->n <= 0) return cudaSuccess;
-  if (p->source_active) return cudaErrorInvalidValue;
-  return launch_walk_core(p, w, v_walk, nullptr, work, flags, per_lane, stream, launches);
-}
 
 }  // namespace mlmc
