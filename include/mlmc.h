@@ -538,7 +538,10 @@ mlmc_status mlmc_learn_proposal(mlmc_plan *plan, mlmc_mlp *mlp, const double *v,
  * earlier rounds' ones) with the proposal installed by the previous one.  With tilted clocks the MLP's
  * target is 0.5 (log(|x-hat| + 1e-3 max|x-hat|) + log(|v| + 1e-3 max|v|)):
  * the zero-variance h of a walk at scaled time s is exp((1-s)tA)v, from x at
- * the start to v at the end, and this is its geometric mean.  The MLP's
+ * the start to v at the end, and this is its geometric mean; and the first
+ * pilot already walks with the tilt of h0 = sqrt(T_3 |v|), T_3 the
+ * third-order Taylor value of exp(t|A|)|v| (the paper's walk would give
+ * pilot estimates with the heavy tails the tilt removes).  The MLP's
  * training rows are weighted by degree (row i counted 1 + floor(deg_i /
  * mean degree) times, at most 4n rows): the few rows with many
  * off-diagonals set the laws of every row around them.  final_loss is the

@@ -366,6 +366,14 @@ __global__ void k_abs_float32(int64_t n, const double* __restrict__ in, float* _
   }
 }
 
+// h_i = sqrt((a_i + fa) (|b_i| + fb)) in FP32.
+__global__ void k_sqrt_product(int64_t n, const float* __restrict__ a, const double* __restrict__ b,
+                               float fa, float fb, float* __restrict__ h) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    h[i] = sqrtf((a[i] + fa) * (fabsf(static_cast<float>(b[i])) + fb));
+}
+
 __global__ void k_to_float32(int64_t n, const double* __restrict__ in, float* __restrict__ out) {
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x)
@@ -762,7 +770,10 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
     return mfail(MLMC_ERR_INVALID_ARG, "mlmc_learn_tilt: backward-mode plans only");
   const bool clocks = (tilt & MLMC_TILT_CLOCKS) != 0;
   const bool was = p->proposal_active;
-  p->proposal_active = false;  // the first pilot uses the paper's jump law
+  const bool was_clocks = p->clock_tilt;
+  // The first pilot uses the paper's walk (jumps only) or, with tilted
+  // clocks, the tilt of h0 = sqrt(T_3 |v|) (below).
+  p->proposal_active = false;
   double* sums = nullptr;
   double* dv = nullptr;
   __nv_bfloat16* feat = nullptr;
@@ -791,6 +802,7 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
     if (e_ != cudaSuccess) {                                                                   \
       cleanup();                                                                               \
       p->proposal_active = was;                                                                \
+      p->clock_tilt = was_clocks;                                                              \
       return mfail(MLMC_ERR_CUDA, std::string("learn proposal ") + (what) + ": " +             \
                                       cudaGetErrorString(e_));                                 \
     }                                                                                          \
@@ -836,6 +848,26 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
     LP_CUDA(cudaStreamSynchronize(p->stream), "sync");
     for (double q : hv) vmax = std::max(vmax, std::fabs(q));
   }
+  mlmc_status st = MLMC_OK;
+  if (clocks) {
+    // Warm start: the first pilot walks with the tilt of h0 = sqrt((T_3 +
+    // f) (|v| + f_v)), the third-order Taylor value of exp(t|A|)|v| (a
+    // feature above) in place of x: the paper's walk gives pilot estimates
+    // with the heavy tails the tilt exists to remove (long stays at rows of
+    // large t d_ii), and a network fitted to them would misjudge exactly
+    // those rows.
+    k_sqrt_product<<<g, 256, 0, p->stream>>>(p->n, pv + 5 * p->n, dv, static_cast<float>(1e-6),
+                                             static_cast<float>(1e-3 * vmax + 1e-30), h);
+    p->launches++;
+    LP_CUDA(cudaGetLastError(), "warm start");
+    st = mlmc_plan_set_tilt(p, h, alpha, tilt);
+    if (st != MLMC_OK) {
+      cleanup();
+      p->proposal_active = was;
+      p->clock_tilt = was_clocks;
+      return st;
+    }
+  }
   // Training rows weighted by degree: row i appears 1 + floor(deg_i / mean
   // deg) times (at most 4n rows in all).  Rows with many off-diagonals are
   // few, but their h sets the clocks and jump laws of every row around them,
@@ -861,7 +893,6 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
                             p->stream), "write rows");
     LP_CUDA(cudaStreamSynchronize(p->stream), "sync");
   }
-  mlmc_status st = MLMC_OK;
   for (int32_t round = 0; round < rounds; ++round) {
     LP_CUDA(cudaMemsetAsync(sums, 0, sizeof(double) * (p->n + kTotSlots), p->stream), "memset");
     WalkLaunch w;
@@ -916,7 +947,10 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
     if (st != MLMC_OK) break;
   }
   cleanup();
-  if (st != MLMC_OK) p->proposal_active = was;
+  if (st != MLMC_OK) {
+    p->proposal_active = was;
+    p->clock_tilt = was_clocks;
+  }
   return st;
 #undef LP_CUDA
 }
