@@ -195,44 +195,55 @@ __global__ void __launch_bounds__(128)
 }
 
 // z = H2 w3 + b3, and (training) dz, dA2 = dz w3 [A2 > 0] (FP32 and BF16),
-// the loss and dw3 / db3 partial sums.
+// the loss and dw3 / db3 partial sums.  One warp per row at a time: lane l
+// holds hidden units l and l + 32 (coalesced row reads), z is a warp sum,
+// and the lanes keep their dw3 sums in registers until the warp's last row
+// (one atomic per hidden unit and warp).
 __global__ void k_mlp_head(int64_t M, const float* __restrict__ h2, const float* __restrict__ a2,
                            const float* __restrict__ p, const float* __restrict__ y,
                            float* __restrict__ z, float* __restrict__ da2,
                            __nv_bfloat16* __restrict__ da2_bf16, float* __restrict__ grad,
                            float* __restrict__ loss) {
-  const float* w3 = p + kOffW3;
+  static_assert(kHid == 64, "two hidden units per lane");
+  const int lane = threadIdx.x & 31;
+  const float w3a = p[kOffW3 + lane];
+  const float w3b = p[kOffW3 + lane + 32];
   const float b3 = p[kOffB3];
-  __shared__ float s_dw3[kHid];
-  __shared__ float s_db3, s_loss;
-  if (threadIdx.x < kHid) s_dw3[threadIdx.x] = 0.f;
-  if (threadIdx.x == 0) s_db3 = s_loss = 0.f;
-  __syncthreads();
   const float inv_b = 1.0f / static_cast<float>(M);
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < M;
-       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    float zi = b3;
-    for (int j = 0; j < kHid; ++j) zi += h2[i * kHid + j] * w3[j];
-    if (z) z[i] = zi;
+  float dwa = 0.f, dwb = 0.f, db = 0.f, ls = 0.f;
+  const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x >> 5) + (threadIdx.x >> 5); i < M;
+       i += warps) {
+    const float ha = h2[i * kHid + lane];
+    const float hb = h2[i * kHid + lane + 32];
+    float zi = ha * w3a + hb * w3b;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) zi += __shfl_xor_sync(0xFFFFFFFFu, zi, o);
+    zi += b3;
+    if (z && lane == 0) z[i] = zi;
     if (y) {
       const float r = zi - y[i];
       const float dz = 2.0f * r * inv_b;
-      atomicAdd(&s_loss, r * r * inv_b);
-      atomicAdd(&s_db3, dz);
-      for (int j = 0; j < kHid; ++j) {
-        atomicAdd(&s_dw3[j], dz * h2[i * kHid + j]);
-        const float d = a2[i * kHid + j] > 0.f ? dz * w3[j] : 0.f;
-        da2[i * kHid + j] = d;
-        da2_bf16[i * kHid + j] = __float2bfloat16_rn(d);
+      if (lane == 0) {
+        ls += r * r * inv_b;
+        db += dz;
       }
+      dwa += dz * ha;
+      dwb += dz * hb;
+      const float da = a2[i * kHid + lane] > 0.f ? dz * w3a : 0.f;
+      const float dbb = a2[i * kHid + lane + 32] > 0.f ? dz * w3b : 0.f;
+      da2[i * kHid + lane] = da;
+      da2[i * kHid + lane + 32] = dbb;
+      da2_bf16[i * kHid + lane] = __float2bfloat16_rn(da);
+      da2_bf16[i * kHid + lane + 32] = __float2bfloat16_rn(dbb);
     }
   }
-  __syncthreads();
   if (y) {
-    if (threadIdx.x < kHid) atomicAdd(&grad[kOffW3 + threadIdx.x], s_dw3[threadIdx.x]);
-    if (threadIdx.x == 0) {
-      atomicAdd(&grad[kOffB3], s_db3);
-      atomicAdd(loss, s_loss);
+    if (dwa != 0.f) atomicAdd(&grad[kOffW3 + lane], dwa);
+    if (dwb != 0.f) atomicAdd(&grad[kOffW3 + lane + 32], dwb);
+    if (lane == 0) {
+      if (db != 0.f) atomicAdd(&grad[kOffB3], db);
+      if (ls != 0.f) atomicAdd(loss, ls);
     }
   }
 }
@@ -555,7 +566,8 @@ mlmc_status forward(mlmc_mlp* m, const __nv_bfloat16* x, int64_t M, float* z, co
            "layer 1");
   MLP_CUDA(tile<kHid>(m, M, m->d_h1, m->d_w2t, m->d_p + kOffB2, true, nullptr, m->d_h2, m->d_a2),
            "layer 2");
-  const unsigned g = static_cast<unsigned>(std::min<int64_t>((M + 255) / 256, m->num_sms * 4));
+  // one warp per row: 8 rows per block of 256 at a time
+  const unsigned g = static_cast<unsigned>(std::min<int64_t>((M + 7) / 8, m->num_sms * 8));
   if (train) MLP_CUDA(cudaMemsetAsync(m->d_loss, 0, sizeof(float), m->stream), "memset");
   k_mlp_head<<<std::max(1u, g), 256, 0, m->stream>>>(M, m->d_h2, m->d_a2, m->d_p, train ? y : nullptr,
                                                        z, m->d_da2, m->d_da2b, m->d_g, m->d_loss);

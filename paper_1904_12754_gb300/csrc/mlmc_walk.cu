@@ -351,25 +351,6 @@ static_assert(31u + kScreenWalks32 <= WarpQueue<false>::kCap, "FP32 screening qu
 static_assert(31u + 32u * kScreenWays <= WarpQueue<true>::kCap, "FP64 screening queue too small");
 static_assert((WarpQueue<false>::kCap & (WarpQueue<false>::kCap - 1)) == 0, "ring size");
 static_assert((WarpQueue<true>::kCap & (WarpQueue<true>::kCap - 1)) == 0, "ring size");
-// FP32 walks of rows that are not screened (t L_row > 1, long walks): the
-// next walks' draw 0 is computed 32 at a time at full width, before lanes
-// take them.  Its word 1 gives the first holding time (walks whose first
-// time reaches s = 1 never jump and are only counted), words 2-3 the first
-// jump and word 0 the holding time after it, so a lane starting a walk
-// needs no draw of its own and no divergent first holding time.  A ring of
-// 64: a round adds at most 32 entries and runs while fewer than 32 are
-// queued.  It shares the screened rows' queue memory (an item is one or
-// the other).
-struct FreshQueue {
-  static constexpr uint32_t kCap = 64;
-  uint32_t r[kCap];
-  uint32_t x0[kCap];
-  uint32_t x2[kCap];
-  uint32_t x3[kCap];
-  float s1[kCap];
-};
-static_assert(31u + 32u <= FreshQueue::kCap, "fresh queue too small");
-static_assert(sizeof(FreshQueue) <= sizeof(WarpQueue<false>), "fresh queue must fit the screening queue");
 constexpr uint32_t kQueueCap = 64;  // the end queue's ring
 
 // Per-warp queue of walks that ended at s = 1 (their samples are evaluated 32
@@ -967,69 +948,20 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
       // walk claim the next unclaimed walks of the item and every live lane
       // makes one event; few lanes end per iteration, so the samples of
       // ended walks go to the end queue.
-      uint4 xq = make_uint4(0u, 0u, 0u, 0u);  // FP32: a fresh walk's draw 0
-      if constexpr (!FP64) {
-        // Draw 0 of the next walks, 32 at a time (see FreshQueue).
-        FreshQueue* fq = reinterpret_cast<FreshQueue*>(q);
-        while (qtail - qhead < 32u && claimed < span) {
-          const uint32_t rs = claimed + static_cast<uint32_t>(lane);
-          const bool valid = rs < span;
-          uint4 x = make_uint4(0u, 0u, 0u, 0u);
-          T s1 = static_cast<T>(1);
-          if (valid) {
-            const uint64_t rep = rep_base + rs;
-            x = keys.draw(make_uint4(static_cast<uint32_t>(rep), row32, 0u,
-                                     a.ctr3 | (static_cast<uint32_t>(rep >> 32) << 8)));
-            s1 = P::mul(neglog32(uniform32(x.y)), static_cast<T>(m0.inv_rate));
-          }
-          const bool push = valid && s1 < static_cast<T>(1);
-          if (valid && !push) {
-            ++n_still;  // never jumps: only counted
-            if (TRACE) trace_still(rs);
-          }
-          const unsigned pm = __ballot_sync(kFull, push);
-          if (push) {
-            const uint32_t slot = (qtail + static_cast<uint32_t>(__popc(pm & lanes_below))) &
-                                  (FreshQueue::kCap - 1);
-            fq->r[slot] = rs;
-            fq->x0[slot] = x.x;
-            fq->x2[slot] = x.z;
-            fq->x3[slot] = x.w;
-            fq->s1[slot] = s1;
-          }
-          qtail += static_cast<uint32_t>(__popc(pm));
-          claimed = min(claimed + 32u, span);
+      const unsigned idle = __ballot_sync(kFull, !live);
+      if (!live) {
+        const uint32_t k = claimed + static_cast<uint32_t>(__popc(idle & lanes_below));
+        if (k < span) {
+          start_walk(k);
+          live = true;
+          fresh = true;
         }
-        __syncwarp();
-        const unsigned idle = __ballot_sync(kFull, !live);
-        if (!live) {
-          const uint32_t k = qhead + static_cast<uint32_t>(__popc(idle & lanes_below));
-          if (k < qtail) {
-            const uint32_t slot = k & (FreshQueue::kCap - 1);
-            start_walk(fq->r[slot]);
-            xq = make_uint4(fq->x0[slot], 0u, fq->x2[slot], fq->x3[slot]);
-            s_pend = static_cast<T>(fq->s1[slot]);
-            live = true;
-            fresh = true;
-          }
-        }
-        qhead = min(qhead + static_cast<uint32_t>(__popc(idle)), qtail);
-        __syncwarp();  // queue slots read above are free for the next round
-      } else {
-        const unsigned idle = __ballot_sync(kFull, !live);
-        if (!live) {
-          const uint32_t k = claimed + static_cast<uint32_t>(__popc(idle & lanes_below));
-          if (k < span) {
-            start_walk(k);
-            live = true;
-          }
-        }
-        claimed = min(claimed + static_cast<uint32_t>(__popc(idle)), span);
       }
+      claimed = min(claimed + static_cast<uint32_t>(__popc(idle)), span);
       if (!__any_sync(kFull, live)) break;  // every walk of the item done
       if (live) {
+        const uint4 x = keys.draw(make_uint4(c_lo, row32, e, c_hi));
         if constexpr (FP64) {
-          const uint4 x = keys.draw(make_uint4(c_lo, row32, e, c_hi));
           const T s_new = P::add(s, P::mul(P::neglog(P::uniform(x)), static_cast<T>(m.inv_rate)));
           if (!(s_new < static_cast<T>(1))) {
             finish(0, true);
@@ -1040,13 +972,14 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
           }
         } else {
           // Draw e gives the pending jump (words 2, 3) and the holding time
-          // after it (word 0); a fresh walk's draw 0 (and its first holding
-          // time, from word 1) came from the queue.
-          uint4 x = xq;
-          if (!fresh) x = keys.draw(make_uint4(c_lo, row32, e, c_hi));
-          fresh = false;
+          // after it (word 0); a fresh walk first draws its first holding
+          // time from word 1 (rows with 1/(tL) < 1: no shared block word).
+          if (fresh) {
+            s_pend = P::add(s, P::mul(neglog32(uniform32(x.y)), static_cast<T>(m.inv_rate)));
+            fresh = false;
+          }
           if (!(s_pend < static_cast<T>(1))) {
-            finish(0, true);  // never jumped (not reached: still walks are not queued)
+            finish(0, true);  // never jumped
           } else if (static_cast<int64_t>(e) >= a.max_jumps) {
             stop_limit(s_pend, true);
           } else if (!jump(s_pend, x.z, x.w)) {
