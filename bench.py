@@ -6,24 +6,25 @@ of a seeded Barabasi-Albert graph, n = 100000, m = 4, beta = 1/lambda_max
 (power iteration), FP32 walk weights with Kahan sums and an FP64 final sum,
 4 initial levels from l0 (Eq. 16), relative RMS tolerance 1e-3.
 
-One step = one pass of the whole hot path: rebuild the split quantities and
-alias tables on the device from the resident CSR, then mlmc_expmv (pilot,
-optimal M_l, top-ups, extra levels, final FP64 sum) with a new seed.  With
-beta = 1/lambda_max the per-walk weight e^{beta int d} has a variance that
-grows like e^{beta d_max} (hub sojourns; beta d_max = 32 here), so the 1e-3
-target is out of reach for the plain estimator: each step runs the controller
-to its wall-clock budget (--step-budget) and `value` is the walk-steps/s of
-those steps (one walk-step = one event = one holding-time draw; jumps + 1 per
-walk).  The time to 1e-3 is measured on the same graph with beta = 1/d_max,
-the value the paper uses for scale-free networks (Sec. 5), and reported as
-time_to_tol.
+One step = one pass of the whole hot path with a new seed: rebuild the split
+quantities and alias tables on the device from the resident CSR; learn the
+tilt (pilot walks, MLP training on the tensor cores, tilted-clock proposal
+tables); mlmc_expmv to the tolerance (pilot, optimal M_l, top-ups, extra
+levels, final FP64 sum).  `value` = the solve's walk-steps (one walk-step =
+one event = one holding-time draw; jumps + 1 per walk) / the step's time, and
+time_to_tol.learned_s = the step time.  With beta = 1/lambda_max the plain
+walk's weight e^{beta int d} has a variance that grows like e^{beta d_max}
+(hub sojourns; beta d_max = 32 here), so the plain walk is run beside it for a
+fixed budget and its time to 1e-3 is projected from the error it reaches.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py --workload kernel|batch|learned|precision|levels|complexity|source|forward|c1
 
 --impl reference times the CPU oracle (the paper's Algorithm 2 interval loop,
 OpenMP over rows) on bounded samples of the same workload.
-N > 1 (torchrun): every rank solves its own replica of the workload with its
-own seeds (weak scaling; no collective on the data path).
+N > 1 (torchrun): one problem sharded over the ranks (each rank walks its part
+of every level's walks; the level sums are all-reduced before each controller
+decision): strong scaling.
 """
 from __future__ import annotations
 
@@ -46,6 +47,24 @@ if ROOT not in sys.path:
 METRIC = "walk-steps/s; time to 1e-3 rel err vs FP64 exp(tA)v, learned vs plain, 1 GB300"
 UNIT = "walk-steps/s"
 L2_FLUSH_BYTES = 256 << 20
+
+
+def _fp64_judge(a, t, v, f=None):
+    """FP64 exp(tA)v from the library routine scipy.sparse.linalg.
+    expm_multiply (Al-Mohy and Higham's truncated Taylor with scaling), the
+    reference each result's error is stated against.  With a constant source
+    f: u(t) = exp(tA)v + int_0^t exp(sA)f ds, the first n entries of exp(tB)
+    [v; 1] for the augmented B = [[A, f], [0, 0]]."""
+    import scipy.sparse as sp
+    from scipy.sparse.linalg import expm_multiply
+    m = a.scipy().tocsr()
+    if f is None:
+        return expm_multiply(t * m, np.asarray(v, dtype=np.float64))
+    n = m.shape[0]
+    b = sp.bmat([[m, sp.csr_matrix(np.asarray(f, dtype=np.float64).reshape(n, 1))],
+                 [None, sp.csr_matrix((1, 1))]], format="csr")
+    y = expm_multiply(t * b, np.append(np.asarray(v, dtype=np.float64), 1.0))
+    return y[:n]
 
 
 def _env_rank():
@@ -254,6 +273,7 @@ def run_ours(args):
     table_ms = e0.elapsed_time(e1)
 
     mlp_launches = [0]
+    learn_log = []
 
     def step(seed, v_in, x_out):
         """One pass of the hot path: tables, learned proposal with tilted
@@ -265,6 +285,7 @@ def run_ours(args):
             net.learn_tilt(plan, v_in, seed=seed, pilot_walks=args.pilot, steps=300,
                            batch=8192, clocks=True, rounds=args.rounds)
             mlp_launches[0] += net.launch_count()
+        learn_log.append(plan.learn_report())
         if dist is not None:
             h = torch.from_numpy(plan.export_h()).cuda()
             dist.broadcast(h, 0)
@@ -365,12 +386,11 @@ def run_ours(args):
     cpu = None
     err = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        from oracle import reference as R
         cv, cores, sample = _oracle_sample(w, info["l0"], seconds=args.ref_seconds)
         cv1, _, sample1 = _oracle_sample(w, info["l0"], seconds=5.0, seed=2, nthreads=1)
         _oracle_sample(w, info["l0"], seconds=0.1, seed=3, nthreads=cores)  # restore the thread count
         t_ref = time.perf_counter()
-        ref = R.expmv_taylor(w.a.scipy(), w.t, w.v)
+        ref = _fp64_judge(w.a, w.t, w.v)
         t_ref = time.perf_counter() - t_ref
         err = float(np.linalg.norm(x_last - ref) / np.linalg.norm(ref))
         cpu = {"value": cv, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
@@ -390,7 +410,11 @@ def run_ours(args):
                        "step": "table build + learned tilted proposal (pilot walks, MLP "
                                "training, proposal tables) + MLMC solve to the tolerance",
                        "learning": {"rounds": args.rounds, "pilot_walks": args.pilot,
-                                    "mlp_steps": 300, "alpha": 0.1},
+                                    "mlp_steps": 300, "alpha": 0.1,
+                                    "chosen_law_per_timed_step": [
+                                        c for c, _ in learn_log[args.warmup:args.warmup + args.steps]],
+                                    "pilot_var_per_walk_last_timed_step":
+                                        learn_log[args.warmup + args.steps - 1][1]},
                        "l2": "flushed between steps (256 MB write outside the timed events)",
                        "parallelism": f"shard{world}" if world > 1 else "1 GPU"},
             "time_to_tol": {"learned_s": statistics.median(tt), "learned_runs_s": tt,
@@ -621,14 +645,13 @@ def run_learned_workload(args):
     import __graft_entry__ as g
     g.build()
     from paper_1904_12754_gb300 import mlmc as M
-    from oracle import reference as R  # FP64 judge (CPU baseline leg)
     st = torch.cuda.current_stream().cuda_stream
     out = {"metric": "time to rel. RMS tolerance, learned tilted proposal vs plain MLMC",
            "n_gpus": 1, "dtype": "f32", "data": "synthetic", "workloads": {}}
 
     def one(w, tol, plain_budget, learned_budget, name):
         log(f"{name}: n={w.a.n} nnz={w.a.nnz}")
-        ref = R.expmv_taylor(w.a.scipy(), w.t, w.v)
+        ref = _fp64_judge(w.a, w.t, w.v)
         nref = np.linalg.norm(ref)
         dv = torch.from_numpy(w.v).cuda()
         dx = torch.zeros(w.a.n, dtype=torch.float64, device="cuda")
@@ -656,13 +679,15 @@ def run_learned_workload(args):
                                           batch=8192, clocks=True, rounds=args.rounds)
                 torch.cuda.synchronize()
                 t_learn = time.perf_counter() - t0
+                chosen, pilot_var = plan.learn_report()
                 var_l, _ = _level0_variance(plan, dv, 64, 11)
                 tl, el, cl, evl = _timed_solve(plan, dv, dx, 31 + rep)
                 xl = dx.cpu().numpy()
                 runs.append({"learn_s": t_learn, "solve_s": tl, "time_to_tol_s": t_learn + tl,
                              "est_rel_err": el, "converged": cl, "train_loss": loss,
                              "rel_err_vs_fp64": float(np.linalg.norm(xl - ref) / nref),
-                             "level0_var_per_walk": var_l, "walk_steps_per_s": evl / tl})
+                             "level0_var_per_walk": var_l, "walk_steps_per_s": evl / tl,
+                             "pilot_var_per_walk": pilot_var, "chosen_law": chosen})
                 log(f"{name} learned run {rep}: {t_learn:.2f} + {tl:.2f} s, est {el:.3g}, "
                     f"converged {cl}")
                 plan.set_tilt(None)
@@ -695,10 +720,9 @@ def run_precision_workload(args):
     import __graft_entry__ as g
     g.build()
     from paper_1904_12754_gb300 import mlmc as M
-    from oracle import reference as R  # FP64 judge
     st = torch.cuda.current_stream().cuda_stream
     w = I.workload_c4()
-    ref = R.expmv_taylor(w.a.scipy(), w.t, w.v)
+    ref = _fp64_judge(w.a, w.t, w.v)
     nref = np.linalg.norm(ref)
     dv = torch.from_numpy(w.v).cuda()
     dx = torch.zeros(w.a.n, dtype=torch.float64, device="cuda")
@@ -740,13 +764,12 @@ def run_kernel_workload(args):
         w = I.Workload(name="lap3d_g64_t1_fp32", a=a, t=1.0, v=I.uniform_v(a.n, 20190429),
                        precision="fp32", num_levels=3, tol=1e-3, extra={})
     elif args.kernel_matrix == "c4":
-        w = I.workload_c4()          # tables ~233 MB: larger than L2
-        w.precision = "fp32"
+        w = I.workload_c4()          # FP32 tables ~233 MB: larger than L2
     elif args.kernel_matrix == "c5":
-        w = I.workload_c5()          # tables ~272 MB: larger than L2
-        w.precision = "fp32"
+        w = I.workload_c5()          # FP32 tables ~272 MB: larger than L2
     else:
         w = _workload()
+    w.precision = args.kernel_precision
     stream = torch.cuda.current_stream()
     sched = M.schedule_default(precision=M.FP32_KAHAN if w.precision == "fp32" else M.FP64,
                                walks_per_lane=args.walks_per_lane, block_threads=args.block,
@@ -797,17 +820,22 @@ def run_kernel_workload(args):
     peaks, _ = _peaks()
     lv = [dict(coarse=False, walks=res["l0"]["walks"], jumps=res["l0"]["jumps"],
                still_walks=res["l0"]["still_walks"], launches=1)]
+    # the op model and its ALU peak describe the FP32 walk; the FP64 walk is
+    # bound by the FP64 pipe (its counters are in the kernel's ncu summary)
     roof = walk_roofline(lv, 1e-3 * statistics.mean(res["l0"]["launch_ms"]), clocks, peaks,
-                         statistics.mean(res["l0"]["launch_ms"]), proposal=args.kernel_tilt)
+                         statistics.mean(res["l0"]["launch_ms"]),
+                         proposal=args.kernel_tilt) if w.precision == "fp32" else None
     out = {"metric": "walk kernel alone: walk-steps/s at l0 (one launch, L2 flushed before it)",
            "value": res["l0"]["events_per_s"], "unit": UNIT, "higher_is_better": True,
-           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "dtype": "f32",
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "dtype": "f32" if w.precision == "fp32" else "f64",
            "data": "synthetic",
            "config": {"workload": w.name, "n": n, "nnz": w.a.nnz, "t": w.t, "l0": l0,
                       "walks_per_row": reps, "l2": "flushed before each launch",
                       "walks_per_lane": args.walks_per_lane or "default",
                       "block": args.block or "default", "l2_window": l2win,
-                      "walk": "learned tilted clocks and jumps" if args.kernel_tilt else "plain"},
+                      "walk": "learned tilted clocks and jumps" if args.kernel_tilt else "plain",
+                      "precision": w.precision},
            "levels": res, "roofline": roof, "clocks": clocks}
     print(json.dumps(out), flush=True)
     plan.close()
@@ -975,7 +1003,6 @@ def run_source_workload(args):
     import __graft_entry__ as g
     g.build()
     from paper_1904_12754_gb300 import mlmc as M
-    from oracle import reference as R  # FP64 judge
     stream = torch.cuda.current_stream()
     a = I.convdiff_3d(64)
     t = 8.0 / float(abs(a.scipy()).sum(axis=1).max())
@@ -985,8 +1012,8 @@ def run_source_workload(args):
     X, Y, Z = np.meshgrid(xs, xs, xs, indexing="ij")
     v = np.exp(-(X ** 2 + Y ** 2 + Z ** 2)).ravel()
     f = np.ones(a.n)
-    ref_h = R.expmv_taylor(a.scipy(), t, v)
-    ref_s = ref_h + R.expmv_source_taylor(a.scipy(), t, f)
+    ref_h = _fp64_judge(a, t, v)
+    ref_s = _fp64_judge(a, t, v, f)
     dv = torch.from_numpy(v).cuda()
     dx = torch.zeros(a.n, dtype=torch.float64, device="cuda")
     sched = M.schedule_default(precision=M.FP32_KAHAN, num_levels=3, max_levels=10,
@@ -1023,10 +1050,9 @@ def run_forward_workload(args):
     import __graft_entry__ as g
     g.build()
     from paper_1904_12754_gb300 import mlmc as M
-    from oracle import reference as R  # FP64 judge
     stream = torch.cuda.current_stream()
     w = I.workload_c4()
-    ref = R.expmv_taylor(w.a.scipy(), w.t, w.v)
+    ref = _fp64_judge(w.a, w.t, w.v)
     nref = np.linalg.norm(ref)
     dv = torch.from_numpy(w.v).cuda()
     dx = torch.zeros(w.a.n, dtype=torch.float64, device="cuda")
@@ -1054,6 +1080,55 @@ def run_forward_workload(args):
     print(json.dumps(out), flush=True)
 
 
+def run_c1_workload(args):
+    """The FP64 walk on the small 2D Laplacian (32 x 32 grid scaled by 1/h^2,
+    t ||A||_inf = 4, v uniform, 3 levels, tolerance 1e-2): time to the
+    tolerance per solve, walk-steps/s and the error against dense FP64
+    scaling-and-squaring (scipy.linalg.expm), over --steps solves with new
+    seeds after --warmup untimed ones."""
+    import scipy.linalg
+    import torch
+    import mlmc_inputs as I
+    import __graft_entry__ as g
+    g.build()
+    from paper_1904_12754_gb300 import mlmc as M
+    stream = torch.cuda.current_stream()
+    w = I.workload_c1()
+    ref = scipy.linalg.expm(w.t * w.a.scipy().toarray()) @ w.v
+    nref = np.linalg.norm(ref)
+    dv = torch.from_numpy(w.v).cuda()
+    dx = torch.zeros(w.a.n, dtype=torch.float64, device="cuda")
+    sched = M.schedule_default(precision=M.FP64, num_levels=w.num_levels, max_levels=10,
+                               time_budget_s=args.step_budget)
+    runs = []
+    with M.Plan.from_csr(w.a, w.t, sched, rel_tol=w.tol, stream=stream.cuda_stream) as plan:
+        for k in range(args.warmup):
+            _timed_solve(plan, dv, dx, 100 + k)
+        for k in range(args.steps):
+            sec, est, conv, events = _timed_solve(plan, dv, dx, 1000 + k)
+            x = dx.cpu().numpy()
+            levels, _ = plan.stats()
+            runs.append({"seconds": sec, "est_rel_err": est, "converged": conv,
+                         "rel_err_vs_fp64_expm": float(np.linalg.norm(x - ref) / nref),
+                         "walk_steps_per_s": events / sec, "levels": len(levels),
+                         "walks_per_row": [lv["walks_per_row"] for lv in levels]})
+            log(f"c1 solve {k}: {sec * 1e3:.2f} ms, est {est:.3g}, "
+                f"err {runs[-1]['rel_err_vs_fp64_expm']:.3g}")
+        l0 = plan.info()["l0"]
+    errs = [r["rel_err_vs_fp64_expm"] for r in runs]
+    out = {"metric": "time to rel. RMS tolerance 1e-2, FP64 walk",
+           "value": statistics.median(r["seconds"] for r in runs), "unit": "s",
+           "higher_is_better": False, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "dtype": "f64", "data": "synthetic",
+           "config": {"workload": w.name, "n": w.a.n, "nnz": w.a.nnz, "t": w.t, "tol": w.tol,
+                      "l0": l0, "levels": w.num_levels},
+           "walk_steps_per_s": statistics.median(r["walk_steps_per_s"] for r in runs),
+           "all_converged": all(r["converged"] for r in runs),
+           "rel_err_vs_fp64_expm": {"median": statistics.median(errs), "max": max(errs)},
+           "runs": runs}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1072,14 +1147,15 @@ def main():
     ap.add_argument("--pilot", type=int, default=64,
                     help="first-round pilot walks per row of the learned proposal")
     ap.add_argument("--workload", choices=["tc", "batch", "learned", "precision", "kernel",
-                                           "levels", "complexity", "source", "forward"],
+                                           "levels", "complexity", "source", "forward", "c1"],
                     default="tc",
                     help="tc: the metric's workload (default); batch: batched vs plain; "
                          "learned: learned proposal vs plain; precision: FP32 vs FP64 walk; "
                          "kernel: the walk kernel alone; levels: m_l and V_l vs level; "
                          "complexity: MLMC vs single-level MC and the l0 sweep; "
                          "source: the inhomogeneous problem (Algorithm 3); "
-                         "forward: forward vs backward mode")
+                         "forward: forward vs backward mode; c1: the FP64 walk on the small 2D "
+                         "Laplacian")
     ap.add_argument("--max-level", type=int, default=10, help="--workload levels: finest level")
     ap.add_argument("--kernel-reps", type=int, default=4096,
                     help="walks per row of one launch in --workload kernel")
@@ -1090,6 +1166,8 @@ def main():
     ap.add_argument("--kernel-tilt", action="store_true",
                     help="--workload kernel: time the walk with the learned tilted proposal "
                          "(the default workload's solve)")
+    ap.add_argument("--kernel-precision", choices=["fp32", "fp64"], default="fp32",
+                    help="--workload kernel: walk precision (fp64: the all-FP64 walk)")
     ap.add_argument("--l2-persist", type=int, default=1, choices=[0, 1],
                     help="--workload kernel: L2 access-policy window over the tables")
     ap.add_argument("--walks-per-lane", type=int, default=0,
@@ -1119,6 +1197,8 @@ def main():
         run_source_workload(args)
     elif args.workload == "forward":
         run_forward_workload(args)
+    elif args.workload == "c1":
+        run_c1_workload(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -544,11 +544,28 @@ mlmc_status mlmc_learn_proposal(mlmc_plan *plan, mlmc_mlp *mlp, const double *v,
  * pilot estimates with the heavy tails the tilt removes).  The MLP's
  * training rows are weighted by degree (row i counted 1 + floor(deg_i /
  * mean degree) times, at most 4n rows): the few rows with many
- * off-diagonals set the laws of every row around them.  final_loss is the
- * last round's.  Backward-mode plans only. */
+ * off-diagonals set the laws of every row around them.  Every pilot
+ * measures the per-walk variance of the law it walks with (the rows' sample
+ * variances averaged over the rows), and one more pilot of 4 * pilot_walks
+ * walks per row measures the last round's tilt; the law with the smallest
+ * measured variance is the one installed (for MLMC_TILT_JUMPS the paper's
+ * walk is a candidate too: then the plan is left with the plain walk).  The
+ * pilots draw from a stream keyed by a hash of `seed`, never the one
+ * mlmc_expmv draws from with the same seed, so the installed law does not
+ * depend on the walks that estimate x.  final_loss is the last round's.
+ * Backward-mode plans only. */
 mlmc_status mlmc_learn_tilt(mlmc_plan *plan, mlmc_mlp *mlp, const double *v, uint64_t seed,
                             int64_t pilot_walks, int32_t steps, int32_t batch, float lr,
                             double alpha, int32_t tilt, int32_t rounds, float *final_loss);
+
+/* What the plan's last mlmc_learn_tilt / mlmc_learn_proposal measured:
+ * *count (may be NULL) = rounds + 1 pilot variances; var[k] (host, the
+ * first min(cap, count)) = the per-walk variance at l0 of pilot k, which
+ * walked with the law installed before round k (k = rounds: the final
+ * tilt); *chosen (may be NULL) = the index of the law installed (-1 before
+ * any learning). */
+mlmc_status mlmc_plan_learn_report(const mlmc_plan *plan, int32_t *chosen, double *var, int32_t cap,
+                                   int32_t *count);
 
 /* Copy the device tables to host arrays (any pointer may be NULL):
  *   l_ii, dl (= t d_i), inv_rate (1/(t L_ii), +inf when L_ii = 0): n doubles

@@ -107,6 +107,11 @@ struct mlmc_plan {
   int32_t* d_still32_t = nullptr;
   double* d_lam = nullptr;
   bool clock_tilt = false;
+  // The last mlmc_learn_tilt: the per-walk variance each pilot measured
+  // (pilot k walked with the law installed before round k; the last one
+  // with the final tilt) and which law was installed (-1: none).
+  std::vector<double> learn_var;
+  int32_t learn_choice = -1;
   // Forward mode (the tables above are then built from A^T): start weights,
   // their prefix sums and total, scan scratch.
   int64_t* d_wstart = nullptr;

@@ -15,6 +15,12 @@
 // BF16 (round to nearest even); dA2 is rounded to BF16 for the dH1 GEMM;
 // everything else is FP32.
 //
+// Training runs two kernels per step: k_mlp_train_tile does the whole
+// forward and backward pass of 128 batch rows in one CTA (three tcgen05
+// GEMMs, activations in shared memory and TMEM, weight gradients on the CUDA
+// cores), and k_mlp_adam_tiles sums the tiles' gradients and takes the Adam
+// step.  Inference (h for every node) uses the layer kernels below.
+//
 // tcgen05 tile kernel: one CTA of 128 threads computes a 128 x 64 output
 // tile.  Operands are staged in shared memory in the canonical no-swizzle
 // K-major layout (8-row x 16-byte core matrices; core matrices adjacent in K
@@ -24,6 +30,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <limits>
 #include <string>
 #include <vector>
 
@@ -194,112 +201,429 @@ __global__ void __launch_bounds__(128)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
-// z = H2 w3 + b3, and (training) dz, dA2 = dz w3 [A2 > 0] (FP32 and BF16),
-// the loss and dw3 / db3 partial sums.  One warp per row at a time: lane l
-// holds hidden units l and l + 32 (coalesced row reads), z is a warp sum,
-// and the lanes keep their dw3 sums in registers until the warp's last row
-// (one atomic per hidden unit and warp).
-__global__ void k_mlp_head(int64_t M, const float* __restrict__ h2, const float* __restrict__ a2,
-                           const float* __restrict__ p, const float* __restrict__ y,
-                           float* __restrict__ z, float* __restrict__ da2,
-                           __nv_bfloat16* __restrict__ da2_bf16, float* __restrict__ grad,
-                           float* __restrict__ loss) {
+// ---------------------------------------------------------------------------
+// Fused training step: the forward and backward passes of one 128-row tile
+// of a batch in one CTA of 128 threads (thread r = row r = TMEM lane r).
+//
+//   weights  one bulk copy (cp.async.bulk, completion on an mbarrier) of the
+//            operand image the Adam kernel writes after every update: W1^T,
+//            W2^T and W2 as BF16 in the canonical K-major layout, then the
+//            FP32 vectors b1, b2, w3, b3
+//   GEMM 1   A1 = X W1 (+ b1)       tcgen05, K = 16, TMEM columns 0-63
+//   GEMM 2   A2 = H1 W2 (+ b2)      tcgen05, K = 64, columns 64-127
+//   head     z, dz, dA2 = dz w3 [A2 > 0] per row (CUDA cores, registers)
+//   GEMM 3   dH1 = dA2 W2^T         tcgen05, K = 64, columns 128-191, issued
+//            before the CUDA cores sum dW2 = H1^T dA2, db2, dw3, db3 from
+//            shared memory, so the two overlap
+//   then     dA1 = dH1 [A1 > 0]; dW1 = X^T dA1, db1 (CUDA cores)
+//
+// The tile's gradient (and loss) go to its own row of `part`; the Adam or
+// reduction kernel sums the rows, so nothing is accumulated atomically.
+// Rounding points are those of the unfused kernels (see the file header).
+// ---------------------------------------------------------------------------
+constexpr int kImgW1 = 0;                             // W1^T: 64 x 16 BF16, K = 16
+constexpr int kImgW2t = kImgW1 + kHid * kIn * 2;      // W2^T: 64 x 64 BF16 (rows = outputs)
+constexpr int kImgW2 = kImgW2t + kHid * kHid * 2;     // W2: 64 x 64 BF16 (rows = inputs)
+constexpr int kImgVec = kImgW2 + kHid * kHid * 2;     // FP32 b1[64] b2[64] w3[64] b3
+constexpr int kImgBytes = kImgVec + 256 * 4;          // 19456: a multiple of 16
+constexpr int kVecB1 = 0, kVecB2 = 64, kVecW3 = 128, kVecB3 = 192;
+constexpr int kPart = kParams + 1;                    // a tile's gradient, then its loss
+// Shared memory of the fused kernel (byte offsets; every part 128-byte aligned).
+constexpr int kTsImg = 0;
+constexpr int kTsX = kTsImg + kImgBytes;              // X tile, 128 x 16 BF16 (A of GEMM 1)
+constexpr int kTsH1 = kTsX + kTileM * kIn * 2;        // H1, 128 x 64 BF16 (A of GEMM 2)
+constexpr int kTsDA2b = kTsH1 + kTileM * kHid * 2;    // dA2, 128 x 64 BF16 (A of GEMM 3)
+constexpr int kTsDA2 = kTsDA2b + kTileM * kHid * 2;   // dA2, 128 x 64 FP32, row-major
+constexpr int kTsF2 = kTsDA2 + kTileM * kHid * 4;     // H2, then dA1: 128 x 64 FP32
+constexpr int kTsDZ = kTsF2 + kTileM * kHid * 4;      // dz per row
+constexpr int kTsLoss = kTsDZ + kTileM * 4;           // loss term per row
+constexpr int kTsBar = kTsLoss + kTileM * 4;          // 4 mbarriers
+constexpr int kTsSlot = kTsBar + 4 * 8;               // TMEM address
+constexpr int kTrainSmem = kTsSlot + 16;
+constexpr int kTrainTmemCols = 256;                   // three 64-column accumulators
+static_assert(kImgBytes % 16 == 0 && kTsX % 128 == 0 && kTsH1 % 128 == 0 && kTsDA2b % 128 == 0,
+              "operand alignment");
+static_assert(kTsDA2 % 16 == 0 && kTsF2 % 16 == 0 && kTsBar % 8 == 0, "alignment");
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  uint32_t done = 0;
+  for (uint32_t it = 0; it < kWaitLimit && !done; ++it) {
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+  }
+  return done != 0;
+}
+
+// K/16 tcgen05.mma of a 128 x 64 tile into TMEM column `col`, committed to
+// the mbarrier `bar` (issued by one thread).
+template <int K>
+__device__ __forceinline__ void issue_gemm(uint32_t tmem_d, uint32_t a0, uint32_t b0,
+                                           uint32_t bar) {
+  constexpr uint32_t idesc = umma_idesc(kTileM, kHid);
+  constexpr uint32_t lbo = 128, sbo = (K / 8) * 128;
+#pragma unroll
+  for (int ks = 0; ks < K / 16; ++ks) {
+    const uint64_t ad = umma_desc(a0 + ks * 256, lbo, sbo);
+    const uint64_t bd = umma_desc(b0 + ks * 256, lbo, sbo);
+    const uint32_t acc = ks > 0 ? 1u : 0u;
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+  }
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   bar)
+               : "memory");
+}
+
+// 16 FP32 accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t u[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];"
+      : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]),
+        "=r"(u[7]), "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]),
+        "=r"(u[14]), "=r"(u[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(u[j]);
+}
+
+// Eight values as BF16 into one 16-byte row of a core matrix.
+__device__ __forceinline__ void store_bf16x8(unsigned char* dst, const float* v) {
+  __nv_bfloat162 q[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) q[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+  *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(q);
+}
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Rows: batch row b of the tile is x[b] (sample == 0) or x[mix64(seed + b)
+// mod n_src] (a uniform minibatch drawn on the device).
+__global__ void __launch_bounds__(128)
+    k_mlp_train_tile(int64_t M, const __nv_bfloat16* __restrict__ x, const float* __restrict__ y,
+                     int64_t n_src, uint64_t sample_seed, int sample,
+                     const unsigned char* __restrict__ img, float* __restrict__ part,
+                     uint32_t* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+  const int64_t b = static_cast<int64_t>(blockIdx.x) * kTileM + tid;
+  const bool valid = b < M;
+  const uint32_t s0 = smem_u32(smem);
+  const uint32_t bar = s0 + kTsBar;  // mbarriers: weights, GEMM 1, GEMM 2, GEMM 3
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + kTsSlot);
+  const float* vec = reinterpret_cast<const float*>(smem + kTsImg + kImgVec);
+  float* da2f = reinterpret_cast<float*>(smem + kTsDA2);
+  float* f2 = reinterpret_cast<float*>(smem + kTsF2);
+  float* dzs = reinterpret_cast<float*>(smem + kTsDZ);
+  float* lss = reinterpret_cast<float*>(smem + kTsLoss);
+  float* out = part + static_cast<int64_t>(blockIdx.x) * kPart;
+
+  if (tid == 0) {
+    for (int i = 0; i < 4; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar + 8 * i), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (tid == 0) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                 "r"(kImgBytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            s0 + kTsImg),
+        "l"(img), "r"(kImgBytes), "r"(bar)
+        : "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tslot)),
+                 "r"(kTrainTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  // This thread's row of X (zeros past M) and its target.
+  float yv = 0.f;
+  {
+    uint4 lo = make_uint4(0u, 0u, 0u, 0u), hi = lo;
+    if (valid) {
+      int64_t src = b;
+      if (sample) src = static_cast<int64_t>(mix64(sample_seed + static_cast<uint64_t>(b)) %
+                                             static_cast<uint64_t>(n_src));
+      const uint4* xr = reinterpret_cast<const uint4*>(x + src * kIn);
+      lo = xr[0];
+      hi = xr[1];
+      yv = y[src];
+    }
+    *reinterpret_cast<uint4*>(smem + kTsX + core_offset(tid, 0, kIn)) = lo;
+    *reinterpret_cast<uint4*>(smem + kTsX + core_offset(tid, 8, kIn)) = hi;
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  const uint32_t lane_base = static_cast<uint32_t>(warp * 32) << 16;
+  bool ok = __syncthreads_and(mbar_wait(bar, 0));
+
+  // GEMM 1 and its epilogue: H1 = relu(A1), the sign mask of A1 kept in
+  // two registers.
+  uint32_t mask1[2] = {0u, 0u};
+  if (ok) {
+    if (tid == 0) issue_gemm<kIn>(tmem, s0 + kTsX, s0 + kTsImg + kImgW1, bar + 8);
+    ok = __syncthreads_and(mbar_wait(bar + 8, 0));
+  }
+  if (ok) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+    for (int cb = 0; cb < kHid / 16; ++cb) {
+      float v[16];
+      tmem_ld16(tmem + lane_base + cb * 16, v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const float a = v[j] + vec[kVecB1 + cb * 16 + j];
+        if (a > 0.f) mask1[cb >> 1] |= 1u << ((cb & 1) * 16 + j);
+        v[j] = fmaxf(a, 0.f);
+      }
+      store_bf16x8(smem + kTsH1 + core_offset(tid, cb * 16, kHid), v);
+      store_bf16x8(smem + kTsH1 + core_offset(tid, cb * 16 + 8, kHid), v + 8);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (tid == 0) issue_gemm<kHid>(tmem + 64, s0 + kTsH1, s0 + kTsImg + kImgW2t, bar + 16);
+    ok = __syncthreads_and(mbar_wait(bar + 16, 0));
+  }
+  // GEMM 2's epilogue and the head: H2, z, dz, dA2 (FP32 and BF16).
+  if (ok) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    uint32_t mask2[2] = {0u, 0u};
+    float z = 0.f;
+#pragma unroll
+    for (int cb = 0; cb < kHid / 16; ++cb) {
+      float v[16];
+      tmem_ld16(tmem + lane_base + 64 + cb * 16, v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int col = cb * 16 + j;
+        const float a = v[j] + vec[kVecB2 + col];
+        if (a > 0.f) mask2[cb >> 1] |= 1u << ((cb & 1) * 16 + j);
+        const float h = fmaxf(a, 0.f);
+        f2[tid * kHid + col] = h;
+        z += h * vec[kVecW3 + col];
+      }
+    }
+    z += vec[kVecB3];
+    const float inv_b = 1.0f / static_cast<float>(M);
+    const float r = z - yv;
+    const float dz = valid ? 2.0f * r * inv_b : 0.f;
+    dzs[tid] = dz;
+    lss[tid] = valid ? r * r * inv_b : 0.f;
+#pragma unroll
+    for (int cb = 0; cb < kHid / 16; ++cb) {
+      float d[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int col = cb * 16 + j;
+        d[j] = (mask2[cb >> 1] >> ((cb & 1) * 16 + j)) & 1u ? dz * vec[kVecW3 + col] : 0.f;
+        da2f[tid * kHid + col] = d[j];
+      }
+      store_bf16x8(smem + kTsDA2b + core_offset(tid, cb * 16, kHid), d);
+      store_bf16x8(smem + kTsDA2b + core_offset(tid, cb * 16 + 8, kHid), d + 8);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // GEMM 3 runs while the CUDA cores sum dW2 = H1^T dA2 (a 4 x 8 block of
+    // it per thread), db2, dw3 and db3.
+    if (tid == 0) issue_gemm<kHid>(tmem + 128, s0 + kTsDA2b, s0 + kTsImg + kImgW2, bar + 24);
+    {
+      const int k0 = 4 * (tid >> 3), j0 = 8 * (tid & 7);
+      float acc[4][8];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+      for (int rr = 0; rr < kTileM; ++rr) {
+        const uint2 hb = *reinterpret_cast<const uint2*>(smem + kTsH1 + core_offset(rr, k0, kHid));
+        const float2 h01 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&hb.x));
+        const float2 h23 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&hb.y));
+        const float hv[4] = {h01.x, h01.y, h23.x, h23.y};
+        const float4 d0 = *reinterpret_cast<const float4*>(da2f + rr * kHid + j0);
+        const float4 d1 = *reinterpret_cast<const float4*>(da2f + rr * kHid + j0 + 4);
+        const float dv[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(hv[i], dv[j], acc[i][j]);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) out[kOffW2 + (k0 + i) * kHid + j0 + j] = acc[i][j];
+    }
+    if (tid < kHid) {
+      float s = 0.f;
+      for (int rr = 0; rr < kTileM; ++rr) s += da2f[rr * kHid + tid];
+      out[kOffB2 + tid] = s;
+    } else {
+      const int j = tid - kHid;
+      float s = 0.f;
+      for (int rr = 0; rr < kTileM; ++rr) s = fmaf(dzs[rr], f2[rr * kHid + j], s);
+      out[kOffW3 + j] = s;
+    }
+    if (warp == 0) {
+      float sd = 0.f, sl = 0.f;
+      for (int rr = tid; rr < kTileM; rr += 32) {
+        sd += dzs[rr];
+        sl += lss[rr];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        sd += __shfl_xor_sync(0xFFFFFFFFu, sd, o);
+        sl += __shfl_xor_sync(0xFFFFFFFFu, sl, o);
+      }
+      if (tid == 0) {
+        out[kOffB3] = sd;
+        out[kParams] = sl;
+      }
+    }
+    // every thread is done with H2 (f2) before dA1 overwrites it
+    ok = __syncthreads_and(mbar_wait(bar + 24, 0));
+  }
+  // GEMM 3's epilogue: dA1 = dH1 [A1 > 0] into f2; then dW1 = X^T dA1 (a
+  // row of 8 per thread) and db1.
+  if (ok) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+    for (int cb = 0; cb < kHid / 16; ++cb) {
+      float v[16];
+      tmem_ld16(tmem + lane_base + 128 + cb * 16, v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        f2[tid * kHid + cb * 16 + j] = (mask1[cb >> 1] >> ((cb & 1) * 16 + j)) & 1u ? v[j] : 0.f;
+    }
+    __syncthreads();
+    const int k = tid >> 3, j0 = 8 * (tid & 7);
+    float acc[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[j] = 0.f;
+    for (int rr = 0; rr < kTileM; ++rr) {
+      const float xv = __bfloat162float(
+          *reinterpret_cast<const __nv_bfloat16*>(smem + kTsX + core_offset(rr, k, kIn)));
+      const float4 d0 = *reinterpret_cast<const float4*>(f2 + rr * kHid + j0);
+      const float4 d1 = *reinterpret_cast<const float4*>(f2 + rr * kHid + j0 + 4);
+      acc[0] = fmaf(xv, d0.x, acc[0]);
+      acc[1] = fmaf(xv, d0.y, acc[1]);
+      acc[2] = fmaf(xv, d0.z, acc[2]);
+      acc[3] = fmaf(xv, d0.w, acc[3]);
+      acc[4] = fmaf(xv, d1.x, acc[4]);
+      acc[5] = fmaf(xv, d1.y, acc[5]);
+      acc[6] = fmaf(xv, d1.z, acc[6]);
+      acc[7] = fmaf(xv, d1.w, acc[7]);
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) out[kOffW1 + k * kHid + j0 + j] = acc[j];
+    if (tid < kHid) {
+      float s = 0.f;
+      for (int rr = 0; rr < kTileM; ++rr) s += f2[rr * kHid + tid];
+      out[kOffB1 + tid] = s;
+    }
+  }
+  if (!ok) {
+    // a completion wait gave up: the tile contributes nothing
+    if (tid == 0) atomicOr(err, 1u);
+    for (int e = tid; e < kPart; e += kTileM) out[e] = 0.f;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kTrainTmemCols));
+}
+
+// The operand image of parameter e (value w) in `img` (see the fused kernel).
+__device__ __forceinline__ void image_store(unsigned char* img, int e, float w) {
+  float* vec = reinterpret_cast<float*>(img + kImgVec);
+  if (e < kOffB1) {
+    const int k = (e - kOffW1) / kHid, j = (e - kOffW1) % kHid;
+    *reinterpret_cast<__nv_bfloat16*>(img + kImgW1 + core_offset(j, k, kIn)) = __float2bfloat16_rn(w);
+  } else if (e < kOffW2) {
+    vec[kVecB1 + e - kOffB1] = w;
+  } else if (e < kOffB2) {
+    const int i = (e - kOffW2) / kHid, j = (e - kOffW2) % kHid;
+    const __nv_bfloat16 q = __float2bfloat16_rn(w);
+    *reinterpret_cast<__nv_bfloat16*>(img + kImgW2t + core_offset(j, i, kHid)) = q;
+    *reinterpret_cast<__nv_bfloat16*>(img + kImgW2 + core_offset(i, j, kHid)) = q;
+  } else if (e < kOffW3) {
+    vec[kVecB2 + e - kOffB2] = w;
+  } else if (e < kOffB3) {
+    vec[kVecW3 + e - kOffW3] = w;
+  } else {
+    vec[kVecB3] = w;
+  }
+}
+
+__global__ void k_mlp_image(const float* __restrict__ p, unsigned char* __restrict__ img) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < kParams; e += gridDim.x * blockDim.x)
+    image_store(img, e, p[e]);
+}
+
+// Sum the tiles' rows of `part`: the gradient (into grad, if given) and the
+// loss (into *loss).  With m1 != nullptr also one Adam step on the FP32
+// master parameters, whose new values go to the operand image.
+__global__ void k_mlp_adam_tiles(float* __restrict__ p, const float* __restrict__ part, int tiles,
+                                 float* __restrict__ grad, float* __restrict__ loss,
+                                 float* __restrict__ m1, float* __restrict__ m2, float lr, float b1,
+                                 float b2, float eps, float c1, float c2,
+                                 unsigned char* __restrict__ img) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < kPart; e += gridDim.x * blockDim.x) {
+    float g = 0.f;
+    for (int t = 0; t < tiles; ++t) g += part[static_cast<int64_t>(t) * kPart + e];
+    if (e == kParams) {
+      if (loss) *loss = g;
+      continue;
+    }
+    if (grad) grad[e] = g;
+    if (m1) {
+      m1[e] = b1 * m1[e] + (1.f - b1) * g;
+      m2[e] = b2 * m2[e] + (1.f - b2) * g * g;
+      p[e] -= lr * (m1[e] / c1) / (sqrtf(m2[e] / c2) + eps);
+      image_store(img, e, p[e]);
+    }
+  }
+}
+
+// z = H2 w3 + b3 (inference).  One warp per row at a time: lane l holds
+// hidden units l and l + 32 (coalesced row reads), z is a warp sum.
+__global__ void k_mlp_head(int64_t M, const float* __restrict__ h2, const float* __restrict__ p,
+                           float* __restrict__ z) {
   static_assert(kHid == 64, "two hidden units per lane");
   const int lane = threadIdx.x & 31;
   const float w3a = p[kOffW3 + lane];
   const float w3b = p[kOffW3 + lane + 32];
   const float b3 = p[kOffB3];
-  const float inv_b = 1.0f / static_cast<float>(M);
-  float dwa = 0.f, dwb = 0.f, db = 0.f, ls = 0.f;
   const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x >> 5) + (threadIdx.x >> 5); i < M;
        i += warps) {
-    const float ha = h2[i * kHid + lane];
-    const float hb = h2[i * kHid + lane + 32];
-    float zi = ha * w3a + hb * w3b;
+    float zi = h2[i * kHid + lane] * w3a + h2[i * kHid + lane + 32] * w3b;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) zi += __shfl_xor_sync(0xFFFFFFFFu, zi, o);
-    zi += b3;
-    if (z && lane == 0) z[i] = zi;
-    if (y) {
-      const float r = zi - y[i];
-      const float dz = 2.0f * r * inv_b;
-      if (lane == 0) {
-        ls += r * r * inv_b;
-        db += dz;
-      }
-      dwa += dz * ha;
-      dwb += dz * hb;
-      const float da = a2[i * kHid + lane] > 0.f ? dz * w3a : 0.f;
-      const float dbb = a2[i * kHid + lane + 32] > 0.f ? dz * w3b : 0.f;
-      da2[i * kHid + lane] = da;
-      da2[i * kHid + lane + 32] = dbb;
-      da2_bf16[i * kHid + lane] = __float2bfloat16_rn(da);
-      da2_bf16[i * kHid + lane + 32] = __float2bfloat16_rn(dbb);
-    }
+    if (lane == 0) z[i] = zi + b3;
   }
-  if (y) {
-    if (dwa != 0.f) atomicAdd(&grad[kOffW3 + lane], dwa);
-    if (dwb != 0.f) atomicAdd(&grad[kOffW3 + lane + 32], dwb);
-    if (lane == 0) {
-      if (db != 0.f) atomicAdd(&grad[kOffB3], db);
-      if (ls != 0.f) atomicAdd(loss, ls);
-    }
-  }
-}
-
-// grad_W[k][j] += sum_i in[i][k] d[i][j] and grad_b[j] += sum_i d[i][j],
-// with in given as bf16 (X or H1) and d as fp32 (dA1 or dA2); d may be
-// masked by a pre-activation sign (dA1 = dH1 [A1 > 0]).
-template <int KIN>
-__global__ void k_mlp_wgrad(int64_t M, const __nv_bfloat16* __restrict__ in,
-                            const float* __restrict__ d, const float* __restrict__ mask_pre,
-                            float* __restrict__ gW, float* __restrict__ gb) {
-  __shared__ float s_in[32][KIN];
-  __shared__ float s_d[32][kHid];
-  // each thread owns KIN*64/256 weight entries
-  constexpr int kPer = KIN * kHid / 256;
-  float acc[kPer];
-  float accb = 0.f;
-#pragma unroll
-  for (int q = 0; q < kPer; ++q) acc[q] = 0.f;
-  for (int64_t base = static_cast<int64_t>(blockIdx.x) * 32; base < M;
-       base += static_cast<int64_t>(gridDim.x) * 32) {
-    for (int e = threadIdx.x; e < 32 * KIN; e += 256) {
-      const int r = e / KIN, k = e % KIN;
-      s_in[r][k] = base + r < M ? __bfloat162float(in[(base + r) * KIN + k]) : 0.f;
-    }
-    for (int e = threadIdx.x; e < 32 * kHid; e += 256) {
-      const int r = e / kHid, j = e % kHid;
-      float dv = 0.f;
-      if (base + r < M) {
-        dv = d[(base + r) * kHid + j];
-        if (mask_pre && !(mask_pre[(base + r) * kHid + j] > 0.f)) dv = 0.f;
-      }
-      s_d[r][j] = dv;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < kPer; ++q) {
-      const int e = threadIdx.x * kPer + q;
-      const int k = e / kHid, j = e % kHid;
-      float s = 0.f;
-      for (int r = 0; r < 32; ++r) s += s_in[r][k] * s_d[r][j];
-      acc[q] += s;
-    }
-    if (threadIdx.x < kHid) {
-      float s = 0.f;
-      for (int r = 0; r < 32; ++r) s += s_d[r][threadIdx.x];
-      accb += s;
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int q = 0; q < kPer; ++q) {
-    const int e = threadIdx.x * kPer + q;
-    atomicAdd(&gW[e], acc[q]);
-  }
-  if (threadIdx.x < kHid) atomicAdd(&gb[threadIdx.x], accb);
 }
 
 // BF16 operand copies of the weights: W1t [64][16] = W1^T, W2t [64][64] =
@@ -315,18 +639,6 @@ __global__ void k_mlp_pack(const float* __restrict__ p, __nv_bfloat16* __restric
     const int k = e / kHid, j = e % kHid;
     w2t[j * kHid + k] = __float2bfloat16_rn(p[kOffW2 + e]);
     w2[e] = __float2bfloat16_rn(p[kOffW2 + e]);
-  }
-}
-
-// Adam on the FP32 master parameters.
-__global__ void k_mlp_adam(float* __restrict__ p, const float* __restrict__ g,
-                           float* __restrict__ m1, float* __restrict__ m2, float lr, float b1,
-                           float b2, float eps, float c1, float c2) {
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < kParams; e += gridDim.x * blockDim.x) {
-    const float ge = g[e];
-    m1[e] = b1 * m1[e] + (1.f - b1) * ge;
-    m2[e] = b2 * m2[e] + (1.f - b2) * ge * ge;
-    p[e] -= lr * (m1[e] / c1) / (sqrtf(m2[e] / c2) + eps);
   }
 }
 
@@ -481,23 +793,21 @@ struct mlmc_mlp {
   cudaStream_t stream = nullptr;
   int num_sms = 0;
   float* d_p = nullptr;      // FP32 master parameters
-  float* d_g = nullptr;      // gradients
+  float* d_g = nullptr;      // gradients (mlmc_mlp_loss_grad)
   float* d_m1 = nullptr;     // Adam moments
   float* d_m2 = nullptr;
   float* d_loss = nullptr;
   uint32_t* d_err = nullptr;
-  __nv_bfloat16* d_w1t = nullptr;
+  __nv_bfloat16* d_w1t = nullptr;  // inference operands (k_mlp_pack)
   __nv_bfloat16* d_w2t = nullptr;
   __nv_bfloat16* d_w2 = nullptr;
-  // activations for up to cap rows
+  unsigned char* d_img = nullptr;  // the fused training kernel's operand image
+  float* d_part = nullptr;         // per-tile gradients and losses
+  int64_t part_tiles = 0;
+  // inference activations for up to cap rows
   int64_t cap = 0;
   __nv_bfloat16* d_h1 = nullptr;
-  float* d_a1 = nullptr;
-  float* d_a2 = nullptr;
   float* d_h2 = nullptr;
-  float* d_da2 = nullptr;
-  __nv_bfloat16* d_da2b = nullptr;
-  float* d_dh1 = nullptr;
   int64_t adam_t = 0;
   int64_t launches = 0;
 };
@@ -520,21 +830,24 @@ mlmc_status mfail(mlmc_status st, const std::string& msg) {
 mlmc_status ensure_cap(mlmc_mlp* m, int64_t rows) {
   if (rows <= m->cap) return MLMC_OK;
   cudaFree(m->d_h1);
-  cudaFree(m->d_a1);
-  cudaFree(m->d_a2);
   cudaFree(m->d_h2);
-  cudaFree(m->d_da2);
-  cudaFree(m->d_da2b);
-  cudaFree(m->d_dh1);
+  m->d_h1 = nullptr;
+  m->d_h2 = nullptr;
+  m->cap = 0;
   const size_t r = static_cast<size_t>(rows) * kHid;
   MLP_CUDA(cudaMalloc(&m->d_h1, r * 2), "alloc");
-  MLP_CUDA(cudaMalloc(&m->d_a1, r * 4), "alloc");
-  MLP_CUDA(cudaMalloc(&m->d_a2, r * 4), "alloc");
   MLP_CUDA(cudaMalloc(&m->d_h2, r * 4), "alloc");
-  MLP_CUDA(cudaMalloc(&m->d_da2, r * 4), "alloc");
-  MLP_CUDA(cudaMalloc(&m->d_da2b, r * 2), "alloc");
-  MLP_CUDA(cudaMalloc(&m->d_dh1, r * 4), "alloc");
   m->cap = rows;
+  return MLMC_OK;
+}
+
+mlmc_status ensure_tiles(mlmc_mlp* m, int64_t tiles) {
+  if (tiles <= m->part_tiles) return MLMC_OK;
+  cudaFree(m->d_part);
+  m->d_part = nullptr;
+  m->part_tiles = 0;
+  MLP_CUDA(cudaMalloc(&m->d_part, sizeof(float) * static_cast<size_t>(tiles) * kPart), "alloc");
+  m->part_tiles = tiles;
   return MLMC_OK;
 }
 
@@ -555,38 +868,51 @@ cudaError_t tile(mlmc_mlp* m, int64_t M, const __nv_bfloat16* A, const __nv_bflo
   return cudaGetLastError();
 }
 
-// Forward of rows x[0..M) (bf16, 16 wide) into z (and the activations).
-mlmc_status forward(mlmc_mlp* m, const __nv_bfloat16* x, int64_t M, float* z, const float* y,
-                    bool train) {
+// Inference: z = MLP(x) for rows x[0..M) (bf16, 16 wide).
+mlmc_status forward(mlmc_mlp* m, const __nv_bfloat16* x, int64_t M, float* z) {
   mlmc_status st = ensure_cap(m, M);
   if (st != MLMC_OK) return st;
   MLP_CUDA((k_mlp_pack<<<1, 256, 0, m->stream>>>(m->d_p, m->d_w1t, m->d_w2t, m->d_w2),
             cudaGetLastError()), "pack");
-  MLP_CUDA(tile<kIn>(m, M, x, m->d_w1t, m->d_p + kOffB1, true, m->d_h1, nullptr, m->d_a1),
+  MLP_CUDA(tile<kIn>(m, M, x, m->d_w1t, m->d_p + kOffB1, true, m->d_h1, nullptr, nullptr),
            "layer 1");
-  MLP_CUDA(tile<kHid>(m, M, m->d_h1, m->d_w2t, m->d_p + kOffB2, true, nullptr, m->d_h2, m->d_a2),
+  MLP_CUDA(tile<kHid>(m, M, m->d_h1, m->d_w2t, m->d_p + kOffB2, true, nullptr, m->d_h2, nullptr),
            "layer 2");
   // one warp per row: 8 rows per block of 256 at a time
   const unsigned g = static_cast<unsigned>(std::min<int64_t>((M + 7) / 8, m->num_sms * 8));
-  if (train) MLP_CUDA(cudaMemsetAsync(m->d_loss, 0, sizeof(float), m->stream), "memset");
-  k_mlp_head<<<std::max(1u, g), 256, 0, m->stream>>>(M, m->d_h2, m->d_a2, m->d_p, train ? y : nullptr,
-                                                       z, m->d_da2, m->d_da2b, m->d_g, m->d_loss);
+  k_mlp_head<<<std::max(1u, g), 256, 0, m->stream>>>(M, m->d_h2, m->d_p, z);
   MLP_CUDA(cudaGetLastError(), "head");
   m->launches += 2;
   return MLMC_OK;
 }
 
-mlmc_status backward(mlmc_mlp* m, const __nv_bfloat16* x, int64_t M) {
-  // dH1 = dA2 W2^T on the tensor cores; then the weight gradients.
-  MLP_CUDA(tile<kHid>(m, M, m->d_da2b, m->d_w2, nullptr, false, nullptr, m->d_dh1, nullptr), "dH1");
-  const unsigned g = static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>((M + 31) / 32, m->num_sms * 4)));
-  k_mlp_wgrad<kHid><<<g, 256, 0, m->stream>>>(M, m->d_h1, m->d_da2, nullptr, m->d_g + kOffW2,
-                                               m->d_g + kOffB2);
-  MLP_CUDA(cudaGetLastError(), "dW2");
-  k_mlp_wgrad<kIn><<<g, 256, 0, m->stream>>>(M, x, m->d_dh1, m->d_a1, m->d_g + kOffW1,
-                                              m->d_g + kOffB1);
-  MLP_CUDA(cudaGetLastError(), "dW1");
-  m->launches += 2;
+// The fused forward and backward of M batch rows (x[b], or a device-drawn
+// minibatch of the n_src rows when sample), one CTA per 128 rows; the
+// tiles' gradients and losses land in d_part.
+mlmc_status train_tiles(mlmc_mlp* m, const __nv_bfloat16* x, const float* y, int64_t n_src,
+                        int64_t M, bool sample, uint64_t sample_seed, int64_t* tiles_out) {
+  static bool attr_done = false;
+  if (!attr_done) {
+    MLP_CUDA(cudaFuncSetAttribute(k_mlp_train_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  kTrainSmem), "smem attribute");
+    attr_done = true;
+  }
+  const int64_t tiles = (M + kTileM - 1) / kTileM;
+  mlmc_status st = ensure_tiles(m, tiles);
+  if (st != MLMC_OK) return st;
+  k_mlp_train_tile<<<static_cast<unsigned>(tiles), kTileM, kTrainSmem, m->stream>>>(
+      M, x, y, n_src, sample_seed, sample ? 1 : 0, m->d_img, m->d_part, m->d_err);
+  MLP_CUDA(cudaGetLastError(), "train tile");
+  m->launches++;
+  *tiles_out = tiles;
+  return MLMC_OK;
+}
+
+// The operand image from the current parameters.
+mlmc_status make_image(mlmc_mlp* m) {
+  k_mlp_image<<<(kParams + 255) / 256, 256, 0, m->stream>>>(m->d_p, m->d_img);
+  MLP_CUDA(cudaGetLastError(), "image");
+  m->launches++;
   return MLMC_OK;
 }
 
@@ -623,6 +949,8 @@ mlmc_status mlmc_mlp_create(mlmc_mlp** out, uint64_t seed, void* cuda_stream) {
   if ((e = cudaMalloc(&m->d_w1t, kIn * kHid * 2)) != cudaSuccess) return bail(e);
   if ((e = cudaMalloc(&m->d_w2t, kHid * kHid * 2)) != cudaSuccess) return bail(e);
   if ((e = cudaMalloc(&m->d_w2, kHid * kHid * 2)) != cudaSuccess) return bail(e);
+  if ((e = cudaMalloc(&m->d_img, kImgBytes)) != cudaSuccess) return bail(e);
+  if ((e = cudaMemset(m->d_img, 0, kImgBytes)) != cudaSuccess) return bail(e);
   // He-style initialisation from a seeded host generator (splitmix64).
   std::vector<float> p(kParams, 0.f);
   uint64_t s = seed ^ 0x9E3779B97F4A7C15ull;
@@ -656,13 +984,10 @@ void mlmc_mlp_destroy(mlmc_mlp* m) {
   cudaFree(m->d_w1t);
   cudaFree(m->d_w2t);
   cudaFree(m->d_w2);
+  cudaFree(m->d_img);
+  cudaFree(m->d_part);
   cudaFree(m->d_h1);
-  cudaFree(m->d_a1);
-  cudaFree(m->d_a2);
   cudaFree(m->d_h2);
-  cudaFree(m->d_da2);
-  cudaFree(m->d_da2b);
-  cudaFree(m->d_dh1);
   delete m;
 }
 
@@ -680,7 +1005,7 @@ mlmc_status mlmc_mlp_params(mlmc_mlp* m, const float* set, float* get) {
 
 mlmc_status mlmc_mlp_forward(mlmc_mlp* m, const uint16_t* x, int64_t n, float* z) {
   if (!m || !x || !z || n < 1) return mfail(MLMC_ERR_INVALID_ARG, "mlmc_mlp_forward: bad argument");
-  mlmc_status st = forward(m, reinterpret_cast<const __nv_bfloat16*>(x), n, z, nullptr, false);
+  mlmc_status st = forward(m, reinterpret_cast<const __nv_bfloat16*>(x), n, z);
   if (st != MLMC_OK) return st;
   return check_err(m);
 }
@@ -688,13 +1013,16 @@ mlmc_status mlmc_mlp_forward(mlmc_mlp* m, const uint16_t* x, int64_t n, float* z
 mlmc_status mlmc_mlp_loss_grad(mlmc_mlp* m, const uint16_t* x, const float* y, int64_t n,
                                float* loss, float* grad) {
   if (!m || !x || !y || n < 1) return mfail(MLMC_ERR_INVALID_ARG, "mlmc_mlp_loss_grad: bad argument");
-  MLP_CUDA(cudaMemsetAsync(m->d_g, 0, kParams * 4, m->stream), "memset");
-  float* zs = nullptr;
-  MLP_CUDA(cudaMallocAsync(&zs, sizeof(float) * n, m->stream), "alloc z");
-  mlmc_status st = forward(m, reinterpret_cast<const __nv_bfloat16*>(x), n, zs, y, true);
-  if (st == MLMC_OK) st = backward(m, reinterpret_cast<const __nv_bfloat16*>(x), n);
-  cudaFreeAsync(zs, m->stream);
+  mlmc_status st = make_image(m);
+  int64_t tiles = 0;
+  if (st == MLMC_OK)
+    st = train_tiles(m, reinterpret_cast<const __nv_bfloat16*>(x), y, n, n, false, 0, &tiles);
   if (st != MLMC_OK) return st;
+  k_mlp_adam_tiles<<<(kPart + 255) / 256, 256, 0, m->stream>>>(
+      m->d_p, m->d_part, static_cast<int>(tiles), m->d_g, m->d_loss, nullptr, nullptr, 0.f, 0.f,
+      0.f, 0.f, 1.f, 1.f, nullptr);
+  MLP_CUDA(cudaGetLastError(), "reduce");
+  m->launches++;
   if (loss) MLP_CUDA(cudaMemcpyAsync(loss, m->d_loss, 4, cudaMemcpyDefault, m->stream), "loss");
   if (grad) MLP_CUDA(cudaMemcpyAsync(grad, m->d_g, kParams * 4, cudaMemcpyDefault, m->stream), "grad");
   return check_err(m);
@@ -705,49 +1033,28 @@ mlmc_status mlmc_mlp_train(mlmc_mlp* m, const uint16_t* x, const float* y, int64
   if (!m || !x || !y || n < 1 || steps < 1 || batch < 1)
     return mfail(MLMC_ERR_INVALID_ARG, "mlmc_mlp_train: bad argument");
   const int64_t B = std::min<int64_t>(batch, n);
-  __nv_bfloat16* xb = nullptr;
-  float* yb = nullptr;
-  int64_t* idx = nullptr;
-  float* zs = nullptr;
-  MLP_CUDA(cudaMalloc(&xb, sizeof(__nv_bfloat16) * B * kIn), "alloc");
-  MLP_CUDA(cudaMalloc(&yb, sizeof(float) * B), "alloc");
-  MLP_CUDA(cudaMalloc(&idx, sizeof(int64_t) * B), "alloc");
-  MLP_CUDA(cudaMalloc(&zs, sizeof(float) * B), "alloc");
-  std::vector<int64_t> h_idx(B);
-  uint64_t s = seed * 0x9E3779B97F4A7C15ull + 1;
-  mlmc_status st = MLMC_OK;
+  // Two launches per step: the fused forward and backward of the batch's
+  // tiles (rows drawn on the device), then the tiles' sum and the Adam
+  // step, which also rewrites the operand image for the next step.
+  mlmc_status st = make_image(m);
   for (int it = 0; it < steps && st == MLMC_OK; ++it) {
-    for (int64_t r = 0; r < B; ++r) {  // uniform minibatch rows (xorshift)
-      s ^= s << 13;
-      s ^= s >> 7;
-      s ^= s << 17;
-      h_idx[r] = static_cast<int64_t>(s % static_cast<uint64_t>(n));
-    }
-    if (cudaMemcpyAsync(idx, h_idx.data(), sizeof(int64_t) * B, cudaMemcpyHostToDevice, m->stream) != cudaSuccess) {
-      st = mfail(MLMC_ERR_CUDA, "mlp train: copy idx");
-      break;
-    }
-    k_gather<<<m->num_sms * 2, 256, 0, m->stream>>>(B, idx, reinterpret_cast<const __nv_bfloat16*>(x), y, xb, yb);
-    cudaMemsetAsync(m->d_g, 0, kParams * 4, m->stream);
-    st = forward(m, xb, B, zs, yb, true);
-    if (st == MLMC_OK) st = backward(m, xb, B);
+    int64_t tiles = 0;
+    const uint64_t sample_seed = (seed * 0x9E3779B97F4A7C15ull) ^ (static_cast<uint64_t>(it) << 40);
+    st = train_tiles(m, reinterpret_cast<const __nv_bfloat16*>(x), y, n, B, true, sample_seed,
+                     &tiles);
     if (st != MLMC_OK) break;
     ++m->adam_t;
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.f - std::pow(b1, static_cast<float>(m->adam_t));
     const float c2 = 1.f - std::pow(b2, static_cast<float>(m->adam_t));
-    k_mlp_adam<<<(kParams + 255) / 256, 256, 0, m->stream>>>(m->d_p, m->d_g, m->d_m1, m->d_m2, lr,
-                                                              b1, b2, 1e-8f, c1, c2);
-    m->launches += 2;
+    k_mlp_adam_tiles<<<(kPart + 255) / 256, 256, 0, m->stream>>>(
+        m->d_p, m->d_part, static_cast<int>(tiles), nullptr, m->d_loss, m->d_m1, m->d_m2, lr, b1,
+        b2, 1e-8f, c1, c2, m->d_img);
+    m->launches++;
     if (cudaGetLastError() != cudaSuccess) st = mfail(MLMC_ERR_CUDA, "mlp train: launch");
   }
-  cudaStreamSynchronize(m->stream);
-  if (st == MLMC_OK && final_loss) cudaMemcpy(final_loss, m->d_loss, 4, cudaMemcpyDeviceToHost);
-  cudaFree(xb);
-  cudaFree(yb);
-  cudaFree(idx);
-  cudaFree(zs);
   if (st != MLMC_OK) return st;
+  if (final_loss) MLP_CUDA(cudaMemcpyAsync(final_loss, m->d_loss, 4, cudaMemcpyDefault, m->stream), "loss");
   return check_err(m);
 }
 
@@ -781,6 +1088,13 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
   if (p->sched.mode != MLMC_BACKWARD)
     return mfail(MLMC_ERR_INVALID_ARG, "mlmc_learn_tilt: backward-mode plans only");
   const bool clocks = (tilt & MLMC_TILT_CLOCKS) != 0;
+  // The pilots draw from their own stream (a hash of seed), never from the
+  // one mlmc_expmv draws with the same seed: the tilt must not depend on the
+  // walks that later estimate x.
+  uint64_t learn_seed = seed ^ 0x6C6561726E74696Cull;
+  learn_seed = (learn_seed ^ (learn_seed >> 30)) * 0xBF58476D1CE4E5B9ull;
+  learn_seed = (learn_seed ^ (learn_seed >> 27)) * 0x94D049BB133111EBull;
+  learn_seed ^= learn_seed >> 31;
   const bool was = p->proposal_active;
   const bool was_clocks = p->clock_tilt;
   // The first pilot uses the paper's walk (jumps only) or, with tilted
@@ -793,10 +1107,12 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
   float* z = nullptr;
   float* h = nullptr;
   float* pv = nullptr;  // v, k^m v (m = 1..4), T_3 and two Taylor terms (8 x n floats)
+  float* best_h = nullptr;        // the tilt with the smallest pilot variance so far
   int64_t* widx = nullptr;        // training rows, weighted by degree (see below)
   __nv_bfloat16* wfeat = nullptr;
   float* wy = nullptr;
   auto cleanup = [&]() {
+    cudaFree(best_h);
     cudaFree(widx);
     cudaFree(wfeat);
     cudaFree(wy);
@@ -826,6 +1142,7 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
   LP_CUDA(cudaMalloc(&z, sizeof(float) * p->n), "alloc");
   LP_CUDA(cudaMalloc(&h, sizeof(float) * p->n), "alloc");
   LP_CUDA(cudaMalloc(&pv, sizeof(float) * p->n * 8), "alloc");
+  LP_CUDA(cudaMalloc(&best_h, sizeof(float) * p->n), "alloc");
   LP_CUDA(cudaMemcpyAsync(dv, v, sizeof(double) * p->n, cudaMemcpyDefault, p->stream), "copy v");
   const unsigned g = static_cast<unsigned>(std::min<int64_t>((p->n + 255) / 256, p->num_sms * 8));
   // Features (fixed over the rounds: they use the paper's jump law).
@@ -905,33 +1222,64 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
                             p->stream), "write rows");
     LP_CUDA(cudaStreamSynchronize(p->stream), "sync");
   }
-  for (int32_t round = 0; round < rounds; ++round) {
-    LP_CUDA(cudaMemsetAsync(sums, 0, sizeof(double) * (p->n + kTotSlots), p->stream), "memset");
+  // One pilot at l0 with the plan's current walk law: walks [rep_begin,
+  // rep_begin + reps) of every row.  Leaves x-hat (the per-row means) in
+  // sums, its largest magnitude in *xmax, and the per-walk variance of the
+  // law (the rows' sample variances, averaged over the rows) in *var.
+  auto pilot = [&](int64_t rep_begin, int64_t reps, double* xmax, double* var) -> cudaError_t {
+    cudaError_t e = cudaMemsetAsync(sums, 0, sizeof(double) * (p->n + kTotSlots), p->stream);
+    if (e != cudaSuccess) return e;
     WalkLaunch w;
     w.level = p->l0;
     w.coarse = false;
-    // Later rounds walk with the previous tilt, whose samples are cheap and
-    // much less noisy: four times the first round's walks per row.
-    const int64_t round_walks = round == 0 ? pilot_walks : 4 * pilot_walks;
-    w.rep_begin = round == 0 ? 0 : pilot_walks + 4 * pilot_walks * (round - 1);
-    w.reps = round_walks;
-    w.seed = seed;
+    w.rep_begin = rep_begin;
+    w.reps = reps;
+    w.seed = learn_seed;
     w.v = dv;
     w.sum_y = sums;
     w.totals = sums + p->n;
-    LP_CUDA(launch_walk(p, w), "pilot walks");
-    // x-hat = sums / pilot, in place
-    const double scale = 1.0 / static_cast<double>(round_walks);
-    double xmax = 0.0;
-    {
-      std::vector<double> hsum(p->n);
-      LP_CUDA(cudaMemcpyAsync(hsum.data(), sums, sizeof(double) * p->n, cudaMemcpyDeviceToHost, p->stream), "read");
-      LP_CUDA(cudaStreamSynchronize(p->stream), "sync");
-      for (auto& q : hsum) {
-        q *= scale;
-        xmax = std::max(xmax, std::fabs(q));
-      }
-      LP_CUDA(cudaMemcpyAsync(sums, hsum.data(), sizeof(double) * p->n, cudaMemcpyHostToDevice, p->stream), "write");
+    if ((e = launch_walk(p, w)) != cudaSuccess) return e;
+    std::vector<double> hsum(p->n + kTotSlots);
+    e = cudaMemcpyAsync(hsum.data(), sums, sizeof(double) * (p->n + kTotSlots),
+                        cudaMemcpyDeviceToHost, p->stream);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(p->stream)) != cudaSuccess) return e;
+    const double scale = 1.0 / static_cast<double>(reps);
+    double sq = 0.0;
+    *xmax = 0.0;
+    for (int64_t i = 0; i < p->n; ++i) {
+      sq += hsum[i] * hsum[i] * scale;
+      hsum[i] *= scale;
+      *xmax = std::max(*xmax, std::fabs(hsum[i]));
+    }
+    *var = reps > 1 ? (hsum[p->n + kTotY2] - sq) / static_cast<double>(reps - 1) /
+                          static_cast<double>(p->n)
+                    : std::numeric_limits<double>::infinity();
+    return cudaMemcpyAsync(sums, hsum.data(), sizeof(double) * p->n, cudaMemcpyHostToDevice,
+                           p->stream);
+  };
+  // Every pilot measures the law it walks with; the tilt with the smallest
+  // measured variance is the one installed at the end (the warm start, or
+  // for jumps only the paper's walk, h = 1, are candidates too).
+  double best_var = std::numeric_limits<double>::infinity();
+  p->learn_var.clear();
+  p->learn_choice = -1;
+  int64_t next_rep = 0;
+  for (int32_t round = 0; round < rounds; ++round) {
+    // Later rounds walk with the previous tilt, whose samples are cheap and
+    // much less noisy: four times the first round's walks per row.
+    const int64_t round_walks = round == 0 ? pilot_walks : 4 * pilot_walks;
+    double xmax = 0.0, var = 0.0;
+    LP_CUDA(pilot(next_rep, round_walks, &xmax, &var), "pilot walks");
+    next_rep += round_walks;
+    p->learn_var.push_back(var);
+    if (var < best_var) {
+      best_var = var;
+      p->learn_choice = round;
+      // (round 0 without clocks walks the paper's law: nothing to keep)
+      if (round > 0 || clocks)
+        LP_CUDA(cudaMemcpyAsync(best_h, h, sizeof(float) * p->n, cudaMemcpyDeviceToDevice,
+                                p->stream), "keep tilt");
     }
     // Targets log(|x-hat| + 1e-3 max|x-hat|) (rows the pilot never reached
     // do not get arbitrarily small h), averaged with log(|v| + 1e-3 max|v|)
@@ -949,7 +1297,7 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
     LP_CUDA(cudaStreamSynchronize(p->stream), "sync");
     st = mlmc_mlp_train(m, reinterpret_cast<const uint16_t*>(wfeat), wy, n_train, steps, batch, lr,
                         seed ^ (0xABCDEFull + static_cast<uint64_t>(round)), final_loss);
-    if (st == MLMC_OK) st = forward(m, feat, p->n, z, nullptr, false);
+    if (st == MLMC_OK) st = forward(m, feat, p->n, z);
     if (st == MLMC_OK) st = check_err(m);
     if (st != MLMC_OK) break;
     k_exp_h<<<g, 256, 0, p->stream>>>(p->n, z, h);
@@ -958,6 +1306,17 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
     st = mlmc_plan_set_tilt(p, h, alpha, tilt);
     if (st != MLMC_OK) break;
   }
+  if (st == MLMC_OK) {
+    // The last round's tilt is measured like the others; if an earlier law
+    // had the smaller variance, that one is installed instead.
+    double xmax = 0.0, var = 0.0;
+    LP_CUDA(pilot(next_rep, 4 * pilot_walks, &xmax, &var), "final pilot");
+    p->learn_var.push_back(var);
+    if (var < best_var)
+      p->learn_choice = rounds;
+    else
+      st = mlmc_plan_set_tilt(p, p->learn_choice == 0 && !clocks ? nullptr : best_h, alpha, tilt);
+  }
   cleanup();
   if (st != MLMC_OK) {
     p->proposal_active = was;
@@ -965,6 +1324,16 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
   }
   return st;
 #undef LP_CUDA
+}
+
+mlmc_status mlmc_plan_learn_report(const mlmc_plan* p, int32_t* chosen, double* var, int32_t cap,
+                                   int32_t* count) {
+  if (!p || (cap > 0 && !var) || cap < 0) return mfail(MLMC_ERR_INVALID_ARG, "mlmc_plan_learn_report: bad argument");
+  const int32_t k = static_cast<int32_t>(p->learn_var.size());
+  if (count) *count = k;
+  if (chosen) *chosen = p->learn_choice;
+  for (int32_t i = 0; i < k && i < cap; ++i) var[i] = p->learn_var[static_cast<size_t>(i)];
+  return MLMC_OK;
 }
 
 }  // extern "C"

@@ -352,6 +352,13 @@ static_assert(31u + 32u * kScreenWays <= WarpQueue<true>::kCap, "FP64 screening 
 static_assert((WarpQueue<false>::kCap & (WarpQueue<false>::kCap - 1)) == 0, "ring size");
 static_assert((WarpQueue<true>::kCap & (WarpQueue<true>::kCap - 1)) == 0, "ring size");
 constexpr uint32_t kQueueCap = 64;  // the end queue's ring
+// FP32 walks of rows that are not screened (long walks): jumps a lane makes
+// per iteration of the one-wave loop before the warp's claim and end votes.
+#ifndef MLMC_LONG_EVENTS
+#define MLMC_LONG_EVENTS 2
+#endif
+constexpr int kLongEvents = MLMC_LONG_EVENTS;
+static_assert(kLongEvents >= 1 && kLongEvents <= 8, "jumps per iteration");
 
 // Per-warp queue of walks that ended at s = 1 (their samples are evaluated 32
 // at a time): the exponents and the end state with the sign in bit 31.  At
@@ -971,22 +978,44 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
             finish(2, true);
           }
         } else {
-          // Draw e gives the pending jump (words 2, 3) and the holding time
-          // after it (word 0); a fresh walk first draws its first holding
-          // time from word 1 (rows with 1/(tL) < 1: no shared block word).
-          if (fresh) {
-            s_pend = P::add(s, P::mul(neglog32(uniform32(x.y)), static_cast<T>(m.inv_rate)));
-            fresh = false;
+          // Up to kLongEvents jumps per lane per iteration: the claim, the
+          // end bookkeeping and the warp votes around them are paid once for
+          // both.  Draw e gives the pending jump (words 2, 3) and the holding
+          // time after it (word 0); a fresh walk first takes its first
+          // holding time from word 1 (rows with 1/(tL) < 1: no shared block
+          // word).  One end site: status -1 while the walk goes on.
+          // (one per iteration with a source term or output times: their
+          // per-segment sums need the registers)
+          constexpr int kEvents = (SRC || TIMES) ? 1 : kLongEvents;
+          int status = -1;
+          for (int k = 0; k < kEvents; ++k) {
+            const uint4 xk = k == 0 ? x : keys.draw(make_uint4(c_lo, row32, e, c_hi));
+            if (fresh) {
+              s_pend = P::add(s, P::mul(neglog32(uniform32(xk.y)), static_cast<T>(m.inv_rate)));
+              fresh = false;
+            }
+            if (!(s_pend < static_cast<T>(1))) {
+              status = 0;  // never jumped
+              break;
+            }
+            if (static_cast<int64_t>(e) >= a.max_jumps) {
+              status = 1;
+              break;
+            }
+            if (!jump(s_pend, xk.z, xk.w)) {
+              status = 2;
+              break;
+            }
+            s_pend = P::add(s, P::mul(neglog32(uniform32(xk.x)), static_cast<T>(m.inv_rate)));
+            if (!(s_pend < static_cast<T>(1))) {
+              status = 0;
+              break;
+            }
           }
-          if (!(s_pend < static_cast<T>(1))) {
-            finish(0, true);  // never jumped
-          } else if (static_cast<int64_t>(e) >= a.max_jumps) {
+          if (status == 1) {
             stop_limit(s_pend, true);
-          } else if (!jump(s_pend, x.z, x.w)) {
-            finish(2, true);
-          } else {
-            s_pend = P::add(s, P::mul(neglog32(uniform32(x.x)), static_cast<T>(m.inv_rate)));
-            if (!(s_pend < static_cast<T>(1))) finish(0, true);
+          } else if (status >= 0) {
+            finish(status, true);
           }
         }
       }

@@ -113,6 +113,7 @@ def load(build_if_missing: bool = False):
     lib.mlmc_plan_set_tilt.argtypes = [P, P, D, I32]
     lib.mlmc_export_tilt.argtypes = [P] + [P] * 6
     lib.mlmc_export_h.argtypes = [P, P]
+    lib.mlmc_plan_learn_report.argtypes = [P, ct.POINTER(I32), P, I32, ct.POINTER(I32)]
     lib.mlmc_shard_buffer_doubles.argtypes = [P]
     lib.mlmc_shard_buffer_doubles.restype = I64
     lib.mlmc_shard_range.argtypes = [I64, I32, I32, ct.POINTER(I64), ct.POINTER(I64)]
@@ -145,7 +146,8 @@ def load(build_if_missing: bool = False):
                  "mlmc_export_tables", "mlmc_batch_create", "mlmc_batch_expmv",
                  "mlmc_batch_stats", "mlmc_batch_info", "mlmc_batch_autotune",
                  "mlmc_plan_set_proposal", "mlmc_plan_set_tilt", "mlmc_export_tilt",
-                 "mlmc_export_h", "mlmc_shard_range", "mlmc_plan_set_shard",
+                 "mlmc_export_h", "mlmc_plan_learn_report", "mlmc_shard_range",
+                 "mlmc_plan_set_shard",
                  "mlmc_plan_set_source", "mlmc_plan_l2_window",
                  "mlmc_plan_save_state", "mlmc_plan_load_state", "mlmc_expmv_resume",
                  "mlmc_export_proposal",
@@ -407,6 +409,15 @@ class Plan:
         h = np.zeros(self.n, np.float32)
         _check(self._lib.mlmc_export_h(self._h, _ptr(h)))
         return h
+
+    def learn_report(self):
+        """mlmc_plan_learn_report: (index of the installed law, per-walk
+        variance at l0 of each pilot of the last learning)."""
+        chosen, count = ct.c_int32(-1), ct.c_int32(0)
+        var = np.zeros(16)
+        _check(self._lib.mlmc_plan_learn_report(self._h, ct.byref(chosen), _ptr(var), 16,
+                                                ct.byref(count)))
+        return int(chosen.value), [float(x) for x in var[:min(count.value, 16)]]
 
     def shard_buffer_doubles(self) -> int:
         return int(self._lib.mlmc_shard_buffer_doubles(self._h))

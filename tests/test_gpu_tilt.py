@@ -201,9 +201,34 @@ def test_learned_tilt_beats_the_plain_walk():
             net.learn_tilt(plan, v, seed=99, pilot_walks=64, steps=300, batch=8192, clocks=True,
                            rounds=2)
         vt, m = _level0_var(plan, v, 256, 5)
+        chosen, pv = plan.learn_report()
         xs = np.zeros(b.n)
         plan.expmv(v, xs, seed=23)
         _, est = plan.stats()
     assert vt < vp / 5, (vt, vp)
+    # three pilots (the warm start's, round 1's tilt, the final tilt): the
+    # installed law is the one with the smallest measured variance
+    assert len(pv) == 3 and 0 <= chosen <= 2 and pv[chosen] == min(pv), (chosen, pv)
     err = np.linalg.norm(xs - x) / np.linalg.norm(x)
     assert est <= 1e-3 and err <= 2e-3, (err, est)
+
+
+def test_learning_keeps_the_better_law():
+    # The paper's walk on a graph where its variance is already small (a 2D
+    # Laplacian with v = 1): whatever the network learns from 8 walks per
+    # row, the plan ends with the law whose pilot measured the smallest
+    # variance, and the installed law is what the plan walks with.
+    from paper_1904_12754_gb300 import mlmc as M
+    a = I.laplacian_2d(40)
+    t, v = 0.5, np.ones(a.n)
+    with make_plan(a, t, 1, rel_tol=1e-3, num_levels=3, max_levels=6) as plan:
+        with M.MLP(seed=1, stream=stream_handle()) as net:
+            net.learn_proposal(plan, v, seed=4, pilot_walks=8, steps=20, batch=512)
+        chosen, pv = plan.learn_report()
+        assert len(pv) == 2 and pv[chosen] == min(pv), (chosen, pv)
+        if chosen == 0:
+            # the paper's walk won: no proposal is left on the plan
+            with pytest.raises(M.MlmcError):
+                plan.export_h()
+        else:
+            assert np.all(plan.export_h() > 0)
