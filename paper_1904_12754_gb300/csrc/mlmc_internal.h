@@ -107,6 +107,12 @@ struct mlmc_plan {
   int32_t* d_still32_t = nullptr;
   double* d_lam = nullptr;
   bool clock_tilt = false;
+  // Rows the table builds give a block each (stored length 256..8192): the
+  // list (d_heavy), its device count and, once classified, its host count
+  // (-1 before).
+  int32_t* d_heavy = nullptr;
+  uint32_t* d_heavy_count = nullptr;
+  int64_t heavy_count = -1;
   // The last mlmc_learn_tilt: the per-walk variance each pilot measured
   // (pilot k walked with the law installed before round k; the last one
   // with the final tilt) and which law was installed (-1: none).

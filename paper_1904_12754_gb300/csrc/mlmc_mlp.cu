@@ -233,9 +233,12 @@ constexpr int kTsImg = 0;
 constexpr int kTsX = kTsImg + kImgBytes;              // X tile, 128 x 16 BF16 (A of GEMM 1)
 constexpr int kTsH1 = kTsX + kTileM * kIn * 2;        // H1, 128 x 64 BF16 (A of GEMM 2)
 constexpr int kTsDA2b = kTsH1 + kTileM * kHid * 2;    // dA2, 128 x 64 BF16 (A of GEMM 3)
-constexpr int kTsDA2 = kTsDA2b + kTileM * kHid * 2;   // dA2, 128 x 64 FP32, row-major
-constexpr int kTsF2 = kTsDA2 + kTileM * kHid * 4;     // H2, then dA1: 128 x 64 FP32
-constexpr int kTsDZ = kTsF2 + kTileM * kHid * 4;      // dz per row
+// FP32 row-major tiles with a row stride of 68 floats: a thread's 16-byte
+// stores into its own row then fall in 8 distinct bank groups per warp.
+constexpr int kLd = 68;
+constexpr int kTsDA2 = kTsDA2b + kTileM * kHid * 2;   // dA2, 128 x 64 FP32
+constexpr int kTsF2 = kTsDA2 + kTileM * kLd * 4;      // H2, then dA1: 128 x 64 FP32
+constexpr int kTsDZ = kTsF2 + kTileM * kLd * 4;       // dz per row
 constexpr int kTsLoss = kTsDZ + kTileM * 4;           // loss term per row
 constexpr int kTsBar = kTsLoss + kTileM * 4;          // 4 mbarriers
 constexpr int kTsSlot = kTsBar + 4 * 8;               // TMEM address
@@ -420,10 +423,13 @@ __global__ void __launch_bounds__(128)
         const int col = cb * 16 + j;
         const float a = v[j] + vec[kVecB2 + col];
         if (a > 0.f) mask2[cb >> 1] |= 1u << ((cb & 1) * 16 + j);
-        const float h = fmaxf(a, 0.f);
-        f2[tid * kHid + col] = h;
-        z += h * vec[kVecW3 + col];
+        v[j] = fmaxf(a, 0.f);
+        z += v[j] * vec[kVecW3 + col];
       }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        *reinterpret_cast<float4*>(f2 + tid * kLd + cb * 16 + 4 * i) =
+            make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
     }
     z += vec[kVecB3];
     const float inv_b = 1.0f / static_cast<float>(M);
@@ -438,8 +444,11 @@ __global__ void __launch_bounds__(128)
       for (int j = 0; j < 16; ++j) {
         const int col = cb * 16 + j;
         d[j] = (mask2[cb >> 1] >> ((cb & 1) * 16 + j)) & 1u ? dz * vec[kVecW3 + col] : 0.f;
-        da2f[tid * kHid + col] = d[j];
       }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        *reinterpret_cast<float4*>(da2f + tid * kLd + cb * 16 + 4 * i) =
+            make_float4(d[4 * i], d[4 * i + 1], d[4 * i + 2], d[4 * i + 3]);
       store_bf16x8(smem + kTsDA2b + core_offset(tid, cb * 16, kHid), d);
       store_bf16x8(smem + kTsDA2b + core_offset(tid, cb * 16 + 8, kHid), d + 8);
     }
@@ -462,8 +471,8 @@ __global__ void __launch_bounds__(128)
         const float2 h01 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&hb.x));
         const float2 h23 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&hb.y));
         const float hv[4] = {h01.x, h01.y, h23.x, h23.y};
-        const float4 d0 = *reinterpret_cast<const float4*>(da2f + rr * kHid + j0);
-        const float4 d1 = *reinterpret_cast<const float4*>(da2f + rr * kHid + j0 + 4);
+        const float4 d0 = *reinterpret_cast<const float4*>(da2f + rr * kLd + j0);
+        const float4 d1 = *reinterpret_cast<const float4*>(da2f + rr * kLd + j0 + 4);
         const float dv[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
 #pragma unroll
         for (int i = 0; i < 4; ++i)
@@ -477,12 +486,12 @@ __global__ void __launch_bounds__(128)
     }
     if (tid < kHid) {
       float s = 0.f;
-      for (int rr = 0; rr < kTileM; ++rr) s += da2f[rr * kHid + tid];
+      for (int rr = 0; rr < kTileM; ++rr) s += da2f[rr * kLd + tid];
       out[kOffB2 + tid] = s;
     } else {
       const int j = tid - kHid;
       float s = 0.f;
-      for (int rr = 0; rr < kTileM; ++rr) s = fmaf(dzs[rr], f2[rr * kHid + j], s);
+      for (int rr = 0; rr < kTileM; ++rr) s = fmaf(dzs[rr], f2[rr * kLd + j], s);
       out[kOffW3 + j] = s;
     }
     if (warp == 0) {
@@ -514,7 +523,11 @@ __global__ void __launch_bounds__(128)
       tmem_ld16(tmem + lane_base + 128 + cb * 16, v);
 #pragma unroll
       for (int j = 0; j < 16; ++j)
-        f2[tid * kHid + cb * 16 + j] = (mask1[cb >> 1] >> ((cb & 1) * 16 + j)) & 1u ? v[j] : 0.f;
+        if (!((mask1[cb >> 1] >> ((cb & 1) * 16 + j)) & 1u)) v[j] = 0.f;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        *reinterpret_cast<float4*>(f2 + tid * kLd + cb * 16 + 4 * i) =
+            make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
     }
     __syncthreads();
     const int k = tid >> 3, j0 = 8 * (tid & 7);
@@ -524,8 +537,8 @@ __global__ void __launch_bounds__(128)
     for (int rr = 0; rr < kTileM; ++rr) {
       const float xv = __bfloat162float(
           *reinterpret_cast<const __nv_bfloat16*>(smem + kTsX + core_offset(rr, k, kIn)));
-      const float4 d0 = *reinterpret_cast<const float4*>(f2 + rr * kHid + j0);
-      const float4 d1 = *reinterpret_cast<const float4*>(f2 + rr * kHid + j0 + 4);
+      const float4 d0 = *reinterpret_cast<const float4*>(f2 + rr * kLd + j0);
+      const float4 d1 = *reinterpret_cast<const float4*>(f2 + rr * kLd + j0 + 4);
       acc[0] = fmaf(xv, d0.x, acc[0]);
       acc[1] = fmaf(xv, d0.y, acc[1]);
       acc[2] = fmaf(xv, d0.z, acc[2]);
@@ -539,7 +552,7 @@ __global__ void __launch_bounds__(128)
     for (int j = 0; j < 8; ++j) out[kOffW1 + k * kHid + j0 + j] = acc[j];
     if (tid < kHid) {
       float s = 0.f;
-      for (int rr = 0; rr < kTileM; ++rr) s += f2[rr * kHid + tid];
+      for (int rr = 0; rr < kTileM; ++rr) s += f2[rr * kLd + tid];
       out[kOffB1 + tid] = s;
     }
   }
