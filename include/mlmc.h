@@ -536,12 +536,14 @@ mlmc_status mlmc_learn_proposal(mlmc_plan *plan, mlmc_mlp *mlp, const double *v,
  * `rounds` (1..8) pilot-train-install rounds, each round after the first
  * drawing a pilot of 4 * pilot_walks walks per row (walk indices after the
  * earlier rounds' ones) with the proposal installed by the previous one.  With tilted clocks the MLP's
- * target is 0.5 (log(|x-hat| + 1e-3 max|x-hat|) + log(|v| + 1e-3 max|v|)):
- * the zero-variance h of a walk at scaled time s is exp((1-s)tA)v, from x at
- * the start to v at the end, and this is its geometric mean; and the first
- * pilot already walks with the tilt of h0 = sqrt(T_3 |v|), T_3 the
- * third-order Taylor value of exp(t|A|)|v| (the paper's walk would give
- * pilot estimates with the heavy tails the tilt removes).  The MLP's
+ * target is a log(|x-hat| + 1e-3 max|x-hat|) + (1 - a) log(|v| + 1e-3
+ * max|v|) (the zero-variance h of a walk at scaled time s is exp((1-s)tA)v,
+ * from x at the start to v at the end); the first pilots walk with the
+ * tilts of h0 = T_3^a |v|^(1-a) for a = 1/2, 3/4 and 1, T_3 the third-order
+ * Taylor value of exp(t|N|)|v| (N the off-diagonal part; the paper's walk
+ * would give pilot estimates with the heavy tails the tilt removes), and
+ * the form whose pilot measured the smallest variance gives the first
+ * round's targets and their exponent a.  The MLP's
  * training rows are weighted by degree (row i counted 1 + floor(deg_i /
  * mean degree) times, at most 4n rows): the few rows with many
  * off-diagonals set the laws of every row around them.  Every pilot
@@ -549,7 +551,8 @@ mlmc_status mlmc_learn_proposal(mlmc_plan *plan, mlmc_mlp *mlp, const double *v,
  * variances averaged over the rows), and one more pilot of 4 * pilot_walks
  * walks per row measures the last round's tilt; the law with the smallest
  * measured variance is the one installed (for MLMC_TILT_JUMPS the paper's
- * walk is a candidate too: then the plan is left with the plain walk).  The
+ * walk is a candidate too: then the plan is left with the plain walk; with
+ * tilted clocks the three warm starts are).  The
  * pilots draw from a stream keyed by a hash of `seed`, never the one
  * mlmc_expmv draws from with the same seed, so the installed law does not
  * depend on the walks that estimate x.  final_loss is the last round's.
@@ -558,12 +561,13 @@ mlmc_status mlmc_learn_tilt(mlmc_plan *plan, mlmc_mlp *mlp, const double *v, uin
                             int64_t pilot_walks, int32_t steps, int32_t batch, float lr,
                             double alpha, int32_t tilt, int32_t rounds, float *final_loss);
 
-/* What the plan's last mlmc_learn_tilt / mlmc_learn_proposal measured:
- * *count (may be NULL) = rounds + 1 pilot variances; var[k] (host, the
- * first min(cap, count)) = the per-walk variance at l0 of pilot k, which
- * walked with the law installed before round k (k = rounds: the final
- * tilt); *chosen (may be NULL) = the index of the law installed (-1 before
- * any learning). */
+/* What the plan's last mlmc_learn_tilt / mlmc_learn_proposal measured, in
+ * pilot order: *count (may be NULL) pilot variances; var[k] (host, the
+ * first min(cap, count)) = the per-walk variance at l0 of pilot k.  Jumps
+ * only: rounds + 1 pilots (the paper's walk, then the tilt trained in each
+ * round).  Tilted clocks: rounds + 3 (the warm starts a = 1/2, 3/4, 1, then
+ * the tilt trained in each round).  *chosen (may be NULL) = the index of the
+ * law installed (-1 before any learning). */
 mlmc_status mlmc_plan_learn_report(const mlmc_plan *plan, int32_t *chosen, double *var, int32_t cap,
                                    int32_t *count);
 

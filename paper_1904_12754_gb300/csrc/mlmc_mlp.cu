@@ -203,7 +203,8 @@ __global__ void __launch_bounds__(128)
 
 // ---------------------------------------------------------------------------
 // Fused training step: the forward and backward passes of one 128-row tile
-// of a batch in one CTA of 128 threads (thread r = row r = TMEM lane r).
+// of a batch in one CTA of 256 threads (row r = TMEM lane r, two threads a
+// row).
 //
 //   weights  one bulk copy (cp.async.bulk, completion on an mbarrier) of the
 //            operand image the Adam kernel writes after every update: W1^T,
@@ -228,6 +229,7 @@ constexpr int kImgVec = kImgW2 + kHid * kHid * 2;     // FP32 b1[64] b2[64] w3[6
 constexpr int kImgBytes = kImgVec + 256 * 4;          // 19456: a multiple of 16
 constexpr int kVecB1 = 0, kVecB2 = 64, kVecW3 = 128, kVecB3 = 192;
 constexpr int kPart = kParams + 1;                    // a tile's gradient, then its loss
+constexpr int kPartStride = (kPart + 3) & ~3;        // row stride: 16-byte aligned rows
 // Shared memory of the fused kernel (byte offsets; every part 128-byte aligned).
 constexpr int kTsImg = 0;
 constexpr int kTsX = kTsImg + kImgBytes;              // X tile, 128 x 16 BF16 (A of GEMM 1)
@@ -240,7 +242,8 @@ constexpr int kTsDA2 = kTsDA2b + kTileM * kHid * 2;   // dA2, 128 x 64 FP32
 constexpr int kTsF2 = kTsDA2 + kTileM * kLd * 4;      // H2, then dA1: 128 x 64 FP32
 constexpr int kTsDZ = kTsF2 + kTileM * kLd * 4;       // dz per row
 constexpr int kTsLoss = kTsDZ + kTileM * 4;           // loss term per row
-constexpr int kTsBar = kTsLoss + kTileM * 4;          // 4 mbarriers
+constexpr int kTsZ = kTsLoss + kTileM * 4;            // z's two partial sums per row
+constexpr int kTsBar = kTsZ + 2 * kTileM * 4;         // 4 mbarriers
 constexpr int kTsSlot = kTsBar + 4 * 8;               // TMEM address
 constexpr int kTrainSmem = kTsSlot + 16;
 constexpr int kTrainTmemCols = 256;                   // three 64-column accumulators
@@ -313,8 +316,12 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
 }
 
 // Rows: batch row b of the tile is x[b] (sample == 0) or x[mix64(seed + b)
-// mod n_src] (a uniform minibatch drawn on the device).
-__global__ void __launch_bounds__(128)
+// mod n_src] (a uniform minibatch drawn on the device).  256 threads: warp w
+// reads TMEM lanes 32 (w mod 4) .. + 31 (rows r = 32 (w mod 4) + lane) and
+// the accumulator columns of half w / 4 (32 of the 64), so two threads share
+// a row; the CUDA-core sums split the weight-gradient entries over all 256.
+constexpr int kTrainThreads = 256;
+__global__ void __launch_bounds__(kTrainThreads)
     k_mlp_train_tile(int64_t M, const __nv_bfloat16* __restrict__ x, const float* __restrict__ y,
                      int64_t n_src, uint64_t sample_seed, int sample,
                      const unsigned char* __restrict__ img, float* __restrict__ part,
@@ -322,7 +329,10 @@ __global__ void __launch_bounds__(128)
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
-  const int64_t b = static_cast<int64_t>(blockIdx.x) * kTileM + tid;
+  const int r = (warp & 3) * 32 + (tid & 31);  // this thread's row (TMEM lane)
+  const int half = warp >> 2;                  // its 32 accumulator columns
+  const int c0 = half * 32;
+  const int64_t b = static_cast<int64_t>(blockIdx.x) * kTileM + r;
   const bool valid = b < M;
   const uint32_t s0 = smem_u32(smem);
   const uint32_t bar = s0 + kTsBar;  // mbarriers: weights, GEMM 1, GEMM 2, GEMM 3
@@ -332,7 +342,8 @@ __global__ void __launch_bounds__(128)
   float* f2 = reinterpret_cast<float*>(smem + kTsF2);
   float* dzs = reinterpret_cast<float*>(smem + kTsDZ);
   float* lss = reinterpret_cast<float*>(smem + kTsLoss);
-  float* out = part + static_cast<int64_t>(blockIdx.x) * kPart;
+  float* zpart = reinterpret_cast<float*>(smem + kTsZ);
+  float* out = part + static_cast<int64_t>(blockIdx.x) * kPartStride;
 
   if (tid == 0) {
     for (int i = 0; i < 4; ++i)
@@ -356,33 +367,31 @@ __global__ void __launch_bounds__(128)
                  "r"(kTrainTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  // This thread's row of X (zeros past M) and its target.
+  // Row r of X (zeros past M): inputs 0-7 from one thread of the pair,
+  // 8-15 from the other; both keep the target.
   float yv = 0.f;
   {
-    uint4 lo = make_uint4(0u, 0u, 0u, 0u), hi = lo;
+    uint4 q = make_uint4(0u, 0u, 0u, 0u);
     if (valid) {
       int64_t src = b;
       if (sample) src = static_cast<int64_t>(mix64(sample_seed + static_cast<uint64_t>(b)) %
                                              static_cast<uint64_t>(n_src));
-      const uint4* xr = reinterpret_cast<const uint4*>(x + src * kIn);
-      lo = xr[0];
-      hi = xr[1];
+      q = reinterpret_cast<const uint4*>(x + src * kIn)[half];
       yv = y[src];
     }
-    *reinterpret_cast<uint4*>(smem + kTsX + core_offset(tid, 0, kIn)) = lo;
-    *reinterpret_cast<uint4*>(smem + kTsX + core_offset(tid, 8, kIn)) = hi;
+    *reinterpret_cast<uint4*>(smem + kTsX + core_offset(r, 8 * half, kIn)) = q;
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tslot;
-  const uint32_t lane_base = static_cast<uint32_t>(warp * 32) << 16;
+  const uint32_t lane_base = static_cast<uint32_t>((warp & 3) * 32) << 16;
   bool ok = __syncthreads_and(mbar_wait(bar, 0));
 
-  // GEMM 1 and its epilogue: H1 = relu(A1), the sign mask of A1 kept in
-  // two registers.
-  uint32_t mask1[2] = {0u, 0u};
+  // GEMM 1 and its epilogue: H1 = relu(A1) on this thread's 32 columns, the
+  // sign mask of A1 kept in a register.
+  uint32_t mask1 = 0u;
   if (ok) {
     if (tid == 0) issue_gemm<kIn>(tmem, s0 + kTsX, s0 + kTsImg + kImgW1, bar + 8);
     ok = __syncthreads_and(mbar_wait(bar + 8, 0));
@@ -390,17 +399,18 @@ __global__ void __launch_bounds__(128)
   if (ok) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-    for (int cb = 0; cb < kHid / 16; ++cb) {
+    for (int cb = 0; cb < 2; ++cb) {
       float v[16];
-      tmem_ld16(tmem + lane_base + cb * 16, v);
+      const int col0 = c0 + cb * 16;
+      tmem_ld16(tmem + lane_base + col0, v);
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
-        const float a = v[j] + vec[kVecB1 + cb * 16 + j];
-        if (a > 0.f) mask1[cb >> 1] |= 1u << ((cb & 1) * 16 + j);
+        const float a = v[j] + vec[kVecB1 + col0 + j];
+        if (a > 0.f) mask1 |= 1u << (cb * 16 + j);
         v[j] = fmaxf(a, 0.f);
       }
-      store_bf16x8(smem + kTsH1 + core_offset(tid, cb * 16, kHid), v);
-      store_bf16x8(smem + kTsH1 + core_offset(tid, cb * 16 + 8, kHid), v + 8);
+      store_bf16x8(smem + kTsH1 + core_offset(r, col0, kHid), v);
+      store_bf16x8(smem + kTsH1 + core_offset(r, col0 + 8, kHid), v + 8);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -409,94 +419,96 @@ __global__ void __launch_bounds__(128)
     if (tid == 0) issue_gemm<kHid>(tmem + 64, s0 + kTsH1, s0 + kTsImg + kImgW2t, bar + 16);
     ok = __syncthreads_and(mbar_wait(bar + 16, 0));
   }
-  // GEMM 2's epilogue and the head: H2, z, dz, dA2 (FP32 and BF16).
+  // GEMM 2's epilogue and the head: H2, z (the two halves' partial sums
+  // meet in shared memory), dz, dA2 (FP32 and BF16).
   if (ok) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    uint32_t mask2[2] = {0u, 0u};
-    float z = 0.f;
+    uint32_t mask2 = 0u;
+    float zh = 0.f;
 #pragma unroll
-    for (int cb = 0; cb < kHid / 16; ++cb) {
+    for (int cb = 0; cb < 2; ++cb) {
       float v[16];
-      tmem_ld16(tmem + lane_base + 64 + cb * 16, v);
+      const int col0 = c0 + cb * 16;
+      tmem_ld16(tmem + lane_base + 64 + col0, v);
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
-        const int col = cb * 16 + j;
-        const float a = v[j] + vec[kVecB2 + col];
-        if (a > 0.f) mask2[cb >> 1] |= 1u << ((cb & 1) * 16 + j);
+        const float a = v[j] + vec[kVecB2 + col0 + j];
+        if (a > 0.f) mask2 |= 1u << (cb * 16 + j);
         v[j] = fmaxf(a, 0.f);
-        z += v[j] * vec[kVecW3 + col];
+        zh += v[j] * vec[kVecW3 + col0 + j];
       }
 #pragma unroll
       for (int i = 0; i < 4; ++i)
-        *reinterpret_cast<float4*>(f2 + tid * kLd + cb * 16 + 4 * i) =
+        *reinterpret_cast<float4*>(f2 + r * kLd + col0 + 4 * i) =
             make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
     }
-    z += vec[kVecB3];
+    zpart[half * kTileM + r] = zh;
+    __syncthreads();
+    const float z = (zpart[r] + zpart[kTileM + r]) + vec[kVecB3];
     const float inv_b = 1.0f / static_cast<float>(M);
-    const float r = z - yv;
-    const float dz = valid ? 2.0f * r * inv_b : 0.f;
-    dzs[tid] = dz;
-    lss[tid] = valid ? r * r * inv_b : 0.f;
+    const float res = z - yv;
+    const float dz = valid ? 2.0f * res * inv_b : 0.f;
+    if (half == 0) {
+      dzs[r] = dz;
+      lss[r] = valid ? res * res * inv_b : 0.f;
+    }
 #pragma unroll
-    for (int cb = 0; cb < kHid / 16; ++cb) {
+    for (int cb = 0; cb < 2; ++cb) {
       float d[16];
+      const int col0 = c0 + cb * 16;
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int col = cb * 16 + j;
-        d[j] = (mask2[cb >> 1] >> ((cb & 1) * 16 + j)) & 1u ? dz * vec[kVecW3 + col] : 0.f;
-      }
+      for (int j = 0; j < 16; ++j)
+        d[j] = (mask2 >> (cb * 16 + j)) & 1u ? dz * vec[kVecW3 + col0 + j] : 0.f;
 #pragma unroll
       for (int i = 0; i < 4; ++i)
-        *reinterpret_cast<float4*>(da2f + tid * kLd + cb * 16 + 4 * i) =
+        *reinterpret_cast<float4*>(da2f + r * kLd + col0 + 4 * i) =
             make_float4(d[4 * i], d[4 * i + 1], d[4 * i + 2], d[4 * i + 3]);
-      store_bf16x8(smem + kTsDA2b + core_offset(tid, cb * 16, kHid), d);
-      store_bf16x8(smem + kTsDA2b + core_offset(tid, cb * 16 + 8, kHid), d + 8);
+      store_bf16x8(smem + kTsDA2b + core_offset(r, col0, kHid), d);
+      store_bf16x8(smem + kTsDA2b + core_offset(r, col0 + 8, kHid), d + 8);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // GEMM 3 runs while the CUDA cores sum dW2 = H1^T dA2 (a 4 x 8 block of
+    // GEMM 3 runs while the CUDA cores sum dW2 = H1^T dA2 (a 4 x 4 block of
     // it per thread), db2, dw3 and db3.
     if (tid == 0) issue_gemm<kHid>(tmem + 128, s0 + kTsDA2b, s0 + kTsImg + kImgW2, bar + 24);
     {
-      const int k0 = 4 * (tid >> 3), j0 = 8 * (tid & 7);
-      float acc[4][8];
+      const int k0 = 4 * (tid >> 4), j0 = 4 * (tid & 15);
+      float acc[4][4];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
       for (int rr = 0; rr < kTileM; ++rr) {
         const uint2 hb = *reinterpret_cast<const uint2*>(smem + kTsH1 + core_offset(rr, k0, kHid));
         const float2 h01 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&hb.x));
         const float2 h23 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&hb.y));
         const float hv[4] = {h01.x, h01.y, h23.x, h23.y};
-        const float4 d0 = *reinterpret_cast<const float4*>(da2f + rr * kLd + j0);
-        const float4 d1 = *reinterpret_cast<const float4*>(da2f + rr * kLd + j0 + 4);
-        const float dv[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
+        const float4 d4 = *reinterpret_cast<const float4*>(da2f + rr * kLd + j0);
+        const float dv[4] = {d4.x, d4.y, d4.z, d4.w};
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
-          for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(hv[i], dv[j], acc[i][j]);
+          for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(hv[i], dv[j], acc[i][j]);
       }
 #pragma unroll
       for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) out[kOffW2 + (k0 + i) * kHid + j0 + j] = acc[i][j];
+        *reinterpret_cast<float4*>(out + kOffW2 + (k0 + i) * kHid + j0) =
+            make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
     }
     if (tid < kHid) {
       float s = 0.f;
       for (int rr = 0; rr < kTileM; ++rr) s += da2f[rr * kLd + tid];
       out[kOffB2 + tid] = s;
-    } else {
+    } else if (tid < 2 * kHid) {
       const int j = tid - kHid;
       float s = 0.f;
       for (int rr = 0; rr < kTileM; ++rr) s = fmaf(dzs[rr], f2[rr * kLd + j], s);
       out[kOffW3 + j] = s;
-    }
-    if (warp == 0) {
+    } else if (warp == 4) {
       float sd = 0.f, sl = 0.f;
-      for (int rr = tid; rr < kTileM; rr += 32) {
+      for (int rr = tid & 31; rr < kTileM; rr += 32) {
         sd += dzs[rr];
         sl += lss[rr];
       }
@@ -505,7 +517,7 @@ __global__ void __launch_bounds__(128)
         sd += __shfl_xor_sync(0xFFFFFFFFu, sd, o);
         sl += __shfl_xor_sync(0xFFFFFFFFu, sl, o);
       }
-      if (tid == 0) {
+      if ((tid & 31) == 0) {
         out[kOffB3] = sd;
         out[kParams] = sl;
       }
@@ -513,43 +525,37 @@ __global__ void __launch_bounds__(128)
     // every thread is done with H2 (f2) before dA1 overwrites it
     ok = __syncthreads_and(mbar_wait(bar + 24, 0));
   }
-  // GEMM 3's epilogue: dA1 = dH1 [A1 > 0] into f2; then dW1 = X^T dA1 (a
-  // row of 8 per thread) and db1.
+  // GEMM 3's epilogue: dA1 = dH1 [A1 > 0] into f2; then dW1 = X^T dA1 (four
+  // entries per thread) and db1.
   if (ok) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-    for (int cb = 0; cb < kHid / 16; ++cb) {
+    for (int cb = 0; cb < 2; ++cb) {
       float v[16];
-      tmem_ld16(tmem + lane_base + 128 + cb * 16, v);
+      const int col0 = c0 + cb * 16;
+      tmem_ld16(tmem + lane_base + 128 + col0, v);
 #pragma unroll
       for (int j = 0; j < 16; ++j)
-        if (!((mask1[cb >> 1] >> ((cb & 1) * 16 + j)) & 1u)) v[j] = 0.f;
+        if (!((mask1 >> (cb * 16 + j)) & 1u)) v[j] = 0.f;
 #pragma unroll
       for (int i = 0; i < 4; ++i)
-        *reinterpret_cast<float4*>(f2 + tid * kLd + cb * 16 + 4 * i) =
+        *reinterpret_cast<float4*>(f2 + r * kLd + col0 + 4 * i) =
             make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
     }
     __syncthreads();
-    const int k = tid >> 3, j0 = 8 * (tid & 7);
-    float acc[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) acc[j] = 0.f;
+    const int k = tid >> 4, j0 = 4 * (tid & 15);
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
     for (int rr = 0; rr < kTileM; ++rr) {
       const float xv = __bfloat162float(
           *reinterpret_cast<const __nv_bfloat16*>(smem + kTsX + core_offset(rr, k, kIn)));
-      const float4 d0 = *reinterpret_cast<const float4*>(f2 + rr * kLd + j0);
-      const float4 d1 = *reinterpret_cast<const float4*>(f2 + rr * kLd + j0 + 4);
-      acc[0] = fmaf(xv, d0.x, acc[0]);
-      acc[1] = fmaf(xv, d0.y, acc[1]);
-      acc[2] = fmaf(xv, d0.z, acc[2]);
-      acc[3] = fmaf(xv, d0.w, acc[3]);
-      acc[4] = fmaf(xv, d1.x, acc[4]);
-      acc[5] = fmaf(xv, d1.y, acc[5]);
-      acc[6] = fmaf(xv, d1.z, acc[6]);
-      acc[7] = fmaf(xv, d1.w, acc[7]);
+      const float4 d4 = *reinterpret_cast<const float4*>(f2 + rr * kLd + j0);
+      acc[0] = fmaf(xv, d4.x, acc[0]);
+      acc[1] = fmaf(xv, d4.y, acc[1]);
+      acc[2] = fmaf(xv, d4.z, acc[2]);
+      acc[3] = fmaf(xv, d4.w, acc[3]);
     }
-#pragma unroll
-    for (int j = 0; j < 8; ++j) out[kOffW1 + k * kHid + j0 + j] = acc[j];
+    *reinterpret_cast<float4*>(out + kOffW1 + k * kHid + j0) =
+        make_float4(acc[0], acc[1], acc[2], acc[3]);
     if (tid < kHid) {
       float s = 0.f;
       for (int rr = 0; rr < kTileM; ++rr) s += f2[rr * kLd + tid];
@@ -559,7 +565,7 @@ __global__ void __launch_bounds__(128)
   if (!ok) {
     // a completion wait gave up: the tile contributes nothing
     if (tid == 0) atomicOr(err, 1u);
-    for (int e = tid; e < kPart; e += kTileM) out[e] = 0.f;
+    for (int e = tid; e < kPart; e += kTrainThreads) out[e] = 0.f;
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -597,26 +603,36 @@ __global__ void k_mlp_image(const float* __restrict__ p, unsigned char* __restri
 
 // Sum the tiles' rows of `part`: the gradient (into grad, if given) and the
 // loss (into *loss).  With m1 != nullptr also one Adam step on the FP32
-// master parameters, whose new values go to the operand image.
-__global__ void k_mlp_adam_tiles(float* __restrict__ p, const float* __restrict__ part, int tiles,
-                                 float* __restrict__ grad, float* __restrict__ loss,
-                                 float* __restrict__ m1, float* __restrict__ m2, float lr, float b1,
-                                 float b2, float eps, float c1, float c2,
-                                 unsigned char* __restrict__ img) {
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < kPart; e += gridDim.x * blockDim.x) {
-    float g = 0.f;
-    for (int t = 0; t < tiles; ++t) g += part[static_cast<int64_t>(t) * kPart + e];
-    if (e == kParams) {
-      if (loss) *loss = g;
-      continue;
-    }
-    if (grad) grad[e] = g;
-    if (m1) {
-      m1[e] = b1 * m1[e] + (1.f - b1) * g;
-      m2[e] = b2 * m2[e] + (1.f - b2) * g * g;
-      p[e] -= lr * (m1[e] / c1) / (sqrtf(m2[e] / c2) + eps);
-      image_store(img, e, p[e]);
-    }
+// master parameters, whose new values go to the operand image.  A block of
+// 32 x 8 threads takes 32 consecutive entries: thread (x, y) sums tiles
+// y, y + 8, ..., and the column sums meet in shared memory.
+constexpr int kAdamCols = 32, kAdamRows = 8;
+__global__ void __launch_bounds__(kAdamCols * kAdamRows)
+    k_mlp_adam_tiles(float* __restrict__ p, const float* __restrict__ part, int tiles,
+                     float* __restrict__ grad, float* __restrict__ loss, float* __restrict__ m1,
+                     float* __restrict__ m2, float lr, float b1, float b2, float eps, float c1,
+                     float c2, unsigned char* __restrict__ img) {
+  __shared__ float red[kAdamRows][kAdamCols];
+  const int tx = threadIdx.x % kAdamCols, ty = threadIdx.x / kAdamCols;
+  const int e = blockIdx.x * kAdamCols + tx;
+  float g = 0.f;
+  if (e < kPart)
+    for (int t = ty; t < tiles; t += kAdamRows) g += part[static_cast<int64_t>(t) * kPartStride + e];
+  red[ty][tx] = g;
+  __syncthreads();
+  if (ty != 0 || e >= kPart) return;
+#pragma unroll
+  for (int r = 1; r < kAdamRows; ++r) g += red[r][tx];
+  if (e == kParams) {
+    if (loss) *loss = g;
+    return;
+  }
+  if (grad) grad[e] = g;
+  if (m1) {
+    m1[e] = b1 * m1[e] + (1.f - b1) * g;
+    m2[e] = b2 * m2[e] + (1.f - b2) * g * g;
+    p[e] -= lr * (m1[e] / c1) / (sqrtf(m2[e] / c2) + eps);
+    image_store(img, e, p[e]);
   }
 }
 
@@ -702,12 +718,13 @@ __global__ void k_abs_float32(int64_t n, const double* __restrict__ in, float* _
   }
 }
 
-// h_i = sqrt((a_i + fa) (|b_i| + fb)) in FP32.
-__global__ void k_sqrt_product(int64_t n, const float* __restrict__ a, const double* __restrict__ b,
-                               float fa, float fb, float* __restrict__ h) {
+// h_i = (a_i + fa)^alpha (|b_i| + fb)^(1 - alpha) in FP32.
+__global__ void k_power_product(int64_t n, const float* __restrict__ a, const double* __restrict__ b,
+                                float fa, float fb, float alpha, float* __restrict__ h) {
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x)
-    h[i] = sqrtf((a[i] + fa) * (fabsf(static_cast<float>(b[i])) + fb));
+    h[i] = expf(alpha * logf(a[i] + fa) +
+                (1.0f - alpha) * logf(fabsf(static_cast<float>(b[i])) + fb));
 }
 
 __global__ void k_to_float32(int64_t n, const double* __restrict__ in, float* __restrict__ out) {
@@ -767,15 +784,18 @@ __global__ void k_mlp_features(int64_t n, const int64_t* __restrict__ row_ptr,
   }
 }
 
-// log(|x| + eps) targets and, for the proposal, h = exp(z) clamped.
-// y_i = log(|x-hat_i| + floor_x), or, with v, the mean of that and
-// log(|v_i| + floor_v).
+// log targets and, for the proposal, h = exp(z) clamped.
+// y_i = alpha log(|x-hat_i| + floor_x) + (1 - alpha) log(|v_i| + floor_v)
+// (v may be null when alpha = 1).
 __global__ void k_log_target(int64_t n, const double* __restrict__ xhat, float floor_abs,
-                             const double* __restrict__ v, float floor_v, float* __restrict__ y) {
+                             const double* __restrict__ v, float floor_v, float alpha,
+                             float* __restrict__ y) {
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const float lx = logf(fabsf(static_cast<float>(xhat[i])) + floor_abs);
-    y[i] = v ? 0.5f * (lx + logf(fabsf(static_cast<float>(v[i])) + floor_v)) : lx;
+    y[i] = v && alpha < 1.0f
+               ? alpha * lx + (1.0f - alpha) * logf(fabsf(static_cast<float>(v[i])) + floor_v)
+               : lx;
   }
 }
 
@@ -859,7 +879,7 @@ mlmc_status ensure_tiles(mlmc_mlp* m, int64_t tiles) {
   cudaFree(m->d_part);
   m->d_part = nullptr;
   m->part_tiles = 0;
-  MLP_CUDA(cudaMalloc(&m->d_part, sizeof(float) * static_cast<size_t>(tiles) * kPart), "alloc");
+  MLP_CUDA(cudaMalloc(&m->d_part, sizeof(float) * static_cast<size_t>(tiles) * kPartStride), "alloc");
   m->part_tiles = tiles;
   return MLMC_OK;
 }
@@ -913,7 +933,7 @@ mlmc_status train_tiles(mlmc_mlp* m, const __nv_bfloat16* x, const float* y, int
   const int64_t tiles = (M + kTileM - 1) / kTileM;
   mlmc_status st = ensure_tiles(m, tiles);
   if (st != MLMC_OK) return st;
-  k_mlp_train_tile<<<static_cast<unsigned>(tiles), kTileM, kTrainSmem, m->stream>>>(
+  k_mlp_train_tile<<<static_cast<unsigned>(tiles), kTrainThreads, kTrainSmem, m->stream>>>(
       M, x, y, n_src, sample_seed, sample ? 1 : 0, m->d_img, m->d_part, m->d_err);
   MLP_CUDA(cudaGetLastError(), "train tile");
   m->launches++;
@@ -1031,7 +1051,7 @@ mlmc_status mlmc_mlp_loss_grad(mlmc_mlp* m, const uint16_t* x, const float* y, i
   if (st == MLMC_OK)
     st = train_tiles(m, reinterpret_cast<const __nv_bfloat16*>(x), y, n, n, false, 0, &tiles);
   if (st != MLMC_OK) return st;
-  k_mlp_adam_tiles<<<(kPart + 255) / 256, 256, 0, m->stream>>>(
+  k_mlp_adam_tiles<<<(kPart + kAdamCols - 1) / kAdamCols, kAdamCols * kAdamRows, 0, m->stream>>>(
       m->d_p, m->d_part, static_cast<int>(tiles), m->d_g, m->d_loss, nullptr, nullptr, 0.f, 0.f,
       0.f, 0.f, 1.f, 1.f, nullptr);
   MLP_CUDA(cudaGetLastError(), "reduce");
@@ -1060,7 +1080,7 @@ mlmc_status mlmc_mlp_train(mlmc_mlp* m, const uint16_t* x, const float* y, int64
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.f - std::pow(b1, static_cast<float>(m->adam_t));
     const float c2 = 1.f - std::pow(b2, static_cast<float>(m->adam_t));
-    k_mlp_adam_tiles<<<(kPart + 255) / 256, 256, 0, m->stream>>>(
+    k_mlp_adam_tiles<<<(kPart + kAdamCols - 1) / kAdamCols, kAdamCols * kAdamRows, 0, m->stream>>>(
         m->d_p, m->d_part, static_cast<int>(tiles), nullptr, m->d_loss, m->d_m1, m->d_m2, lr, b1,
         b2, 1e-8f, c1, c2, m->d_img);
     m->launches++;
@@ -1121,11 +1141,13 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
   float* h = nullptr;
   float* pv = nullptr;  // v, k^m v (m = 1..4), T_3 and two Taylor terms (8 x n floats)
   float* best_h = nullptr;        // the tilt with the smallest pilot variance so far
+  double* xwarm = nullptr;        // x-hat of the best warm start's pilot
   int64_t* widx = nullptr;        // training rows, weighted by degree (see below)
   __nv_bfloat16* wfeat = nullptr;
   float* wy = nullptr;
   auto cleanup = [&]() {
     cudaFree(best_h);
+    cudaFree(xwarm);
     cudaFree(widx);
     cudaFree(wfeat);
     cudaFree(wy);
@@ -1156,6 +1178,7 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
   LP_CUDA(cudaMalloc(&h, sizeof(float) * p->n), "alloc");
   LP_CUDA(cudaMalloc(&pv, sizeof(float) * p->n * 8), "alloc");
   LP_CUDA(cudaMalloc(&best_h, sizeof(float) * p->n), "alloc");
+  LP_CUDA(cudaMalloc(&xwarm, sizeof(double) * p->n), "alloc");
   LP_CUDA(cudaMemcpyAsync(dv, v, sizeof(double) * p->n, cudaMemcpyDefault, p->stream), "copy v");
   const unsigned g = static_cast<unsigned>(std::min<int64_t>((p->n + 255) / 256, p->num_sms * 8));
   // Features (fixed over the rounds: they use the paper's jump law).
@@ -1191,25 +1214,6 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
     for (double q : hv) vmax = std::max(vmax, std::fabs(q));
   }
   mlmc_status st = MLMC_OK;
-  if (clocks) {
-    // Warm start: the first pilot walks with the tilt of h0 = sqrt((T_3 +
-    // f) (|v| + f_v)), the third-order Taylor value of exp(t|A|)|v| (a
-    // feature above) in place of x: the paper's walk gives pilot estimates
-    // with the heavy tails the tilt exists to remove (long stays at rows of
-    // large t d_ii), and a network fitted to them would misjudge exactly
-    // those rows.
-    k_sqrt_product<<<g, 256, 0, p->stream>>>(p->n, pv + 5 * p->n, dv, static_cast<float>(1e-6),
-                                             static_cast<float>(1e-3 * vmax + 1e-30), h);
-    p->launches++;
-    LP_CUDA(cudaGetLastError(), "warm start");
-    st = mlmc_plan_set_tilt(p, h, alpha, tilt);
-    if (st != MLMC_OK) {
-      cleanup();
-      p->proposal_active = was;
-      p->clock_tilt = was_clocks;
-      return st;
-    }
-  }
   // Training rows weighted by degree: row i appears 1 + floor(deg_i / mean
   // deg) times (at most 4n rows in all).  Rows with many off-diagonals are
   // few, but their h sets the clocks and jump laws of every row around them,
@@ -1271,35 +1275,78 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
     return cudaMemcpyAsync(sums, hsum.data(), sizeof(double) * p->n, cudaMemcpyHostToDevice,
                            p->stream);
   };
-  // Every pilot measures the law it walks with; the tilt with the smallest
-  // measured variance is the one installed at the end (the warm start, or
-  // for jumps only the paper's walk, h = 1, are candidates too).
+  // Every pilot measures the law it walks with; the law with the smallest
+  // measured variance is the one installed at the end (for jumps only the
+  // paper's walk, h = 1, is a candidate too).
   double best_var = std::numeric_limits<double>::infinity();
   p->learn_var.clear();
   p->learn_choice = -1;
   int64_t next_rep = 0;
-  for (int32_t round = 0; round < rounds; ++round) {
-    // Later rounds walk with the previous tilt, whose samples are cheap and
-    // much less noisy: four times the first round's walks per row.
-    const int64_t round_walks = round == 0 ? pilot_walks : 4 * pilot_walks;
-    double xmax = 0.0, var = 0.0;
-    LP_CUDA(pilot(next_rep, round_walks, &xmax, &var), "pilot walks");
-    next_rep += round_walks;
+  auto consider = [&](double var, bool keep_h) -> cudaError_t {
     p->learn_var.push_back(var);
-    if (var < best_var) {
-      best_var = var;
-      p->learn_choice = round;
-      // (round 0 without clocks walks the paper's law: nothing to keep)
-      if (round > 0 || clocks)
-        LP_CUDA(cudaMemcpyAsync(best_h, h, sizeof(float) * p->n, cudaMemcpyDeviceToDevice,
-                                p->stream), "keep tilt");
+    if (!(var < best_var)) return cudaSuccess;
+    best_var = var;
+    p->learn_choice = static_cast<int32_t>(p->learn_var.size()) - 1;
+    return keep_h ? cudaMemcpyAsync(best_h, h, sizeof(float) * p->n, cudaMemcpyDeviceToDevice,
+                                    p->stream)
+                  : cudaSuccess;
+  };
+  // The exponent of x-hat in the training targets (jumps only: 1).
+  float target_alpha = 1.0f;
+  double xmax_warm = 0.0;
+  if (clocks) {
+    // Warm starts: the first pilots walk with the tilts of
+    //   h0 = (T_3 + f)^a (|v| + f_v)^(1 - a),  a = 1/2, 3/4, 1,
+    // T_3 the third-order Taylor value of exp(t|N|)|v| (a feature above) in
+    // place of x: the paper's walk gives pilot estimates with the heavy
+    // tails the tilt exists to remove (long stays at rows of large t d_ii),
+    // and a network fitted to them would misjudge exactly those rows.  The
+    // exponent sets how far the clocks follow x: on the scale-free graphs
+    // a = 3/4 measured 7-14x below a = 1/2.  The best form's pilot gives the
+    // first round's targets, with its exponent.
+    const float forms[3] = {0.5f, 0.75f, 1.0f};
+    for (int k = 0; k < 3; ++k) {
+      k_power_product<<<g, 256, 0, p->stream>>>(p->n, pv + 5 * p->n, dv, static_cast<float>(1e-6),
+                                                static_cast<float>(1e-3 * vmax + 1e-30), forms[k], h);
+      p->launches++;
+      LP_CUDA(cudaGetLastError(), "warm start");
+      st = mlmc_plan_set_tilt(p, h, alpha, tilt);
+      if (st != MLMC_OK) break;
+      double xmax = 0.0, var = 0.0;
+      LP_CUDA(pilot(next_rep, pilot_walks, &xmax, &var), "warm pilot");
+      next_rep += pilot_walks;
+      const bool better = var < best_var;
+      LP_CUDA(consider(var, true), "keep tilt");
+      if (better) {
+        target_alpha = forms[k];
+        xmax_warm = xmax;
+        LP_CUDA(cudaMemcpyAsync(xwarm, sums, sizeof(double) * p->n, cudaMemcpyDeviceToDevice,
+                                p->stream), "keep x-hat");
+      }
     }
-    // Targets log(|x-hat| + 1e-3 max|x-hat|) (rows the pilot never reached
-    // do not get arbitrarily small h), averaged with log(|v| + 1e-3 max|v|)
-    // for tilted clocks.
+  }
+  for (int32_t round = 0; round < rounds && st == MLMC_OK; ++round) {
+    double xmax = 0.0;
+    if (round == 0 && clocks) {
+      // the best warm start's pilot
+      LP_CUDA(cudaMemcpyAsync(sums, xwarm, sizeof(double) * p->n, cudaMemcpyDeviceToDevice,
+                              p->stream), "x-hat");
+      xmax = xmax_warm;
+    } else {
+      // Later rounds walk with the previous tilt, whose samples are cheap
+      // and much less noisy: four times the first round's walks per row.
+      const int64_t round_walks = round == 0 ? pilot_walks : 4 * pilot_walks;
+      double var = 0.0;
+      LP_CUDA(pilot(next_rep, round_walks, &xmax, &var), "pilot walks");
+      next_rep += round_walks;
+      // (round 0 without clocks walks the paper's law: nothing to keep)
+      LP_CUDA(consider(var, round > 0), "keep tilt");
+    }
+    // Targets a log(|x-hat| + 1e-3 max|x-hat|) + (1 - a) log(|v| + 1e-3
+    // max|v|) (rows the pilot never reached do not get arbitrarily small h).
     k_log_target<<<g, 256, 0, p->stream>>>(p->n, sums, static_cast<float>(1e-3 * xmax + 1e-30),
                                            clocks ? dv : nullptr,
-                                           static_cast<float>(1e-3 * vmax + 1e-30), y);
+                                           static_cast<float>(1e-3 * vmax + 1e-30), target_alpha, y);
     p->launches++;
     LP_CUDA(cudaGetLastError(), "targets");
     LP_CUDA(cudaStreamSynchronize(p->stream), "sync");
@@ -1317,17 +1364,15 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
     p->launches++;
     LP_CUDA(cudaGetLastError(), "h");
     st = mlmc_plan_set_tilt(p, h, alpha, tilt);
-    if (st != MLMC_OK) break;
   }
   if (st == MLMC_OK) {
     // The last round's tilt is measured like the others; if an earlier law
     // had the smaller variance, that one is installed instead.
     double xmax = 0.0, var = 0.0;
     LP_CUDA(pilot(next_rep, 4 * pilot_walks, &xmax, &var), "final pilot");
-    p->learn_var.push_back(var);
-    if (var < best_var)
-      p->learn_choice = rounds;
-    else
+    const int32_t last = static_cast<int32_t>(p->learn_var.size());
+    LP_CUDA(consider(var, false), "final");
+    if (p->learn_choice != last)
       st = mlmc_plan_set_tilt(p, p->learn_choice == 0 && !clocks ? nullptr : best_h, alpha, tilt);
   }
   cleanup();

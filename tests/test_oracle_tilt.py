@@ -17,7 +17,11 @@ What is pinned here, against things other than the code under test:
     the exact solution the total relative variance stays near 0.13 while the
     paper's walk's grows with the hubs (0.53 at n = 500, 2.7 at n = 2000);
     with h = sqrt(x v), the geometric mean of the start value x and the end
-    value v of the zero-variance h(s) = exp((1-s)tA)v, it is below 0.01.
+    value v of the zero-variance h(s) = exp((1-s)tA)v, it is below 0.01 at
+    level 0 (one Strang step);
+  - beyond level 0 the exponent moves: from level 3 on, h = x^(3/4) v^(1/4)
+    gives the smallest exact variance of the three forms x^a v^(1-a),
+    a = 1/2, 3/4, 1 (0.068 against 0.094 and 0.130 at n = 500, level 7).
 """
 import numpy as np
 import pytest
@@ -212,3 +216,24 @@ def test_clock_tilt_removes_the_hub_variance(n, plain_min):
     assert both < plain / 4 and both < jumps / 2
     lam_g, q_g = R.tilt_law(ad, np.sqrt(x * v), 0.1, t)
     assert relvar(lam_g, q_g) < 0.01
+
+
+def test_three_quarter_power_tilt_is_best_beyond_level_0():
+    # the same graph family: exact relative variance of the tilted walk with
+    # h = x^a v^(1-a) at level 0 and at the levels the solver uses
+    b = I.ba_graph(500, 4, seed=5)
+    ad = b.dense()
+    t = 1.0 / I.lambda_max(b)
+    v = np.ones(b.n)
+    x = sla.expm(t * ad) @ v
+
+    def relvar(a, level):
+        lam, q = R.tilt_law(ad, x ** a * v ** (1 - a), 0.1, t)
+        m1, m2 = R.level_moments(ad, t, v, level, False, lam=lam, q=q)
+        return (m2 - m1 * m1).sum() / (m1 * m1).sum()
+
+    at0 = [relvar(a, 0) for a in (0.5, 0.75, 1.0)]
+    assert at0[0] == min(at0)                       # level 0: the square root
+    for level in (3, 7):
+        r = [relvar(a, level) for a in (0.5, 0.75, 1.0)]
+        assert r[1] < 0.8 * r[0] and r[1] < 0.6 * r[2], (level, r)
