@@ -365,7 +365,8 @@ def run_ours(args):
     e2e_value = e2e_events / t_e2e_all
 
     peaks, peak_kind = _peaks()
-    roof = walk_roofline(level_log, walk_s, clocks, peaks, total_ms, proposal=True)
+    roof = walk_roofline(level_log, walk_s, clocks, peaks, total_ms, proposal=True,
+                         capture=w.name.startswith("ba_n100000_m4"))
 
     # The plain walk on the same plan and budget: its error estimate after
     # the budget, and the time 1e-3 would take at its measured variance
@@ -469,15 +470,23 @@ OPS_END_STILL = 1
 # A proposal walk's jump also loads the entry's log-ratios and adds one to
 # the exponent (the row record comes from the record table, not the entry).
 OPS_JUMP_PROPOSAL = 2
-# From one ncu capture of the walk kernel on this workload (a 4.1e8-walk
-# launch at l0 after an L2 flush): DRAM bytes per launch (the fused tables are
-# read once, everything else hits L2), issue-slot use and instructions per
-# event.  None when the kernel has changed since the capture.
-TRAFFIC_CAPTURE = None
-ISSUE_CAPTURE = None
+# From one ncu capture (--set full, one launch) of the proposal walk kernel
+# on this workload: a launch of 4.1e8 walks at l0 (4096 per row, 5.22e8
+# events) after an L2 flush, with the learned tilted clocks.  DRAM bytes per
+# launch (the proposal tables are read once, everything else hits L2: 98.3%),
+# issue-slot use and instructions per event.  Set to None when the kernel
+# changes.
+TRAFFIC_CAPTURE = 28.834e6
+ISSUE_CAPTURE = {"issue_active": 0.761, "threads_per_instruction": 26.78,
+                 "warp_instructions_per_event": 3.10, "l2_hit": 0.983,
+                 "dram_bytes_per_event": 0.055, "launch_ms": 1.755,
+                 "capture": "k_walk<FP32, proposal> at l0, BA n=1e5, 4096 walks per row, "
+                            "bench.py --workload kernel --kernel-tilt"}
 
 
-def walk_roofline(level_log, walk_s, clocks, peaks, total_ms, num_sms=None, proposal=False):
+def walk_roofline(level_log, walk_s, clocks, peaks, total_ms, num_sms=None, proposal=False,
+                  capture=False):
+    """capture: the capture constants above describe this kernel and workload."""
     ops = 0.0
     events = 0
     launches = 0
@@ -506,11 +515,13 @@ def walk_roofline(level_log, walk_s, clocks, peaks, total_ms, num_sms=None, prop
     gather_gbs = gather / walk_s / 1e9 if walk_s > 0 else 0.0
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s",
             "frac": achieved / peak if peak else None,
-            "traffic": TRAFFIC_CAPTURE,
+            "traffic": TRAFFIC_CAPTURE if capture else None,
+            "traffic_per": ("launch of 4.1e8 walks at l0 after an L2 flush (the capture's launch)"
+                            if capture else None),
             "kernel": "k_walk<FP32%s> (mlmc_walk.cu)" % (", proposal" if proposal else ""),
             "peak_source": f"{num_sms} SMs x 128 lanes x {sm_mhz:.0f} MHz (SM count of the device, "
                            "median SM clock sampled in the run)",
-            "issue": ISSUE_CAPTURE,
+            "issue": ISSUE_CAPTURE if capture else None,
             "ops_per_event": ops / events if events else None,
             "walk_launches": launches,
             "avg_launch_ms": 1e3 * walk_s / launches if launches else None,
@@ -823,8 +834,9 @@ def run_kernel_workload(args):
     # the op model and its ALU peak describe the FP32 walk; the FP64 walk is
     # bound by the FP64 pipe (its counters are in the kernel's ncu summary)
     roof = walk_roofline(lv, 1e-3 * statistics.mean(res["l0"]["launch_ms"]), clocks, peaks,
-                         statistics.mean(res["l0"]["launch_ms"]),
-                         proposal=args.kernel_tilt) if w.precision == "fp32" else None
+                         statistics.mean(res["l0"]["launch_ms"]), proposal=args.kernel_tilt,
+                         capture=args.kernel_tilt and args.kernel_matrix == "ba"
+                         ) if w.precision == "fp32" else None
     out = {"metric": "walk kernel alone: walk-steps/s at l0 (one launch, L2 flushed before it)",
            "value": res["l0"]["events_per_s"], "unit": UNIT, "higher_is_better": True,
            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,

@@ -67,6 +67,7 @@ void free_plan(mlmc_plan* p) {
   cudaFree(p->d_tables);
   cudaFree(p->d_lii);
   cudaFree(p->d_heavy);
+  cudaFree(p->d_train_rows);
   cudaFree(p->d_is_block);
   cudaFree(p->d_glob);
   cudaFree(p->d_times);

@@ -107,17 +107,22 @@ struct mlmc_plan {
   int32_t* d_still32_t = nullptr;
   double* d_lam = nullptr;
   bool clock_tilt = false;
-  // Rows the table builds give a block each (stored length 256..8192): the
+  // Rows the table builds give a block each (stored length 32..8192): the
   // list (d_heavy), its device count and, once classified, its host count
   // (-1 before).
   int32_t* d_heavy = nullptr;
   uint32_t* d_heavy_count = nullptr;
   int64_t heavy_count = -1;
+  int heavy_cap = 0;  // the longest listed row's length, rounded up to 4
   // The last mlmc_learn_tilt: the per-walk variance each pilot measured
   // (pilot k walked with the law installed before round k; the last one
   // with the final tilt) and which law was installed (-1: none).
   std::vector<double> learn_var;
   int32_t learn_choice = -1;
+  // The learning's training rows (row i repeated 1 + deg_i / mean degree
+  // times), kept across calls: they depend on the matrix alone.
+  int64_t* d_train_rows = nullptr;
+  int64_t n_train_rows = 0;
   // Forward mode (the tables above are then built from A^T): start weights,
   // their prefix sums and total, scan scratch.
   int64_t* d_wstart = nullptr;

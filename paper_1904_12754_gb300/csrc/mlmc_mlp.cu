@@ -1142,13 +1142,11 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
   float* pv = nullptr;  // v, k^m v (m = 1..4), T_3 and two Taylor terms (8 x n floats)
   float* best_h = nullptr;        // the tilt with the smallest pilot variance so far
   double* xwarm = nullptr;        // x-hat of the best warm start's pilot
-  int64_t* widx = nullptr;        // training rows, weighted by degree (see below)
   __nv_bfloat16* wfeat = nullptr;
   float* wy = nullptr;
   auto cleanup = [&]() {
     cudaFree(best_h);
     cudaFree(xwarm);
-    cudaFree(widx);
     cudaFree(wfeat);
     cudaFree(wy);
     cudaFree(pv);
@@ -1218,8 +1216,8 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
   // deg) times (at most 4n rows in all).  Rows with many off-diagonals are
   // few, but their h sets the clocks and jump laws of every row around them,
   // and an MLP fitted to rows drawn uniformly would fit them worst.
-  int64_t n_train = 0;
-  {
+  // (The list depends on the matrix alone: the plan keeps it.)
+  if (!p->d_train_rows) {
     std::vector<int64_t> rp(p->n + 1);
     LP_CUDA(cudaMemcpyAsync(rp.data(), p->d_row_ptr, sizeof(int64_t) * (p->n + 1),
                             cudaMemcpyDeviceToHost, p->stream), "read row_ptr");
@@ -1231,14 +1229,20 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
       const int64_t c = 1 + static_cast<int64_t>(static_cast<double>(rp[i + 1] - rp[i]) / mean_deg);
       for (int64_t k = 0; k < c && static_cast<int64_t>(idx.size()) < 4 * p->n; ++k) idx.push_back(i);
     }
-    n_train = static_cast<int64_t>(idx.size());
-    LP_CUDA(cudaMalloc(&widx, sizeof(int64_t) * n_train), "alloc");
-    LP_CUDA(cudaMalloc(&wfeat, sizeof(__nv_bfloat16) * n_train * kIn), "alloc");
-    LP_CUDA(cudaMalloc(&wy, sizeof(float) * n_train), "alloc");
-    LP_CUDA(cudaMemcpyAsync(widx, idx.data(), sizeof(int64_t) * n_train, cudaMemcpyHostToDevice,
-                            p->stream), "write rows");
-    LP_CUDA(cudaStreamSynchronize(p->stream), "sync");
+    int64_t* rows = nullptr;
+    LP_CUDA(cudaMalloc(&rows, sizeof(int64_t) * idx.size()), "alloc");
+    cudaError_t e = cudaMemcpyAsync(rows, idx.data(), sizeof(int64_t) * idx.size(),
+                                    cudaMemcpyHostToDevice, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) cudaFree(rows);
+    LP_CUDA(e, "write rows");
+    p->d_train_rows = rows;
+    p->n_train_rows = static_cast<int64_t>(idx.size());
   }
+  const int64_t n_train = p->n_train_rows;
+  const int64_t* widx = p->d_train_rows;
+  LP_CUDA(cudaMalloc(&wfeat, sizeof(__nv_bfloat16) * n_train * kIn), "alloc");
+  LP_CUDA(cudaMalloc(&wy, sizeof(float) * n_train), "alloc");
   // One pilot at l0 with the plan's current walk law: walks [rep_begin,
   // rep_begin + reps) of every row.  Leaves x-hat (the per-row means) in
   // sums, its largest magnitude in *xmax, and the per-walk variance of the

@@ -15,7 +15,10 @@ namespace {
 constexpr int kTableBlock = 256;
 // Rows with kHeavyLo..kHeavyHi stored entries are built by a block each
 // (k_build_tables_heavy, k_build_is_tables_heavy); the others by a thread.
-constexpr int kHeavyLo = 256;
+// The thread-per-row build's time is set by its longest rows (their FP64
+// divisions and logarithms and the Vose pass run one after another), so
+// everything past a few dozen entries goes to the blocks.
+constexpr int kHeavyLo = 32;
 constexpr int kHeavyHi = 8192;
 __host__ __device__ __forceinline__ bool heavy_len(int64_t len) {
   return len >= kHeavyLo && len <= kHeavyHi;
@@ -305,8 +308,8 @@ __global__ void k_build_is_tables(int64_t n, const int64_t* __restrict__ row_ptr
 }
 
 // ---------------------------------------------------------------------------
-// Long rows (kHeavyLo <= row length <= kHeavyHi, the hubs of a scale-free
-// graph): one block per row instead of one thread, with the row's working
+// Long rows (kHeavyLo <= row length <= kHeavyHi: the hubs of a scale-free
+// graph and the rows around them): one block per row instead of one thread, with the row's working
 // values in shared memory.  The sums stay sequential in stored order and the
 // Vose pairing stays one sequence of pops and pushes (thread 0), so the
 // tables are the same bits as the one-thread build; the per-entry arithmetic
@@ -315,18 +318,22 @@ __global__ void k_build_is_tables(int64_t n, const int64_t* __restrict__ row_ptr
 // build's time (a 1241-entry row: about 4 ms).
 // ---------------------------------------------------------------------------
 constexpr int kHeavyBlock = 256;
-// Shared memory per entry: p (8 bytes), queue link (4), alias bucket (4),
-// and for proposal tables lr (4).
-constexpr size_t kHeavySmemPlain = static_cast<size_t>(kHeavyHi) * 16;
-constexpr size_t kHeavySmemIS = static_cast<size_t>(kHeavyHi) * 20;
+// Shared memory per entry of the longest listed row (cap entries): p (8
+// bytes), queue link (4), alias bucket (4), and for proposal tables lr (4).
+constexpr size_t heavy_smem_plain(int cap) { return static_cast<size_t>(cap) * 16; }
+constexpr size_t heavy_smem_is(int cap) { return static_cast<size_t>(cap) * 20; }
 
-// Rows whose length is in [kHeavyLo, kHeavyHi] (any order).
+// Rows whose length is in [kHeavyLo, kHeavyHi] (any order); count[0] gets
+// their number, count[1] the longest of them.
 __global__ void k_heavy_rows(int64_t n, const int64_t* __restrict__ row_ptr,
                              int32_t* __restrict__ list, uint32_t* __restrict__ count) {
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int64_t len = row_ptr[i + 1] - row_ptr[i];
-    if (heavy_len(len)) list[atomicAdd(count, 1u)] = static_cast<int32_t>(i);
+    if (heavy_len(len)) {
+      list[atomicAdd(count, 1u)] = static_cast<int32_t>(i);
+      atomicMax(count + 1, static_cast<uint32_t>(len));
+    }
   }
 }
 
@@ -384,7 +391,7 @@ __device__ __forceinline__ int64_t diag_pos(const int32_t* __restrict__ col, int
 }
 
 __global__ void __launch_bounds__(kHeavyBlock)
-    k_build_tables_heavy(const int32_t* __restrict__ list, const uint32_t* __restrict__ count,
+    k_build_tables_heavy(const int32_t* __restrict__ list, const uint32_t* __restrict__ count, int cap,
                          double t, const int64_t* __restrict__ row_ptr,
                          const int32_t* __restrict__ col, const double* __restrict__ val,
                          Meta32* __restrict__ meta32, Meta64* __restrict__ meta64,
@@ -392,8 +399,8 @@ __global__ void __launch_bounds__(kHeavyBlock)
                          unsigned long long* __restrict__ dmax_bits) {
   extern __shared__ __align__(16) unsigned char hs[];
   double* p = reinterpret_cast<double*>(hs);
-  int32_t* nxt = reinterpret_cast<int32_t*>(hs + kHeavyHi * 8);
-  int32_t* ali = reinterpret_cast<int32_t*>(hs + kHeavyHi * 12);
+  int32_t* nxt = reinterpret_cast<int32_t*>(hs + cap * 8);
+  int32_t* ali = reinterpret_cast<int32_t*>(hs + cap * 12);
   __shared__ double s_lsum;
   const uint32_t rows = *count;
   for (uint32_t it = blockIdx.x; it < rows; it += gridDim.x) {
@@ -458,7 +465,8 @@ __global__ void __launch_bounds__(kHeavyBlock)
 
 __global__ void __launch_bounds__(kHeavyBlock)
     k_build_is_tables_heavy(const int32_t* __restrict__ list, const uint32_t* __restrict__ count,
-                            const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                            int cap, const int64_t* __restrict__ row_ptr,
+                            const int32_t* __restrict__ col,
                             const double* __restrict__ val, const double* __restrict__ lii,
                             const float* __restrict__ h, double alpha,
                             AliasEntryIS* __restrict__ alias, bool clocks, double t,
@@ -466,9 +474,9 @@ __global__ void __launch_bounds__(kHeavyBlock)
                             double* __restrict__ lam_out) {
   extern __shared__ __align__(16) unsigned char hs[];
   double* p = reinterpret_cast<double*>(hs);
-  int32_t* nxt = reinterpret_cast<int32_t*>(hs + kHeavyHi * 8);
-  int32_t* ali = reinterpret_cast<int32_t*>(hs + kHeavyHi * 12);
-  float* lrs = reinterpret_cast<float*>(hs + kHeavyHi * 16);
+  int32_t* nxt = reinterpret_cast<int32_t*>(hs + cap * 8);
+  int32_t* ali = reinterpret_cast<int32_t*>(hs + cap * 12);
+  float* lrs = reinterpret_cast<float*>(hs + cap * 16);
   __shared__ double s_hsum, s_lr_clock;
   const uint32_t rows = *count;
   for (uint32_t it = blockIdx.x; it < rows; it += gridDim.x) {
@@ -630,24 +638,25 @@ __global__ void __launch_bounds__(256) k_still_index(int64_t n, const Meta32* __
 cudaError_t classify_heavy_rows(mlmc_plan* p) {
   if (p->heavy_count >= 0) return cudaSuccess;
   cudaError_t err = cudaMalloc(&p->d_heavy, sizeof(int32_t) * static_cast<size_t>(p->n > 0 ? p->n : 1) +
-                                                sizeof(uint32_t));
+                                                2 * sizeof(uint32_t));
   if (err != cudaSuccess) return err;
   uint32_t* count = reinterpret_cast<uint32_t*>(p->d_heavy + (p->n > 0 ? p->n : 1));
-  if ((err = cudaMemsetAsync(count, 0, sizeof(uint32_t), p->stream)) != cudaSuccess) return err;
+  if ((err = cudaMemsetAsync(count, 0, 2 * sizeof(uint32_t), p->stream)) != cudaSuccess) return err;
   k_heavy_rows<<<grid_for(p, p->n, kTableBlock), kTableBlock, 0, p->stream>>>(p->n, p->d_row_ptr,
                                                                               p->d_heavy, count);
   p->launches++;
-  uint32_t h = 0;
-  if ((err = cudaMemcpyAsync(&h, count, sizeof(h), cudaMemcpyDeviceToHost, p->stream)) != cudaSuccess)
+  uint32_t h[2] = {0, 0};
+  if ((err = cudaMemcpyAsync(h, count, sizeof(h), cudaMemcpyDeviceToHost, p->stream)) != cudaSuccess)
     return err;
   if ((err = cudaStreamSynchronize(p->stream)) != cudaSuccess) return err;
   p->d_heavy_count = count;
-  p->heavy_count = h;
+  p->heavy_count = h[0];
+  p->heavy_cap = static_cast<int>((h[1] + 3u) & ~3u);
   return cudaSuccess;
 }
 
 int heavy_grid(const mlmc_plan* p) {
-  const int64_t cap = static_cast<int64_t>(p->num_sms) * 2;
+  const int64_t cap = static_cast<int64_t>(p->num_sms) * 8;
   return static_cast<int>(p->heavy_count < cap ? p->heavy_count : cap);
 }
 
@@ -665,12 +674,12 @@ cudaError_t launch_build_tables(mlmc_plan* p) {
     static bool attr = false;
     if (!attr) {
       err = cudaFuncSetAttribute(k_build_tables_heavy, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(kHeavySmemPlain));
+                                 static_cast<int>(heavy_smem_plain(kHeavyHi)));
       if (err != cudaSuccess) return err;
       attr = true;
     }
-    k_build_tables_heavy<<<heavy_grid(p), kHeavyBlock, kHeavySmemPlain, p->stream>>>(
-        p->d_heavy, p->d_heavy_count, p->t, p->d_row_ptr, p->d_col, p->d_val, p->d_meta32,
+    k_build_tables_heavy<<<heavy_grid(p), kHeavyBlock, heavy_smem_plain(p->heavy_cap), p->stream>>>(
+        p->d_heavy, p->d_heavy_count, p->heavy_cap, p->t, p->d_row_ptr, p->d_col, p->d_val, p->d_meta32,
         p->d_meta64, p->d_lii, p->d_alias, reinterpret_cast<unsigned long long*>(p->d_norm2));
     p->launches++;
   }
@@ -705,12 +714,12 @@ cudaError_t launch_build_is_tables(mlmc_plan* p) {
     if (!attr) {
       err = cudaFuncSetAttribute(k_build_is_tables_heavy,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(kHeavySmemIS));
+                                 static_cast<int>(heavy_smem_is(kHeavyHi)));
       if (err != cudaSuccess) return err;
       attr = true;
     }
-    k_build_is_tables_heavy<<<heavy_grid(p), kHeavyBlock, kHeavySmemIS, p->stream>>>(
-        p->d_heavy, p->d_heavy_count, p->d_row_ptr, p->d_col, p->d_val, p->d_lii, p->d_h,
+    k_build_is_tables_heavy<<<heavy_grid(p), kHeavyBlock, heavy_smem_is(p->heavy_cap), p->stream>>>(
+        p->d_heavy, p->d_heavy_count, p->heavy_cap, p->d_row_ptr, p->d_col, p->d_val, p->d_lii, p->d_h,
         p->alpha, p->d_alias_is, p->clock_tilt, p->t, p->d_meta32_t, p->d_meta64_t, p->d_lam);
     p->launches++;
   }

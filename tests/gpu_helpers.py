@@ -103,18 +103,19 @@ def small_problems():
     hub.val[lo:hi] = np.where(hub.col[lo:hi] == 5, hub.val[lo:hi], 0.0)
     out["hub_777"] = (hub, 0.2, rng.standard_normal(n))
     # rows whose stored lengths sit on both sides of the table builds'
-    # block-per-row range [256, 8192]: 255, 256 (with its diagonal), 8192,
-    # 8193 (with its diagonal); the other rows short
+    # block-per-row range [32, 8192]: 31, 32 (with its diagonal), 255, 256,
+    # 8192, 8193 (with its diagonal); the other rows short
     n = 9000
     rows, cols, vals = [], [], []
-    for i, (length, diag) in enumerate(((255, False), (256, True), (8192, False), (8193, True))):
+    lengths = ((31, False), (32, True), (255, False), (256, True), (8192, False), (8193, True))
+    for i, (length, diag) in enumerate(lengths):
         off = rng.choice(np.setdiff1d(np.arange(n), [i]), length - (1 if diag else 0),
                          replace=False)
         cc = np.sort(np.concatenate([off, [i]]) if diag else off)
         rows.append(np.full(cc.size, i))
         cols.append(cc)
         vals.append(rng.uniform(0.1, 1.0, cc.size) * rng.choice([-1, 1], cc.size) / length)
-    for i in range(4, n):
+    for i in range(len(lengths), n):
         cc = np.unique(np.concatenate([rng.integers(0, n, 3), [i]]))
         rows.append(np.full(cc.size, i))
         cols.append(cc)

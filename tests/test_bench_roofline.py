@@ -41,7 +41,12 @@ def test_op_model_counts_each_part_once():
     g = 2 * (32 * 150 + 4 * 100)
     assert r["gather"]["achieved"] == pytest.approx(g / walk_s / 1e9, rel=1e-12)
     assert r["gather"]["frac"] == pytest.approx(r["gather"]["achieved"] / 8000.0, rel=1e-12)
-    assert r["traffic"] == bench.TRAFFIC_CAPTURE
+    # the capture's DRAM bytes and issue figures describe one kernel and
+    # workload: reported only when the caller says the line is that one
+    assert r["traffic"] is None and r["issue"] is None
+    c = bench.walk_roofline([lv0, lv1], walk_s, clocks, peaks, total_ms=2.0, num_sms=152,
+                            proposal=True, capture=True)
+    assert c["traffic"] == bench.TRAFFIC_CAPTURE and c["issue"] == bench.ISSUE_CAPTURE
     assert r["bound"] == "alu" and r["unit"] == "Gop/s"
 
 
