@@ -282,8 +282,8 @@ def run_ours(args):
         0's h, so that every rank walks the same law."""
         plan.rebuild()
         with M.MLP(seed=3, stream=stream.cuda_stream) as net:
-            net.learn_tilt(plan, v_in, seed=seed, pilot_walks=args.pilot, steps=300,
-                           batch=8192, clocks=True, rounds=args.rounds)
+            net.learn_tilt(plan, v_in, seed=seed, pilot_walks=args.pilot, steps=args.mlp_steps,
+                           batch=args.mlp_batch, clocks=True, rounds=args.rounds)
             mlp_launches[0] += net.launch_count()
         learn_log.append(plan.learn_report())
         if dist is not None:
@@ -411,7 +411,8 @@ def run_ours(args):
                        "step": "table build + learned tilted proposal (pilot walks, MLP "
                                "training, proposal tables) + MLMC solve to the tolerance",
                        "learning": {"rounds": args.rounds, "pilot_walks": args.pilot,
-                                    "mlp_steps": 300, "alpha": 0.1,
+                                    "mlp_steps": args.mlp_steps, "mlp_batch": args.mlp_batch,
+                                    "alpha": 0.1,
                                     "chosen_law_per_timed_step": [
                                         c for c, _ in learn_log[args.warmup:args.warmup + args.steps]],
                                     "pilot_var_per_walk_last_timed_step":
@@ -686,8 +687,9 @@ def run_learned_workload(args):
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 with M.MLP(seed=3, stream=st) as net:
-                    loss = net.learn_tilt(plan, dv, seed=5 + rep, pilot_walks=args.pilot, steps=300,
-                                          batch=8192, clocks=True, rounds=args.rounds)
+                    loss = net.learn_tilt(plan, dv, seed=5 + rep, pilot_walks=args.pilot,
+                                          steps=args.mlp_steps, batch=args.mlp_batch, clocks=True,
+                                          rounds=args.rounds)
                 torch.cuda.synchronize()
                 t_learn = time.perf_counter() - t0
                 chosen, pilot_var = plan.learn_report()
@@ -792,7 +794,8 @@ def run_kernel_workload(args):
     if args.kernel_tilt:
         # the walk the default workload's solve runs: learned tilted clocks
         with M.MLP(seed=3, stream=stream.cuda_stream) as net:
-            net.learn_tilt(plan, dv, seed=5, pilot_walks=args.pilot, steps=300, batch=8192,
+            net.learn_tilt(plan, dv, seed=5, pilot_walks=args.pilot, steps=args.mlp_steps,
+                           batch=args.mlp_batch,
                            clocks=True, rounds=args.rounds)
     l2win = plan.l2_window()
     sums = torch.zeros(n, dtype=torch.float64, device="cuda")
@@ -1154,7 +1157,11 @@ def main():
                          "default workload runs to it")
     ap.add_argument("--plain-budget", type=float, default=8.0,
                     help="budget of the plain (untilted) comparison solve of the default workload")
-    ap.add_argument("--rounds", type=int, default=3,
+    ap.add_argument("--mlp-steps", type=int, default=150,
+                    help="Adam steps per round of the learned proposal's training")
+    ap.add_argument("--mlp-batch", type=int, default=16384,
+                    help="rows per training step (128 per CTA of the fused training kernel)")
+    ap.add_argument("--rounds", type=int, default=2,
                     help="pilot-train-install rounds of the learned proposal (mlmc_learn_tilt)")
     ap.add_argument("--pilot", type=int, default=64,
                     help="first-round pilot walks per row of the learned proposal")

@@ -21,13 +21,14 @@ def stream_handle() -> int:
 
 
 def make_plan(a, t, precision, l0=None, num_levels=3, max_levels=8, rel_tol=1e-2, pilot=64,
-              max_jumps=1 << 20, **kw):
+              max_jumps=1 << 20, stream=None, **kw):
     from paper_1904_12754_gb300 import mlmc as M
     sched = M.schedule_default(precision=precision, num_levels=num_levels, max_levels=max_levels,
                                pilot_walks=pilot, max_jumps_per_walk=max_jumps, **kw)
     if l0 is not None:
         sched.l0 = l0
-    return M.Plan.from_csr(a, t, sched, rel_tol=rel_tol, stream=stream_handle())
+    return M.Plan.from_csr(a, t, sched, rel_tol=rel_tol,
+                           stream=stream if stream is not None else stream_handle())
 
 
 def gpu_trace(plan, level, coarse, rep_begin, reps, v, seed):
