@@ -55,3 +55,25 @@ def test_a_walk_that_never_jumps_costs_a_quarter_draw_and_a_test():
     more = bench.walk_roofline([_level(8, 0, 8)], 1.0, {"sm_mhz": 1000.0}, {}, 1.0, num_sms=152)
     per_still = (more["achieved"] - base["achieved"]) * 1e9 / 4
     assert per_still == pytest.approx(42 / 4 + 2 + 1, rel=1e-12)
+
+
+def test_fp64_judge_agrees_with_the_oracle_taylor():
+    # bench.py states every error against scipy's expm_multiply; on the
+    # metric's graph (smaller) and with a source term it must agree with the
+    # oracle's FP64 Taylor values to rounding
+    import numpy as np
+    import mlmc_inputs as I
+    from oracle import reference as R
+    b = I.ba_graph(3000, 4, seed=5)
+    t = 1.0 / I.lambda_max(b)
+    v = np.ones(b.n)
+    x = bench._fp64_judge(b, t, v)
+    ref = R.expmv_taylor(b.scipy(), t, v)
+    assert np.linalg.norm(x - ref) <= 1e-12 * np.linalg.norm(ref)
+    a = I.convdiff_3d(8)
+    t = 8.0 / float(abs(a.scipy()).sum(axis=1).max())
+    v = np.random.default_rng(2).random(a.n)
+    f = np.ones(a.n)
+    u = bench._fp64_judge(a, t, v, f)
+    ref = R.expmv_taylor(a.scipy(), t, v) + R.expmv_source_taylor(a.scipy(), t, f)
+    assert np.linalg.norm(u - ref) <= 1e-12 * np.linalg.norm(ref)
