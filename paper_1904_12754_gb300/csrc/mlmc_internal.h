@@ -2,6 +2,7 @@
 #pragma once
 
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -213,6 +214,21 @@ int l2_window_attr(const mlmc_plan* p, const void* base, size_t bytes, cudaLaunc
 
 // Table kernels (mlmc_tables.cu).
 cudaError_t launch_validate(mlmc_plan* p);
+// Raise `func`'s dynamic shared memory limit to `bytes` once per device
+// (the attribute belongs to the current device's context); `done` holds one
+// bit per device already set.
+template <typename F>
+cudaError_t ensure_dynamic_smem(F* func, int bytes, std::atomic<uint64_t>& done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const uint64_t bit = dev >= 0 && dev < 64 ? (uint64_t{1} << dev) : 0;
+  if (bit && (done.load() & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess && bit) done.fetch_or(bit);
+  return e;
+}
+
 cudaError_t launch_build_tables(mlmc_plan* p);
 cudaError_t launch_build_is_tables(mlmc_plan* p);
 

@@ -887,13 +887,9 @@ mlmc_status ensure_tiles(mlmc_mlp* m, int64_t tiles) {
 template <int K>
 cudaError_t tile(mlmc_mlp* m, int64_t M, const __nv_bfloat16* A, const __nv_bfloat16* B,
                  const float* bias, bool relu, __nv_bfloat16* ob, float* of, float* pre) {
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(k_mlp_tile<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kTileSmem);
-    if (e != cudaSuccess) return e;
-    attr_done = true;
-  }
+  static std::atomic<uint64_t> attr_done{0};
+  cudaError_t e = ensure_dynamic_smem(k_mlp_tile<K>, kTileSmem, attr_done);
+  if (e != cudaSuccess) return e;
   const unsigned grid = static_cast<unsigned>((M + kTileM - 1) / kTileM);
   if (grid == 0) return cudaSuccess;
   k_mlp_tile<K><<<grid, 128, kTileSmem, m->stream>>>(M, A, B, bias, relu, ob, of, pre, m->d_err);
@@ -924,12 +920,8 @@ mlmc_status forward(mlmc_mlp* m, const __nv_bfloat16* x, int64_t M, float* z) {
 // tiles' gradients and losses land in d_part.
 mlmc_status train_tiles(mlmc_mlp* m, const __nv_bfloat16* x, const float* y, int64_t n_src,
                         int64_t M, bool sample, uint64_t sample_seed, int64_t* tiles_out) {
-  static bool attr_done = false;
-  if (!attr_done) {
-    MLP_CUDA(cudaFuncSetAttribute(k_mlp_train_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  kTrainSmem), "smem attribute");
-    attr_done = true;
-  }
+  static std::atomic<uint64_t> attr_done{0};
+  MLP_CUDA(ensure_dynamic_smem(k_mlp_train_tile, kTrainSmem, attr_done), "smem attribute");
   const int64_t tiles = (M + kTileM - 1) / kTileM;
   mlmc_status st = ensure_tiles(m, tiles);
   if (st != MLMC_OK) return st;

@@ -671,13 +671,9 @@ cudaError_t launch_build_tables(mlmc_plan* p) {
       p->d_alias, reinterpret_cast<unsigned long long*>(p->d_norm2));
   p->launches++;
   if (p->heavy_count > 0) {
-    static bool attr = false;
-    if (!attr) {
-      err = cudaFuncSetAttribute(k_build_tables_heavy, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(heavy_smem_plain(kHeavyHi)));
-      if (err != cudaSuccess) return err;
-      attr = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    err = ensure_dynamic_smem(k_build_tables_heavy, static_cast<int>(heavy_smem_plain(kHeavyHi)), attr);
+    if (err != cudaSuccess) return err;
     k_build_tables_heavy<<<heavy_grid(p), kHeavyBlock, heavy_smem_plain(p->heavy_cap), p->stream>>>(
         p->d_heavy, p->d_heavy_count, p->heavy_cap, p->t, p->d_row_ptr, p->d_col, p->d_val, p->d_meta32,
         p->d_meta64, p->d_lii, p->d_alias, reinterpret_cast<unsigned long long*>(p->d_norm2));
@@ -710,14 +706,9 @@ cudaError_t launch_build_is_tables(mlmc_plan* p) {
       p->clock_tilt, p->t, p->d_meta32_t, p->d_meta64_t, p->d_lam);
   p->launches++;
   if (p->heavy_count > 0) {
-    static bool attr = false;
-    if (!attr) {
-      err = cudaFuncSetAttribute(k_build_is_tables_heavy,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(heavy_smem_is(kHeavyHi)));
-      if (err != cudaSuccess) return err;
-      attr = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    err = ensure_dynamic_smem(k_build_is_tables_heavy, static_cast<int>(heavy_smem_is(kHeavyHi)), attr);
+    if (err != cudaSuccess) return err;
     k_build_is_tables_heavy<<<heavy_grid(p), kHeavyBlock, heavy_smem_is(p->heavy_cap), p->stream>>>(
         p->d_heavy, p->d_heavy_count, p->heavy_cap, p->d_row_ptr, p->d_col, p->d_val, p->d_lii, p->d_h,
         p->alpha, p->d_alias_is, p->clock_tilt, p->t, p->d_meta32_t, p->d_meta64_t, p->d_lam);
