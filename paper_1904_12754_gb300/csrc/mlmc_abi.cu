@@ -83,6 +83,7 @@ void free_plan(mlmc_plan* p) {
   cudaFree(p->d_x);
   cudaFree(p->d_norm2);
   cudaFree(p->d_sumpair);
+  cudaFree(p->d_red_part);
   cudaFree(p->d_wstart);
   cudaFree(p->d_cdf);
   cudaFree(p->d_guide);
@@ -489,6 +490,7 @@ mlmc_status mlmc_plan_create(mlmc_plan** out, int64_t n, int64_t nnz, const int6
   PLAN_CUDA(dev_alloc(&p->d_x, n), "alloc x");
   PLAN_CUDA(dev_alloc(&p->d_norm2, 4), "alloc scalars");
   PLAN_CUDA(dev_alloc(&p->d_sumpair, 2), "alloc scalars");
+  PLAN_CUDA(dev_alloc(&p->d_red_part, static_cast<size_t>(red_partials(p->num_sms))), "alloc partials");
   PLAN_CUDA(cudaMemsetAsync(p->d_sumpair, 0, 2 * sizeof(double), p->stream), "memset");
   double* sums = nullptr;
   PLAN_CUDA(dev_alloc(&sums, static_cast<size_t>(n) * s.max_levels), "alloc level sums");

@@ -159,6 +159,7 @@ struct mlmc_plan {
   double* d_x = nullptr;                       // [n]
   double* d_norm2 = nullptr;                   // [4]
   double* d_sumpair = nullptr;                 // [2] sum, sum of squares
+  double* d_red_part = nullptr;                // [red_partials(num_sms)] per-block partials
   std::vector<mlmc::LevelAcc> levels;          // per level slot (index l - l0)
   std::vector<mlmc_level_stats> last_stats;
   // Rows walked by the controller (ENTRY mode: one row); -1 = every row.
@@ -229,6 +230,8 @@ cudaError_t ensure_dynamic_smem(F* func, int bytes, std::atomic<uint64_t>& done)
   return e;
 }
 
+// Doubles of per-block partials the controller's reductions need.
+int64_t red_partials(int num_sms);
 cudaError_t launch_build_tables(mlmc_plan* p);
 cudaError_t launch_build_is_tables(mlmc_plan* p);
 

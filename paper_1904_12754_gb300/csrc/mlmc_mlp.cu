@@ -784,6 +784,64 @@ __global__ void k_mlp_features(int64_t n, const int64_t* __restrict__ row_ptr,
   }
 }
 
+// A pilot's row sums S_i (M walks each) to x-hat_i = S_i / M in place, with
+// per-block partials of sum_i S_i^2 / M (part[b]) and max_i |x-hat_i|
+// (part[gridDim.x + b]); fixed grid and reduction order, so the pilot's
+// variance is the same number on every run.
+constexpr int kStatBlocks = 256;
+__global__ void __launch_bounds__(256) k_pilot_stats(int64_t n, double scale, double* __restrict__ sums,
+                                                     double* __restrict__ part) {
+  __shared__ double s_sq[8], s_mx[8];
+  double sq = 0.0, mx = 0.0;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const double sv = sums[i];
+    sq += sv * sv * scale;
+    const double x = sv * scale;
+    sums[i] = x;
+    mx = fmax(mx, fabs(x));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sq += __shfl_xor_sync(0xFFFFFFFFu, sq, o);
+    mx = fmax(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    s_sq[warp] = sq;
+    s_mx[warp] = mx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) {
+      a += s_sq[w];
+      b = fmax(b, s_mx[w]);
+    }
+    part[blockIdx.x] = a;
+    part[gridDim.x + blockIdx.x] = b;
+  }
+}
+
+// Per-block partials of max_i |v_i| into part[b] (fixed grid of kStatBlocks).
+__global__ void __launch_bounds__(256) k_absmax_partials(int64_t n, const double* __restrict__ v,
+                                                         double* __restrict__ part) {
+  __shared__ double s_mx[8];
+  double mx = 0.0;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    mx = fmax(mx, fabs(v[i]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
+  if ((threadIdx.x & 31) == 0) s_mx[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) b = fmax(b, s_mx[w]);
+    part[blockIdx.x] = b;
+  }
+}
+
 // log targets and, for the proposal, h = exp(z) clamped.
 // y_i = alpha log(|x-hat_i| + floor_x) + (1 - alpha) log(|v_i| + floor_v)
 // (v may be null when alpha = 1).
@@ -1134,11 +1192,13 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
   float* pv = nullptr;  // v, k^m v (m = 1..4), T_3 and two Taylor terms (8 x n floats)
   float* best_h = nullptr;        // the tilt with the smallest pilot variance so far
   double* xwarm = nullptr;        // x-hat of the best warm start's pilot
+  double* stats = nullptr;        // a pilot's per-block partial sums (k_pilot_stats)
   __nv_bfloat16* wfeat = nullptr;
   float* wy = nullptr;
   auto cleanup = [&]() {
     cudaFree(best_h);
     cudaFree(xwarm);
+    cudaFree(stats);
     cudaFree(wfeat);
     cudaFree(wy);
     cudaFree(pv);
@@ -1169,6 +1229,7 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
   LP_CUDA(cudaMalloc(&pv, sizeof(float) * p->n * 8), "alloc");
   LP_CUDA(cudaMalloc(&best_h, sizeof(float) * p->n), "alloc");
   LP_CUDA(cudaMalloc(&xwarm, sizeof(double) * p->n), "alloc");
+  LP_CUDA(cudaMalloc(&stats, sizeof(double) * 2 * kStatBlocks), "alloc");
   LP_CUDA(cudaMemcpyAsync(dv, v, sizeof(double) * p->n, cudaMemcpyDefault, p->stream), "copy v");
   const unsigned g = static_cast<unsigned>(std::min<int64_t>((p->n + 255) / 256, p->num_sms * 8));
   // Features (fixed over the rounds: they use the paper's jump law).
@@ -1198,10 +1259,13 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
   LP_CUDA(cudaGetLastError(), "features");
   double vmax = 0.0;
   {
-    std::vector<double> hv(p->n);
-    LP_CUDA(cudaMemcpyAsync(hv.data(), dv, sizeof(double) * p->n, cudaMemcpyDeviceToHost, p->stream), "read v");
+    k_absmax_partials<<<kStatBlocks, 256, 0, p->stream>>>(p->n, dv, stats);
+    p->launches++;
+    std::vector<double> hv(kStatBlocks);
+    LP_CUDA(cudaMemcpyAsync(hv.data(), stats, sizeof(double) * kStatBlocks, cudaMemcpyDeviceToHost,
+                            p->stream), "read max |v|");
     LP_CUDA(cudaStreamSynchronize(p->stream), "sync");
-    for (double q : hv) vmax = std::max(vmax, std::fabs(q));
+    for (double q : hv) vmax = std::max(vmax, q);
   }
   mlmc_status st = MLMC_OK;
   // Training rows weighted by degree: row i appears 1 + floor(deg_i / mean
@@ -1252,24 +1316,30 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
     w.sum_y = sums;
     w.totals = sums + p->n;
     if ((e = launch_walk(p, w)) != cudaSuccess) return e;
-    std::vector<double> hsum(p->n + kTotSlots);
-    e = cudaMemcpyAsync(hsum.data(), sums, sizeof(double) * (p->n + kTotSlots),
-                        cudaMemcpyDeviceToHost, p->stream);
+    // x-hat in place and the variance's sums on the device; only the
+    // partials and the sum of squares come back
+    k_pilot_stats<<<kStatBlocks, 256, 0, p->stream>>>(p->n, 1.0 / static_cast<double>(reps), sums,
+                                                      stats);
+    p->launches++;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    std::vector<double> hs(2 * kStatBlocks + 1);
+    e = cudaMemcpyAsync(hs.data(), stats, sizeof(double) * 2 * kStatBlocks, cudaMemcpyDeviceToHost,
+                        p->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(hs.data() + 2 * kStatBlocks, sums + p->n + kTotY2, sizeof(double),
+                          cudaMemcpyDeviceToHost, p->stream);
     if (e != cudaSuccess) return e;
     if ((e = cudaStreamSynchronize(p->stream)) != cudaSuccess) return e;
-    const double scale = 1.0 / static_cast<double>(reps);
     double sq = 0.0;
     *xmax = 0.0;
-    for (int64_t i = 0; i < p->n; ++i) {
-      sq += hsum[i] * hsum[i] * scale;
-      hsum[i] *= scale;
-      *xmax = std::max(*xmax, std::fabs(hsum[i]));
+    for (int b = 0; b < kStatBlocks; ++b) {
+      sq += hs[b];
+      *xmax = std::max(*xmax, hs[kStatBlocks + b]);
     }
-    *var = reps > 1 ? (hsum[p->n + kTotY2] - sq) / static_cast<double>(reps - 1) /
+    *var = reps > 1 ? (hs[2 * kStatBlocks] - sq) / static_cast<double>(reps - 1) /
                           static_cast<double>(p->n)
                     : std::numeric_limits<double>::infinity();
-    return cudaMemcpyAsync(sums, hsum.data(), sizeof(double) * p->n, cudaMemcpyHostToDevice,
-                           p->stream);
+    return cudaSuccess;
   };
   // Every pilot measures the law it walks with; the law with the smallest
   // measured variance is the one installed at the end (for jumps only the

@@ -29,8 +29,9 @@ __device__ __forceinline__ double block_sum(double v) {
   return v;
 }
 
+// Per-block partial sums of a and a^2: part[b], part[gridDim.x + b].
 __global__ void __launch_bounds__(kRedBlock) k_sum_sumsq(int64_t n, const double* __restrict__ a,
-                                                         double* __restrict__ out) {
+                                                         double* __restrict__ part) {
   double s1 = 0.0, s2 = 0.0;
   for (int64_t i = blockIdx.x * static_cast<int64_t>(kRedBlock) + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * kRedBlock) {
@@ -42,14 +43,31 @@ __global__ void __launch_bounds__(kRedBlock) k_sum_sumsq(int64_t n, const double
   __syncthreads();
   s2 = block_sum(s2);
   if (threadIdx.x == 0) {
-    atomicAdd(out, s1);
-    atomicAdd(out + 1, s2);
+    part[blockIdx.x] = s1;
+    part[gridDim.x + blockIdx.x] = s2;
   }
 }
 
+// out[k] = the sum of parts[k * g .. k * g + g) for k < count, in a fixed
+// order (lane j adds partials j, j + 32, ...; then a fixed shuffle tree): the
+// controller's sums are the same bits on every run and on every rank of a
+// sharded solve, so every rank takes the same decisions.  One warp.
+__global__ void k_combine(int g, int count, const double* __restrict__ parts,
+                          double* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  for (int k = 0; k < count; ++k) {
+    double v = 0.0;
+    for (int b = lane; b < g; b += 32) v += parts[static_cast<int64_t>(k) * g + b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    if (lane == 0) out[k] = v;
+  }
+}
+
+// x = sum_l S_l / M_l and per-block partials of ||x||^2 (part[b]).
 __global__ void __launch_bounds__(kRedBlock) k_finalize(int64_t n, FinalizeArgs f,
                                                         double* __restrict__ x,
-                                                        double* __restrict__ norm2) {
+                                                        double* __restrict__ part) {
   double acc = 0.0;
   for (int64_t i = blockIdx.x * static_cast<int64_t>(kRedBlock) + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * kRedBlock) {
@@ -59,7 +77,7 @@ __global__ void __launch_bounds__(kRedBlock) k_finalize(int64_t n, FinalizeArgs 
     acc += xi * xi;
   }
   acc = block_sum(acc);
-  if (threadIdx.x == 0) atomicAdd(norm2, acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc;
 }
 
 int red_grid(const mlmc_plan* p) {
@@ -106,10 +124,14 @@ cudaError_t launch_finalize_times(mlmc_plan* p, int num_levels, int n_times, dou
 }
 
 cudaError_t launch_sum_sumsq(mlmc_plan* p, const double* a, double* out) {
-  k_sum_sumsq<<<red_grid(p), kRedBlock, 0, p->stream>>>(p->n, a, out);
-  p->launches++;
+  const int g = red_grid(p);
+  k_sum_sumsq<<<g, kRedBlock, 0, p->stream>>>(p->n, a, p->d_red_part);
+  k_combine<<<1, 32, 0, p->stream>>>(g, 2, p->d_red_part, out);
+  p->launches += 2;
   return cudaGetLastError();
 }
+
+int64_t red_partials(int num_sms) { return 2 * static_cast<int64_t>(num_sms) * 8; }
 
 cudaError_t launch_finalize(mlmc_plan* p, int num_levels, double* x, double* norm2) {
   if (num_levels > kMaxLevels) return cudaErrorInvalidValue;
@@ -120,10 +142,10 @@ cudaError_t launch_finalize(mlmc_plan* p, int num_levels, double* x, double* nor
     f.inv_m[k] = L.reps > 0 ? 1.0 / static_cast<double>(L.reps) : 0.0;
   }
   f.count = num_levels;
-  cudaError_t err = cudaMemsetAsync(norm2, 0, sizeof(double), p->stream);
-  if (err != cudaSuccess) return err;
-  k_finalize<<<red_grid(p), kRedBlock, 0, p->stream>>>(p->n, f, x, norm2);
-  p->launches++;
+  const int g = red_grid(p);
+  k_finalize<<<g, kRedBlock, 0, p->stream>>>(p->n, f, x, p->d_red_part);
+  k_combine<<<1, 32, 0, p->stream>>>(g, 1, p->d_red_part, norm2);
+  p->launches += 2;
   return cudaGetLastError();
 }
 
