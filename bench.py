@@ -73,8 +73,8 @@ def _env_rank():
 
 
 def aggregate_over_ranks(dist, elapsed: float, count: float, device="cpu"):
-    """Whole-job figures of a weak-scaling run: (max elapsed over ranks, sum
-    of counts over ranks).  Without a process group, the rank's own pair."""
+    """Whole-job figures of a multi-rank run: (max elapsed over ranks, sum of
+    counts over ranks).  Without a process group, the rank's own pair."""
     if dist is None:
         return float(elapsed), float(count)
     import torch
@@ -231,11 +231,16 @@ def run_reference(args):
 def run_ours(args):
     import torch
     rank, world, local = _env_rank()
-    torch.cuda.set_device(local)
+    # one rank per GPU; with more ranks than GPUs (a host-side gloo check of
+    # the sharded path) ranks share devices, whose kernels never wait on
+    # one another: the exchange is the host all-reduce
+    torch.cuda.set_device(local % torch.cuda.device_count())
     dist = None
+    coll = "cuda"
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        dist.init_process_group(args.dist_backend)
+        coll = "cuda" if args.dist_backend == "nccl" else "cpu"
     import __graft_entry__ as g
     if rank == 0:
         g.build()
@@ -287,9 +292,9 @@ def run_ours(args):
             mlp_launches[0] += net.launch_count()
         learn_log.append(plan.learn_report())
         if dist is not None:
-            h = torch.from_numpy(plan.export_h()).cuda()
+            h = torch.from_numpy(plan.export_h()).to(coll)
             dist.broadcast(h, 0)
-            plan.set_tilt(h, 0.1, clocks=True)
+            plan.set_tilt(h.cpu().numpy() if coll == "cpu" else h, 0.1, clocks=True)
         rc = plan.expmv(v_in, x_out, seed, allow_not_converged=True)
         levels, est = plan.stats()
         plan.set_tilt(None)
@@ -343,7 +348,7 @@ def run_ours(args):
     total_ms = float(sum(step_ms))
     # whole-job aggregate.  Sharded: the walk-steps are counted once (every
     # rank's stats describe the whole solve), the time is the slowest rank's.
-    total_ms_all, _ = aggregate_over_ranks(dist, total_ms, events, "cuda")
+    total_ms_all, _ = aggregate_over_ranks(dist, total_ms, events, coll)
     value = events / (total_ms_all * 1e-3)
     x_last = dx.cpu().numpy()
 
@@ -361,7 +366,7 @@ def run_ours(args):
         e2e_events += sum(lv["walks_per_row"] * n + lv["jumps"] for lv in levels)
     t_e2e = time.perf_counter() - t_e2e
     log(f"e2e: {t_e2e:.2f} s for {args.steps} step(s)")
-    t_e2e_all, _ = aggregate_over_ranks(dist, t_e2e, e2e_events, "cuda")
+    t_e2e_all, _ = aggregate_over_ranks(dist, t_e2e, e2e_events, coll)
     e2e_value = e2e_events / t_e2e_all
 
     peaks, peak_kind = _peaks()
@@ -1147,6 +1152,9 @@ def run_c1_workload(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--dist-backend", choices=["nccl", "gloo"], default="nccl",
+                    help="N > 1: the process group's backend (gloo: a host-side check of the "
+                         "sharded path; ranks may share a GPU)")
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
