@@ -1180,6 +1180,28 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
   learn_seed ^= learn_seed >> 31;
   const bool was = p->proposal_active;
   const bool was_clocks = p->clock_tilt;
+  const double was_alpha = p->alpha;
+  // The plan's proposal before the call (h), put back if the call fails.
+  float* saved_h = nullptr;
+  if (was && p->d_h) {
+    if (cudaMalloc(&saved_h, sizeof(float) * p->n) != cudaSuccess ||
+        cudaMemcpyAsync(saved_h, p->d_h, sizeof(float) * p->n, cudaMemcpyDeviceToDevice,
+                        p->stream) != cudaSuccess) {
+      cudaFree(saved_h);
+      return mfail(MLMC_ERR_CUDA, "mlmc_learn_tilt: saving the plan's proposal failed");
+    }
+  }
+  auto restore = [&]() {
+    if (was && saved_h) {
+      if (mlmc_plan_set_tilt(p, saved_h, was_alpha,
+                             was_clocks ? (MLMC_TILT_JUMPS | MLMC_TILT_CLOCKS) : MLMC_TILT_JUMPS) !=
+          MLMC_OK)
+        p->proposal_active = p->clock_tilt = false;  // the paper's walk: always consistent
+    } else {
+      p->proposal_active = was;
+      p->clock_tilt = was_clocks;
+    }
+  };
   // The first pilot uses the paper's walk (jumps only) or, with tilted
   // clocks, the tilt of h0 = sqrt(T_3 |v|) (below).
   p->proposal_active = false;
@@ -1208,16 +1230,17 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
     cudaFree(y);
     cudaFree(z);
     cudaFree(h);
+    cudaFree(saved_h);
   };
 #define LP_CUDA(call, what)                                                                    \
   do {                                                                                         \
     cudaError_t e_ = (call);                                                                   \
     if (e_ != cudaSuccess) {                                                                   \
+      const std::string msg_ = std::string("learn proposal ") + (what) + ": " +                \
+                               cudaGetErrorString(e_);                                         \
+      restore();                                                                               \
       cleanup();                                                                               \
-      p->proposal_active = was;                                                                \
-      p->clock_tilt = was_clocks;                                                              \
-      return mfail(MLMC_ERR_CUDA, std::string("learn proposal ") + (what) + ": " +             \
-                                      cudaGetErrorString(e_));                                 \
+      return mfail(MLMC_ERR_CUDA, msg_);                                                       \
     }                                                                                          \
   } while (0)
   LP_CUDA(cudaMalloc(&sums, sizeof(double) * (p->n + kTotSlots)), "alloc");
@@ -1438,14 +1461,17 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
     LP_CUDA(pilot(next_rep, 4 * pilot_walks, &xmax, &var), "final pilot");
     const int32_t last = static_cast<int32_t>(p->learn_var.size());
     LP_CUDA(consider(var, false), "final");
-    if (p->learn_choice != last)
+    if (p->learn_choice < 0)
+      st = mfail(MLMC_ERR_NUMERIC, "mlmc_learn_tilt: no pilot measured a finite variance");
+    else if (p->learn_choice != last)
       st = mlmc_plan_set_tilt(p, p->learn_choice == 0 && !clocks ? nullptr : best_h, alpha, tilt);
   }
-  cleanup();
   if (st != MLMC_OK) {
-    p->proposal_active = was;
-    p->clock_tilt = was_clocks;
+    const std::string msg = mlmc_last_error();
+    restore();
+    set_error(msg);  // the first failure's message, not the restore's
   }
+  cleanup();
   return st;
 #undef LP_CUDA
 }

@@ -236,3 +236,25 @@ def test_learning_keeps_the_better_law():
                 plan.export_h()
         else:
             assert np.all(plan.export_h() > 0)
+
+
+def test_failed_learning_leaves_the_previous_proposal():
+    # a right-hand side with a NaN: no pilot measures a finite variance (or
+    # the network's h is rejected); the call fails and the plan keeps the
+    # tilt it had, bit for bit, and still solves
+    from paper_1904_12754_gb300 import mlmc as M
+    b, t, v = _ba_tc(2000)
+    x = R.expmv(b.scipy(), t, v)
+    h0 = np.sqrt(x * v).astype(np.float32)
+    with make_plan(b, t, 1, rel_tol=1e-2, num_levels=3, max_levels=6) as plan:
+        plan.set_tilt(h0, 0.1, clocks=True)
+        bad = v.copy()
+        bad[7] = np.nan
+        with M.MLP(seed=3, stream=stream_handle()) as net:
+            with pytest.raises(M.MlmcError):
+                net.learn_tilt(plan, bad, seed=1, pilot_walks=16, steps=10, batch=1024,
+                               clocks=True, rounds=1)
+        assert np.array_equal(plan.export_h(), h0)
+        xs = np.zeros(b.n)
+        plan.expmv(v, xs, seed=5)
+        assert np.linalg.norm(xs - x) / np.linalg.norm(x) <= 2e-2
