@@ -258,3 +258,26 @@ def test_failed_learning_leaves_the_previous_proposal():
         xs = np.zeros(b.n)
         plan.expmv(v, xs, seed=5)
         assert np.linalg.norm(xs - x) / np.linalg.norm(x) <= 2e-2
+
+
+@pytest.mark.parametrize("leaves", [5, 40])
+def test_learning_on_tiny_graphs(leaves):
+    # a star of 6 or 41 nodes (the 40-leaf hub goes to the block-per-row
+    # table build): fewer rows than one training tile, and the learned
+    # solve still reaches the tolerance against the FP64 judge
+    from paper_1904_12754_gb300 import mlmc as M
+    b = I.star_graph(leaves)
+    t = 0.5 / I.lambda_max(b)
+    v = np.ones(b.n)
+    x = R.expmv(b.scipy(), t, v)
+    with make_plan(b, t, 1, rel_tol=1e-3, num_levels=3, max_levels=6) as plan:
+        with M.MLP(seed=3, stream=stream_handle()) as net:
+            net.learn_tilt(plan, v, seed=2, pilot_walks=64, steps=20, batch=256, clocks=True,
+                           rounds=2)
+        chosen, pv = plan.learn_report()
+        assert len(pv) == 5 and 0 <= chosen < 5
+        xs = np.zeros(b.n)
+        plan.expmv(v, xs, seed=8)
+        _, est = plan.stats()
+    assert est <= 1e-3
+    assert np.linalg.norm(xs - x) / np.linalg.norm(x) <= 2e-3
