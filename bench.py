@@ -386,7 +386,9 @@ def run_ours(args):
     plain = {"budget_s": args.plain_budget, "seconds": sec_p, "est_rel_err": est_p,
              "converged": conv_p, "walk_steps_per_s": ev_p / sec_p,
              "projected_time_to_tol_s": sec_p * (est_p / w.tol) ** 2,
-             "projection": "seconds x (est_rel_err / tol)^2 at the measured variance"}
+             "projection": "seconds x (est_rel_err / tol)^2 at the measured variance; a lower "
+                           "bound here: the plain walk's heavy-tailed weights make its own error "
+                           "estimate unreliable"}
     log(f"plain: {sec_p:.2f} s, est {est_p:.3g}, projected {plain['projected_time_to_tol_s']:.3g} s")
 
     cpu = None
