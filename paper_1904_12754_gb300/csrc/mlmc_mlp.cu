@@ -673,21 +673,32 @@ __global__ void k_mlp_pack(const float* __restrict__ p, __nv_bfloat16* __restric
 
 // out_i = sum_{j != i} (|a_ij| / L_ii) in_j: one step of the paper's jump
 // law k (Eq. 12); rows without jumps keep in_i.
+// One warp per row: the lanes take the row's entries in turn and their sums
+// meet in a warp reduction (a hub row is not left to one thread).
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  return v;
+}
+
 __global__ void k_jump_mean(int64_t n, const int64_t* __restrict__ row_ptr,
                             const int32_t* __restrict__ col, const double* __restrict__ val,
                             const double* __restrict__ lii, const float* __restrict__ in,
                             float* __restrict__ out) {
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
-       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x >> 5) + (threadIdx.x >> 5); i < n;
+       i += warps) {
     const double L = lii[i];
     if (!(L > 0.0)) {
-      out[i] = in[i];
+      if (lane == 0) out[i] = in[i];
       continue;
     }
     double acc = 0.0;
-    for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q)
+    for (int64_t q = row_ptr[i] + lane; q < row_ptr[i + 1]; q += 32)
       if (col[q] != i) acc += fabs(val[q]) * static_cast<double>(in[col[q]]);
-    out[i] = static_cast<float>(acc / L);
+    acc = warp_sum_d(acc);
+    if (lane == 0) out[i] = static_cast<float>(acc / L);
   }
 }
 
@@ -698,14 +709,19 @@ __global__ void k_abs_taylor_step(int64_t n, const int64_t* __restrict__ row_ptr
                                   const int32_t* __restrict__ col, const double* __restrict__ val,
                                   double scale, const float* __restrict__ in,
                                   float* __restrict__ term_out, float* __restrict__ acc) {
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
-       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x >> 5) + (threadIdx.x >> 5); i < n;
+       i += warps) {
     double s = 0.0;
-    for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q)
+    for (int64_t q = row_ptr[i] + lane; q < row_ptr[i + 1]; q += 32)
       if (col[q] != i) s += fabs(val[q]) * static_cast<double>(in[col[q]]);
-    const float tv = static_cast<float>(scale * s);
-    term_out[i] = tv;
-    acc[i] += tv;
+    s = warp_sum_d(s);
+    if (lane == 0) {
+      const float tv = static_cast<float>(scale * s);
+      term_out[i] = tv;
+      acc[i] += tv;
+    }
   }
 }
 
@@ -746,8 +762,10 @@ __global__ void k_mlp_features(int64_t n, const int64_t* __restrict__ row_ptr,
                                const float* __restrict__ p1, const float* __restrict__ p2,
                                const float* __restrict__ p3, const float* __restrict__ p4,
                                const float* __restrict__ taylor3, __nv_bfloat16* __restrict__ x) {
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
-       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x >> 5) + (threadIdx.x >> 5); i < n;
+       i += warps) {
     float f[kIn];
     const Meta64 m = meta[i];
     f[0] = 1.f;
@@ -761,7 +779,7 @@ __global__ void k_mlp_features(int64_t n, const int64_t* __restrict__ row_ptr,
     f[8] = p4[i];
     float sd = 0.f, mx = 0.f, sdl = 0.f;
     int c = 0;
-    for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q) {
+    for (int64_t q = row_ptr[i] + lane; q < row_ptr[i + 1]; q += 32) {
       const int64_t j = col[q];
       if (j == i) continue;
       const Meta64 mj = meta[j];
@@ -771,6 +789,14 @@ __global__ void k_mlp_features(int64_t n, const int64_t* __restrict__ row_ptr,
       sdl += static_cast<float>(mj.dl);
       ++c;
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      sd += __shfl_xor_sync(0xFFFFFFFFu, sd, o);
+      mx = fmaxf(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
+      sdl += __shfl_xor_sync(0xFFFFFFFFu, sdl, o);
+      c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+    }
+    if (lane != 0) continue;
     const float ic = c > 0 ? 1.f / static_cast<float>(c) : 0.f;
     f[9] = sd * ic;
     f[10] = mx;
@@ -1255,11 +1281,13 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
   LP_CUDA(cudaMalloc(&stats, sizeof(double) * 2 * kStatBlocks), "alloc");
   LP_CUDA(cudaMemcpyAsync(dv, v, sizeof(double) * p->n, cudaMemcpyDefault, p->stream), "copy v");
   const unsigned g = static_cast<unsigned>(std::min<int64_t>((p->n + 255) / 256, p->num_sms * 8));
+  // warp-per-row kernels: 8 rows per block of 256
+  const unsigned gw = static_cast<unsigned>(std::min<int64_t>((p->n + 7) / 8, p->num_sms * 16));
   // Features (fixed over the rounds: they use the paper's jump law).
   k_to_float32<<<g, 256, 0, p->stream>>>(p->n, dv, pv);
   p->launches++;
   for (int mstep = 1; mstep <= 4; ++mstep)
-    k_jump_mean<<<g, 256, 0, p->stream>>>(p->n, p->d_row_ptr, p->d_col, p->d_val, p->d_lii,
+    k_jump_mean<<<gw, 256, 0, p->stream>>>(p->n, p->d_row_ptr, p->d_col, p->d_val, p->d_lii,
                                            pv + (mstep - 1) * p->n, pv + mstep * p->n);
     p->launches++;
   {
@@ -1269,13 +1297,13 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
     k_abs_float32<<<g, 256, 0, p->stream>>>(p->n, dv, ta, t3);
     p->launches++;
     for (int mstep = 1; mstep <= 3; ++mstep) {
-      k_abs_taylor_step<<<g, 256, 0, p->stream>>>(p->n, p->d_row_ptr, p->d_col, p->d_val,
+      k_abs_taylor_step<<<gw, 256, 0, p->stream>>>(p->n, p->d_row_ptr, p->d_col, p->d_val,
                                                   p->t / mstep, ta, tb, t3);
       p->launches++;
       std::swap(ta, tb);
     }
   }
-  k_mlp_features<<<g, 256, 0, p->stream>>>(p->n, p->d_row_ptr, p->d_col, p->d_meta64, p->d_lii, p->t,
+  k_mlp_features<<<gw, 256, 0, p->stream>>>(p->n, p->d_row_ptr, p->d_col, p->d_meta64, p->d_lii, p->t,
                                             pv, pv + p->n, pv + 2 * p->n, pv + 3 * p->n,
                                             pv + 4 * p->n, pv + 5 * p->n, feat);
   p->launches++;
