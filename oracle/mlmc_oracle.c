@@ -34,6 +34,17 @@
  *   R3  scaled time s = tau/beta in [0,1]: rate beta*L_jj, grid points k/N.
  *       A jump at exactly s = k/N happens after grid point k is sampled; a
  *       jump at s >= 1 is not taken.
+ *   R19 (not in the paper) a proposal may change with time: K equal pieces
+ *       [p/K, (p+1)/K) of s, each with its own rates, jump law and d_i
+ *       (orc_ctx.pieces).  A holding time that reaches the piece's end b is
+ *       carried into the next piece by memorylessness: the pending jump time
+ *       s becomes b + (s - b) * inv_rate_next / inv_rate_now (one fused
+ *       multiply-add after the quotient; infinite when either inverse rate
+ *       is), which is the unused part of the exponential at the new rate.
+ *       The grid's integrand takes each interval's own piece at both of its
+ *       ends, so a grid point on a piece boundary gets the mean of the two
+ *       pieces' values (the trapezoid of each piece); N must be a multiple
+ *       of K on every level walked.
  *
  * Build: gcc -O2 -fopenmp -ffp-contract=off -shared -fPIC (FMA contraction
  * must be off so that every rounding is the IEEE one written here).
@@ -477,6 +488,10 @@ typedef struct {
     int64_t max_jumps;
     const double *f;           /* NULL, or the constant source vector F of Algorithm 3 */
     double t;                  /* the time t (the source term's quadrature step is t/N) */
+    int32_t pieces;            /* 0 or 1: one law; K > 1: R19's time pieces, with dl,
+                                * inv_rate and inv_rate32 holding K blocks of n rows and
+                                * the alias arrays K blocks of row_ptr[n] entries */
+    int32_t pad_pieces;
 } orc_ctx;
 
 typedef struct {
@@ -542,7 +557,8 @@ static void orc_draw_k(const orc_ctx *c, orc_ctr k, uint32_t event, uint32_t x[4
 }
 
 /* Holding time in state j from draw x, in the walk's time precision, added
- * to the clock value `from`. */
+ * to the clock value `from`.  With time pieces j indexes the piece's block
+ * (piece * n + state). */
 static double orc_hold(const orc_ctx *c, int64_t j, const uint32_t x[4], double from)
 {
     if (c->precision == ORC_FP32) {
@@ -560,13 +576,14 @@ static double orc_hold32_word(const orc_ctx *c, int64_t j, uint32_t w, double fr
     return (double)((float)from + s);
 }
 
-/* Choose the next state from row j's alias table with draw words x2, x3;
- * *lr receives log(k/q) of the chosen column (0 without a proposal). */
+/* Choose the next state from row j's alias table (of time piece `piece`)
+ * with draw words x2, x3; *lr receives log(k/q) of the chosen column (0
+ * without a proposal). */
 static int64_t orc_jump(const orc_ctx *c, int64_t j, const uint32_t x[4], int32_t *sign,
-                        double *lr)
+                        double *lr, int32_t piece)
 {
     uint32_t b = (uint32_t)(((uint64_t)x[2] * (uint64_t)(uint32_t)c->deg[j]) >> 32);
-    int64_t pos = c->row_ptr[j] + b;
+    int64_t pos = (int64_t)piece * c->row_ptr[c->n] + c->row_ptr[j] + b;
     int64_t to;
     int neg;
     *lr = 0.0;
@@ -581,6 +598,24 @@ static int64_t orc_jump(const orc_ctx *c, int64_t j, const uint32_t x[4], int32_
     }
     if (neg) *sign = -*sign;
     return to;
+}
+
+/* R19: the pending jump time t_next >= b of state j carried from piece p
+ * into piece p + 1 at the boundary b = step / N. */
+static double orc_cross(const orc_ctx *c, int64_t j, int32_t p, double t_next, int64_t step,
+                        int64_t N)
+{
+    const int64_t now = (int64_t)p * c->n + j, next = now + c->n;
+    if (c->precision == ORC_FP32) {
+        const float b = (float)step / (float)N;
+        const float ir = c->inv_rate32[now], irn = c->inv_rate32[next];
+        if (isinf(ir) || isinf(irn)) return (double)INFINITY;
+        return (double)fmaf((float)t_next - b, irn / ir, b);
+    }
+    const double b = (double)step / (double)N;
+    const double ir = c->inv_rate[now], irn = c->inv_rate[next];
+    if (isinf(ir) || isinf(irn)) return INFINITY;
+    return fma(t_next - b, irn / ir, b);
 }
 
 static int orc_before(const orc_ctx *c, double t_next, int64_t n_step, int64_t N)
@@ -619,8 +654,17 @@ static int orc_walk_core(const orc_ctx *c, int64_t row, orc_ctr kc, int level, i
                          int32_t n_times, double *y_times)
 {
     const int64_t N = (int64_t)1 << level;
-    int64_t j = row;
+    /* R19: K time pieces of `per` intervals each; the walk's current piece
+     * is that of the interval being walked. */
+    const int32_t K = c->pieces > 1 ? c->pieces : 1;
+    if (K > 1 && (N % K != 0 || c->f != NULL || n_times > 1 || c->variant != ORC_RESIDUAL)) {
+        memset(out, 0, sizeof(*out));
+        out->status = -1;
+        return -1;
+    }
+    const int64_t per = N / K;
     int32_t sign = 1;
+    int64_t j = row;
     uint32_t ndraw = 0;   /* Philox draws used so far */
     int64_t jumps = 0;
     uint32_t hash = 2166136261u;
@@ -671,7 +715,9 @@ static int orc_walk_core(const orc_ctx *c, int64_t row, orc_ctr kc, int level, i
     }
 
     for (int64_t step = 1; step <= N; ++step) {
-        double g = c->dl[j] / (double)N;
+        const int32_t pc = (int32_t)((step - 1) / per);  /* piece of this interval */
+        const double *dlp = c->dl + (int64_t)pc * c->n;
+        double g = dlp[j] / (double)N;
         eta2 = eta2 * exp(g / 2.0);
         if (step % 2 != 0) eta1 = eta1 * exp(g);
         if (c->variant == ORC_REDRAW) {
@@ -688,13 +734,14 @@ static int orc_walk_core(const orc_ctx *c, int64_t row, orc_ctr kc, int level, i
             double lr = 0.0;
             /* FP32: jump k + 1 takes draw k (draw 0 is already at hand). */
             if (packed && jumps > 0) orc_draw_k(c, kc, ndraw++, x);
-            j = orc_jump(c, j, x, &sign, &lr);
+            j = orc_jump(c, j, x, &sign, &lr, pc);
             log_is = log_is + lr;
             hash = (hash ^ (uint32_t)j) * 16777619u;
             jumps = jumps + 1;
             /* R1: the new holding time uses the new state's rate; the
              * literal reading uses the state just left. */
-            const int64_t rate_state = (c->variant == ORC_LITERAL_RATE) ? from : j;
+            const int64_t rate_state = ((c->variant == ORC_LITERAL_RATE) ? from : j) +
+                                       (int64_t)pc * c->n;
             if (packed) {
                 t_next = orc_hold32_word(c, rate_state, x[0], t_next);
             } else {
@@ -702,7 +749,7 @@ static int orc_walk_core(const orc_ctx *c, int64_t row, orc_ctr kc, int level, i
                 t_next = orc_hold(c, rate_state, x, t_next);
             }
         }
-        g = c->dl[j] / (double)N;
+        g = dlp[j] / (double)N;
         eta2 = eta2 * exp(g / 2.0);
         if (step % 2 == 0) eta1 = eta1 * exp(g);
         if (src_on) {
@@ -715,10 +762,14 @@ static int orc_walk_core(const orc_ctx *c, int64_t row, orc_ctr kc, int level, i
             }
         }
         if (step % 2 == 0) {
-            /* Pair (X_{step-2}, X_{step-1}, X_step) of Eq. 7. */
-            double d0 = c->dl[x_prev2] / (double)N;
-            double d1 = c->dl[x_prev1] / (double)N;
-            double d2 = c->dl[j] / (double)N;
+            /* Pair (X_{step-2}, X_{step-1}, X_step) of Eq. 7.  Each point
+             * takes the piece of the pair's interval next to it (R19); the
+             * middle point, between intervals step-1 and step, the mean of
+             * both (one value when they share a piece). */
+            const double *dla = c->dl + (int64_t)((step - 2) / per) * c->n;
+            double d0 = dla[x_prev2] / (double)N;
+            double d1 = ((dla[x_prev1] + dlp[x_prev1]) / 2.0) / (double)N;
+            double d2 = dlp[j] / (double)N;
             log_f = log_f + (d0 / 2.0 + d1 + d2 / 2.0);
             log_c = log_c + (d0 + d2);
             diff = diff + ((d1 - d0 / 2.0) - d2 / 2.0);
@@ -740,6 +791,8 @@ static int orc_walk_core(const orc_ctx *c, int64_t row, orc_ctr kc, int level, i
             }
             y_times[step / (N / n_times) - 1] = y;
         }
+        /* R19: the pending jump time passes into the next piece. */
+        if (K > 1 && step % per == 0 && step < N) t_next = orc_cross(c, j, pc, t_next, step, N);
     }
     if (N == 1) {
         /* Level 0 has one interval and no pair: the fine exponent is

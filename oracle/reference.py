@@ -405,6 +405,52 @@ def _moments_from_kernels(ks, ku, dl, v, level: int, coarse: bool):
     return m1, m2
 
 
+def _functional_pieces(kernels, dls, c: np.ndarray, g: np.ndarray, per: int):
+    """_functional with a law per time piece (reading R19): the step over
+    interval k+1 (from grid point k to k+1) uses the kernel of its piece
+    k // per; grid point k takes half of its weight c_k from each adjacent
+    interval's piece (all of it at the ends 0 and N), so a point on a piece
+    boundary gets the mean of the two pieces' dl."""
+    n_steps = c.size - 1
+    piece = lambda interval: (interval - 1) // per  # interval = 1..N
+    w = np.exp(c[n_steps] * dls[piece(n_steps)]) * g
+    for k in range(n_steps - 1, -1, -1):
+        right = piece(k + 1)
+        w = kernels[right] @ w
+        if k == 0:
+            e = c[0] * dls[right]
+        else:
+            e = 0.5 * c[k] * (dls[piece(k)] + dls[right])
+        w = np.exp(e) * w
+    return w
+
+
+def level_moments_pieces(a_dense: np.ndarray, t: float, v: np.ndarray, level: int,
+                         coarse: bool, laws):
+    """level_moments for a walk whose law changes with time (reading R19):
+    ``laws`` holds K pairs (lam, q), pair p for the scaled times
+    [p/K, (p+1)/K); N = 2^level must be a multiple of K."""
+    n_steps = 1 << level
+    k_pieces = len(laws)
+    if n_steps % k_pieces:
+        raise ValueError("the grid must hold every piece boundary")
+    ks, ku, dls = [], [], []
+    for lam, q in laws:
+        g1, g2, dl = walk_generators(a_dense, t, lam, q)
+        ks.append(expm_pade13(g1 / n_steps))
+        ku.append(expm_pade13(g2 / n_steps))
+        dls.append(dl)
+    per = n_steps // k_pieces
+    v = np.asarray(v, dtype=np.float64)
+    cf, cc = _weights(level, coarse)
+    f = lambda kern, c, g: _functional_pieces(kern, dls, c, g, per)
+    if not coarse:
+        return f(ks, cf, v), f(ku, 2 * cf, v * v)
+    m1 = f(ks, cf, v) - f(ks, cc, v)
+    m2 = f(ku, 2 * cf, v * v) - 2.0 * f(ku, cf + cc, v * v) + f(ku, 2 * cc, v * v)
+    return m1, m2
+
+
 def brute_moments(a_dense: np.ndarray, t: float, v: np.ndarray, level: int, coarse: bool):
     """(E[Y], E[Y^2]) per start row by summing over every skeleton path
     (X_1, ..., X_N) in {0..n-1}^N with probability prod K(X_{k-1}, X_k)

@@ -58,7 +58,8 @@ class Ctx(ct.Structure):
                 ("alias_col", ct.c_void_p), ("alias_neg", ct.c_void_p), ("v", ct.c_void_p),
                 ("lr_keep", ct.c_void_p), ("lr_alias", ct.c_void_p), ("seed", ct.c_uint64),
                 ("precision", ct.c_int32), ("variant", ct.c_int32), ("max_jumps", ct.c_int64),
-                ("f", ct.c_void_p), ("t", ct.c_double)]
+                ("f", ct.c_void_p), ("t", ct.c_double), ("pieces", ct.c_int32),
+                ("pad_pieces", ct.c_int32)]
 
 
 def lib():
@@ -153,6 +154,8 @@ class Tables:
     lr_keep: np.ndarray = None   # proposal tables only: log(k/q) of the kept column
     lr_alias: np.ndarray = None  # ... and of the alias column
     lam: np.ndarray = None       # tilted clocks only: the walk's rates lambda_i
+    pieces: int = 1              # R19 time pieces: per-row arrays hold `pieces` blocks of n,
+                                 # entry arrays `pieces` blocks of nnz (build_tables_pieces)
 
 
 def build_tables(a, t: float, h=None, alpha: float = 0.1, clocks: bool = False) -> Tables:
@@ -216,6 +219,25 @@ def build_tables(a, t: float, h=None, alpha: float = 0.1, clocks: bool = False) 
                   alias_col, alias_neg, lr_keep, lr_alias, lam)
 
 
+def build_tables_pieces(a, t: float, hs, alpha: float = 0.1) -> Tables:
+    """Tilted-clock tables of a proposal that changes with time (reading
+    R19): ``hs`` holds K rows of h, row p for the piece [p/K, (p+1)/K) of
+    scaled time; piece p's tables are build_tables(a, t, hs[p], alpha,
+    clocks=True), stacked piece after piece."""
+    hs = np.asarray(hs, dtype=np.float32)
+    if hs.ndim != 2 or hs.shape[0] < 1:
+        raise ValueError("hs: K rows of n values")
+    parts = [build_tables(a, t, hs[p], alpha, clocks=True) for p in range(hs.shape[0])]
+    if len(parts) == 1:
+        return parts[0]
+    b0 = parts[0]
+    cat = lambda name: np.ascontiguousarray(np.concatenate([getattr(q, name) for q in parts]))
+    return Tables(b0.n, b0.row_ptr, b0.a_ii, b0.L, b0.deg, cat("dl"), cat("inv_rate"),
+                  cat("inv_rate32"), cat("dl32"), cat("thr"), cat("keep_col"), cat("keep_neg"),
+                  cat("alias_col"), cat("alias_neg"), cat("lr_keep"), cat("lr_alias"), cat("lam"),
+                  len(parts))
+
+
 class Walker:
     """Replays walks of Algorithm 2 on one matrix, time and right-hand side."""
 
@@ -237,7 +259,8 @@ class Walker:
                        _p(tb.keep_col).value, _p(tb.keep_neg).value, _p(tb.alias_col).value,
                        _p(tb.alias_neg).value, _p(self.v).value, lrk, lra, ct.c_uint64(seed),
                        precision, variant, max_jumps,
-                       _p(self.f).value if self.f is not None else None, float(t))
+                       _p(self.f).value if self.f is not None else None, float(t),
+                       tb.pieces, 0)
 
     def walk(self, row: int, rep: int, level: int, coarse: bool) -> WalkRec:
         r = WalkRec()
