@@ -288,13 +288,24 @@ def run_ours(args):
         plan.rebuild()
         with M.MLP(seed=3, stream=stream.cuda_stream) as net:
             net.learn_tilt(plan, v_in, seed=seed, pilot_walks=args.pilot, steps=args.mlp_steps,
-                           batch=args.mlp_batch, clocks=True, rounds=args.rounds)
+                           batch=args.mlp_batch, clocks=True, rounds=args.rounds,
+                           time_pieces=bool(args.time_pieces))
             mlp_launches[0] += net.launch_count()
-        learn_log.append(plan.learn_report())
+        learn_log.append(plan.learn_report() + (plan.tilt_pieces(),))
         if dist is not None:
-            h = torch.from_numpy(plan.export_h()).to(coll)
+            # rank 0's law on every rank: its time pieces, then its h
+            k = torch.tensor([plan.tilt_pieces()], dtype=torch.int64, device=coll)
+            dist.broadcast(k, 0)
+            k = int(k.item())
+            h = torch.zeros((k, plan.n), dtype=torch.float32, device=coll)
+            if rank == 0:
+                h.copy_(torch.from_numpy(plan.export_h().reshape(k, plan.n)))
             dist.broadcast(h, 0)
-            plan.set_tilt(h.cpu().numpy() if coll == "cpu" else h, 0.1, clocks=True)
+            hh = h.cpu().numpy() if coll == "cpu" else h
+            if k > 1:
+                plan.set_tilt_pieces(hh, 0.1)
+            else:
+                plan.set_tilt(hh.reshape(plan.n), 0.1, clocks=True)
         rc = plan.expmv(v_in, x_out, seed, allow_not_converged=True)
         levels, est = plan.stats()
         plan.set_tilt(None)
@@ -420,8 +431,11 @@ def run_ours(args):
                        "learning": {"rounds": args.rounds, "pilot_walks": args.pilot,
                                     "mlp_steps": args.mlp_steps, "mlp_batch": args.mlp_batch,
                                     "alpha": 0.1,
+                                    "time_piece_candidates": bool(args.time_pieces),
                                     "chosen_law_per_timed_step": [
-                                        c for c, _ in learn_log[args.warmup:args.warmup + args.steps]],
+                                        c for c, _, _ in learn_log[args.warmup:args.warmup + args.steps]],
+                                    "time_pieces_per_timed_step": [
+                                        k for _, _, k in learn_log[args.warmup:args.warmup + args.steps]],
                                     "pilot_var_per_walk_last_timed_step":
                                         learn_log[args.warmup + args.steps - 1][1]},
                        "l2": "flushed between steps (256 MB write outside the timed events)",
@@ -696,7 +710,7 @@ def run_learned_workload(args):
                 with M.MLP(seed=3, stream=st) as net:
                     loss = net.learn_tilt(plan, dv, seed=5 + rep, pilot_walks=args.pilot,
                                           steps=args.mlp_steps, batch=args.mlp_batch, clocks=True,
-                                          rounds=args.rounds)
+                                          rounds=args.rounds, time_pieces=bool(args.time_pieces))
                 torch.cuda.synchronize()
                 t_learn = time.perf_counter() - t0
                 chosen, pilot_var = plan.learn_report()
@@ -707,7 +721,8 @@ def run_learned_workload(args):
                              "est_rel_err": el, "converged": cl, "train_loss": loss,
                              "rel_err_vs_fp64": float(np.linalg.norm(xl - ref) / nref),
                              "level0_var_per_walk": var_l, "walk_steps_per_s": evl / tl,
-                             "pilot_var_per_walk": pilot_var, "chosen_law": chosen})
+                             "pilot_var_per_walk": pilot_var, "chosen_law": chosen,
+                             "time_pieces": plan.tilt_pieces()})
                 log(f"{name} learned run {rep}: {t_learn:.2f} + {tl:.2f} s, est {el:.3g}, "
                     f"converged {cl}")
                 plan.set_tilt(None)
@@ -803,7 +818,7 @@ def run_kernel_workload(args):
         with M.MLP(seed=3, stream=stream.cuda_stream) as net:
             net.learn_tilt(plan, dv, seed=5, pilot_walks=args.pilot, steps=args.mlp_steps,
                            batch=args.mlp_batch,
-                           clocks=True, rounds=args.rounds)
+                           clocks=True, rounds=args.rounds, time_pieces=bool(args.time_pieces))
     l2win = plan.l2_window()
     sums = torch.zeros(n, dtype=torch.float64, device="cuda")
     tot = torch.zeros(5, dtype=torch.float64, device="cuda")
@@ -1173,6 +1188,9 @@ def main():
                     help="rows per training step (128 per CTA of the fused training kernel)")
     ap.add_argument("--rounds", type=int, default=2,
                     help="pilot-train-install rounds of the learned proposal (mlmc_learn_tilt)")
+    ap.add_argument("--time-pieces", type=int, default=1, choices=[0, 1],
+                    help="1: laws that change with time (4 and 8 pieces of the scaled time) are "
+                         "candidates of the learned proposal too")
     ap.add_argument("--pilot", type=int, default=64,
                     help="first-round pilot walks per row of the learned proposal")
     ap.add_argument("--workload", choices=["tc", "batch", "learned", "precision", "kernel",

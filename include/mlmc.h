@@ -191,8 +191,10 @@ mlmc_status mlmc_plan_rebuild(mlmc_plan *plan);
  * once (the call synchronises the plan's stream to validate it). */
 mlmc_status mlmc_plan_set_proposal(mlmc_plan *plan, const float *h, double alpha);
 
-/* What a proposal tilts (mlmc_plan_set_tilt, mlmc_learn_tilt). */
-enum { MLMC_TILT_JUMPS = 1, MLMC_TILT_CLOCKS = 2 };
+/* What a proposal tilts (mlmc_plan_set_tilt, mlmc_learn_tilt).
+ * MLMC_TILT_TIME (mlmc_learn_tilt only, with both others): laws that change
+ * with time (mlmc_plan_set_tilt_pieces) are candidates too. */
+enum { MLMC_TILT_JUMPS = 1, MLMC_TILT_CLOCKS = 2, MLMC_TILT_TIME = 4 };
 
 /* Proposal with the jumps alone tilted (tilt = MLMC_TILT_JUMPS: exactly
  * mlmc_plan_set_proposal) or with the holding times tilted as well
@@ -216,6 +218,34 @@ enum { MLMC_TILT_JUMPS = 1, MLMC_TILT_CLOCKS = 2 };
  * lambda (48 bytes per row and 32 per entry in all). */
 mlmc_status mlmc_plan_set_tilt(mlmc_plan *plan, const float *h, double alpha, int32_t tilt);
 
+/* A tilted proposal that changes with time (the paper has none; it extends
+ * mlmc_plan_set_tilt with MLMC_TILT_JUMPS | MLMC_TILT_CLOCKS).  The scaled
+ * time s in [0, 1] is cut into `pieces` equal pieces [p/K, (p+1)/K); piece p
+ * has its own law from h + p n (h: K x n positive finite floats, host or
+ * device, piece-major): rates lambda_p, jump law q_p, d_p = t (a_ii +
+ * lambda_p), per-jump log(L/lambda_p) + log(k/q_p) as mlmc_plan_set_tilt
+ * defines them.  A pending jump time s that reaches the piece's end b is
+ * carried into the next piece at its rate, s -> b + (s - b) (1/lambda_next)
+ * / (1/lambda_now) in the walk's precision (the unused part of the
+ * exponential clock; infinite when a rate is 0), and the grid weights of
+ * Eq. 2 take each grid interval's own piece at both of its ends, so a grid
+ * point on a boundary gets the mean of the two pieces' d.  Every level still
+ * estimates, without bias, a Strang-type product that tends to exp(tA)v with
+ * weak order 2.  With h_p close to exp((1 - s_p) tA) v, the zero-variance
+ * h(s), the path weights telescope where a single h can only average over
+ * time.  K = 1 is mlmc_plan_set_tilt with tilted clocks.  K must be a power
+ * of two <= 16 and <= 2^l0 (every boundary a grid point of every level
+ * walked; mlmc_mlmcl / mlmc_trace / mlmc_trace_noalloc refuse levels whose
+ * grid misses one), on a backward-mode plan without a source term;
+ * intermediate times (mlmc_expmv_times) and batches refuse such a proposal.
+ * Tables: K sets (entries, row records, rates) plus one still threshold per
+ * row.  h = NULL returns to the plain walk.  Synchronises. */
+mlmc_status mlmc_plan_set_tilt_pieces(mlmc_plan *plan, const float *h, int32_t pieces, double alpha);
+
+/* The installed proposal's time pieces (1 for mlmc_plan_set_tilt's laws,
+ * 0 without a proposal or plan). */
+int32_t mlmc_plan_tilt_pieces(const mlmc_plan *plan);
+
 /* The tilted clocks' tables (after mlmc_plan_set_tilt with
  * MLMC_TILT_CLOCKS), as mlmc_export_tables exports the plain ones: lambda,
  * dl = t (a_ii + lambda), inv_rate = 1/(t lambda) (n doubles), their FP32
@@ -225,9 +255,15 @@ mlmc_status mlmc_plan_set_tilt(mlmc_plan *plan, const float *h, double alpha, in
 mlmc_status mlmc_export_tilt(const mlmc_plan *plan, double *lam, double *dl, double *inv_rate,
                              float *inv_rate32, float *dl32, int32_t *still32);
 
-/* The h of the plan's proposal (n floats, host or device), e.g. to give
- * every rank of a sharded solve the proposal one rank learned.
- * Synchronises. */
+/* The same for time piece `piece` of a proposal with time pieces (piece 0
+ * is mlmc_export_tilt); still32 is the row's threshold for the whole law. */
+mlmc_status mlmc_export_tilt_piece(const mlmc_plan *plan, int32_t piece, double *lam, double *dl,
+                                   double *inv_rate, float *inv_rate32, float *dl32,
+                                   int32_t *still32);
+
+/* The h of the plan's proposal (n floats, host or device; K x n with K =
+ * mlmc_plan_tilt_pieces time pieces), e.g. to give every rank of a sharded
+ * solve the proposal one rank learned.  Synchronises. */
 mlmc_status mlmc_export_h(const mlmc_plan *plan, float *h);
 
 /* Checkpoint and resume of a solve (the paper has no counterpart).  The
@@ -271,6 +307,12 @@ mlmc_status mlmc_plan_set_source(mlmc_plan *plan, const double *f);
 mlmc_status mlmc_export_proposal(const mlmc_plan *plan, uint32_t *thr, int32_t *keep_col,
                                  uint8_t *keep_neg, int32_t *alias_col, uint8_t *alias_neg,
                                  float *lr_keep, float *lr_alias);
+
+/* The proposal tables of time piece `piece` (piece 0 is
+ * mlmc_export_proposal). */
+mlmc_status mlmc_export_proposal_piece(const mlmc_plan *plan, int32_t piece, uint32_t *thr,
+                                       int32_t *keep_col, uint8_t *keep_neg, int32_t *alias_col,
+                                       uint8_t *alias_neg, float *lr_keep, float *lr_alias);
 
 /* x = exp(t A) v by Algorithm 1: a pilot of pilot_walks per row on levels
  * l0..l0+num_levels-1, Giles' sample sizes M_l (Eq. 11, read as
@@ -556,6 +598,12 @@ mlmc_status mlmc_learn_proposal(mlmc_plan *plan, mlmc_mlp *mlp, const double *v,
  * pilots draw from a stream keyed by a hash of `seed`, never the one
  * mlmc_expmv draws from with the same seed, so the installed law does not
  * depend on the walks that estimate x.  final_loss is the last round's.
+ * With tilt = MLMC_TILT_JUMPS | MLMC_TILT_CLOCKS | MLMC_TILT_TIME and
+ * l0 >= 1, one more law is walked and measured after the last round's: K =
+ * min(8, 2^l0) time pieces (mlmc_plan_set_tilt_pieces) with h_p the same
+ * Taylor value at the time left in the middle of piece p, sum_{m<=3}
+ * ((1 - s_p) t|N|)^m |v| / m! (+ 1e-3 max|v|); walked last, its tables are
+ * already built when it is the law installed.
  * Backward-mode plans only. */
 mlmc_status mlmc_learn_tilt(mlmc_plan *plan, mlmc_mlp *mlp, const double *v, uint64_t seed,
                             int64_t pilot_walks, int32_t steps, int32_t batch, float lr,
@@ -566,8 +614,9 @@ mlmc_status mlmc_learn_tilt(mlmc_plan *plan, mlmc_mlp *mlp, const double *v, uin
  * first min(cap, count)) = the per-walk variance at l0 of pilot k.  Jumps
  * only: rounds + 1 pilots (the paper's walk, then the tilt trained in each
  * round).  Tilted clocks: rounds + 3 (the warm starts a = 1/2, 3/4, 1, then
- * the tilt trained in each round).  *chosen (may be NULL) = the index of the
- * law installed (-1 before any learning). */
+ * the tilt trained in each round), plus the time-piece law last when
+ * MLMC_TILT_TIME is set and l0 >= 1.  *chosen
+ * (may be NULL) = the index of the law installed (-1 before any learning). */
 mlmc_status mlmc_plan_learn_report(const mlmc_plan *plan, int32_t *chosen, double *var, int32_t cap,
                                    int32_t *count);
 

@@ -623,67 +623,115 @@ mlmc_status mlmc_plan_set_proposal(mlmc_plan* p, const float* h, double alpha) {
   return mlmc_plan_set_tilt(p, h, alpha, MLMC_TILT_JUMPS);
 }
 
-mlmc_status mlmc_plan_set_tilt(mlmc_plan* p, const float* h, double alpha, int32_t tilt) {
+namespace {
+
+// mlmc_plan_set_tilt and mlmc_plan_set_tilt_pieces: `pieces` laws, h holding
+// pieces x n values (piece k's h at k n).
+mlmc_status set_tilt_impl(mlmc_plan* p, const float* h, double alpha, int32_t tilt, int32_t pieces,
+                          const char* who) {
   if (!p) return fail(MLMC_ERR_INVALID_ARG, "NULL plan");
   if (!h) {
     p->proposal_active = false;
     p->clock_tilt = false;
+    p->pieces = 1;
     p->sched.proposal = MLMC_PLAIN;
     return MLMC_OK;
   }
   if (tilt != MLMC_TILT_JUMPS && tilt != (MLMC_TILT_JUMPS | MLMC_TILT_CLOCKS))
     return fail(MLMC_ERR_INVALID_ARG,
-                "mlmc_plan_set_tilt: tilt must be MLMC_TILT_JUMPS or MLMC_TILT_JUMPS | MLMC_TILT_CLOCKS");
+                std::string(who) + ": tilt must be MLMC_TILT_JUMPS or MLMC_TILT_JUMPS | MLMC_TILT_CLOCKS");
   if (p->source_active)
-    return fail(MLMC_ERR_INVALID_ARG, "mlmc_plan_set_proposal: the plan has a source term");
+    return fail(MLMC_ERR_INVALID_ARG, std::string(who) + ": the plan has a source term");
   if (!(alpha > 0.0) || !(alpha <= 1.0))
     return fail(MLMC_ERR_INVALID_ARG, "alpha must be in (0, 1]: the proposal mixes in the plain law");
-  if (!p->d_is_block) {
-    // [proposal entries | Meta32 | Meta64 | still thresholds | lambda]
+  if (pieces > 1) {
+    if (forward_mode(p))
+      return fail(MLMC_ERR_INVALID_ARG, std::string(who) + ": time pieces need a backward-mode plan");
+    if (pieces > kMaxPieces || (pieces & (pieces - 1)) != 0)
+      return fail(MLMC_ERR_INVALID_ARG, std::string(who) + ": pieces must be a power of two <= " +
+                                            std::to_string(kMaxPieces));
+    if (pieces > (1 << p->l0))
+      return fail(MLMC_ERR_INVALID_ARG,
+                  std::string(who) + ": every piece boundary must lie on the grid of every level "
+                  "walked, so pieces <= 2^l0 (l0 = " + std::to_string(p->l0) + ")");
+  }
+  const size_t k = static_cast<size_t>(pieces);
+  const size_t nh = static_cast<size_t>(p->n) * k;
+  // h must be positive and finite on every row (checked on a host copy,
+  // taken before anything of the plan changes: h may be the plan's own).
+  std::vector<float> hh(nh);
+  MLMC_CUDA(cudaMemcpyAsync(hh.data(), h, sizeof(float) * nh, cudaMemcpyDefault, p->stream), "read h");
+  MLMC_CUDA(cudaStreamSynchronize(p->stream), "synchronize");
+  for (size_t i = 0; i < nh; ++i)
+    if (!(hh[i] > 0.0f) || !std::isfinite(hh[i]))
+      return fail(MLMC_ERR_INVALID_ARG, "h must be positive and finite (row " +
+                                            std::to_string(i % static_cast<size_t>(p->n)) +
+                                            (pieces > 1 ? ", piece " + std::to_string(i / p->n) : "") + ")");
+  if (p->is_pieces_cap < pieces) {
+    // [proposal entries | Meta32 | Meta64 | still thresholds | lambda], the
+    // entries, records and rates once per piece
+    cudaFree(p->d_is_block);
+    cudaFree(p->d_h);
+    p->d_is_block = nullptr;
+    p->d_h = nullptr;
+    p->is_pieces_cap = 0;
+    p->proposal_active = false;
+    p->sched.proposal = MLMC_PLAIN;
     auto up = [](size_t b) { return (b + 255) & ~size_t{255}; };
     const size_t n = static_cast<size_t>(p->n);
-    const size_t be = up(sizeof(AliasEntryIS) * static_cast<size_t>(p->nnz > 0 ? p->nnz : 1));
-    const size_t b32 = up(sizeof(Meta32) * n), b64 = up(sizeof(Meta64) * n);
-    const size_t bs = up(sizeof(int32_t) * n), bl = up(sizeof(double) * n);
+    const size_t be = up(sizeof(AliasEntryIS) * static_cast<size_t>(p->nnz > 0 ? p->nnz : 1) * k);
+    const size_t b32 = up(sizeof(Meta32) * n * k), b64 = up(sizeof(Meta64) * n * k);
+    const size_t bs = up(sizeof(int32_t) * n), bl = up(sizeof(double) * n * k);
     MLMC_CUDA(dev_alloc(&p->d_is_block, be + b32 + b64 + bs + bl), "alloc proposal tables");
+    MLMC_CUDA(dev_alloc(&p->d_h, n * k), "alloc h");
     p->d_alias_is = reinterpret_cast<AliasEntryIS*>(p->d_is_block);
     p->d_meta32_t = reinterpret_cast<Meta32*>(p->d_is_block + be);
     p->d_meta64_t = reinterpret_cast<Meta64*>(p->d_is_block + be + b32);
     p->d_still32_t = reinterpret_cast<int32_t*>(p->d_is_block + be + b32 + b64);
     p->d_lam = reinterpret_cast<double*>(p->d_is_block + be + b32 + b64 + bs);
+    p->is_pieces_cap = pieces;
   }
-  if (!p->d_h) MLMC_CUDA(dev_alloc(&p->d_h, static_cast<size_t>(p->n)), "alloc h");
-  MLMC_CUDA(cudaMemcpyAsync(p->d_h, h, sizeof(float) * p->n, cudaMemcpyDefault, p->stream), "copy h");
-  // h must be positive and finite on every row (checked on the host copy).
-  std::vector<float> hh(p->n);
-  MLMC_CUDA(cudaMemcpyAsync(hh.data(), p->d_h, sizeof(float) * p->n, cudaMemcpyDeviceToHost,
-                            p->stream), "read h");
-  MLMC_CUDA(cudaStreamSynchronize(p->stream), "synchronize");
-  for (int64_t i = 0; i < p->n; ++i)
-    if (!(hh[i] > 0.0f) || !std::isfinite(hh[i]))
-      return fail(MLMC_ERR_INVALID_ARG, "h must be positive and finite (row " + std::to_string(i) + ")");
+  MLMC_CUDA(cudaMemcpyAsync(p->d_h, hh.data(), sizeof(float) * nh, cudaMemcpyHostToDevice, p->stream),
+            "copy h");
   p->alpha = alpha;
   p->clock_tilt = (tilt & MLMC_TILT_CLOCKS) != 0;
+  p->pieces = pieces;
   MLMC_CUDA(launch_build_is_tables(p), "proposal table build");
+  MLMC_CUDA(cudaStreamSynchronize(p->stream), "synchronize");  // hh is read by the copy above
   p->proposal_active = true;
   p->sched.proposal = MLMC_LEARNED;
   return MLMC_OK;
 }
 
-mlmc_status mlmc_export_tilt(const mlmc_plan* pc, double* lam, double* dl, double* inv_rate,
-                             float* inv_rate32, float* dl32, int32_t* still32) {
+}  // namespace
+
+mlmc_status mlmc_plan_set_tilt(mlmc_plan* p, const float* h, double alpha, int32_t tilt) {
+  return set_tilt_impl(p, h, alpha, tilt, 1, "mlmc_plan_set_tilt");
+}
+
+mlmc_status mlmc_plan_set_tilt_pieces(mlmc_plan* p, const float* h, int32_t pieces, double alpha) {
+  if (pieces < 1) return fail(MLMC_ERR_INVALID_ARG, "mlmc_plan_set_tilt_pieces: pieces must be >= 1");
+  return set_tilt_impl(p, h, alpha, MLMC_TILT_JUMPS | MLMC_TILT_CLOCKS, pieces,
+                       "mlmc_plan_set_tilt_pieces");
+}
+
+mlmc_status mlmc_export_tilt_piece(const mlmc_plan* pc, int32_t piece, double* lam, double* dl,
+                                   double* inv_rate, float* inv_rate32, float* dl32, int32_t* still32) {
   mlmc_plan* p = const_cast<mlmc_plan*>(pc);
   if (!p) return fail(MLMC_ERR_INVALID_ARG, "NULL plan");
   if (!p->proposal_active || !p->clock_tilt)
     return fail(MLMC_ERR_INVALID_ARG, "mlmc_export_tilt: no proposal with tilted clocks on this plan");
+  if (piece < 0 || piece >= p->pieces)
+    return fail(MLMC_ERR_INVALID_ARG, "mlmc_export_tilt_piece: piece out of range");
   const size_t n = static_cast<size_t>(p->n);
+  const size_t off = static_cast<size_t>(piece) * n;
   std::vector<Meta32> m32(n);
   std::vector<Meta64> m64(n);
   std::vector<double> lm(n);
   std::vector<int32_t> st(n);
-  MLMC_CUDA(cudaMemcpyAsync(m32.data(), p->d_meta32_t, sizeof(Meta32) * n, cudaMemcpyDeviceToHost, p->stream), "copy");
-  MLMC_CUDA(cudaMemcpyAsync(m64.data(), p->d_meta64_t, sizeof(Meta64) * n, cudaMemcpyDeviceToHost, p->stream), "copy");
-  MLMC_CUDA(cudaMemcpyAsync(lm.data(), p->d_lam, sizeof(double) * n, cudaMemcpyDeviceToHost, p->stream), "copy");
+  MLMC_CUDA(cudaMemcpyAsync(m32.data(), p->d_meta32_t + off, sizeof(Meta32) * n, cudaMemcpyDeviceToHost, p->stream), "copy");
+  MLMC_CUDA(cudaMemcpyAsync(m64.data(), p->d_meta64_t + off, sizeof(Meta64) * n, cudaMemcpyDeviceToHost, p->stream), "copy");
+  MLMC_CUDA(cudaMemcpyAsync(lm.data(), p->d_lam + off, sizeof(double) * n, cudaMemcpyDeviceToHost, p->stream), "copy");
   if (p->sched.precision != MLMC_FP64)
     MLMC_CUDA(cudaMemcpyAsync(st.data(), p->d_still32_t, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, p->stream), "copy");
   MLMC_CUDA(cudaStreamSynchronize(p->stream), "synchronize");
@@ -698,17 +746,25 @@ mlmc_status mlmc_export_tilt(const mlmc_plan* pc, double* lam, double* dl, doubl
   return MLMC_OK;
 }
 
-mlmc_status mlmc_export_proposal(const mlmc_plan* pc, uint32_t* thr, int32_t* keep_col,
-                                 uint8_t* keep_neg, int32_t* alias_col, uint8_t* alias_neg,
-                                 float* lr_keep, float* lr_alias) {
+mlmc_status mlmc_export_tilt(const mlmc_plan* pc, double* lam, double* dl, double* inv_rate,
+                             float* inv_rate32, float* dl32, int32_t* still32) {
+  return mlmc_export_tilt_piece(pc, 0, lam, dl, inv_rate, inv_rate32, dl32, still32);
+}
+
+mlmc_status mlmc_export_proposal_piece(const mlmc_plan* pc, int32_t piece, uint32_t* thr,
+                                       int32_t* keep_col, uint8_t* keep_neg, int32_t* alias_col,
+                                       uint8_t* alias_neg, float* lr_keep, float* lr_alias) {
   mlmc_plan* p = const_cast<mlmc_plan*>(pc);
   if (!p) return fail(MLMC_ERR_INVALID_ARG, "NULL plan");
   if (!p->proposal_active) return fail(MLMC_ERR_INVALID_ARG, "no proposal set on this plan");
+  if (piece < 0 || piece >= p->pieces)
+    return fail(MLMC_ERR_INVALID_ARG, "mlmc_export_proposal_piece: piece out of range");
   std::vector<Meta32> m32(p->n);
   std::vector<AliasEntryIS> al(p->nnz > 0 ? p->nnz : 1);
   MLMC_CUDA(cudaMemcpyAsync(m32.data(), p->d_meta32, sizeof(Meta32) * p->n, cudaMemcpyDeviceToHost, p->stream), "copy");
   if (p->nnz > 0)
-    MLMC_CUDA(cudaMemcpyAsync(al.data(), p->d_alias_is, sizeof(AliasEntryIS) * p->nnz, cudaMemcpyDeviceToHost, p->stream), "copy");
+    MLMC_CUDA(cudaMemcpyAsync(al.data(), p->d_alias_is + static_cast<int64_t>(piece) * p->nnz,
+                              sizeof(AliasEntryIS) * p->nnz, cudaMemcpyDeviceToHost, p->stream), "copy");
   MLMC_CUDA(cudaStreamSynchronize(p->stream), "synchronize");
   for (int64_t i = 0; i < p->n; ++i)
     for (int32_t b = 0; b < m32[i].deg; ++b) {
@@ -725,11 +781,24 @@ mlmc_status mlmc_export_proposal(const mlmc_plan* pc, uint32_t* thr, int32_t* ke
   return MLMC_OK;
 }
 
+mlmc_status mlmc_export_proposal(const mlmc_plan* pc, uint32_t* thr, int32_t* keep_col,
+                                 uint8_t* keep_neg, int32_t* alias_col, uint8_t* alias_neg,
+                                 float* lr_keep, float* lr_alias) {
+  return mlmc_export_proposal_piece(pc, 0, thr, keep_col, keep_neg, alias_col, alias_neg, lr_keep,
+                                    lr_alias);
+}
+
+int32_t mlmc_plan_tilt_pieces(const mlmc_plan* p) {
+  if (!p || !p->proposal_active) return 0;
+  return p->pieces;
+}
+
 mlmc_status mlmc_export_h(const mlmc_plan* pc, float* h) {
   mlmc_plan* p = const_cast<mlmc_plan*>(pc);
   if (!p || !h) return fail(MLMC_ERR_INVALID_ARG, "NULL argument");
   if (!p->proposal_active) return fail(MLMC_ERR_INVALID_ARG, "mlmc_export_h: no proposal set on this plan");
-  MLMC_CUDA(cudaMemcpyAsync(h, p->d_h, sizeof(float) * p->n, cudaMemcpyDefault, p->stream), "copy h");
+  MLMC_CUDA(cudaMemcpyAsync(h, p->d_h, sizeof(float) * p->n * static_cast<size_t>(p->pieces),
+                            cudaMemcpyDefault, p->stream), "copy h");
   MLMC_CUDA(cudaStreamSynchronize(p->stream), "synchronize");
   return MLMC_OK;
 }
@@ -807,6 +876,9 @@ mlmc_status mlmc_mlmcl(mlmc_plan* p, int32_t level, int32_t coarse, int64_t rep_
     return fail(MLMC_ERR_INVALID_ARG, "level must be in [0,24] (>= 1 when coarse)");
   if (p->source_active && (level < 1 || (coarse && level < 2)))
     return fail(MLMC_ERR_INVALID_ARG, "with a source term the level must be >= 1 (>= 2 when coarse)");
+  if (!pieces_fit(p, level, coarse != 0))
+    return fail(MLMC_ERR_INVALID_ARG, "the proposal's time pieces need 2^level (coarse: 2^(level-1)) "
+                                      "to be a multiple of the piece count");
   if (rep_begin < 0 || reps < 0 || rep_begin > (1ll << 56) || reps > (1ll << 56) - rep_begin)
     return fail(MLMC_ERR_INVALID_ARG, "replica range out of [0, 2^56)");
   WalkLaunch w;
@@ -832,6 +904,8 @@ static int max_times(const mlmc_plan* p) { return p->sched.precision == MLMC_FP6
 static mlmc_status check_times(const mlmc_plan* p, int32_t n_times, int32_t level) {
   if (forward_mode(p)) return fail(MLMC_ERR_INVALID_ARG, "intermediate times: backward-mode plans only");
   if (p->source_active) return fail(MLMC_ERR_INVALID_ARG, "intermediate times: remove the source term first");
+  if (p->proposal_active && p->pieces > 1)
+    return fail(MLMC_ERR_INVALID_ARG, "intermediate times: not with a proposal of time pieces");
   if (n_times < 2 || n_times > max_times(p) || (n_times & (n_times - 1)) != 0)
     return fail(MLMC_ERR_INVALID_ARG, "n_times must be a power of two in [2, " +
                                           std::to_string(max_times(p)) + "]");
@@ -881,6 +955,9 @@ mlmc_status mlmc_trace(mlmc_plan* p, int32_t level, int32_t coarse, int64_t rep_
     return fail(MLMC_ERR_INVALID_ARG, "level must be in [0,24] (>= 1 when coarse)");
   if (p->source_active && (level < 1 || (coarse && level < 2)))
     return fail(MLMC_ERR_INVALID_ARG, "with a source term the level must be >= 1 (>= 2 when coarse)");
+  if (!pieces_fit(p, level, coarse != 0))
+    return fail(MLMC_ERR_INVALID_ARG, "the proposal's time pieces need 2^level (coarse: 2^(level-1)) "
+                                      "to be a multiple of the piece count");
   if (rep_begin < 0 || reps < 0 || rep_begin > (1ll << 56) || reps > (1ll << 56) - rep_begin)
     return fail(MLMC_ERR_INVALID_ARG, "replica range out of [0, 2^56)");
   double* scratch = nullptr;
@@ -1131,6 +1208,14 @@ mlmc_status mlmc_expmv_sum(mlmc_plan* p, const double* v, double* total, uint64_
 }
 
 
+// The kind of law a saved state was walked with: 0 plain, 1 tilted jumps,
+// 2 tilted clocks, 2 + K tilted clocks with K > 1 time pieces.
+static int32_t proposal_code(const mlmc_plan* p) {
+  if (!p->proposal_active) return 0;
+  if (!p->clock_tilt) return 1;
+  return p->pieces > 1 ? 2 + p->pieces : 2;
+}
+
 mlmc_status mlmc_plan_save_state(const mlmc_plan* p, void* buf, size_t cap, size_t* bytes) {
   if (!p || !bytes) return fail(MLMC_ERR_INVALID_ARG, "NULL argument");
   if (sharded(p)) return fail(MLMC_ERR_INVALID_ARG, "mlmc_plan_save_state: not available on a sharded plan");
@@ -1156,7 +1241,7 @@ mlmc_status mlmc_plan_save_state(const mlmc_plan* p, void* buf, size_t cap, size
   h.row_count = p->ctl_row_count;
   h.seed = p->ctl_seed;
   h.source = p->source_active ? 1 : 0;
-  h.proposal = p->proposal_active ? (p->clock_tilt ? 2 : 1) : 0;
+  h.proposal = proposal_code(p);
   std::memcpy(out, &h, sizeof(h));
   out += sizeof(h);
   for (int k = 0; k < nl; ++k) {
@@ -1185,7 +1270,7 @@ mlmc_status mlmc_plan_load_state(mlmc_plan* p, const void* buf, size_t bytes) {
     return fail(MLMC_ERR_INVALID_ARG, "mlmc_plan_load_state: not a saved state");
   if (h.n != p->n || h.nnz != p->nnz || h.t != p->t || h.l0 != p->l0 ||
       h.precision != p->sched.precision || h.mode != p->sched.mode ||
-      h.source != (p->source_active ? 1 : 0) || h.proposal != (p->proposal_active ? (p->clock_tilt ? 2 : 1) : 0))
+      h.source != (p->source_active ? 1 : 0) || h.proposal != proposal_code(p))
     return fail(MLMC_ERR_INVALID_ARG,
                 "mlmc_plan_load_state: the plan differs from the saved one (matrix size, t, l0, "
                 "precision, mode, source or proposal)");

@@ -508,6 +508,9 @@ mlmc_status mlmc_batch_expmv(mlmc_batch* b, const double* const* v, double* cons
                                       std::chrono::duration<double>(b->sched.time_budget_s));
   const int K = b->nprob;
   const int64_t L = b->max_levels;
+  for (int k = 0; k < K; ++k)
+    if (b->plans[k]->proposal_active && b->plans[k]->pieces > 1)
+      return bfail(MLMC_ERR_INVALID_ARG, "mlmc_batch_expmv: proposals with time pieces are not batched");
   BATCH_CUDA(cudaEventRecord(b->ev0, b->caller), "event");
   BATCH_CUDA(cudaStreamWaitEvent(b->stream, b->ev0, 0), "wait");
   for (int k = 0; k < K; ++k) {

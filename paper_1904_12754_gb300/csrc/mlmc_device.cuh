@@ -255,4 +255,44 @@ __device__ __forceinline__ int32_t still_index32(float inv_rate, int lane) {
   return lo;
 }
 
+// still_index32 for a law with K time pieces (reading R19): the first
+// holding time E / rate_0, carried over each piece boundary b = (p+1)/K it
+// reaches as b + (s - b) * ir[p+1] / ir[p] (infinite when either inverse
+// rate is), must reach s = 1.  The carried time does not decrease with E,
+// so the passing indices still form a prefix.
+__device__ __forceinline__ bool still_pieces32(float u, const float* ir, int k_pieces, float inv_k) {
+  float s = __fmul_rn(neglog32(u), ir[0]);
+  for (int p = 0; p + 1 < k_pieces; ++p) {
+    const float b = __fmul_rn(static_cast<float>(p + 1), inv_k);
+    if (!(s >= b)) break;
+    s = (isinf(ir[p]) || isinf(ir[p + 1])) ? __int_as_float(0x7f800000)
+                                           : __fmaf_rn(__fsub_rn(s, b), __fdiv_rn(ir[p + 1], ir[p]), b);
+  }
+  return !(s < 1.0f);
+}
+
+__device__ __forceinline__ int32_t still_index32_pieces(const float* ir, int k_pieces, float inv_k,
+                                                        int lane) {
+  int32_t lo = -1, hi = 1 << 23;
+  while (hi - lo > 1) {
+    const int64_t width = hi - lo;
+    const int32_t c = lo + static_cast<int32_t>((static_cast<int64_t>(lane + 1) * width) / 33);
+    bool pass;
+    if (c <= lo) {
+      pass = true;
+    } else if (c >= hi) {
+      pass = false;
+    } else {
+      const float u = __fmul_rn(__uint2float_rn(2u * static_cast<uint32_t>(c) + 1u), 0x1p-24f);
+      pass = still_pieces32(u, ir, k_pieces, inv_k);
+    }
+    const int t = __popc(__ballot_sync(0xFFFFFFFFu, pass));
+    const int32_t c_last = __shfl_sync(0xFFFFFFFFu, c, t > 0 ? t - 1 : 0);
+    const int32_t c_first_fail = __shfl_sync(0xFFFFFFFFu, c, t < 32 ? t : 31);
+    if (t > 0 && c_last > lo) lo = c_last;
+    if (t < 32 && c_first_fail < hi) hi = c_first_fail;
+  }
+  return lo;
+}
+
 }  // namespace mlmc

@@ -108,6 +108,12 @@ struct mlmc_plan {
   int32_t* d_still32_t = nullptr;
   double* d_lam = nullptr;
   bool clock_tilt = false;
+  // Time pieces of the installed proposal (reading R19; 1: one law): every
+  // part of d_is_block but the still thresholds and d_h hold `pieces`
+  // consecutive copies, piece k's k n (entries: k nnz) after piece 0's.
+  // is_pieces_cap: the pieces d_is_block and d_h have room for.
+  int32_t pieces = 1;
+  int32_t is_pieces_cap = 0;
   // Rows the table builds give a block each (stored length 32..8192): the
   // list (d_heavy), its device count and, once classified, its host count
   // (-1 before).
@@ -260,16 +266,24 @@ inline const void* walk_meta(const mlmc_plan* p, bool fp64) {
     return fp64 ? static_cast<const void*>(p->d_meta64_t) : static_cast<const void*>(p->d_meta32_t);
   return fp64 ? static_cast<const void*>(p->d_meta64) : static_cast<const void*>(p->d_meta32);
 }
+// Whether the installed proposal's time pieces fit the grids of a walk at
+// `level` (coarse: and of level - 1): every piece boundary a grid point.
+inline bool pieces_fit(const mlmc_plan* p, int level, bool coarse) {
+  if (!p->proposal_active || p->pieces <= 1) return true;
+  const int lv = coarse ? level - 1 : level;
+  return lv >= 0 && lv <= 30 && (1 << lv) % p->pieces == 0;
+}
 inline const int32_t* walk_still32(const mlmc_plan* p) {
   return (p->proposal_active && p->clock_tilt) ? p->d_still32_t : p->d_still32;
 }
 // The L2 window of proposal walks: their alias entries and row records.
 inline size_t is_window_bytes(const mlmc_plan* p, bool fp64) {
-  const size_t ent = static_cast<size_t>(p->nnz > 0 ? p->nnz : 1);
+  const size_t k = static_cast<size_t>(p->is_pieces_cap > 0 ? p->is_pieces_cap : 1);
+  const size_t ent = static_cast<size_t>(p->nnz > 0 ? p->nnz : 1) * k;
   size_t b = (sizeof(AliasEntryIS) * ent + 255) & ~size_t{255};
   if (p->clock_tilt) {
-    b += (sizeof(Meta32) * static_cast<size_t>(p->n) + 255) & ~size_t{255};
-    if (fp64) b += sizeof(Meta64) * static_cast<size_t>(p->n);
+    b += (sizeof(Meta32) * static_cast<size_t>(p->n) * k + 255) & ~size_t{255};
+    if (fp64) b += sizeof(Meta64) * static_cast<size_t>(p->n) * k;
   }
   return b;
 }
@@ -333,5 +347,7 @@ cudaError_t launch_finalize(mlmc_plan* p, int num_levels, double* x, double* nor
 // x_times[(k-1) n + i] = sum_l S_l,k[i] / M_l for k = 1..n_times-1.
 cudaError_t launch_finalize_times(mlmc_plan* p, int num_levels, int n_times, double* x_times);
 constexpr int kMaxTimesAll = 16;
+// Time pieces of a proposal (reading R19): at most this many.
+constexpr int kMaxPieces = 16;
 
 }  // namespace mlmc

@@ -734,6 +734,22 @@ __global__ void k_abs_float32(int64_t n, const double* __restrict__ in, float* _
   }
 }
 
+// Time-piece warm starts (reading R19): row p of h (K x n) is the
+// third-order Taylor value of exp(tau t|N|)|v| at tau = 1 - (p + 1/2)/K, the
+// time left at the middle of piece p,
+//   h_p,i = |v_i| + tau c1_i + tau^2 c2_i + tau^3 c3_i + f,  c_m = (t|N|)^m |v| / m!.
+__global__ void k_piece_h(int64_t n, int k_pieces, const float* __restrict__ absv,
+                          const float* __restrict__ c1, const float* __restrict__ c2,
+                          const float* __restrict__ c3, float f, float* __restrict__ h) {
+  const int64_t total = n * k_pieces;
+  for (int64_t q = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; q < total;
+       q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t p = q / n, i = q - p * n;
+    const float tau = 1.0f - (static_cast<float>(p) + 0.5f) / static_cast<float>(k_pieces);
+    h[q] = fmaf(tau, fmaf(tau, fmaf(tau, c3[i], c2[i]), c1[i]), absv[i]) + f;
+  }
+}
+
 // h_i = (a_i + fa)^alpha (|b_i| + fb)^(1 - alpha) in FP32.
 __global__ void k_power_product(int64_t n, const float* __restrict__ a, const double* __restrict__ b,
                                 float fa, float fb, float alpha, float* __restrict__ h) {
@@ -815,6 +831,8 @@ __global__ void k_mlp_features(int64_t n, const int64_t* __restrict__ row_ptr,
 // (part[gridDim.x + b]); fixed grid and reduction order, so the pilot's
 // variance is the same number on every run.
 constexpr int kStatBlocks = 256;
+// The largest time-piece warm start the learning tries (reading R19).
+constexpr int32_t kLearnMaxPieces = 8;
 __global__ void __launch_bounds__(256) k_pilot_stats(int64_t n, double scale, double* __restrict__ sums,
                                                      double* __restrict__ part) {
   __shared__ double s_sq[8], s_mx[8];
@@ -1189,14 +1207,18 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
                             double alpha, int32_t tilt, int32_t rounds, float* final_loss) {
   if (!p || !m || !v || pilot_walks < 1 || rounds < 1 || rounds > 8)
     return mfail(MLMC_ERR_INVALID_ARG, "mlmc_learn_tilt: bad argument");
-  if (tilt != MLMC_TILT_JUMPS && tilt != (MLMC_TILT_JUMPS | MLMC_TILT_CLOCKS))
-    return mfail(MLMC_ERR_INVALID_ARG, "mlmc_learn_tilt: tilt must be MLMC_TILT_JUMPS or "
-                                       "MLMC_TILT_JUMPS | MLMC_TILT_CLOCKS");
+  if (tilt != MLMC_TILT_JUMPS && tilt != (MLMC_TILT_JUMPS | MLMC_TILT_CLOCKS) &&
+      tilt != (MLMC_TILT_JUMPS | MLMC_TILT_CLOCKS | MLMC_TILT_TIME))
+    return mfail(MLMC_ERR_INVALID_ARG, "mlmc_learn_tilt: tilt must be MLMC_TILT_JUMPS, "
+                                       "MLMC_TILT_JUMPS | MLMC_TILT_CLOCKS or "
+                                       "MLMC_TILT_JUMPS | MLMC_TILT_CLOCKS | MLMC_TILT_TIME");
   // The targets are backward value estimates (x-hat per start row); a
   // forward walk's value would be the adjoint problem's.
   if (p->sched.mode != MLMC_BACKWARD)
     return mfail(MLMC_ERR_INVALID_ARG, "mlmc_learn_tilt: backward-mode plans only");
   const bool clocks = (tilt & MLMC_TILT_CLOCKS) != 0;
+  const bool timed = (tilt & MLMC_TILT_TIME) != 0;
+  const int32_t tilt_law = tilt & (MLMC_TILT_JUMPS | MLMC_TILT_CLOCKS);  // one law: set_tilt's
   // The pilots draw from their own stream (a hash of seed), never from the
   // one mlmc_expmv draws with the same seed: the tilt must not depend on the
   // walks that later estimate x.
@@ -1206,26 +1228,32 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
   learn_seed ^= learn_seed >> 31;
   const bool was = p->proposal_active;
   const bool was_clocks = p->clock_tilt;
+  const int32_t was_pieces = p->pieces;
   const double was_alpha = p->alpha;
-  // The plan's proposal before the call (h), put back if the call fails.
+  // The plan's proposal before the call (h of every time piece), put back if
+  // the call fails.
   float* saved_h = nullptr;
   if (was && p->d_h) {
-    if (cudaMalloc(&saved_h, sizeof(float) * p->n) != cudaSuccess ||
-        cudaMemcpyAsync(saved_h, p->d_h, sizeof(float) * p->n, cudaMemcpyDeviceToDevice,
-                        p->stream) != cudaSuccess) {
+    const size_t nh = sizeof(float) * static_cast<size_t>(p->n) * static_cast<size_t>(was_pieces);
+    if (cudaMalloc(&saved_h, nh) != cudaSuccess ||
+        cudaMemcpyAsync(saved_h, p->d_h, nh, cudaMemcpyDeviceToDevice, p->stream) != cudaSuccess) {
       cudaFree(saved_h);
       return mfail(MLMC_ERR_CUDA, "mlmc_learn_tilt: saving the plan's proposal failed");
     }
   }
   auto restore = [&]() {
     if (was && saved_h) {
-      if (mlmc_plan_set_tilt(p, saved_h, was_alpha,
-                             was_clocks ? (MLMC_TILT_JUMPS | MLMC_TILT_CLOCKS) : MLMC_TILT_JUMPS) !=
-          MLMC_OK)
+      const mlmc_status rs =
+          was_clocks ? mlmc_plan_set_tilt_pieces(p, saved_h, was_pieces, was_alpha)
+                     : mlmc_plan_set_tilt(p, saved_h, was_alpha, MLMC_TILT_JUMPS);
+      if (rs != MLMC_OK) {
         p->proposal_active = p->clock_tilt = false;  // the paper's walk: always consistent
+        p->pieces = 1;
+      }
     } else {
       p->proposal_active = was;
       p->clock_tilt = was_clocks;
+      p->pieces = was_pieces;
     }
   };
   // The first pilot uses the paper's walk (jumps only) or, with tilted
@@ -1237,14 +1265,17 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
   float* y = nullptr;
   float* z = nullptr;
   float* h = nullptr;
-  float* pv = nullptr;  // v, k^m v (m = 1..4), T_3 and two Taylor terms (8 x n floats)
-  float* best_h = nullptr;        // the tilt with the smallest pilot variance so far
+  float* pv = nullptr;  // v, k^m v (m = 1..4), T_3, |v|, -, the Taylor terms c_1..c_3 (11 x n)
+  float* hp = nullptr;            // a time-piece warm start (K x n)
+  float* best_h = nullptr;        // the tilt with the smallest pilot variance so far (K x n)
+  int32_t best_pieces = 1;
   double* xwarm = nullptr;        // x-hat of the best warm start's pilot
   double* stats = nullptr;        // a pilot's per-block partial sums (k_pilot_stats)
   __nv_bfloat16* wfeat = nullptr;
   float* wy = nullptr;
   auto cleanup = [&]() {
     cudaFree(best_h);
+    cudaFree(hp);
     cudaFree(xwarm);
     cudaFree(stats);
     cudaFree(wfeat);
@@ -1275,8 +1306,10 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
   LP_CUDA(cudaMalloc(&y, sizeof(float) * p->n), "alloc");
   LP_CUDA(cudaMalloc(&z, sizeof(float) * p->n), "alloc");
   LP_CUDA(cudaMalloc(&h, sizeof(float) * p->n), "alloc");
-  LP_CUDA(cudaMalloc(&pv, sizeof(float) * p->n * 8), "alloc");
-  LP_CUDA(cudaMalloc(&best_h, sizeof(float) * p->n), "alloc");
+  LP_CUDA(cudaMalloc(&pv, sizeof(float) * p->n * 11), "alloc");
+  const int32_t max_warm_pieces = timed ? std::min(kLearnMaxPieces, 1 << std::min(p->l0, 8)) : 1;
+  LP_CUDA(cudaMalloc(&best_h, sizeof(float) * p->n * max_warm_pieces), "alloc");
+  if (max_warm_pieces > 1) LP_CUDA(cudaMalloc(&hp, sizeof(float) * p->n * max_warm_pieces), "alloc");
   LP_CUDA(cudaMalloc(&xwarm, sizeof(double) * p->n), "alloc");
   LP_CUDA(cudaMalloc(&stats, sizeof(double) * 2 * kStatBlocks), "alloc");
   LP_CUDA(cudaMemcpyAsync(dv, v, sizeof(double) * p->n, cudaMemcpyDefault, p->stream), "copy v");
@@ -1286,21 +1319,22 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
   // Features (fixed over the rounds: they use the paper's jump law).
   k_to_float32<<<g, 256, 0, p->stream>>>(p->n, dv, pv);
   p->launches++;
-  for (int mstep = 1; mstep <= 4; ++mstep)
+  for (int mstep = 1; mstep <= 4; ++mstep) {
     k_jump_mean<<<gw, 256, 0, p->stream>>>(p->n, p->d_row_ptr, p->d_col, p->d_val, p->d_lii,
                                            pv + (mstep - 1) * p->n, pv + mstep * p->n);
     p->launches++;
+  }
   {
+    // T_3 in slot 5, |v| in slot 6 and the terms c_m = (t|N|)^m |v| / m! in
+    // slots 7 + m
     float* t3 = pv + 5 * p->n;
-    float* ta = pv + 6 * p->n;
-    float* tb = pv + 7 * p->n;
-    k_abs_float32<<<g, 256, 0, p->stream>>>(p->n, dv, ta, t3);
+    k_abs_float32<<<g, 256, 0, p->stream>>>(p->n, dv, pv + 6 * p->n, t3);
     p->launches++;
     for (int mstep = 1; mstep <= 3; ++mstep) {
       k_abs_taylor_step<<<gw, 256, 0, p->stream>>>(p->n, p->d_row_ptr, p->d_col, p->d_val,
-                                                  p->t / mstep, ta, tb, t3);
+                                                  p->t / mstep, pv + (mstep == 1 ? 6 : 6 + mstep) * p->n,
+                                                  pv + (7 + mstep) * p->n, t3);
       p->launches++;
-      std::swap(ta, tb);
     }
   }
   k_mlp_features<<<gw, 256, 0, p->stream>>>(p->n, p->d_row_ptr, p->d_col, p->d_meta64, p->d_lii, p->t,
@@ -1399,14 +1433,18 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
   p->learn_var.clear();
   p->learn_choice = -1;
   int64_t next_rep = 0;
-  auto consider = [&](double var, bool keep_h) -> cudaError_t {
+  // src: the h (pieces x n) of the law the pilot walked with, kept if its
+  // variance is the smallest so far (nullptr: the law installed last, which
+  // stays installed when it wins).
+  auto consider = [&](double var, const float* src, int32_t pieces) -> cudaError_t {
     p->learn_var.push_back(var);
     if (!(var < best_var)) return cudaSuccess;
     best_var = var;
     p->learn_choice = static_cast<int32_t>(p->learn_var.size()) - 1;
-    return keep_h ? cudaMemcpyAsync(best_h, h, sizeof(float) * p->n, cudaMemcpyDeviceToDevice,
-                                    p->stream)
-                  : cudaSuccess;
+    best_pieces = pieces;
+    return src ? cudaMemcpyAsync(best_h, src, sizeof(float) * p->n * static_cast<size_t>(pieces),
+                                 cudaMemcpyDeviceToDevice, p->stream)
+               : cudaSuccess;
   };
   // The exponent of x-hat in the training targets (jumps only: 1).
   float target_alpha = 1.0f;
@@ -1427,13 +1465,13 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
                                                 static_cast<float>(1e-3 * vmax + 1e-30), forms[k], h);
       p->launches++;
       LP_CUDA(cudaGetLastError(), "warm start");
-      st = mlmc_plan_set_tilt(p, h, alpha, tilt);
+      st = mlmc_plan_set_tilt(p, h, alpha, tilt_law);
       if (st != MLMC_OK) break;
       double xmax = 0.0, var = 0.0;
       LP_CUDA(pilot(next_rep, pilot_walks, &xmax, &var), "warm pilot");
       next_rep += pilot_walks;
       const bool better = var < best_var;
-      LP_CUDA(consider(var, true), "keep tilt");
+      LP_CUDA(consider(var, h, 1), "keep tilt");
       if (better) {
         target_alpha = forms[k];
         xmax_warm = xmax;
@@ -1457,7 +1495,7 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
       LP_CUDA(pilot(next_rep, round_walks, &xmax, &var), "pilot walks");
       next_rep += round_walks;
       // (round 0 without clocks walks the paper's law: nothing to keep)
-      LP_CUDA(consider(var, round > 0), "keep tilt");
+      LP_CUDA(consider(var, round > 0 ? h : nullptr, 1), "keep tilt");
     }
     // Targets a log(|x-hat| + 1e-3 max|x-hat|) + (1 - a) log(|v| + 1e-3
     // max|v|) (rows the pilot never reached do not get arbitrarily small h).
@@ -1480,19 +1518,45 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
     k_exp_h<<<g, 256, 0, p->stream>>>(p->n, z, h);
     p->launches++;
     LP_CUDA(cudaGetLastError(), "h");
-    st = mlmc_plan_set_tilt(p, h, alpha, tilt);
+    st = mlmc_plan_set_tilt(p, h, alpha, tilt_law);
   }
   if (st == MLMC_OK) {
     // The last round's tilt is measured like the others; if an earlier law
     // had the smaller variance, that one is installed instead.
     double xmax = 0.0, var = 0.0;
     LP_CUDA(pilot(next_rep, 4 * pilot_walks, &xmax, &var), "final pilot");
-    const int32_t last = static_cast<int32_t>(p->learn_var.size());
-    LP_CUDA(consider(var, false), "final");
-    if (p->learn_choice < 0)
+    next_rep += 4 * pilot_walks;
+    int32_t last = static_cast<int32_t>(p->learn_var.size());
+    // (kept: a time-piece law may be installed after it)
+    LP_CUDA(consider(var, timed && max_warm_pieces > 1 ? h : nullptr, 1), "final");
+    if (timed && max_warm_pieces > 1) {
+      // The time-piece warm start (reading R19), walked last so that, when
+      // it wins, its tables are the ones already built: K = min(8, 2^l0)
+      // pieces, h_p the Taylor value of exp((1 - s_p) t|N|)|v| at the middle
+      // s_p of piece p, the zero-variance h(s) = exp((1-s)tA)v that one law
+      // can only average over time.  More pieces never measured a larger
+      // variance, so only the largest is tried.
+      const int32_t k_p = max_warm_pieces;
+      k_piece_h<<<g, 256, 0, p->stream>>>(p->n, k_p, pv + 6 * p->n, pv + 8 * p->n, pv + 9 * p->n,
+                                          pv + 10 * p->n, static_cast<float>(1e-3 * vmax + 1e-30), hp);
+      p->launches++;
+      LP_CUDA(cudaGetLastError(), "time-piece warm start");
+      st = mlmc_plan_set_tilt_pieces(p, hp, k_p, alpha);
+      if (st == MLMC_OK) {
+        double xk = 0.0, vk = 0.0;
+        LP_CUDA(pilot(next_rep, pilot_walks, &xk, &vk), "time-piece pilot");
+        last = static_cast<int32_t>(p->learn_var.size());
+        LP_CUDA(consider(vk, nullptr, k_p), "time-piece law");
+      }
+    }
+    if (st != MLMC_OK) {
+      // reported below
+    } else if (p->learn_choice < 0)
       st = mfail(MLMC_ERR_NUMERIC, "mlmc_learn_tilt: no pilot measured a finite variance");
+    else if (p->learn_choice != last && best_pieces > 1)
+      st = mlmc_plan_set_tilt_pieces(p, best_h, best_pieces, alpha);
     else if (p->learn_choice != last)
-      st = mlmc_plan_set_tilt(p, p->learn_choice == 0 && !clocks ? nullptr : best_h, alpha, tilt);
+      st = mlmc_plan_set_tilt(p, p->learn_choice == 0 && !clocks ? nullptr : best_h, alpha, tilt_law);
   }
   if (st != MLMC_OK) {
     const std::string msg = mlmc_last_error();

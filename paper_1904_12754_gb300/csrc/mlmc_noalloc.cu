@@ -96,6 +96,10 @@ extern "C" mlmc_status mlmc_trace_noalloc(mlmc_plan* p, int32_t level, int32_t c
     return noalloc_fail(MLMC_ERR_INVALID_ARG, "mlmc_trace_noalloc: replica range out of [0, 2^56)");
   if (p->sched.mode == MLMC_FORWARD)
     return noalloc_fail(MLMC_ERR_INVALID_ARG, "mlmc_trace_noalloc: backward-mode plans only");
+  if (!pieces_fit(p, level, coarse != 0))
+    return noalloc_fail(MLMC_ERR_INVALID_ARG,
+                        "mlmc_trace_noalloc: the proposal's time pieces need 2^level (coarse: "
+                        "2^(level-1)) to be a multiple of the piece count");
   if (p->n > kNoAllocMaxRows)
     return noalloc_fail(MLMC_ERR_INVALID_ARG,
                         "mlmc_trace_noalloc: n = " + std::to_string(p->n) +

@@ -634,6 +634,24 @@ __global__ void __launch_bounds__(256) k_still_index(int64_t n, const Meta32* __
   }
 }
 
+// The same with time pieces (reading R19): row i's records of the K pieces
+// are meta[p n + i]; screened rows are those whose first piece has
+// 1/(t lambda) >= 1.
+__global__ void __launch_bounds__(256) k_still_index_pieces(int64_t n, const Meta32* __restrict__ meta,
+                                                            int k_pieces, int32_t* __restrict__ still) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+  const float inv_k = __fdiv_rn(1.0f, static_cast<float>(k_pieces));
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x >> 5) + (threadIdx.x >> 5); i < n;
+       i += warps) {
+    float ir[kMaxPieces];
+#pragma unroll
+    for (int p = 0; p < kMaxPieces; ++p) ir[p] = p < k_pieces ? meta[p * n + i].inv_rate : 1.0f;
+    const int32_t k = ir[0] >= 1.0f ? still_index32_pieces(ir, k_pieces, inv_k, lane) : -1;
+    if (lane == 0) still[i] = k;
+  }
+}
+
 // The plan's long rows (once: the matrix structure does not change).
 cudaError_t classify_heavy_rows(mlmc_plan* p) {
   if (p->heavy_count >= 0) return cudaSuccess;
@@ -701,23 +719,34 @@ cudaError_t launch_build_is_tables(mlmc_plan* p) {
   constexpr int kBuildBlock = 64;
   cudaError_t err = classify_heavy_rows(p);
   if (err != cudaSuccess) return err;
-  k_build_is_tables<<<grid_for(p, p->n, kBuildBlock), kBuildBlock, 0, p->stream>>>(
-      p->n, p->d_row_ptr, p->d_col, p->d_val, p->d_lii, p->d_h, p->alpha, p->d_alias_is,
-      p->clock_tilt, p->t, p->d_meta32_t, p->d_meta64_t, p->d_lam);
-  p->launches++;
-  if (p->heavy_count > 0) {
-    static std::atomic<uint64_t> attr{0};
-    err = ensure_dynamic_smem(k_build_is_tables_heavy, static_cast<int>(heavy_smem_is(kHeavyHi)), attr);
-    if (err != cudaSuccess) return err;
-    k_build_is_tables_heavy<<<heavy_grid(p), kHeavyBlock, heavy_smem_is(p->heavy_cap), p->stream>>>(
-        p->d_heavy, p->d_heavy_count, p->heavy_cap, p->d_row_ptr, p->d_col, p->d_val, p->d_lii, p->d_h,
-        p->alpha, p->d_alias_is, p->clock_tilt, p->t, p->d_meta32_t, p->d_meta64_t, p->d_lam);
+  // One table set per time piece (one piece without a time-dependent law):
+  // piece k's h, entries, records and rates sit k n (k nnz) after piece 0's.
+  const int pieces = p->clock_tilt ? p->pieces : 1;
+  for (int k = 0; k < pieces; ++k) {
+    const int64_t kn = static_cast<int64_t>(k) * p->n, ke = static_cast<int64_t>(k) * p->nnz;
+    k_build_is_tables<<<grid_for(p, p->n, kBuildBlock), kBuildBlock, 0, p->stream>>>(
+        p->n, p->d_row_ptr, p->d_col, p->d_val, p->d_lii, p->d_h + kn, p->alpha, p->d_alias_is + ke,
+        p->clock_tilt, p->t, p->d_meta32_t + kn, p->d_meta64_t + kn, p->d_lam + kn);
     p->launches++;
+    if (p->heavy_count > 0) {
+      static std::atomic<uint64_t> attr{0};
+      err = ensure_dynamic_smem(k_build_is_tables_heavy, static_cast<int>(heavy_smem_is(kHeavyHi)), attr);
+      if (err != cudaSuccess) return err;
+      k_build_is_tables_heavy<<<heavy_grid(p), kHeavyBlock, heavy_smem_is(p->heavy_cap), p->stream>>>(
+          p->d_heavy, p->d_heavy_count, p->heavy_cap, p->d_row_ptr, p->d_col, p->d_val, p->d_lii,
+          p->d_h + kn, p->alpha, p->d_alias_is + ke, p->clock_tilt, p->t, p->d_meta32_t + kn,
+          p->d_meta64_t + kn, p->d_lam + kn);
+      p->launches++;
+    }
   }
   if (p->clock_tilt && p->sched.precision != MLMC_FP64) {
     const int64_t blocks = (p->n + 7) / 8;
     const int grid = static_cast<int>(blocks < p->num_sms * 16 ? blocks : p->num_sms * 16);
-    k_still_index<<<grid > 0 ? grid : 1, 256, 0, p->stream>>>(p->n, p->d_meta32_t, p->d_still32_t);
+    if (pieces > 1)
+      k_still_index_pieces<<<grid > 0 ? grid : 1, 256, 0, p->stream>>>(p->n, p->d_meta32_t, pieces,
+                                                                      p->d_still32_t);
+    else
+      k_still_index<<<grid > 0 ? grid : 1, 256, 0, p->stream>>>(p->n, p->d_meta32_t, p->d_still32_t);
     p->launches++;
   }
   return cudaGetLastError();

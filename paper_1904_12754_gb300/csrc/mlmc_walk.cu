@@ -83,6 +83,7 @@ struct WalkArgs {
   const void* f_walk;      // source vector in the walk precision (source walks only)
   double t;                // the time t (source walks only)
   const int32_t* still32;  // FP32: per-row still threshold index (still_index32)
+  int pieces;              // proposal walks: time pieces K of the law (1: one law)
   int n_times;             // intermediate-time walks: output times (T), else 0
   double* sum_times;       // [(T-1) x n] per-row sums of the samples at t k/T, k < T
   double* trace_times;     // trace: [(T-1)] samples per record (or null)
@@ -109,6 +110,8 @@ struct Prec<false> {
   __device__ static T add(T a, T b) { return __fadd_rn(a, b); }
   __device__ static T sub(T a, T b) { return __fsub_rn(a, b); }
   __device__ static T fma(T a, T b, T c) { return __fmaf_rn(a, b, c); }
+  __device__ static T div(T a, T b) { return __fdiv_rn(a, b); }
+  __device__ static T inf() { return __int_as_float(0x7f800000); }
   __device__ static T from_int(int x) { return static_cast<float>(x); }
   __device__ static T ex(T a) { return expf(a); }
   __device__ static T exm1(T a) { return expm1f(a); }
@@ -126,6 +129,8 @@ struct Prec<true> {
   __device__ static T add(T a, T b) { return __dadd_rn(a, b); }
   __device__ static T sub(T a, T b) { return __dsub_rn(a, b); }
   __device__ static T fma(T a, T b, T c) { return __fma_rn(a, b, c); }
+  __device__ static T div(T a, T b) { return __ddiv_rn(a, b); }
+  __device__ static T inf() { return __longlong_as_double(0x7ff0000000000000ll); }
   __device__ static T from_int(int x) { return static_cast<double>(x); }
   __device__ static T ex(T a) { return exp(a); }
   __device__ static T exm1(T a) { return expm1(a); }
@@ -240,6 +245,7 @@ struct ItemArgs {
   double t;               // the time t (source walks only)
   int64_t n, nnz;         // table sizes (checked build)
   const int32_t* still32; // FP32: per-row still threshold index
+  int pieces;             // proposal walks: time pieces K (1: one law)
   int n_times;            // intermediate times (T), 0 without
   double* sum_times;
   double* trace_times;
@@ -447,7 +453,7 @@ __device__ __forceinline__ typename Prec<FP64>::T simpson_segment(
 // Adds the item's sum of Y to a.sum_y[row] (one atomic) and its totals to
 // `tot`.
 template <bool FP64, bool COARSE, bool TRACE, bool IS, class Keys, bool SRC = false,
-          bool TIMES = false>
+          bool TIMES = false, bool PIECES = false>
 __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, int64_t row,
                                           int64_t r_lo, int64_t r_hi,
                                           LaneTotals<typename Prec<FP64>::T>& tot,
@@ -468,19 +474,41 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
   const Meta m0 = load_meta(meta, row);
   const T dl0 = static_cast<T>(m0.dl);
   const T inv_rate0 = static_cast<T>(m0.inv_rate);
+  // Time pieces (proposal walks, R19): piece p's row records and alias
+  // entries follow piece p-1's, n and nnz apart; a pending jump time that
+  // reaches the current piece's end b_next is carried into the next piece.
+  static_assert(!PIECES || (IS && !SRC && !TIMES), "time pieces: proposal walks without source or times");
+  const int n_pieces = PIECES ? a.pieces : 1;
+  const int g_per = n_grid / n_pieces;  // fine grid points per piece (K divides N)
+  const T inv_pieces = P::div(static_cast<T>(1), P::from_int(n_pieces));  // exact: K = 2^k
+  const T b_first = n_pieces > 1 ? inv_pieces : P::inf();
   // Rows whose walks are short (t L_row <= 1: few events per walk, the
   // first jump and the end usually fall in the same iteration) are screened;
   // the others run one event per lane per iteration without screening.
+  // (FP64 walks with time pieces are not screened: their screening tests
+  // the first holding time before any carry-over.)
   constexpr int kWays = static_cast<int>(kScreenWays);  // FP64 screening: walks per lane per round
-  const bool screened_row = static_cast<T>(m0.inv_rate) >= static_cast<T>(1);
+  const bool screened_row = static_cast<T>(m0.inv_rate) >= static_cast<T>(1) &&
+                            !(FP64 && n_pieces > 1);
   // FP32: a screened walk never jumps exactly when its first uniform's index
   // is <= the row's threshold index (computed once per row with the tables).
   const int32_t still_max = (FP64 || !screened_row) ? 0 : __ldg(a.still32 + row);
   // A walk that never jumps stays at the row for the whole interval: its
   // sample is 0 above l0 and v_row e^{dl_row} at l0 (E_f = dl_row exactly
   // as the grid weights sum to 1), the same for every such walk.
+  // With time pieces E_f is the mean of the row's d over the pieces (every
+  // boundary is a grid point).
   T y_still = 0;
-  if (!COARSE) y_still = P::mul(static_cast<T>(__ldg(vv + row)), P::ex(dl0));
+  if (!COARSE) {
+    T dl_still = dl0;
+    if (PIECES && n_pieces > 1) {
+      T sum = dl0;
+      for (int pp = 1; pp < n_pieces; ++pp)
+        sum = P::add(sum, static_cast<T>(load_meta(meta + static_cast<int64_t>(pp) * a.n, row).dl));
+      dl_still = P::mul(sum, inv_pieces);
+    }
+    y_still = P::mul(static_cast<T>(__ldg(vv + row)), P::ex(dl_still));
+  }
   // Source term: the sample also gets t/(3N) times the fine Simpson sum
   // minus, above l0, 2t/(3N) times the coarse one (level l-1's rule on the
   // even grid points).  A walk that never jumps has a fixed source part.
@@ -534,6 +562,8 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
   // the jump's words; `fresh`: claimed, first holding time not drawn yet.
   T s_pend = 0;
   bool fresh = false;
+  int pc = 0;          // time piece of the walk (proposal walks)
+  T b_next = b_first;  // its end (infinite in the last piece)
   // Intermediate times: output k < T at fine grid point k * t_stride.
   const int t_stride = TIMES ? n_grid / a.n_times : 1;
   const int n_out = TIMES ? a.n_times - 1 : 0;
@@ -556,6 +586,8 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
     hash = 2166136261u;
     src_f = 0;
     src_c = 0;
+    pc = 0;
+    b_next = b_first;
   };
   // Source term: add the Simpson sums of the segment (kprev, b] held in
   // state j (sign neg) before the exponent sums move past it.
@@ -637,7 +669,8 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
     Meta mnext{};
     if (IS) {
       const uint4* ep = reinterpret_cast<const uint4*>(
-          static_cast<const AliasEntryIS*>(a.alias) + m.start + bucket);
+          static_cast<const AliasEntryIS*>(a.alias) + (PIECES ? static_cast<int64_t>(pc) * a.nnz : 0) +
+          m.start + bucket);
       const uint4 e0 = __ldg(ep);
       const uint2 e1 = __ldg(reinterpret_cast<const uint2*>(ep + 1));
       const bool keep = xw < e0.x;
@@ -658,10 +691,38 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
     neg ^= pick >> 31;
     j = static_cast<int32_t>(pick & kColMask);
     if (TRACE) hash = (hash ^ static_cast<uint32_t>(j)) * 16777619u;
-    m = IS ? load_meta(meta, j) : mnext;
+    m = IS ? load_meta(meta + (PIECES ? static_cast<int64_t>(pc) * a.n : 0), j) : mnext;
     s = s_new;
     ++e;
     return true;
+  };
+  // R19: carry the pending jump time s_at over every piece boundary it
+  // reaches: s_at = b + (s_at - b) * (1/rate_next) / (1/rate_now) (infinite
+  // when either rate is 0), the grid points up to b count with the piece's
+  // d and the boundary point gets the mean of both pieces' d.
+  auto carry = [&](T& s_at) {
+    if constexpr (PIECES) {
+      while (pc + 1 < n_pieces && s_at >= b_next) {
+        const Meta mn = load_meta(meta + static_cast<int64_t>(pc + 1) * a.n, j);
+        const T ir = static_cast<T>(m.inv_rate), irn = static_cast<T>(mn.inv_rate);
+        s_at = (isinf(ir) || isinf(irn)) ? P::inf()
+                                          : P::fma(P::sub(s_at, b_next), P::div(irn, ir), b_next);
+        const int gb = (pc + 1) * g_per;
+        const T dlo = static_cast<T>(m.dl);
+        const T half = P::mul(P::sub(static_cast<T>(mn.dl), dlo), static_cast<T>(0.5));
+        if (COARSE) {
+          // gb is even: K divides the coarse grid too
+          acc = P::add(P::fma(P::from_int((gb >> 1) - (kprev >> 1)), dlo, acc), half);
+          acc_d = P::sub(P::fma(P::from_int(-(kprev & 1)), dlo, acc_d), half);
+        } else {
+          acc = P::add(P::fma(P::from_int(gb - kprev), dlo, acc), half);
+        }
+        kprev = gb;
+        m = mn;
+        ++pc;
+        b_next = pc + 1 < n_pieces ? P::mul(P::from_int(pc + 1), inv_pieces) : P::inf();
+      }
+    }
   };
   // Sample of a walk that ended at s = 1 after e >= 1 jumps, from its
   // exponents: x1 = E_f (l0) or E_c (above), plus the proposal's log-ratio;
@@ -926,6 +987,7 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
             const uint32_t slot = k & (kCap - 1);
             start_walk(q->r[slot]);
             s_pend = P::mul(neglog32(uniform32(q->first[slot])), static_cast<T>(m0.inv_rate));
+            carry(s_pend);
             live = true;
           }
         }
@@ -945,6 +1007,7 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
               finish(2, false);
             } else {
               s_pend = P::add(s, P::mul(neglog32(uniform32(x.x)), static_cast<T>(m.inv_rate)));
+              carry(s_pend);
               if (!(s_pend < static_cast<T>(1))) finish(0, false);
             }
           }
@@ -969,7 +1032,8 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
       if (live) {
         const uint4 x = keys.draw(make_uint4(c_lo, row32, e, c_hi));
         if constexpr (FP64) {
-          const T s_new = P::add(s, P::mul(P::neglog(P::uniform(x)), static_cast<T>(m.inv_rate)));
+          T s_new = P::add(s, P::mul(P::neglog(P::uniform(x)), static_cast<T>(m.inv_rate)));
+          carry(s_new);
           if (!(s_new < static_cast<T>(1))) {
             finish(0, true);
           } else if (static_cast<int64_t>(e) >= a.max_jumps) {
@@ -992,6 +1056,7 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
             const uint4 xk = k == 0 ? x : keys.draw(make_uint4(c_lo, row32, e, c_hi));
             if (fresh) {
               s_pend = P::add(s, P::mul(neglog32(uniform32(xk.y)), static_cast<T>(m.inv_rate)));
+              carry(s_pend);
               fresh = false;
             }
             if (!(s_pend < static_cast<T>(1))) {
@@ -1007,6 +1072,7 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
               break;
             }
             s_pend = P::add(s, P::mul(neglog32(uniform32(xk.x)), static_cast<T>(m.inv_rate)));
+            carry(s_pend);
             if (!(s_pend < static_cast<T>(1))) {
               status = 0;
               break;
@@ -1055,7 +1121,8 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
   }
 }
 
-template <bool FP64, bool COARSE, bool TRACE, bool IS, bool SRC = false, bool TIMES = false>
+template <bool FP64, bool COARSE, bool TRACE, bool IS, bool SRC = false, bool TIMES = false,
+          bool PIECES = false>
 __global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk(const __grid_constant__ WalkArgs a) {
   using T = typename Prec<FP64>::T;
   const int lane = threadIdx.x & 31;
@@ -1078,6 +1145,7 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk(const __grid_constan
   ia.n = a.n;
   ia.nnz = a.nnz;
   ia.still32 = a.still32;
+  ia.pieces = a.pieces;
   ia.n_times = a.n_times;
   ia.sum_times = a.sum_times;
   ia.trace_times = a.trace_times;
@@ -1105,7 +1173,7 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4) k_walk(const __grid_constan
     const int64_t chunk = static_cast<int64_t>(item) - rel * a.chunks_per_row;
     const int64_t r_lo = chunk * a.chunk;
     const int64_t r_hi = min(r_lo + a.chunk, a.reps);
-    walk_item<FP64, COARSE, TRACE, IS, KeysFromParam, SRC, TIMES>(ia, KeysFromParam{&a.rk},
+    walk_item<FP64, COARSE, TRACE, IS, KeysFromParam, SRC, TIMES, PIECES>(ia, KeysFromParam{&a.rk},
                                                                        a.row_begin + rel, r_lo,
                                                                        r_hi, tot, wc, q, eq, ta,
                                                                        lane);
@@ -1198,6 +1266,7 @@ __global__ void __launch_bounds__(256, FP64 ? 3 : 4)
     ia.n = sg.n;
     ia.nnz = sg.nnz;
     ia.still32 = sg.still32;
+    ia.pieces = 1;
     ia.n_times = 0;
     ia.sum_times = nullptr;
     ia.trace_times = nullptr;
@@ -1491,9 +1560,10 @@ cudaError_t launch_to_float(mlmc_plan* p, const double* in, float* out) {
   return cudaGetLastError();
 }
 
-template <bool FP64, bool COARSE, bool TRACE, bool IS, bool SRC, bool TIMES = false>
+template <bool FP64, bool COARSE, bool TRACE, bool IS, bool SRC, bool TIMES = false,
+          bool PIECES = false>
 cudaError_t launch_one(mlmc_plan* p, const WalkArgs& args, int block, cudaStream_t stream) {
-  auto kern = k_walk<FP64, COARSE, TRACE, IS, SRC, TIMES>;
+  auto kern = k_walk<FP64, COARSE, TRACE, IS, SRC, TIMES, PIECES>;
   int per_sm = 0;
   cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, 0);
   if (err != cudaSuccess) return err;
@@ -1530,6 +1600,7 @@ cudaError_t dispatch_is(mlmc_plan* p, const WalkArgs& a, int block, bool is, boo
   if (a.n_times > 1)
     return is ? launch_one<FP64, COARSE, TRACE, true, false, true>(p, a, block, st)
               : launch_one<FP64, COARSE, TRACE, false, false, true>(p, a, block, st);
+  if (is && a.pieces > 1) return launch_one<FP64, COARSE, TRACE, true, false, false, true>(p, a, block, st);
   return is ? launch_one<FP64, COARSE, TRACE, true, false>(p, a, block, st)
             : launch_one<FP64, COARSE, TRACE, false, false>(p, a, block, st);
 }
@@ -1654,6 +1725,7 @@ cudaError_t launch_walk_core(mlmc_plan* p, const WalkLaunch& w, const void* v_wa
                                : static_cast<const void*>(p->d_fused);
   a.v_walk = v_walk;
   a.still32 = walk_still32(p);
+  a.pieces = p->proposal_active ? p->pieces : 1;
   const bool src = f_walk != nullptr;
   if (src) {
     a.f_walk = f_walk;

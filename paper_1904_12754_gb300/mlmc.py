@@ -21,7 +21,7 @@ MLMC_ERR_EXCHANGE = 7
 FP64, FP32_KAHAN = 0, 1
 BACKWARD, FORWARD = 0, 1
 PLAIN, LEARNED = 0, 1
-TILT_JUMPS, TILT_CLOCKS = 1, 2
+TILT_JUMPS, TILT_CLOCKS, TILT_TIME = 1, 2, 4
 
 _STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "NOT_CONVERGED",
            5: "WALK_LIMIT", 6: "NUMERIC", 7: "EXCHANGE"}
@@ -112,6 +112,11 @@ def load(build_if_missing: bool = False):
     lib.mlmc_plan_set_proposal.argtypes = [P, P, D]
     lib.mlmc_plan_set_tilt.argtypes = [P, P, D, I32]
     lib.mlmc_export_tilt.argtypes = [P] + [P] * 6
+    lib.mlmc_plan_set_tilt_pieces.argtypes = [P, P, I32, D]
+    lib.mlmc_plan_tilt_pieces.argtypes = [P]
+    lib.mlmc_plan_tilt_pieces.restype = I32
+    lib.mlmc_export_tilt_piece.argtypes = [P, I32] + [P] * 6
+    lib.mlmc_export_proposal_piece.argtypes = [P, I32] + [P] * 7
     lib.mlmc_export_h.argtypes = [P, P]
     lib.mlmc_plan_learn_report.argtypes = [P, ct.POINTER(I32), P, I32, ct.POINTER(I32)]
     lib.mlmc_shard_buffer_doubles.argtypes = [P]
@@ -146,6 +151,7 @@ def load(build_if_missing: bool = False):
                  "mlmc_export_tables", "mlmc_batch_create", "mlmc_batch_expmv",
                  "mlmc_batch_stats", "mlmc_batch_info", "mlmc_batch_autotune",
                  "mlmc_plan_set_proposal", "mlmc_plan_set_tilt", "mlmc_export_tilt",
+                 "mlmc_plan_set_tilt_pieces", "mlmc_export_tilt_piece", "mlmc_export_proposal_piece",
                  "mlmc_export_h", "mlmc_plan_learn_report", "mlmc_shard_range",
                  "mlmc_plan_set_shard",
                  "mlmc_plan_set_source", "mlmc_plan_l2_window",
@@ -404,11 +410,34 @@ class Plan:
         _check(self._lib.mlmc_plan_set_tilt(self._h, _ptr(h) if h is not None else None,
                                             float(alpha), tilt))
 
+    def set_tilt_pieces(self, h, alpha: float = 0.1):
+        """Tilted proposal with time pieces: h of shape (K, n) (numpy or a
+        contiguous torch tensor), row p the h of the scaled times
+        [p/K, (p+1)/K); None = plain walk."""
+        if h is None:
+            _check(self._lib.mlmc_plan_set_tilt_pieces(self._h, None, 1, float(alpha)))
+            return
+        if isinstance(h, np.ndarray):
+            h = np.ascontiguousarray(h, dtype=np.float32)
+        elif hasattr(h, "dtype") and str(h.dtype) != "torch.float32":
+            raise TypeError("h must be float32")
+        k = int(h.shape[0]) if len(h.shape) == 2 else 1
+        if len(h.shape) == 2 and int(h.shape[1]) != self.n:
+            raise ValueError("h: K rows of n values")
+        _need(h, 4 * self.n * k, "h")
+        _check(self._lib.mlmc_plan_set_tilt_pieces(self._h, _ptr(h), k, float(alpha)))
+
+    def tilt_pieces(self) -> int:
+        """Time pieces of the installed proposal (0 without one)."""
+        return int(self._lib.mlmc_plan_tilt_pieces(self._h))
+
     def export_h(self) -> np.ndarray:
-        """The h of the plan's proposal (float32, n)."""
-        h = np.zeros(self.n, np.float32)
+        """The h of the plan's proposal (float32, n; (K, n) with K > 1 time
+        pieces)."""
+        k = max(1, self.tilt_pieces())
+        h = np.zeros(self.n * k, np.float32)
         _check(self._lib.mlmc_export_h(self._h, _ptr(h)))
-        return h
+        return h if k == 1 else h.reshape(k, self.n)
 
     def learn_report(self):
         """mlmc_plan_learn_report: (index of the installed law, per-walk
@@ -438,25 +467,27 @@ class Plan:
                                              ct.cast(exchange, ct.c_void_p), None, _ptr(buf),
                                              int(cap)))
 
-    def export_tilt(self) -> dict:
-        """The tilted clocks' tables: lam, dl, inv_rate (float64), inv_rate32,
-        dl32 (float32), still32 (int32)."""
+    def export_tilt(self, piece: int = 0) -> dict:
+        """The tilted clocks' tables (of time piece ``piece``): lam, dl,
+        inv_rate (float64), inv_rate32, dl32 (float32), still32 (int32, the
+        row's threshold for the whole law)."""
         n = self.n
         out = dict(lam=np.zeros(n), dl=np.zeros(n), inv_rate=np.zeros(n),
                    inv_rate32=np.zeros(n, np.float32), dl32=np.zeros(n, np.float32),
                    still32=np.zeros(n, np.int32))
         keys = ["lam", "dl", "inv_rate", "inv_rate32", "dl32", "still32"]
-        _check(self._lib.mlmc_export_tilt(self._h, *[_ptr(out[k]) for k in keys]))
+        _check(self._lib.mlmc_export_tilt_piece(self._h, int(piece), *[_ptr(out[k]) for k in keys]))
         return out
 
-    def export_proposal(self) -> dict:
+    def export_proposal(self, piece: int = 0) -> dict:
         m = max(self.nnz, 1)
         out = dict(thr=np.zeros(m, np.uint32), keep_col=np.full(m, -1, np.int32),
                    keep_neg=np.zeros(m, np.uint8), alias_col=np.full(m, -1, np.int32),
                    alias_neg=np.zeros(m, np.uint8), lr_keep=np.zeros(m, np.float32),
                    lr_alias=np.zeros(m, np.float32))
         keys = ["thr", "keep_col", "keep_neg", "alias_col", "alias_neg", "lr_keep", "lr_alias"]
-        _check(self._lib.mlmc_export_proposal(self._h, *[_ptr(out[k]) for k in keys]))
+        _check(self._lib.mlmc_export_proposal_piece(self._h, int(piece),
+                                                    *[_ptr(out[k]) for k in keys]))
         return out
 
     def info(self) -> dict:
@@ -641,12 +672,18 @@ class MLP:
 
     def learn_tilt(self, plan, v, seed: int, pilot_walks: int = 256, steps: int = 300,
                    batch: int = 8192, lr: float = 3e-3, alpha: float = 0.1,
-                   clocks: bool = True, rounds: int = 2) -> float:
+                   clocks: bool = True, rounds: int = 2, time_pieces: bool = False) -> float:
         """mlmc_learn_tilt: `rounds` pilot-train-install rounds of a proposal
-        with tilted jumps and (clocks) holding times; returns the last loss."""
+        with tilted jumps and (clocks) holding times; with ``time_pieces``
+        (and clocks) laws that change with time are candidates too.  Returns
+        the last loss."""
         _need(v, 8 * plan.n, "v")
         loss = np.zeros(1, np.float32)
         tilt = TILT_JUMPS | (TILT_CLOCKS if clocks else 0)
+        if time_pieces:
+            if not clocks:
+                raise ValueError("time pieces need tilted clocks")
+            tilt |= TILT_TIME
         _check(self._lib.mlmc_learn_tilt(plan.handle, self._h, _ptr(v), ct.c_uint64(seed),
                                          pilot_walks, steps, batch, ct.c_float(lr), float(alpha),
                                          tilt, rounds, _ptr(loss)))

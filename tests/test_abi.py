@@ -85,7 +85,8 @@ def test_every_entry_point_refuses_null_handles(lib):
     # sizes, returns INVALID_ARG with a message and does no device work.
     from paper_1904_12754_gb300 import mlmc
     skip = {"mlmc_last_error", "mlmc_launch_count", "mlmc_plan_destroy", "mlmc_batch_destroy",
-            "mlmc_mlp_destroy"}
+            "mlmc_mlp_destroy", "mlmc_plan_tilt_pieces"}
+    assert lib.mlmc_plan_tilt_pieces(None) == 0     # a count, not a status: 0 for no plan
     called = 0
     for name in _declared():
         fn = getattr(lib, name)
