@@ -178,12 +178,20 @@ __global__ void k_build_tables(int64_t n, double t, const int64_t* __restrict__ 
 // every entry's lr gains log(L_ii / lambda_i), the clock's likelihood ratio
 // per jump.  The same IEEE operations in the same order as the host
 // definition, so the records are identical bit for bit.
-__global__ void k_build_is_tables(int64_t n, const int64_t* __restrict__ row_ptr,
+__global__ void k_build_is_tables(int64_t n, int64_t nnz, const int64_t* __restrict__ row_ptr,
                                   const int32_t* __restrict__ col, const double* __restrict__ val,
                                   const double* __restrict__ lii, const float* __restrict__ h,
                                   double alpha, AliasEntryIS* __restrict__ alias, bool clocks,
                                   double t, Meta32* __restrict__ m32t, Meta64* __restrict__ m64t,
                                   double* __restrict__ lam_out) {
+  // grid.y: the time piece (reading R19) whose h, entries, records and rates
+  // sit piece n (entries: piece nnz) after piece 0's
+  const int64_t kp = blockIdx.y;
+  h += kp * n;
+  alias += kp * nnz;
+  if (m32t) m32t += kp * n;
+  if (m64t) m64t += kp * n;
+  if (lam_out) lam_out += kp * n;
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int64_t rb = row_ptr[i];
@@ -465,7 +473,7 @@ __global__ void __launch_bounds__(kHeavyBlock)
 
 __global__ void __launch_bounds__(kHeavyBlock)
     k_build_is_tables_heavy(const int32_t* __restrict__ list, const uint32_t* __restrict__ count,
-                            int cap, const int64_t* __restrict__ row_ptr,
+                            int cap, int64_t n, int64_t nnz, const int64_t* __restrict__ row_ptr,
                             const int32_t* __restrict__ col,
                             const double* __restrict__ val, const double* __restrict__ lii,
                             const float* __restrict__ h, double alpha,
@@ -478,6 +486,13 @@ __global__ void __launch_bounds__(kHeavyBlock)
   int32_t* ali = reinterpret_cast<int32_t*>(hs + cap * 12);
   float* lrs = reinterpret_cast<float*>(hs + cap * 16);
   __shared__ double s_hsum, s_lr_clock;
+  // grid.y: the time piece, as in k_build_is_tables
+  const int64_t kp = blockIdx.y;
+  h += kp * n;
+  alias += kp * nnz;
+  if (m32t) m32t += kp * n;
+  if (m64t) m64t += kp * n;
+  if (lam_out) lam_out += kp * n;
   const uint32_t rows = *count;
   for (uint32_t it = blockIdx.x; it < rows; it += gridDim.x) {
     const int64_t i = list[it];
@@ -721,23 +736,22 @@ cudaError_t launch_build_is_tables(mlmc_plan* p) {
   if (err != cudaSuccess) return err;
   // One table set per time piece (one piece without a time-dependent law):
   // piece k's h, entries, records and rates sit k n (k nnz) after piece 0's.
+  // (all pieces in one launch: grid.y = pieces)
   const int pieces = p->clock_tilt ? p->pieces : 1;
-  for (int k = 0; k < pieces; ++k) {
-    const int64_t kn = static_cast<int64_t>(k) * p->n, ke = static_cast<int64_t>(k) * p->nnz;
-    k_build_is_tables<<<grid_for(p, p->n, kBuildBlock), kBuildBlock, 0, p->stream>>>(
-        p->n, p->d_row_ptr, p->d_col, p->d_val, p->d_lii, p->d_h + kn, p->alpha, p->d_alias_is + ke,
-        p->clock_tilt, p->t, p->d_meta32_t + kn, p->d_meta64_t + kn, p->d_lam + kn);
+  k_build_is_tables<<<dim3(grid_for(p, p->n, kBuildBlock), pieces), kBuildBlock, 0, p->stream>>>(
+      p->n, p->nnz, p->d_row_ptr, p->d_col, p->d_val, p->d_lii, p->d_h, p->alpha, p->d_alias_is,
+      p->clock_tilt, p->t, p->d_meta32_t, p->d_meta64_t, p->d_lam);
+  p->launches++;
+  if (p->heavy_count > 0) {
+    static std::atomic<uint64_t> attr{0};
+    err = ensure_dynamic_smem(k_build_is_tables_heavy, static_cast<int>(heavy_smem_is(kHeavyHi)), attr);
+    if (err != cudaSuccess) return err;
+    k_build_is_tables_heavy<<<dim3(heavy_grid(p), pieces), kHeavyBlock, heavy_smem_is(p->heavy_cap),
+                              p->stream>>>(
+        p->d_heavy, p->d_heavy_count, p->heavy_cap, p->n, p->nnz, p->d_row_ptr, p->d_col, p->d_val,
+        p->d_lii, p->d_h, p->alpha, p->d_alias_is, p->clock_tilt, p->t, p->d_meta32_t, p->d_meta64_t,
+        p->d_lam);
     p->launches++;
-    if (p->heavy_count > 0) {
-      static std::atomic<uint64_t> attr{0};
-      err = ensure_dynamic_smem(k_build_is_tables_heavy, static_cast<int>(heavy_smem_is(kHeavyHi)), attr);
-      if (err != cudaSuccess) return err;
-      k_build_is_tables_heavy<<<heavy_grid(p), kHeavyBlock, heavy_smem_is(p->heavy_cap), p->stream>>>(
-          p->d_heavy, p->d_heavy_count, p->heavy_cap, p->d_row_ptr, p->d_col, p->d_val, p->d_lii,
-          p->d_h + kn, p->alpha, p->d_alias_is + ke, p->clock_tilt, p->t, p->d_meta32_t + kn,
-          p->d_meta64_t + kn, p->d_lam + kn);
-      p->launches++;
-    }
   }
   if (p->clock_tilt && p->sched.precision != MLMC_FP64) {
     const int64_t blocks = (p->n + 7) / 8;
