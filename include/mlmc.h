@@ -603,7 +603,10 @@ mlmc_status mlmc_learn_proposal(mlmc_plan *plan, mlmc_mlp *mlp, const double *v,
  * min(8, 2^l0) time pieces (mlmc_plan_set_tilt_pieces) with h_p the same
  * Taylor value at the time left in the middle of piece p, sum_{m<=3}
  * ((1 - s_p) t|N|)^m |v| / m! (+ 1e-3 max|v|); walked last, its tables are
- * already built when it is the law installed.
+ * already built when it is the law installed.  It costs more per walk (its
+ * carry-overs, K table sets), so it is installed only when its variance
+ * times its pilot's walk time per walk (CUDA events around the launch) is
+ * below the best law's: the work to reach a given error.
  * Backward-mode plans only. */
 mlmc_status mlmc_learn_tilt(mlmc_plan *plan, mlmc_mlp *mlp, const double *v, uint64_t seed,
                             int64_t pilot_walks, int32_t steps, int32_t batch, float lr,

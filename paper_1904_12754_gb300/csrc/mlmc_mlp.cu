@@ -1273,7 +1273,10 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
   double* stats = nullptr;        // a pilot's per-block partial sums (k_pilot_stats)
   __nv_bfloat16* wfeat = nullptr;
   float* wy = nullptr;
+  cudaEvent_t ev_a = nullptr, ev_b = nullptr;  // a pilot's walk launch, timed
   auto cleanup = [&]() {
+    if (ev_a) cudaEventDestroy(ev_a);
+    if (ev_b) cudaEventDestroy(ev_b);
     cudaFree(best_h);
     cudaFree(hp);
     cudaFree(xwarm);
@@ -1300,6 +1303,8 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
       return mfail(MLMC_ERR_CUDA, msg_);                                                       \
     }                                                                                          \
   } while (0)
+  LP_CUDA(cudaEventCreate(&ev_a), "event");
+  LP_CUDA(cudaEventCreate(&ev_b), "event");
   LP_CUDA(cudaMalloc(&sums, sizeof(double) * (p->n + kTotSlots)), "alloc");
   LP_CUDA(cudaMalloc(&dv, sizeof(double) * p->n), "alloc");
   LP_CUDA(cudaMalloc(&feat, sizeof(__nv_bfloat16) * p->n * kIn), "alloc");
@@ -1388,6 +1393,9 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
   // rep_begin + reps) of every row.  Leaves x-hat (the per-row means) in
   // sums, its largest magnitude in *xmax, and the per-walk variance of the
   // law (the rows' sample variances, averaged over the rows) in *var.
+  // The pilot's walk time per walk (ms), from CUDA events on the plan's
+  // stream around its launch.
+  double pilot_cost = 0.0;
   auto pilot = [&](int64_t rep_begin, int64_t reps, double* xmax, double* var) -> cudaError_t {
     cudaError_t e = cudaMemsetAsync(sums, 0, sizeof(double) * (p->n + kTotSlots), p->stream);
     if (e != cudaSuccess) return e;
@@ -1400,7 +1408,9 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
     w.v = dv;
     w.sum_y = sums;
     w.totals = sums + p->n;
+    if ((e = cudaEventRecord(ev_a, p->stream)) != cudaSuccess) return e;
     if ((e = launch_walk(p, w)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(ev_b, p->stream)) != cudaSuccess) return e;
     // x-hat in place and the variance's sums on the device; only the
     // partials and the sum of squares come back
     k_pilot_stats<<<kStatBlocks, 256, 0, p->stream>>>(p->n, 1.0 / static_cast<double>(reps), sums,
@@ -1424,12 +1434,18 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
     *var = reps > 1 ? (hs[2 * kStatBlocks] - sq) / static_cast<double>(reps - 1) /
                           static_cast<double>(p->n)
                     : std::numeric_limits<double>::infinity();
+    float ms = 0.0f;
+    if ((e = cudaEventElapsedTime(&ms, ev_a, ev_b)) != cudaSuccess) return e;
+    pilot_cost = static_cast<double>(ms) / (static_cast<double>(reps) * static_cast<double>(p->n));
     return cudaSuccess;
   };
   // Every pilot measures the law it walks with; the law with the smallest
   // measured variance is the one installed at the end (for jumps only the
-  // paper's walk, h = 1, is a candidate too).
+  // paper's walk, h = 1, is a candidate too).  A law with time pieces costs
+  // more per walk (its carry-overs, K sets of tables): it has to win on
+  // variance x the pilot's walk time per walk, the work to a given error.
   double best_var = std::numeric_limits<double>::infinity();
+  double best_cost = 0.0;
   p->learn_var.clear();
   p->learn_choice = -1;
   int64_t next_rep = 0;
@@ -1438,8 +1454,10 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
   // stays installed when it wins).
   auto consider = [&](double var, const float* src, int32_t pieces) -> cudaError_t {
     p->learn_var.push_back(var);
-    if (!(var < best_var)) return cudaSuccess;
+    const bool better = pieces > 1 ? var * pilot_cost < best_var * best_cost : var < best_var;
+    if (!better) return cudaSuccess;
     best_var = var;
+    best_cost = pilot_cost;
     p->learn_choice = static_cast<int32_t>(p->learn_var.size()) - 1;
     best_pieces = pieces;
     return src ? cudaMemcpyAsync(best_h, src, sizeof(float) * p->n * static_cast<size_t>(pieces),
@@ -1535,7 +1553,8 @@ mlmc_status mlmc_learn_tilt(mlmc_plan* p, mlmc_mlp* m, const double* v, uint64_t
       // pieces, h_p the Taylor value of exp((1 - s_p) t|N|)|v| at the middle
       // s_p of piece p, the zero-variance h(s) = exp((1-s)tA)v that one law
       // can only average over time.  More pieces never measured a larger
-      // variance, so only the largest is tried.
+      // variance, so only the largest is tried; it is installed when its
+      // variance x walk time per walk is below the best single law's.
       const int32_t k_p = max_warm_pieces;
       k_piece_h<<<g, 256, 0, p->stream>>>(p->n, k_p, pv + 6 * p->n, pv + 8 * p->n, pv + 9 * p->n,
                                           pv + 10 * p->n, static_cast<float>(1e-3 * vmax + 1e-30), hp);
