@@ -382,10 +382,11 @@ def run_ours(args):
 
     peaks, peak_kind = _peaks()
     # the law of the last timed step: the capture constants describe the
-    # one-law kernel, and a law with time pieces runs its own variant
+    # one-law kernel and the 8-piece one (a law with time pieces runs its
+    # own variant)
     pieces = learn_log[args.warmup + args.steps - 1][2]
     roof = walk_roofline(level_log, walk_s, clocks, peaks, total_ms, proposal=True,
-                         capture=w.name.startswith("ba_n100000_m4") and pieces <= 1,
+                         capture=w.name.startswith("ba_n100000_m4") and pieces in (1, 8),
                          pieces=pieces)
 
     # The plain walk on the same plan and budget: its error estimate after
@@ -507,7 +508,17 @@ ISSUE_CAPTURE = {"issue_active": 0.761, "threads_per_instruction": 26.78,
                  "warp_instructions_per_event": 3.10, "l2_hit": 0.983,
                  "dram_bytes_per_event": 0.055, "launch_ms": 1.755,
                  "capture": "k_walk<FP32, proposal> at l0, BA n=1e5, 4096 walks per row, "
-                            "bench.py --workload kernel --kernel-tilt"}
+                            "bench.py --workload kernel --kernel-tilt --time-pieces 0"}
+# The same capture of the walk with the learned law of 8 time pieces (the law
+# the default step installs on this graph): the same launch (4.1e8 walks,
+# 1.16e8 jumps, 5.26e8 events).  Its 8 table sets (218 MB) exceed L2, so
+# the tables are read from DRAM about five times over.
+TRAFFIC_CAPTURE_PIECES = 1.278e9
+ISSUE_CAPTURE_PIECES = {"issue_active": 0.701, "threads_per_instruction": 17.50,
+                        "warp_instructions_per_event": 8.71, "l2_hit": 0.891,
+                        "dram_bytes_per_event": 2.43, "launch_ms": 5.816,
+                        "capture": "k_walk<FP32, proposal, 8 time pieces> at l0, BA n=1e5, 4096 "
+                                   "walks per row, bench.py --workload kernel --kernel-tilt"}
 
 
 def walk_roofline(level_log, walk_s, clocks, peaks, total_ms, num_sms=None, proposal=False,
@@ -543,7 +554,7 @@ def walk_roofline(level_log, walk_s, clocks, peaks, total_ms, num_sms=None, prop
     gather_gbs = gather / walk_s / 1e9 if walk_s > 0 else 0.0
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s",
             "frac": achieved / peak if peak else None,
-            "traffic": TRAFFIC_CAPTURE if capture else None,
+            "traffic": (TRAFFIC_CAPTURE_PIECES if pieces == 8 else TRAFFIC_CAPTURE) if capture else None,
             "traffic_per": ("launch of 4.1e8 walks at l0 after an L2 flush (the capture's launch)"
                             if capture else None),
             "kernel": "k_walk<FP32%s%s> (mlmc_walk.cu)" % (
@@ -551,7 +562,7 @@ def walk_roofline(level_log, walk_s, clocks, peaks, total_ms, num_sms=None, prop
                 f", {pieces} time pieces" if pieces > 1 else ""),
             "peak_source": f"{num_sms} SMs x 128 lanes x {sm_mhz:.0f} MHz (SM count of the device, "
                            "median SM clock sampled in the run)",
-            "issue": ISSUE_CAPTURE if capture else None,
+            "issue": (ISSUE_CAPTURE_PIECES if pieces == 8 else ISSUE_CAPTURE) if capture else None,
             "ops_per_event": ops / events if events else None,
             "walk_launches": launches,
             "avg_launch_ms": 1e3 * walk_s / launches if launches else None,
@@ -866,10 +877,11 @@ def run_kernel_workload(args):
                still_walks=res["l0"]["still_walks"], launches=1)]
     # the op model and its ALU peak describe the FP32 walk; the FP64 walk is
     # bound by the FP64 pipe (its counters are in the kernel's ncu summary)
+    pieces = plan.tilt_pieces() if args.kernel_tilt else 1
     roof = walk_roofline(lv, 1e-3 * statistics.mean(res["l0"]["launch_ms"]), clocks, peaks,
                          statistics.mean(res["l0"]["launch_ms"]), proposal=args.kernel_tilt,
-                         capture=args.kernel_tilt and args.kernel_matrix == "ba"
-                         ) if w.precision == "fp32" else None
+                         capture=args.kernel_tilt and args.kernel_matrix == "ba" and pieces in (1, 8),
+                         pieces=pieces) if w.precision == "fp32" else None
     out = {"metric": "walk kernel alone: walk-steps/s at l0 (one launch, L2 flushed before it)",
            "value": res["l0"]["events_per_s"], "unit": UNIT, "higher_is_better": True,
            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
