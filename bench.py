@@ -85,6 +85,25 @@ def aggregate_over_ranks(dist, elapsed: float, count: float, device="cpu"):
     return float(tmax[0]), float(t[1])
 
 
+def share_law(plan, dist, rank: int, coll="cpu"):
+    """Install rank 0's learned law on every rank of a sharded solve: its
+    time pieces K, then its h (K x n), both broadcast from rank 0 (the ranks
+    must walk the same law)."""
+    import torch
+    k = torch.tensor([plan.tilt_pieces()], dtype=torch.int64, device=coll)
+    dist.broadcast(k, 0)
+    k = int(k.item())
+    h = torch.zeros((k, plan.n), dtype=torch.float32, device=coll)
+    if rank == 0:
+        h.copy_(torch.from_numpy(np.asarray(plan.export_h()).reshape(k, plan.n)))
+    dist.broadcast(h, 0)
+    hh = h.cpu().numpy() if coll == "cpu" else h
+    if k > 1:
+        plan.set_tilt_pieces(hh, 0.1)
+    else:
+        plan.set_tilt(hh.reshape(plan.n), 0.1, clocks=True)
+
+
 def _workload():
     import mlmc_inputs as I
     return I.workload_c2()
@@ -293,19 +312,7 @@ def run_ours(args):
             mlp_launches[0] += net.launch_count()
         learn_log.append(plan.learn_report() + (plan.tilt_pieces(),))
         if dist is not None:
-            # rank 0's law on every rank: its time pieces, then its h
-            k = torch.tensor([plan.tilt_pieces()], dtype=torch.int64, device=coll)
-            dist.broadcast(k, 0)
-            k = int(k.item())
-            h = torch.zeros((k, plan.n), dtype=torch.float32, device=coll)
-            if rank == 0:
-                h.copy_(torch.from_numpy(plan.export_h().reshape(k, plan.n)))
-            dist.broadcast(h, 0)
-            hh = h.cpu().numpy() if coll == "cpu" else h
-            if k > 1:
-                plan.set_tilt_pieces(hh, 0.1)
-            else:
-                plan.set_tilt(hh.reshape(plan.n), 0.1, clocks=True)
+            share_law(plan, dist, rank, coll)
         rc = plan.expmv(v_in, x_out, seed, allow_not_converged=True)
         levels, est = plan.stats()
         plan.set_tilt(None)
