@@ -724,23 +724,26 @@ mlmc_status mlmc_export_tilt_piece(const mlmc_plan* pc, int32_t piece, double* l
   if (piece < 0 || piece >= p->pieces)
     return fail(MLMC_ERR_INVALID_ARG, "mlmc_export_tilt_piece: piece out of range");
   const size_t n = static_cast<size_t>(p->n);
+  const size_t k = static_cast<size_t>(p->pieces);
   const size_t off = static_cast<size_t>(piece) * n;
-  std::vector<Meta32> m32(n);
-  std::vector<Meta64> m64(n);
+  // the records are state-major (row i's record of piece q at i K + q)
+  std::vector<Meta32> m32(n * k);
+  std::vector<Meta64> m64(n * k);
   std::vector<double> lm(n);
   std::vector<int32_t> st(n);
-  MLMC_CUDA(cudaMemcpyAsync(m32.data(), p->d_meta32_t + off, sizeof(Meta32) * n, cudaMemcpyDeviceToHost, p->stream), "copy");
-  MLMC_CUDA(cudaMemcpyAsync(m64.data(), p->d_meta64_t + off, sizeof(Meta64) * n, cudaMemcpyDeviceToHost, p->stream), "copy");
+  MLMC_CUDA(cudaMemcpyAsync(m32.data(), p->d_meta32_t, sizeof(Meta32) * n * k, cudaMemcpyDeviceToHost, p->stream), "copy");
+  MLMC_CUDA(cudaMemcpyAsync(m64.data(), p->d_meta64_t, sizeof(Meta64) * n * k, cudaMemcpyDeviceToHost, p->stream), "copy");
   MLMC_CUDA(cudaMemcpyAsync(lm.data(), p->d_lam + off, sizeof(double) * n, cudaMemcpyDeviceToHost, p->stream), "copy");
   if (p->sched.precision != MLMC_FP64)
     MLMC_CUDA(cudaMemcpyAsync(st.data(), p->d_still32_t, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, p->stream), "copy");
   MLMC_CUDA(cudaStreamSynchronize(p->stream), "synchronize");
   for (size_t i = 0; i < n; ++i) {
+    const size_t r = i * k + static_cast<size_t>(piece);
     if (lam) lam[i] = lm[i];
-    if (dl) dl[i] = m64[i].dl;
-    if (inv_rate) inv_rate[i] = m64[i].inv_rate;
-    if (inv_rate32) inv_rate32[i] = m32[i].inv_rate;
-    if (dl32) dl32[i] = m32[i].dl;
+    if (dl) dl[i] = m64[r].dl;
+    if (inv_rate) inv_rate[i] = m64[r].inv_rate;
+    if (inv_rate32) inv_rate32[i] = m32[r].inv_rate;
+    if (dl32) dl32[i] = m32[r].dl;
     if (still32) still32[i] = p->sched.precision != MLMC_FP64 ? st[i] : -1;
   }
   return MLMC_OK;

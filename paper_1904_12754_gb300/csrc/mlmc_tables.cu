@@ -184,13 +184,13 @@ __global__ void k_build_is_tables(int64_t n, int64_t nnz, const int64_t* __restr
                                   double alpha, AliasEntryIS* __restrict__ alias, bool clocks,
                                   double t, Meta32* __restrict__ m32t, Meta64* __restrict__ m64t,
                                   double* __restrict__ lam_out) {
-  // grid.y: the time piece (reading R19) whose h, entries, records and rates
-  // sit piece n (entries: piece nnz) after piece 0's
-  const int64_t kp = blockIdx.y;
+  // grid.y: the time piece (reading R19).  Its h, entries and rates sit
+  // piece n (entries: piece nnz) after piece 0's; the row records are
+  // state-major, row i's record of piece kp at i K + kp (K = gridDim.y), so
+  // that a walk's later pieces of one state share its cache line.
+  const int64_t kp = blockIdx.y, kk = gridDim.y;
   h += kp * n;
   alias += kp * nnz;
-  if (m32t) m32t += kp * n;
-  if (m64t) m64t += kp * n;
   if (lam_out) lam_out += kp * n;
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
@@ -229,7 +229,7 @@ __global__ void k_build_is_tables(int64_t n, int64_t nnz, const int64_t* __restr
       m32.deg = k;
       m32.inv_rate = __double2float_rn(inv_rate);
       m32.dl = __double2float_rn(dl);
-      m32t[i] = m32;
+      m32t[i * kk + kp] = m32;
       Meta64 m64;
       m64.start = static_cast<int32_t>(rb);
       m64.deg = k;
@@ -237,7 +237,7 @@ __global__ void k_build_is_tables(int64_t n, int64_t nnz, const int64_t* __restr
       m64.pad1 = 0;
       m64.inv_rate = inv_rate;
       m64.dl = dl;
-      m64t[i] = m64;
+      m64t[i * kk + kp] = m64;
       lam_out[i] = lam;
     }
     if (k == 0) continue;
@@ -486,12 +486,10 @@ __global__ void __launch_bounds__(kHeavyBlock)
   int32_t* ali = reinterpret_cast<int32_t*>(hs + cap * 12);
   float* lrs = reinterpret_cast<float*>(hs + cap * 16);
   __shared__ double s_hsum, s_lr_clock;
-  // grid.y: the time piece, as in k_build_is_tables
-  const int64_t kp = blockIdx.y;
+  // grid.y: the time piece, as in k_build_is_tables (records state-major)
+  const int64_t kp = blockIdx.y, kk = gridDim.y;
   h += kp * n;
   alias += kp * nnz;
-  if (m32t) m32t += kp * n;
-  if (m64t) m64t += kp * n;
   if (lam_out) lam_out += kp * n;
   const uint32_t rows = *count;
   for (uint32_t it = blockIdx.x; it < rows; it += gridDim.x) {
@@ -530,7 +528,7 @@ __global__ void __launch_bounds__(kHeavyBlock)
         m32.deg = k;
         m32.inv_rate = __double2float_rn(inv_rate);
         m32.dl = __double2float_rn(dl);
-        m32t[i] = m32;
+        m32t[i * kk + kp] = m32;
         Meta64 m64;
         m64.start = static_cast<int32_t>(rb);
         m64.deg = k;
@@ -538,7 +536,7 @@ __global__ void __launch_bounds__(kHeavyBlock)
         m64.pad1 = 0;
         m64.inv_rate = inv_rate;
         m64.dl = dl;
-        m64t[i] = m64;
+        m64t[i * kk + kp] = m64;
         lam_out[i] = lam;
       }
       s_hsum = hsum;
@@ -650,7 +648,7 @@ __global__ void __launch_bounds__(256) k_still_index(int64_t n, const Meta32* __
 }
 
 // The same with time pieces (reading R19): row i's records of the K pieces
-// are meta[p n + i]; screened rows are those whose first piece has
+// are meta[i K + p]; screened rows are those whose first piece has
 // 1/(t lambda) >= 1.
 __global__ void __launch_bounds__(256) k_still_index_pieces(int64_t n, const Meta32* __restrict__ meta,
                                                             int k_pieces, int32_t* __restrict__ still) {
@@ -661,7 +659,7 @@ __global__ void __launch_bounds__(256) k_still_index_pieces(int64_t n, const Met
        i += warps) {
     float ir[kMaxPieces];
 #pragma unroll
-    for (int p = 0; p < kMaxPieces; ++p) ir[p] = p < k_pieces ? meta[p * n + i].inv_rate : 1.0f;
+    for (int p = 0; p < kMaxPieces; ++p) ir[p] = p < k_pieces ? meta[i * k_pieces + p].inv_rate : 1.0f;
     const int32_t k = ir[0] >= 1.0f ? still_index32_pieces(ir, k_pieces, inv_k, lane) : -1;
     if (lane == 0) still[i] = k;
   }

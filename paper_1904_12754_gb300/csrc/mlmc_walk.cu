@@ -471,14 +471,16 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
   const T n_fine = P::from_int(n_grid);
   const T inv_n = static_cast<T>(1.0 / n_grid);  // exact: a power of two
   const int n_coarse = n_grid >> 1;
-  const Meta m0 = load_meta(meta, row);
-  const T dl0 = static_cast<T>(m0.dl);
-  const T inv_rate0 = static_cast<T>(m0.inv_rate);
-  // Time pieces (proposal walks, R19): piece p's row records and alias
-  // entries follow piece p-1's, n and nnz apart; a pending jump time that
-  // reaches the current piece's end b_next is carried into the next piece.
+  // Time pieces (proposal walks, R19): piece p's alias entries follow
+  // piece p-1's, nnz apart; the row records are state-major, state j's record
+  // of piece p at j K + p (one cache line for a state's pieces); a pending
+  // jump time that reaches the current piece's end b_next is carried into
+  // the next piece.
   static_assert(!PIECES || (IS && !SRC && !TIMES), "time pieces: proposal walks without source or times");
   const int n_pieces = PIECES ? a.pieces : 1;
+  const Meta m0 = load_meta(meta, row * n_pieces);
+  const T dl0 = static_cast<T>(m0.dl);
+  const T inv_rate0 = static_cast<T>(m0.inv_rate);
   const int g_per = n_grid / n_pieces;  // fine grid points per piece (K divides N)
   const T inv_pieces = P::div(static_cast<T>(1), P::from_int(n_pieces));  // exact: K = 2^k
   const T b_first = n_pieces > 1 ? inv_pieces : P::inf();
@@ -504,7 +506,7 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
     if (PIECES && n_pieces > 1) {
       T sum = dl0;
       for (int pp = 1; pp < n_pieces; ++pp)
-        sum = P::add(sum, static_cast<T>(load_meta(meta + static_cast<int64_t>(pp) * a.n, row).dl));
+        sum = P::add(sum, static_cast<T>(load_meta(meta, row * n_pieces + pp).dl));
       dl_still = P::mul(sum, inv_pieces);
     }
     y_still = P::mul(static_cast<T>(__ldg(vv + row)), P::ex(dl_still));
@@ -691,7 +693,8 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
     neg ^= pick >> 31;
     j = static_cast<int32_t>(pick & kColMask);
     if (TRACE) hash = (hash ^ static_cast<uint32_t>(j)) * 16777619u;
-    m = IS ? load_meta(meta + (PIECES ? static_cast<int64_t>(pc) * a.n : 0), j) : mnext;
+    m = IS ? load_meta(meta, PIECES ? static_cast<int64_t>(j) * n_pieces + pc : static_cast<int64_t>(j))
+           : mnext;
     s = s_new;
     ++e;
     return true;
@@ -703,7 +706,7 @@ __device__ __forceinline__ void walk_item(const ItemArgs& a, const Keys& keys, i
   auto carry = [&](T& s_at) {
     if constexpr (PIECES) {
       while (pc + 1 < n_pieces && s_at >= b_next) {
-        const Meta mn = load_meta(meta + static_cast<int64_t>(pc + 1) * a.n, j);
+        const Meta mn = load_meta(meta, static_cast<int64_t>(j) * n_pieces + pc + 1);
         const T ir = static_cast<T>(m.inv_rate), irn = static_cast<T>(mn.inv_rate);
         s_at = (isinf(ir) || isinf(irn)) ? P::inf()
                                           : P::fma(P::sub(s_at, b_next), P::div(irn, ir), b_next);
