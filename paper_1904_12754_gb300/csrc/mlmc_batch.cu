@@ -373,6 +373,9 @@ mlmc_status mlmc_batch_create(mlmc_batch** out, mlmc_plan* const* plans, int32_t
       return bail(bfail(MLMC_ERR_INVALID_ARG, "mlmc_batch_create: backward-mode plans only"));
     if (p->source_active)
       return bail(bfail(MLMC_ERR_INVALID_ARG, "mlmc_batch_create: plans with a source term are not batched"));
+    if (p->proposal_active && p->pieces > 1)
+      return bail(bfail(MLMC_ERR_INVALID_ARG,
+                        "mlmc_batch_create: proposals with time pieces are not batched"));
     if ((p->sched.precision == MLMC_FP64) != b->fp64)
       return bail(bfail(MLMC_ERR_INVALID_ARG, "mlmc_batch_create: plans differ in precision"));
     if (p->device != plans[0]->device)
