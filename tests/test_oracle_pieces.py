@@ -166,3 +166,36 @@ def test_time_pieces_cut_the_variance_on_ba_graphs():
             hs = [_taylor_h(ad, t, v, 1.0 - (p + 0.5) / k) for p in range(k)]
             got[k] = relvar(_laws(ad, t, hs), level)
         assert got[2] < base / 2.5 and got[4] < base / 8.0, (level, base, got)
+
+
+@pytest.mark.parametrize("precision", [W.FP64, W.FP32])
+def test_rows_without_off_diagonals_keep_their_walks(precision):
+    # a row with no off-diagonal entries has rate 0 in every piece (inverse
+    # rate infinite): its walks never jump, the carry-over keeps their
+    # pending time infinite, and the sample is v_i e^{t a_ii} exactly; the
+    # other rows still match the exact moments
+    import scipy.sparse as sp
+    base = I.random_sparse(8, 3, seed=14, signed=True, diag=True).dense()
+    base[3, :] = 0.0
+    base[3, 3] = -0.7
+    a = I.to_csr(sp.csr_matrix(base))
+    ad = a.dense()
+    t = 0.6
+    v = np.random.default_rng(4).random(8) + 0.1
+    hs = _hs(a.n, 4, 5)
+    m1, _ = R.level_moments_pieces(ad, t, v, 2, False, _laws(ad, t, hs))
+    tb = W.build_tables_pieces(a, t, hs, 0.1)
+    assert np.all(np.isinf(tb.inv_rate.reshape(4, a.n)[:, 3]))
+    reps = 1 << 15
+    wk = W.Walker(a, t, v, seed=9, precision=precision, tables=tb)
+    rec = wk.walks(np.repeat(np.arange(a.n), reps), np.tile(np.arange(reps), a.n), 2, False)
+    assert np.all(rec["status"] == 0)
+    y = rec["y"].reshape(a.n, reps)
+    jumps = rec["jumps"].reshape(a.n, reps)
+    assert np.all(jumps[3] == 0)
+    assert np.allclose(y[3], v[3] * np.exp(-0.7 * t), rtol=1e-12 if precision == W.FP64 else 1e-6)
+    assert abs(m1[3] - v[3] * np.exp(-0.7 * t)) <= 1e-12 * v[3]
+    others = [i for i in range(a.n) if i != 3]
+    sd = y[others].std(axis=1) / np.sqrt(reps)
+    z = (y[others].mean(axis=1) - m1[others]) / np.maximum(sd, 1e-300)
+    assert np.all(np.abs(z) < 4.5), z
